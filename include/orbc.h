@@ -1,0 +1,197 @@
+/*
+ * orbc.h -- C ABI of the GB300-native Voronoi-cell-list CGMD hot path of
+ * OpenRBC (Tang, Lu, Li, Evangelinos, Grinberg, Sachdeva & Karniadakis,
+ * arXiv 1701.02059).
+ *
+ * The calls follow the paper's statement of the problem: set up a system,
+ * build the adaptive Voronoi cell list, evaluate forces and torques, and
+ * advance positions and orientations ("Software Overview": time-stepping
+ * loop of force and torque followed by the update of position and
+ * orientation; "Spatial Searching Algorithm": group particles into adaptive
+ * clusters, compute interactions between neighbouring clusters, update the
+ * cluster composition, repeat).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an orbc_status; no C++ exception crosses the ABI.
+ *   - Pointers named host_* or documented as host pointers are read or
+ *     written synchronously and stay owned by the caller.  The library owns
+ *     every device allocation it makes and frees it in orbc_destroy /
+ *     orbc_arena_destroy.
+ *   - Arrays of 3-vectors are row-major [n][3] doubles.  Getters write in
+ *     particle-id order (ids are 0..n-1).
+ *   - Units are reduced: sigma (length), epsilon (energy), tau (time).
+ *   - The state is held on a fixed-point grid of 2^-40 (sigma, sigma/tau,
+ *     1, 1/tau): inputs are rounded to it (round-half-even) and every value
+ *     read back is an exact double.
+ *   - A failed call leaves the handle usable unless it returns
+ *     ORBC_E_STATE; orbc_last_error() describes the last failure.
+ *   - Calls on one handle are not thread-safe; distinct handles are
+ *     independent.  Work is issued on the stream given at creation and every
+ *     call that returns data to the host synchronises that stream.
+ */
+#ifndef ORBC_H
+#define ORBC_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define ORBC_API __attribute__((visibility("default")))
+#else
+#define ORBC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ORBC_OK = 0,
+    ORBC_E_ARG = -1,       /* invalid argument (null pointer, size, NaN, range) */
+    ORBC_E_NOMEM = -2,     /* device allocation failed or HBM budget exceeded   */
+    ORBC_E_CUDA = -3,      /* CUDA runtime error                                */
+    ORBC_E_STATE = -4,     /* call out of order, or the device state is invalid */
+    ORBC_E_NAN = -5,       /* non-finite force or state detected on the device  */
+    ORBC_E_TIMEOUT = -6    /* a bounded device wait gave up                     */
+} orbc_status;
+
+typedef enum {
+    ORBC_F32_FORCE_F64_STATE = 0,  /* FP32 pair/bond forces, exact fixed-point accumulation and state */
+    ORBC_F64_ALL = 1               /* FP64 pair/bond forces and FP64 integrator increments             */
+} orbc_precision;
+
+/* Particle types of the two-component red-cell model ("Initial structure
+ * generation"): lipids carry an orientation; junctions and spectrin beads
+ * are point particles joined by bonds. */
+enum { ORBC_LIPID = 0, ORBC_JUNCTION = 1, ORBC_SPECTRIN = 2 };
+
+/*
+ * Model, integrator and cell-list parameters.  orbc_default_params() fills
+ * the values used throughout this project.
+ *
+ * Pair potential (the paper cites the two-component CGMD model without its
+ * formulas; these follow the one-particle-thick lipid model it builds on,
+ * Yuan et al., PRE 82, 011905, 2010).  With r_ij = x_i - x_j, rh = r_ij/r:
+ *   a = (n_i x rh).(n_j x rh) + s0 (n_j - n_i).rh - s0^2, phi = 1 + mu (a - 1)
+ *   U = eps[(rmin/r)^4 - 2 (rmin/r)^2] + (1 - phi) eps      r < rmin
+ *   U = -eps cos^(2 zeta)((pi/2)(r - rmin)/(rc - rmin)) phi  rmin <= r < rc
+ * with rmin = 2^(1/6) sigma.  Every pair that is not lipid-lipid is purely
+ * repulsive WCA (eps_wca, sigma_wca, cutoff 2^(1/6) sigma_wca) and bonded
+ * pairs are excluded from it ("Force Evaluation": protein interactions use
+ * the lipid cells with a wider search cutoff).
+ *
+ * Integrator: BAOAB Langevin (translational for all particles, rotational
+ * for lipids with Cayley rotations of the director), noise from
+ * Philox4x32-10 keyed by (seed, instance; particle id, step, substream).
+ */
+typedef struct {
+    double eps, sigma, rc_lipid, mu, sin_theta0;   /* lipid-lipid potential               */
+    int zeta;                                      /* cos^(2 zeta) tail exponent           */
+    int pad0;
+    double eps_wca, sigma_wca;                     /* excluded volume of non-lipid pairs   */
+    double dt, kT, gamma_t, gamma_r, mass, inertia;/* integrator                           */
+    double box[3];                                 /* box lengths on periodic axes         */
+    int periodic[3];                               /* 1 = periodic axis                    */
+    int n_centroids;                               /* Voronoi cells                        */
+    int n_lloyd_init;                              /* k-means rounds at initialisation     */
+    int rebuild_every;                             /* rebuild cadence in steps (>= 1)      */
+    double skin;                                   /* neighbour skin (sigma), 0 = none     */
+    double grid_h;                                 /* centroid-search grid edge, 0 = auto  */
+    unsigned long long seed;
+    unsigned instance;                             /* Philox key word, per ensemble member */
+    orbc_precision precision;
+} orbc_params;
+
+typedef struct orbc_system orbc_system;   /* opaque; owns its device memory */
+
+/* Fills p with the project's defaults: eps = sigma = 1, rc = 2.6, mu = 3,
+ * zeta = 4, sin_theta0 = 0, eps_wca = sigma_wca = 1, dt = 0.01, kT = 0.2,
+ * gamma_t = gamma_r = 1, mass = inertia = 1, no periodic axis,
+ * n_centroids = 64, n_lloyd_init = 10, rebuild_every = 1, skin = 0,
+ * grid_h = 0, seed = 0, instance = 0, ORBC_F32_FORCE_F64_STATE. */
+ORBC_API void orbc_default_params(orbc_params* p);
+
+/* Creates a handle.  cuda_stream is a cudaStream_t (NULL = the library's own
+ * non-blocking stream).  The device is the current CUDA device.
+ * Errors: ORBC_E_ARG for null pointers or invalid parameters (non-positive
+ * dt or box on a periodic axis, n_centroids < 1, rebuild_every < 1, skin > 0
+ * required when rebuild_every > 1), ORBC_E_CUDA. */
+ORBC_API int orbc_create(const orbc_params* params, void* cuda_stream, orbc_system** out);
+
+/* Copies n particles from host memory ("Initial structure generation": the
+ * system's particles with their types).  pos, vel: [n][3]; ori, angvel:
+ * [n][3], read for lipids only (ori must be unit, angvel is projected
+ * perpendicular to it); type: [n] (ORBC_LIPID/JUNCTION/SPECTRIN); id: [n],
+ * a permutation of 0..n-1.  Invalidates cells and forces.
+ * Errors: ORBC_E_ARG (null pointer, n < 1, non-finite value, |x| >= 4096
+ * sigma, unknown type, ids not a permutation), ORBC_E_NOMEM, ORBC_E_CUDA. */
+ORBC_API int orbc_set_particles(orbc_system* s, int n, const double* pos, const double* vel, const double* ori,
+                       const double* angvel, const unsigned char* type, const unsigned* id);
+
+/* Harmonic bonds 1/2 kb (r - r0)^2 between particle ids ("Force
+ * Evaluation": a list of bonds between proteins is maintained).  ij: [nb][2]
+ * ids; r0, kb: [nb].  At most 8 bonds per particle.  Call after
+ * orbc_set_particles.  Errors: ORBC_E_ARG, ORBC_E_STATE, ORBC_E_NOMEM. */
+ORBC_API int orbc_set_bonds(orbc_system* s, int nb, const int* ij, const double* r0, const double* kb);
+
+/* Initial k-means clustering ("Spatial Searching Algorithm"): centroids
+ * [n_centroids][3] from host memory, or NULL to seed them from the lipids in
+ * id order (centroid k = lipid floor(k N_L / K)); then n_lloyd_init rounds of
+ * nearest-centroid assignment and centroid update; then the two-level
+ * reorder (centroids along a Morton curve, particles stably by cell) and the
+ * neighbouring-cell lists.  Errors: ORBC_E_ARG (more centroids than lipids),
+ * ORBC_E_STATE (no particles), ORBC_E_NOMEM, ORBC_E_CUDA. */
+ORBC_API int orbc_init_cells(orbc_system* s, const double* centroids);
+
+/* One update of the Voronoi cells ("Spatial Searching Algorithm": online EM
+ * update of centroid location and particle ownership, then the two-level
+ * reorder): centroid M-step from the current ownership, Morton relabel,
+ * exact nearest-centroid E-step, stable counting sort of the particles and
+ * their state, cell radii and neighbouring-cell lists.
+ * Errors: ORBC_E_STATE (cells not initialised), ORBC_E_CUDA. */
+ORBC_API int orbc_rebuild_cells(orbc_system* s);
+
+/* Forces and torques on every particle through the quad loop over cells,
+ * neighbouring cells and their particles, plus bonds ("Force Evaluation").
+ * energies_out (host, nullable): [U_pair, U_bond, K_trans, K_rot, W] with W
+ * the virial sum of r_ij . F_ij over pairs and bonds.
+ * Errors: ORBC_E_STATE (cells not initialised), ORBC_E_NAN, ORBC_E_CUDA. */
+ORBC_API int orbc_compute_forces(orbc_system* s, double* energies_out);
+
+/* Advances nsteps BAOAB steps ("Software Overview": force and torque, then
+ * position and orientation update), rebuilding the cells every
+ * rebuild_every steps or when a particle has moved more than the skin.
+ * Errors: ORBC_E_ARG (nsteps < 0), ORBC_E_STATE, ORBC_E_NAN, ORBC_E_CUDA. */
+ORBC_API int orbc_integrate(orbc_system* s, int nsteps);
+
+/* Host copies of the state in id order; any pointer may be NULL.  step:
+ * number of steps taken. */
+ORBC_API int orbc_get_state(orbc_system* s, double* pos, double* vel, double* ori, double* angvel, long long* step);
+
+/* Forces and torques of the last force evaluation, in id order. */
+ORBC_API int orbc_get_forces(orbc_system* s, double* force, double* torque);
+
+/* Cell list: cell_of_id [n]; slot_ids [n] (id stored at each storage slot,
+ * the particle reorder); centroids [K][3]; cell_start [K+1]; radius [K];
+ * adj_ptr [K+1] and adj [adj_len] (neighbouring cells, ascending, CSR).
+ * Any pointer may be NULL; orbc_get_adjacency_len gives adj_len. */
+ORBC_API int orbc_get_cells(orbc_system* s, int* cell_of_id, unsigned* slot_ids, double* centroids, int* cell_start,
+                   double* radius, int* adj_ptr, int* adj);
+ORBC_API int orbc_get_adjacency_len(orbc_system* s, long long* len);
+
+/* Debug: every interacting pair found by the quad loop, as (id_lo, id_hi),
+ * sorted; writes up to cap pairs to host memory and the total to *npairs. */
+ORBC_API int orbc_dump_pairs(orbc_system* s, long long cap, unsigned* pairs, long long* npairs);
+
+/* Sizes and timing of the last call: per-kernel device times in ms of the
+ * last orbc_integrate / orbc_compute_forces when timing is on. */
+ORBC_API int orbc_set_timing(orbc_system* s, int on);
+ORBC_API int orbc_get_kernel_times(orbc_system* s, char* names_csv, int names_cap, float* ms, int cap, int* count);
+
+ORBC_API const char* orbc_last_error(const orbc_system* s);
+ORBC_API void orbc_destroy(orbc_system* s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ORBC_H */

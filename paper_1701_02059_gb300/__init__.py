@@ -1,0 +1,155 @@
+"""GB300-native hot path of OpenRBC's Voronoi-cell-list coarse-grained MD
+(arXiv 1701.02059): adaptive Voronoi cell list, orientation-dependent lipid
+pair forces, spectrin bonds and a BAOAB Langevin integrator, all in CUDA
+kernels for sm_103a behind the C ABI of include/orbc.h.
+
+``System`` is a thin wrapper over that ABI (host numpy arrays in, host numpy
+arrays out); it does no arithmetic of its own.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native
+from ._native import F32_FORCE_F64_STATE, F64_ALL, OrbcError, Params, default_params, load
+
+__all__ = ["System", "Params", "default_params", "load", "OrbcError", "F32_FORCE_F64_STATE", "F64_ALL"]
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def make_params(**kw) -> Params:
+    """orbc_params with the library defaults, overridden by keyword."""
+    p = default_params()
+    for k, v in kw.items():
+        if k in ("box", "periodic"):
+            for a in range(3):
+                getattr(p, k)[a] = v[a]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class System:
+    """One membrane on the GPU.  Methods map one to one onto the C ABI."""
+
+    def __init__(self, params: Params, stream: int | None = None):
+        self._L = load()
+        self._h = C.c_void_p()
+        self._check(self._L.orbc_create(C.byref(params), C.c_void_p(stream) if stream else None, C.byref(self._h)),
+                    "orbc_create")
+        self.params = params
+        self.n = 0
+        self.K = params.n_centroids
+
+    def _check(self, rc, what):
+        if rc != 0:
+            msg = self._L.orbc_last_error(self._h).decode() if self._h else what
+            raise OrbcError(rc, f"{what}: {msg}")
+
+    def close(self):
+        if self._h:
+            self._L.orbc_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -------------------------------------------------------------- set-up
+    def set_particles(self, pos, vel, ori, angvel, typ, ids):
+        arrs = [np.ascontiguousarray(pos, np.float64), np.ascontiguousarray(vel, np.float64),
+                np.ascontiguousarray(ori, np.float64), np.ascontiguousarray(angvel, np.float64),
+                np.ascontiguousarray(typ, np.uint8), np.ascontiguousarray(ids, np.uint32)]
+        self.n = len(arrs[4])
+        self._check(self._L.orbc_set_particles(self._h, self.n, *[_p(a) for a in arrs]), "orbc_set_particles")
+
+    def set_bonds(self, ij, r0, kb):
+        ij = np.ascontiguousarray(ij, np.int32)
+        r0 = np.ascontiguousarray(r0, np.float64)
+        kb = np.ascontiguousarray(kb, np.float64)
+        self._check(self._L.orbc_set_bonds(self._h, len(r0), _p(ij), _p(r0), _p(kb)), "orbc_set_bonds")
+
+    def load_membrane(self, mem):
+        self.set_particles(mem.pos, mem.vel, mem.ori, mem.angvel, mem.type, mem.id)
+        if len(mem.r0):
+            self.set_bonds(mem.bonds, mem.r0, mem.kb)
+
+    def init_cells(self, centroids=None):
+        c = None if centroids is None else np.ascontiguousarray(centroids, np.float64)
+        self._check(self._L.orbc_init_cells(self._h, _p(c)), "orbc_init_cells")
+
+    # -------------------------------------------------------------- the path
+    def rebuild_cells(self):
+        self._check(self._L.orbc_rebuild_cells(self._h), "orbc_rebuild_cells")
+
+    def compute_forces(self, energies: bool = False):
+        e = np.zeros(5) if energies else None
+        self._check(self._L.orbc_compute_forces(self._h, _p(e)), "orbc_compute_forces")
+        return e
+
+    def integrate(self, nsteps: int):
+        self._check(self._L.orbc_integrate(self._h, int(nsteps)), "orbc_integrate")
+
+    # -------------------------------------------------------------- getters
+    def state(self):
+        n = self.n
+        pos, vel, ori, w = (np.zeros((n, 3)) for _ in range(4))
+        step = C.c_longlong(0)
+        self._check(self._L.orbc_get_state(self._h, _p(pos), _p(vel), _p(ori), _p(w), C.byref(step)), "orbc_get_state")
+        return {"pos": pos, "vel": vel, "ori": ori, "angvel": w, "step": step.value}
+
+    def forces(self):
+        F, T = np.zeros((self.n, 3)), np.zeros((self.n, 3))
+        self._check(self._L.orbc_get_forces(self._h, _p(F), _p(T)), "orbc_get_forces")
+        return F, T
+
+    def cells(self):
+        n, K = self.n, self.K
+        L = C.c_longlong(0)
+        self._check(self._L.orbc_get_adjacency_len(self._h, C.byref(L)), "orbc_get_adjacency_len")
+        cell = np.zeros(n, np.int32)
+        slots = np.zeros(n, np.uint32)
+        c = np.zeros((K, 3))
+        start = np.zeros(K + 1, np.int32)
+        R = np.zeros(K)
+        ptr = np.zeros(K + 1, np.int32)
+        adj = np.zeros(max(L.value, 1), np.int32)
+        self._check(self._L.orbc_get_cells(self._h, _p(cell), _p(slots), _p(c), _p(start), _p(R), _p(ptr), _p(adj)),
+                    "orbc_get_cells")
+        return {"cell_of_id": cell, "slot_ids": slots, "centroids": c, "start": start, "radius": R, "adj_ptr": ptr,
+                "adj": adj[:L.value]}
+
+    def pairs(self):
+        cnt = C.c_longlong(0)
+        self._check(self._L.orbc_dump_pairs(self._h, 0, None, C.byref(cnt)), "orbc_dump_pairs")
+        out = np.zeros((max(cnt.value, 1), 2), np.uint32)
+        self._check(self._L.orbc_dump_pairs(self._h, cnt.value, _p(out), C.byref(cnt)), "orbc_dump_pairs")
+        return out[:cnt.value]
+
+    def set_timing(self, on: bool):
+        self._check(self._L.orbc_set_timing(self._h, 1 if on else 0), "orbc_set_timing")
+
+    def kernel_times(self):
+        buf = C.create_string_buffer(4096)
+        ms = (C.c_float * 64)()
+        cnt = C.c_int(0)
+        self._check(self._L.orbc_get_kernel_times(self._h, buf, 4096, ms, 64, C.byref(cnt)), "orbc_get_kernel_times")
+        out = {}
+        names = buf.value.decode().split(",") if buf.value else []
+        for q, nm in enumerate(names[:cnt.value]):
+            name, launches = nm.rsplit(":", 1)
+            out[name] = {"ms": float(ms[q]), "launches": int(launches)}
+        return out

@@ -1,0 +1,89 @@
+"""ctypes binding of liborbc.so (the C ABI of include/orbc.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+library.  Loading fails loudly when the library is missing; there is no CPU
+fallback."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liborbc.so")
+
+ORBC_OK, ORBC_E_ARG, ORBC_E_NOMEM, ORBC_E_CUDA, ORBC_E_STATE, ORBC_E_NAN, ORBC_E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
+F32_FORCE_F64_STATE, F64_ALL = 0, 1
+STATUS_NAMES = {0: "ORBC_OK", -1: "ORBC_E_ARG", -2: "ORBC_E_NOMEM", -3: "ORBC_E_CUDA", -4: "ORBC_E_STATE",
+                -5: "ORBC_E_NAN", -6: "ORBC_E_TIMEOUT"}
+
+EXPORTS = [
+    "orbc_default_params", "orbc_create", "orbc_set_particles", "orbc_set_bonds", "orbc_init_cells",
+    "orbc_rebuild_cells", "orbc_compute_forces", "orbc_integrate", "orbc_get_state", "orbc_get_forces",
+    "orbc_get_cells", "orbc_get_adjacency_len", "orbc_dump_pairs", "orbc_set_timing", "orbc_get_kernel_times",
+    "orbc_last_error", "orbc_destroy",
+]
+
+
+class Params(C.Structure):
+    """Mirror of orbc_params."""
+    _fields_ = [("eps", C.c_double), ("sigma", C.c_double), ("rc_lipid", C.c_double), ("mu", C.c_double),
+                ("sin_theta0", C.c_double), ("zeta", C.c_int), ("pad0", C.c_int),
+                ("eps_wca", C.c_double), ("sigma_wca", C.c_double),
+                ("dt", C.c_double), ("kT", C.c_double), ("gamma_t", C.c_double), ("gamma_r", C.c_double),
+                ("mass", C.c_double), ("inertia", C.c_double),
+                ("box", C.c_double * 3), ("periodic", C.c_int * 3),
+                ("n_centroids", C.c_int), ("n_lloyd_init", C.c_int), ("rebuild_every", C.c_int),
+                ("skin", C.c_double), ("grid_h", C.c_double), ("seed", C.c_ulonglong), ("instance", C.c_uint),
+                ("precision", C.c_int)]
+
+
+class OrbcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load liborbc.so (built by paper_1701_02059_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"liborbc.so not found at {p}: build it with python -m paper_1701_02059_gb300.build")
+    L = C.CDLL(p)
+    V = C.c_void_p
+    L.orbc_default_params.argtypes = [C.POINTER(Params)]
+    L.orbc_default_params.restype = None
+    L.orbc_create.argtypes = [C.POINTER(Params), V, C.POINTER(V)]
+    L.orbc_set_particles.argtypes = [V, C.c_int, V, V, V, V, V, V]
+    L.orbc_set_bonds.argtypes = [V, C.c_int, V, V, V]
+    L.orbc_init_cells.argtypes = [V, V]
+    L.orbc_rebuild_cells.argtypes = [V]
+    L.orbc_compute_forces.argtypes = [V, V]
+    L.orbc_integrate.argtypes = [V, C.c_int]
+    L.orbc_get_state.argtypes = [V, V, V, V, V, V]
+    L.orbc_get_forces.argtypes = [V, V, V]
+    L.orbc_get_cells.argtypes = [V, V, V, V, V, V, V, V]
+    L.orbc_get_adjacency_len.argtypes = [V, C.POINTER(C.c_longlong)]
+    L.orbc_dump_pairs.argtypes = [V, C.c_longlong, V, C.POINTER(C.c_longlong)]
+    L.orbc_set_timing.argtypes = [V, C.c_int]
+    L.orbc_get_kernel_times.argtypes = [V, C.c_char_p, C.c_int, V, C.c_int, C.POINTER(C.c_int)]
+    L.orbc_last_error.argtypes = [V]
+    L.orbc_last_error.restype = C.c_char_p
+    L.orbc_destroy.argtypes = [V]
+    L.orbc_destroy.restype = None
+    for name in EXPORTS:
+        getattr(L, name).restype = getattr(L, name).restype if name in ("orbc_default_params", "orbc_last_error",
+                                                                        "orbc_destroy") else C.c_int
+    _lib = L
+    return L
+
+
+def default_params() -> Params:
+    p = Params()
+    load().orbc_default_params(C.byref(p))
+    return p

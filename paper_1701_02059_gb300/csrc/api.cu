@@ -1,0 +1,890 @@
+// Host orchestration of the hot path and the C ABI declared in orbc.h.
+#include "ensemble.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "../../include/orbc.h"
+
+namespace orbc {
+
+// ============================================================== Ensemble basics
+Ensemble::Ensemble(cudaStream_t s) : stream(s) {}
+
+Ensemble::~Ensemble() { free_all(); }
+
+void Ensemble::free_all() {
+    for (void* p : allocs_) cudaFree(p);
+    allocs_.clear();
+    for (int* p : scan_tmp_) if (p) cudaFree(p);
+    scan_tmp_.clear();
+    scan_tmp_n_.clear();
+    if (ev0_) { cudaEventDestroy(ev0_); ev0_ = nullptr; }
+    if (ev1_) { cudaEventDestroy(ev1_); ev1_ = nullptr; }
+    d_dump = nullptr;
+    d_dump_count = nullptr;
+    dump_cap = 0;
+}
+
+template <typename T>
+T* Ensemble::alloc(size_t count) {
+    void* p = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw CudaError(cudaErrorMemoryAllocation, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    allocs_.push_back(p);
+    CK(cudaMemsetAsync(p, 0, bytes, stream));
+    return (T*)p;
+}
+
+View Ensemble::view() {
+    View v;
+    v.B = B; v.N = N; v.Ktot = Ktot; v.Gtot = Gtot;
+    v.inst = d_inst; v.inst_p0 = d_p0; v.inst_k0 = d_k0;
+    v.xq = d_state[cur_][0]; v.vq = d_state[cur_][1]; v.nq = d_state[cur_][2]; v.wq = d_state[cur_][3];
+    v.type = d_type[cur_]; v.id = d_id[cur_];
+    v.cell = d_cell; v.slot_of_id = d_slot_of_id;
+    v.F = d_F; v.T = d_T;
+    v.mq = d_mq; v.mo = d_mo;
+    v.cq = d_cq; v.cell_start = d_cell_start; v.R = d_R; v.adj_ptr = d_adj_ptr; v.adj = d_adj; v.adj_cap = adj_cap;
+    v.gstart = d_gstart; v.gcent = d_gcent; v.gcf = d_gcf;
+    v.bptr = d_bptr; v.bpartner = d_bpartner; v.br0 = d_br0; v.bkb = d_bkb; v.br0_d = d_br0_d; v.bkb_d = d_bkb_d;
+    v.status = d_status;
+    return v;
+}
+
+View Ensemble::view_alt() {
+    cur_ ^= 1;
+    View v = view();
+    cur_ ^= 1;
+    return v;
+}
+
+void Ensemble::swap_state() { cur_ ^= 1; }
+
+void Ensemble::sync() { CK(cudaStreamSynchronize(stream)); }
+
+unsigned Ensemble::read_status(bool clear) {
+    unsigned s = 0;
+    CK(cudaMemcpyAsync(&s, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    if (clear && s) CK(cudaMemsetAsync(d_status, 0, sizeof(unsigned), stream));
+    return s;
+}
+
+// ---------------------------------------------------------------- timing
+struct PendingTime { std::string name; cudaEvent_t a, b; };
+static thread_local std::vector<PendingTime> g_pending;
+
+void Ensemble::tic(const char* name) {
+    if (!timing) return;
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    CK(cudaEventRecord(a, stream));
+    g_pending.push_back({name, a, b});
+    open_ = name;
+}
+
+void Ensemble::toc() {
+    if (!timing || g_pending.empty()) return;
+    CK(cudaEventRecord(g_pending.back().b, stream));
+    open_ = nullptr;
+}
+
+static void collect_times(std::vector<Ensemble::TimedKernel>& out) {
+    for (auto& p : g_pending) {
+        float ms = 0;
+        if (cudaEventSynchronize(p.b) == cudaSuccess) cudaEventElapsedTime(&ms, p.a, p.b);
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+        auto it = std::find_if(out.begin(), out.end(), [&](const Ensemble::TimedKernel& t) { return t.name == p.name; });
+        if (it == out.end()) { out.push_back({p.name, 0.0, 0}); it = out.end() - 1; }
+        it->ms += ms;
+        it->launches += 1;
+    }
+    g_pending.clear();
+}
+
+// ---------------------------------------------------------------- set-up
+static Inst make_inst(const Params& P) {
+    Inst I;
+    std::memset(&I, 0, sizeof(I));
+    const double two_sixth = 1.122462048309373;
+    I.eps = (float)P.eps; I.rmin = (float)(two_sixth * P.sigma); I.rc = (float)P.rc_lipid; I.mu = (float)P.mu;
+    I.s0 = (float)P.sin_theta0; I.eps_wca = (float)P.eps_wca; I.sig_wca = (float)P.sigma_wca; I.zeta = P.zeta;
+    I.eps_d = P.eps; I.rmin_d = two_sixth * P.sigma; I.rc_d = P.rc_lipid; I.mu_d = P.mu; I.s0_d = P.sin_theta0;
+    I.eps_wca_d = P.eps_wca; I.sig_wca_d = P.sigma_wca;
+    const double rcw = two_sixth * P.sigma_wca;
+    I.rc2_ll = P.rc_lipid * P.rc_lipid;
+    I.rc2_wca = rcw * rcw;
+    I.rc2f_ll = (float)I.rc2_ll;
+    I.rc2f_wca = (float)I.rc2_wca;
+    I.rs = std::max(P.rc_lipid, rcw);
+    I.rsf = (float)I.rs;
+    I.skin = P.skin;
+    for (int a = 0; a < 3; a++) {
+        I.periodic[a] = P.periodic[a];
+        I.box[a] = P.periodic[a] ? P.box[a] : 0.0;
+        I.boxq[a] = P.periodic[a] ? llrint(P.box[a] * kGrid) : 0;
+        I.boxf[a] = (float)I.box[a];
+    }
+    const double h = 0.5 * P.dt;
+    I.h_m_d = h / P.mass; I.h_i_d = h / P.inertia; I.hdt_d = h;
+    const double ct = std::exp(-P.gamma_t * P.dt), cr = std::exp(-P.gamma_r * P.dt);
+    I.ct_m1_d = std::expm1(-P.gamma_t * P.dt);
+    I.cr_m1_d = std::expm1(-P.gamma_r * P.dt);
+    I.st_d = std::sqrt(std::max(0.0, (1.0 - ct * ct) * P.kT / P.mass));
+    I.sr_d = std::sqrt(std::max(0.0, (1.0 - cr * cr) * P.kT / P.inertia));
+    I.h_m = (float)I.h_m_d; I.h_i = (float)I.h_i_d; I.hdt = (float)I.hdt_d;
+    I.ct_m1 = (float)I.ct_m1_d; I.cr_m1 = (float)I.cr_m1_d; I.st = (float)I.st_d; I.sr = (float)I.sr_d;
+    I.mass = P.mass; I.inertia = P.inertia;
+    I.seed = P.seed; I.instance = P.instance;
+    I.rebuild_every = P.rebuild_every;
+    I.n_lloyd = P.n_lloyd_init;
+    return I;
+}
+
+void Ensemble::setup(const std::vector<HostInstance>& list) {
+    free_all();
+    B = (int)list.size();
+    if (B < 1) throw ArgError("no instance");
+    precision = list[0].prm.precision;
+    N = 0; Ktot = 0;
+    inst_h.assign(B, Inst());
+    prm_h.clear();
+    std::vector<int> p0(B + 1, 0), k0(B + 1, 0);
+    for (int b = 0; b < B; b++) {
+        const HostInstance& h = list[b];
+        if (h.prm.precision != precision) throw ArgError("all instances of a batch need the same precision");
+        inst_h[b] = make_inst(h.prm);
+        inst_h[b].p0 = N; inst_h[b].n = h.n;
+        inst_h[b].k0 = Ktot; inst_h[b].K = h.prm.n_centroids;
+        inst_h[b].nlip = (int)std::count(h.type.begin(), h.type.end(), (unsigned char)kLipid);
+        prm_h.push_back(h.prm);
+        N += h.n;
+        Ktot += h.prm.n_centroids;
+        p0[b + 1] = N;
+        k0[b + 1] = Ktot;
+    }
+    step_h.assign(B, 0);
+    for (int b = 0; b < B; b++) step_h[b] = list[b].step0;
+    d_inst = alloc<Inst>(B);
+    d_p0 = alloc<int>(B + 1);
+    d_k0 = alloc<int>(B + 1);
+    CK(cudaMemcpyAsync(d_p0, p0.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(d_k0, k0.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice, stream));
+    for (int s = 0; s < 2; s++) {
+        for (int q = 0; q < 4; q++) d_state[s][q] = alloc<long long>((size_t)3 * N);
+        d_type[s] = alloc<unsigned char>(N);
+        d_id[s] = alloc<unsigned>(N);
+    }
+    cur_ = 0;
+    d_cell = alloc<int>(N);
+    d_slot_of_id = alloc<int>(N);
+    d_F = alloc<long long>((size_t)3 * N);
+    d_T = alloc<long long>((size_t)3 * N);
+    d_mq = alloc<int4>(N);
+    d_mo = alloc<float4>(N);
+    d_cq = alloc<long long>((size_t)3 * Ktot);
+    d_cq_tmp = alloc<long long>((size_t)3 * Ktot);
+    d_cell_start = alloc<int>(Ktot + 1);
+    d_R = alloc<double>(Ktot);
+    d_adj_ptr = alloc<int>(Ktot + 1);
+    d_adjcount = alloc<int>(Ktot + 1);
+    adj_cap = (long long)Ktot * 64;
+    d_adj = alloc<int>(adj_cap);
+    d_gcent = alloc<int>(Ktot);
+    d_gcf = alloc<float4>(Ktot);
+    d_gidx = alloc<int>(Ktot);
+    d_status = alloc<unsigned>(1);
+    d_S = alloc<long long>((size_t)3 * Ktot);
+    d_cnt = alloc<int>(Ktot + 1);
+    d_bbox = alloc<long long>((size_t)6 * B);
+    d_keys = alloc<unsigned long long>(Ktot);
+    d_sortrec = alloc<unsigned char>((size_t)16 * ((Ktot + 1023) / 1024) * 1024);
+    d_new_of_old = alloc<int>(Ktot);
+    d_cell_new = alloc<int>(N);
+    d_perm = alloc<int>(N);
+    d_rmax = alloc<unsigned long long>(B);
+    d_energy = alloc<long long>((size_t)8 * B);
+    d_step = alloc<long long>(B);
+    CK(cudaMemcpyAsync(d_step, step_h.data(), sizeof(long long) * B, cudaMemcpyHostToDevice, stream));
+    bool any_skin = false;
+    for (auto& h : list) any_skin |= (h.prm.rebuild_every > 1);
+    d_xref = any_skin ? alloc<long long>((size_t)3 * N) : nullptr;
+
+    // state, axis-major
+    std::vector<long long> ax((size_t)3 * N);
+    std::vector<unsigned char> ty(N);
+    std::vector<unsigned> ids(N);
+    std::vector<int> slot(N);
+    const std::vector<long long> HostInstance::*fields[4] = {&HostInstance::xq, &HostInstance::vq, &HostInstance::nq,
+                                                               &HostInstance::wq};
+    for (int q = 0; q < 4; q++) {
+        for (int b = 0; b < B; b++) {
+            const HostInstance& h = list[b];
+            const std::vector<long long>& src = h.*fields[q];
+            for (int i = 0; i < h.n; i++)
+                for (int a = 0; a < 3; a++) ax[(size_t)a * N + p0[b] + i] = src[(size_t)3 * i + a];
+        }
+        CK(cudaMemcpyAsync(d_state[0][q], ax.data(), sizeof(long long) * 3 * N, cudaMemcpyHostToDevice, stream));
+        CK(cudaStreamSynchronize(stream));
+    }
+    for (int b = 0; b < B; b++) {
+        const HostInstance& h = list[b];
+        for (int i = 0; i < h.n; i++) {
+            ty[p0[b] + i] = h.type[i];
+            ids[p0[b] + i] = h.id[i];
+            slot[p0[b] + h.id[i]] = p0[b] + i;
+        }
+    }
+    CK(cudaMemcpyAsync(d_type[0], ty.data(), N, cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(d_id[0], ids.data(), sizeof(unsigned) * N, cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(d_slot_of_id, slot.data(), sizeof(int) * N, cudaMemcpyHostToDevice, stream));
+
+    // bonds: CSR by (p0 + id), both directions
+    std::vector<int> bptr(N + 1, 0);
+    for (int b = 0; b < B; b++) {
+        const HostInstance& h = list[b];
+        int nb = (int)h.r0.size();
+        for (int q = 0; q < nb; q++) {
+            bptr[p0[b] + h.bonds[2 * q] + 1]++;
+            bptr[p0[b] + h.bonds[2 * q + 1] + 1]++;
+        }
+    }
+    for (int i = 0; i < N; i++) {
+        if (bptr[i + 1] > kMaxBondsPerParticle) throw ArgError("more than 8 bonds on one particle");
+        bptr[i + 1] += bptr[i];
+    }
+    int nbe = bptr[N];
+    std::vector<int> part(std::max(nbe, 1));
+    std::vector<float> r0f(std::max(nbe, 1)), kbf(std::max(nbe, 1));
+    std::vector<double> r0d(std::max(nbe, 1)), kbd(std::max(nbe, 1));
+    std::vector<int> fill(N, 0);
+    for (int b = 0; b < B; b++) {
+        const HostInstance& h = list[b];
+        int nb = (int)h.r0.size();
+        for (int q = 0; q < nb; q++) {
+            int i = h.bonds[2 * q], j = h.bonds[2 * q + 1];
+            int gi = p0[b] + i, gj = p0[b] + j;
+            int si = bptr[gi] + fill[gi]++, sj = bptr[gj] + fill[gj]++;
+            part[si] = j; part[sj] = i;
+            r0f[si] = r0f[sj] = (float)h.r0[q];
+            kbf[si] = kbf[sj] = (float)h.kb[q];
+            r0d[si] = r0d[sj] = h.r0[q];
+            kbd[si] = kbd[sj] = h.kb[q];
+        }
+    }
+    d_bptr = alloc<int>(N + 1);
+    d_bpartner = alloc<int>(std::max(nbe, 1));
+    d_br0 = alloc<float>(std::max(nbe, 1));
+    d_bkb = alloc<float>(std::max(nbe, 1));
+    d_br0_d = alloc<double>(std::max(nbe, 1));
+    d_bkb_d = alloc<double>(std::max(nbe, 1));
+    CK(cudaMemcpyAsync(d_bptr, bptr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, stream));
+    if (nbe > 0) {
+        CK(cudaMemcpyAsync(d_bpartner, part.data(), sizeof(int) * nbe, cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(d_br0, r0f.data(), sizeof(float) * nbe, cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(d_bkb, kbf.data(), sizeof(float) * nbe, cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(d_br0_d, r0d.data(), sizeof(double) * nbe, cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(d_bkb_d, kbd.data(), sizeof(double) * nbe, cudaMemcpyHostToDevice, stream));
+    }
+
+    // initial centroids (host) and the centroid-grid geometry of each instance
+    std::vector<long long> c0((size_t)3 * Ktot);
+    Gtot = 0;
+    for (int b = 0; b < B; b++) {
+        const HostInstance& h = list[b];
+        Inst& I = inst_h[b];
+        const int K = I.K;
+        std::vector<long long> c((size_t)3 * K);
+        if (!h.centroids.empty()) {
+            for (int q = 0; q < 3 * K; q++) c[q] = llrint(h.centroids[q] * kGrid);
+        } else {
+            // lipids in id order, centroid k = lipid floor(k N_L / K)
+            std::vector<int> by_id(h.n);
+            for (int i = 0; i < h.n; i++) by_id[h.id[i]] = i;
+            std::vector<int> lip;
+            lip.reserve(h.n);
+            for (int idv = 0; idv < h.n; idv++)
+                if (h.type[by_id[idv]] == kLipid) lip.push_back(by_id[idv]);
+            if ((int)lip.size() < K) throw ArgError("more centroids than lipids");
+            for (int k = 0; k < K; k++) {
+                int s = lip[(size_t)((long long)k * (long long)lip.size() / K)];
+                for (int a = 0; a < 3; a++) c[(size_t)3 * k + a] = h.xq[(size_t)3 * s + a];
+            }
+        }
+        for (int k = 0; k < K; k++)
+            for (int a = 0; a < 3; a++)
+                if (I.periodic[a]) c[(size_t)3 * k + a] = floor_mod_ll(c[(size_t)3 * k + a], I.boxq[a]);
+        for (int k = 0; k < K; k++)
+            for (int a = 0; a < 3; a++) c0[(size_t)a * Ktot + I.k0 + k] = c[(size_t)3 * k + a];
+        // grid: edge ~ centroid spacing on a membrane of this many lipids
+        double hgrid = h.prm.grid_h > 0 ? h.prm.grid_h : std::sqrt(1.0863 * std::max(I.nlip, 1) / (double)K);
+        hgrid = std::max(hgrid, 1.0);
+        double lo[3], hi[3];
+        for (int a = 0; a < 3; a++) {
+            lo[a] = 1e300; hi[a] = -1e300;
+            for (int k = 0; k < K; k++) {
+                double x = c[(size_t)3 * k + a] * kGridInv;
+                lo[a] = std::min(lo[a], x);
+                hi[a] = std::max(hi[a], x);
+            }
+        }
+        for (int tries = 0;; tries++) {
+            long long G = 1;
+            for (int a = 0; a < 3; a++) {
+                if (I.periodic[a]) {
+                    I.gdim[a] = std::max(1, (int)std::floor(I.box[a] / hgrid));
+                    I.gh[a] = (float)(I.box[a] / I.gdim[a]);
+                    I.gorg[a] = 0;
+                } else {
+                    double o = lo[a] - hgrid;
+                    I.gdim[a] = std::max(1, (int)std::ceil((hi[a] - lo[a] + 2 * hgrid) / hgrid));
+                    I.gh[a] = (float)hgrid;
+                    I.gorg[a] = llrint(o * kGrid);
+                }
+                I.ginv[a] = 1.0f / I.gh[a];
+                G *= I.gdim[a];
+            }
+            if (G <= (1ll << 24) || tries > 20) break;
+            hgrid *= 1.25;
+        }
+        I.g0 = Gtot;
+        Gtot += (long long)I.gdim[0] * I.gdim[1] * I.gdim[2];
+    }
+    d_gstart = alloc<int>(Gtot + 1);
+    d_gcount = alloc<int>(Gtot + 1);
+    CK(cudaMemcpyAsync(d_cq, c0.data(), sizeof(long long) * 3 * Ktot, cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(d_inst, inst_h.data(), sizeof(Inst) * B, cudaMemcpyHostToDevice, stream));
+    // warm the scan scratch for the largest size used later
+    scan_exclusive(d_gcount, d_gstart, Gtot + 1);
+    scan_exclusive(d_cnt, d_cell_start, Ktot + 1);
+    CK(cudaStreamSynchronize(stream));
+    n_lloyd_.clear();
+    for (auto& h : list) n_lloyd_.push_back(h.prm.n_lloyd_init);
+    cells_valid = false;
+    forces_valid = false;
+}
+
+void Ensemble::init_cells() {
+    int iters = 0;
+    for (int x : n_lloyd_) iters = std::max(iters, x);
+    for (int it = 0; it < iters; it++) {
+        tic("grid");
+        build_grid();
+        toc();
+        tic("estep");
+        estep(d_cell);
+        toc();
+        tic("mstep");
+        mstep_iter(d_cell, it);
+        toc();
+    }
+    finish_cells();
+    unsigned st = read_status(true);
+    if (st) throw StateError("cell initialisation flagged status " + std::to_string(st));
+    collect_times(kernel_times);
+}
+
+void Ensemble::compute_forces(bool energies) {
+    if (!cells_valid) throw StateError("cells not initialised");
+    tic("pairs");
+    launch_pairs(energies, false);
+    toc();
+    if (energies) launch_kinetic();
+    forces_valid = true;
+}
+
+void Ensemble::energies(std::vector<double>& out) {
+    std::vector<long long> e((size_t)8 * B);
+    CK(cudaMemcpyAsync(e.data(), d_energy, sizeof(long long) * 8 * B, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    out.assign((size_t)5 * B, 0.0);
+    for (int b = 0; b < B; b++)
+        for (int q = 0; q < 5; q++) out[(size_t)5 * b + q] = (double)e[(size_t)8 * b + q] * kForceUnit;
+}
+
+void Ensemble::integrate(int nsteps) {
+    if (!cells_valid) throw StateError("cells not initialised");
+    if (!forces_valid) {
+        tic("pairs");
+        launch_pairs(false, false);
+        toc();
+    }
+    for (int s = 0; s < nsteps; s++) {
+        tic("integrate_baoa");
+        launch_integrate_first();
+        toc();
+        const int re = prm_h[0].rebuild_every;
+        bool due = (re <= 1) || ((step_h[0] + 1) % re == 0);
+        if (!due && d_xref) due = displacement_exceeds_skin();
+        if (due) {
+            tic("rebuild");
+            rebuild();
+            toc();
+        } else {
+            tic("mirrors");
+            mirrors();
+            toc();
+        }
+        tic("pairs");
+        launch_pairs(false, false);
+        toc();
+        tic("integrate_kick");
+        launch_kick(false);
+        toc();
+        for (auto& x : step_h) x++;
+    }
+    forces_valid = true;
+    collect_times(kernel_times);
+}
+
+// ---------------------------------------------------------------- getters
+void Ensemble::get_state(int b, double* pos, double* vel, double* ori, double* angvel, long long* step) {
+    const Inst& I = inst_h[b];
+    const int n = I.n;
+    std::vector<long long> buf((size_t)n);
+    std::vector<unsigned> ids(n);
+    CK(cudaMemcpyAsync(ids.data(), d_id[cur_] + I.p0, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, stream));
+    double* outs[4] = {pos, vel, ori, angvel};
+    for (int q = 0; q < 4; q++) {
+        if (!outs[q]) continue;
+        for (int a = 0; a < 3; a++) {
+            CK(cudaMemcpyAsync(buf.data(), d_state[cur_][q] + (size_t)a * N + I.p0, sizeof(long long) * n,
+                               cudaMemcpyDeviceToHost, stream));
+            CK(cudaStreamSynchronize(stream));
+            for (int i = 0; i < n; i++) outs[q][(size_t)3 * ids[i] + a] = (double)buf[i] * kGridInv;
+        }
+    }
+    if (step) {
+        long long s = 0;
+        CK(cudaMemcpyAsync(&s, d_step + b, sizeof(long long), cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        *step = s;
+    }
+    CK(cudaStreamSynchronize(stream));
+}
+
+void Ensemble::get_forces(int b, double* f, double* t) {
+    const Inst& I = inst_h[b];
+    const int n = I.n;
+    std::vector<long long> buf((size_t)n);
+    std::vector<unsigned> ids(n);
+    CK(cudaMemcpyAsync(ids.data(), d_id[cur_] + I.p0, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, stream));
+    long long* src[2] = {d_F, d_T};
+    double* outs[2] = {f, t};
+    for (int q = 0; q < 2; q++) {
+        if (!outs[q]) continue;
+        for (int a = 0; a < 3; a++) {
+            CK(cudaMemcpyAsync(buf.data(), src[q] + (size_t)a * N + I.p0, sizeof(long long) * n, cudaMemcpyDeviceToHost,
+                               stream));
+            CK(cudaStreamSynchronize(stream));
+            for (int i = 0; i < n; i++) outs[q][(size_t)3 * ids[i] + a] = (double)buf[i] * kForceUnit;
+        }
+    }
+    CK(cudaStreamSynchronize(stream));
+}
+
+void Ensemble::get_cells(int b, int* cell_of_id, unsigned* slot_ids, double* centroids, int* cell_start,
+                         double* radius, int* adj_ptr, int* adj) {
+    const Inst& I = inst_h[b];
+    const int n = I.n, K = I.K;
+    std::vector<unsigned> ids(n);
+    std::vector<int> cl(n);
+    CK(cudaMemcpyAsync(ids.data(), d_id[cur_] + I.p0, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(cl.data(), d_cell + I.p0, sizeof(int) * n, cudaMemcpyDeviceToHost, stream));
+    std::vector<int> cs(K + 1), ap(K + 1);
+    CK(cudaMemcpyAsync(cs.data(), d_cell_start + I.k0, sizeof(int) * (K + 1), cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(ap.data(), d_adj_ptr + I.k0, sizeof(int) * (K + 1), cudaMemcpyDeviceToHost, stream));
+    std::vector<double> R(K);
+    CK(cudaMemcpyAsync(R.data(), d_R + I.k0, sizeof(double) * K, cudaMemcpyDeviceToHost, stream));
+    std::vector<long long> c((size_t)3 * K);
+    for (int a = 0; a < 3; a++)
+        CK(cudaMemcpyAsync(c.data() + (size_t)a * K, d_cq + (size_t)a * Ktot + I.k0, sizeof(long long) * K,
+                           cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    for (int i = 0; i < n; i++) {
+        if (cell_of_id) cell_of_id[ids[i]] = cl[i] - I.k0;
+        if (slot_ids) slot_ids[i] = ids[i];
+    }
+    if (centroids)
+        for (int k = 0; k < K; k++)
+            for (int a = 0; a < 3; a++) centroids[(size_t)3 * k + a] = (double)c[(size_t)a * K + k] * kGridInv;
+    if (cell_start) for (int k = 0; k <= K; k++) cell_start[k] = cs[k] - I.p0;
+    if (radius) std::copy(R.begin(), R.end(), radius);
+    if (adj_ptr) for (int k = 0; k <= K; k++) adj_ptr[k] = ap[k] - ap[0];
+    if (adj) {
+        long long L = ap[K] - ap[0];
+        std::vector<int> a((size_t)std::max(L, 1ll));
+        if (L > 0)
+            CK(cudaMemcpyAsync(a.data(), d_adj + ap[0], sizeof(int) * L, cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        for (long long q = 0; q < L; q++) adj[q] = a[q] - I.k0;
+    }
+}
+
+long long Ensemble::adjacency_len(int b) {
+    const Inst& I = inst_h[b];
+    int ap[2];
+    CK(cudaMemcpyAsync(&ap[0], d_adj_ptr + I.k0, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(&ap[1], d_adj_ptr + I.k0 + I.K, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    return ap[1] - ap[0];
+}
+
+long long Ensemble::dump_pairs(int b, long long cap, unsigned* pairs) {
+    if (!cells_valid) throw StateError("cells not initialised");
+    if (B != 1) throw ArgError("pair dump is available for single-instance systems");
+    (void)b;
+    // size the buffer generously: at most 64 partners per particle
+    long long want = std::max<long long>((long long)N * 64, 1024);
+    if (dump_cap < want) {
+        d_dump = alloc<unsigned>((size_t)2 * want);
+        d_dump_count = alloc<unsigned long long>(1);
+        dump_cap = want;
+    }
+    CK(cudaMemsetAsync(d_dump_count, 0, sizeof(unsigned long long), stream));
+    launch_pairs(false, true);
+    unsigned long long cnt = 0;
+    CK(cudaMemcpyAsync(&cnt, d_dump_count, sizeof(cnt), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    long long n = (long long)std::min<unsigned long long>(cnt, (unsigned long long)dump_cap);
+    std::vector<unsigned> h((size_t)2 * std::max(n, 1ll));
+    if (n > 0) CK(cudaMemcpyAsync(h.data(), d_dump, sizeof(unsigned) * 2 * n, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    std::vector<std::pair<unsigned, unsigned>> v((size_t)n);
+    for (long long q = 0; q < n; q++) v[q] = {h[2 * q], h[2 * q + 1]};
+    std::sort(v.begin(), v.end());
+    long long w = std::min(n, cap);
+    for (long long q = 0; q < w && pairs; q++) { pairs[2 * q] = v[q].first; pairs[2 * q + 1] = v[q].second; }
+    return (long long)cnt;
+}
+
+}  // namespace orbc
+
+// ============================================================== C ABI
+using namespace orbc;
+
+struct orbc_system {
+    Params prm;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Ensemble* ens = nullptr;
+    HostInstance host;
+    bool have_particles = false;
+    std::string err;
+};
+
+// Current device state back into the host copy (exact: grid values), so a
+// re-setup keeps the trajectory.
+static void pull_state(orbc_system* s) {
+    HostInstance& h = s->host;
+    const int n = h.n;
+    std::vector<double> pos((size_t)3 * n), vel((size_t)3 * n), ori((size_t)3 * n), w((size_t)3 * n);
+    long long step = 0;
+    s->ens->get_state(0, pos.data(), vel.data(), ori.data(), w.data(), &step);
+    std::vector<unsigned> ids(n);
+    for (int i = 0; i < n; i++) ids[i] = (unsigned)i;
+    std::vector<unsigned char> ty(n);
+    for (int i = 0; i < n; i++) ty[h.id[i]] = h.type[i];
+    for (int i = 0; i < n; i++)
+        for (int a = 0; a < 3; a++) {
+            h.xq[(size_t)3 * i + a] = llrint(pos[(size_t)3 * i + a] * kGrid);
+            h.vq[(size_t)3 * i + a] = llrint(vel[(size_t)3 * i + a] * kGrid);
+            h.nq[(size_t)3 * i + a] = llrint(ori[(size_t)3 * i + a] * kGrid);
+            h.wq[(size_t)3 * i + a] = llrint(w[(size_t)3 * i + a] * kGrid);
+        }
+    h.id = ids;
+    h.type = ty;
+    h.step0 = step;
+}
+
+static int fail(orbc_system* s, int code, const std::string& what) {
+    if (s) s->err = what;
+    return code;
+}
+
+template <typename F>
+static int guarded(orbc_system* s, F&& f) {
+    try {
+        f();
+        return ORBC_OK;
+    } catch (const ArgError& e) {
+        return fail(s, ORBC_E_ARG, e.what());
+    } catch (const StateError& e) {
+        return fail(s, ORBC_E_STATE, e.what());
+    } catch (const CudaError& e) {
+        return fail(s, e.code == cudaErrorMemoryAllocation ? ORBC_E_NOMEM : ORBC_E_CUDA, e.what());
+    } catch (const std::bad_alloc&) {
+        return fail(s, ORBC_E_NOMEM, "host allocation failed");
+    } catch (const std::exception& e) {
+        return fail(s, ORBC_E_CUDA, e.what());
+    }
+}
+
+static Params to_params(const orbc_params* p) {
+    Params P;
+    P.eps = p->eps; P.sigma = p->sigma; P.rc_lipid = p->rc_lipid; P.mu = p->mu; P.sin_theta0 = p->sin_theta0;
+    P.zeta = p->zeta; P.eps_wca = p->eps_wca; P.sigma_wca = p->sigma_wca;
+    P.dt = p->dt; P.kT = p->kT; P.gamma_t = p->gamma_t; P.gamma_r = p->gamma_r; P.mass = p->mass; P.inertia = p->inertia;
+    for (int a = 0; a < 3; a++) { P.box[a] = p->box[a]; P.periodic[a] = p->periodic[a] ? 1 : 0; }
+    P.n_centroids = p->n_centroids; P.n_lloyd_init = p->n_lloyd_init; P.rebuild_every = p->rebuild_every;
+    P.skin = p->skin; P.grid_h = p->grid_h; P.seed = p->seed; P.instance = p->instance;
+    P.precision = (int)p->precision;
+    return P;
+}
+
+static void check_params(const Params& P) {
+    auto fin = [](double x) { return std::isfinite(x); };
+    if (!(fin(P.eps) && fin(P.sigma) && P.sigma > 0 && fin(P.rc_lipid) && P.rc_lipid > 1.122462048309373 * P.sigma))
+        throw ArgError("invalid lipid potential parameters (need rc_lipid > 2^(1/6) sigma)");
+    if (P.zeta < 1 || P.zeta > 16) throw ArgError("zeta must be in 1..16");
+    if (!(fin(P.eps_wca) && fin(P.sigma_wca) && P.sigma_wca > 0)) throw ArgError("invalid WCA parameters");
+    if (!(P.dt > 0 && fin(P.dt) && P.mass > 0 && P.inertia > 0 && P.kT >= 0 && P.gamma_t >= 0 && P.gamma_r >= 0))
+        throw ArgError("invalid integrator parameters");
+    for (int a = 0; a < 3; a++)
+        if (P.periodic[a] && !(P.box[a] > 0 && P.box[a] < 4096)) throw ArgError("periodic axis needs 0 < box < 4096");
+    if (P.n_centroids < 1) throw ArgError("n_centroids must be >= 1");
+    if (P.n_lloyd_init < 0) throw ArgError("n_lloyd_init must be >= 0");
+    if (P.rebuild_every < 1) throw ArgError("rebuild_every must be >= 1");
+    if (P.rebuild_every > 1 && !(P.skin > 0)) throw ArgError("rebuild_every > 1 needs a positive skin");
+    if (!(P.skin >= 0 && fin(P.skin)) || !(P.grid_h >= 0 && fin(P.grid_h))) throw ArgError("invalid skin or grid_h");
+    if (P.precision != 0 && P.precision != 1) throw ArgError("unknown precision");
+}
+
+extern "C" {
+
+void orbc_default_params(orbc_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->eps = 1.0; p->sigma = 1.0; p->rc_lipid = 2.6; p->mu = 3.0; p->sin_theta0 = 0.0; p->zeta = 4;
+    p->eps_wca = 1.0; p->sigma_wca = 1.0;
+    p->dt = 0.01; p->kT = 0.2; p->gamma_t = 1.0; p->gamma_r = 1.0; p->mass = 1.0; p->inertia = 1.0;
+    p->n_centroids = 64; p->n_lloyd_init = 10; p->rebuild_every = 1; p->skin = 0.0; p->grid_h = 0.0;
+    p->seed = 0; p->instance = 0; p->precision = ORBC_F32_FORCE_F64_STATE;
+}
+
+int orbc_create(const orbc_params* params, void* cuda_stream, orbc_system** out) {
+    if (!params || !out) return ORBC_E_ARG;
+    *out = nullptr;
+    orbc_system* s = new (std::nothrow) orbc_system();
+    if (!s) return ORBC_E_NOMEM;
+    int rc = guarded(s, [&] {
+        s->prm = to_params(params);
+        check_params(s->prm);
+        if (cuda_stream) s->stream = (cudaStream_t)cuda_stream;
+        else { CK(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)); s->own_stream = true; }
+        s->ens = new Ensemble(s->stream);
+    });
+    if (rc != ORBC_OK) {
+        delete s;
+        return rc;
+    }
+    *out = s;
+    return ORBC_OK;
+}
+
+int orbc_set_particles(orbc_system* s, int n, const double* pos, const double* vel, const double* ori,
+                       const double* angvel, const unsigned char* type, const unsigned* id) {
+    if (!s) return ORBC_E_ARG;
+    return guarded(s, [&] {
+        if (n < 1 || !pos || !vel || !ori || !angvel || !type || !id) throw ArgError("null pointer or n < 1");
+        HostInstance h;
+        h.prm = s->prm;
+        h.n = n;
+        h.xq.resize((size_t)3 * n); h.vq.resize((size_t)3 * n); h.nq.assign((size_t)3 * n, 0); h.wq.assign((size_t)3 * n, 0);
+        h.type.assign(type, type + n);
+        h.id.assign(id, id + n);
+        std::vector<char> seen(n, 0);
+        for (int i = 0; i < n; i++) {
+            if (id[i] >= (unsigned)n || seen[id[i]]) throw ArgError("ids must be a permutation of 0..n-1");
+            seen[id[i]] = 1;
+            if (type[i] > 2) throw ArgError("unknown particle type");
+            for (int a = 0; a < 3; a++) {
+                double x = pos[3 * i + a], v = vel[3 * i + a];
+                if (!std::isfinite(x) || !std::isfinite(v)) throw ArgError("non-finite position or velocity");
+                if (std::fabs(x) >= 4096.0) throw ArgError("|position| must be < 4096 sigma");
+                if (std::fabs(v) >= 1e6) throw ArgError("|velocity| too large");
+                h.xq[(size_t)3 * i + a] = llrint(x * kGrid);
+                h.vq[(size_t)3 * i + a] = llrint(v * kGrid);
+            }
+            if (type[i] == kLipid) {
+                double o[3], w[3];
+                for (int a = 0; a < 3; a++) { o[a] = ori[3 * i + a]; w[a] = angvel[3 * i + a]; }
+                for (int a = 0; a < 3; a++)
+                    if (!std::isfinite(o[a]) || !std::isfinite(w[a])) throw ArgError("non-finite orientation");
+                double nn = std::sqrt(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]);
+                if (std::fabs(nn - 1.0) > 1e-6) throw ArgError("lipid orientation must be a unit vector");
+                for (int a = 0; a < 3; a++) {
+                    h.nq[(size_t)3 * i + a] = llrint(o[a] * kGrid);
+                    h.wq[(size_t)3 * i + a] = llrint(w[a] * kGrid);
+                }
+            }
+        }
+        s->host = std::move(h);
+        s->have_particles = true;
+        s->ens->setup({s->host});
+    });
+}
+
+int orbc_set_bonds(orbc_system* s, int nb, const int* ij, const double* r0, const double* kb) {
+    if (!s) return ORBC_E_ARG;
+    return guarded(s, [&] {
+        if (!s->have_particles) throw StateError("set particles before bonds");
+        if (nb < 0 || (nb > 0 && (!ij || !r0 || !kb))) throw ArgError("invalid bond arrays");
+        for (int q = 0; q < nb; q++) {
+            if (ij[2 * q] < 0 || ij[2 * q] >= s->host.n || ij[2 * q + 1] < 0 || ij[2 * q + 1] >= s->host.n ||
+                ij[2 * q] == ij[2 * q + 1])
+                throw ArgError("bond id out of range");
+            if (!(r0[q] >= 0 && std::isfinite(r0[q]) && kb[q] >= 0 && std::isfinite(kb[q]))) throw ArgError("invalid bond constants");
+        }
+        s->host.bonds.assign(ij, ij + 2 * (size_t)nb);
+        s->host.r0.assign(r0, r0 + nb);
+        s->host.kb.assign(kb, kb + nb);
+        s->ens->setup({s->host});
+    });
+}
+
+int orbc_init_cells(orbc_system* s, const double* centroids) {
+    if (!s) return ORBC_E_ARG;
+    return guarded(s, [&] {
+        if (!s->have_particles) throw StateError("no particles");
+        if (s->ens->B == 1) pull_state(s);
+        if (centroids) {
+            for (int q = 0; q < 3 * s->prm.n_centroids; q++)
+                if (!std::isfinite(centroids[q]) || std::fabs(centroids[q]) >= 4096.0) throw ArgError("invalid centroid");
+            s->host.centroids.assign(centroids, centroids + 3 * (size_t)s->prm.n_centroids);
+        } else {
+            s->host.centroids.clear();
+        }
+        s->ens->setup({s->host});
+        s->ens->init_cells();
+    });
+}
+
+int orbc_rebuild_cells(orbc_system* s) {
+    if (!s) return ORBC_E_ARG;
+    return guarded(s, [&] {
+        if (!s->ens->cells_valid) throw StateError("cells not initialised");
+        s->ens->rebuild();
+        unsigned st = s->ens->read_status(true);
+        if (st) throw StateError("rebuild flagged status " + std::to_string(st));
+    });
+}
+
+static int status_code(unsigned st) {
+    if (st & kStatusTimeout) return ORBC_E_TIMEOUT;
+    if (st & (kStatusNaN | kStatusPairForceRange)) return ORBC_E_NAN;
+    return ORBC_E_STATE;
+}
+
+int orbc_compute_forces(orbc_system* s, double* energies_out) {
+    if (!s) return ORBC_E_ARG;
+    unsigned st = 0;
+    int rc = guarded(s, [&] {
+        s->ens->compute_forces(energies_out != nullptr);
+        st = s->ens->read_status(true);
+        if (!st && energies_out) {
+            std::vector<double> e;
+            s->ens->energies(e);
+            for (int q = 0; q < 5; q++) energies_out[q] = e[q];
+        }
+    });
+    if (rc == ORBC_OK && st) return fail(s, status_code(st), "device status " + std::to_string(st));
+    return rc;
+}
+
+int orbc_integrate(orbc_system* s, int nsteps) {
+    if (!s) return ORBC_E_ARG;
+    if (nsteps < 0) return fail(s, ORBC_E_ARG, "nsteps < 0");
+    unsigned st = 0;
+    int rc = guarded(s, [&] {
+        s->ens->integrate(nsteps);
+        st = s->ens->read_status(true);
+    });
+    if (rc == ORBC_OK && st) return fail(s, status_code(st), "device status " + std::to_string(st));
+    return rc;
+}
+
+int orbc_get_state(orbc_system* s, double* pos, double* vel, double* ori, double* angvel, long long* step) {
+    if (!s) return ORBC_E_ARG;
+    return guarded(s, [&] {
+        if (!s->have_particles) throw StateError("no particles");
+        s->ens->get_state(0, pos, vel, ori, angvel, step);
+    });
+}
+
+int orbc_get_forces(orbc_system* s, double* force, double* torque) {
+    if (!s) return ORBC_E_ARG;
+    return guarded(s, [&] {
+        if (!s->ens->forces_valid) throw StateError("forces not computed");
+        s->ens->get_forces(0, force, torque);
+    });
+}
+
+int orbc_get_cells(orbc_system* s, int* cell_of_id, unsigned* slot_ids, double* centroids, int* cell_start,
+                   double* radius, int* adj_ptr, int* adj) {
+    if (!s) return ORBC_E_ARG;
+    return guarded(s, [&] {
+        if (!s->ens->cells_valid) throw StateError("cells not initialised");
+        s->ens->get_cells(0, cell_of_id, slot_ids, centroids, cell_start, radius, adj_ptr, adj);
+    });
+}
+
+int orbc_get_adjacency_len(orbc_system* s, long long* len) {
+    if (!s || !len) return ORBC_E_ARG;
+    return guarded(s, [&] {
+        if (!s->ens->cells_valid) throw StateError("cells not initialised");
+        *len = s->ens->adjacency_len(0);
+    });
+}
+
+int orbc_dump_pairs(orbc_system* s, long long cap, unsigned* pairs, long long* npairs) {
+    if (!s || !npairs || cap < 0) return ORBC_E_ARG;
+    return guarded(s, [&] { *npairs = s->ens->dump_pairs(0, cap, pairs); });
+}
+
+int orbc_set_timing(orbc_system* s, int on) {
+    if (!s) return ORBC_E_ARG;
+    s->ens->timing = on != 0;
+    s->ens->reset_times();
+    return ORBC_OK;
+}
+
+int orbc_get_kernel_times(orbc_system* s, char* names_csv, int names_cap, float* ms, int cap, int* count) {
+    if (!s || !count) return ORBC_E_ARG;
+    auto& t = s->ens->kernel_times;
+    *count = (int)t.size();
+    std::string names;
+    for (size_t q = 0; q < t.size(); q++) {
+        if (q) names += ",";
+        names += t[q].name + ":" + std::to_string(t[q].launches);
+        if (ms && (int)q < cap) ms[q] = (float)t[q].ms;
+    }
+    if (names_csv && names_cap > 0) {
+        std::strncpy(names_csv, names.c_str(), (size_t)names_cap - 1);
+        names_csv[names_cap - 1] = 0;
+    }
+    return ORBC_OK;
+}
+
+const char* orbc_last_error(const orbc_system* s) { return s ? s->err.c_str() : "null handle"; }
+
+void orbc_destroy(orbc_system* s) {
+    if (!s) return;
+    if (s->ens) {
+        cudaStreamSynchronize(s->stream);
+        delete s->ens;
+    }
+    if (s->own_stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,713 @@
+// Adaptive Voronoi cell list (arXiv 1701.02059, "Spatial Searching
+// Algorithm"): centroid M-step, Morton relabel of the centroids, exact
+// nearest-centroid E-step on a centroid grid, stable counting sort of the
+// particles with the state gather, cell radii and neighbouring-cell lists.
+//
+// Every discrete output (cell of each particle, storage permutation,
+// centroids, neighbouring cells) equals the FP64 definition bit for bit:
+// integer arithmetic where the definition is integer (M-step, sort), FP32
+// prefilters with a proven rounding band and an FP64 re-decision inside the
+// band where the definition compares FP64 distances.
+#include "ensemble.cuh"
+
+namespace orbc {
+
+// ============================================================== M-step
+// S_k = sum over lipids of minimg(x_i - c_k) on the 2^-40 grid (int64, exact,
+// order-independent), n_k = lipid count.  Warp-aggregated 64-bit atomics.
+__global__ void k_mstep_accum(View v, const int* __restrict__ cell_of, long long* __restrict__ S,
+                              int* __restrict__ cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool act = i < v.N;
+    int c = -1;
+    long long d[3] = {0, 0, 0};
+    if (act && v.type[i] == kLipid) {
+        c = cell_of[i];
+        int b = find_inst(v.inst_k0, v.B, c);
+        const Inst& I = v.inst[b];
+        for (int a = 0; a < 3; a++)
+            d[a] = minimg_q(v.xq[(size_t)a * v.N + i] - v.cq[(size_t)a * v.Ktot + c], I.boxq[a], I.periodic[a]);
+    }
+    const unsigned full = 0xffffffffu;   // every lane of the warp reaches this point
+    unsigned grp = __match_any_sync(full, c);
+    int leader = __ffs(grp) - 1;
+    int lane = threadIdx.x & 31;
+    long long s0 = d[0], s1 = d[1], s2 = d[2];
+    int n = (c >= 0) ? 1 : 0;
+    // the group leader sums its members (exact integers, any order)
+    long long a0 = 0, a1 = 0, a2 = 0;
+    int an = 0;
+    unsigned m = grp;
+    while (m) {
+        int src = __ffs(m) - 1;
+        m &= m - 1;
+        a0 += __shfl_sync(grp, s0, src);
+        a1 += __shfl_sync(grp, s1, src);
+        a2 += __shfl_sync(grp, s2, src);
+        an += __shfl_sync(grp, n, src);
+    }
+    if (c >= 0 && lane == leader) {
+        atomicAdd((unsigned long long*)&S[(size_t)0 * v.Ktot + c], (unsigned long long)a0);
+        atomicAdd((unsigned long long*)&S[(size_t)1 * v.Ktot + c], (unsigned long long)a1);
+        atomicAdd((unsigned long long*)&S[(size_t)2 * v.Ktot + c], (unsigned long long)a2);
+        atomicAdd(&cnt[c], an);
+    }
+}
+
+// c_k <- c_k + floor((2 S_k + n_k) / (2 n_k)); periodic axes wrap into [0, L).
+__global__ void k_mstep_finish(View v, long long* __restrict__ S, int* __restrict__ cnt, int iter) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= v.Ktot) return;
+    int b = find_inst(v.inst_k0, v.B, k);
+    const Inst& I = v.inst[b];
+    int n = (iter < 0 || iter < I.n_lloyd) ? cnt[k] : 0;   // instances past their k-means rounds keep c
+    for (int a = 0; a < 3; a++) {
+        long long c = v.cq[(size_t)a * v.Ktot + k];
+        if (n > 0) c += floor_div_ll(2 * S[(size_t)a * v.Ktot + k] + n, 2 * (long long)n);
+        if (I.periodic[a]) c = floor_mod_ll(c, I.boxq[a]);
+        v.cq[(size_t)a * v.Ktot + k] = c;
+        S[(size_t)a * v.Ktot + k] = 0;
+    }
+    cnt[k] = 0;
+}
+
+// ============================================================== Morton relabel
+__global__ void k_fill_bbox(long long* bb, int B) {
+    for (int t = threadIdx.x; t < B * 6; t += blockDim.x) bb[t] = ((t % 6) < 3) ? 0x7fffffffffffffffll : (-0x7fffffffffffffffll - 1);
+}
+
+// Bounding box of each instance's centroids (exact int64 min/max).
+__global__ void k_bbox(View v, long long* __restrict__ bb /* [B][6] */) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= v.Ktot) return;
+    int b = find_inst(v.inst_k0, v.B, k);
+    for (int a = 0; a < 3; a++) {
+        long long c = v.cq[(size_t)a * v.Ktot + k];
+        atomicMin((long long*)&bb[b * 6 + a], c);
+        atomicMax((long long*)&bb[b * 6 + 3 + a], c);
+    }
+}
+
+__device__ inline unsigned long long spread3(unsigned long long x) {
+    x &= 0x1fffffull;
+    x = (x | (x << 32)) & 0x1f00000000ffffull;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+// Key: 21 bits per axis, q = min(2^21 - 1, floor((c - lo) * 2^21 / (hi - lo)))
+// in FP64 exactly as the definition (c - lo is exact on the grid).
+__global__ void k_morton_keys(View v, const long long* __restrict__ bb, unsigned long long* __restrict__ key) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= v.Ktot) return;
+    int b = find_inst(v.inst_k0, v.B, k);
+    unsigned long long kk = 0;
+    for (int a = 0; a < 3; a++) {
+        double lo = grid_to_double(bb[b * 6 + a]), hi = grid_to_double(bb[b * 6 + 3 + a]);
+        double s = (hi > lo) ? __ddiv_rn(2097152.0, __dsub_rn(hi, lo)) : 0.0;
+        double t = __dmul_rn(__dsub_rn(grid_to_double(v.cq[(size_t)a * v.Ktot + k]), lo), s);
+        double f = floor(t);
+        unsigned long long q = (f >= 2097151.0) ? 2097151ull : (unsigned long long)f;
+        kk |= spread3(q) << a;
+    }
+    key[k] = kk;
+}
+
+// Sort of (instance, key, index): bitonic sort of 1024-element tiles in
+// shared memory, then each element's rank inside its instance is its rank in
+// its own tile plus, for every other tile of the instance, the number of
+// smaller elements there (binary search).  Keys are unique with the index.
+constexpr int kTile = 1024;
+
+struct SortRec { unsigned long long key; int idx; int inst; };
+
+__device__ inline bool rec_less(const SortRec& a, const SortRec& b) {
+    if (a.inst != b.inst) return a.inst < b.inst;
+    if (a.key != b.key) return a.key < b.key;
+    return a.idx < b.idx;
+}
+
+__global__ void k_tile_sort(View v, const unsigned long long* __restrict__ key, SortRec* __restrict__ out) {
+    __shared__ SortRec sh[kTile];
+    int base = blockIdx.x * kTile;
+    for (int t = threadIdx.x; t < kTile; t += blockDim.x) {
+        int k = base + t;
+        SortRec r;
+        if (k < v.Ktot) { r.key = key[k]; r.idx = k; r.inst = find_inst(v.inst_k0, v.B, k); }
+        else { r.key = ~0ull; r.idx = 0x7fffffff; r.inst = 0x7fffffff; }
+        sh[t] = r;
+    }
+    __syncthreads();
+    for (int size = 2; size <= kTile; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < kTile; t += blockDim.x) {
+                int p = t ^ stride;
+                if (p > t) {
+                    bool up = (t & size) == 0;
+                    SortRec a = sh[t], c = sh[p];
+                    if (rec_less(c, a) == up) { sh[t] = c; sh[p] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int t = threadIdx.x; t < kTile; t += blockDim.x) out[base + t] = sh[t];
+}
+
+// rank -> new cell index; writes order[new] = old and the permuted centroids.
+__global__ void k_rank_scatter(View v, const SortRec* __restrict__ tiles, int ntiles, const long long* __restrict__ cq_old,
+                               int* __restrict__ new_of_old) {
+    int pos = blockIdx.x * blockDim.x + threadIdx.x;   // position in the tiled array
+    if (pos >= ntiles * kTile) return;
+    SortRec me = tiles[pos];
+    if (me.idx >= v.Ktot) return;
+    const Inst& I = v.inst[me.inst];
+    // rank inside the instance: over every tile holding part of the instance,
+    // (records smaller than me) - (records of smaller instances)
+    int rank = 0;
+    int t0 = I.k0 / kTile, t1 = (I.k0 + I.K - 1) / kTile;
+    for (int t = t0; t <= t1; t++) {
+        const SortRec* T = tiles + (size_t)t * kTile;
+        int lo = 0, hi = kTile;   // first element not less than me
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (rec_less(T[mid], me)) lo = mid + 1; else hi = mid;
+        }
+        // count only records of my instance that are smaller
+        int lo2 = 0, hi2 = kTile;   // first record of my instance
+        SortRec first; first.inst = me.inst; first.key = 0; first.idx = -1;
+        while (lo2 < hi2) {
+            int mid = (lo2 + hi2) >> 1;
+            if (rec_less(T[mid], first)) lo2 = mid + 1; else hi2 = mid;
+        }
+        rank += lo - lo2;
+    }
+    int nk = I.k0 + rank;
+    new_of_old[me.idx] = nk;
+    for (int a = 0; a < 3; a++) v.cq[(size_t)a * v.Ktot + nk] = cq_old[(size_t)a * v.Ktot + me.idx];
+}
+
+// ============================================================== centroid grid
+// Fixed per-instance geometry (origin, edge, dims); edge cells extend to
+// infinity, so the face-distance bound of the shell search stays valid for
+// centroids and particles outside the box.
+__device__ inline int grid_coord(long long xq, const Inst& I, int a, float& rel) {
+    long long d = xq - I.gorg[a];
+    if (I.periodic[a]) d = floor_mod_ll(d, I.boxq[a]);
+    // >> 20: units of 2^-20 sigma, |.| < 2^31 for |d| < 2048 sigma
+    long long s = d >> 20;
+    if (s > 2147483647ll) s = 2147483647ll;
+    if (s < -2147483647ll) s = -2147483647ll;
+    rel = (float)(int)s * 9.5367431640625e-07f;
+    int g = (int)floorf(rel * I.ginv[a]);
+    if (g < 0) g = 0;
+    if (g >= I.gdim[a]) g = I.gdim[a] - 1;
+    return g;
+}
+
+__global__ void k_grid_count(View v, int* __restrict__ gcount, int* __restrict__ gidx) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= v.Ktot) return;
+    int b = find_inst(v.inst_k0, v.B, k);
+    const Inst& I = v.inst[b];
+    float r[3];
+    int gx = grid_coord(v.cq[k], I, 0, r[0]);
+    int gy = grid_coord(v.cq[(size_t)v.Ktot + k], I, 1, r[1]);
+    int gz = grid_coord(v.cq[(size_t)2 * v.Ktot + k], I, 2, r[2]);
+    long long g = I.g0 + ((long long)gz * I.gdim[1] + gy) * I.gdim[0] + gx;
+    gidx[k] = (int)g;
+    atomicAdd(&gcount[g], 1);
+}
+
+__global__ void k_grid_fill(View v, const int* __restrict__ gidx, int* __restrict__ cursor) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= v.Ktot) return;
+    int b = find_inst(v.inst_k0, v.B, k);
+    const Inst& I = v.inst[b];
+    int g = gidx[k];
+    int pos = v.gstart[g] + atomicAdd(&cursor[g], 1);
+    float r[3];
+    grid_coord(v.cq[k], I, 0, r[0]);
+    grid_coord(v.cq[(size_t)v.Ktot + k], I, 1, r[1]);
+    grid_coord(v.cq[(size_t)2 * v.Ktot + k], I, 2, r[2]);
+    v.gcent[pos] = k;
+    v.gcf[pos] = make_float4(r[0], r[1], r[2], __int_as_float(k));
+}
+
+// ============================================================== E-step
+// Exact nearest centroid (ties to the lowest index) of every particle.
+// FP32 distances relative to the grid origin have an absolute error below
+// kBand (coordinates < 2048 sigma carry <= 1.3e-4 sigma each); the shell
+// search stops once the unexplored region is farther than best + band, and
+// every centroid within band of the FP32 best is re-scored in FP64 with the
+// definition's operation order.  A single candidate in the band is the
+// exact answer without FP64.
+constexpr float kBandE = 2e-3f;
+
+__device__ inline float axis_dist(float p, float c, const Inst& I, int a) {
+    float d = p - c;
+    if (I.periodic[a]) d -= I.boxf[a] * rintf(d / I.boxf[a]);
+    return d;
+}
+
+__device__ inline int wrap_idx(int x, int n) { x %= n; return x < 0 ? x + n : x; }
+
+// Is grid index w (wrapped) inside the cube of Chebyshev radius r around g?
+__device__ inline bool in_cube(const int w[3], const int g[3], int r, const Inst& I) {
+    for (int a = 0; a < 3; a++) {
+        if (I.periodic[a]) {
+            if (2 * r + 1 >= I.gdim[a]) continue;
+            int d = wrap_idx(w[a] - g[a], I.gdim[a]);
+            if (min(d, I.gdim[a] - d) > r) return false;
+        } else {
+            if (w[a] < g[a] - r || w[a] > g[a] + r) return false;
+        }
+    }
+    return true;
+}
+
+// Visit every grid cell of cube(r) \ cube(r - 1) exactly once (periodic axes
+// wrap; once an axis is fully covered it is enumerated without repeats).
+template <typename F>
+__device__ inline void for_shell(const int g[3], int r, const Inst& I, F&& f) {
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; a++) {
+        if (I.periodic[a]) {
+            if (2 * r + 1 >= I.gdim[a]) { lo[a] = 0; hi[a] = I.gdim[a] - 1; }
+            else { lo[a] = g[a] - r; hi[a] = g[a] + r; }
+        } else {
+            lo[a] = max(0, g[a] - r);
+            hi[a] = min(I.gdim[a] - 1, g[a] + r);
+        }
+    }
+    for (int z = lo[2]; z <= hi[2]; z++)
+        for (int y = lo[1]; y <= hi[1]; y++)
+            for (int x = lo[0]; x <= hi[0]; x++) {
+                int w[3] = { I.periodic[0] ? wrap_idx(x, I.gdim[0]) : x, I.periodic[1] ? wrap_idx(y, I.gdim[1]) : y,
+                             I.periodic[2] ? wrap_idx(z, I.gdim[2]) : z };
+                if (r > 0 && in_cube(w, g, r - 1, I)) continue;
+                long long gg = I.g0 + ((long long)w[2] * I.gdim[1] + w[1]) * I.gdim[0] + w[0];
+                f(gg);
+            }
+}
+
+// lower bound of the distance from p to anything outside the searched cube
+__device__ inline float shell_bound(const float p[3], const int g[3], int r, const Inst& I, bool& exhausted) {
+    float lb = 3.0e38f;
+    exhausted = true;
+    for (int a = 0; a < 3; a++) {
+        if (I.periodic[a]) {
+            if (2 * r + 1 >= I.gdim[a]) continue;
+            float h = I.gh[a];
+            float lo = p[a] - (g[a] - r) * h, hi = (g[a] + r + 1) * h - p[a];
+            lb = fminf(lb, fminf(lo, hi));
+            exhausted = false;
+        } else {
+            if (g[a] - r > 0) { lb = fminf(lb, p[a] - (g[a] - r) * I.gh[a]); exhausted = false; }
+            if (g[a] + r < I.gdim[a] - 1) { lb = fminf(lb, (g[a] + r + 1) * I.gh[a] - p[a]); exhausted = false; }
+        }
+    }
+    return lb;
+}
+
+__global__ void k_estep(View v, int* __restrict__ cell_out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= v.N) return;
+    int b = find_inst(v.inst_p0, v.B, i);
+    const Inst& I = v.inst[b];
+    long long xq[3] = { v.xq[i], v.xq[(size_t)v.N + i], v.xq[(size_t)2 * v.N + i] };
+    float p[3];
+    int g[3];
+    for (int a = 0; a < 3; a++) g[a] = grid_coord(xq[a], I, a, p[a]);
+    float best = 3.0e38f;     // FP32 distance squared
+    int r = 0;
+    const int rmax = max(I.gdim[0], max(I.gdim[1], I.gdim[2]));
+    for (;; r++) {
+        for_shell(g, r, I, [&](long long gg) {
+            for (int q = v.gstart[gg]; q < v.gstart[gg + 1]; q++) {
+                float4 c = v.gcf[q];
+                float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1), dz = axis_dist(p[2], c.z, I, 2);
+                float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                best = fminf(best, d2);
+            }
+        });
+        bool ex;
+        float lb = shell_bound(p, g, r, I, ex);
+        if (ex || r >= rmax) break;
+        if (best < 3.0e38f && lb > sqrtf(best) + kBandE) break;
+    }
+    // second pass over the searched cube: candidates within the band
+    float lim = sqrtf(best) + kBandE;
+    float lim2 = lim * lim;
+    int ncand = 0, k1 = -1, bestk = -1;
+    double best64 = 0.0;
+    for (int rr = 0; rr <= r; rr++) {
+        for_shell(g, rr, I, [&](long long gg) {
+            for (int q = v.gstart[gg]; q < v.gstart[gg + 1]; q++) {
+                float4 c = v.gcf[q];
+                float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1), dz = axis_dist(p[2], c.z, I, 2);
+                float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (d2 <= lim2) {
+                    int k = __float_as_int(c.w);
+                    ncand++;
+                    if (ncand == 1) { k1 = k; continue; }
+                    if (ncand == 2) {
+                        best64 = dist2_grid_d(xq[0], xq[1], xq[2], v.cq[k1], v.cq[(size_t)v.Ktot + k1],
+                                              v.cq[(size_t)2 * v.Ktot + k1], I);
+                        bestk = k1;
+                    }
+                    double d64 = dist2_grid_d(xq[0], xq[1], xq[2], v.cq[k], v.cq[(size_t)v.Ktot + k],
+                                              v.cq[(size_t)2 * v.Ktot + k], I);
+                    if (d64 < best64 || (d64 == best64 && k < bestk)) { best64 = d64; bestk = k; }
+                }
+            }
+        });
+    }
+    if (ncand == 0) {   // unreachable for finite input: the search covers every centroid
+        atomicOr(v.status, kStatusGridRange);
+        cell_out[i] = I.k0;
+        return;
+    }
+    cell_out[i] = (ncand == 1) ? k1 : bestk;
+}
+
+// ============================================================== stable counting sort
+__global__ void k_hist(int N, const int* __restrict__ cell, int* __restrict__ cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) atomicAdd(&cnt[cell[i]], 1);
+}
+
+__global__ void k_scatter(int N, const int* __restrict__ cell, const int* __restrict__ start, int* __restrict__ cursor,
+                          int* __restrict__ tmp) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int c = cell[i];
+    tmp[start[c] + atomicAdd(&cursor[c], 1)] = i;
+}
+
+// Sort each cell's slot list ascending (= old storage order), which makes the
+// scatter stable.  One block per cell, bitonic in shared memory.
+constexpr int kSegMax = 2048;
+__global__ void k_segsort(int Ktot, const int* __restrict__ start, int* __restrict__ tmp, unsigned* status) {
+    __shared__ int sh[kSegMax];
+    int k = blockIdx.x;
+    if (k >= Ktot) return;
+    int s = start[k], e = start[k + 1], n = e - s;
+    if (n <= 1) return;
+    if (n > kSegMax) { if (threadIdx.x == 0) atomicOr(status, kStatusCellOverflow); return; }
+    int m = 1;
+    while (m < n) m <<= 1;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) sh[t] = (t < n) ? tmp[s + t] : 0x7fffffff;
+    __syncthreads();
+    for (int size = 2; size <= m; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                int p = t ^ stride;
+                if (p > t) {
+                    bool up = (t & size) == 0;
+                    int a = sh[t], c = sh[p];
+                    if ((c < a) == up) { sh[t] = c; sh[p] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    for (int t = threadIdx.x; t < n; t += blockDim.x) tmp[s + t] = sh[t];
+}
+
+// ============================================================== gather + mirrors
+__device__ inline int mirror_coord(long long xq, long long cq, const Inst& I, int a, unsigned* status) {
+    long long d = minimg_q(xq - cq, I.boxq[a], I.periodic[a]);
+    long long r = (d + (1ll << (kMirrorShift - 1))) >> kMirrorShift;
+    if (r > 2147483647ll || r < -2147483647ll) { atomicOr(status, kStatusMirrorRange); r = 0; }
+    return (int)r;
+}
+
+__global__ void k_gather(View v, View o, const int* __restrict__ perm, const int* __restrict__ cell_new,
+                         long long* __restrict__ xref) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= v.N) return;
+    int s = perm[p];
+    size_t N = v.N;
+    int c = cell_new[s];
+    int b = find_inst(v.inst_p0, v.B, p);
+    const Inst& I = v.inst[b];
+    long long x[3];
+    for (int a = 0; a < 3; a++) {
+        x[a] = o.xq[a * N + s];
+        v.xq[a * N + p] = x[a];
+        v.vq[a * N + p] = o.vq[a * N + s];
+        v.nq[a * N + p] = o.nq[a * N + s];
+        v.wq[a * N + p] = o.wq[a * N + s];
+        if (xref) xref[a * N + p] = x[a];
+    }
+    unsigned char t = o.type[s];
+    unsigned id = o.id[s];
+    v.type[p] = t;
+    v.id[p] = id;
+    v.cell[p] = c;
+    v.slot_of_id[I.p0 + id] = p;
+    int4 m;
+    m.x = mirror_coord(x[0], v.cq[c], I, 0, v.status);
+    m.y = mirror_coord(x[1], v.cq[(size_t)v.Ktot + c], I, 1, v.status);
+    m.z = mirror_coord(x[2], v.cq[(size_t)2 * v.Ktot + c], I, 2, v.status);
+    m.w = t;
+    v.mq[p] = m;
+    float4 no;
+    no.x = ll_to_float(v.nq[p]) * (float)kGridInv;
+    no.y = ll_to_float(v.nq[N + p]) * (float)kGridInv;
+    no.z = ll_to_float(v.nq[2 * N + p]) * (float)kGridInv;
+    no.w = __int_as_float(p);
+    v.mo[p] = no;
+}
+
+// Mirrors of the current order (after integration without a rebuild).
+__global__ void k_mirrors(View v) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= v.N) return;
+    size_t N = v.N;
+    int c = v.cell[p];
+    int b = find_inst(v.inst_p0, v.B, p);
+    const Inst& I = v.inst[b];
+    int4 m;
+    m.x = mirror_coord(v.xq[p], v.cq[c], I, 0, v.status);
+    m.y = mirror_coord(v.xq[N + p], v.cq[(size_t)v.Ktot + c], I, 1, v.status);
+    m.z = mirror_coord(v.xq[2 * N + p], v.cq[(size_t)2 * v.Ktot + c], I, 2, v.status);
+    m.w = v.type[p];
+    v.mq[p] = m;
+    float4 no;
+    no.x = ll_to_float(v.nq[p]) * (float)kGridInv;
+    no.y = ll_to_float(v.nq[N + p]) * (float)kGridInv;
+    no.z = ll_to_float(v.nq[2 * N + p]) * (float)kGridInv;
+    no.w = __int_as_float(p);
+    v.mo[p] = no;
+}
+
+// ============================================================== cell radius
+// R_k = max_i |x_i - c_k| over the cell (all types), equal to the FP64
+// definition: FP32 from the exact mirror (error < 1e-6 sigma) finds the
+// candidates within band of the maximum, FP64 decides among them.
+constexpr float kBandR = 1e-5f;
+__global__ void k_radius(View v, unsigned long long* __restrict__ rmax_bits /* [B] */) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= v.Ktot) return;
+    int k = warp;
+    int b = find_inst(v.inst_k0, v.B, k);
+    const Inst& I = v.inst[b];
+    int s = v.cell_start[k], e = v.cell_start[k + 1];
+    float mx = 0.f;
+    for (int p = s + lane; p < e; p += 32) {
+        int4 m = v.mq[p];
+        float dx = m.x * kMirrorUnit, dy = m.y * kMirrorUnit, dz = m.z * kMirrorUnit;
+        mx = fmaxf(mx, sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))));
+    }
+    for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    double best = 0.0;
+    long long cx = v.cq[k], cy = v.cq[(size_t)v.Ktot + k], cz = v.cq[(size_t)2 * v.Ktot + k];
+    size_t N = v.N;
+    for (int p = s + lane; p < e; p += 32) {
+        int4 m = v.mq[p];
+        float dx = m.x * kMirrorUnit, dy = m.y * kMirrorUnit, dz = m.z * kMirrorUnit;
+        float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        if (d >= mx - kBandR) {
+            double d2 = dist2_grid_d(v.xq[p], v.xq[N + p], v.xq[2 * N + p], cx, cy, cz, I);
+            best = fmax(best, d2);
+        }
+    }
+    for (int off = 16; off; off >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, off));
+    if (lane == 0) {
+        double R = __dsqrt_rn(best);
+        v.R[k] = R;
+        atomicMax(&rmax_bits[b], (unsigned long long)__double_as_longlong(R));
+    }
+}
+
+// ============================================================== neighbouring cells
+// nbr(k) = { j : |c_k - c_j| < ((R_k + R_j) + r_s + 2 skin)(1 + 1e-12) },
+// evaluated exactly as the FP64 definition for candidates within a band of
+// the threshold, and by an FP32 test with margin elsewhere.
+constexpr float kBandA = 2e-3f;
+
+template <bool FILL>
+__global__ void k_adjacency(View v, const unsigned long long* __restrict__ rmax_bits, int* __restrict__ count) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= v.Ktot) return;
+    int b = find_inst(v.inst_k0, v.B, k);
+    const Inst& I = v.inst[b];
+    double Rk = v.R[k];
+    double Rmax = __longlong_as_double((long long)rmax_bits[b]);
+    float reach = (float)(Rk + Rmax + I.rs + 2.0 * I.skin) + kBandA;
+    long long cx = v.cq[k], cy = v.cq[(size_t)v.Ktot + k], cz = v.cq[(size_t)2 * v.Ktot + k];
+    float p[3];
+    int g[3];
+    g[0] = grid_coord(cx, I, 0, p[0]);
+    g[1] = grid_coord(cy, I, 1, p[1]);
+    g[2] = grid_coord(cz, I, 2, p[2]);
+    int n = 0;
+    int out0 = FILL ? v.adj_ptr[k] : 0;
+    const double tail = (I.rs) + (I.skin + I.skin);
+    for (int r = 0;; r++) {
+        for_shell(g, r, I, [&](long long gg) {
+            for (int q = v.gstart[gg]; q < v.gstart[gg + 1]; q++) {
+                float4 c = v.gcf[q];
+                int j = __float_as_int(c.w);
+                float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1), dz = axis_dist(p[2], c.z, I, 2);
+                float df = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                double t = __dadd_rn(__dadd_rn(Rk, v.R[j]), tail);
+                float tf = (float)t;
+                bool in;
+                if (df < tf - kBandA) in = true;
+                else if (df > tf + kBandA) in = false;
+                else {
+                    double d = __dsqrt_rn(dist2_grid_d(cx, cy, cz, v.cq[j], v.cq[(size_t)v.Ktot + j],
+                                                       v.cq[(size_t)2 * v.Ktot + j], I));
+                    // same operation order as the definition: ((Rk + Rj) + rs) + (skin + skin)
+                    double tt = __dadd_rn(__dadd_rn(__dadd_rn(Rk, v.R[j]), I.rs), __dadd_rn(I.skin, I.skin));
+                    tt = __dmul_rn(tt, 1.0 + 1e-12);
+                    in = d < tt;
+                }
+                if (in) {
+                    if (FILL) {
+                        if (out0 + n < v.adj_cap) v.adj[out0 + n] = j;
+                        else atomicOr(v.status, kStatusAdjOverflow);
+                    }
+                    n++;
+                }
+            }
+        });
+        bool ex;
+        float lb = shell_bound(p, g, r, I, ex);
+        if (ex || lb > reach) break;
+    }
+    if (!FILL) count[k] = n;
+    else {
+        // ascending row (insertion sort, rows are short)
+        int* row = v.adj + out0;
+        if (out0 + n > v.adj_cap) return;
+        for (int a = 1; a < n; a++) {
+            int x = row[a];
+            int c = a - 1;
+            while (c >= 0 && row[c] > x) { row[c + 1] = row[c]; c--; }
+            row[c + 1] = x;
+        }
+    }
+}
+
+// ============================================================== host side
+static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
+
+void Ensemble::build_grid() {
+    View v = view();
+    CK(cudaMemsetAsync(d_gcount, 0, sizeof(int) * (Gtot + 1), stream));
+    k_grid_count<<<nblk(Ktot, 256), 256, 0, stream>>>(v, d_gcount, d_gidx);
+    CK(cudaGetLastError());
+    scan_exclusive(d_gcount, d_gstart, Gtot + 1);
+    CK(cudaMemsetAsync(d_gcount, 0, sizeof(int) * (Gtot + 1), stream));
+    k_grid_fill<<<nblk(Ktot, 256), 256, 0, stream>>>(v, d_gidx, d_gcount);
+    CK(cudaGetLastError());
+}
+
+void Ensemble::mstep_iter(const int* cell_of, int iter) {
+    View v = view();
+    k_mstep_accum<<<nblk(N, 256), 256, 0, stream>>>(v, cell_of, d_S, d_cnt);
+    CK(cudaGetLastError());
+    k_mstep_finish<<<nblk(Ktot, 256), 256, 0, stream>>>(v, d_S, d_cnt, iter);
+    CK(cudaGetLastError());
+}
+
+void Ensemble::mirrors() {
+    k_mirrors<<<nblk(N, 256), 256, 0, stream>>>(view());
+    CK(cudaGetLastError());
+}
+
+// Skin trigger: has any particle moved more than the skin since the last
+// rebuild?  FP32 estimate with a margin that errs towards rebuilding (a
+// rebuild never changes the forces, only where they are found).
+__global__ void k_displacement(View v, const long long* __restrict__ xref, unsigned* __restrict__ flag) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= v.N) return;
+    int b = find_inst(v.inst_p0, v.B, p);
+    const Inst& I = v.inst[b];
+    size_t N = v.N;
+    float d2 = 0.f;
+    for (int a = 0; a < 3; a++) {
+        float d = ll_to_float(minimg_q(v.xq[a * N + p] - xref[a * N + p], I.boxq[a], I.periodic[a])) * (float)kGridInv;
+        d2 = fmaf(d, d, d2);
+    }
+    float s = (float)I.skin * (1.0f - 1e-5f);
+    if (d2 > s * s) atomicOr(flag, 1u);
+}
+
+bool Ensemble::displacement_exceeds_skin() {
+    CK(cudaMemsetAsync(d_cnt + Ktot, 0, sizeof(int), stream));
+    k_displacement<<<nblk(N, 256), 256, 0, stream>>>(view(), d_xref, (unsigned*)(d_cnt + Ktot));
+    CK(cudaGetLastError());
+    unsigned f = 0;
+    CK(cudaMemcpyAsync(&f, d_cnt + Ktot, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    return f != 0;
+}
+
+void Ensemble::estep(int* cell_out) {
+    k_estep<<<nblk(N, 128), 128, 0, stream>>>(view(), cell_out);
+    CK(cudaGetLastError());
+}
+
+void Ensemble::morton_relabel() {
+    View v = view();
+    // bbox init: min = +inf, max = -inf
+    k_fill_bbox<<<1, 64, 0, stream>>>(d_bbox, B);
+    k_bbox<<<nblk(Ktot, 256), 256, 0, stream>>>(v, d_bbox);
+    k_morton_keys<<<nblk(Ktot, 256), 256, 0, stream>>>(v, d_bbox, d_keys);
+    int ntiles = nblk(Ktot, kTile);
+    k_tile_sort<<<ntiles, 256, 0, stream>>>(v, d_keys, (SortRec*)d_sortrec);
+    CK(cudaMemcpyAsync(d_cq_tmp, d_cq, sizeof(long long) * 3 * Ktot, cudaMemcpyDeviceToDevice, stream));
+    k_rank_scatter<<<nblk((long long)ntiles * kTile, 256), 256, 0, stream>>>(v, (const SortRec*)d_sortrec, ntiles, d_cq_tmp,
+                                                                            d_new_of_old);
+    CK(cudaGetLastError());
+}
+
+void Ensemble::finish_cells() {
+    View v = view();
+    morton_relabel();
+    build_grid();
+    estep(d_cell_new);
+    // stable counting sort
+    CK(cudaMemsetAsync(d_cnt, 0, sizeof(int) * (Ktot + 1), stream));
+    k_hist<<<nblk(N, 256), 256, 0, stream>>>(N, d_cell_new, d_cnt);
+    scan_exclusive(d_cnt, d_cell_start, Ktot + 1);
+    CK(cudaMemsetAsync(d_cnt, 0, sizeof(int) * (Ktot + 1), stream));
+    k_scatter<<<nblk(N, 256), 256, 0, stream>>>(N, d_cell_new, d_cell_start, d_cnt, d_perm);
+    k_segsort<<<Ktot, 256, 0, stream>>>(Ktot, d_cell_start, d_perm, d_status);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(d_cnt, 0, sizeof(int) * (Ktot + 1), stream));
+    // gather into the second buffer set, then swap
+    swap_state();
+    View nv = view();
+    View ov = view_alt();
+    k_gather<<<nblk(N, 256), 256, 0, stream>>>(nv, ov, d_perm, d_cell_new, d_xref);
+    CK(cudaGetLastError());
+    // radii and neighbouring cells
+    CK(cudaMemsetAsync(d_rmax, 0, sizeof(unsigned long long) * B, stream));
+    k_radius<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(nv, d_rmax);
+    k_adjacency<false><<<nblk(Ktot, 128), 128, 0, stream>>>(nv, d_rmax, d_adjcount);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(d_adjcount + Ktot, 0, sizeof(int), stream));
+    scan_exclusive(d_adjcount, d_adj_ptr, Ktot + 1);
+    nv = view();
+    k_adjacency<true><<<nblk(Ktot, 128), 128, 0, stream>>>(nv, d_rmax, d_adjcount);
+    CK(cudaGetLastError());
+    cells_valid = true;
+    forces_valid = false;
+    n_rebuilds++;
+}
+
+void Ensemble::rebuild() {
+    mstep(d_cell);
+    finish_cells();
+}
+
+}  // namespace orbc

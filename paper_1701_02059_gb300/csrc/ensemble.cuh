@@ -1,0 +1,178 @@
+// Host-side owner of a packed batch of instances (one or many membranes)
+// and the launchers of every kernel of the hot path.  The plain C-ABI
+// system is a batch of one; the batched arena packs many instances into the
+// same arrays so every phase is one launch over all of them.
+#pragma once
+#include "orbc_internal.cuh"
+
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+namespace orbc {
+
+struct CudaError : std::runtime_error {
+    cudaError_t code;
+    CudaError(cudaError_t c, const std::string& what) : std::runtime_error(what), code(c) {}
+};
+
+#define CK(x)                                                                                                   \
+    do {                                                                                                        \
+        cudaError_t e_ = (x);                                                                                   \
+        if (e_ != cudaSuccess)                                                                                  \
+            throw ::orbc::CudaError(e_, std::string(cudaGetErrorString(e_)) + " at " + __FILE__ + ":" +         \
+                                            std::to_string(__LINE__) + " (" #x ")");                            \
+    } while (0)
+
+struct ArgError : std::runtime_error {
+    explicit ArgError(const std::string& w) : std::runtime_error(w) {}
+};
+struct StateError : std::runtime_error {
+    explicit StateError(const std::string& w) : std::runtime_error(w) {}
+};
+
+// Physical and run parameters of one instance (mirrors orbc_params).
+struct Params {
+    double eps = 1, sigma = 1, rc_lipid = 2.6, mu = 3, sin_theta0 = 0;
+    int zeta = 4;
+    double eps_wca = 1, sigma_wca = 1;
+    double dt = 0.01, kT = 0.2, gamma_t = 1, gamma_r = 1, mass = 1, inertia = 1;
+    double box[3] = {0, 0, 0};
+    int periodic[3] = {0, 0, 0};
+    int n_centroids = 64, n_lloyd_init = 10, rebuild_every = 1;
+    double skin = 0, grid_h = 0;
+    unsigned long long seed = 0;
+    unsigned instance = 0;
+    int precision = 0;   // 0 = FP32 forces, 1 = FP64 everywhere
+};
+
+// One instance as given by the caller (host memory, id order not required).
+struct HostInstance {
+    Params prm;
+    int n = 0;
+    std::vector<long long> xq, vq, nq, wq;   // [n][3] on the 2^-40 grid
+    std::vector<unsigned char> type;
+    std::vector<unsigned> id;
+    std::vector<int> bonds;                  // [nb][2] ids
+    std::vector<double> r0, kb;
+    std::vector<double> centroids;           // optional initial centroids [K][3]
+    long long step0 = 0;                     // steps already taken
+};
+
+class Ensemble {
+public:
+    explicit Ensemble(cudaStream_t s);
+    ~Ensemble();
+    Ensemble(const Ensemble&) = delete;
+    Ensemble& operator=(const Ensemble&) = delete;
+
+    // set-up: particles and bonds of every instance; allocates everything
+    void setup(const std::vector<HostInstance>& list);
+    void init_cells();                       // seeding + Lloyd + reorder
+    void rebuild();                          // one EM update + reorder
+    void compute_forces(bool energies);
+    void integrate(int nsteps);
+    void energies(std::vector<double>& out); // [B][5] after compute_forces(true)
+
+    // host copies (instance b, id order)
+    void get_state(int b, double* pos, double* vel, double* ori, double* angvel, long long* step);
+    void get_forces(int b, double* f, double* t);
+    void get_cells(int b, int* cell_of_id, unsigned* slot_ids, double* centroids, int* cell_start, double* radius,
+                   int* adj_ptr, int* adj);
+    long long adjacency_len(int b);
+    long long dump_pairs(int b, long long cap, unsigned* pairs);
+    unsigned read_status(bool clear);
+    void sync();
+
+    // timing of individual kernels (CUDA events on the stream)
+    bool timing = false;
+    struct TimedKernel { std::string name; double ms = 0; int launches = 0; };
+    std::vector<TimedKernel> kernel_times;
+    void reset_times() { kernel_times.clear(); }
+
+    int B = 0, N = 0, Ktot = 0;
+    long long Gtot = 0;
+    bool cells_valid = false, forces_valid = false;
+    long long n_rebuilds = 0;
+    std::vector<Inst> inst_h;
+    std::vector<Params> prm_h;
+    std::vector<long long> step_h;
+    cudaStream_t stream;
+    int precision = 0;
+
+    View view();
+    View view_alt();
+    void swap_state();
+    void scan_exclusive(const int* in, int* out, long long n);
+
+    // phases
+    void build_grid();
+    void mstep(const int* cell_of) { mstep_iter(cell_of, -1); }
+    void mstep_iter(const int* cell_of, int iter);   // iter < 0: every instance updates
+    bool displacement_exceeds_skin();
+    void launch_kinetic();
+    void estep(int* cell_out);
+    void morton_relabel();
+    void finish_cells();
+    void launch_pairs(bool energies, bool dump);
+    void launch_integrate_first();
+    void launch_kick(bool energies);
+    void mirrors();
+
+    // timing helpers
+    struct Timer;
+    void tic(const char* name);
+    void toc();
+
+private:
+    void free_all();
+    template <typename T> T* alloc(size_t count);
+    std::vector<void*> allocs_;
+    int cur_ = 0;
+    // timing state
+    cudaEvent_t ev0_ = nullptr, ev1_ = nullptr;
+    const char* open_ = nullptr;
+
+public:
+    // device arrays (see View for meanings)
+    Inst* d_inst = nullptr;
+    int *d_p0 = nullptr, *d_k0 = nullptr;
+    long long* d_state[2][4] = {{nullptr}};
+    unsigned char* d_type[2] = {nullptr, nullptr};
+    unsigned* d_id[2] = {nullptr, nullptr};
+    int* d_cell = nullptr;
+    int* d_slot_of_id = nullptr;
+    long long *d_F = nullptr, *d_T = nullptr;
+    int4* d_mq = nullptr;
+    float4* d_mo = nullptr;
+    long long *d_cq = nullptr, *d_cq_tmp = nullptr;
+    int* d_cell_start = nullptr;
+    double* d_R = nullptr;
+    int *d_adj_ptr = nullptr, *d_adj = nullptr, *d_adjcount = nullptr;
+    long long adj_cap = 0;
+    int *d_gstart = nullptr, *d_gcount = nullptr, *d_gcent = nullptr, *d_gidx = nullptr;
+    float4* d_gcf = nullptr;
+    int *d_bptr = nullptr, *d_bpartner = nullptr;
+    float *d_br0 = nullptr, *d_bkb = nullptr;
+    double *d_br0_d = nullptr, *d_bkb_d = nullptr;
+    unsigned* d_status = nullptr;
+    long long* d_S = nullptr;
+    int* d_cnt = nullptr;
+    long long* d_bbox = nullptr;
+    unsigned long long* d_keys = nullptr;
+    void* d_sortrec = nullptr;
+    int* d_new_of_old = nullptr;
+    int *d_cell_new = nullptr, *d_perm = nullptr;
+    unsigned long long* d_rmax = nullptr;
+    long long* d_xref = nullptr;
+    long long* d_energy = nullptr;           // [B][8] fixed-point sums
+    long long* d_step = nullptr;             // [B]
+    unsigned* d_dump = nullptr;
+    unsigned long long* d_dump_count = nullptr;
+    long long dump_cap = 0;
+    std::vector<int> n_lloyd_;
+    std::vector<int*> scan_tmp_;
+    std::vector<long long> scan_tmp_n_;
+};
+
+}  // namespace orbc

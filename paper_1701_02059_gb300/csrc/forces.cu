@@ -1,0 +1,597 @@
+// Pair and bond forces through the Voronoi cells (arXiv 1701.02059, "Force
+// Evaluation"): the quad loop over cell v_i, its neighbouring cells v_j, the
+// particles of v_i and the particles of v_j, with the lipid cells reused at
+// the wider search cutoff for protein pairs and the bond list for linked
+// proteins.
+//
+// GPU design (one CTA of 4 warps per cell):
+//   1. the mirrors of every neighbouring cell (contiguous after the sort) are
+//      staged in shared memory by 1-D bulk async copies (TMA) completing on
+//      an mbarrier, then moved into the cell's own frame: an exact int32
+//      offset (wrap-around arithmetic) and an FP32 copy for filtering;
+//   2. each lane owns one particle i and filters every staged candidate j
+//      with FP32 distances (band 1e-4 sigma), appending hits to a per-lane
+//      queue in shared memory;
+//   3. queued pairs are evaluated with the exact integer displacement
+//      (2^-26 sigma), the type-pair cutoff decided in FP64 inside a 1e-6 sigma
+//      band, and the FP32 (or FP64) potential; force and torque on i are
+//      accumulated exactly in split integers, so the sum does not depend on
+//      the order or on how candidates are split across warps;
+//   4. every pair is computed from both sides (no atomics to other cells, as
+//      the paper does across patch boundaries); bonds of i are added in the
+//      epilogue.
+#include "ensemble.cuh"
+
+namespace orbc {
+
+constexpr int kPairThreads = 128;
+constexpr int kStageCap = 576;     // staged particles per pass (static shared memory < 48 KB)
+constexpr int kQCap = 32;          // queued hits per lane before a flush
+constexpr int kMaxNbr = 64;        // neighbouring cells per pass
+constexpr float kFilterBand = 1e-4f;
+constexpr float kCutBand = 1e-6f;
+
+// ---------------------------------------------------------------- pair terms
+// Lipid pair (see the header of orbc.h for the potential).  d = x_j - x_i.
+// Returns U; adds force on i and torque on i.
+template <typename T>
+__device__ inline T lipid_terms(const Inst& I, T dx, T dy, T dz, T r2, T nix, T niy, T niz, T njx, T njy, T njz,
+                                T& fx, T& fy, T& fz, T& tx, T& ty, T& tz);
+
+__device__ inline float taylor_cos(float x) {
+    // Maclaurin series of cos through x^14 on [0, pi/2]; truncation < 1e-9
+    float x2 = x * x;
+    float p = -1.1470745597729725e-11f;
+    p = fmaf(p, x2, 2.08767569878681e-09f);
+    p = fmaf(p, x2, -2.755731922398589e-07f);
+    p = fmaf(p, x2, 2.48015873015873e-05f);
+    p = fmaf(p, x2, -0.001388888888888889f);
+    p = fmaf(p, x2, 0.041666666666666664f);
+    p = fmaf(p, x2, -0.5f);
+    return fmaf(p, x2, 1.0f);
+}
+__device__ inline float taylor_sin(float x) {
+    // Maclaurin series of sin through x^15 on [0, pi/2]; truncation < 1e-10
+    float x2 = x * x;
+    float p = -7.647163731819816e-13f;
+    p = fmaf(p, x2, 1.6059043836821613e-10f);
+    p = fmaf(p, x2, -2.505210838544172e-08f);
+    p = fmaf(p, x2, 2.7557319223985893e-06f);
+    p = fmaf(p, x2, -0.0001984126984126984f);
+    p = fmaf(p, x2, 0.008333333333333333f);
+    p = fmaf(p, x2, -0.16666666666666666f);
+    return x * fmaf(p, x2, 1.0f);
+}
+
+template <>
+__device__ inline float lipid_terms<float>(const Inst& I, float dx, float dy, float dz, float r2, float nix, float niy,
+                                           float niz, float njx, float njy, float njz, float& fx, float& fy, float& fz,
+                                           float& tx, float& ty, float& tz) {
+    float rinv = rsqrtf(r2);
+    float r = r2 * rinv;
+    // rh = r_ij / r = -(d) / r
+    float hx = -dx * rinv, hy = -dy * rinv, hz = -dz * rinv;
+    float s0 = I.s0;
+    float nin = fmaf(nix, njx, fmaf(niy, njy, niz * njz));
+    float nir = fmaf(nix, hx, fmaf(niy, hy, niz * hz));
+    float njr = fmaf(njx, hx, fmaf(njy, hy, njz * hz));
+    float a = fmaf(s0, njr - nir, fmaf(-nir, njr, nin)) - s0 * s0;
+    float phi = fmaf(I.mu, a - 1.0f, 1.0f);
+    float f, fp, g, gp;
+    if (r < I.rmin) {
+        float q = I.rmin * rinv;
+        float q2 = q * q, q4 = q2 * q2;
+        f = fmaf(I.eps, q4 - 2.0f * q2, I.eps);
+        fp = 4.0f * I.eps * rinv * (q2 - q4);
+        g = -I.eps;
+        gp = 0.0f;
+    } else {
+        float w = 1.5707963267948966f / (I.rc - I.rmin);
+        float th = w * (r - I.rmin);
+        float c = taylor_cos(th), sn = taylor_sin(th);
+        float cp = 1.0f;
+        for (int k = 0; k < 2 * I.zeta - 1; k++) cp *= c;
+        f = 0.0f;
+        fp = 0.0f;
+        g = -I.eps * cp * c;
+        gp = I.eps * (float)(2 * I.zeta) * cp * sn * w;
+    }
+    float U = fmaf(g, phi, f);
+    float wx = fmaf(s0, njx - nix, fmaf(-njr, nix, -nir * njx));
+    float wy = fmaf(s0, njy - niy, fmaf(-njr, niy, -nir * njy));
+    float wz = fmaf(s0, njz - niz, fmaf(-njr, niz, -nir * njz));
+    float wr = fmaf(wx, hx, fmaf(wy, hy, wz * hz));
+    float radial = fmaf(gp, phi, fp);
+    float gm = g * I.mu;
+    float gmr = gm * rinv;
+    fx += -radial * hx - gmr * fmaf(-wr, hx, wx);
+    fy += -radial * hy - gmr * fmaf(-wr, hy, wy);
+    fz += -radial * hz - gmr * fmaf(-wr, hz, wz);
+    // da/dn_i = n_j - (n_j.rh + s0) rh ; tau_i = -g mu (n_i x da/dn_i)
+    float js = njr + s0;
+    float gx = fmaf(-js, hx, njx), gy = fmaf(-js, hy, njy), gz = fmaf(-js, hz, njz);
+    tx += -gm * (niy * gz - niz * gy);
+    ty += -gm * (niz * gx - nix * gz);
+    tz += -gm * (nix * gy - niy * gx);
+    return U;
+}
+
+template <>
+__device__ inline double lipid_terms<double>(const Inst& I, double dx, double dy, double dz, double r2, double nix,
+                                             double niy, double niz, double njx, double njy, double njz, double& fx,
+                                             double& fy, double& fz, double& tx, double& ty, double& tz) {
+    double r = sqrt(r2);
+    double hx = -dx / r, hy = -dy / r, hz = -dz / r;
+    double s0 = I.s0_d;
+    double nin = nix * njx + niy * njy + niz * njz;
+    double nir = nix * hx + niy * hy + niz * hz;
+    double njr = njx * hx + njy * hy + njz * hz;
+    double a = nin - nir * njr + s0 * (njr - nir) - s0 * s0;
+    double phi = 1.0 + I.mu_d * (a - 1.0);
+    double f, fp, g, gp;
+    if (r < I.rmin_d) {
+        double q = I.rmin_d / r;
+        double q2 = q * q, q4 = q2 * q2;
+        f = I.eps_d * (q4 - 2.0 * q2) + I.eps_d;
+        fp = I.eps_d * (-4.0 * q4 / r + 4.0 * q2 / r);
+        g = -I.eps_d;
+        gp = 0.0;
+    } else {
+        double w = 1.5707963267948966 / (I.rc_d - I.rmin_d);
+        double th = w * (r - I.rmin_d);
+        double c, sn;
+        sincos(th, &sn, &c);
+        double cp = 1.0;
+        for (int k = 0; k < 2 * I.zeta - 1; k++) cp *= c;
+        f = 0.0;
+        fp = 0.0;
+        g = -I.eps_d * cp * c;
+        gp = I.eps_d * (double)(2 * I.zeta) * cp * sn * w;
+    }
+    double U = f + g * phi;
+    double wx = -njr * nix - nir * njx + s0 * (njx - nix);
+    double wy = -njr * niy - nir * njy + s0 * (njy - niy);
+    double wz = -njr * niz - nir * njz + s0 * (njz - niz);
+    double wr = wx * hx + wy * hy + wz * hz;
+    double radial = fp + gp * phi;
+    double gm = g * I.mu_d;
+    fx += -radial * hx - gm * (wx - wr * hx) / r;
+    fy += -radial * hy - gm * (wy - wr * hy) / r;
+    fz += -radial * hz - gm * (wz - wr * hz) / r;
+    double js = njr + s0;
+    double gx = njx - js * hx, gy = njy - js * hy, gz = njz - js * hz;
+    tx += -gm * (niy * gz - niz * gy);
+    ty += -gm * (niz * gx - nix * gz);
+    tz += -gm * (nix * gy - niy * gx);
+    return U;
+}
+
+// WCA; d = x_j - x_i; adds the force on i.
+template <typename T>
+__device__ inline T wca_terms(const Inst& I, T dx, T dy, T dz, T r2, T& fx, T& fy, T& fz) {
+    T sig = (sizeof(T) == 4) ? (T)I.sig_wca : (T)I.sig_wca_d;
+    T e = (sizeof(T) == 4) ? (T)I.eps_wca : (T)I.eps_wca_d;
+    T s2 = sig * sig / r2;
+    T s6 = s2 * s2 * s2;
+    T s12 = s6 * s6;
+    T fr = (T)4 * e * ((T)12 * s12 - (T)6 * s6) / r2;
+    fx -= fr * dx;
+    fy -= fr * dy;
+    fz -= fr * dz;
+    return (T)4 * e * (s12 - s6) + e;
+}
+
+// ---------------------------------------------------------------- accumulators
+template <typename T> struct Acc;
+template <> struct Acc<float> {
+    SplitAcc f[3], t[3], u, w;
+    int np, nb;
+    __device__ void zero() { for (int a = 0; a < 3; a++) { f[a].zero(); t[a].zero(); } u.zero(); w.zero(); np = 0; nb = 0; }
+    __device__ void add_pair(float fx, float fy, float fz, float tx, float ty, float tz) {
+        f[0].add(fx); f[1].add(fy); f[2].add(fz); t[0].add(tx); t[1].add(ty); t[2].add(tz); np++;
+    }
+    __device__ void add_bond(float fx, float fy, float fz) { f[0].add(fx); f[1].add(fy); f[2].add(fz); nb++; }
+    __device__ long long F(int a) const { return f[a].finish(np + nb); }
+    __device__ long long Tq(int a) const { return t[a].finish(np); }
+};
+template <> struct Acc<double> {
+    long long f[3], t[3];
+    int np, nb;
+    __device__ void zero() { for (int a = 0; a < 3; a++) { f[a] = 0; t[a] = 0; } np = 0; nb = 0; }
+    __device__ static long long q(double v) { return __double2ll_rn(v * 4294967296.0); }
+    __device__ void add_pair(double fx, double fy, double fz, double tx, double ty, double tz) {
+        f[0] += q(fx); f[1] += q(fy); f[2] += q(fz); t[0] += q(tx); t[1] += q(ty); t[2] += q(tz); np++;
+    }
+    __device__ void add_bond(double fx, double fy, double fz) { f[0] += q(fx); f[1] += q(fy); f[2] += q(fz); nb++; }
+    __device__ long long F(int a) const { return f[a]; }
+    __device__ long long Tq(int a) const { return t[a]; }
+};
+
+// exact FP64 inclusion decision for a pair inside the cutoff band
+__device__ inline bool exact_inside(const View& v, const Inst& I, int pi, int pj, bool ll) {
+    size_t N = v.N;
+    double d2 = dist2_grid_d(v.xq[pj], v.xq[N + pj], v.xq[2 * N + pj], v.xq[pi], v.xq[N + pi], v.xq[2 * N + pi], I);
+    return d2 < (ll ? I.rc2_ll : I.rc2_wca);
+}
+
+__device__ inline bool is_bonded(const View& v, const Inst& I, unsigned idi, unsigned idj) {
+    int s = v.bptr[I.p0 + idi], e = v.bptr[I.p0 + idi + 1];
+    for (int q = s; q < e; q++)
+        if ((unsigned)v.bpartner[q] == idj) return true;
+    return false;
+}
+
+// ---------------------------------------------------------------- TMA helpers
+__device__ inline unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ inline void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ inline void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ inline void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ inline bool mbar_try_wait(unsigned long long* bar, unsigned phase) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after ~2^22 polls (with back-off, well over a
+// second), records a timeout in the status word and returns false.
+__device__ inline bool mbar_wait_bounded(unsigned long long* bar, unsigned phase, unsigned* status) {
+    for (unsigned it = 0; it < (1u << 22); it++) {
+        if (mbar_try_wait(bar, phase)) return true;
+        if (it > 64) __nanosleep(256);
+    }
+    atomicOr(status, kStatusTimeout);
+    return false;
+}
+
+// ---------------------------------------------------------------- the kernel
+struct NbrInfo {
+    int base;       // first staged index
+    int cnt;
+    int start;      // global slot of the first particle
+    int ox, oy, oz; // exact offset c_l - c_k at 2^-26 sigma (wrap-around int32)
+    float fx, fy, fz;
+};
+
+template <typename T, bool ENERGY, bool DUMP>
+__global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __restrict__ energy /* [B][8] */,
+                                                         unsigned* __restrict__ dump, unsigned long long* __restrict__ dump_count,
+                                                         long long dump_cap) {
+    __shared__ alignas(16) int4 sq[kStageCap];
+    __shared__ alignas(16) float4 so[kStageCap];
+    __shared__ alignas(16) float4 sy[kStageCap];
+    // hit queues during the pair loop; split-combination buffer afterwards
+    __shared__ alignas(16) unsigned char scratch[kPairThreads / 32 * kQCap * 32 * 4];
+    __shared__ NbrInfo nb[kMaxNbr];
+    __shared__ unsigned long long bar;
+    __shared__ int s_nstage, s_next, s_self;
+    unsigned (*qbuf)[kQCap][32] = reinterpret_cast<unsigned (*)[kQCap][32]>(scratch);
+
+    const int k = blockIdx.x;
+    const int b = find_inst(v.inst_k0, v.B, k);
+    const Inst& I = v.inst[b];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cs = v.cell_start[k], ce = v.cell_start[k + 1];
+    const int a0 = v.adj_ptr[k];
+    const int a1 = (int)min((long long)v.adj_ptr[k + 1], v.adj_cap);   // overflow is flagged by the adjacency pass
+    const long long ckx = v.cq[k], cky = v.cq[(size_t)v.Ktot + k], ckz = v.cq[(size_t)2 * v.Ktot + k];
+    const float rs_b = I.rsf + kFilterBand;
+    const float rs2f = rs_b * rs_b;
+    const float rcl = sqrtf(I.rc2f_ll), rcw = sqrtf(I.rc2f_wca);
+    const float ll_lo = (rcl - kCutBand) * (rcl - kCutBand), ll_hi = (rcl + kCutBand) * (rcl + kCutBand);
+    const float w_lo = (rcw - kCutBand) * (rcw - kCutBand), w_hi = (rcw + kCutBand) * (rcw + kCutBand);
+    const size_t N = v.N;
+    unsigned phase = 0;
+    if (tid == 0) mbar_init(&bar, 1);
+    __syncthreads();
+
+    for (int it0 = cs; it0 < ce; it0 += kPairThreads) {
+        const int nti = min(kPairThreads, ce - it0);           // particles of this i-tile
+        const int groups = (nti + 31) >> 5;                    // warps for one pass over i
+        const int nsplit = (groups == 1) ? 4 : (groups == 2 ? 2 : 1);
+        const int igrp = warp % groups;
+        const int jsplit = warp / groups;
+        const bool wactive = jsplit < nsplit;
+        const int li = igrp * 32 + lane;
+        const bool ivalid = wactive && li < nti;
+        const int pi = it0 + li;
+        int4 qi = make_int4(0, 0, 0, 0);
+        float4 oi = make_float4(0, 0, 0, 0);
+        float yix = 0, yiy = 0, yiz = 0;
+        unsigned idi = 0;
+        if (ivalid) {
+            qi = v.mq[pi];
+            oi = v.mo[pi];
+            yix = qi.x * kMirrorUnit; yiy = qi.y * kMirrorUnit; yiz = qi.z * kMirrorUnit;
+            if (DUMP) idi = v.id[pi];
+        }
+        const int ti = qi.w & 0xff;
+        Acc<T> acc;
+        acc.zero();
+        T up = 0, vir = 0;
+
+        // passes over chunks of neighbouring cells
+        for (int na = a0; na < a1;) {
+            __syncthreads();
+            if (tid == 0) {
+                int tot = 0, m = 0, nn = na, self = -1;
+                while (nn < a1 && m < kMaxNbr) {
+                    int l = v.adj[nn];
+                    int s = v.cell_start[l], c = v.cell_start[l + 1] - s;
+                    if (tot + c > kStageCap) {
+                        if (m == 0) { atomicOr(v.status, kStatusCellOverflow); nn++; }   // cell larger than a stage
+                        break;
+                    }
+                    long long dx = minimg_q(v.cq[l] - ckx, I.boxq[0], I.periodic[0]);
+                    long long dy = minimg_q(v.cq[(size_t)v.Ktot + l] - cky, I.boxq[1], I.periodic[1]);
+                    long long dz = minimg_q(v.cq[(size_t)2 * v.Ktot + l] - ckz, I.boxq[2], I.periodic[2]);
+                    long long ox = (dx + (1ll << (kMirrorShift - 1))) >> kMirrorShift;
+                    long long oy = (dy + (1ll << (kMirrorShift - 1))) >> kMirrorShift;
+                    long long oz = (dz + (1ll << (kMirrorShift - 1))) >> kMirrorShift;
+                    NbrInfo inf;
+                    inf.base = tot; inf.cnt = c; inf.start = s;
+                    inf.ox = (int)(unsigned)(unsigned long long)ox;
+                    inf.oy = (int)(unsigned)(unsigned long long)oy;
+                    inf.oz = (int)(unsigned)(unsigned long long)oz;
+                    inf.fx = (float)ox * kMirrorUnit; inf.fy = (float)oy * kMirrorUnit; inf.fz = (float)oz * kMirrorUnit;
+                    if (l == k) self = tot;
+                    nb[m] = inf;
+                    tot += c;
+                    m++;
+                    nn++;
+                }
+                s_nstage = m;
+                s_next = nn;
+                s_self = self;
+                if (m > 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_expect_tx(&bar, (unsigned)tot * 32u);
+                    for (int q = 0; q < m; q++)
+                        if (nb[q].cnt > 0) {
+                            bulk_g2s(&sq[nb[q].base], v.mq + nb[q].start, nb[q].cnt * 16u, &bar);
+                            bulk_g2s(&so[nb[q].base], v.mo + nb[q].start, nb[q].cnt * 16u, &bar);
+                        }
+                }
+            }
+            __syncthreads();
+            const int m = s_nstage;
+            const int next = s_next;
+            const int selfj = (s_self >= 0 && ivalid) ? s_self + (pi - cs) : -1;
+            if (m == 0) { na = next; continue; }
+            bool ok = mbar_wait_bounded(&bar, phase, v.status);
+            if (__syncthreads_or(!ok)) {
+                // give the copies in flight a second bounded wait, then leave
+                if (ok == false) mbar_wait_bounded(&bar, phase, v.status);
+                return;
+            }
+            phase ^= 1u;
+            // move the staged mirrors into this cell's frame
+            const int total = nb[m - 1].base + nb[m - 1].cnt;
+            for (int q = 0; q < m; q++) {
+                const NbrInfo inf = nb[q];
+                for (int j = inf.base + tid; j < inf.base + inf.cnt; j += kPairThreads) {
+                    int4 s = sq[j];
+                    float4 y;
+                    y.x = fmaf((float)s.x, kMirrorUnit, inf.fx);
+                    y.y = fmaf((float)s.y, kMirrorUnit, inf.fy);
+                    y.z = fmaf((float)s.z, kMirrorUnit, inf.fz);
+                    y.w = __int_as_float(s.w);
+                    s.x = (int)((unsigned)s.x + (unsigned)inf.ox);
+                    s.y = (int)((unsigned)s.y + (unsigned)inf.oy);
+                    s.z = (int)((unsigned)s.z + (unsigned)inf.oz);
+                    sq[j] = s;
+                    sy[j] = y;
+                }
+            }
+            __syncthreads();
+
+            // filter + evaluate
+            if (wactive) {
+                const int jb = (total * jsplit) / nsplit, je = (total * (jsplit + 1)) / nsplit;
+                int qn = 0;
+                auto flush = [&]() {
+                    int qmax = qn;
+                    for (int off = 16; off; off >>= 1) qmax = max(qmax, __shfl_xor_sync(0xffffffffu, qmax, off));
+                    for (int t = 0; t < qmax; t++) {
+                        if (t >= qn) continue;
+                        const int j = (int)qbuf[warp][t][lane];
+                        const int4 sj = sq[j];
+                        const int tj = sj.w & 0xff;
+                        const bool ll = (ti == kLipid) && (tj == kLipid);
+                        const int dxq = (int)((unsigned)sj.x - (unsigned)qi.x);
+                        const int dyq = (int)((unsigned)sj.y - (unsigned)qi.y);
+                        const int dzq = (int)((unsigned)sj.z - (unsigned)qi.z);
+                        const float dxf = (float)dxq * kMirrorUnit, dyf = (float)dyq * kMirrorUnit, dzf = (float)dzq * kMirrorUnit;
+                        const float r2f = fmaf(dxf, dxf, fmaf(dyf, dyf, dzf * dzf));
+                        const float lo = ll ? ll_lo : w_lo, hi = ll ? ll_hi : w_hi;
+                        if (r2f >= hi) continue;
+                        const float4 oj = so[j];
+                        const int pj = __float_as_int(oj.w);
+                        bool in = r2f < lo;
+                        if (!in) in = exact_inside(v, I, pi, pj, ll);
+                        if (in && !ll && is_bonded(v, I, v.id[pi], v.id[pj])) in = false;
+                        if (!in) continue;
+                        T fx = 0, fy = 0, fz = 0, tx = 0, ty = 0, tz = 0, U;
+                        T dx, dy, dz, r2;
+                        if constexpr (sizeof(T) == 4) {
+                            dx = dxf; dy = dyf; dz = dzf; r2 = r2f;
+                        } else {
+                            dx = grid_to_double(minimg_q(v.xq[pj] - v.xq[pi], I.boxq[0], I.periodic[0]));
+                            dy = grid_to_double(minimg_q(v.xq[N + pj] - v.xq[N + pi], I.boxq[1], I.periodic[1]));
+                            dz = grid_to_double(minimg_q(v.xq[2 * N + pj] - v.xq[2 * N + pi], I.boxq[2], I.periodic[2]));
+                            r2 = dx * dx + dy * dy + dz * dz;
+                        }
+                        if (ll) {
+                            T nix, niy, niz, njx, njy, njz;
+                            if constexpr (sizeof(T) == 4) {
+                                nix = oi.x; niy = oi.y; niz = oi.z; njx = oj.x; njy = oj.y; njz = oj.z;
+                            } else {
+                                nix = grid_to_double(v.nq[pi]); niy = grid_to_double(v.nq[N + pi]);
+                                niz = grid_to_double(v.nq[2 * N + pi]);
+                                njx = grid_to_double(v.nq[pj]); njy = grid_to_double(v.nq[N + pj]);
+                                njz = grid_to_double(v.nq[2 * N + pj]);
+                            }
+                            U = lipid_terms<T>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz);
+                        } else {
+                            U = wca_terms<T>(I, dx, dy, dz, r2, fx, fy, fz);
+                        }
+                        if constexpr (sizeof(T) == 4) {
+                            if (fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))) >= 1000.f ||
+                                fmaxf(fabsf(tx), fmaxf(fabsf(ty), fabsf(tz))) >= 1000.f)
+                                atomicOr(v.status, kStatusPairForceRange);
+                        }
+                        acc.add_pair(fx, fy, fz, tx, ty, tz);
+                        if (ENERGY) {
+                            up += (T)0.5 * U;
+                            vir += (T)0.5 * -(dx * fx + dy * fy + dz * fz);
+                        }
+                        if (DUMP) {
+                            unsigned idj = v.id[pj];
+                            if (idi < idj) {
+                                unsigned long long slot = atomicAdd(dump_count, 1ull);
+                                if ((long long)slot < dump_cap) { dump[2 * slot] = idi; dump[2 * slot + 1] = idj; }
+                            }
+                        }
+                    }
+                    qn = 0;
+                    __syncwarp();
+                };
+                for (int j0 = jb; j0 < je; j0 += 8) {
+                    const int jend = min(j0 + 8, je);
+                    for (int j = j0; j < jend; j++) {
+                        const float4 y = sy[j];
+                        const float ex = y.x - yix, ey = y.y - yiy, ez = y.z - yiz;
+                        const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                        if (ivalid && d2 < rs2f && j != selfj) { qbuf[warp][qn][lane] = (unsigned)j; qn++; }
+                    }
+                    if (__any_sync(0xffffffffu, qn > kQCap - 8)) flush();
+                }
+                flush();
+            }
+            na = next;
+        }
+
+        // bonds of i (each bond evaluated from both ends)
+        T ub = 0;
+        if (ivalid && jsplit == 0 && ti != kLipid) {
+            const unsigned id = v.id[pi];
+            const int s = v.bptr[I.p0 + id], e = v.bptr[I.p0 + id + 1];
+            for (int q = s; q < e; q++) {
+                const int pj = v.slot_of_id[I.p0 + v.bpartner[q]];
+                const long long ddx = minimg_q(v.xq[pj] - v.xq[pi], I.boxq[0], I.periodic[0]);
+                const long long ddy = minimg_q(v.xq[N + pj] - v.xq[N + pi], I.boxq[1], I.periodic[1]);
+                const long long ddz = minimg_q(v.xq[2 * N + pj] - v.xq[2 * N + pi], I.boxq[2], I.periodic[2]);
+                T dx, dy, dz, r0, kb;
+                if constexpr (sizeof(T) == 4) {
+                    dx = ll_to_float(ddx) * (float)kGridInv; dy = ll_to_float(ddy) * (float)kGridInv;
+                    dz = ll_to_float(ddz) * (float)kGridInv;
+                    r0 = v.br0[q]; kb = v.bkb[q];
+                } else {
+                    dx = grid_to_double(ddx); dy = grid_to_double(ddy); dz = grid_to_double(ddz);
+                    r0 = v.br0_d[q]; kb = v.bkb_d[q];
+                }
+                const T r = sqrt(dx * dx + dy * dy + dz * dz);
+                const T dr = r - r0;
+                const T c = kb * dr / r;
+                acc.add_bond(c * dx, c * dy, c * dz);
+                if (ENERGY) {
+                    ub += (T)0.25 * kb * dr * dr;
+                    vir += (T)0.5 * -(c * (dx * dx + dy * dy + dz * dz));
+                }
+            }
+        }
+
+        // combine the j-splits (exact integer sums) and write
+        __syncthreads();
+        if constexpr (sizeof(T) == 4) {
+            int (*red)[14] = reinterpret_cast<int (*)[14]>(scratch);
+            for (int q = tid; q < kPairThreads * 14; q += kPairThreads) (&red[0][0])[q] = 0;
+            __syncthreads();
+            if (ivalid) {
+                atomicAdd(&red[li][0], acc.f[0].h); atomicAdd(&red[li][1], acc.f[0].l);
+                atomicAdd(&red[li][2], acc.f[1].h); atomicAdd(&red[li][3], acc.f[1].l);
+                atomicAdd(&red[li][4], acc.f[2].h); atomicAdd(&red[li][5], acc.f[2].l);
+                atomicAdd(&red[li][6], acc.t[0].h); atomicAdd(&red[li][7], acc.t[0].l);
+                atomicAdd(&red[li][8], acc.t[1].h); atomicAdd(&red[li][9], acc.t[1].l);
+                atomicAdd(&red[li][10], acc.t[2].h); atomicAdd(&red[li][11], acc.t[2].l);
+                atomicAdd(&red[li][12], acc.np); atomicAdd(&red[li][13], acc.nb);
+            }
+            __syncthreads();
+            if (tid < nti) {
+                const int np = red[tid][12], nbd = red[tid][13];
+                const int p = it0 + tid;
+                for (int a = 0; a < 3; a++) {
+                    SplitAcc f; f.h = red[tid][2 * a]; f.l = red[tid][2 * a + 1];
+                    SplitAcc t; t.h = red[tid][6 + 2 * a]; t.l = red[tid][6 + 2 * a + 1];
+                    v.F[a * N + p] = f.finish(np + nbd);
+                    v.T[a * N + p] = t.finish(np);
+                }
+            }
+        } else {
+            long long (*red64)[6] = reinterpret_cast<long long (*)[6]>(scratch);
+            for (int q = tid; q < kPairThreads * 6; q += kPairThreads) (&red64[0][0])[q] = 0;
+            __syncthreads();
+            if (ivalid)
+                for (int a = 0; a < 3; a++) {
+                    atomicAdd((unsigned long long*)&red64[li][a], (unsigned long long)acc.F(a));
+                    atomicAdd((unsigned long long*)&red64[li][3 + a], (unsigned long long)acc.Tq(a));
+                }
+            __syncthreads();
+            if (tid < nti) {
+                const int p = it0 + tid;
+                for (int a = 0; a < 3; a++) { v.F[a * N + p] = red64[tid][a]; v.T[a * N + p] = red64[tid][3 + a]; }
+            }
+        }
+        if (ENERGY) {
+            // per-particle energies to fixed point, exact integer sums per instance
+            long long eu = 0, ew = 0, eb = 0;
+            if (ivalid) {
+                eu = __double2ll_rn((double)up * 4294967296.0);
+                ew = __double2ll_rn((double)vir * 4294967296.0);
+                eb = __double2ll_rn((double)ub * 4294967296.0);
+            }
+            for (int off = 16; off; off >>= 1) {
+                eu += __shfl_xor_sync(0xffffffffu, eu, off);
+                ew += __shfl_xor_sync(0xffffffffu, ew, off);
+                eb += __shfl_xor_sync(0xffffffffu, eb, off);
+            }
+            if (lane == 0) {
+                atomicAdd((unsigned long long*)&energy[b * 8 + 0], (unsigned long long)eu);
+                atomicAdd((unsigned long long*)&energy[b * 8 + 1], (unsigned long long)eb);
+                atomicAdd((unsigned long long*)&energy[b * 8 + 4], (unsigned long long)ew);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- host launchers
+void Ensemble::launch_pairs(bool energies, bool dump) {
+    View v = view();
+    if (energies) CK(cudaMemsetAsync(d_energy, 0, sizeof(long long) * 8 * B, stream));
+    if (precision == 0) {
+        if (dump) k_pairs<float, false, true><<<Ktot, kPairThreads, 0, stream>>>(v, d_energy, d_dump, d_dump_count, dump_cap);
+        else if (energies) k_pairs<float, true, false><<<Ktot, kPairThreads, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
+        else k_pairs<float, false, false><<<Ktot, kPairThreads, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
+    } else {
+        if (dump) k_pairs<double, false, true><<<Ktot, kPairThreads, 0, stream>>>(v, d_energy, d_dump, d_dump_count, dump_cap);
+        else if (energies) k_pairs<double, true, false><<<Ktot, kPairThreads, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
+        else k_pairs<double, false, false><<<Ktot, kPairThreads, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
+    }
+    CK(cudaGetLastError());
+}
+
+}  // namespace orbc

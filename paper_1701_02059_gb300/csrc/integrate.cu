@@ -1,0 +1,216 @@
+// Time stepping ("Software Overview": force and torque, then update of
+// position and orientation).  Reading: BAOAB Langevin (Leimkuhler & Matthews
+// 2013), translational for every particle and rotational for lipids, with
+// Cayley rotations of the director and uniform unit-variance noise from
+// Philox4x32-10 keyed by (seed, instance; id, step, substream).
+//
+// State is int64 on the 2^-40 grid; every update is an increment computed in
+// FP32 (FP64 for ORBC_F64_ALL) and rounded onto the grid, so accumulation is
+// exact integer arithmetic and no FP64 operation runs in the FP32 path.
+#include "ensemble.cuh"
+
+namespace orbc {
+
+template <typename T> struct Num;
+template <> struct Num<float> {
+    static __device__ float st(long long q) { return ll_to_float(q) * (float)kGridInv; }
+    static __device__ float frc(long long q) { return ll_to_float(q) * (float)kForceUnit; }
+    static __device__ long long grid(float x) { return float_to_grid(x); }
+    static __device__ float noise(unsigned w) { return noise_f(w); }
+};
+template <> struct Num<double> {
+    static __device__ double st(long long q) { return grid_to_double(q); }
+    static __device__ double frc(long long q) { return __ll2double_rn(q) * kForceUnit; }
+    static __device__ long long grid(double x) { return double_to_grid(x); }
+    static __device__ double noise(unsigned w) { return noise_d(w); }
+};
+
+template <typename T> struct Consts;
+template <> struct Consts<float> {
+    float hm, hi, hdt, ctm1, st, crm1, sr;
+    __device__ Consts(const Inst& I) : hm(I.h_m), hi(I.h_i), hdt(I.hdt), ctm1(I.ct_m1), st(I.st), crm1(I.cr_m1), sr(I.sr) {}
+};
+template <> struct Consts<double> {
+    double hm, hi, hdt, ctm1, st, crm1, sr;
+    __device__ Consts(const Inst& I)
+        : hm(I.h_m_d), hi(I.h_i_d), hdt(I.hdt_d), ctm1(I.ct_m1_d), st(I.st_d), crm1(I.cr_m1_d), sr(I.sr_d) {}
+};
+
+// Cayley rotation of the director by the rotation vector h w:
+// a = h w / 2, n' = n + 2/(1 + |a|^2) (a x n + a x (a x n)); the increment is
+// added to the grid value.
+template <typename T>
+__device__ inline void cayley(long long nq[3], const long long wq[3], T h) {
+    using V = Num<T>;
+    T n0 = V::st(nq[0]), n1 = V::st(nq[1]), n2 = V::st(nq[2]);
+    T a0 = (T)0.5 * h * V::st(wq[0]), a1 = (T)0.5 * h * V::st(wq[1]), a2 = (T)0.5 * h * V::st(wq[2]);
+    T aa = a0 * a0 + a1 * a1 + a2 * a2;
+    T k = (T)2 / ((T)1 + aa);
+    T b0 = a1 * n2 - a2 * n1, b1 = a2 * n0 - a0 * n2, b2 = a0 * n1 - a1 * n0;      // a x n
+    T c0 = a1 * b2 - a2 * b1, c1 = a2 * b0 - a0 * b2, c2 = a0 * b1 - a1 * b0;      // a x (a x n)
+    nq[0] += V::grid(k * (b0 + c0));
+    nq[1] += V::grid(k * (b1 + c1));
+    nq[2] += V::grid(k * (b2 + c2));
+}
+
+// Unit-norm correction n <- n (1 - delta/2), delta = |n|^2 - 1, first order
+// (|delta| stays at the rounding level, ~1e-9).
+__device__ inline void renormalise(long long nq[3], float) {
+    // exact |n_q|^2 - 2^80 in 128-bit integer arithmetic
+    unsigned long long H = 0, L = 0;
+    for (int a = 0; a < 3; a++) {
+        unsigned long long u = (unsigned long long)(nq[a] < 0 ? -nq[a] : nq[a]);
+        unsigned long long lo = u * u, hi = __umul64hi(u, u);
+        unsigned long long L2 = L + lo;
+        H += hi + (L2 < L ? 1ull : 0ull);
+        L = L2;
+    }
+    long long hd = (long long)H - (1ll << 16);     // multiples of 2^64
+    if (hd != 0 && hd != -1) return;               // far from unit length: leave (not reached in practice)
+    long long D = (long long)L;                    // exact when |D| < 2^63
+    float delta = ll_to_float(D) * 8.271806125530277e-25f;   // 2^-80
+    for (int a = 0; a < 3; a++) nq[a] -= float_to_grid(Num<float>::st(nq[a]) * 0.5f * delta);
+}
+__device__ inline void renormalise(long long nq[3], double) {
+    double n0 = grid_to_double(nq[0]), n1 = grid_to_double(nq[1]), n2 = grid_to_double(nq[2]);
+    double delta = (n0 * n0 + n1 * n1 + n2 * n2) - 1.0;
+    nq[0] -= double_to_grid(n0 * 0.5 * delta);
+    nq[1] -= double_to_grid(n1 * 0.5 * delta);
+    nq[2] -= double_to_grid(n2 * 0.5 * delta);
+}
+
+template <typename T>
+__device__ inline void kick(long long vq[3], long long wq[3], const long long nq[3], const View& v, int p, bool lipid,
+                            const Consts<T>& C) {
+    using V = Num<T>;
+    const size_t N = v.N;
+    for (int a = 0; a < 3; a++) vq[a] += V::grid(C.hm * V::frc(v.F[a * N + p]));
+    if (lipid) {
+        T t0 = V::frc(v.T[p]), t1 = V::frc(v.T[N + p]), t2 = V::frc(v.T[2 * N + p]);
+        T n0 = V::st(nq[0]), n1 = V::st(nq[1]), n2 = V::st(nq[2]);
+        T tn = t0 * n0 + t1 * n1 + t2 * n2;
+        wq[0] += V::grid(C.hi * (t0 - tn * n0));
+        wq[1] += V::grid(C.hi * (t1 - tn * n1));
+        wq[2] += V::grid(C.hi * (t2 - tn * n2));
+    }
+}
+
+// B A O A of one step (the final B follows the force evaluation).
+template <typename T>
+__global__ void k_baoa(View v, const long long* __restrict__ steps) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= v.N) return;
+    using V = Num<T>;
+    const int b = find_inst(v.inst_p0, v.B, p);
+    const Inst& I = v.inst[b];
+    const Consts<T> C(I);
+    const size_t N = v.N;
+    const bool lipid = v.type[p] == kLipid;
+    long long xq[3], vq[3], nq[3] = {0, 0, 0}, wq[3] = {0, 0, 0};
+    for (int a = 0; a < 3; a++) { xq[a] = v.xq[a * N + p]; vq[a] = v.vq[a * N + p]; }
+    if (lipid) for (int a = 0; a < 3; a++) { nq[a] = v.nq[a * N + p]; wq[a] = v.wq[a * N + p]; }
+    // B
+    kick<T>(vq, wq, nq, v, p, lipid, C);
+    // A
+    for (int a = 0; a < 3; a++) xq[a] += V::grid(C.hdt * V::st(vq[a]));
+    if (lipid) cayley<T>(nq, wq, C.hdt);
+    // O
+    const unsigned id = v.id[p];
+    const unsigned long long step = (unsigned long long)steps[b];
+    const uint2 key = make_uint2((unsigned)I.seed, (unsigned)(I.seed >> 32) ^ I.instance);
+    uint4 w0 = philox4x32_10(make_uint4(id, (unsigned)step, (unsigned)(step >> 32), 0u), key);
+    T xi[3] = { V::noise(w0.x), V::noise(w0.y), V::noise(w0.z) };
+    for (int a = 0; a < 3; a++) vq[a] += V::grid(C.ctm1 * V::st(vq[a]) + C.st * xi[a]);
+    if (lipid) {
+        uint4 w1 = philox4x32_10(make_uint4(id, (unsigned)step, (unsigned)(step >> 32), 1u), key);
+        T r0 = V::noise(w1.x), r1 = V::noise(w1.y), r2 = V::noise(w1.z);
+        T n0 = V::st(nq[0]), n1 = V::st(nq[1]), n2 = V::st(nq[2]);
+        T rn = r0 * n0 + r1 * n1 + r2 * n2;
+        wq[0] += V::grid(C.crm1 * V::st(wq[0]) + C.sr * (r0 - rn * n0));
+        wq[1] += V::grid(C.crm1 * V::st(wq[1]) + C.sr * (r1 - rn * n1));
+        wq[2] += V::grid(C.crm1 * V::st(wq[2]) + C.sr * (r2 - rn * n2));
+    }
+    // A
+    for (int a = 0; a < 3; a++) xq[a] += V::grid(C.hdt * V::st(vq[a]));
+    if (lipid) {
+        cayley<T>(nq, wq, C.hdt);
+        renormalise(nq, (T)0);
+    }
+    for (int a = 0; a < 3; a++) { v.xq[a * N + p] = xq[a]; v.vq[a * N + p] = vq[a]; }
+    if (lipid) for (int a = 0; a < 3; a++) { v.nq[a * N + p] = nq[a]; v.wq[a * N + p] = wq[a]; }
+}
+
+// Final B of the step; advances the step counter of every instance.
+template <typename T>
+__global__ void k_kick(View v, long long* __restrict__ steps) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= v.N) return;
+    const int b = find_inst(v.inst_p0, v.B, p);
+    const Inst& I = v.inst[b];
+    const Consts<T> C(I);
+    const size_t N = v.N;
+    const bool lipid = v.type[p] == kLipid;
+    long long vq[3], nq[3] = {0, 0, 0}, wq[3] = {0, 0, 0};
+    for (int a = 0; a < 3; a++) vq[a] = v.vq[a * N + p];
+    if (lipid) for (int a = 0; a < 3; a++) { nq[a] = v.nq[a * N + p]; wq[a] = v.wq[a * N + p]; }
+    kick<T>(vq, wq, nq, v, p, lipid, C);
+    for (int a = 0; a < 3; a++) v.vq[a * N + p] = vq[a];
+    if (lipid) for (int a = 0; a < 3; a++) v.wq[a * N + p] = wq[a];
+    if (p == I.p0) steps[b] += 1;
+}
+
+// Kinetic energies K_trans = sum m v^2 / 2, K_rot = sum_lipids I w^2 / 2,
+// per particle in FP64, summed exactly as 2^-32 fixed point.
+__global__ void k_kinetic(View v, long long* __restrict__ energy) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    long long kt = 0, kr = 0;
+    int b = -1;
+    if (p < v.N) {
+        b = find_inst(v.inst_p0, v.B, p);
+        const Inst& I = v.inst[b];
+        const size_t N = v.N;
+        double s = 0.0, r = 0.0;
+        for (int a = 0; a < 3; a++) { double x = grid_to_double(v.vq[a * N + p]); s += x * x; }
+        kt = __double2ll_rn(0.5 * I.mass * s * 4294967296.0);
+        if (v.type[p] == kLipid) {
+            for (int a = 0; a < 3; a++) { double x = grid_to_double(v.wq[a * N + p]); r += x * x; }
+            kr = __double2ll_rn(0.5 * I.inertia * r * 4294967296.0);
+        }
+    }
+    // warp-aggregate per instance
+    const unsigned grp = __match_any_sync(0xffffffffu, b);
+    long long st = 0, sr = 0;
+    unsigned m = grp;
+    while (m) {
+        int src = __ffs(m) - 1;
+        m &= m - 1;
+        st += __shfl_sync(grp, kt, src);
+        sr += __shfl_sync(grp, kr, src);
+    }
+    if (b >= 0 && (int)(threadIdx.x & 31) == __ffs(grp) - 1) {
+        atomicAdd((unsigned long long*)&energy[b * 8 + 2], (unsigned long long)st);
+        atomicAdd((unsigned long long*)&energy[b * 8 + 3], (unsigned long long)sr);
+    }
+}
+
+static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
+
+void Ensemble::launch_integrate_first() {
+    if (precision == 0) k_baoa<float><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
+    else k_baoa<double><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
+    CK(cudaGetLastError());
+}
+
+void Ensemble::launch_kick(bool energies) {
+    if (precision == 0) k_kick<float><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
+    else k_kick<double><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
+    CK(cudaGetLastError());
+    (void)energies;
+}
+
+void Ensemble::launch_kinetic() {
+    k_kinetic<<<nblk(N, 256), 256, 0, stream>>>(view(), d_energy);
+    CK(cudaGetLastError());
+}
+
+}  // namespace orbc

@@ -1,0 +1,263 @@
+// Internal definitions shared by the CUDA translation units of liborbc.
+//
+// Number formats (chosen for GB300, where FP64 arithmetic and every
+// conversion to or from a 64-bit type run at ~1-2 results/clock/SM against
+// 128 FP32 FMAs):
+//   - state (x, v, director n, angular velocity w): int64 on a 2^-40 grid,
+//     so every value is an exact double and updates are exact integer adds;
+//   - forces and torques: int64 at 2^-32 (eps/sigma, eps), accumulated from
+//     FP32 pair terms through two exact int32 partial sums per component;
+//   - pair-kernel mirror: int32 position relative to the particle's own
+//     centroid at 2^-26 sigma, plus a float4 director;
+//   - FP64 only where a discrete decision must equal the FP64 definition
+//     (nearest centroid, cell radius, neighbouring cells, cutoff inclusion)
+//     and only for the rare candidates inside a rounding band.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace orbc {
+
+constexpr int kGridShift = 40;                       // state: 2^-40
+constexpr double kGrid = 1099511627776.0;            // 2^40
+constexpr double kGridInv = 9.094947017729282e-13;   // 2^-40
+constexpr int kMirrorShift = 14;                     // mirror = state >> 14 -> 2^-26 sigma
+constexpr float kMirrorUnit = 1.4901161193847656e-08f;  // 2^-26
+constexpr double kForceUnit = 2.3283064365386963e-10;   // force/torque/energy fixed point 2^-32
+constexpr float kMagic = 12582912.0f;                // 1.5 * 2^23
+constexpr int kMagicBits = 0x4B400000;
+constexpr int kMaxBondsPerParticle = 8;
+constexpr int kLipid = 0;
+
+// ---------------------------------------------------------------- per-instance descriptor
+struct Inst {
+    // ranges in the packed arrays
+    int p0, n;          // particles
+    int k0, K;          // cells
+    long long g0;       // grid cells
+    int gdim[3];
+    int nlip;
+    long long gorg[3];  // grid origin on the 2^-40 grid
+    float gh[3], ginv[3];  // grid edge per axis and its inverse (sigma)
+    // box
+    double box[3];
+    long long boxq[3];  // box on the 2^-40 grid
+    float boxf[3];
+    int periodic[3];
+    // potential
+    float eps, rmin, rc, mu, s0, eps_wca, sig_wca;
+    int zeta;
+    double eps_d, rmin_d, rc_d, mu_d, s0_d, eps_wca_d, sig_wca_d;
+    double rc2_ll, rc2_wca;     // FP64 squared type-pair cutoffs (inclusion decision)
+    double rs, skin;            // search cutoff and skin
+    float rc2f_ll, rc2f_wca, rsf;
+    // integrator (host-computed constants)
+    float h_m, h_i;             // dt/2/m, dt/2/I
+    float hdt;                  // dt/2
+    float ct_m1, st, cr_m1, sr; // exp(-g dt) - 1 and noise amplitudes
+    double h_m_d, h_i_d, hdt_d, ct_m1_d, st_d, cr_m1_d, sr_d;
+    double mass, inertia;
+    unsigned long long seed;
+    unsigned instance;
+    int rebuild_every;
+    int n_lloyd;        // k-means rounds at initialisation
+};
+
+// ---------------------------------------------------------------- packed device arrays
+struct View {
+    int B;                      // instances
+    int N, Ktot;
+    long long Gtot;
+    const Inst* inst;           // [B]
+    const int* inst_p0;         // [B+1] particle offsets
+    const int* inst_k0;         // [B+1] cell offsets
+    // state (storage order, sorted by cell)
+    long long *xq, *vq, *nq, *wq;   // [3][N] each (axis-major)
+    unsigned char* type;
+    unsigned* id;
+    int* cell;                      // global cell of each slot
+    int* slot_of_id;                // [N] indexed by p0 + id
+    // forces (fixed point 2^-32)
+    long long *F, *T;               // [3][N]
+    // mirrors for the pair kernel
+    int4* mq;                       // x - c at 2^-26 sigma, w = type
+    float4* mo;                     // director, w = slot (int bits)
+    // cells
+    long long* cq;                  // [3][Ktot] centroids on the 2^-40 grid
+    int* cell_start;                // [Ktot+1]
+    double* R;                      // [Ktot] cell radius
+    int* adj_ptr;                   // [Ktot+1]
+    int* adj;                       // [adj_cap]
+    long long adj_cap;
+    // centroid search grid
+    int* gstart;                    // [Gtot+1]
+    int* gcent;                     // [Ktot] centroid ids in grid order
+    float4* gcf;                    // [Ktot] centroid xyz rel. to grid origin, w = id bits
+    // bonds: CSR by (p0 + id)
+    int* bptr;                      // [N+1]
+    int* bpartner;                  // partner id (instance-local)
+    float* br0;
+    float* bkb;
+    double* br0_d;
+    double* bkb_d;
+    // status word written by kernels (bit flags, see kStatus*)
+    unsigned* status;
+};
+
+enum : unsigned {
+    kStatusNaN = 1u,
+    kStatusCellOverflow = 2u,
+    kStatusAdjOverflow = 4u,
+    kStatusMirrorRange = 8u,
+    kStatusPairForceRange = 16u,
+    kStatusTimeout = 32u,
+    kStatusGridRange = 64u,
+};
+
+// ---------------------------------------------------------------- small helpers
+__host__ __device__ inline long long floor_div_ll(long long a, long long b) {   // b > 0
+    long long q = a / b;
+    if ((a % b != 0) && (a < 0)) q -= 1;
+    return q;
+}
+__host__ __device__ inline long long floor_mod_ll(long long a, long long b) { return a - b * floor_div_ll(a, b); }
+
+// Minimum image on the 2^-40 grid: d - L * round(d / L), ties rounding up.
+__device__ inline long long minimg_q(long long d, long long L, int per) {
+    if (!per) return d;
+    // FP32 estimate of round(d/L), then exact correction with integer compares
+    long long k = (long long)rintf((float)d / (float)L);
+    long long r = d - k * L;
+    while (2 * r >= L) { r -= L; }
+    while (2 * r < -L) { r += L; }
+    return r;
+}
+
+// Exact double of a grid value.
+__device__ inline double grid_to_double(long long q) { return __ll2double_rn(q) * kGridInv; }
+
+// FP64 minimum image as the definition states it: d - L * rint(d / L).
+__device__ inline double minimg_d(double d, double L, int per) {
+    if (!per) return d;
+    double q = __ddiv_rn(d, L);
+    double r = rint(q);
+    double p = __dmul_rn(L, r);
+    return __dsub_rn(d, p);
+}
+
+// Squared distance ((dx*dx + dy*dy) + dz*dz) between two grid points, FP64
+// without contraction, minimum image with the FP64 box.
+__device__ inline double dist2_grid_d(long long ax, long long ay, long long az, long long bx, long long by,
+                                      long long bz, const Inst& I) {
+    double dx = minimg_d(__dsub_rn(grid_to_double(ax), grid_to_double(bx)), I.box[0], I.periodic[0]);
+    double dy = minimg_d(__dsub_rn(grid_to_double(ay), grid_to_double(by)), I.box[1], I.periodic[1]);
+    double dz = minimg_d(__dsub_rn(grid_to_double(az), grid_to_double(bz)), I.box[2], I.periodic[2]);
+    double s = __dmul_rn(dx, dx);
+    s = __dadd_rn(s, __dmul_rn(dy, dy));
+    s = __dadd_rn(s, __dmul_rn(dz, dz));
+    return s;
+}
+
+// int64 -> float without a 64-bit conversion: hi * 2^32 + lo.
+__device__ inline float ll_to_float(long long v) {
+    int hi = (int)(v >> 32);
+    unsigned lo = (unsigned)(v & 0xffffffffull);
+    return fmaf((float)hi, 4294967296.0f, (float)lo);
+}
+
+// ---------------------------------------------------------------- exact fixed-point accumulation
+// A per-pair FP32 value f contributes round(f * 2^32) to an int64 sum.  With
+// h = round(f * 2^12) and l = round((f * 2^12 - h) * 2^20) (both exact FP32
+// operations via the 1.5*2^23 magic constant, valid for |f| < 1024),
+// round(f 2^32) = h 2^20 + l.  The raw float bits of the magic sums are added
+// as int32 and the magic offset removed at the end, so each component costs
+// four FP32 operations and two integer adds; integer sums make the result
+// independent of summation order.
+struct SplitAcc {
+    int h, l;
+    __device__ inline void zero() { h = 0; l = 0; }
+    __device__ inline void add(float f) {
+        float t = fmaf(f, 4096.0f, kMagic);
+        float hf = t - kMagic;
+        float r = fmaf(f, 4096.0f, -hf);
+        float u = fmaf(r, 1048576.0f, kMagic);
+        h += __float_as_int(t);
+        l += __float_as_int(u);
+    }
+    __device__ inline long long finish(int count) const {
+        int hh = h - count * kMagicBits;
+        int ll = l - count * kMagicBits;
+        return ((long long)hh << 20) + (long long)ll;
+    }
+};
+
+// Round a float to the 2^-40 grid as int64 (exact FP32 splitting, |v| < 2^11).
+__device__ inline long long float_to_grid(float v) {
+    // v * 2^40 = h * 2^20 + l  with h = round(v * 2^20), |v * 2^20| < 2^22 required -> |v| < 4
+    // for larger increments fall back to a split at 2^-8
+    if (fabsf(v) < 3.9f) {
+        float t = fmaf(v, 1048576.0f, kMagic);
+        float hf = t - kMagic;
+        float r = fmaf(v, 1048576.0f, -hf);
+        float u = fmaf(r, 1048576.0f, kMagic);
+        int h = __float_as_int(t) - kMagicBits;
+        int l = __float_as_int(u) - kMagicBits;
+        return ((long long)h << 20) + (long long)l;
+    }
+    // |v| < 2^11: h = round(v * 2^8), r scaled by 2^16 twice
+    float t = fmaf(v, 256.0f, kMagic);
+    float hf = t - kMagic;
+    float r = fmaf(v, 256.0f, -hf);               // |r| <= 0.5, exact
+    float t2 = fmaf(r, 65536.0f, kMagic);
+    float hf2 = t2 - kMagic;
+    float r2 = fmaf(r, 65536.0f, -hf2);
+    float u = fmaf(r2, 65536.0f, kMagic);
+    long long h = __float_as_int(t) - kMagicBits;
+    long long m = __float_as_int(t2) - kMagicBits;
+    long long l = __float_as_int(u) - kMagicBits;
+    return (h << 32) + (m << 16) + l;
+}
+
+// Round a double to the 2^-40 grid (FP64 path only).
+__device__ inline long long double_to_grid(double v) { return __double2ll_rn(v * kGrid); }
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Counter-based generator of Salmon, Moraes, Dror & Shaw (SC'11).
+__device__ inline uint4 philox4x32_10(uint4 c, uint2 k) {
+    const unsigned M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        unsigned hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        unsigned hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        uint4 n;
+        n.x = hi1 ^ c.y ^ k.x;
+        n.y = lo1;
+        n.z = hi0 ^ c.w ^ k.y;
+        n.w = lo0;
+        c = n;
+        k.x += W0;
+        k.y += W1;
+    }
+    return c;
+}
+
+// Unit-variance uniform noise from a 32-bit word: sqrt(12) ((w + 1/2) 2^-32 - 1/2).
+__device__ inline float noise_f(unsigned w) {
+    float s = (float)(int)(w ^ 0x80000000u);            // w - 2^31
+    return 3.46410161513775f * fmaf(s, 2.3283064365386963e-10f, 1.16415321826934814e-10f);
+}
+__device__ inline double noise_d(unsigned w) {
+    double u = (__uint2double_rn(w) + 0.5) * 2.3283064365386963e-10;
+    return 3.4641016151377544 * (u - 0.5);
+}
+
+__device__ inline int find_inst(const int* off, int B, int x) {   // off[B+1], returns b with off[b] <= x < off[b+1]
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace orbc
