@@ -1,0 +1,327 @@
+"""Throughput of the Voronoi-cell-list CGMD step on a 4,000,000-particle
+biconcave red cell (Evans-Fung shape, 65,536 Voronoi cells, FP32 forces with
+64-bit fixed-point state, cells rebuilt every step).
+
+One JSON line on stdout (rank 0).  A step is one pass of the whole hot path:
+B-A-O-A update, Voronoi rebuild (M-step, Morton relabel, E-step, stable sort,
+radii, neighbouring cells), pair + bond forces, final B.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload rbc-4m|vesicle-62k|patch-2304] [--precision f32|f64]
+
+--impl reference times the FP64 CPU oracle on this machine's host cores on a
+bounded sample of the same workload.  Under torchrun (N > 1) every rank runs
+an independent replica (the path is replicas-only across GPUs) and value is
+the total particle-steps/s over all ranks; the reference arm runs on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s at 4M-particle RBC"
+UNIT = "particle-steps/s"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT = 152
+FP32_LANES = 128
+MAX_SM_MHZ = 2070.0
+# algorithmic work of the hot loop (per half-list pair and per half-list
+# candidate test), counted from the pair expression
+FLOP_PER_PAIR = 100.0
+FLOP_PER_CANDIDATE = 9.0
+
+
+def workload(name: str):
+    from synth import membranes as M
+    if name == "rbc-4m":
+        return M.rbc_4m()
+    if name == "vesicle-62k":
+        return M.vesicle_62k()
+    if name == "patch-2304":
+        return M.flat_patch_2304()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def params_for(mem, precision: str, G):
+    return G.make_params(kT=mem.kT, n_centroids=mem.n_centroids, box=mem.box, periodic=mem.periodic,
+                         seed=2, precision=G.F64_ALL if precision == "f64" else G.F32_FORCE_F64_STATE)
+
+
+def oracle_params(mem, oracle):
+    return (oracle.model(box=mem.box, periodic=mem.periodic),
+            oracle.run(kT=mem.kT, n_centroids=mem.n_centroids, seed=2))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([t.strip() for t in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = sorted(float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit())
+        mx = max((float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()), default=None)
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for q, nm in enumerate(names):
+                if len(r) > 5 + q and r[5 + q].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def algorithmic_work(g, mem):
+    """Half-list pairs and candidate tests of the quad loop over cells."""
+    import numpy as np
+    c = g.cells()
+    cnt = np.diff(c["start"]).astype(np.int64)
+    ptr, adj = c["adj_ptr"], c["adj"]
+    cand = 0
+    for k in range(len(cnt)):
+        js = adj[ptr[k]:ptr[k + 1]]
+        js = js[js >= k]
+        cand += int(sum(cnt[k] * cnt[j] if j != k else cnt[k] * (cnt[k] - 1) // 2 for j in js))
+    npairs = g.pair_count()
+    return npairs, cand
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    import paper_1701_02059_gb300 as G
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    mem = workload(args.workload)
+    stream = torch.cuda.Stream()
+    g = G.System(params_for(mem, args.precision, G), stream=stream.cuda_stream)
+    g.load_membrane(mem)
+    g.init_cells()
+    g.integrate(args.warmup)
+    # per-kernel timing (CUDA events recorded by the library on its stream)
+    g.set_timing(True)
+    clocks = ClockSampler(dev)
+    launches0 = g.launch_count()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    ev0.record(stream)
+    g.integrate(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = g.launch_count() - launches0
+    times = g.kernel_times()
+    g.set_timing(False)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = mem.n * args.steps * world / (ms * 1e-3)
+
+    # roofline of the dominant kernel (pair forces: plain FP32 ALU work)
+    pk = times.get("pairs", {"ms": float("nan"), "launches": 1})
+    npairs, ncand = algorithmic_work(g, mem)
+    flops = npairs * FLOP_PER_PAIR + ncand * FLOP_PER_CANDIDATE
+    pair_ms = pk["ms"] / max(pk["launches"], 1)
+    peak_tflops = SM_COUNT * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    achieved = flops / (pair_ms * 1e-3) / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "pairs_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tr = json.load(open(tpath))
+            if tr.get("workload") == args.workload and tr.get("kernel_rev") == KERNEL_REV:
+                traffic = tr["bytes_per_launch"]
+        except Exception:
+            traffic = None
+    roof = {"bound": "alu", "kernel": "k_pairs", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
+            "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": traffic,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+            "flops_per_launch": flops, "half_list_pairs": npairs, "half_list_candidates": ncand,
+            "kernel_ms": round(pair_ms, 4)}
+    breakdown = {k: round(v["ms"] / max(v["launches"], 1), 4) for k, v in times.items()}
+
+    g.close()
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h2d = sum(a.nbytes for a in (mem.pos, mem.vel, mem.ori, mem.angvel, mem.type, mem.id, mem.bonds, mem.r0, mem.kb))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g2 = G.System(params_for(mem, args.precision, G), stream=stream.cuda_stream)
+        g2.load_membrane(mem)
+        g2.init_cells()
+        g2.integrate(args.steps)
+        st = g2.state()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1)
+        d2h = sum(st[k].nbytes for k in ("pos", "vel", "ori", "angvel"))
+        e2e = {"value": mem.n * args.steps * world / (ems * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "includes": "upload, k-means initialisation, steps, state read-back"}
+        g2.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(mem, budget_s=args.cpu_budget)
+
+    line = {"metric": METRIC if args.workload == "rbc-4m" else f"particle-steps/s at {args.workload}",
+            "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "f32" else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "particles": mem.n, "voronoi_cells": mem.n_centroids,
+                       "precision": ("FP32 forces, int64 fixed-point state (2^-40)" if args.precision == "f32"
+                                     else "FP64 forces and increments, int64 fixed-point state"),
+                       "rebuild_every": 1, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (state and mirrors ~0.9 GB)"},
+            "roofline": roof, "kernel_ms_per_launch": breakdown, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks.summary()}
+    return line
+
+
+def cpu_baseline(mem, budget_s=30.0, steps=None):
+    """The FP64 oracle as it stands, on this machine's host cores: k-means
+    initialisation (untimed), then whole steps until the budget is spent."""
+    import oracle
+    m, r = oracle_params(mem, oracle)
+    s = oracle.OracleSystem(m, r)
+    s.load(mem)
+    s.init_cells()
+    s.compute_forces()
+    done, t0 = 0, time.perf_counter()
+    while True:
+        s.integrate(1)
+        done += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and done >= steps) or (steps is None and (el > budget_s or done >= 3)) or el > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": round(mem.n * done / el, 1), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{done} whole step(s) of the {mem.n}-particle workload after k-means initialisation, {el:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    mem = workload(args.workload)
+    import oracle
+    m, r = oracle_params(mem, oracle)
+    s = oracle.OracleSystem(m, r)
+    s.load(mem)
+    s.init_cells()
+    s.compute_forces()
+    # bounded sample: warm-up and timed steps capped so the run ends within minutes
+    t = time.perf_counter()
+    s.integrate(1)
+    per = time.perf_counter() - t
+    w = max(0, min(args.warmup, int(30.0 / max(per, 1e-9))) - 1)
+    if w:
+        s.integrate(w)
+    k = max(1, min(args.steps, int(120.0 / max(per, 1e-9))))
+    t = time.perf_counter()
+    s.integrate(k)
+    el = time.perf_counter() - t
+    value = mem.n * k / el
+    sample = f"{k} of {args.steps} timed steps (budget 120 s) of the {mem.n}-particle workload, {min(args.warmup, w + 1)} warm-up"
+    return {"metric": METRIC if args.workload == "rbc-4m" else f"particle-steps/s at {args.workload}",
+            "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": k, "warmup": args.warmup,
+            "ms_per_step": round(el / k * 1e3, 2), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "particles": mem.n, "voronoi_cells": mem.n_centroids},
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+KERNEL_REV = "pairs-v1"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="rbc-4m")
+    ap.add_argument("--precision", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--cpu-budget", type=float, default=25.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

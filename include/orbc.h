@@ -187,6 +187,9 @@ ORBC_API int orbc_dump_pairs(orbc_system* s, long long cap, unsigned* pairs, lon
 ORBC_API int orbc_set_timing(orbc_system* s, int on);
 ORBC_API int orbc_get_kernel_times(orbc_system* s, char* names_csv, int names_cap, float* ms, int cap, int* count);
 
+/* Number of CUDA kernels this handle has launched since creation. */
+ORBC_API int orbc_get_launch_count(orbc_system* s, long long* count);
+
 ORBC_API const char* orbc_last_error(const orbc_system* s);
 ORBC_API void orbc_destroy(orbc_system* s);
 

@@ -316,22 +316,32 @@ static void or_bondmap_free(or_bondmap* bm)
     bm->ptr = bm->nbr = NULL;
 }
 
-static inline int or_bonded(const or_bondmap* bm, int ida, int idb)
+/* Reading of the bonded exclusions (the paper keeps a bond list for linked
+ * proteins but states no non-bonded exclusion rule): pairs that are bonded
+ * (1-2) or share a bond partner (1-3) carry no excluded-volume term, as in
+ * bead-spring chain models; chains of 0.55 sigma bonds meeting at a junction
+ * would otherwise start inside each other's repulsive core. */
+static inline int or_excluded(const or_bondmap* bm, int ida, int idb)
 {
     if (!bm || !bm->ptr) return 0;
-    for (int q = bm->ptr[ida]; q < bm->ptr[ida + 1]; q++) if (bm->nbr[q] == idb) return 1;
+    for (int q = bm->ptr[ida]; q < bm->ptr[ida + 1]; q++) {
+        int c = bm->nbr[q];
+        if (c == idb) return 1;
+        for (int w = bm->ptr[idb]; w < bm->ptr[idb + 1]; w++)
+            if (bm->nbr[w] == c) return 1;
+    }
     return 0;
 }
 
 /* Does pair (i, j) interact?  Strict FP64 inclusion d^2 < rc^2 with the
- * type-pair cutoff; bonded protein pairs are excluded from the
+ * type-pair cutoff; 1-2 and 1-3 bonded protein pairs are excluded from the
  * excluded-volume term. */
 static inline int or_interacts(const or_model* m, const or_bondmap* bm, int ti, int tj, int idi, int idj,
                                double r2)
 {
     double rc = or_pair_cut(m, ti, tj);
     if (!(r2 < rc * rc)) return 0;
-    if (!(ti == OR_LIPID && tj == OR_LIPID) && or_bonded(bm, idi, idj)) return 0;
+    if (!(ti == OR_LIPID && tj == OR_LIPID) && or_excluded(bm, idi, idj)) return 0;
     return 1;
 }
 

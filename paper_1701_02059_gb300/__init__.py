@@ -132,6 +132,11 @@ class System:
         return {"cell_of_id": cell, "slot_ids": slots, "centroids": c, "start": start, "radius": R, "adj_ptr": ptr,
                 "adj": adj[:L.value]}
 
+    def pair_count(self) -> int:
+        cnt = C.c_longlong(0)
+        self._check(self._L.orbc_dump_pairs(self._h, 0, None, C.byref(cnt)), "orbc_dump_pairs")
+        return cnt.value
+
     def pairs(self):
         cnt = C.c_longlong(0)
         self._check(self._L.orbc_dump_pairs(self._h, 0, None, C.byref(cnt)), "orbc_dump_pairs")
@@ -141,6 +146,11 @@ class System:
 
     def set_timing(self, on: bool):
         self._check(self._L.orbc_set_timing(self._h, 1 if on else 0), "orbc_set_timing")
+
+    def launch_count(self) -> int:
+        c = C.c_longlong(0)
+        self._check(self._L.orbc_get_launch_count(self._h, C.byref(c)), "orbc_get_launch_count")
+        return c.value
 
     def kernel_times(self):
         buf = C.create_string_buffer(4096)

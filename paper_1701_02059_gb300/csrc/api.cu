@@ -49,7 +49,7 @@ View Ensemble::view() {
     v.xq = d_state[cur_][0]; v.vq = d_state[cur_][1]; v.nq = d_state[cur_][2]; v.wq = d_state[cur_][3];
     v.type = d_type[cur_]; v.id = d_id[cur_];
     v.cell = d_cell; v.slot_of_id = d_slot_of_id;
-    v.F = d_F; v.T = d_T;
+    v.F = d_F; v.T = d_T; v.Fbig = d_Fbig;
     v.mq = d_mq; v.mo = d_mo;
     v.cq = d_cq; v.cell_start = d_cell_start; v.R = d_R; v.adj_ptr = d_adj_ptr; v.adj = d_adj; v.adj_cap = adj_cap;
     v.gstart = d_gstart; v.gcent = d_gcent; v.gcf = d_gcf;
@@ -189,6 +189,7 @@ void Ensemble::setup(const std::vector<HostInstance>& list) {
     d_slot_of_id = alloc<int>(N);
     d_F = alloc<long long>((size_t)3 * N);
     d_T = alloc<long long>((size_t)3 * N);
+    d_Fbig = alloc<long long>((size_t)6 * N);
     d_mq = alloc<int4>(N);
     d_mo = alloc<float4>(N);
     d_cq = alloc<long long>((size_t)3 * Ktot);
@@ -211,6 +212,7 @@ void Ensemble::setup(const std::vector<HostInstance>& list) {
     d_new_of_old = alloc<int>(Ktot);
     d_cell_new = alloc<int>(N);
     d_perm = alloc<int>(N);
+    d_cell_tmp = alloc<int>(N);
     d_rmax = alloc<unsigned long long>(B);
     d_energy = alloc<long long>((size_t)8 * B);
     d_step = alloc<long long>(B);
@@ -543,27 +545,30 @@ long long Ensemble::dump_pairs(int b, long long cap, unsigned* pairs) {
     if (!cells_valid) throw StateError("cells not initialised");
     if (B != 1) throw ArgError("pair dump is available for single-instance systems");
     (void)b;
-    // size the buffer generously: at most 64 partners per particle
-    long long want = std::max<long long>((long long)N * 64, 1024);
-    if (dump_cap < want) {
+    // cap == 0 or no output: count only
+    long long want = pairs ? cap : 0;
+    if (!d_dump_count) d_dump_count = alloc<unsigned long long>(1);
+    if (want > dump_cap) {
         d_dump = alloc<unsigned>((size_t)2 * want);
-        d_dump_count = alloc<unsigned long long>(1);
         dump_cap = want;
     }
+    long long saved = dump_cap;
+    if (want == 0) dump_cap = 0;
     CK(cudaMemsetAsync(d_dump_count, 0, sizeof(unsigned long long), stream));
     launch_pairs(false, true);
+    dump_cap = saved;
     unsigned long long cnt = 0;
     CK(cudaMemcpyAsync(&cnt, d_dump_count, sizeof(cnt), cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
-    long long n = (long long)std::min<unsigned long long>(cnt, (unsigned long long)dump_cap);
+    if (want == 0) return (long long)cnt;
+    long long n = (long long)std::min<unsigned long long>(cnt, (unsigned long long)want);
     std::vector<unsigned> h((size_t)2 * std::max(n, 1ll));
     if (n > 0) CK(cudaMemcpyAsync(h.data(), d_dump, sizeof(unsigned) * 2 * n, cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
     std::vector<std::pair<unsigned, unsigned>> v((size_t)n);
     for (long long q = 0; q < n; q++) v[q] = {h[2 * q], h[2 * q + 1]};
     std::sort(v.begin(), v.end());
-    long long w = std::min(n, cap);
-    for (long long q = 0; q < w && pairs; q++) { pairs[2 * q] = v[q].first; pairs[2 * q + 1] = v[q].second; }
+    for (long long q = 0; q < n; q++) { pairs[2 * q] = v[q].first; pairs[2 * q + 1] = v[q].second; }
     return (long long)cnt;
 }
 
@@ -872,6 +877,12 @@ int orbc_get_kernel_times(orbc_system* s, char* names_csv, int names_cap, float*
         std::strncpy(names_csv, names.c_str(), (size_t)names_cap - 1);
         names_csv[names_cap - 1] = 0;
     }
+    return ORBC_OK;
+}
+
+int orbc_get_launch_count(orbc_system* s, long long* count) {
+    if (!s || !count) return ORBC_E_ARG;
+    *count = s->ens->launches;
     return ORBC_OK;
 }
 

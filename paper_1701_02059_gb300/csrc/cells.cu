@@ -10,6 +10,8 @@
 // band where the definition compares FP64 distances.
 #include "ensemble.cuh"
 
+#include <algorithm>
+
 namespace orbc {
 
 // ============================================================== M-step
@@ -71,20 +73,99 @@ __global__ void k_mstep_finish(View v, long long* __restrict__ S, int* __restric
     cnt[k] = 0;
 }
 
+// Rebuild M-step on cell-sorted particles: one warp per cell sums its lipids'
+// grid displacements (exact int64, shuffles), updates the centroid and
+// folds it into the instance bounding box (block-level, then atomics).
+__global__ void k_mstep_sorted(View v, long long* __restrict__ bb) {
+    __shared__ long long wmin[8][3], wmax[8][3];
+    __shared__ int winst[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = blockIdx.x * 8 + warp;
+    int b = -1;
+    long long c[3] = {0, 0, 0};
+    if (k < v.Ktot) {
+        b = find_inst(v.inst_k0, v.B, k);
+        const Inst& I = v.inst[b];
+        const int s = v.cell_start[k], e = v.cell_start[k + 1];
+        for (int a = 0; a < 3; a++) c[a] = v.cq[(size_t)a * v.Ktot + k];
+        long long S0 = 0, S1 = 0, S2 = 0;
+        int n = 0;
+        const size_t N = v.N;
+        for (int p = s + lane; p < e; p += 32) {
+            if (v.type[p] != kLipid) continue;
+            S0 += minimg_q(v.xq[p] - c[0], I.boxq[0], I.periodic[0]);
+            S1 += minimg_q(v.xq[N + p] - c[1], I.boxq[1], I.periodic[1]);
+            S2 += minimg_q(v.xq[2 * N + p] - c[2], I.boxq[2], I.periodic[2]);
+            n++;
+        }
+        for (int off = 16; off; off >>= 1) {
+            S0 += __shfl_xor_sync(0xffffffffu, S0, off);
+            S1 += __shfl_xor_sync(0xffffffffu, S1, off);
+            S2 += __shfl_xor_sync(0xffffffffu, S2, off);
+            n += __shfl_xor_sync(0xffffffffu, n, off);
+        }
+        long long S[3] = {S0, S1, S2};
+        for (int a = 0; a < 3; a++) {
+            if (n > 0) c[a] += floor_div_ll(2 * S[a] + n, 2 * (long long)n);
+            if (I.periodic[a]) c[a] = floor_mod_ll(c[a], I.boxq[a]);
+        }
+        if (lane == 0)
+            for (int a = 0; a < 3; a++) v.cq[(size_t)a * v.Ktot + k] = c[a];
+    }
+    if (lane == 0) {
+        winst[warp] = b;
+        for (int a = 0; a < 3; a++) { wmin[warp][a] = c[a]; wmax[warp][a] = c[a]; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int cur = -1;
+        long long mn[3], mx[3];
+        for (int w = 0; w <= 8; w++) {
+            int bw = (w < 8) ? winst[w] : -2;
+            if (bw != cur) {
+                if (cur >= 0)
+                    for (int a = 0; a < 3; a++) { atomicMin(&bb[cur * 6 + a], mn[a]); atomicMax(&bb[cur * 6 + 3 + a], mx[a]); }
+                cur = bw;
+                if (bw >= 0) for (int a = 0; a < 3; a++) { mn[a] = wmin[w][a]; mx[a] = wmax[w][a]; }
+            } else if (bw >= 0) {
+                for (int a = 0; a < 3; a++) { mn[a] = min(mn[a], wmin[w][a]); mx[a] = max(mx[a], wmax[w][a]); }
+            }
+        }
+    }
+}
+
 // ============================================================== Morton relabel
 __global__ void k_fill_bbox(long long* bb, int B) {
     for (int t = threadIdx.x; t < B * 6; t += blockDim.x) bb[t] = ((t % 6) < 3) ? 0x7fffffffffffffffll : (-0x7fffffffffffffffll - 1);
 }
 
-// Bounding box of each instance's centroids (exact int64 min/max).
+// Bounding box of each instance's centroids (exact int64 min/max), reduced
+// per block before the atomics.
 __global__ void k_bbox(View v, long long* __restrict__ bb /* [B][6] */) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= v.Ktot) return;
-    int b = find_inst(v.inst_k0, v.B, k);
-    for (int a = 0; a < 3; a++) {
-        long long c = v.cq[(size_t)a * v.Ktot + k];
-        atomicMin((long long*)&bb[b * 6 + a], c);
-        atomicMax((long long*)&bb[b * 6 + 3 + a], c);
+    __shared__ long long smin[256][3], smax[256][3];
+    __shared__ int sb[256];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = threadIdx.x;
+    sb[t] = -1;
+    if (k < v.Ktot) {
+        sb[t] = find_inst(v.inst_k0, v.B, k);
+        for (int a = 0; a < 3; a++) smin[t][a] = smax[t][a] = v.cq[(size_t)a * v.Ktot + k];
+    }
+    __syncthreads();
+    if (t == 0) {
+        int cur = -2;
+        long long mn[3] = {0, 0, 0}, mx[3] = {0, 0, 0};
+        for (int q = 0; q <= 256; q++) {
+            int bq = (q < 256) ? sb[q] : -3;
+            if (bq != cur) {
+                if (cur >= 0)
+                    for (int a = 0; a < 3; a++) { atomicMin(&bb[cur * 6 + a], mn[a]); atomicMax(&bb[cur * 6 + 3 + a], mx[a]); }
+                cur = bq;
+                if (bq >= 0) for (int a = 0; a < 3; a++) { mn[a] = smin[q][a]; mx[a] = smax[q][a]; }
+            } else if (bq >= 0) {
+                for (int a = 0; a < 3; a++) { mn[a] = min(mn[a], smin[q][a]); mx[a] = max(mx[a], smax[q][a]); }
+            }
+        }
     }
 }
 
@@ -313,9 +394,7 @@ __device__ inline float shell_bound(const float p[3], const int g[3], int r, con
     return lb;
 }
 
-__global__ void k_estep(View v, int* __restrict__ cell_out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= v.N) return;
+__device__ void estep_one(const View& v, int i, int* __restrict__ cell_out) {
     int b = find_inst(v.inst_p0, v.B, i);
     const Inst& I = v.inst[b];
     long long xq[3] = { v.xq[i], v.xq[(size_t)v.N + i], v.xq[(size_t)2 * v.N + i] };
@@ -374,6 +453,126 @@ __global__ void k_estep(View v, int* __restrict__ cell_out) {
     cell_out[i] = (ncand == 1) ? k1 : bestk;
 }
 
+// ---- warp-cooperative search for instances without periodic axes: the
+// 32 queries of a warp (consecutive storage slots, hence neighbours in space)
+// share one grid region [lo - r, hi + r]; every lane scores every centroid
+// of the region (broadcast loads), and the region grows by one ring until
+// each lane's unexplored space is provably farther than its band.
+template <typename F>
+__device__ inline void region_ring(const Inst& I, const int lo[3], const int hi[3], int r, F&& f) {
+    int a0[3], a1[3];
+    for (int a = 0; a < 3; a++) { a0[a] = max(0, lo[a] - r); a1[a] = min(I.gdim[a] - 1, hi[a] + r); }
+    for (int z = a0[2]; z <= a1[2]; z++)
+        for (int y = a0[1]; y <= a1[1]; y++)
+            for (int x = a0[0]; x <= a1[0]; x++) {
+                if (r > 0 && x >= lo[0] - r + 1 && x <= hi[0] + r - 1 && y >= lo[1] - r + 1 && y <= hi[1] + r - 1 &&
+                    z >= lo[2] - r + 1 && z <= hi[2] + r - 1)
+                    continue;
+                f(I.g0 + ((long long)z * I.gdim[1] + y) * I.gdim[0] + x);
+            }
+}
+
+__device__ inline float region_bound(const Inst& I, const float p[3], const int lo[3], const int hi[3], int r,
+                                     bool& exhausted) {
+    float lb = 3.0e38f;
+    exhausted = true;
+    for (int a = 0; a < 3; a++) {
+        if (lo[a] - r > 0) { lb = fminf(lb, p[a] - (lo[a] - r) * I.gh[a]); exhausted = false; }
+        if (hi[a] + r < I.gdim[a] - 1) { lb = fminf(lb, (hi[a] + r + 1) * I.gh[a] - p[a]); exhausted = false; }
+    }
+    return lb;
+}
+
+__device__ inline void warp_box(const int g[3], bool valid, int lo[3], int hi[3]) {
+    for (int a = 0; a < 3; a++) {
+        int l = valid ? g[a] : 0x7fffffff, h = valid ? g[a] : -1;
+        for (int off = 16; off; off >>= 1) {
+            l = min(l, __shfl_xor_sync(0xffffffffu, l, off));
+            h = max(h, __shfl_xor_sync(0xffffffffu, h, off));
+        }
+        lo[a] = l;
+        hi[a] = h;
+    }
+}
+
+__global__ void k_estep_warp(View v, int* __restrict__ cell_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < v.N;
+    const int b = valid ? find_inst(v.inst_p0, v.B, i) : -1;
+    int b0 = __shfl_sync(0xffffffffu, b, 0);
+    const int bfirst = __reduce_max_sync(0xffffffffu, valid ? b : -1);
+    if (b0 < 0) b0 = bfirst;
+    const bool same = __all_sync(0xffffffffu, !valid || b == b0);
+    if (b0 < 0) return;
+    const Inst& I = v.inst[b0];
+    const bool periodic = I.periodic[0] | I.periodic[1] | I.periodic[2];
+    if (!same || periodic) {
+        // mixed instances or periodic axes: per-thread shell search
+        if (valid) estep_one(v, i, cell_out);
+        return;
+    }
+    long long xq[3] = {0, 0, 0};
+    float p[3] = {0, 0, 0};
+    int g[3] = {0, 0, 0};
+    if (valid) {
+        xq[0] = v.xq[i]; xq[1] = v.xq[(size_t)v.N + i]; xq[2] = v.xq[(size_t)2 * v.N + i];
+        for (int a = 0; a < 3; a++) g[a] = grid_coord(xq[a], I, a, p[a]);
+    }
+    int lo[3], hi[3];
+    warp_box(g, valid, lo, hi);
+    float best = 3.0e38f, second = 3.0e38f;
+    int bk = -1;
+    int r = 0;
+    for (;; r++) {
+        region_ring(I, lo, hi, r, [&](long long gg) {
+            const int q1 = v.gstart[gg + 1];
+            for (int q = v.gstart[gg]; q < q1; q++) {
+                const float4 c = v.gcf[q];
+                const float dx = p[0] - c.x, dy = p[1] - c.y, dz = p[2] - c.z;
+                const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (d2 < best) { second = best; best = d2; bk = __float_as_int(c.w); }
+                else if (d2 < second) second = d2;
+            }
+        });
+        bool ex;
+        const float lb = region_bound(I, p, lo, hi, r, ex);
+        const bool done = !valid || ex || (best < 3.0e38f && lb > sqrtf(best) + kBandE);
+        if (__all_sync(0xffffffffu, done)) break;
+    }
+    // tie band: every centroid within the band of the FP32 best is re-scored in FP64
+    const float lim = sqrtf(best) + kBandE;
+    const bool amb = valid && second <= lim * lim;
+    if (__any_sync(0xffffffffu, amb)) {
+        double best64 = 1e300;
+        int bk64 = -1;
+        for (int rr = 0; rr <= r; rr++)
+            region_ring(I, lo, hi, rr, [&](long long gg) {
+                const int q1 = v.gstart[gg + 1];
+                for (int q = v.gstart[gg]; q < q1; q++) {
+                    const float4 c = v.gcf[q];
+                    const float dx = p[0] - c.x, dy = p[1] - c.y, dz = p[2] - c.z;
+                    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    if (amb && d2 <= lim * lim) {
+                        const int k = __float_as_int(c.w);
+                        const double d64 = dist2_grid_d(xq[0], xq[1], xq[2], v.cq[k], v.cq[(size_t)v.Ktot + k],
+                                                        v.cq[(size_t)2 * v.Ktot + k], I);
+                        if (d64 < best64 || (d64 == best64 && k < bk64)) { best64 = d64; bk64 = k; }
+                    }
+                }
+            });
+        if (amb) bk = bk64;
+    }
+    if (valid) {
+        if (bk < 0) { atomicOr(v.status, kStatusGridRange); bk = I.k0; }
+        cell_out[i] = bk;
+    }
+}
+
+__global__ void k_estep(View v, int* __restrict__ cell_out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < v.N) estep_one(v, i, cell_out);
+}
+
 // ============================================================== stable counting sort
 __global__ void k_hist(int N, const int* __restrict__ cell, int* __restrict__ cnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -393,11 +592,9 @@ __global__ void k_scatter(int N, const int* __restrict__ cell, const int* __rest
 constexpr int kSegMax = 2048;
 __global__ void k_segsort(int Ktot, const int* __restrict__ start, int* __restrict__ tmp, unsigned* status) {
     __shared__ int sh[kSegMax];
-    int k = blockIdx.x;
-    if (k >= Ktot) return;
+    for (int k = blockIdx.x; k < Ktot; k += gridDim.x) {
     int s = start[k], e = start[k + 1], n = e - s;
-    if (n <= 1) return;
-    if (n > kSegMax) { if (threadIdx.x == 0) atomicOr(status, kStatusCellOverflow); return; }
+    if (n <= 128 || n > kSegMax) continue;   // warp kernel / k_segrank
     int m = 1;
     while (m < n) m <<= 1;
     for (int t = threadIdx.x; t < m; t += blockDim.x) sh[t] = (t < n) ? tmp[s + t] : 0x7fffffff;
@@ -415,6 +612,73 @@ __global__ void k_segsort(int Ktot, const int* __restrict__ start, int* __restri
             __syncthreads();
         }
     for (int t = threadIdx.x; t < n; t += blockDim.x) tmp[s + t] = sh[t];
+    __syncthreads();
+    }
+}
+
+// Cells of up to 128 particles: one warp, bitonic network over 4 values per
+// lane (element e = lane + 32 q), shuffles for strides < 32.
+__global__ void k_segsort_warp(int Ktot, const int* __restrict__ start, int* __restrict__ tmp) {
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= Ktot) return;
+    const int s = start[k], n = start[k + 1] - s;
+    if (n <= 1 || n > 128) return;
+    int val[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) val[q] = (lane + 32 * q < n) ? tmp[s + lane + 32 * q] : 0x7fffffff;
+#pragma unroll
+    for (int size = 2; size <= 128; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+                const int qs = stride >> 5;
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    if (q & qs) continue;
+                    const int e = lane + 32 * q;
+                    const bool up = (e & size) == 0;
+                    const int a = val[q], c = val[q | qs];
+                    val[q] = up ? min(a, c) : max(a, c);
+                    val[q | qs] = up ? max(a, c) : min(a, c);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int e = lane + 32 * q;
+                    const int other = __shfl_xor_sync(0xffffffffu, val[q], stride);
+                    const bool up = (e & size) == 0;
+                    const bool lower = (e & stride) == 0;
+                    val[q] = (lower == up) ? min(val[q], other) : max(val[q], other);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+        if (lane + 32 * q < n) tmp[s + lane + 32 * q] = val[q];
+}
+
+// Cells larger than kSegMax: each slot's rank among its cell's (distinct)
+// old indices, O(n^2) per such cell; writes the ordered list to out.
+__global__ void k_segrank(int N, const int* __restrict__ cell, const int* __restrict__ start, const int* __restrict__ tmp,
+                          int* __restrict__ out) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;   // slot in the scattered order
+    if (q >= N) return;
+    int c = cell[tmp[q]];
+    int s = start[c], e = start[c + 1];
+    if (e - s <= kSegMax) return;
+    int me = tmp[q], r = 0;
+    for (int t = s; t < e; t++) r += (tmp[t] < me);
+    out[s + r] = me;
+}
+
+__global__ void k_segcopy(int N, const int* __restrict__ cell, const int* __restrict__ start, const int* __restrict__ src,
+                          int* __restrict__ tmp) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= N) return;
+    int c = cell[tmp[q]];
+    if (start[c + 1] - start[c] > kSegMax) tmp[q] = src[q];
 }
 
 // ============================================================== gather + mirrors
@@ -531,10 +795,32 @@ __global__ void k_radius(View v, unsigned long long* __restrict__ rmax_bits /* [
 // the threshold, and by an FP32 test with margin elsewhere.
 constexpr float kBandA = 2e-3f;
 
+// exact neighbouring-cell test of (k, j), FP32 with a margin outside the
+// band and the definition's FP64 operations inside it
+__device__ inline bool adj_test(const View& v, const Inst& I, int k, int j, double Rk, float df, long long cx,
+                                long long cy, long long cz, double tail) {
+    const double t = __dadd_rn(__dadd_rn(Rk, v.R[j]), tail);
+    const float tf = (float)t;
+    if (df < tf - kBandA) return true;
+    if (df > tf + kBandA) return false;
+    const double d = __dsqrt_rn(dist2_grid_d(cx, cy, cz, v.cq[j], v.cq[(size_t)v.Ktot + j], v.cq[(size_t)2 * v.Ktot + j], I));
+    // same operation order as the definition: ((Rk + Rj) + rs) + (skin + skin)
+    double tt = __dadd_rn(__dadd_rn(__dadd_rn(Rk, v.R[j]), I.rs), __dadd_rn(I.skin, I.skin));
+    tt = __dmul_rn(tt, 1.0 + 1e-12);
+    return d < tt;
+}
+
+__device__ inline void sort_row(int* row, int n) {
+    for (int a = 1; a < n; a++) {
+        int x = row[a];
+        int c = a - 1;
+        while (c >= 0 && row[c] > x) { row[c + 1] = row[c]; c--; }
+        row[c + 1] = x;
+    }
+}
+
 template <bool FILL>
-__global__ void k_adjacency(View v, const unsigned long long* __restrict__ rmax_bits, int* __restrict__ count) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= v.Ktot) return;
+__device__ void adj_one(const View& v, const unsigned long long* __restrict__ rmax_bits, int* __restrict__ count, int k) {
     int b = find_inst(v.inst_k0, v.B, k);
     const Inst& I = v.inst[b];
     double Rk = v.R[k];
@@ -556,19 +842,7 @@ __global__ void k_adjacency(View v, const unsigned long long* __restrict__ rmax_
                 int j = __float_as_int(c.w);
                 float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1), dz = axis_dist(p[2], c.z, I, 2);
                 float df = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                double t = __dadd_rn(__dadd_rn(Rk, v.R[j]), tail);
-                float tf = (float)t;
-                bool in;
-                if (df < tf - kBandA) in = true;
-                else if (df > tf + kBandA) in = false;
-                else {
-                    double d = __dsqrt_rn(dist2_grid_d(cx, cy, cz, v.cq[j], v.cq[(size_t)v.Ktot + j],
-                                                       v.cq[(size_t)2 * v.Ktot + j], I));
-                    // same operation order as the definition: ((Rk + Rj) + rs) + (skin + skin)
-                    double tt = __dadd_rn(__dadd_rn(__dadd_rn(Rk, v.R[j]), I.rs), __dadd_rn(I.skin, I.skin));
-                    tt = __dmul_rn(tt, 1.0 + 1e-12);
-                    in = d < tt;
-                }
+                bool in = adj_test(v, I, k, j, Rk, df, cx, cy, cz, tail);
                 if (in) {
                     if (FILL) {
                         if (out0 + n < v.adj_cap) v.adj[out0 + n] = j;
@@ -585,15 +859,71 @@ __global__ void k_adjacency(View v, const unsigned long long* __restrict__ rmax_
     if (!FILL) count[k] = n;
     else {
         // ascending row (insertion sort, rows are short)
-        int* row = v.adj + out0;
         if (out0 + n > v.adj_cap) return;
-        for (int a = 1; a < n; a++) {
-            int x = row[a];
-            int c = a - 1;
-            while (c >= 0 && row[c] > x) { row[c + 1] = row[c]; c--; }
-            row[c + 1] = x;
-        }
+        sort_row(v.adj + out0, n);
     }
+}
+
+
+template <bool FILL>
+__global__ void k_adjacency(View v, const unsigned long long* __restrict__ rmax_bits, int* __restrict__ count) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = k < v.Ktot;
+    const int b = valid ? find_inst(v.inst_k0, v.B, k) : -1;
+    const int b0 = __reduce_max_sync(0xffffffffu, b);
+    if (b0 < 0) return;
+    const bool same = __all_sync(0xffffffffu, !valid || b == b0);
+    const Inst& I = v.inst[b0];
+    if (!same || (I.periodic[0] | I.periodic[1] | I.periodic[2])) {
+        if (valid) adj_one<FILL>(v, rmax_bits, count, k);
+        return;
+    }
+    // warp-cooperative: 32 consecutive (Morton-ordered) cells share a region
+    const double Rmax = __longlong_as_double((long long)rmax_bits[b0]);
+    const double tail = (I.rs) + (I.skin + I.skin);
+    double Rk = 0;
+    long long cx = 0, cy = 0, cz = 0;
+    float p[3] = {0, 0, 0};
+    int g[3] = {0, 0, 0};
+    float reach = 0;
+    if (valid) {
+        Rk = v.R[k];
+        cx = v.cq[k]; cy = v.cq[(size_t)v.Ktot + k]; cz = v.cq[(size_t)2 * v.Ktot + k];
+        g[0] = grid_coord(cx, I, 0, p[0]);
+        g[1] = grid_coord(cy, I, 1, p[1]);
+        g[2] = grid_coord(cz, I, 2, p[2]);
+        reach = (float)(Rk + Rmax + I.rs + 2.0 * I.skin) + kBandA;
+    }
+    int lo[3], hi[3];
+    warp_box(g, valid, lo, hi);
+    int n = 0;
+    const int out0 = (FILL && valid) ? v.adj_ptr[k] : 0;
+    for (int r = 0;; r++) {
+        region_ring(I, lo, hi, r, [&](long long gg) {
+            const int q1 = v.gstart[gg + 1];
+            for (int q = v.gstart[gg]; q < q1; q++) {
+                const float4 c = v.gcf[q];
+                const float dx = p[0] - c.x, dy = p[1] - c.y, dz = p[2] - c.z;
+                const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (valid && d2 <= reach * reach) {
+                    const int j = __float_as_int(c.w);
+                    if (adj_test(v, I, k, j, Rk, sqrtf(d2), cx, cy, cz, tail)) {
+                        if (FILL) {
+                            if (out0 + n < v.adj_cap) v.adj[out0 + n] = j;
+                            else atomicOr(v.status, kStatusAdjOverflow);
+                        }
+                        n++;
+                    }
+                }
+            }
+        });
+        bool ex;
+        const float lb = region_bound(I, p, lo, hi, r, ex);
+        if (__all_sync(0xffffffffu, !valid || ex || lb > reach)) break;
+    }
+    if (!valid) return;
+    if (!FILL) count[k] = n;
+    else if (out0 + n <= v.adj_cap) sort_row(v.adj + out0, n);
 }
 
 // ============================================================== host side
@@ -603,23 +933,28 @@ void Ensemble::build_grid() {
     View v = view();
     CK(cudaMemsetAsync(d_gcount, 0, sizeof(int) * (Gtot + 1), stream));
     k_grid_count<<<nblk(Ktot, 256), 256, 0, stream>>>(v, d_gcount, d_gidx);
+    launches++;
     CK(cudaGetLastError());
     scan_exclusive(d_gcount, d_gstart, Gtot + 1);
     CK(cudaMemsetAsync(d_gcount, 0, sizeof(int) * (Gtot + 1), stream));
     k_grid_fill<<<nblk(Ktot, 256), 256, 0, stream>>>(v, d_gidx, d_gcount);
+    launches++;
     CK(cudaGetLastError());
 }
 
 void Ensemble::mstep_iter(const int* cell_of, int iter) {
     View v = view();
     k_mstep_accum<<<nblk(N, 256), 256, 0, stream>>>(v, cell_of, d_S, d_cnt);
+    launches++;
     CK(cudaGetLastError());
     k_mstep_finish<<<nblk(Ktot, 256), 256, 0, stream>>>(v, d_S, d_cnt, iter);
+    launches++;
     CK(cudaGetLastError());
 }
 
 void Ensemble::mirrors() {
     k_mirrors<<<nblk(N, 256), 256, 0, stream>>>(view());
+    launches++;
     CK(cudaGetLastError());
 }
 
@@ -644,6 +979,7 @@ __global__ void k_displacement(View v, const long long* __restrict__ xref, unsig
 bool Ensemble::displacement_exceeds_skin() {
     CK(cudaMemsetAsync(d_cnt + Ktot, 0, sizeof(int), stream));
     k_displacement<<<nblk(N, 256), 256, 0, stream>>>(view(), d_xref, (unsigned*)(d_cnt + Ktot));
+    launches++;
     CK(cudaGetLastError());
     unsigned f = 0;
     CK(cudaMemcpyAsync(&f, d_cnt + Ktot, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
@@ -652,21 +988,30 @@ bool Ensemble::displacement_exceeds_skin() {
 }
 
 void Ensemble::estep(int* cell_out) {
-    k_estep<<<nblk(N, 128), 128, 0, stream>>>(view(), cell_out);
+    k_estep_warp<<<nblk(N, 128), 128, 0, stream>>>(view(), cell_out);
+    launches++;
     CK(cudaGetLastError());
 }
 
 void Ensemble::morton_relabel() {
     View v = view();
-    // bbox init: min = +inf, max = -inf
-    k_fill_bbox<<<1, 64, 0, stream>>>(d_bbox, B);
-    k_bbox<<<nblk(Ktot, 256), 256, 0, stream>>>(v, d_bbox);
+    if (!bbox_ready_) {
+        // bbox init: min = +inf, max = -inf
+        k_fill_bbox<<<1, 64, 0, stream>>>(d_bbox, B);
+        launches++;
+        k_bbox<<<nblk(Ktot, 256), 256, 0, stream>>>(v, d_bbox);
+        launches++;
+    }
+    bbox_ready_ = false;
     k_morton_keys<<<nblk(Ktot, 256), 256, 0, stream>>>(v, d_bbox, d_keys);
+    launches++;
     int ntiles = nblk(Ktot, kTile);
     k_tile_sort<<<ntiles, 256, 0, stream>>>(v, d_keys, (SortRec*)d_sortrec);
+    launches++;
     CK(cudaMemcpyAsync(d_cq_tmp, d_cq, sizeof(long long) * 3 * Ktot, cudaMemcpyDeviceToDevice, stream));
     k_rank_scatter<<<nblk((long long)ntiles * kTile, 256), 256, 0, stream>>>(v, (const SortRec*)d_sortrec, ntiles, d_cq_tmp,
                                                                             d_new_of_old);
+    launches++;
     CK(cudaGetLastError());
 }
 
@@ -678,10 +1023,19 @@ void Ensemble::finish_cells() {
     // stable counting sort
     CK(cudaMemsetAsync(d_cnt, 0, sizeof(int) * (Ktot + 1), stream));
     k_hist<<<nblk(N, 256), 256, 0, stream>>>(N, d_cell_new, d_cnt);
+    launches++;
     scan_exclusive(d_cnt, d_cell_start, Ktot + 1);
     CK(cudaMemsetAsync(d_cnt, 0, sizeof(int) * (Ktot + 1), stream));
     k_scatter<<<nblk(N, 256), 256, 0, stream>>>(N, d_cell_new, d_cell_start, d_cnt, d_perm);
-    k_segsort<<<Ktot, 256, 0, stream>>>(Ktot, d_cell_start, d_perm, d_status);
+    launches++;
+    k_segsort_warp<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(Ktot, d_cell_start, d_perm);
+    launches++;
+    k_segsort<<<std::min(Ktot, 1024), 256, 0, stream>>>(Ktot, d_cell_start, d_perm, d_status);
+    launches++;
+    k_segrank<<<nblk(N, 256), 256, 0, stream>>>(N, d_cell_new, d_cell_start, d_perm, d_cell_tmp);
+    launches++;
+    k_segcopy<<<nblk(N, 256), 256, 0, stream>>>(N, d_cell_new, d_cell_start, d_cell_tmp, d_perm);
+    launches++;
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(d_cnt, 0, sizeof(int) * (Ktot + 1), stream));
     // gather into the second buffer set, then swap
@@ -689,16 +1043,20 @@ void Ensemble::finish_cells() {
     View nv = view();
     View ov = view_alt();
     k_gather<<<nblk(N, 256), 256, 0, stream>>>(nv, ov, d_perm, d_cell_new, d_xref);
+    launches++;
     CK(cudaGetLastError());
     // radii and neighbouring cells
     CK(cudaMemsetAsync(d_rmax, 0, sizeof(unsigned long long) * B, stream));
     k_radius<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(nv, d_rmax);
+    launches++;
     k_adjacency<false><<<nblk(Ktot, 128), 128, 0, stream>>>(nv, d_rmax, d_adjcount);
+    launches++;
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(d_adjcount + Ktot, 0, sizeof(int), stream));
     scan_exclusive(d_adjcount, d_adj_ptr, Ktot + 1);
     nv = view();
     k_adjacency<true><<<nblk(Ktot, 128), 128, 0, stream>>>(nv, d_rmax, d_adjcount);
+    launches++;
     CK(cudaGetLastError());
     cells_valid = true;
     forces_valid = false;
@@ -706,7 +1064,13 @@ void Ensemble::finish_cells() {
 }
 
 void Ensemble::rebuild() {
-    mstep(d_cell);
+    // M-step on the cell-sorted particles, fused with the centroid bounding box
+    k_fill_bbox<<<1, 64, 0, stream>>>(d_bbox, B);
+    launches++;
+    k_mstep_sorted<<<nblk(Ktot, 8), 256, 0, stream>>>(view(), d_bbox);
+    launches++;
+    CK(cudaGetLastError());
+    bbox_ready_ = true;
     finish_cells();
 }
 

@@ -94,6 +94,7 @@ public:
     long long Gtot = 0;
     bool cells_valid = false, forces_valid = false;
     long long n_rebuilds = 0;
+    long long launches = 0;               // kernels launched by this ensemble
     std::vector<Inst> inst_h;
     std::vector<Params> prm_h;
     std::vector<long long> step_h;
@@ -129,6 +130,7 @@ private:
     template <typename T> T* alloc(size_t count);
     std::vector<void*> allocs_;
     int cur_ = 0;
+    bool bbox_ready_ = false;   // set by the fused M-step of a rebuild
     // timing state
     cudaEvent_t ev0_ = nullptr, ev1_ = nullptr;
     const char* open_ = nullptr;
@@ -142,7 +144,7 @@ public:
     unsigned* d_id[2] = {nullptr, nullptr};
     int* d_cell = nullptr;
     int* d_slot_of_id = nullptr;
-    long long *d_F = nullptr, *d_T = nullptr;
+    long long *d_F = nullptr, *d_T = nullptr, *d_Fbig = nullptr;
     int4* d_mq = nullptr;
     float4* d_mo = nullptr;
     long long *d_cq = nullptr, *d_cq_tmp = nullptr;
@@ -162,7 +164,7 @@ public:
     unsigned long long* d_keys = nullptr;
     void* d_sortrec = nullptr;
     int* d_new_of_old = nullptr;
-    int *d_cell_new = nullptr, *d_perm = nullptr;
+    int *d_cell_new = nullptr, *d_perm = nullptr, *d_cell_tmp = nullptr;
     unsigned long long* d_rmax = nullptr;
     long long* d_xref = nullptr;
     long long* d_energy = nullptr;           // [B][8] fixed-point sums

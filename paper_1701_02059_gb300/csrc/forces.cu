@@ -184,15 +184,28 @@ __device__ inline T wca_terms(const Inst& I, T dx, T dy, T dz, T r2, T& fx, T& f
 // ---------------------------------------------------------------- accumulators
 template <typename T> struct Acc;
 template <> struct Acc<float> {
-    SplitAcc f[3], t[3], u, w;
-    int np, nb;
-    __device__ void zero() { for (int a = 0; a < 3; a++) { f[a].zero(); t[a].zero(); } u.zero(); w.zero(); np = 0; nb = 0; }
-    __device__ void add_pair(float fx, float fy, float fz, float tx, float ty, float tz) {
-        f[0].add(fx); f[1].add(fy); f[2].add(fz); t[0].add(tx); t[1].add(ty); t[2].add(tz); np++;
+    // fast path: split int32 sums (|component| < 1000); wider values go to
+    // an int64 side array with atomics (exact, rare)
+    SplitAcc f[3], t[3];
+    int nf, nt;
+    long long* big;   // [6][N]
+    size_t N;
+    int p;
+    bool used_big;
+    __device__ void zero() { for (int a = 0; a < 3; a++) { f[a].zero(); t[a].zero(); } nf = 0; nt = 0; used_big = false; }
+    __device__ void wide(int c, float x) {
+        atomicAdd((unsigned long long*)&big[(size_t)c * N + p], (unsigned long long)__float2ll_rn(x * 4294967296.0f));
+        used_big = true;
     }
-    __device__ void add_bond(float fx, float fy, float fz) { f[0].add(fx); f[1].add(fy); f[2].add(fz); nb++; }
-    __device__ long long F(int a) const { return f[a].finish(np + nb); }
-    __device__ long long Tq(int a) const { return t[a].finish(np); }
+    __device__ void add3(SplitAcc* s, int& n, int c0, float x, float y, float z) {
+        if (fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z))) < 1000.0f) { s[0].add(x); s[1].add(y); s[2].add(z); n++; }
+        else { wide(c0, x); wide(c0 + 1, y); wide(c0 + 2, z); }
+    }
+    __device__ void add_pair(float fx, float fy, float fz, float tx, float ty, float tz) {
+        add3(f, nf, 0, fx, fy, fz);
+        add3(t, nt, 3, tx, ty, tz);
+    }
+    __device__ void add_bond(float fx, float fy, float fz) { add3(f, nf, 0, fx, fy, fz); }
 };
 template <> struct Acc<double> {
     long long f[3], t[3];
@@ -214,10 +227,17 @@ __device__ inline bool exact_inside(const View& v, const Inst& I, int pi, int pj
     return d2 < (ll ? I.rc2_ll : I.rc2_wca);
 }
 
-__device__ inline bool is_bonded(const View& v, const Inst& I, unsigned idi, unsigned idj) {
-    int s = v.bptr[I.p0 + idi], e = v.bptr[I.p0 + idi + 1];
-    for (int q = s; q < e; q++)
-        if ((unsigned)v.bpartner[q] == idj) return true;
+// 1-2 and 1-3 bonded pairs carry no excluded-volume term (bonded directly,
+// or sharing a bond partner).
+__device__ inline bool is_excluded(const View& v, const Inst& I, unsigned idi, unsigned idj) {
+    const int s = v.bptr[I.p0 + idi], e = v.bptr[I.p0 + idi + 1];
+    const int s2 = v.bptr[I.p0 + idj], e2 = v.bptr[I.p0 + idj + 1];
+    for (int q = s; q < e; q++) {
+        const int c = v.bpartner[q];
+        if ((unsigned)c == idj) return true;
+        for (int w = s2; w < e2; w++)
+            if (v.bpartner[w] == c) return true;
+    }
     return false;
 }
 
@@ -277,7 +297,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
     __shared__ alignas(16) unsigned char scratch[kPairThreads / 32 * kQCap * 32 * 4];
     __shared__ NbrInfo nb[kMaxNbr];
     __shared__ unsigned long long bar;
-    __shared__ int s_nstage, s_next, s_self;
+    __shared__ int s_nstage, s_next, s_next_off, s_self, s_self_lo, s_self_hi;
     unsigned (*qbuf)[kQCap][32] = reinterpret_cast<unsigned (*)[kQCap][32]>(scratch);
 
     const int k = blockIdx.x;
@@ -321,20 +341,19 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
         const int ti = qi.w & 0xff;
         Acc<T> acc;
         acc.zero();
+        if constexpr (sizeof(T) == 4) { acc.big = v.Fbig; acc.N = N; acc.p = pi; }
         T up = 0, vir = 0;
 
-        // passes over chunks of neighbouring cells
-        for (int na = a0; na < a1;) {
+        // passes over chunks of neighbouring cells (a cell larger than the
+        // stage is split across passes)
+        for (int na = a0, na_off = 0; na < a1;) {
             __syncthreads();
             if (tid == 0) {
-                int tot = 0, m = 0, nn = na, self = -1;
-                while (nn < a1 && m < kMaxNbr) {
-                    int l = v.adj[nn];
-                    int s = v.cell_start[l], c = v.cell_start[l + 1] - s;
-                    if (tot + c > kStageCap) {
-                        if (m == 0) { atomicOr(v.status, kStatusCellOverflow); nn++; }   // cell larger than a stage
-                        break;
-                    }
+                int tot = 0, m = 0, nn = na, off = na_off, sb = 0, slo = -1, shi = -1;
+                while (nn < a1 && m < kMaxNbr && tot < kStageCap) {
+                    const int l = v.adj[nn];
+                    const int s = v.cell_start[l], c = v.cell_start[l + 1] - s;
+                    const int take = min(c - off, kStageCap - tot);
                     long long dx = minimg_q(v.cq[l] - ckx, I.boxq[0], I.periodic[0]);
                     long long dy = minimg_q(v.cq[(size_t)v.Ktot + l] - cky, I.boxq[1], I.periodic[1]);
                     long long dz = minimg_q(v.cq[(size_t)2 * v.Ktot + l] - ckz, I.boxq[2], I.periodic[2]);
@@ -342,20 +361,23 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
                     long long oy = (dy + (1ll << (kMirrorShift - 1))) >> kMirrorShift;
                     long long oz = (dz + (1ll << (kMirrorShift - 1))) >> kMirrorShift;
                     NbrInfo inf;
-                    inf.base = tot; inf.cnt = c; inf.start = s;
+                    inf.base = tot; inf.cnt = take; inf.start = s + off;
                     inf.ox = (int)(unsigned)(unsigned long long)ox;
                     inf.oy = (int)(unsigned)(unsigned long long)oy;
                     inf.oz = (int)(unsigned)(unsigned long long)oz;
                     inf.fx = (float)ox * kMirrorUnit; inf.fy = (float)oy * kMirrorUnit; inf.fz = (float)oz * kMirrorUnit;
-                    if (l == k) self = tot;
+                    if (l == k) { sb = tot - off; slo = tot; shi = tot + take; }
                     nb[m] = inf;
-                    tot += c;
+                    tot += take;
                     m++;
+                    if (take < c - off) { off += take; break; }   // rest of this cell in the next pass
                     nn++;
+                    off = 0;
                 }
                 s_nstage = m;
                 s_next = nn;
-                s_self = self;
+                s_next_off = off;
+                s_self = sb; s_self_lo = slo; s_self_hi = shi;
                 if (m > 0) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     mbar_expect_tx(&bar, (unsigned)tot * 32u);
@@ -368,9 +390,10 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
             }
             __syncthreads();
             const int m = s_nstage;
-            const int next = s_next;
-            const int selfj = (s_self >= 0 && ivalid) ? s_self + (pi - cs) : -1;
-            if (m == 0) { na = next; continue; }
+            const int next = s_next, next_off = s_next_off;
+            int selfj = (s_self_lo >= 0 && ivalid) ? s_self + (pi - cs) : -1;
+            if (selfj < s_self_lo || selfj >= s_self_hi) selfj = -1;
+            if (m == 0) { na = next; na_off = next_off; continue; }
             bool ok = mbar_wait_bounded(&bar, phase, v.status);
             if (__syncthreads_or(!ok)) {
                 // give the copies in flight a second bounded wait, then leave
@@ -422,7 +445,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
                         const int pj = __float_as_int(oj.w);
                         bool in = r2f < lo;
                         if (!in) in = exact_inside(v, I, pi, pj, ll);
-                        if (in && !ll && is_bonded(v, I, v.id[pi], v.id[pj])) in = false;
+                        if (in && !ll && is_excluded(v, I, v.id[pi], v.id[pj])) in = false;
                         if (!in) continue;
                         T fx = 0, fy = 0, fz = 0, tx = 0, ty = 0, tz = 0, U;
                         T dx, dy, dz, r2;
@@ -448,11 +471,8 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
                         } else {
                             U = wca_terms<T>(I, dx, dy, dz, r2, fx, fy, fz);
                         }
-                        if constexpr (sizeof(T) == 4) {
-                            if (fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))) >= 1000.f ||
-                                fmaxf(fabsf(tx), fmaxf(fabsf(ty), fabsf(tz))) >= 1000.f)
-                                atomicOr(v.status, kStatusPairForceRange);
-                        }
+                        if (!(fabsf(fx) + fabsf(fy) + fabsf(fz) + fabsf(tx) + fabsf(ty) + fabsf(tz) < (T)3.0e30))
+                            atomicOr(v.status, kStatusNaN);
                         acc.add_pair(fx, fy, fz, tx, ty, tz);
                         if (ENERGY) {
                             up += (T)0.5 * U;
@@ -482,6 +502,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
                 flush();
             }
             na = next;
+            na_off = next_off;
         }
 
         // bonds of i (each bond evaluated from both ends)
@@ -527,17 +548,23 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
                 atomicAdd(&red[li][6], acc.t[0].h); atomicAdd(&red[li][7], acc.t[0].l);
                 atomicAdd(&red[li][8], acc.t[1].h); atomicAdd(&red[li][9], acc.t[1].l);
                 atomicAdd(&red[li][10], acc.t[2].h); atomicAdd(&red[li][11], acc.t[2].l);
-                atomicAdd(&red[li][12], acc.np); atomicAdd(&red[li][13], acc.nb);
+                atomicAdd(&red[li][12], acc.nf); atomicAdd(&red[li][13], acc.nt);
             }
             __syncthreads();
+            const bool any_big = __syncthreads_or(ivalid && acc.used_big);
             if (tid < nti) {
-                const int np = red[tid][12], nbd = red[tid][13];
+                const int nfr = red[tid][12], ntr = red[tid][13];
                 const int p = it0 + tid;
                 for (int a = 0; a < 3; a++) {
                     SplitAcc f; f.h = red[tid][2 * a]; f.l = red[tid][2 * a + 1];
                     SplitAcc t; t.h = red[tid][6 + 2 * a]; t.l = red[tid][6 + 2 * a + 1];
-                    v.F[a * N + p] = f.finish(np + nbd);
-                    v.T[a * N + p] = t.finish(np);
+                    long long fb = 0, tb = 0;
+                    if (any_big) {
+                        fb = v.Fbig[(size_t)a * N + p]; tb = v.Fbig[(size_t)(3 + a) * N + p];
+                        v.Fbig[(size_t)a * N + p] = 0; v.Fbig[(size_t)(3 + a) * N + p] = 0;
+                    }
+                    v.F[a * N + p] = f.finish(nfr) + fb;
+                    v.T[a * N + p] = t.finish(ntr) + tb;
                 }
             }
         } else {
@@ -591,6 +618,7 @@ void Ensemble::launch_pairs(bool energies, bool dump) {
         else if (energies) k_pairs<double, true, false><<<Ktot, kPairThreads, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
         else k_pairs<double, false, false><<<Ktot, kPairThreads, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
     }
+    launches++;
     CK(cudaGetLastError());
 }
 

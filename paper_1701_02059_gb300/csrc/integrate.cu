@@ -198,18 +198,21 @@ static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 void Ensemble::launch_integrate_first() {
     if (precision == 0) k_baoa<float><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
     else k_baoa<double><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
+    launches++;
     CK(cudaGetLastError());
 }
 
 void Ensemble::launch_kick(bool energies) {
     if (precision == 0) k_kick<float><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
     else k_kick<double><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
+    launches++;
     CK(cudaGetLastError());
     (void)energies;
 }
 
 void Ensemble::launch_kinetic() {
     k_kinetic<<<nblk(N, 256), 256, 0, stream>>>(view(), d_energy);
+    launches++;
     CK(cudaGetLastError());
 }
 

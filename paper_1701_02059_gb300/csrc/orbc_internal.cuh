@@ -79,6 +79,7 @@ struct View {
     int* slot_of_id;                // [N] indexed by p0 + id
     // forces (fixed point 2^-32)
     long long *F, *T;               // [3][N]
+    long long* Fbig;                // [6][N] wide per-pair contributions (normally zero)
     // mirrors for the pair kernel
     int4* mq;                       // x - c at 2^-26 sigma, w = type
     float4* mo;                     // director, w = slot (int bits)

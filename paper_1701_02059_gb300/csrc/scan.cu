@@ -48,6 +48,7 @@ void Ensemble::scan_exclusive(const int* in, int* out, long long n) {
     long long nb = (n + kScanBlock - 1) / kScanBlock;
     if (nb == 1) {
         k_scan_block<<<1, 256, 0, stream>>>(in, out, n, nullptr);
+        launches++;
         CK(cudaGetLastError());
         return;
     }
@@ -69,17 +70,20 @@ void Ensemble::scan_exclusive(const int* in, int* out, long long n) {
     }
     // up: block scans producing sums at each level
     k_scan_block<<<(int)nb, 256, 0, stream>>>(in, out, n, lv[0].first);
+    launches++;
     for (size_t l = 0; l + 1 < lv.size(); l++) {
         long long cnt = lv[l].second;
         int* sums = lv[l].first;
         int* scanned = lv[l].first + cnt + 1;
         long long nbl = (cnt + kScanBlock - 1) / kScanBlock;
         k_scan_block<<<(int)nbl, 256, 0, stream>>>(sums, scanned, cnt, lv[l + 1].first);
+        launches++;
     }
     {
         size_t l = lv.size() - 1;
         long long cnt = lv[l].second;
         k_scan_block<<<1, 256, 0, stream>>>(lv[l].first, lv[l].first + cnt + 1, cnt, nullptr);
+        launches++;
     }
     // down: add scanned offsets
     for (long long l = (long long)lv.size() - 2; l >= 0; l--) {
@@ -87,8 +91,10 @@ void Ensemble::scan_exclusive(const int* in, int* out, long long n) {
         int* scanned = lv[l].first + cnt + 1;
         const int* offs = lv[l + 1].first + lv[l + 1].second + 1;
         k_scan_add<<<(int)((cnt + 255) / 256), 256, 0, stream>>>(scanned, cnt, offs);
+        launches++;
     }
     k_scan_add<<<(int)((n + 255) / 256), 256, 0, stream>>>(out, n, lv[0].first + lv[0].second + 1);
+    launches++;
     CK(cudaGetLastError());
 }
 

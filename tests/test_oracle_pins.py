@@ -541,3 +541,18 @@ def test_periodic_minimum_image_against_scipy():
     a = oracle.assign_brute(x, c, box, (1, 1, 1))
     _, b = cKDTree(c, boxsize=box).query(np.mod(x, box), k=1)
     assert np.array_equal(a, b)
+
+
+def test_one_three_exclusion():
+    """Spectrin beads two bonds apart (sharing a bond partner) carry no
+    excluded-volume term; three bonds apart they do."""
+    m = oracle.model()
+    # chain 0-1-2-3 folded so that 0..2 and 0..3 are both within the WCA cutoff
+    x = np.array([[0.0, 0.0, 0.0], [0.6, 0.0, 0.0], [0.6, 0.6, 0.0], [0.0, 0.6, 0.0]])
+    typ = np.full(4, 2, np.uint8)
+    ids = np.arange(4, dtype=np.uint32)
+    bonds = np.array([[0, 1], [1, 2], [2, 3]], np.int32)
+    pairs = {tuple(p) for p in oracle.pairs_brute(m, x, typ, ids, bonds).tolist()}
+    assert (0, 2) not in pairs and (1, 3) not in pairs      # 1-3
+    assert (0, 3) in pairs                                  # 1-4
+    assert (0, 1) not in pairs                              # 1-2
