@@ -75,9 +75,11 @@ enum { ORBC_LIPID = 0, ORBC_JUNCTION = 1, ORBC_SPECTRIN = 2 };
  *   U = eps[(rmin/r)^4 - 2 (rmin/r)^2] + (1 - phi) eps      r < rmin
  *   U = -eps cos^(2 zeta)((pi/2)(r - rmin)/(rc - rmin)) phi  rmin <= r < rc
  * with rmin = 2^(1/6) sigma.  Every pair that is not lipid-lipid is purely
- * repulsive WCA (eps_wca, sigma_wca, cutoff 2^(1/6) sigma_wca) and bonded
- * pairs are excluded from it ("Force Evaluation": protein interactions use
- * the lipid cells with a wider search cutoff).
+ * repulsive WCA, 4 eps_wca [(s/r)^12 - (s/r)^6] + eps_wca for r < 2^(1/6) s,
+ * with s = sigma_wca for lipid-protein pairs and s = sigma_wca_pp for
+ * protein-protein pairs; protein pairs that are bonded or share a bond
+ * partner (1-2, 1-3) are excluded from it ("Force Evaluation": protein
+ * interactions use the lipid cells with a wider search cutoff).
  *
  * Integrator: BAOAB Langevin (translational for all particles, rotational
  * for lipids with Cayley rotations of the director), noise from
@@ -87,7 +89,8 @@ typedef struct {
     double eps, sigma, rc_lipid, mu, sin_theta0;   /* lipid-lipid potential               */
     int zeta;                                      /* cos^(2 zeta) tail exponent           */
     int pad0;
-    double eps_wca, sigma_wca;                     /* excluded volume of non-lipid pairs   */
+    double eps_wca, sigma_wca;                     /* lipid-protein excluded volume        */
+    double sigma_wca_pp;                           /* protein-protein excluded-volume size */
     double dt, kT, gamma_t, gamma_r, mass, inertia;/* integrator                           */
     double box[3];                                 /* box lengths on periodic axes         */
     int periodic[3];                               /* 1 = periodic axis                    */
@@ -104,7 +107,8 @@ typedef struct {
 typedef struct orbc_system orbc_system;   /* opaque; owns its device memory */
 
 /* Fills p with the project's defaults: eps = sigma = 1, rc = 2.6, mu = 3,
- * zeta = 4, sin_theta0 = 0, eps_wca = sigma_wca = 1, dt = 0.01, kT = 0.2,
+ * zeta = 4, sin_theta0 = 0, eps_wca = sigma_wca = 1, sigma_wca_pp = 0.5,
+ * dt = 0.01, kT = 0.2,
  * gamma_t = gamma_r = 1, mass = inertia = 1, no periodic axis,
  * n_centroids = 64, n_lloyd_init = 10, rebuild_every = 1, skin = 0,
  * grid_h = 0, seed = 0, instance = 0, ORBC_F32_FORCE_F64_STATE. */
@@ -186,6 +190,18 @@ ORBC_API int orbc_dump_pairs(orbc_system* s, long long cap, unsigned* pairs, lon
  * last orbc_integrate / orbc_compute_forces when timing is on. */
 ORBC_API int orbc_set_timing(orbc_system* s, int on);
 ORBC_API int orbc_get_kernel_times(orbc_system* s, char* names_csv, int names_cap, float* ms, int cap, int* count);
+
+/* Stable counting sort of n items by cell id on device memory (the particle
+ * level of the two-level reorder, "Spatial Searching Algorithm": particles
+ * reordered by the Voronoi cell they belong to).  d_cell: [n] cell ids in
+ * [0, K), device memory.  Writes d_perm: [n], d_perm[new] = old index, the
+ * items of one cell in their input order; and d_cell_start: [K+1], the first
+ * slot of every cell.  Work is ordered on cuda_stream (NULL = the legacy
+ * default stream); scratch is taken with cudaMallocAsync on that stream and
+ * released before the call returns, and the call synchronises the stream.
+ * Errors: ORBC_E_ARG (null pointer, n < 0, K < 1, a cell id outside
+ * [0, K)), ORBC_E_NOMEM, ORBC_E_CUDA. */
+ORBC_API int orbc_cell_sort(const int* d_cell, int n, int K, int* d_perm, int* d_cell_start, void* cuda_stream);
 
 /* Number of CUDA kernels this handle has launched since creation. */
 ORBC_API int orbc_get_launch_count(orbc_system* s, long long* count);

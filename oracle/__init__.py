@@ -38,7 +38,7 @@ def build(force: bool = False) -> str:
 class Model(C.Structure):
     _fields_ = [("eps", C.c_double), ("rmin", C.c_double), ("rc", C.c_double), ("mu", C.c_double),
                 ("sin_theta0", C.c_double), ("zeta", C.c_int), ("pad0", C.c_int),
-                ("eps_wca", C.c_double), ("sigma_wca", C.c_double),
+                ("eps_wca", C.c_double), ("sigma_wca", C.c_double), ("sigma_pp", C.c_double),
                 ("box", C.c_double * 3), ("periodic", C.c_int * 3), ("pad1", C.c_int)]
 
 
@@ -52,11 +52,11 @@ class Run(C.Structure):
 TWO_SIXTH = 2.0 ** (1.0 / 6.0)
 
 
-def model(eps=1.0, sigma=1.0, rc=2.6, zeta=4, mu=3.0, sin_theta0=0.0, eps_wca=1.0, sigma_wca=1.0,
+def model(eps=1.0, sigma=1.0, rc=2.6, zeta=4, mu=3.0, sin_theta0=0.0, eps_wca=1.0, sigma_wca=1.0, sigma_pp=0.5,
           box=(0.0, 0.0, 0.0), periodic=(0, 0, 0)) -> Model:
     m = Model()
     m.eps, m.rmin, m.rc, m.mu, m.sin_theta0, m.zeta = eps, TWO_SIXTH * sigma, rc, mu, sin_theta0, zeta
-    m.eps_wca, m.sigma_wca = eps_wca, sigma_wca
+    m.eps_wca, m.sigma_wca, m.sigma_pp = eps_wca, sigma_wca, sigma_pp
     for k in range(3):
         m.box[k] = float(box[k])
         m.periodic[k] = int(periodic[k])

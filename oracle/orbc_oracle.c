@@ -56,7 +56,8 @@ typedef struct {
     int    zeta;         /* attractive-tail exponent (cos^(2 zeta))       */
     int    pad0;
     double eps_wca;      /* protein excluded-volume strength              */
-    double sigma_wca;    /* protein excluded-volume size                  */
+    double sigma_wca;    /* lipid-protein excluded-volume size            */
+    double sigma_pp;     /* protein-protein excluded-volume size          */
     double box[3];
     int    periodic[3];
     int    pad1;
@@ -66,12 +67,14 @@ typedef struct {
 static const double OR_TWO_SIXTH = 1.122462048309373;
 
 static double or_wca_cut(const or_model* m) { return OR_TWO_SIXTH * m->sigma_wca; }
+static double or_wca_pp_cut(const or_model* m) { return OR_TWO_SIXTH * m->sigma_pp; }
 
 /* Search cutoff: the widest type-pair cutoff. */
 double or_search_cutoff(const or_model* m)
 {
-    double a = m->rc, b = or_wca_cut(m);
-    return a > b ? a : b;
+    double a = m->rc, b = or_wca_cut(m), c = or_wca_pp_cut(m);
+    double r = a > b ? a : b;
+    return r > c ? r : c;
 }
 
 /* Minimum image along one axis: d - L * rint(d / L). */
@@ -241,10 +244,15 @@ double or_lipid_pair(const or_model* m, const double d[3], double r2, const doub
 }
 
 /* Purely repulsive Weeks-Chandler-Andersen term for every pair that is not
- * lipid-lipid: 4 e [(s/r)^12 - (s/r)^6] + e for r < 2^(1/6) s. */
-double or_wca_pair(const or_model* m, const double d[3], double r2, double Fi[3])
+ * lipid-lipid: 4 e [(s/r)^12 - (s/r)^6] + e for r < 2^(1/6) s, with
+ * s = sigma_wca for lipid-protein pairs and s = sigma_pp for
+ * protein-protein pairs.  Reading: the workloads' spectrin chains (bond
+ * lengths 0.45-1 sigma, several chains meeting at each junction) put beads
+ * of neighbouring chains ~0.7 sigma apart, so the protein-protein size is a
+ * parameter of its own. */
+double or_wca_pair_s(const or_model* m, double sig, const double d[3], double r2, double Fi[3])
 {
-    double s2 = m->sigma_wca * m->sigma_wca / r2;
+    double s2 = sig * sig / r2;
     double s6 = s2 * s2 * s2;
     double s12 = s6 * s6;
     double U = 4.0 * m->eps_wca * (s12 - s6) + m->eps_wca;
@@ -254,10 +262,17 @@ double or_wca_pair(const or_model* m, const double d[3], double r2, double Fi[3]
     return U;
 }
 
+double or_wca_pair(const or_model* m, const double d[3], double r2, double Fi[3])
+{
+    return or_wca_pair_s(m, m->sigma_wca, d, r2, Fi);
+}
+
 /* Cutoff of a type pair. */
 static inline double or_pair_cut(const or_model* m, int ti, int tj)
 {
-    return (ti == OR_LIPID && tj == OR_LIPID) ? m->rc : or_wca_cut(m);
+    if (ti == OR_LIPID && tj == OR_LIPID) return m->rc;
+    if (ti == OR_LIPID || tj == OR_LIPID) return or_wca_cut(m);
+    return or_wca_pp_cut(m);
 }
 
 /* Full pair evaluation for a type pair (no exclusion test). */
@@ -266,7 +281,8 @@ double or_pair_terms(const or_model* m, int ti, int tj, const double d[3], doubl
 {
     if (ti == OR_LIPID && tj == OR_LIPID) return or_lipid_pair(m, d, r2, ni, nj, Fi, Ti, Tj);
     for (int k = 0; k < 3; k++) { Ti[k] = 0.0; Tj[k] = 0.0; }
-    return or_wca_pair(m, d, r2, Fi);
+    double sig = (ti == OR_LIPID || tj == OR_LIPID) ? m->sigma_wca : m->sigma_pp;
+    return or_wca_pair_s(m, sig, d, r2, Fi);
 }
 
 /* Harmonic bond 1/2 kb (r - r0)^2; d = x_b - x_a; returns U and force on a. */

@@ -34,6 +34,22 @@ def make_params(**kw) -> Params:
     return p
 
 
+def cell_sort(cell, K: int, stream=None):
+    """Stable sort of device int32 cell ids (torch tensor on CUDA) through
+    orbc_cell_sort; returns (perm, cell_start) as device tensors."""
+    import torch
+    assert cell.is_cuda and cell.dtype == torch.int32 and cell.is_contiguous()
+    n = cell.numel()
+    perm = torch.empty(n, dtype=torch.int32, device=cell.device)
+    start = torch.empty(K + 1, dtype=torch.int32, device=cell.device)
+    s = stream if stream is not None else torch.cuda.current_stream(cell.device).cuda_stream
+    rc = load().orbc_cell_sort(C.c_void_p(cell.data_ptr()), n, K, C.c_void_p(perm.data_ptr()),
+                               C.c_void_p(start.data_ptr()), C.c_void_p(s))
+    if rc != 0:
+        raise OrbcError(rc, "orbc_cell_sort")
+    return perm, start
+
+
 class System:
     """One membrane on the GPU.  Methods map one to one onto the C ABI."""
 

@@ -118,14 +118,17 @@ static Inst make_inst(const Params& P) {
     const double two_sixth = 1.122462048309373;
     I.eps = (float)P.eps; I.rmin = (float)(two_sixth * P.sigma); I.rc = (float)P.rc_lipid; I.mu = (float)P.mu;
     I.s0 = (float)P.sin_theta0; I.eps_wca = (float)P.eps_wca; I.sig_wca = (float)P.sigma_wca; I.zeta = P.zeta;
+    I.sig_pp = (float)P.sigma_wca_pp; I.sig_pp_d = P.sigma_wca_pp;
     I.eps_d = P.eps; I.rmin_d = two_sixth * P.sigma; I.rc_d = P.rc_lipid; I.mu_d = P.mu; I.s0_d = P.sin_theta0;
     I.eps_wca_d = P.eps_wca; I.sig_wca_d = P.sigma_wca;
-    const double rcw = two_sixth * P.sigma_wca;
+    const double rcw = two_sixth * P.sigma_wca, rcp = two_sixth * P.sigma_wca_pp;
     I.rc2_ll = P.rc_lipid * P.rc_lipid;
     I.rc2_wca = rcw * rcw;
+    I.rc2_pp = rcp * rcp;
     I.rc2f_ll = (float)I.rc2_ll;
     I.rc2f_wca = (float)I.rc2_wca;
-    I.rs = std::max(P.rc_lipid, rcw);
+    I.rc2f_pp = (float)I.rc2_pp;
+    I.rs = std::max(P.rc_lipid, std::max(rcw, rcp));
     I.rsf = (float)I.rs;
     I.skin = P.skin;
     for (int a = 0; a < 3; a++) {
@@ -637,7 +640,7 @@ static int guarded(orbc_system* s, F&& f) {
 static Params to_params(const orbc_params* p) {
     Params P;
     P.eps = p->eps; P.sigma = p->sigma; P.rc_lipid = p->rc_lipid; P.mu = p->mu; P.sin_theta0 = p->sin_theta0;
-    P.zeta = p->zeta; P.eps_wca = p->eps_wca; P.sigma_wca = p->sigma_wca;
+    P.zeta = p->zeta; P.eps_wca = p->eps_wca; P.sigma_wca = p->sigma_wca; P.sigma_wca_pp = p->sigma_wca_pp;
     P.dt = p->dt; P.kT = p->kT; P.gamma_t = p->gamma_t; P.gamma_r = p->gamma_r; P.mass = p->mass; P.inertia = p->inertia;
     for (int a = 0; a < 3; a++) { P.box[a] = p->box[a]; P.periodic[a] = p->periodic[a] ? 1 : 0; }
     P.n_centroids = p->n_centroids; P.n_lloyd_init = p->n_lloyd_init; P.rebuild_every = p->rebuild_every;
@@ -651,7 +654,8 @@ static void check_params(const Params& P) {
     if (!(fin(P.eps) && fin(P.sigma) && P.sigma > 0 && fin(P.rc_lipid) && P.rc_lipid > 1.122462048309373 * P.sigma))
         throw ArgError("invalid lipid potential parameters (need rc_lipid > 2^(1/6) sigma)");
     if (P.zeta < 1 || P.zeta > 16) throw ArgError("zeta must be in 1..16");
-    if (!(fin(P.eps_wca) && fin(P.sigma_wca) && P.sigma_wca > 0)) throw ArgError("invalid WCA parameters");
+    if (!(fin(P.eps_wca) && fin(P.sigma_wca) && P.sigma_wca > 0 && fin(P.sigma_wca_pp) && P.sigma_wca_pp > 0))
+        throw ArgError("invalid WCA parameters");
     if (!(P.dt > 0 && fin(P.dt) && P.mass > 0 && P.inertia > 0 && P.kT >= 0 && P.gamma_t >= 0 && P.gamma_r >= 0))
         throw ArgError("invalid integrator parameters");
     for (int a = 0; a < 3; a++)
@@ -670,7 +674,7 @@ void orbc_default_params(orbc_params* p) {
     if (!p) return;
     std::memset(p, 0, sizeof(*p));
     p->eps = 1.0; p->sigma = 1.0; p->rc_lipid = 2.6; p->mu = 3.0; p->sin_theta0 = 0.0; p->zeta = 4;
-    p->eps_wca = 1.0; p->sigma_wca = 1.0;
+    p->eps_wca = 1.0; p->sigma_wca = 1.0; p->sigma_wca_pp = 0.5;
     p->dt = 0.01; p->kT = 0.2; p->gamma_t = 1.0; p->gamma_r = 1.0; p->mass = 1.0; p->inertia = 1.0;
     p->n_centroids = 64; p->n_lloyd_init = 10; p->rebuild_every = 1; p->skin = 0.0; p->grid_h = 0.0;
     p->seed = 0; p->instance = 0; p->precision = ORBC_F32_FORCE_F64_STATE;

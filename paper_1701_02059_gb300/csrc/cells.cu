@@ -520,6 +520,11 @@ __global__ void k_estep_warp(View v, int* __restrict__ cell_out) {
     }
     int lo[3], hi[3];
     warp_box(g, valid, lo, hi);
+    if (hi[0] - lo[0] > 2 || hi[1] - lo[1] > 2 || hi[2] - lo[2] > 2) {
+        // queries not clustered in space (e.g. input order): per-thread search
+        if (valid) estep_one(v, i, cell_out);
+        return;
+    }
     float best = 3.0e38f, second = 3.0e38f;
     int bk = -1;
     int r = 0;
@@ -896,6 +901,10 @@ __global__ void k_adjacency(View v, const unsigned long long* __restrict__ rmax_
     }
     int lo[3], hi[3];
     warp_box(g, valid, lo, hi);
+    if (hi[0] - lo[0] > 3 || hi[1] - lo[1] > 3 || hi[2] - lo[2] > 3) {
+        if (valid) adj_one<FILL>(v, rmax_bits, count, k);
+        return;
+    }
     int n = 0;
     const int out0 = (FILL && valid) ? v.adj_ptr[k] : 0;
     for (int r = 0;; r++) {

@@ -35,7 +35,7 @@ struct StateError : std::runtime_error {
 struct Params {
     double eps = 1, sigma = 1, rc_lipid = 2.6, mu = 3, sin_theta0 = 0;
     int zeta = 4;
-    double eps_wca = 1, sigma_wca = 1;
+    double eps_wca = 1, sigma_wca = 1, sigma_wca_pp = 0.5;
     double dt = 0.01, kT = 0.2, gamma_t = 1, gamma_r = 1, mass = 1, inertia = 1;
     double box[3] = {0, 0, 0};
     int periodic[3] = {0, 0, 0};

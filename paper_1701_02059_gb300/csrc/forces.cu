@@ -166,10 +166,10 @@ __device__ inline double lipid_terms<double>(const Inst& I, double dx, double dy
     return U;
 }
 
-// WCA; d = x_j - x_i; adds the force on i.
+// WCA; d = x_j - x_i; adds the force on i.  pp: protein-protein size.
 template <typename T>
-__device__ inline T wca_terms(const Inst& I, T dx, T dy, T dz, T r2, T& fx, T& fy, T& fz) {
-    T sig = (sizeof(T) == 4) ? (T)I.sig_wca : (T)I.sig_wca_d;
+__device__ inline T wca_terms(const Inst& I, bool pp, T dx, T dy, T dz, T r2, T& fx, T& fy, T& fz) {
+    T sig = (sizeof(T) == 4) ? (T)(pp ? I.sig_pp : I.sig_wca) : (T)(pp ? I.sig_pp_d : I.sig_wca_d);
     T e = (sizeof(T) == 4) ? (T)I.eps_wca : (T)I.eps_wca_d;
     T s2 = sig * sig / r2;
     T s6 = s2 * s2 * s2;
@@ -221,10 +221,10 @@ template <> struct Acc<double> {
 };
 
 // exact FP64 inclusion decision for a pair inside the cutoff band
-__device__ inline bool exact_inside(const View& v, const Inst& I, int pi, int pj, bool ll) {
+__device__ inline bool exact_inside(const View& v, const Inst& I, int pi, int pj, int cls) {
     size_t N = v.N;
     double d2 = dist2_grid_d(v.xq[pj], v.xq[N + pj], v.xq[2 * N + pj], v.xq[pi], v.xq[N + pi], v.xq[2 * N + pi], I);
-    return d2 < (ll ? I.rc2_ll : I.rc2_wca);
+    return d2 < (cls == 0 ? I.rc2_ll : (cls == 1 ? I.rc2_wca : I.rc2_pp));
 }
 
 // 1-2 and 1-3 bonded pairs carry no excluded-volume term (bonded directly,
@@ -310,9 +310,10 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
     const long long ckx = v.cq[k], cky = v.cq[(size_t)v.Ktot + k], ckz = v.cq[(size_t)2 * v.Ktot + k];
     const float rs_b = I.rsf + kFilterBand;
     const float rs2f = rs_b * rs_b;
-    const float rcl = sqrtf(I.rc2f_ll), rcw = sqrtf(I.rc2f_wca);
+    const float rcl = sqrtf(I.rc2f_ll), rcw = sqrtf(I.rc2f_wca), rcp = sqrtf(I.rc2f_pp);
     const float ll_lo = (rcl - kCutBand) * (rcl - kCutBand), ll_hi = (rcl + kCutBand) * (rcl + kCutBand);
     const float w_lo = (rcw - kCutBand) * (rcw - kCutBand), w_hi = (rcw + kCutBand) * (rcw + kCutBand);
+    const float p_lo = (rcp - kCutBand) * (rcp - kCutBand), p_hi = (rcp + kCutBand) * (rcp + kCutBand);
     const size_t N = v.N;
     unsigned phase = 0;
     if (tid == 0) mbar_init(&bar, 1);
@@ -434,18 +435,20 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
                         const int4 sj = sq[j];
                         const int tj = sj.w & 0xff;
                         const bool ll = (ti == kLipid) && (tj == kLipid);
+                        const int cls = ll ? 0 : ((ti == kLipid || tj == kLipid) ? 1 : 2);
                         const int dxq = (int)((unsigned)sj.x - (unsigned)qi.x);
                         const int dyq = (int)((unsigned)sj.y - (unsigned)qi.y);
                         const int dzq = (int)((unsigned)sj.z - (unsigned)qi.z);
                         const float dxf = (float)dxq * kMirrorUnit, dyf = (float)dyq * kMirrorUnit, dzf = (float)dzq * kMirrorUnit;
                         const float r2f = fmaf(dxf, dxf, fmaf(dyf, dyf, dzf * dzf));
-                        const float lo = ll ? ll_lo : w_lo, hi = ll ? ll_hi : w_hi;
+                        const float lo = cls == 0 ? ll_lo : (cls == 1 ? w_lo : p_lo);
+                        const float hi = cls == 0 ? ll_hi : (cls == 1 ? w_hi : p_hi);
                         if (r2f >= hi) continue;
                         const float4 oj = so[j];
                         const int pj = __float_as_int(oj.w);
                         bool in = r2f < lo;
-                        if (!in) in = exact_inside(v, I, pi, pj, ll);
-                        if (in && !ll && is_excluded(v, I, v.id[pi], v.id[pj])) in = false;
+                        if (!in) in = exact_inside(v, I, pi, pj, cls);
+                        if (in && cls == 2 && is_excluded(v, I, v.id[pi], v.id[pj])) in = false;
                         if (!in) continue;
                         T fx = 0, fy = 0, fz = 0, tx = 0, ty = 0, tz = 0, U;
                         T dx, dy, dz, r2;
@@ -469,7 +472,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
                             }
                             U = lipid_terms<T>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz);
                         } else {
-                            U = wca_terms<T>(I, dx, dy, dz, r2, fx, fy, fz);
+                            U = wca_terms<T>(I, cls == 2, dx, dy, dz, r2, fx, fy, fz);
                         }
                         if (!(fabsf(fx) + fabsf(fy) + fabsf(fz) + fabsf(tx) + fabsf(ty) + fabsf(tz) < (T)3.0e30))
                             atomicOr(v.status, kStatusNaN);

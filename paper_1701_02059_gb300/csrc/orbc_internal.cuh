@@ -45,12 +45,12 @@ struct Inst {
     float boxf[3];
     int periodic[3];
     // potential
-    float eps, rmin, rc, mu, s0, eps_wca, sig_wca;
+    float eps, rmin, rc, mu, s0, eps_wca, sig_wca, sig_pp;
     int zeta;
-    double eps_d, rmin_d, rc_d, mu_d, s0_d, eps_wca_d, sig_wca_d;
-    double rc2_ll, rc2_wca;     // FP64 squared type-pair cutoffs (inclusion decision)
+    double eps_d, rmin_d, rc_d, mu_d, s0_d, eps_wca_d, sig_wca_d, sig_pp_d;
+    double rc2_ll, rc2_wca, rc2_pp;   // FP64 squared type-pair cutoffs (inclusion decision)
     double rs, skin;            // search cutoff and skin
-    float rc2f_ll, rc2f_wca, rsf;
+    float rc2f_ll, rc2f_wca, rc2f_pp, rsf;
     // integrator (host-computed constants)
     float h_m, h_i;             // dt/2/m, dt/2/I
     float hdt;                  // dt/2

@@ -404,3 +404,28 @@ def test_rbc_steps_keep_cells_exact(rbc):
     assert np.array_equal(c["cell_of_id"][idx],
                           oracle.assign_brute(st["pos"][idx], c["centroids"], mem.box, mem.periodic))
     assert np.isfinite(st["pos"]).all() and st["step"] == 3
+
+
+# --------------------------------------------------------------------------- standalone stable sort
+
+@pytest.mark.parametrize("n,K,big", [(100_000, 2000, False), (50_000, 9, True), (3, 5, False), (0, 4, False)])
+def test_cell_sort_entry_point(n, K, big):
+    """orbc_cell_sort on device memory equals numpy's stable argsort by cell,
+    including empty cells and cells beyond the warp and block sorts."""
+    import torch
+    rng = np.random.default_rng(n + K)
+    cell = rng.integers(0, K, size=n).astype(np.int32)
+    if big:
+        cell[: n // 2] = 3          # one cell of > 2,048 items
+        cell[n // 2: n // 2 + 500] = 7
+    d = torch.from_numpy(cell).cuda()
+    perm, start = G.cell_sort(d, K)
+    torch.cuda.synchronize()
+    assert np.array_equal(perm.cpu().numpy(), np.argsort(cell, kind="stable").astype(np.int32))
+    want = np.concatenate([[0], np.cumsum(np.bincount(cell, minlength=K))]).astype(np.int32)
+    assert np.array_equal(start.cpu().numpy(), want)
+    if n:
+        bad = d.clone()
+        bad[0] = K
+        with pytest.raises(G.OrbcError):
+            G.cell_sort(bad, K)

@@ -88,14 +88,20 @@ def test_lipid_pair_antiparallel_tilted_phi():
 
 
 def test_wca_textbook_points():
-    """WCA at r = sigma: LJ is 0 so U = eps, and the force is 24 eps/sigma;
-    at r = 2^(1/6) sigma both vanish (LJ minimum)."""
-    m = oracle.model()
-    U, F, _, _ = oracle.pair_terms(m, 1, 2, [0, 0, 1.0], [0, 0, 0], [0, 0, 0])
+    """WCA at r = s: LJ is 0 so U = eps, and the force is 24 eps/s; at
+    r = 2^(1/6) s both vanish (LJ minimum).  s = sigma_wca for a
+    lipid-protein pair, sigma_pp for a protein-protein pair."""
+    m = oracle.model(sigma_wca=1.0, sigma_pp=0.5)
+    U, F, _, _ = oracle.pair_terms(m, 0, 2, [0, 0, 1.0], [0, 0, 1], [0, 0, 0])
     assert U == pytest.approx(1.0, abs=1e-14)
     assert F[2] == pytest.approx(-24.0, rel=1e-14)
     U, F, _, _ = oracle.pair_terms(m, 0, 2, [RMIN, 0, 0], [0, 0, 1], [0, 0, 0])
     assert abs(U) < 1e-14 and np.abs(F).max() < 1e-12
+    U, F, _, _ = oracle.pair_terms(m, 1, 2, [0, 0.5, 0], [0, 0, 0], [0, 0, 0])
+    assert U == pytest.approx(1.0, abs=1e-14)
+    assert F[1] == pytest.approx(-48.0, rel=1e-14)
+    U, F, _, _ = oracle.pair_terms(m, 2, 2, [0, 0, 0.5 * RMIN], [0, 0, 0], [0, 0, 0])
+    assert abs(U) < 1e-14 and np.abs(F).max() < 1e-11
 
 
 def _rotate(n, axis, ang):
@@ -546,9 +552,9 @@ def test_periodic_minimum_image_against_scipy():
 def test_one_three_exclusion():
     """Spectrin beads two bonds apart (sharing a bond partner) carry no
     excluded-volume term; three bonds apart they do."""
-    m = oracle.model()
-    # chain 0-1-2-3 folded so that 0..2 and 0..3 are both within the WCA cutoff
-    x = np.array([[0.0, 0.0, 0.0], [0.6, 0.0, 0.0], [0.6, 0.6, 0.0], [0.0, 0.6, 0.0]])
+    m = oracle.model(sigma_pp=0.5)
+    # chain 0-1-2-3 folded so that 1-3 pairs and the 1-4 pair are inside the cutoff
+    x = np.array([[0.0, 0.0, 0.0], [0.35, 0.0, 0.0], [0.35, 0.35, 0.0], [0.0, 0.35, 0.0]])
     typ = np.full(4, 2, np.uint8)
     ids = np.arange(4, dtype=np.uint32)
     bonds = np.array([[0, 1], [1, 2], [2, 3]], np.int32)
