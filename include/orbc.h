@@ -203,6 +203,22 @@ ORBC_API int orbc_get_kernel_times(orbc_system* s, char* names_csv, int names_ca
  * [0, K)), ORBC_E_NOMEM, ORBC_E_CUDA. */
 ORBC_API int orbc_cell_sort(const int* d_cell, int n, int K, int* d_perm, int* d_cell_start, void* cuda_stream);
 
+/* orbc_cell_sort for callers that cannot allocate device memory (a pool or
+ * arena allocator that owns the device, a runtime that forbids cudaMalloc
+ * after start-up).  The paper has no counterpart; this is a deployment
+ * variant.  Same arguments, results and errors as orbc_cell_sort; it calls
+ * no allocator.  Its scratch is one fixed array of about 4.7 MB in the
+ * library's device memory, present on every device that loads the library
+ * until the process exits, which bounds the sizes: n <= 1,048,576 and
+ * K <= 65,536, larger requests return ORBC_E_NOMEM.  The first call on each
+ * device looks up the array's device address with that device current
+ * (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  Every call reuses the same array and zeroes what must start at
+ * zero; calls that overlap on the GPU (other streams, other threads) race
+ * on it and must be serialised by the caller.  Synchronises the stream. */
+ORBC_API int orbc_cell_sort_noalloc(const int* d_cell, int n, int K, int* d_perm, int* d_cell_start,
+                                    void* cuda_stream);
+
 /* Number of CUDA kernels this handle has launched since creation. */
 ORBC_API int orbc_get_launch_count(orbc_system* s, long long* count);
 

@@ -20,7 +20,7 @@ EXPORTS = [
     "orbc_default_params", "orbc_create", "orbc_set_particles", "orbc_set_bonds", "orbc_init_cells",
     "orbc_rebuild_cells", "orbc_compute_forces", "orbc_integrate", "orbc_get_state", "orbc_get_forces",
     "orbc_get_cells", "orbc_get_adjacency_len", "orbc_dump_pairs", "orbc_set_timing", "orbc_get_kernel_times",
-    "orbc_get_launch_count", "orbc_last_error", "orbc_destroy", "orbc_cell_sort",
+    "orbc_get_launch_count", "orbc_last_error", "orbc_destroy", "orbc_cell_sort", "orbc_cell_sort_noalloc",
 ]
 
 
@@ -74,6 +74,7 @@ def load(path: str | None = None):
     L.orbc_get_kernel_times.argtypes = [V, C.c_char_p, C.c_int, V, C.c_int, C.POINTER(C.c_int)]
     L.orbc_get_launch_count.argtypes = [V, C.POINTER(C.c_longlong)]
     L.orbc_cell_sort.argtypes = [V, C.c_int, C.c_int, V, V, V]
+    L.orbc_cell_sort_noalloc.argtypes = [V, C.c_int, C.c_int, V, V, V]
     L.orbc_last_error.argtypes = [V]
     L.orbc_last_error.restype = C.c_char_p
     L.orbc_destroy.argtypes = [V]

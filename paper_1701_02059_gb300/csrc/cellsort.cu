@@ -6,6 +6,8 @@
 // bitonic up to 128, block bitonic up to 2048, exact rank beyond).
 #include "ensemble.cuh"
 
+#include <mutex>
+
 #include "../../include/orbc.h"
 
 namespace orbc {
@@ -103,6 +105,64 @@ extern "C" int orbc_cell_sort(const int* d_cell, int n, int K, int* d_perm, int*
         return rc;
     } catch (const std::exception&) {
         if (buf) cudaFreeAsync(buf, st);
+        return ORBC_E_CUDA;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Variant for callers that cannot allocate device memory: code running under
+// a pool or arena allocator that owns the whole device, or inside a runtime
+// that forbids cudaMalloc after start-up.  Its scratch is a fixed array in
+// the library's own device memory, present on every device that loads the
+// library until the process exits.
+namespace orbc {
+constexpr int kStaticMaxItems = 1 << 20;   // n <= 1,048,576
+constexpr int kStaticMaxCells = 1 << 16;   // K <= 65,536
+constexpr size_t kStaticInts = 2 * ((size_t)kStaticMaxCells + 1) + (size_t)kStaticMaxItems + 64;
+static __device__ __align__(256) int g_cell_sort_scratch[kStaticInts];   // ~4.7 MB per device
+
+// Host code may not use g_cell_sort_scratch as a device address: its host
+// name is only a stand-in.  The device address is looked up once per device
+// (with that device current) and cached.
+static std::mutex g_scratch_mu;
+static int* g_scratch_addr[64] = {nullptr};
+
+static int* static_scratch(int dev) {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!g_scratch_addr[dev]) {
+        int* p = nullptr;
+        if (cudaGetSymbolAddress((void**)&p, g_cell_sort_scratch) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_scratch_addr[dev] = p;
+    }
+    return g_scratch_addr[dev];
+}
+}  // namespace orbc
+
+extern "C" int orbc_cell_sort_noalloc(const int* d_cell, int n, int K, int* d_perm, int* d_cell_start,
+                                      void* cuda_stream) {
+    using namespace orbc;
+    if (n < 0 || K < 1 || (n > 0 && (!d_cell || !d_perm)) || !d_cell_start) return ORBC_E_ARG;
+    if (n > kStaticMaxItems || K > kStaticMaxCells) return ORBC_E_NOMEM;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return ORBC_E_CUDA; }
+    int* base = static_scratch(dev);
+    if (!base) return ORBC_E_CUDA;
+    try {
+        int* counts = base;
+        int* cursor = counts + (K + 1);
+        int* tmp = cursor + (K + 1);
+        unsigned* flag = (unsigned*)(tmp + n);
+        if (n > 0 && !cell_sort_cells_valid(d_cell, n, K, st, flag)) return ORBC_E_ARG;
+        if (n > 0) cell_sort_run(d_cell, n, K, d_perm, d_cell_start, st, counts, cursor, tmp, flag);
+        else CK(cudaMemsetAsync(d_cell_start, 0, sizeof(int) * (K + 1), st));
+        CK(cudaStreamSynchronize(st));
+        return ORBC_OK;
+    } catch (const std::exception&) {
         return ORBC_E_CUDA;
     }
 }
