@@ -130,6 +130,8 @@ static Inst make_inst(const Params& P) {
     I.rc2f_pp = (float)I.rc2_pp;
     I.rs = std::max(P.rc_lipid, std::max(rcw, rcp));
     I.rsf = (float)I.rs;
+    I.aw = (float)(1.5707963267948966 / (P.rc_lipid - two_sixth * P.sigma));
+    I.eps2z_aw = (float)(P.eps * 2.0 * P.zeta * (1.5707963267948966 / (P.rc_lipid - two_sixth * P.sigma)));
     I.skin = P.skin;
     for (int a = 0; a < 3; a++) {
         I.periodic[a] = P.periodic[a];
@@ -217,6 +219,10 @@ void Ensemble::setup(const std::vector<HostInstance>& list) {
     d_perm = alloc<int>(N);
     d_cell_tmp = alloc<int>(N);
     d_rmax = alloc<unsigned long long>(B);
+    d_rho = alloc<float>(Ktot);
+    d_cf = alloc<float4>(Ktot);
+    d_dmax = alloc<unsigned>(B);
+    prev_adj_valid_ = false;
     d_energy = alloc<long long>((size_t)8 * B);
     d_step = alloc<long long>(B);
     CK(cudaMemcpyAsync(d_step, step_h.data(), sizeof(long long) * B, cudaMemcpyHostToDevice, stream));

@@ -76,7 +76,7 @@ __global__ void k_mstep_finish(View v, long long* __restrict__ S, int* __restric
 // Rebuild M-step on cell-sorted particles: one warp per cell sums its lipids'
 // grid displacements (exact int64, shuffles), updates the centroid and
 // folds it into the instance bounding box (block-level, then atomics).
-__global__ void k_mstep_sorted(View v, long long* __restrict__ bb) {
+__global__ void k_mstep_sorted(View v, long long* __restrict__ bb, unsigned* __restrict__ dmax) {
     __shared__ long long wmin[8][3], wmax[8][3];
     __shared__ int winst[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -105,12 +105,19 @@ __global__ void k_mstep_sorted(View v, long long* __restrict__ bb) {
             n += __shfl_xor_sync(0xffffffffu, n, off);
         }
         long long S[3] = {S0, S1, S2};
+        float mv2 = 0.f;
         for (int a = 0; a < 3; a++) {
-            if (n > 0) c[a] += floor_div_ll(2 * S[a] + n, 2 * (long long)n);
+            long long step = 0;
+            if (n > 0) step = floor_div_ll(2 * S[a] + n, 2 * (long long)n);
+            const float sf = ll_to_float(step) * (float)kGridInv;
+            mv2 = fmaf(sf, sf, mv2);
+            c[a] += step;
             if (I.periodic[a]) c[a] = floor_mod_ll(c[a], I.boxq[a]);
         }
-        if (lane == 0)
+        if (lane == 0) {
             for (int a = 0; a < 3; a++) v.cq[(size_t)a * v.Ktot + k] = c[a];
+            if (dmax) atomicMax(&dmax[b], __float_as_uint(sqrtf(mv2) * 1.0001f + 1e-6f));
+        }
     }
     if (lane == 0) {
         winst[warp] = b;
@@ -239,6 +246,8 @@ __global__ void k_tile_sort(View v, const unsigned long long* __restrict__ key, 
 }
 
 // rank -> new cell index; writes order[new] = old and the permuted centroids.
+// Tiles wholly below or above a record need no search (nearly sorted keys
+// between rebuilds make this the common case).
 __global__ void k_rank_scatter(View v, const SortRec* __restrict__ tiles, int ntiles, const long long* __restrict__ cq_old,
                                int* __restrict__ new_of_old) {
     int pos = blockIdx.x * blockDim.x + threadIdx.x;   // position in the tiled array
@@ -248,21 +257,27 @@ __global__ void k_rank_scatter(View v, const SortRec* __restrict__ tiles, int nt
     const Inst& I = v.inst[me.inst];
     // rank inside the instance: over every tile holding part of the instance,
     // (records smaller than me) - (records of smaller instances)
+    SortRec first;
+    first.inst = me.inst; first.key = 0; first.idx = -1;
     int rank = 0;
     int t0 = I.k0 / kTile, t1 = (I.k0 + I.K - 1) / kTile;
     for (int t = t0; t <= t1; t++) {
         const SortRec* T = tiles + (size_t)t * kTile;
-        int lo = 0, hi = kTile;   // first element not less than me
-        while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if (rec_less(T[mid], me)) lo = mid + 1; else hi = mid;
+        const SortRec tmin = T[0], tmax = T[kTile - 1];
+        int lo, lo2;
+        if (rec_less(tmax, me)) lo = kTile;
+        else if (!rec_less(tmin, me)) lo = 0;
+        else {
+            int a = 0, c = kTile;
+            while (a < c) { int mid = (a + c) >> 1; if (rec_less(T[mid], me)) a = mid + 1; else c = mid; }
+            lo = a;
         }
-        // count only records of my instance that are smaller
-        int lo2 = 0, hi2 = kTile;   // first record of my instance
-        SortRec first; first.inst = me.inst; first.key = 0; first.idx = -1;
-        while (lo2 < hi2) {
-            int mid = (lo2 + hi2) >> 1;
-            if (rec_less(T[mid], first)) lo2 = mid + 1; else hi2 = mid;
+        if (rec_less(tmax, first)) lo2 = kTile;
+        else if (!rec_less(tmin, first)) lo2 = 0;
+        else {
+            int a = 0, c = kTile;
+            while (a < c) { int mid = (a + c) >> 1; if (rec_less(T[mid], first)) a = mid + 1; else c = mid; }
+            lo2 = a;
         }
         rank += lo - lo2;
     }
@@ -303,7 +318,7 @@ __global__ void k_grid_count(View v, int* __restrict__ gcount, int* __restrict__
     atomicAdd(&gcount[g], 1);
 }
 
-__global__ void k_grid_fill(View v, const int* __restrict__ gidx, int* __restrict__ cursor) {
+__global__ void k_grid_fill(View v, const int* __restrict__ gidx, int* __restrict__ cursor, float4* __restrict__ cf) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= v.Ktot) return;
     int b = find_inst(v.inst_k0, v.B, k);
@@ -316,6 +331,7 @@ __global__ void k_grid_fill(View v, const int* __restrict__ gidx, int* __restric
     grid_coord(v.cq[(size_t)2 * v.Ktot + k], I, 2, r[2]);
     v.gcent[pos] = k;
     v.gcf[pos] = make_float4(r[0], r[1], r[2], __int_as_float(k));
+    if (cf) cf[k] = make_float4(r[0], r[1], r[2], 0.f);
 }
 
 // ============================================================== E-step
@@ -578,6 +594,95 @@ __global__ void k_estep(View v, int* __restrict__ cell_out) {
     if (i < v.N) estep_one(v, i, cell_out);
 }
 
+// Rebuild E-step from the previous cell list (the paper's guess from the
+// previous particle, made exact): the candidates are the particle's previous
+// cell and its previous neighbouring cells, renumbered by the Morton
+// relabel.  Every centroid outside that set was at least rho_k from the old
+// centroid c_k when the list was built (rho_k: distance to the nearest
+// non-neighbour), and every centroid has since moved at most dmax, so none
+// of them is within best + band of the particle when
+//   sqrt(best) + band < rho_k - 2 dmax - |x - c_k|   (FP32 with margins).
+// Particles that fail the test take the grid search.
+constexpr float kCertMargin = 4e-3f;
+__global__ void k_estep_fast(View v, const int* __restrict__ cell_old, const int* __restrict__ adj_ptr_old,
+                             const int* __restrict__ adj_old, const float* __restrict__ rho_old,
+                             const int* __restrict__ new_of_old, const float4* __restrict__ cf,
+                             const unsigned* __restrict__ dmax, int* __restrict__ cell_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = i < v.N;
+    int b = 0, ko = -1, kn = -1;
+    long long xq[3] = {0, 0, 0};
+    float p[3] = {0, 0, 0};
+    if (valid) {
+        b = find_inst(v.inst_p0, v.B, i);
+        xq[0] = v.xq[i]; xq[1] = v.xq[(size_t)v.N + i]; xq[2] = v.xq[(size_t)2 * v.N + i];
+        for (int a = 0; a < 3; a++) grid_coord(xq[a], v.inst[b], a, p[a]);
+        ko = cell_old[i];
+        kn = new_of_old[ko];
+    }
+    const Inst& I = v.inst[b];
+    float best = 3.0e38f, second = 3.0e38f, dself2 = 3.0e38f;
+    int bk = -1;
+    // the warp walks the distinct previous cells of its lanes (usually one or
+    // two); each cell's candidate row is loaded once, one candidate per lane,
+    // and broadcast; every lane scores every candidate of the union
+    unsigned todo = __ballot_sync(0xffffffffu, valid);
+    while (todo) {
+        const int leader = __ffs(todo) - 1;
+        const int kc = __shfl_sync(0xffffffffu, ko, leader);
+        const unsigned grp = __ballot_sync(0xffffffffu, valid && ko == kc);
+        todo &= ~grp;
+        const int a0 = adj_ptr_old[kc], len = adj_ptr_old[kc + 1] - a0;
+        for (int c0 = 0; c0 < len; c0 += 32) {
+            int j = -1;
+            float4 c = make_float4(0, 0, 0, 0);
+            if (c0 + lane < len) {
+                j = new_of_old[adj_old[a0 + c0 + lane]];
+                c = cf[j];
+            }
+            const int cnt = min(32, len - c0);
+            for (int q = 0; q < cnt; q++) {
+                const int jq = __shfl_sync(0xffffffffu, j, q);
+                const float cx = __shfl_sync(0xffffffffu, c.x, q);
+                const float cy = __shfl_sync(0xffffffffu, c.y, q);
+                const float cz = __shfl_sync(0xffffffffu, c.z, q);
+                const float dx = axis_dist(p[0], cx, I, 0), dy = axis_dist(p[1], cy, I, 1), dz = axis_dist(p[2], cz, I, 2);
+                const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (jq == kn) dself2 = d2;
+                if (d2 < best || (d2 == best && jq < bk)) { second = best; best = d2; bk = jq; }
+                else if (d2 < second) second = d2;
+            }
+        }
+    }
+    if (!valid) return;
+    const float lim = sqrtf(best) + kBandE;
+    const float cert = rho_old[ko] - 2.0f * __uint_as_float(dmax[b]) - sqrtf(dself2) - kCertMargin;
+    if (bk < 0 || dself2 >= 3.0e38f || !(lim < cert)) {
+        estep_one(v, i, cell_out);
+        return;
+    }
+    if (second > lim * lim) { cell_out[i] = bk; return; }
+    // tie band among the candidates of the particle's own previous cell: FP64
+    double best64 = 1e300;
+    int bk64 = -1;
+    const int a0 = adj_ptr_old[ko], a1 = adj_ptr_old[ko + 1];
+    for (int q = a0; q < a1; q++) {
+        const int j = new_of_old[adj_old[q]];
+        const float4 c = cf[j];
+        const float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1), dz = axis_dist(p[2], c.z, I, 2);
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (d2 <= lim * lim) {
+            const double d64 = dist2_grid_d(xq[0], xq[1], xq[2], v.cq[j], v.cq[(size_t)v.Ktot + j],
+                                            v.cq[(size_t)2 * v.Ktot + j], I);
+            if (d64 < best64 || (d64 == best64 && j < bk64)) { best64 = d64; bk64 = j; }
+        }
+    }
+    // candidates of other lanes' cells within the band are not in this row:
+    // the certificate excludes them (they are farther than best + band)
+    cell_out[i] = bk64;
+}
+
 // ============================================================== stable counting sort
 __global__ void k_hist(int N, const int* __restrict__ cell, int* __restrict__ cnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -825,7 +930,8 @@ __device__ inline void sort_row(int* row, int n) {
 }
 
 template <bool FILL>
-__device__ void adj_one(const View& v, const unsigned long long* __restrict__ rmax_bits, int* __restrict__ count, int k) {
+__device__ void adj_one(const View& v, const unsigned long long* __restrict__ rmax_bits, int* __restrict__ count, int k,
+                        float* __restrict__ rho_out) {
     int b = find_inst(v.inst_k0, v.B, k);
     const Inst& I = v.inst[b];
     double Rk = v.R[k];
@@ -838,6 +944,7 @@ __device__ void adj_one(const View& v, const unsigned long long* __restrict__ rm
     g[1] = grid_coord(cy, I, 1, p[1]);
     g[2] = grid_coord(cz, I, 2, p[2]);
     int n = 0;
+    float rho = reach - kBandA;
     int out0 = FILL ? v.adj_ptr[k] : 0;
     const double tail = (I.rs) + (I.skin + I.skin);
     for (int r = 0;; r++) {
@@ -848,6 +955,7 @@ __device__ void adj_one(const View& v, const unsigned long long* __restrict__ rm
                 float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1), dz = axis_dist(p[2], c.z, I, 2);
                 float df = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
                 bool in = adj_test(v, I, k, j, Rk, df, cx, cy, cz, tail);
+                if (!in) rho = fminf(rho, df);
                 if (in) {
                     if (FILL) {
                         if (out0 + n < v.adj_cap) v.adj[out0 + n] = j;
@@ -861,7 +969,7 @@ __device__ void adj_one(const View& v, const unsigned long long* __restrict__ rm
         float lb = shell_bound(p, g, r, I, ex);
         if (ex || lb > reach) break;
     }
-    if (!FILL) count[k] = n;
+    if (!FILL) { count[k] = n; if (rho_out) rho_out[k] = rho; }
     else {
         // ascending row (insertion sort, rows are short)
         if (out0 + n > v.adj_cap) return;
@@ -871,7 +979,8 @@ __device__ void adj_one(const View& v, const unsigned long long* __restrict__ rm
 
 
 template <bool FILL>
-__global__ void k_adjacency(View v, const unsigned long long* __restrict__ rmax_bits, int* __restrict__ count) {
+__global__ void k_adjacency(View v, const unsigned long long* __restrict__ rmax_bits, int* __restrict__ count,
+                            float* __restrict__ rho_out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = k < v.Ktot;
     const int b = valid ? find_inst(v.inst_k0, v.B, k) : -1;
@@ -880,7 +989,7 @@ __global__ void k_adjacency(View v, const unsigned long long* __restrict__ rmax_
     const bool same = __all_sync(0xffffffffu, !valid || b == b0);
     const Inst& I = v.inst[b0];
     if (!same || (I.periodic[0] | I.periodic[1] | I.periodic[2])) {
-        if (valid) adj_one<FILL>(v, rmax_bits, count, k);
+        if (valid) adj_one<FILL>(v, rmax_bits, count, k, rho_out);
         return;
     }
     // warp-cooperative: 32 consecutive (Morton-ordered) cells share a region
@@ -902,10 +1011,11 @@ __global__ void k_adjacency(View v, const unsigned long long* __restrict__ rmax_
     int lo[3], hi[3];
     warp_box(g, valid, lo, hi);
     if (hi[0] - lo[0] > 3 || hi[1] - lo[1] > 3 || hi[2] - lo[2] > 3) {
-        if (valid) adj_one<FILL>(v, rmax_bits, count, k);
+        if (valid) adj_one<FILL>(v, rmax_bits, count, k, rho_out);
         return;
     }
     int n = 0;
+    float rho = reach - kBandA;
     const int out0 = (FILL && valid) ? v.adj_ptr[k] : 0;
     for (int r = 0;; r++) {
         region_ring(I, lo, hi, r, [&](long long gg) {
@@ -916,7 +1026,10 @@ __global__ void k_adjacency(View v, const unsigned long long* __restrict__ rmax_
                 const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 if (valid && d2 <= reach * reach) {
                     const int j = __float_as_int(c.w);
-                    if (adj_test(v, I, k, j, Rk, sqrtf(d2), cx, cy, cz, tail)) {
+                    const float dfj = sqrtf(d2);
+                    const bool in = adj_test(v, I, k, j, Rk, dfj, cx, cy, cz, tail);
+                    if (!in) rho = fminf(rho, dfj);
+                    if (in) {
                         if (FILL) {
                             if (out0 + n < v.adj_cap) v.adj[out0 + n] = j;
                             else atomicOr(v.status, kStatusAdjOverflow);
@@ -931,7 +1044,7 @@ __global__ void k_adjacency(View v, const unsigned long long* __restrict__ rmax_
         if (__all_sync(0xffffffffu, !valid || ex || lb > reach)) break;
     }
     if (!valid) return;
-    if (!FILL) count[k] = n;
+    if (!FILL) { count[k] = n; if (rho_out) rho_out[k] = rho; }
     else if (out0 + n <= v.adj_cap) sort_row(v.adj + out0, n);
 }
 
@@ -946,7 +1059,7 @@ void Ensemble::build_grid() {
     CK(cudaGetLastError());
     scan_exclusive(d_gcount, d_gstart, Gtot + 1);
     CK(cudaMemsetAsync(d_gcount, 0, sizeof(int) * (Gtot + 1), stream));
-    k_grid_fill<<<nblk(Ktot, 256), 256, 0, stream>>>(v, d_gidx, d_gcount);
+    k_grid_fill<<<nblk(Ktot, 256), 256, 0, stream>>>(v, d_gidx, d_gcount, d_cf);
     launches++;
     CK(cudaGetLastError());
 }
@@ -1028,7 +1141,14 @@ void Ensemble::finish_cells() {
     View v = view();
     morton_relabel();
     build_grid();
-    estep(d_cell_new);
+    if (prev_adj_valid_) {
+        k_estep_fast<<<nblk(N, 128), 128, 0, stream>>>(v, d_cell, d_adj_ptr, d_adj, d_rho, d_new_of_old, d_cf, d_dmax,
+                                                      d_cell_new);
+        launches++;
+        CK(cudaGetLastError());
+    } else {
+        estep(d_cell_new);
+    }
     // stable counting sort
     CK(cudaMemsetAsync(d_cnt, 0, sizeof(int) * (Ktot + 1), stream));
     k_hist<<<nblk(N, 256), 256, 0, stream>>>(N, d_cell_new, d_cnt);
@@ -1058,13 +1178,14 @@ void Ensemble::finish_cells() {
     CK(cudaMemsetAsync(d_rmax, 0, sizeof(unsigned long long) * B, stream));
     k_radius<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(nv, d_rmax);
     launches++;
-    k_adjacency<false><<<nblk(Ktot, 128), 128, 0, stream>>>(nv, d_rmax, d_adjcount);
+    k_adjacency<false><<<nblk(Ktot, 128), 128, 0, stream>>>(nv, d_rmax, d_adjcount, d_rho);
     launches++;
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(d_adjcount + Ktot, 0, sizeof(int), stream));
     scan_exclusive(d_adjcount, d_adj_ptr, Ktot + 1);
     nv = view();
-    k_adjacency<true><<<nblk(Ktot, 128), 128, 0, stream>>>(nv, d_rmax, d_adjcount);
+    k_adjacency<true><<<nblk(Ktot, 128), 128, 0, stream>>>(nv, d_rmax, d_adjcount, nullptr);
+    prev_adj_valid_ = true;
     launches++;
     CK(cudaGetLastError());
     cells_valid = true;
@@ -1076,7 +1197,8 @@ void Ensemble::rebuild() {
     // M-step on the cell-sorted particles, fused with the centroid bounding box
     k_fill_bbox<<<1, 64, 0, stream>>>(d_bbox, B);
     launches++;
-    k_mstep_sorted<<<nblk(Ktot, 8), 256, 0, stream>>>(view(), d_bbox);
+    CK(cudaMemsetAsync(d_dmax, 0, sizeof(unsigned) * B, stream));
+    k_mstep_sorted<<<nblk(Ktot, 8), 256, 0, stream>>>(view(), d_bbox, d_dmax);
     launches++;
     CK(cudaGetLastError());
     bbox_ready_ = true;

@@ -131,6 +131,7 @@ private:
     std::vector<void*> allocs_;
     int cur_ = 0;
     bool bbox_ready_ = false;   // set by the fused M-step of a rebuild
+    bool prev_adj_valid_ = false;   // the cell list of the previous rebuild can seed the E-step
     // timing state
     cudaEvent_t ev0_ = nullptr, ev1_ = nullptr;
     const char* open_ = nullptr;
@@ -166,6 +167,9 @@ public:
     int* d_new_of_old = nullptr;
     int *d_cell_new = nullptr, *d_perm = nullptr, *d_cell_tmp = nullptr;
     unsigned long long* d_rmax = nullptr;
+    float* d_rho = nullptr;                  // [Ktot] distance to the nearest non-neighbour centroid
+    float4* d_cf = nullptr;                  // [Ktot] FP32 centroids by cell
+    unsigned* d_dmax = nullptr;              // [B] largest centroid move of the last M-step (float bits)
     long long* d_xref = nullptr;
     long long* d_energy = nullptr;           // [B][8] fixed-point sums
     long long* d_step = nullptr;             // [B]

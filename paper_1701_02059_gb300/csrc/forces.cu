@@ -22,11 +22,15 @@
 //      epilogue.
 #include "ensemble.cuh"
 
+#include <mutex>
+
 namespace orbc {
 
 constexpr int kPairThreads = 128;
-constexpr int kStageCap = 576;     // staged particles per pass (static shared memory < 48 KB)
+constexpr int kStageCap = 544;     // staged particles per pass
 constexpr int kQCap = 32;          // queued hits per lane before a flush
+constexpr int kMaxBins = 512;      // spatial bins of the staged particles (in-CTA counting sort)
+static_assert(kStageCap <= 1024 && kMaxBins <= 8192, "bin and rank packing in the staged record");
 constexpr int kMaxNbr = 64;        // neighbouring cells per pass
 constexpr float kFilterBand = 1e-4f;
 constexpr float kCutBand = 1e-6f;
@@ -36,7 +40,7 @@ constexpr float kCutBand = 1e-6f;
 // Returns U; adds force on i and torque on i.
 template <typename T>
 __device__ inline T lipid_terms(const Inst& I, T dx, T dy, T dz, T r2, T nix, T niy, T niz, T njx, T njy, T njz,
-                                T& fx, T& fy, T& fz, T& tx, T& ty, T& tz);
+                                T& fx, T& fy, T& fz, T& tx, T& ty, T& tz, T* tj);
 
 __device__ inline float taylor_cos(float x) {
     // Maclaurin series of cos through x^14 on [0, pi/2]; truncation < 1e-9
@@ -63,63 +67,77 @@ __device__ inline float taylor_sin(float x) {
     return x * fmaf(p, x2, 1.0f);
 }
 
-template <>
-__device__ inline float lipid_terms<float>(const Inst& I, float dx, float dy, float dz, float r2, float nix, float niy,
-                                           float niz, float njx, float njy, float njz, float& fx, float& fy, float& fz,
-                                           float& tx, float& ty, float& tz) {
-    float rinv = rsqrtf(r2);
-    float r = r2 * rinv;
+// FP32 lipid pair; Z > 0 fixes zeta at compile time (Z = 0: runtime zeta).
+template <int Z>
+__device__ inline float lipid_terms_f(const Inst& I, float dx, float dy, float dz, float r2, float nix, float niy,
+                                      float niz, float njx, float njy, float njz, float& fx, float& fy, float& fz,
+                                      float& tx, float& ty, float& tz, float* tj = nullptr) {
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
     // rh = r_ij / r = -(d) / r
-    float hx = -dx * rinv, hy = -dy * rinv, hz = -dz * rinv;
-    float s0 = I.s0;
-    float nin = fmaf(nix, njx, fmaf(niy, njy, niz * njz));
-    float nir = fmaf(nix, hx, fmaf(niy, hy, niz * hz));
-    float njr = fmaf(njx, hx, fmaf(njy, hy, njz * hz));
-    float a = fmaf(s0, njr - nir, fmaf(-nir, njr, nin)) - s0 * s0;
-    float phi = fmaf(I.mu, a - 1.0f, 1.0f);
+    const float hx = -dx * rinv, hy = -dy * rinv, hz = -dz * rinv;
+    const float s0 = I.s0;
+    const float nin = fmaf(nix, njx, fmaf(niy, njy, niz * njz));
+    const float nir = fmaf(nix, hx, fmaf(niy, hy, niz * hz));
+    const float njr = fmaf(njx, hx, fmaf(njy, hy, njz * hz));
+    const float a = fmaf(s0, njr - nir, fmaf(-nir, njr, nin)) - s0 * s0;
+    const float phi = fmaf(I.mu, a - 1.0f, 1.0f);
     float f, fp, g, gp;
     if (r < I.rmin) {
-        float q = I.rmin * rinv;
-        float q2 = q * q, q4 = q2 * q2;
+        const float q = I.rmin * rinv;
+        const float q2 = q * q, q4 = q2 * q2;
         f = fmaf(I.eps, q4 - 2.0f * q2, I.eps);
         fp = 4.0f * I.eps * rinv * (q2 - q4);
         g = -I.eps;
         gp = 0.0f;
     } else {
-        float w = 1.5707963267948966f / (I.rc - I.rmin);
-        float th = w * (r - I.rmin);
-        float c = taylor_cos(th), sn = taylor_sin(th);
-        float cp = 1.0f;
-        for (int k = 0; k < 2 * I.zeta - 1; k++) cp *= c;
+        const float th = I.aw * (r - I.rmin);
+        const float c = taylor_cos(th), sn = taylor_sin(th);
+        float cp;                                   // c^(2 zeta - 1)
+        if (Z == 4) {
+            const float c2 = c * c, c4 = c2 * c2;
+            cp = c4 * c2 * c;
+        } else {
+            cp = 1.0f;
+            for (int k = 0; k < 2 * I.zeta - 1; k++) cp *= c;
+        }
         f = 0.0f;
         fp = 0.0f;
         g = -I.eps * cp * c;
-        gp = I.eps * (float)(2 * I.zeta) * cp * sn * w;
+        gp = I.eps2z_aw * cp * sn;
     }
-    float U = fmaf(g, phi, f);
-    float wx = fmaf(s0, njx - nix, fmaf(-njr, nix, -nir * njx));
-    float wy = fmaf(s0, njy - niy, fmaf(-njr, niy, -nir * njy));
-    float wz = fmaf(s0, njz - niz, fmaf(-njr, niz, -nir * njz));
-    float wr = fmaf(wx, hx, fmaf(wy, hy, wz * hz));
-    float radial = fmaf(gp, phi, fp);
-    float gm = g * I.mu;
-    float gmr = gm * rinv;
+    const float U = fmaf(g, phi, f);
+    const float wx = fmaf(s0, njx - nix, fmaf(-njr, nix, -nir * njx));
+    const float wy = fmaf(s0, njy - niy, fmaf(-njr, niy, -nir * njy));
+    const float wz = fmaf(s0, njz - niz, fmaf(-njr, niz, -nir * njz));
+    const float wr = fmaf(wx, hx, fmaf(wy, hy, wz * hz));
+    const float radial = fmaf(gp, phi, fp);
+    const float gm = g * I.mu;
+    const float gmr = gm * rinv;
     fx += -radial * hx - gmr * fmaf(-wr, hx, wx);
     fy += -radial * hy - gmr * fmaf(-wr, hy, wy);
     fz += -radial * hz - gmr * fmaf(-wr, hz, wz);
     // da/dn_i = n_j - (n_j.rh + s0) rh ; tau_i = -g mu (n_i x da/dn_i)
-    float js = njr + s0;
-    float gx = fmaf(-js, hx, njx), gy = fmaf(-js, hy, njy), gz = fmaf(-js, hz, njz);
+    const float js = njr + s0;
+    const float gx = fmaf(-js, hx, njx), gy = fmaf(-js, hy, njy), gz = fmaf(-js, hz, njz);
     tx += -gm * (niy * gz - niz * gy);
     ty += -gm * (niz * gx - nix * gz);
     tz += -gm * (nix * gy - niy * gx);
+    if (tj) {
+        // da/dn_j = n_i - (n_i.rh - s0) rh ; tau_j = -g mu (n_j x da/dn_j)
+        const float is = nir - s0;
+        const float ux = fmaf(-is, hx, nix), uy = fmaf(-is, hy, niy), uz = fmaf(-is, hz, niz);
+        tj[0] = -gm * (njy * uz - njz * uy);
+        tj[1] = -gm * (njz * ux - njx * uz);
+        tj[2] = -gm * (njx * uy - njy * ux);
+    }
     return U;
 }
 
 template <>
 __device__ inline double lipid_terms<double>(const Inst& I, double dx, double dy, double dz, double r2, double nix,
                                              double niy, double niz, double njx, double njy, double njz, double& fx,
-                                             double& fy, double& fz, double& tx, double& ty, double& tz) {
+                                             double& fy, double& fz, double& tx, double& ty, double& tz, double* tj) {
     double r = sqrt(r2);
     double hx = -dx / r, hy = -dy / r, hz = -dz / r;
     double s0 = I.s0_d;
@@ -163,6 +181,13 @@ __device__ inline double lipid_terms<double>(const Inst& I, double dx, double dy
     tx += -gm * (niy * gz - niz * gy);
     ty += -gm * (niz * gx - nix * gz);
     tz += -gm * (nix * gy - niy * gx);
+    if (tj) {
+        double is = nir - s0;
+        double ux = nix - is * hx, uy = niy - is * hy, uz = niz - is * hz;
+        tj[0] = -gm * (njy * uz - njz * uy);
+        tj[1] = -gm * (njz * ux - njx * uz);
+        tj[2] = -gm * (njx * uy - njy * ux);
+    }
     return U;
 }
 
@@ -184,38 +209,35 @@ __device__ inline T wca_terms(const Inst& I, bool pp, T dx, T dy, T dz, T r2, T&
 // ---------------------------------------------------------------- accumulators
 template <typename T> struct Acc;
 template <> struct Acc<float> {
-    // fast path: split int32 sums (|component| < 1000); wider values go to
-    // an int64 side array with atomics (exact, rare)
+    // fast path: split int32 sums (|component sum| < 1000); wider values go
+    // to an int64 side array with atomics (exact, rare)
     SplitAcc f[3], t[3];
     int nf, nt;
-    long long* big;   // [6][N]
-    size_t N;
-    int p;
     bool used_big;
     __device__ void zero() { for (int a = 0; a < 3; a++) { f[a].zero(); t[a].zero(); } nf = 0; nt = 0; used_big = false; }
-    __device__ void wide(int c, float x) {
-        atomicAdd((unsigned long long*)&big[(size_t)c * N + p], (unsigned long long)__float2ll_rn(x * 4294967296.0f));
+    __device__ void add3(const View& v, int p, SplitAcc* s, int& n, int c0, float x, float y, float z) {
+        if (fabsf(x) + fabsf(y) + fabsf(z) < 1000.0f) { s[0].add(x); s[1].add(y); s[2].add(z); n++; return; }
+        const size_t N = v.N;
+        atomicAdd((unsigned long long*)&v.Fbig[(size_t)c0 * N + p], (unsigned long long)__float2ll_rn(x * 4294967296.0f));
+        atomicAdd((unsigned long long*)&v.Fbig[(size_t)(c0 + 1) * N + p], (unsigned long long)__float2ll_rn(y * 4294967296.0f));
+        atomicAdd((unsigned long long*)&v.Fbig[(size_t)(c0 + 2) * N + p], (unsigned long long)__float2ll_rn(z * 4294967296.0f));
         used_big = true;
     }
-    __device__ void add3(SplitAcc* s, int& n, int c0, float x, float y, float z) {
-        if (fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z))) < 1000.0f) { s[0].add(x); s[1].add(y); s[2].add(z); n++; }
-        else { wide(c0, x); wide(c0 + 1, y); wide(c0 + 2, z); }
+    __device__ void add_pair(const View& v, int p, float fx, float fy, float fz, float tx, float ty, float tz) {
+        add3(v, p, f, nf, 0, fx, fy, fz);
+        add3(v, p, t, nt, 3, tx, ty, tz);
     }
-    __device__ void add_pair(float fx, float fy, float fz, float tx, float ty, float tz) {
-        add3(f, nf, 0, fx, fy, fz);
-        add3(t, nt, 3, tx, ty, tz);
-    }
-    __device__ void add_bond(float fx, float fy, float fz) { add3(f, nf, 0, fx, fy, fz); }
+    __device__ void add_bond(const View& v, int p, float fx, float fy, float fz) { add3(v, p, f, nf, 0, fx, fy, fz); }
 };
 template <> struct Acc<double> {
     long long f[3], t[3];
     int np, nb;
     __device__ void zero() { for (int a = 0; a < 3; a++) { f[a] = 0; t[a] = 0; } np = 0; nb = 0; }
     __device__ static long long q(double v) { return __double2ll_rn(v * 4294967296.0); }
-    __device__ void add_pair(double fx, double fy, double fz, double tx, double ty, double tz) {
+    __device__ void add_pair(const View&, int, double fx, double fy, double fz, double tx, double ty, double tz) {
         f[0] += q(fx); f[1] += q(fy); f[2] += q(fz); t[0] += q(tx); t[1] += q(ty); t[2] += q(tz); np++;
     }
-    __device__ void add_bond(double fx, double fy, double fz) { f[0] += q(fx); f[1] += q(fy); f[2] += q(fz); nb++; }
+    __device__ void add_bond(const View&, int, double fx, double fy, double fz) { f[0] += q(fx); f[1] += q(fy); f[2] += q(fz); nb++; }
     __device__ long long F(int a) const { return f[a]; }
     __device__ long long Tq(int a) const { return t[a]; }
 };
@@ -286,19 +308,48 @@ struct NbrInfo {
     float fx, fy, fz;
 };
 
-template <typename T, bool ENERGY, bool DUMP>
-__global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __restrict__ energy /* [B][8] */,
-                                                         unsigned* __restrict__ dump, unsigned long long* __restrict__ dump_count,
-                                                         long long dump_cap) {
-    __shared__ alignas(16) int4 sq[kStageCap];
-    __shared__ alignas(16) float4 so[kStageCap];
-    __shared__ alignas(16) float4 sy[kStageCap];
+template <typename T>
+__device__ inline T lipid_dispatch(const Inst& I, T dx, T dy, T dz, T r2, T nix, T niy, T niz, T njx, T njy, T njz,
+                                   T& fx, T& fy, T& fz, T& tx, T& ty, T& tz, int zc, T* tj) {
+    if constexpr (sizeof(T) == 4) {
+        if (zc == 4) return lipid_terms_f<4>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz, tj);
+        return lipid_terms_f<0>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz, tj);
+    } else {
+        return lipid_terms<double>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz, tj);
+    }
+}
+
+// reaction of a pair on j (Newton's third law inside the CTA's own cell):
+// exact split integers added to the shared accumulators of j
+__device__ inline void split_parts(float f, int& h, int& l) {
+    const float t = fmaf(f, 4096.0f, kMagic);
+    const float hf = t - kMagic;
+    const float r = fmaf(f, 4096.0f, -hf);
+    const float u = fmaf(r, 1048576.0f, kMagic);
+    h = __float_as_int(t) - kMagicBits;
+    l = __float_as_int(u) - kMagicBits;
+}
+
+template <typename T, bool ENERGY, bool DUMP, int Z>
+__global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __restrict__ energy /* [B][8] */,
+                                                            unsigned* __restrict__ dump,
+                                                            unsigned long long* __restrict__ dump_count,
+                                                            long long dump_cap) {
+    // sy: staged mirrors as copied by TMA (int4: x - c at 2^-26 sigma, type)
+    // sY: the same particles in the cell-k frame (float4), counting-sorted by
+    //     spatial bin; w = type | block << 8 | staged index << 14
+    __shared__ alignas(16) int4 sy[kStageCap];
+    __shared__ alignas(16) float4 sY[kStageCap];
+    __shared__ alignas(16) float4 so[kStageCap];     // director, w = global slot
+    __shared__ int bstart[kMaxBins + 1];
+    __shared__ int rx[kPairThreads][12];               // Newton-3 reactions on the own cell (split ints)
     // hit queues during the pair loop; split-combination buffer afterwards
-    __shared__ alignas(16) unsigned char scratch[kPairThreads / 32 * kQCap * 32 * 4];
+    __shared__ alignas(16) unsigned char scratch[kPairThreads / 32 * kQCap * 32 * 2];
     __shared__ NbrInfo nb[kMaxNbr];
     __shared__ unsigned long long bar;
-    __shared__ int s_nstage, s_next, s_next_off, s_self, s_self_lo, s_self_hi;
-    unsigned (*qbuf)[kQCap][32] = reinterpret_cast<unsigned (*)[kQCap][32]>(scratch);
+    __shared__ int s_nstage, s_next, s_next_off, s_self, s_self_lo, s_self_hi, s_dim[3];
+    __shared__ float s_lo[3], s_binv;
+    unsigned short (*qbuf)[kQCap][32] = reinterpret_cast<unsigned short (*)[kQCap][32]>(scratch);
 
     const int k = blockIdx.x;
     const int b = find_inst(v.inst_k0, v.B, k);
@@ -314,7 +365,10 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
     const float ll_lo = (rcl - kCutBand) * (rcl - kCutBand), ll_hi = (rcl + kCutBand) * (rcl + kCutBand);
     const float w_lo = (rcw - kCutBand) * (rcw - kCutBand), w_hi = (rcw + kCutBand) * (rcw + kCutBand);
     const float p_lo = (rcp - kCutBand) * (rcp - kCutBand), p_hi = (rcp + kCutBand) * (rcp + kCutBand);
+    const float rmargin = (float)(2.0 * I.skin) + 1e-3f;   // particles lie within R_l (+ skin) of their centroid
     const size_t N = v.N;
+    const int zc = (Z > 0) ? Z : I.zeta;
+    const int nk = ce - cs;
     unsigned phase = 0;
     if (tid == 0) mbar_init(&bar, 1);
     __syncthreads();
@@ -329,6 +383,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
         const int li = igrp * 32 + lane;
         const bool ivalid = wactive && li < nti;
         const int pi = it0 + li;
+        const bool whole_cell = (it0 == cs) && (nti == nk);   // Newton-3 possible inside the own cell
         int4 qi = make_int4(0, 0, 0, 0);
         float4 oi = make_float4(0, 0, 0, 0);
         float yix = 0, yiy = 0, yiz = 0;
@@ -339,22 +394,41 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
             yix = qi.x * kMirrorUnit; yiy = qi.y * kMirrorUnit; yiz = qi.z * kMirrorUnit;
             if (DUMP) idi = v.id[pi];
         }
+        for (int q = tid; q < kPairThreads * 12; q += kPairThreads) (&rx[0][0])[q] = 0;
         const int ti = qi.w & 0xff;
         Acc<T> acc;
         acc.zero();
-        if constexpr (sizeof(T) == 4) { acc.big = v.Fbig; acc.N = N; acc.p = pi; }
         T up = 0, vir = 0;
 
         // passes over chunks of neighbouring cells (a cell larger than the
         // stage is split across passes)
         for (int na = a0, na_off = 0; na < a1;) {
             __syncthreads();
-            if (tid == 0) {
-                int tot = 0, m = 0, nn = na, off = na_off, sb = 0, slo = -1, shi = -1;
-                while (nn < a1 && m < kMaxNbr && tot < kStageCap) {
-                    const int l = v.adj[nn];
-                    const int s = v.cell_start[l], c = v.cell_start[l + 1] - s;
-                    const int take = min(c - off, kStageCap - tot);
+            if (warp == 0) {
+                // one lane per neighbouring cell: counts, offsets, staging slots
+                const int nn = na + lane;
+                const bool has = nn < a1 && lane < kMaxNbr;
+                int l = 0, st = 0, c = 0;
+                if (has) {
+                    l = v.adj[nn];
+                    st = v.cell_start[l];
+                    c = v.cell_start[l + 1] - st;
+                    if (lane == 0) { st += na_off; c -= na_off; }
+                }
+                int incl = c;
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, incl, off);
+                    if (lane >= off) incl += t;
+                }
+                const int excl = incl - c;
+                const bool fits = has && incl <= kStageCap;
+                const bool part = has && excl < kStageCap && incl > kStageCap;
+                const unsigned fm = __ballot_sync(0xffffffffu, fits), pm = __ballot_sync(0xffffffffu, part);
+                const int m = __popc(fm) + (pm ? 1 : 0);
+                const bool staged = fits || part;
+                const int take = part ? kStageCap - excl : c;
+                float blo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, bhi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+                if (staged) {
                     long long dx = minimg_q(v.cq[l] - ckx, I.boxq[0], I.periodic[0]);
                     long long dy = minimg_q(v.cq[(size_t)v.Ktot + l] - cky, I.boxq[1], I.periodic[1]);
                     long long dz = minimg_q(v.cq[(size_t)2 * v.Ktot + l] - ckz, I.boxq[2], I.periodic[2]);
@@ -362,39 +436,85 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
                     long long oy = (dy + (1ll << (kMirrorShift - 1))) >> kMirrorShift;
                     long long oz = (dz + (1ll << (kMirrorShift - 1))) >> kMirrorShift;
                     NbrInfo inf;
-                    inf.base = tot; inf.cnt = take; inf.start = s + off;
+                    inf.base = excl; inf.cnt = take; inf.start = st;
                     inf.ox = (int)(unsigned)(unsigned long long)ox;
                     inf.oy = (int)(unsigned)(unsigned long long)oy;
                     inf.oz = (int)(unsigned)(unsigned long long)oz;
                     inf.fx = (float)ox * kMirrorUnit; inf.fy = (float)oy * kMirrorUnit; inf.fz = (float)oz * kMirrorUnit;
-                    if (l == k) { sb = tot - off; slo = tot; shi = tot + take; }
-                    nb[m] = inf;
-                    tot += take;
-                    m++;
-                    if (take < c - off) { off += take; break; }   // rest of this cell in the next pass
-                    nn++;
-                    off = 0;
+                    nb[lane] = inf;
+                    const float Rl = (float)v.R[l] + rmargin;
+                    blo[0] = inf.fx - Rl; blo[1] = inf.fy - Rl; blo[2] = inf.fz - Rl;
+                    bhi[0] = inf.fx + Rl; bhi[1] = inf.fy + Rl; bhi[2] = inf.fz + Rl;
                 }
-                s_nstage = m;
-                s_next = nn;
-                s_next_off = off;
-                s_self = sb; s_self_lo = slo; s_self_hi = shi;
+                const unsigned selfm = __ballot_sync(0xffffffffu, staged && l == k);
+                for (int a = 0; a < 3; a++)
+                    for (int off = 16; off; off >>= 1) {
+                        blo[a] = fminf(blo[a], __shfl_xor_sync(0xffffffffu, blo[a], off));
+                        bhi[a] = fmaxf(bhi[a], __shfl_xor_sync(0xffffffffu, bhi[a], off));
+                    }
+                const int total = __shfl_sync(0xffffffffu, excl + take, max(m - 1, 0));
+                // where the next pass starts: after the last fully staged
+                // neighbour, or inside the partially staged one
+                int nxt = na + __popc(fm), nxo = 0;
+                if (pm) {
+                    const int p = __ffs(pm) - 1;
+                    const int ex_p = __shfl_sync(0xffffffffu, excl, p);
+                    nxt = na + p;
+                    nxo = (p == 0 ? na_off : 0) + (kStageCap - ex_p);
+                }
+                // staged range of the own cell, and where its first particle would sit
+                int slo = -1, shi = -1, sb = 0;
+                {
+                    const int p = selfm ? __ffs(selfm) - 1 : 0;
+                    const int ex_p = __shfl_sync(0xffffffffu, excl, p);
+                    const int tk_p = __shfl_sync(0xffffffffu, take, p);
+                    if (selfm) {
+                        slo = ex_p;
+                        shi = ex_p + tk_p;
+                        sb = ex_p - ((p == 0) ? na_off : 0);
+                    }
+                }
+                if (lane == 0) {
+                    s_nstage = m;
+                    s_next = nxt;
+                    s_next_off = nxo;
+                    s_self = sb; s_self_lo = slo; s_self_hi = shi;
+                    float bsz = rs_b * 1.0001f;
+                    int dim[3] = {1, 1, 1};
+                    if (m > 0) {
+                        for (int tries = 0; tries < 40; tries++) {
+                            long long prod = 1;
+                            for (int a = 0; a < 3; a++) {
+                                dim[a] = max(1, min(kMaxBins, (int)floorf((bhi[a] - blo[a]) / bsz) + 1));
+                                prod *= dim[a];
+                            }
+                            if (prod <= kMaxBins) break;
+                            bsz *= 1.25f;
+                        }
+                    }
+                    for (int a = 0; a < 3; a++) { s_lo[a] = blo[a]; s_dim[a] = dim[a]; }
+                    s_binv = 1.0f / bsz;
+                }
                 if (m > 0) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    mbar_expect_tx(&bar, (unsigned)tot * 32u);
-                    for (int q = 0; q < m; q++)
-                        if (nb[q].cnt > 0) {
-                            bulk_g2s(&sq[nb[q].base], v.mq + nb[q].start, nb[q].cnt * 16u, &bar);
-                            bulk_g2s(&so[nb[q].base], v.mo + nb[q].start, nb[q].cnt * 16u, &bar);
-                        }
+                    if (lane == 0) mbar_expect_tx(&bar, (unsigned)total * 32u);
+                    __syncwarp();
+                    if (staged && take > 0) {
+                        bulk_g2s(&sy[excl], v.mq + st, take * 16u, &bar);
+                        bulk_g2s(&so[excl], v.mo + st, take * 16u, &bar);
+                    }
                 }
             }
+            for (int q = tid; q <= kMaxBins; q += kPairThreads) bstart[q] = 0;
             __syncthreads();
             const int m = s_nstage;
             const int next = s_next, next_off = s_next_off;
-            int selfj = (s_self_lo >= 0 && ivalid) ? s_self + (pi - cs) : -1;
-            if (selfj < s_self_lo || selfj >= s_self_hi) selfj = -1;
             if (m == 0) { na = next; na_off = next_off; continue; }
+            const int sself = s_self, sslo = s_self_lo, sshi = s_self_hi;
+            // Newton-3 inside the own cell when the whole cell is staged and in this i-tile
+            const bool n3 = sizeof(T) == 4 && whole_cell && sslo >= 0 && (sshi - sslo) == nk;
+            int selfj = (sslo >= 0 && ivalid) ? sself + (pi - cs) : -1;
+            if (selfj < sslo || selfj >= sshi) selfj = -1;
             bool ok = mbar_wait_bounded(&bar, phase, v.status);
             if (__syncthreads_or(!ok)) {
                 // give the copies in flight a second bounded wait, then leave
@@ -402,55 +522,91 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
                 return;
             }
             phase ^= 1u;
-            // move the staged mirrors into this cell's frame
-            const int total = nb[m - 1].base + nb[m - 1].cnt;
+            const float blo0 = s_lo[0], blo1 = s_lo[1], blo2 = s_lo[2], binv = s_binv;
+            const int dim0 = s_dim[0], dim1 = s_dim[1], dim2 = s_dim[2];
+
+            // ---- in-CTA counting sort of the staged particles by spatial bin
             for (int q = 0; q < m; q++) {
                 const NbrInfo inf = nb[q];
                 for (int j = inf.base + tid; j < inf.base + inf.cnt; j += kPairThreads) {
-                    int4 s = sq[j];
+                    const int4 r = sy[j];
+                    const float y0 = fmaf((float)r.x, kMirrorUnit, inf.fx), y1 = fmaf((float)r.y, kMirrorUnit, inf.fy),
+                                y2 = fmaf((float)r.z, kMirrorUnit, inf.fz);
+                    const int bx = min(dim0 - 1, max(0, (int)floorf((y0 - blo0) * binv)));
+                    const int by = min(dim1 - 1, max(0, (int)floorf((y1 - blo1) * binv)));
+                    const int bz = min(dim2 - 1, max(0, (int)floorf((y2 - blo2) * binv)));
+                    const int bi = (bz * dim1 + by) * dim0 + bx;
+                    // type | rank in bin << 8 | bin << 18, kept in the staged record
+                    sy[j].w = (r.w & 0xff) | (atomicAdd(&bstart[bi], 1) << 8) | (bi << 18);
+                }
+            }
+            __syncthreads();
+            if (warp == 0) {
+                const int nbins = dim0 * dim1 * dim2;
+                int carry = 0;
+                for (int c0 = 0; c0 < nbins; c0 += 32) {
+                    const int x = (c0 + lane < nbins) ? bstart[c0 + lane] : 0;
+                    int incl = x;
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const int t = __shfl_up_sync(0xffffffffu, incl, off);
+                        if (lane >= off) incl += t;
+                    }
+                    if (c0 + lane < nbins) bstart[c0 + lane] = carry + incl - x;
+                    carry += __shfl_sync(0xffffffffu, incl, 31);
+                }
+                if (lane == 0) bstart[nbins] = carry;
+            }
+            __syncthreads();
+            for (int q = 0; q < m; q++) {
+                const NbrInfo inf = nb[q];
+                for (int j = inf.base + tid; j < inf.base + inf.cnt; j += kPairThreads) {
+                    const int4 r = sy[j];
                     float4 y;
-                    y.x = fmaf((float)s.x, kMirrorUnit, inf.fx);
-                    y.y = fmaf((float)s.y, kMirrorUnit, inf.fy);
-                    y.z = fmaf((float)s.z, kMirrorUnit, inf.fz);
-                    y.w = __int_as_float(s.w);
-                    s.x = (int)((unsigned)s.x + (unsigned)inf.ox);
-                    s.y = (int)((unsigned)s.y + (unsigned)inf.oy);
-                    s.z = (int)((unsigned)s.z + (unsigned)inf.oz);
-                    sq[j] = s;
-                    sy[j] = y;
+                    y.x = fmaf((float)r.x, kMirrorUnit, inf.fx);
+                    y.y = fmaf((float)r.y, kMirrorUnit, inf.fy);
+                    y.z = fmaf((float)r.z, kMirrorUnit, inf.fz);
+                    y.w = __int_as_float((r.w & 0xff) | (q << 8) | (j << 14));
+                    sY[bstart[r.w >> 18] + ((r.w >> 8) & 0x3ff)] = y;
                 }
             }
             __syncthreads();
 
-            // filter + evaluate
+            // filter (the 27 bins around i) + evaluate
             if (wactive) {
-                const int jb = (total * jsplit) / nsplit, je = (total * (jsplit + 1)) / nsplit;
+                const int ibx = min(dim0 - 1, max(0, (int)floorf((yix - blo0) * binv)));
+                const int iby = min(dim1 - 1, max(0, (int)floorf((yiy - blo1) * binv)));
+                const int ibz = min(dim2 - 1, max(0, (int)floorf((yiz - blo2) * binv)));
+                // candidates of the own cell: with Newton-3 only those after i
+                const int jlo_self = n3 ? selfj + 1 : -1;
                 int qn = 0;
                 auto flush = [&]() {
                     int qmax = qn;
                     for (int off = 16; off; off >>= 1) qmax = max(qmax, __shfl_xor_sync(0xffffffffu, qmax, off));
                     for (int t = 0; t < qmax; t++) {
                         if (t >= qn) continue;
-                        const int j = (int)qbuf[warp][t][lane];
-                        const int4 sj = sq[j];
-                        const int tj = sj.w & 0xff;
+                        const int sp = (int)qbuf[warp][t][lane];
+                        const int wbits = __float_as_int(sY[sp].w);
+                        const int tj = wbits & 0xff, qb = (wbits >> 8) & 0x3f, j = wbits >> 14;
+                        const float4 oj = so[j];
+                        const int pj = __float_as_int(oj.w);
+                        const int4 mj = sy[j];
                         const bool ll = (ti == kLipid) && (tj == kLipid);
                         const int cls = ll ? 0 : ((ti == kLipid || tj == kLipid) ? 1 : 2);
-                        const int dxq = (int)((unsigned)sj.x - (unsigned)qi.x);
-                        const int dyq = (int)((unsigned)sj.y - (unsigned)qi.y);
-                        const int dzq = (int)((unsigned)sj.z - (unsigned)qi.z);
+                        const int dxq = (int)((unsigned)mj.x + (unsigned)nb[qb].ox - (unsigned)qi.x);
+                        const int dyq = (int)((unsigned)mj.y + (unsigned)nb[qb].oy - (unsigned)qi.y);
+                        const int dzq = (int)((unsigned)mj.z + (unsigned)nb[qb].oz - (unsigned)qi.z);
                         const float dxf = (float)dxq * kMirrorUnit, dyf = (float)dyq * kMirrorUnit, dzf = (float)dzq * kMirrorUnit;
                         const float r2f = fmaf(dxf, dxf, fmaf(dyf, dyf, dzf * dzf));
                         const float lo = cls == 0 ? ll_lo : (cls == 1 ? w_lo : p_lo);
                         const float hi = cls == 0 ? ll_hi : (cls == 1 ? w_hi : p_hi);
                         if (r2f >= hi) continue;
-                        const float4 oj = so[j];
-                        const int pj = __float_as_int(oj.w);
                         bool in = r2f < lo;
                         if (!in) in = exact_inside(v, I, pi, pj, cls);
                         if (in && cls == 2 && is_excluded(v, I, v.id[pi], v.id[pj])) in = false;
                         if (!in) continue;
+                        const bool react = n3 && j >= sslo && j < sshi;   // j in the own cell: reaction here
                         T fx = 0, fy = 0, fz = 0, tx = 0, ty = 0, tz = 0, U;
+                        T tjv[3] = {0, 0, 0};
                         T dx, dy, dz, r2;
                         if constexpr (sizeof(T) == 4) {
                             dx = dxf; dy = dyf; dz = dzf; r2 = r2f;
@@ -470,37 +626,81 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
                                 njx = grid_to_double(v.nq[pj]); njy = grid_to_double(v.nq[N + pj]);
                                 njz = grid_to_double(v.nq[2 * N + pj]);
                             }
-                            U = lipid_terms<T>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz);
+                            U = lipid_dispatch<T>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz, zc,
+                                                  react ? tjv : (T*)nullptr);
                         } else {
                             U = wca_terms<T>(I, cls == 2, dx, dy, dz, r2, fx, fy, fz);
                         }
-                        if (!(fabsf(fx) + fabsf(fy) + fabsf(fz) + fabsf(tx) + fabsf(ty) + fabsf(tz) < (T)3.0e30))
+                        if (!(fabs(fx) + fabs(fy) + fabs(fz) + fabs(tx) + fabs(ty) + fabs(tz) < (T)3.0e30))
                             atomicOr(v.status, kStatusNaN);
-                        acc.add_pair(fx, fy, fz, tx, ty, tz);
+                        acc.add_pair(v, pi, fx, fy, fz, tx, ty, tz);
+                        if constexpr (sizeof(T) == 4) {
+                            if (react) {
+                                // reaction on j (same cell, same i-tile): -F and tau_j
+                                const int lj = j - sself;
+                                const float fv[6] = {-(float)fx, -(float)fy, -(float)fz,
+                                                     (float)tjv[0], (float)tjv[1], (float)tjv[2]};
+                                for (int h3 = 0; h3 < 2; h3++) {
+                                    const float* w3 = fv + 3 * h3;
+                                    if (fabsf(w3[0]) + fabsf(w3[1]) + fabsf(w3[2]) < 1000.0f) {
+                                        for (int a = 0; a < 3; a++) {
+                                            int hh, ll2;
+                                            split_parts(w3[a], hh, ll2);
+                                            atomicAdd(&rx[lj][6 * h3 + 2 * a], hh);
+                                            atomicAdd(&rx[lj][6 * h3 + 2 * a + 1], ll2);
+                                        }
+                                    } else {
+                                        for (int a = 0; a < 3; a++)
+                                            atomicAdd((unsigned long long*)&v.Fbig[(size_t)(3 * h3 + a) * N + pj],
+                                                      (unsigned long long)__float2ll_rn(w3[a] * 4294967296.0f));
+                                        acc.used_big = true;
+                                    }
+                                }
+                            }
+                        }
                         if (ENERGY) {
-                            up += (T)0.5 * U;
-                            vir += (T)0.5 * -(dx * fx + dy * fy + dz * fz);
+                            const T wgt = react ? (T)1 : (T)0.5;
+                            up += wgt * U;
+                            vir += wgt * -(dx * fx + dy * fy + dz * fz);
                         }
                         if (DUMP) {
-                            unsigned idj = v.id[pj];
-                            if (idi < idj) {
+                            const unsigned idj = v.id[pj];
+                            if (idi < idj || react) {
+                                const unsigned a_ = min(idi, idj), b_ = max(idi, idj);
                                 unsigned long long slot = atomicAdd(dump_count, 1ull);
-                                if ((long long)slot < dump_cap) { dump[2 * slot] = idi; dump[2 * slot + 1] = idj; }
+                                if ((long long)slot < dump_cap) { dump[2 * slot] = a_; dump[2 * slot + 1] = b_; }
                             }
                         }
                     }
                     qn = 0;
                     __syncwarp();
                 };
-                for (int j0 = jb; j0 < je; j0 += 8) {
-                    const int jend = min(j0 + 8, je);
-                    for (int j = j0; j < jend; j++) {
-                        const float4 y = sy[j];
-                        const float ex = y.x - yix, ey = y.y - yiy, ez = y.z - yiz;
-                        const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                        if (ivalid && d2 < rs2f && j != selfj) { qbuf[warp][qn][lane] = (unsigned)j; qn++; }
+                // the 27 neighbouring bins, interleaved across the warps sharing
+                // this i-group; a bin is scanned at most 8 candidates per lane
+                // between warp-uniform queue checks
+                for (int o = jsplit; o < 27; o += nsplit) {
+                    const int bx = ibx + (o % 3) - 1, by = iby + ((o / 3) % 3) - 1, bz = ibz + (o / 9) - 1;
+                    int sp = 0, e = 0;
+                    if (ivalid && bx >= 0 && by >= 0 && bz >= 0 && bx < dim0 && by < dim1 && bz < dim2) {
+                        const int bi = (bz * dim1 + by) * dim0 + bx;
+                        sp = bstart[bi];
+                        e = bstart[bi + 1];
                     }
-                    if (__any_sync(0xffffffffu, qn > kQCap - 8)) flush();
+                    while (__any_sync(0xffffffffu, sp < e)) {
+                        if (__any_sync(0xffffffffu, qn > kQCap - 8)) flush();
+#pragma unroll 4
+                        for (int u = 0; u < 8; u++) {
+                            if (sp >= e) break;
+                            const float4 y = sY[sp];
+                            const float ex = y.x - yix, ey = y.y - yiy, ez = y.z - yiz;
+                            const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                            const int jj = __float_as_int(y.w) >> 14;
+                            const bool self_block = jj >= sslo && jj < sshi;
+                            const bool keep = self_block ? (n3 ? jj >= jlo_self : jj != selfj) : true;
+                            if (d2 < rs2f && keep) { qbuf[warp][qn][lane] = (unsigned short)sp; qn++; }
+                            sp++;
+                        }
+                    }
                 }
                 flush();
             }
@@ -530,7 +730,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
                 const T r = sqrt(dx * dx + dy * dy + dz * dz);
                 const T dr = r - r0;
                 const T c = kb * dr / r;
-                acc.add_bond(c * dx, c * dy, c * dz);
+                acc.add_bond(v, pi, c * dx, c * dy, c * dz);
                 if (ENERGY) {
                     ub += (T)0.25 * kb * dr * dr;
                     vir += (T)0.5 * -(c * (dx * dx + dy * dy + dz * dz));
@@ -538,10 +738,10 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
             }
         }
 
-        // combine the j-splits (exact integer sums) and write
+        // combine the j-splits and the Newton-3 reactions (exact integer sums) and write
         __syncthreads();
         if constexpr (sizeof(T) == 4) {
-            int (*red)[14] = reinterpret_cast<int (*)[14]>(scratch);
+            int (*red)[14] = reinterpret_cast<int (*)[14]>(&sY[0]);
             for (int q = tid; q < kPairThreads * 14; q += kPairThreads) (&red[0][0])[q] = 0;
             __syncthreads();
             if (ivalid) {
@@ -553,7 +753,6 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
                 atomicAdd(&red[li][10], acc.t[2].h); atomicAdd(&red[li][11], acc.t[2].l);
                 atomicAdd(&red[li][12], acc.nf); atomicAdd(&red[li][13], acc.nt);
             }
-            __syncthreads();
             const bool any_big = __syncthreads_or(ivalid && acc.used_big);
             if (tid < nti) {
                 const int nfr = red[tid][12], ntr = red[tid][13];
@@ -561,9 +760,12 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
                 for (int a = 0; a < 3; a++) {
                     SplitAcc f; f.h = red[tid][2 * a]; f.l = red[tid][2 * a + 1];
                     SplitAcc t; t.h = red[tid][6 + 2 * a]; t.l = red[tid][6 + 2 * a + 1];
-                    long long fb = 0, tb = 0;
+                    long long fb = ((long long)rx[tid][2 * a] << 20) + (long long)rx[tid][2 * a + 1];
+                    long long tb = ((long long)rx[tid][6 + 2 * a] << 20) + (long long)rx[tid][6 + 2 * a + 1];
                     if (any_big) {
-                        fb = v.Fbig[(size_t)a * N + p]; tb = v.Fbig[(size_t)(3 + a) * N + p];
+                        // written by atomics in L2: read past L1
+                        fb += __ldcg(&v.Fbig[(size_t)a * N + p]);
+                        tb += __ldcg(&v.Fbig[(size_t)(3 + a) * N + p]);
                         v.Fbig[(size_t)a * N + p] = 0; v.Fbig[(size_t)(3 + a) * N + p] = 0;
                     }
                     v.F[a * N + p] = f.finish(nfr) + fb;
@@ -571,7 +773,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
                 }
             }
         } else {
-            long long (*red64)[6] = reinterpret_cast<long long (*)[6]>(scratch);
+            long long (*red64)[6] = reinterpret_cast<long long (*)[6]>(&sY[0]);
             for (int q = tid; q < kPairThreads * 6; q += kPairThreads) (&red64[0][0])[q] = 0;
             __syncthreads();
             if (ivalid)
@@ -609,17 +811,43 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(View v, long long* __res
 }
 
 // ---------------------------------------------------------------- host launchers
+// The pair kernel runs five CTAs per SM only with the whole unified L1 /
+// shared memory given to shared memory; ask for that once per process.
+template <typename Kern> static void prefer_shared(Kern k) {
+    CK(cudaFuncSetAttribute((const void*)k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                            (int)cudaSharedmemCarveoutMaxShared));
+}
+static void prefer_shared_all() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        prefer_shared(k_pairs<float, false, true, 0>);
+        prefer_shared(k_pairs<float, true, false, 4>);
+        prefer_shared(k_pairs<float, true, false, 0>);
+        prefer_shared(k_pairs<float, false, false, 4>);
+        prefer_shared(k_pairs<float, false, false, 0>);
+        prefer_shared(k_pairs<double, false, true, 0>);
+        prefer_shared(k_pairs<double, true, false, 0>);
+        prefer_shared(k_pairs<double, false, false, 0>);
+    });
+}
+
 void Ensemble::launch_pairs(bool energies, bool dump) {
     View v = view();
     if (energies) CK(cudaMemsetAsync(d_energy, 0, sizeof(long long) * 8 * B, stream));
+    bool z4 = true;
+    for (auto& I : inst_h) z4 = z4 && I.zeta == 4;
+    const dim3 g(Ktot), t(kPairThreads);
+    prefer_shared_all();
     if (precision == 0) {
-        if (dump) k_pairs<float, false, true><<<Ktot, kPairThreads, 0, stream>>>(v, d_energy, d_dump, d_dump_count, dump_cap);
-        else if (energies) k_pairs<float, true, false><<<Ktot, kPairThreads, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
-        else k_pairs<float, false, false><<<Ktot, kPairThreads, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
+        if (dump) k_pairs<float, false, true, 0><<<g, t, 0, stream>>>(v, d_energy, d_dump, d_dump_count, dump_cap);
+        else if (energies && z4) k_pairs<float, true, false, 4><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
+        else if (energies) k_pairs<float, true, false, 0><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
+        else if (z4) k_pairs<float, false, false, 4><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
+        else k_pairs<float, false, false, 0><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
     } else {
-        if (dump) k_pairs<double, false, true><<<Ktot, kPairThreads, 0, stream>>>(v, d_energy, d_dump, d_dump_count, dump_cap);
-        else if (energies) k_pairs<double, true, false><<<Ktot, kPairThreads, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
-        else k_pairs<double, false, false><<<Ktot, kPairThreads, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
+        if (dump) k_pairs<double, false, true, 0><<<g, t, 0, stream>>>(v, d_energy, d_dump, d_dump_count, dump_cap);
+        else if (energies) k_pairs<double, true, false, 0><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
+        else k_pairs<double, false, false, 0><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
     }
     launches++;
     CK(cudaGetLastError());

@@ -51,6 +51,7 @@ struct Inst {
     double rc2_ll, rc2_wca, rc2_pp;   // FP64 squared type-pair cutoffs (inclusion decision)
     double rs, skin;            // search cutoff and skin
     float rc2f_ll, rc2f_wca, rc2f_pp, rsf;
+    float aw, eps2z_aw;         // (pi/2)/(rc - rmin) and eps 2 zeta aw
     // integrator (host-computed constants)
     float h_m, h_i;             // dt/2/m, dt/2/I
     float hdt;                  // dt/2
