@@ -7,7 +7,7 @@ B-A-O-A update, Voronoi rebuild (M-step, Morton relabel, E-step, stable sort,
 radii, neighbouring cells), pair + bond forces, final B.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload rbc-4m|vesicle-62k|patch-2304] [--precision f32|f64]
+                    [--workload rbc-4m|rbc-1m|vesicle-62k|patch-2304] [--precision f32|f64]
 
 --impl reference times the FP64 CPU oracle on this machine's host cores on a
 bounded sample of the same workload.  Under torchrun (N > 1) every rank runs
@@ -44,6 +44,9 @@ def workload(name: str):
     from synth import membranes as M
     if name == "rbc-4m":
         return M.rbc_4m()
+    if name == "rbc-1m":
+        # the same biconcave cell at a quarter of the particles (profiling captures)
+        return M.biconcave(n_lipids=892_756, n_junctions=8_250, n_centroids=16_384, seed=2, name="rbc-1m")
     if name == "vesicle-62k":
         return M.vesicle_62k()
     if name == "patch-2304":
@@ -132,6 +135,21 @@ def algorithmic_work(g, mem):
     return npairs, cand
 
 
+def pairs_traffic(n_particles: int):
+    """DRAM bytes per pair-kernel launch, from the committed ncu summary of
+    the same kernel revision: bytes per particle measured on the 1M-particle
+    cell, scaled by the particles one launch processes.  None when the
+    summary belongs to another revision of the kernel."""
+    import re
+    path = os.path.join(ROOT, "profiles", "k_pairs_rbc-1m_full.md")
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"^traffic_bytes_per_particle:\s*([0-9.eE+]+)\s*\(kernel (\S+)\)", open(path).read(), re.M)
+    if not m or m.group(2) != KERNEL_REV:
+        return None
+    return round(float(m.group(1)) * n_particles)
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -178,15 +196,7 @@ def run_ours(args, rank, world):
     pair_ms = pk["ms"] / max(pk["launches"], 1)
     peak_tflops = SM_COUNT * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
     achieved = flops / (pair_ms * 1e-3) / 1e12
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "pairs_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            tr = json.load(open(tpath))
-            if tr.get("workload") == args.workload and tr.get("kernel_rev") == KERNEL_REV:
-                traffic = tr["bytes_per_launch"]
-        except Exception:
-            traffic = None
+    traffic = pairs_traffic(mem.n)
     roof = {"bound": "alu", "kernel": "k_pairs", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
             "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": traffic,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
@@ -288,7 +298,7 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-KERNEL_REV = "pairs-v1"
+KERNEL_REV = "pairs-v4"
 
 
 def main():
