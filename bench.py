@@ -229,6 +229,9 @@ def run_ours(args, rank, world):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(mem, budget_s=args.cpu_budget)
+    ens = None
+    if rank == 0 and world == 1 and not args.no_ensemble and args.workload == "rbc-4m":
+        ens = run_ensemble(steps=args.ensemble_steps, budget_gb=args.budget_gb)
 
     line = {"metric": METRIC if args.workload == "rbc-4m" else f"particle-steps/s at {args.workload}",
             "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -240,7 +243,7 @@ def run_ours(args, rank, world):
                        "rebuild_every": 1, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (state and mirrors ~0.9 GB)"},
             "roofline": roof, "kernel_ms_per_launch": breakdown, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clocks.summary()}
+            "gpu_launches": launches, "clocks": clocks.summary(), "ensemble": ens}
     return line
 
 
@@ -301,6 +304,78 @@ def run_reference(args, rank, world):
 KERNEL_REV = "pairs-v4"
 
 
+def ensemble_jobs(n_instances: int, steps: int):
+    """The uneven ensemble: patches and vesicles, N log-uniform in [5k, 200k],
+    kT in [0.1, 0.3], seed 3000 + i; all submitted at once."""
+    import paper_1701_02059_gb300 as G
+    from synth import membranes as M
+    jobs = []
+    for i in range(n_instances):
+        m = M.ensemble_member(i)
+        p = G.make_params(kT=m.kT, n_centroids=m.n_centroids, box=m.box, periodic=m.periodic, seed=3000 + i,
+                          instance=i)
+        jobs.append({"params": p, "mem": m, "steps": steps, "arrival_s": 0.0})
+    return jobs
+
+
+def run_ensemble(n_instances=64, steps=500, budget_gb=120.0, max_steps=500):
+    """Batched arena against one-instance-per-launch on the same GPU."""
+    import torch
+    from paper_1701_02059_gb300 import serving
+    jobs = ensemble_jobs(n_instances, steps)
+    torch.cuda.synchronize()
+    _, sb, _ = serving.serve_batched(jobs, int(budget_gb * 2**30), max_steps=max_steps)
+    _, sp, _ = serving.serve_plain(jobs)
+    keep = ("p50_s", "p99_s", "makespan_s", "particle_steps_per_s")
+    return {"instances": n_instances, "steps": steps, "particles": sum(j["mem"].n for j in jobs),
+            "batched": {k: round(sb[k], 4) for k in keep} | {"gpu_launches": sb["gpu_launches"]},
+            "plain": {k: round(sp[k], 4) for k in keep},
+            "p99_speedup": round(sp["p99_s"] / sb["p99_s"], 3),
+            "throughput_speedup": round(sb["particle_steps_per_s"] / sp["particle_steps_per_s"], 3),
+            "timing": "wall clock from submission to retirement, host arrays in and out (set-up, k-means "
+                      "initialisation, steps, state read-back included)"}
+
+
+def run_serving(args):
+    """Served request stream: Poisson arrivals at load x the plain form's
+    measured throughput, continuous batching against FIFO one-at-a-time."""
+    import numpy as np
+    import paper_1701_02059_gb300 as G
+    from paper_1701_02059_gb300 import serving
+    from synth import membranes as M
+    reqs = M.request_stream(n_requests=args.requests, rate_per_s=1.0, seed=4)
+    jobs = []
+    for i, r in enumerate(reqs):
+        m = r["build"]()
+        p = G.make_params(kT=m.kT, n_centroids=m.n_centroids, box=m.box, periodic=m.periodic, seed=40_000 + i,
+                          instance=i)
+        jobs.append({"params": p, "mem": m, "steps": r["steps"], "arrival_s": 0.0})
+    # plain form: measured service times, then FIFO against the arrivals
+    recp, sp, _ = serving.serve_plain(jobs)
+    services = [r["service_s"] for r in recp]
+    C = sp["particle_steps_per_s"]
+    mean_work = float(np.mean([j["mem"].n * j["steps"] for j in jobs]))
+    rate = args.load * C / mean_work
+    arrivals = [r["arrival_s"] / rate for r in reqs]          # unit-rate Poisson times rescaled
+    for j, a in zip(jobs, arrivals):
+        j["arrival_s"] = a
+    lat_p = serving.fifo(services, arrivals)
+    _, sb, _ = serving.serve_batched(jobs, int(args.budget_gb * 2**30), max_steps=args.max_steps)
+    work = sum(j["mem"].n * j["steps"] for j in jobs)
+    plain = {"p50_s": round(float(np.percentile(lat_p, 50)), 4), "p99_s": round(float(np.percentile(lat_p, 99)), 4),
+             "particle_steps_per_s": round(C, 1)}
+    batched = {k: round(sb[k], 4) for k in ("p50_s", "p99_s", "makespan_s", "particle_steps_per_s")}
+    return {"metric": "p99 completion latency of a served request stream", "value": batched["p99_s"], "unit": "s",
+            "n_gpus": 1, "steps": None, "warmup": 0, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serve", "requests": len(jobs), "particles": sum(j["mem"].n for j in jobs),
+                       "particle_steps": work, "rate_per_s": round(rate, 4), "load": args.load,
+                       "hbm_budget_gb": args.budget_gb, "max_steps_per_launch": args.max_steps},
+            "serving": {"batched": batched | {"gpu_launches": sb["gpu_launches"]}, "plain_fifo": plain,
+                        "p99_speedup": round(plain["p99_s"] / batched["p99_s"], 3)},
+            "gpu_launches": sb["gpu_launches"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -312,6 +387,12 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=25.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-vs-plain ensemble comparison")
+    ap.add_argument("--ensemble-steps", type=int, default=500)
+    ap.add_argument("--requests", type=int, default=32, help="served-stream requests (workload serve)")
+    ap.add_argument("--load", type=float, default=0.8, help="arrival rate / plain-form throughput (workload serve)")
+    ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--max-steps", type=int, default=50, help="steps per arena launch (workload serve)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -324,6 +405,8 @@ def main():
         dist.init_process_group("nccl")
     if args.impl == "reference":
         line = run_reference(args, rank, world)
+    elif args.workload == "serve":
+        line = run_serving(args) if rank == 0 else None
     else:
         line = run_ours(args, rank, world)
     if rank == 0 and line is not None:

@@ -225,6 +225,73 @@ ORBC_API int orbc_get_launch_count(orbc_system* s, long long* count);
 ORBC_API const char* orbc_last_error(const orbc_system* s);
 ORBC_API void orbc_destroy(orbc_system* s);
 
+/* ------------------------------------------------------------------------
+ * Batched arena and continuous batching.  The paper runs one membrane per
+ * process; these calls have no counterpart in it.  They keep many
+ * independent instances resident on the device, packed into one set of
+ * arrays, so each phase of the time step ("Software Overview", flow chart)
+ * is one launch over all of them; the step loop is replayed from a CUDA
+ * graph.  An instance is initialised exactly as orbc_init_cells +
+ * orbc_compute_forces would, and its trajectory is bit-identical to the
+ * plain system's whatever else shares the batch.
+ *
+ * Typical loop: admit instances (at any time, also while others run), call
+ * orbc_arena_run repeatedly, poll for finished slots, retire them.
+ */
+typedef struct orbc_arena orbc_arena;   /* opaque; owns its device memory */
+
+/* hbm_budget_bytes bounds the device memory reserved by admitted instances
+ * (packed arrays plus one carried copy each, which a re-pack needs).  All
+ * instances share one precision.  cuda_stream as in orbc_create.
+ * Errors: ORBC_E_ARG (budget 0, unknown precision, null out), ORBC_E_CUDA. */
+ORBC_API int orbc_arena_create(unsigned long long hbm_budget_bytes, orbc_precision precision, void* cuda_stream,
+                               orbc_arena** out);
+
+/* Admits one instance that will take nsteps steps: the same host arrays as
+ * orbc_set_particles and orbc_set_bonds (copied; the caller keeps them).
+ * The instance is initialised on the device now (k-means clustering and
+ * initial forces) and joins the batch at the next orbc_arena_run.  params
+ * must have rebuild_every = 1 and the arena's precision.  *slot receives
+ * the slot number used by poll and retire.
+ * Errors: ORBC_E_NOMEM when the instance does not fit the remaining budget
+ * (nothing is kept; admit again after retiring others), ORBC_E_ARG, ORBC_E_CUDA. */
+ORBC_API int orbc_arena_admit(orbc_arena* a, const orbc_params* params, int n, const double* pos, const double* vel,
+                              const double* ori, const double* angvel, const unsigned char* type, const unsigned* id,
+                              int nb, const int* ij, const double* r0, const double* kb, long long nsteps, int* slot);
+
+/* Re-packs the batch if instances were admitted or finished, then advances
+ * every resident instance by s = min(max_steps, fewest steps any of them has
+ * left) steps (use_graphs != 0: replay of a captured step).  Instances that
+ * reach their step count leave the batch and become finished.  *steps_done
+ * (nullable) receives s (0 when nothing is resident).
+ * Errors: ORBC_E_NAN / ORBC_E_TIMEOUT from the device status, ORBC_E_ARG
+ * (max_steps < 1), ORBC_E_STATE, ORBC_E_CUDA. */
+ORBC_API int orbc_arena_run(orbc_arena* a, int max_steps, int use_graphs, int* steps_done);
+
+/* Finished slots: up to cap slot numbers into done_slots, their count into
+ * *ndone.  Errors: ORBC_E_ARG. */
+ORBC_API int orbc_arena_poll(orbc_arena* a, int* done_slots, int cap, int* ndone);
+
+/* Copies a finished instance's state out in id order (pos, vel, ori, angvel:
+ * [n][3], each nullable; step: nullable) and frees its slot and memory.
+ * Errors: ORBC_E_ARG (slot not finished), ORBC_E_CUDA. */
+ORBC_API int orbc_arena_retire(orbc_arena* a, int slot, double* pos, double* vel, double* ori, double* angvel,
+                               long long* step);
+
+/* Counts of resident, pending (admitted, not yet packed) and finished
+ * instances, resident particles and reserved bytes; each output nullable. */
+ORBC_API int orbc_arena_info(const orbc_arena* a, int* resident, int* pending, int* done, long long* particles,
+                             unsigned long long* bytes_reserved);
+
+/* Kernels the arena has launched so far (graph replays count each kernel). */
+ORBC_API long long orbc_arena_launch_count(const orbc_arena* a);
+
+/* Message of the last failed arena call ("" if none). */
+ORBC_API const char* orbc_arena_last_error(const orbc_arena* a);
+
+/* Frees the arena, its batch and every slot (NULL is ignored). */
+ORBC_API void orbc_arena_destroy(orbc_arena* a);
+
 #ifdef __cplusplus
 }
 #endif

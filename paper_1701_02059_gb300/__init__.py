@@ -15,7 +15,7 @@ import numpy as np
 from . import _native
 from ._native import F32_FORCE_F64_STATE, F64_ALL, OrbcError, Params, default_params, load
 
-__all__ = ["System", "Params", "default_params", "load", "OrbcError", "F32_FORCE_F64_STATE", "F64_ALL"]
+__all__ = ["System", "Arena", "Params", "default_params", "load", "OrbcError", "F32_FORCE_F64_STATE", "F64_ALL"]
 
 
 def _p(a):
@@ -179,3 +179,77 @@ class System:
             name, launches = nm.rsplit(":", 1)
             out[name] = {"ms": float(ms[q]), "launches": int(launches)}
         return out
+
+
+class Arena:
+    """Batched, continuously batched instances on one GPU (orbc_arena_*)."""
+
+    def __init__(self, hbm_budget_bytes: int, precision: int = F32_FORCE_F64_STATE, stream: int | None = None):
+        self._L = load()
+        self._h = C.c_void_p()
+        rc = self._L.orbc_arena_create(int(hbm_budget_bytes), int(precision), C.c_void_p(stream) if stream else None,
+                                       C.byref(self._h))
+        if rc != 0:
+            raise OrbcError(rc, "orbc_arena_create")
+        self.n_of_slot = {}
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise OrbcError(rc, f"{what}: {self._L.orbc_arena_last_error(self._h).decode()}")
+
+    def close(self):
+        if self._h:
+            self._L.orbc_arena_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def admit(self, params: Params, mem, nsteps: int) -> int:
+        """Admit a membrane (synth.membranes.Membrane-like) for nsteps steps;
+        returns its slot.  Raises OrbcError(ORBC_E_NOMEM) when over budget."""
+        arrs = [np.ascontiguousarray(mem.pos, np.float64), np.ascontiguousarray(mem.vel, np.float64),
+                np.ascontiguousarray(mem.ori, np.float64), np.ascontiguousarray(mem.angvel, np.float64),
+                np.ascontiguousarray(mem.type, np.uint8), np.ascontiguousarray(mem.id, np.uint32)]
+        ij = np.ascontiguousarray(mem.bonds, np.int32)
+        r0 = np.ascontiguousarray(mem.r0, np.float64)
+        kb = np.ascontiguousarray(mem.kb, np.float64)
+        slot = C.c_int(-1)
+        self._check(self._L.orbc_arena_admit(self._h, C.byref(params), len(arrs[4]), *[_p(a) for a in arrs], len(r0),
+                                             _p(ij), _p(r0), _p(kb), int(nsteps), C.byref(slot)), "orbc_arena_admit")
+        self.n_of_slot[slot.value] = len(arrs[4])
+        return slot.value
+
+    def run(self, max_steps: int, graphs: bool = True) -> int:
+        s = C.c_int(0)
+        self._check(self._L.orbc_arena_run(self._h, int(max_steps), 1 if graphs else 0, C.byref(s)), "orbc_arena_run")
+        return s.value
+
+    def poll(self):
+        n = C.c_int(0)
+        self._check(self._L.orbc_arena_poll(self._h, None, 0, C.byref(n)), "orbc_arena_poll")
+        out = np.zeros(max(n.value, 1), np.int32)
+        self._check(self._L.orbc_arena_poll(self._h, _p(out), n.value, C.byref(n)), "orbc_arena_poll")
+        return [int(x) for x in out[:n.value]]
+
+    def retire(self, slot: int):
+        n = self.n_of_slot.get(slot, 0)
+        pos, vel, ori, w = (np.zeros((n, 3)) for _ in range(4))
+        step = C.c_longlong(0)
+        self._check(self._L.orbc_arena_retire(self._h, int(slot), _p(pos), _p(vel), _p(ori), _p(w), C.byref(step)),
+                    "orbc_arena_retire")
+        self.n_of_slot.pop(slot, None)
+        return {"pos": pos, "vel": vel, "ori": ori, "angvel": w, "step": step.value}
+
+    def info(self):
+        r, p, d = C.c_int(0), C.c_int(0), C.c_int(0)
+        np_, b = C.c_longlong(0), C.c_ulonglong(0)
+        self._check(self._L.orbc_arena_info(self._h, C.byref(r), C.byref(p), C.byref(d), C.byref(np_), C.byref(b)),
+                    "orbc_arena_info")
+        return {"resident": r.value, "pending": p.value, "done": d.value, "particles": np_.value, "bytes": b.value}
+
+    def launch_count(self) -> int:
+        return int(self._L.orbc_arena_launch_count(self._h))

@@ -21,7 +21,11 @@ EXPORTS = [
     "orbc_rebuild_cells", "orbc_compute_forces", "orbc_integrate", "orbc_get_state", "orbc_get_forces",
     "orbc_get_cells", "orbc_get_adjacency_len", "orbc_dump_pairs", "orbc_set_timing", "orbc_get_kernel_times",
     "orbc_get_launch_count", "orbc_last_error", "orbc_destroy", "orbc_cell_sort", "orbc_cell_sort_noalloc",
+    "orbc_arena_create", "orbc_arena_admit", "orbc_arena_run", "orbc_arena_poll", "orbc_arena_retire",
+    "orbc_arena_info", "orbc_arena_launch_count", "orbc_arena_last_error", "orbc_arena_destroy",
 ]
+_NOT_INT = {"orbc_default_params": None, "orbc_last_error": C.c_char_p, "orbc_destroy": None,
+            "orbc_arena_launch_count": C.c_longlong, "orbc_arena_last_error": C.c_char_p, "orbc_arena_destroy": None}
 
 
 class Params(C.Structure):
@@ -78,10 +82,19 @@ def load(path: str | None = None):
     L.orbc_last_error.argtypes = [V]
     L.orbc_last_error.restype = C.c_char_p
     L.orbc_destroy.argtypes = [V]
-    L.orbc_destroy.restype = None
+    L.orbc_arena_create.argtypes = [C.c_ulonglong, C.c_int, V, C.POINTER(V)]
+    L.orbc_arena_admit.argtypes = [V, C.POINTER(Params), C.c_int, V, V, V, V, V, V, C.c_int, V, V, V,
+                                   C.c_longlong, C.POINTER(C.c_int)]
+    L.orbc_arena_run.argtypes = [V, C.c_int, C.c_int, C.POINTER(C.c_int)]
+    L.orbc_arena_poll.argtypes = [V, V, C.c_int, C.POINTER(C.c_int)]
+    L.orbc_arena_retire.argtypes = [V, C.c_int, V, V, V, V, C.POINTER(C.c_longlong)]
+    L.orbc_arena_info.argtypes = [V, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_longlong), C.POINTER(C.c_ulonglong)]
+    L.orbc_arena_launch_count.argtypes = [V]
+    L.orbc_arena_last_error.argtypes = [V]
+    L.orbc_arena_destroy.argtypes = [V]
     for name in EXPORTS:
-        getattr(L, name).restype = getattr(L, name).restype if name in ("orbc_default_params", "orbc_last_error",
-                                                                        "orbc_destroy") else C.c_int
+        getattr(L, name).restype = _NOT_INT.get(name, C.c_int) if name in _NOT_INT else C.c_int
     _lib = L
     return L
 

@@ -1,5 +1,5 @@
 // Host orchestration of the hot path and the C ABI declared in orbc.h.
-#include "ensemble.cuh"
+#include "abi_common.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -16,8 +16,11 @@ Ensemble::Ensemble(cudaStream_t s) : stream(s) {}
 Ensemble::~Ensemble() { free_all(); }
 
 void Ensemble::free_all() {
+    for (int q = 0; q < 2; q++)
+        if (graph_[q]) { cudaGraphExecDestroy(graph_[q]); graph_[q] = nullptr; }
     for (void* p : allocs_) cudaFree(p);
     allocs_.clear();
+    bytes_ = 0;
     for (int* p : scan_tmp_) if (p) cudaFree(p);
     scan_tmp_.clear();
     scan_tmp_n_.clear();
@@ -38,6 +41,7 @@ T* Ensemble::alloc(size_t count) {
         throw CudaError(cudaErrorMemoryAllocation, "device allocation of " + std::to_string(bytes) + " bytes failed");
     }
     allocs_.push_back(p);
+    bytes_ += bytes;
     CK(cudaMemsetAsync(p, 0, bytes, stream));
     return (T*)p;
 }
@@ -155,30 +159,8 @@ static Inst make_inst(const Params& P) {
     return I;
 }
 
-void Ensemble::setup(const std::vector<HostInstance>& list) {
-    free_all();
-    B = (int)list.size();
-    if (B < 1) throw ArgError("no instance");
-    precision = list[0].prm.precision;
-    N = 0; Ktot = 0;
-    inst_h.assign(B, Inst());
-    prm_h.clear();
-    std::vector<int> p0(B + 1, 0), k0(B + 1, 0);
-    for (int b = 0; b < B; b++) {
-        const HostInstance& h = list[b];
-        if (h.prm.precision != precision) throw ArgError("all instances of a batch need the same precision");
-        inst_h[b] = make_inst(h.prm);
-        inst_h[b].p0 = N; inst_h[b].n = h.n;
-        inst_h[b].k0 = Ktot; inst_h[b].K = h.prm.n_centroids;
-        inst_h[b].nlip = (int)std::count(h.type.begin(), h.type.end(), (unsigned char)kLipid);
-        prm_h.push_back(h.prm);
-        N += h.n;
-        Ktot += h.prm.n_centroids;
-        p0[b + 1] = N;
-        k0[b + 1] = Ktot;
-    }
-    step_h.assign(B, 0);
-    for (int b = 0; b < B; b++) step_h[b] = list[b].step0;
+// Every array whose size follows from B, N and Ktot (not the grid).
+void Ensemble::alloc_core(const std::vector<int>& p0, const std::vector<int>& k0, bool any_skin) {
     d_inst = alloc<Inst>(B);
     d_p0 = alloc<int>(B + 1);
     d_k0 = alloc<int>(B + 1);
@@ -226,9 +208,85 @@ void Ensemble::setup(const std::vector<HostInstance>& list) {
     d_energy = alloc<long long>((size_t)8 * B);
     d_step = alloc<long long>(B);
     CK(cudaMemcpyAsync(d_step, step_h.data(), sizeof(long long) * B, cudaMemcpyHostToDevice, stream));
+    d_xref = any_skin ? alloc<long long>((size_t)3 * N) : nullptr;
+}
+
+// Bond CSR by (p0 + id), both directions; r0 and kb per entry in FP32 and FP64.
+void Ensemble::upload_bonds(const std::vector<BondSpec>& bl, const std::vector<int>& p0) {
+    std::vector<int> bptr(N + 1, 0);
+    for (int b = 0; b < B; b++) {
+        const int nb = (int)bl[b].r0->size();
+        for (int q = 0; q < nb; q++) {
+            bptr[p0[b] + (*bl[b].bonds)[2 * q] + 1]++;
+            bptr[p0[b] + (*bl[b].bonds)[2 * q + 1] + 1]++;
+        }
+    }
+    for (int i = 0; i < N; i++) {
+        if (bptr[i + 1] > kMaxBondsPerParticle) throw ArgError("more than 8 bonds on one particle");
+        bptr[i + 1] += bptr[i];
+    }
+    const int nbe = bptr[N];
+    std::vector<int> part(std::max(nbe, 1));
+    std::vector<float> r0f(std::max(nbe, 1)), kbf(std::max(nbe, 1));
+    std::vector<double> r0d(std::max(nbe, 1)), kbd(std::max(nbe, 1));
+    std::vector<int> fill(N, 0);
+    for (int b = 0; b < B; b++) {
+        const int nb = (int)bl[b].r0->size();
+        for (int q = 0; q < nb; q++) {
+            const int i = (*bl[b].bonds)[2 * q], j = (*bl[b].bonds)[2 * q + 1];
+            const int gi = p0[b] + i, gj = p0[b] + j;
+            const int si = bptr[gi] + fill[gi]++, sj = bptr[gj] + fill[gj]++;
+            part[si] = j; part[sj] = i;
+            r0f[si] = r0f[sj] = (float)(*bl[b].r0)[q];
+            kbf[si] = kbf[sj] = (float)(*bl[b].kb)[q];
+            r0d[si] = r0d[sj] = (*bl[b].r0)[q];
+            kbd[si] = kbd[sj] = (*bl[b].kb)[q];
+        }
+    }
+    d_bptr = alloc<int>(N + 1);
+    d_bpartner = alloc<int>(std::max(nbe, 1));
+    d_br0 = alloc<float>(std::max(nbe, 1));
+    d_bkb = alloc<float>(std::max(nbe, 1));
+    d_br0_d = alloc<double>(std::max(nbe, 1));
+    d_bkb_d = alloc<double>(std::max(nbe, 1));
+    CK(cudaMemcpyAsync(d_bptr, bptr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, stream));
+    if (nbe > 0) {
+        CK(cudaMemcpyAsync(d_bpartner, part.data(), sizeof(int) * nbe, cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(d_br0, r0f.data(), sizeof(float) * nbe, cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(d_bkb, kbf.data(), sizeof(float) * nbe, cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(d_br0_d, r0d.data(), sizeof(double) * nbe, cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(d_bkb_d, kbd.data(), sizeof(double) * nbe, cudaMemcpyHostToDevice, stream));
+    }
+    CK(cudaStreamSynchronize(stream));   // the host vectors die here
+}
+
+void Ensemble::setup(const std::vector<HostInstance>& list) {
+    free_all();
+    B = (int)list.size();
+    if (B < 1) throw ArgError("no instance");
+    precision = list[0].prm.precision;
+    N = 0; Ktot = 0;
+    inst_h.assign(B, Inst());
+    prm_h.clear();
+    std::vector<int> p0(B + 1, 0), k0(B + 1, 0);
+    for (int b = 0; b < B; b++) {
+        const HostInstance& h = list[b];
+        if (h.prm.precision != precision) throw ArgError("all instances of a batch need the same precision");
+        inst_h[b] = make_inst(h.prm);
+        inst_h[b].p0 = N; inst_h[b].n = h.n;
+        inst_h[b].k0 = Ktot; inst_h[b].K = h.prm.n_centroids;
+        inst_h[b].nlip = (int)std::count(h.type.begin(), h.type.end(), (unsigned char)kLipid);
+        prm_h.push_back(h.prm);
+        N += h.n;
+        Ktot += h.prm.n_centroids;
+        p0[b + 1] = N;
+        k0[b + 1] = Ktot;
+    }
+    step_h.assign(B, 0);
+    for (int b = 0; b < B; b++) step_h[b] = list[b].step0;
     bool any_skin = false;
     for (auto& h : list) any_skin |= (h.prm.rebuild_every > 1);
-    d_xref = any_skin ? alloc<long long>((size_t)3 * N) : nullptr;
+    alloc_core(p0, k0, any_skin);
 
     // state, axis-major
     std::vector<long long> ax((size_t)3 * N);
@@ -259,53 +317,10 @@ void Ensemble::setup(const std::vector<HostInstance>& list) {
     CK(cudaMemcpyAsync(d_id[0], ids.data(), sizeof(unsigned) * N, cudaMemcpyHostToDevice, stream));
     CK(cudaMemcpyAsync(d_slot_of_id, slot.data(), sizeof(int) * N, cudaMemcpyHostToDevice, stream));
 
-    // bonds: CSR by (p0 + id), both directions
-    std::vector<int> bptr(N + 1, 0);
-    for (int b = 0; b < B; b++) {
-        const HostInstance& h = list[b];
-        int nb = (int)h.r0.size();
-        for (int q = 0; q < nb; q++) {
-            bptr[p0[b] + h.bonds[2 * q] + 1]++;
-            bptr[p0[b] + h.bonds[2 * q + 1] + 1]++;
-        }
-    }
-    for (int i = 0; i < N; i++) {
-        if (bptr[i + 1] > kMaxBondsPerParticle) throw ArgError("more than 8 bonds on one particle");
-        bptr[i + 1] += bptr[i];
-    }
-    int nbe = bptr[N];
-    std::vector<int> part(std::max(nbe, 1));
-    std::vector<float> r0f(std::max(nbe, 1)), kbf(std::max(nbe, 1));
-    std::vector<double> r0d(std::max(nbe, 1)), kbd(std::max(nbe, 1));
-    std::vector<int> fill(N, 0);
-    for (int b = 0; b < B; b++) {
-        const HostInstance& h = list[b];
-        int nb = (int)h.r0.size();
-        for (int q = 0; q < nb; q++) {
-            int i = h.bonds[2 * q], j = h.bonds[2 * q + 1];
-            int gi = p0[b] + i, gj = p0[b] + j;
-            int si = bptr[gi] + fill[gi]++, sj = bptr[gj] + fill[gj]++;
-            part[si] = j; part[sj] = i;
-            r0f[si] = r0f[sj] = (float)h.r0[q];
-            kbf[si] = kbf[sj] = (float)h.kb[q];
-            r0d[si] = r0d[sj] = h.r0[q];
-            kbd[si] = kbd[sj] = h.kb[q];
-        }
-    }
-    d_bptr = alloc<int>(N + 1);
-    d_bpartner = alloc<int>(std::max(nbe, 1));
-    d_br0 = alloc<float>(std::max(nbe, 1));
-    d_bkb = alloc<float>(std::max(nbe, 1));
-    d_br0_d = alloc<double>(std::max(nbe, 1));
-    d_bkb_d = alloc<double>(std::max(nbe, 1));
-    CK(cudaMemcpyAsync(d_bptr, bptr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, stream));
-    if (nbe > 0) {
-        CK(cudaMemcpyAsync(d_bpartner, part.data(), sizeof(int) * nbe, cudaMemcpyHostToDevice, stream));
-        CK(cudaMemcpyAsync(d_br0, r0f.data(), sizeof(float) * nbe, cudaMemcpyHostToDevice, stream));
-        CK(cudaMemcpyAsync(d_bkb, kbf.data(), sizeof(float) * nbe, cudaMemcpyHostToDevice, stream));
-        CK(cudaMemcpyAsync(d_br0_d, r0d.data(), sizeof(double) * nbe, cudaMemcpyHostToDevice, stream));
-        CK(cudaMemcpyAsync(d_bkb_d, kbd.data(), sizeof(double) * nbe, cudaMemcpyHostToDevice, stream));
-    }
+    // bonds
+    std::vector<BondSpec> bl(B);
+    for (int b = 0; b < B; b++) bl[b] = BondSpec{&list[b].bonds, &list[b].r0, &list[b].kb};
+    upload_bonds(bl, p0);
 
     // initial centroids (host) and the centroid-grid geometry of each instance
     std::vector<long long> c0((size_t)3 * Ktot);
@@ -430,31 +445,36 @@ void Ensemble::integrate(int nsteps) {
         toc();
     }
     for (int s = 0; s < nsteps; s++) {
-        tic("integrate_baoa");
-        launch_integrate_first();
-        toc();
-        const int re = prm_h[0].rebuild_every;
-        bool due = (re <= 1) || ((step_h[0] + 1) % re == 0);
-        if (!due && d_xref) due = displacement_exceeds_skin();
-        if (due) {
-            tic("rebuild");
-            rebuild();
-            toc();
-        } else {
-            tic("mirrors");
-            mirrors();
-            toc();
-        }
-        tic("pairs");
-        launch_pairs(false, false);
-        toc();
-        tic("integrate_kick");
-        launch_kick(false);
-        toc();
+        step_body();
         for (auto& x : step_h) x++;
     }
     forces_valid = true;
     collect_times(kernel_times);
+}
+
+// One time step: B-A-O-A, cell rebuild (or mirrors), forces, B.
+void Ensemble::step_body() {
+    tic("integrate_baoa");
+    launch_integrate_first();
+    toc();
+    const int re = prm_h[0].rebuild_every;
+    bool due = (re <= 1) || ((step_h[0] + 1) % re == 0);
+    if (!due && d_xref) due = displacement_exceeds_skin();
+    if (due) {
+        tic("rebuild");
+        rebuild();
+        toc();
+    } else {
+        tic("mirrors");
+        mirrors();
+        toc();
+    }
+    tic("pairs");
+    launch_pairs(false, false);
+    toc();
+    tic("integrate_kick");
+    launch_kick(false);
+    toc();
 }
 
 // ---------------------------------------------------------------- getters
@@ -627,23 +647,10 @@ static int fail(orbc_system* s, int code, const std::string& what) {
 
 template <typename F>
 static int guarded(orbc_system* s, F&& f) {
-    try {
-        f();
-        return ORBC_OK;
-    } catch (const ArgError& e) {
-        return fail(s, ORBC_E_ARG, e.what());
-    } catch (const StateError& e) {
-        return fail(s, ORBC_E_STATE, e.what());
-    } catch (const CudaError& e) {
-        return fail(s, e.code == cudaErrorMemoryAllocation ? ORBC_E_NOMEM : ORBC_E_CUDA, e.what());
-    } catch (const std::bad_alloc&) {
-        return fail(s, ORBC_E_NOMEM, "host allocation failed");
-    } catch (const std::exception& e) {
-        return fail(s, ORBC_E_CUDA, e.what());
-    }
+    return guarded_call(s ? &s->err : nullptr, std::forward<F>(f));
 }
 
-static Params to_params(const orbc_params* p) {
+Params orbc::to_params(const orbc_params* p) {
     Params P;
     P.eps = p->eps; P.sigma = p->sigma; P.rc_lipid = p->rc_lipid; P.mu = p->mu; P.sin_theta0 = p->sin_theta0;
     P.zeta = p->zeta; P.eps_wca = p->eps_wca; P.sigma_wca = p->sigma_wca; P.sigma_wca_pp = p->sigma_wca_pp;
@@ -655,7 +662,7 @@ static Params to_params(const orbc_params* p) {
     return P;
 }
 
-static void check_params(const Params& P) {
+void orbc::check_params(const Params& P) {
     auto fin = [](double x) { return std::isfinite(x); };
     if (!(fin(P.eps) && fin(P.sigma) && P.sigma > 0 && fin(P.rc_lipid) && P.rc_lipid > 1.122462048309373 * P.sigma))
         throw ArgError("invalid lipid potential parameters (need rc_lipid > 2^(1/6) sigma)");
@@ -672,6 +679,64 @@ static void check_params(const Params& P) {
     if (P.rebuild_every > 1 && !(P.skin > 0)) throw ArgError("rebuild_every > 1 needs a positive skin");
     if (!(P.skin >= 0 && fin(P.skin)) || !(P.grid_h >= 0 && fin(P.grid_h))) throw ArgError("invalid skin or grid_h");
     if (P.precision != 0 && P.precision != 1) throw ArgError("unknown precision");
+}
+
+
+HostInstance orbc::host_instance(const Params& prm, int n, const double* pos, const double* vel, const double* ori,
+                                 const double* angvel, const unsigned char* type, const unsigned* id) {
+    if (n < 1 || !pos || !vel || !ori || !angvel || !type || !id) throw ArgError("null pointer or n < 1");
+    HostInstance h;
+    h.prm = prm;
+    h.n = n;
+    h.xq.resize((size_t)3 * n); h.vq.resize((size_t)3 * n); h.nq.assign((size_t)3 * n, 0); h.wq.assign((size_t)3 * n, 0);
+    h.type.assign(type, type + n);
+    h.id.assign(id, id + n);
+    std::vector<char> seen(n, 0);
+    for (int i = 0; i < n; i++) {
+        if (id[i] >= (unsigned)n || seen[id[i]]) throw ArgError("ids must be a permutation of 0..n-1");
+        seen[id[i]] = 1;
+        if (type[i] > 2) throw ArgError("unknown particle type");
+        for (int a = 0; a < 3; a++) {
+            double x = pos[3 * i + a], v = vel[3 * i + a];
+            if (!std::isfinite(x) || !std::isfinite(v)) throw ArgError("non-finite position or velocity");
+            if (std::fabs(x) >= 4096.0) throw ArgError("|position| must be < 4096 sigma");
+            if (std::fabs(v) >= 1e6) throw ArgError("|velocity| too large");
+            h.xq[(size_t)3 * i + a] = llrint(x * kGrid);
+            h.vq[(size_t)3 * i + a] = llrint(v * kGrid);
+        }
+        if (type[i] == kLipid) {
+            double o[3], w[3];
+            for (int a = 0; a < 3; a++) { o[a] = ori[3 * i + a]; w[a] = angvel[3 * i + a]; }
+            for (int a = 0; a < 3; a++)
+                if (!std::isfinite(o[a]) || !std::isfinite(w[a])) throw ArgError("non-finite orientation");
+            double nn = std::sqrt(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]);
+            if (std::fabs(nn - 1.0) > 1e-6) throw ArgError("lipid orientation must be a unit vector");
+            for (int a = 0; a < 3; a++) {
+                h.nq[(size_t)3 * i + a] = llrint(o[a] * kGrid);
+                h.wq[(size_t)3 * i + a] = llrint(w[a] * kGrid);
+            }
+        }
+    }
+    return h;
+}
+
+void orbc::host_bonds(HostInstance& h, int nb, const int* ij, const double* r0, const double* kb) {
+    if (nb < 0 || (nb > 0 && (!ij || !r0 || !kb))) throw ArgError("invalid bond arrays");
+    for (int q = 0; q < nb; q++) {
+        if (ij[2 * q] < 0 || ij[2 * q] >= h.n || ij[2 * q + 1] < 0 || ij[2 * q + 1] >= h.n || ij[2 * q] == ij[2 * q + 1])
+            throw ArgError("bond id out of range");
+        if (!(r0[q] >= 0 && std::isfinite(r0[q]) && kb[q] >= 0 && std::isfinite(kb[q])))
+            throw ArgError("invalid bond constants");
+    }
+    h.bonds.assign(ij, ij + 2 * (size_t)nb);
+    h.r0.assign(r0, r0 + nb);
+    h.kb.assign(kb, kb + nb);
+}
+
+int orbc::status_code(unsigned st) {
+    if (st & kStatusTimeout) return ORBC_E_TIMEOUT;
+    if (st & (kStatusNaN | kStatusPairForceRange)) return ORBC_E_NAN;
+    return ORBC_E_STATE;
 }
 
 extern "C" {
@@ -710,40 +775,7 @@ int orbc_set_particles(orbc_system* s, int n, const double* pos, const double* v
                        const double* angvel, const unsigned char* type, const unsigned* id) {
     if (!s) return ORBC_E_ARG;
     return guarded(s, [&] {
-        if (n < 1 || !pos || !vel || !ori || !angvel || !type || !id) throw ArgError("null pointer or n < 1");
-        HostInstance h;
-        h.prm = s->prm;
-        h.n = n;
-        h.xq.resize((size_t)3 * n); h.vq.resize((size_t)3 * n); h.nq.assign((size_t)3 * n, 0); h.wq.assign((size_t)3 * n, 0);
-        h.type.assign(type, type + n);
-        h.id.assign(id, id + n);
-        std::vector<char> seen(n, 0);
-        for (int i = 0; i < n; i++) {
-            if (id[i] >= (unsigned)n || seen[id[i]]) throw ArgError("ids must be a permutation of 0..n-1");
-            seen[id[i]] = 1;
-            if (type[i] > 2) throw ArgError("unknown particle type");
-            for (int a = 0; a < 3; a++) {
-                double x = pos[3 * i + a], v = vel[3 * i + a];
-                if (!std::isfinite(x) || !std::isfinite(v)) throw ArgError("non-finite position or velocity");
-                if (std::fabs(x) >= 4096.0) throw ArgError("|position| must be < 4096 sigma");
-                if (std::fabs(v) >= 1e6) throw ArgError("|velocity| too large");
-                h.xq[(size_t)3 * i + a] = llrint(x * kGrid);
-                h.vq[(size_t)3 * i + a] = llrint(v * kGrid);
-            }
-            if (type[i] == kLipid) {
-                double o[3], w[3];
-                for (int a = 0; a < 3; a++) { o[a] = ori[3 * i + a]; w[a] = angvel[3 * i + a]; }
-                for (int a = 0; a < 3; a++)
-                    if (!std::isfinite(o[a]) || !std::isfinite(w[a])) throw ArgError("non-finite orientation");
-                double nn = std::sqrt(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]);
-                if (std::fabs(nn - 1.0) > 1e-6) throw ArgError("lipid orientation must be a unit vector");
-                for (int a = 0; a < 3; a++) {
-                    h.nq[(size_t)3 * i + a] = llrint(o[a] * kGrid);
-                    h.wq[(size_t)3 * i + a] = llrint(w[a] * kGrid);
-                }
-            }
-        }
-        s->host = std::move(h);
+        s->host = host_instance(s->prm, n, pos, vel, ori, angvel, type, id);
         s->have_particles = true;
         s->ens->setup({s->host});
     });
@@ -753,16 +785,7 @@ int orbc_set_bonds(orbc_system* s, int nb, const int* ij, const double* r0, cons
     if (!s) return ORBC_E_ARG;
     return guarded(s, [&] {
         if (!s->have_particles) throw StateError("set particles before bonds");
-        if (nb < 0 || (nb > 0 && (!ij || !r0 || !kb))) throw ArgError("invalid bond arrays");
-        for (int q = 0; q < nb; q++) {
-            if (ij[2 * q] < 0 || ij[2 * q] >= s->host.n || ij[2 * q + 1] < 0 || ij[2 * q + 1] >= s->host.n ||
-                ij[2 * q] == ij[2 * q + 1])
-                throw ArgError("bond id out of range");
-            if (!(r0[q] >= 0 && std::isfinite(r0[q]) && kb[q] >= 0 && std::isfinite(kb[q]))) throw ArgError("invalid bond constants");
-        }
-        s->host.bonds.assign(ij, ij + 2 * (size_t)nb);
-        s->host.r0.assign(r0, r0 + nb);
-        s->host.kb.assign(kb, kb + nb);
+        host_bonds(s->host, nb, ij, r0, kb);
         s->ens->setup({s->host});
     });
 }
@@ -792,12 +815,6 @@ int orbc_rebuild_cells(orbc_system* s) {
         unsigned st = s->ens->read_status(true);
         if (st) throw StateError("rebuild flagged status " + std::to_string(st));
     });
-}
-
-static int status_code(unsigned st) {
-    if (st & kStatusTimeout) return ORBC_E_TIMEOUT;
-    if (st & (kStatusNaN | kStatusPairForceRange)) return ORBC_E_NAN;
-    return ORBC_E_STATE;
 }
 
 int orbc_compute_forces(orbc_system* s, double* energies_out) {

@@ -1,0 +1,508 @@
+// Batched arena: many independent membranes of uneven size resident on the
+// device at once, packed into one set of arrays so that every phase of the
+// time step (B-A-O-A, cell rebuild, forces, B) is one launch over all of
+// them; the step loop is replayed from a CUDA graph.  Instances are admitted
+// against an HBM budget while others run (continuous batching) and leave the
+// batch when they have taken their steps.  Each instance is initialised
+// exactly as a plain system is (k-means clustering, initial forces), and the
+// batch only concatenates per-instance work, so an instance's trajectory is
+// bit-identical alone and in any mix.
+#include "abi_common.cuh"
+
+#include <algorithm>
+#include <memory>
+
+namespace orbc {
+
+// ---------------------------------------------------------------- snapshots
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+void Snapshot::allocate(int n_, int K_) {
+    release();
+    n = n_;
+    K = K_;
+    const size_t s_state = align256(sizeof(long long) * 3 * (size_t)n);
+    const size_t s_u8 = align256((size_t)n);
+    const size_t s_i32 = align256(sizeof(int) * (size_t)n);
+    const size_t s_cs = align256(sizeof(int) * ((size_t)K + 1));
+    const size_t s_cq = align256(sizeof(long long) * 3 * (size_t)K);
+    bytes = 6 * s_state + s_u8 + 2 * s_i32 + s_cs + s_cq;
+    if (cudaMalloc(&block, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        block = nullptr;
+        throw CudaError(cudaErrorMemoryAllocation, "snapshot allocation failed");
+    }
+    char* p = (char*)block;
+    for (int q = 0; q < 4; q++) { state[q] = (long long*)p; p += s_state; }
+    F = (long long*)p; p += s_state;
+    T = (long long*)p; p += s_state;
+    type = (unsigned char*)p; p += s_u8;
+    id = (unsigned*)p; p += s_i32;
+    cell = (int*)p; p += s_i32;
+    cell_start = (int*)p; p += s_cs;
+    cq = (long long*)p;
+}
+
+void Snapshot::release() {
+    if (block) cudaFree(block);
+    block = nullptr;
+    bytes = 0;
+}
+
+__global__ void k_offset(int* __restrict__ a, long long n, int delta) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] += delta;
+}
+
+__global__ void k_slot_of_id(View v) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= v.N) return;
+    const int b = find_inst(v.inst_p0, v.B, p);
+    v.slot_of_id[v.inst[b].p0 + (int)v.id[p]] = p;
+}
+
+static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
+
+static void d2d(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    if (bytes) CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st));
+}
+
+void Ensemble::export_instance(int b, Snapshot& s) {
+    if (!cells_valid || !forces_valid) throw StateError("instance has no cell list or forces to carry");
+    const Inst& I = inst_h[b];
+    const int n = I.n, K = I.K;
+    s.allocate(n, K);
+    s.inst = I;
+    s.prm = prm_h[b];
+    s.step = step_h[b];
+    for (int q = 0; q < 4; q++)
+        for (int a = 0; a < 3; a++)
+            d2d(s.state[q] + (size_t)a * n, d_state[cur_][q] + (size_t)a * N + I.p0, sizeof(long long) * n, stream);
+    for (int a = 0; a < 3; a++) {
+        d2d(s.F + (size_t)a * n, d_F + (size_t)a * N + I.p0, sizeof(long long) * n, stream);
+        d2d(s.T + (size_t)a * n, d_T + (size_t)a * N + I.p0, sizeof(long long) * n, stream);
+        d2d(s.cq + (size_t)a * K, d_cq + (size_t)a * Ktot + I.k0, sizeof(long long) * K, stream);
+    }
+    d2d(s.type, d_type[cur_] + I.p0, (size_t)n, stream);
+    d2d(s.id, d_id[cur_] + I.p0, sizeof(unsigned) * n, stream);
+    d2d(s.cell, d_cell + I.p0, sizeof(int) * n, stream);
+    d2d(s.cell_start, d_cell_start + I.k0, sizeof(int) * (K + 1), stream);
+    k_offset<<<nblk(n, 256), 256, 0, stream>>>(s.cell, n, -I.k0);
+    k_offset<<<nblk(K + 1, 256), 256, 0, stream>>>(s.cell_start, K + 1, -I.p0);
+    launches += 2;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(stream));
+}
+
+void Ensemble::setup_from(const std::vector<const Snapshot*>& list) {
+    free_all();
+    B = (int)list.size();
+    if (B < 1) throw ArgError("no instance");
+    precision = list[0]->prm.precision;
+    N = 0;
+    Ktot = 0;
+    inst_h.assign(B, Inst());
+    prm_h.clear();
+    step_h.assign(B, 0);
+    std::vector<int> p0(B + 1, 0), k0(B + 1, 0);
+    for (int b = 0; b < B; b++) {
+        const Snapshot& s = *list[b];
+        if (s.prm.precision != precision) throw ArgError("all instances of a batch need the same precision");
+        if (s.prm.rebuild_every != 1) throw ArgError("carried instances must rebuild every step");
+        inst_h[b] = s.inst;
+        inst_h[b].p0 = N;
+        inst_h[b].k0 = Ktot;
+        prm_h.push_back(s.prm);
+        step_h[b] = s.step;
+        N += s.n;
+        Ktot += s.K;
+        p0[b + 1] = N;
+        k0[b + 1] = Ktot;
+    }
+    alloc_core(p0, k0, false);
+    Gtot = 0;
+    for (int b = 0; b < B; b++) {
+        inst_h[b].g0 = Gtot;
+        Gtot += (long long)inst_h[b].gdim[0] * inst_h[b].gdim[1] * inst_h[b].gdim[2];
+    }
+    d_gstart = alloc<int>(Gtot + 1);
+    d_gcount = alloc<int>(Gtot + 1);
+    CK(cudaMemcpyAsync(d_inst, inst_h.data(), sizeof(Inst) * B, cudaMemcpyHostToDevice, stream));
+    for (int b = 0; b < B; b++) {
+        const Snapshot& s = *list[b];
+        const int n = s.n, K = s.K;
+        for (int q = 0; q < 4; q++)
+            for (int a = 0; a < 3; a++)
+                d2d(d_state[0][q] + (size_t)a * N + p0[b], s.state[q] + (size_t)a * n, sizeof(long long) * n, stream);
+        for (int a = 0; a < 3; a++) {
+            d2d(d_F + (size_t)a * N + p0[b], s.F + (size_t)a * n, sizeof(long long) * n, stream);
+            d2d(d_T + (size_t)a * N + p0[b], s.T + (size_t)a * n, sizeof(long long) * n, stream);
+            d2d(d_cq + (size_t)a * Ktot + k0[b], s.cq + (size_t)a * K, sizeof(long long) * K, stream);
+        }
+        d2d(d_type[0] + p0[b], s.type, (size_t)n, stream);
+        d2d(d_id[0] + p0[b], s.id, sizeof(unsigned) * n, stream);
+        d2d(d_cell + p0[b], s.cell, sizeof(int) * n, stream);
+        k_offset<<<nblk(n, 256), 256, 0, stream>>>(d_cell + p0[b], n, k0[b]);
+        // instance b's K + 1 offsets; the last one equals the next instance's first
+        d2d(d_cell_start + k0[b], s.cell_start, sizeof(int) * (K + 1), stream);
+        k_offset<<<nblk(K + 1, 256), 256, 0, stream>>>(d_cell_start + k0[b], K + 1, p0[b]);
+        launches += 2;
+    }
+    k_slot_of_id<<<nblk(N, 256), 256, 0, stream>>>(view());
+    launches++;
+    CK(cudaGetLastError());
+    std::vector<BondSpec> bl(B);
+    for (int b = 0; b < B; b++) bl[b] = BondSpec{&list[b]->bonds, &list[b]->r0, &list[b]->kb};
+    upload_bonds(bl, p0);
+    // warm the scan scratch (outputs into arrays the next rebuild rewrites)
+    scan_exclusive(d_gcount, d_gstart, Gtot + 1);
+    scan_exclusive(d_cnt, d_adj_ptr, Ktot + 1);
+    CK(cudaStreamSynchronize(stream));
+    n_lloyd_.assign(B, 0);
+    // the next step starts from the carried forces and ownership; its rebuild
+    // recomputes the mirrors, radii and neighbouring cells
+    cells_valid = true;
+    forces_valid = true;
+}
+
+// ---------------------------------------------------------------- graphs
+void Ensemble::integrate_graph(int nsteps) {
+    if (!cells_valid) throw StateError("cells not initialised");
+    const bool eager = timing || d_xref != nullptr || prm_h[0].rebuild_every != 1;
+    if (eager) {
+        integrate(nsteps);
+        return;
+    }
+    if (!forces_valid) {
+        launch_pairs(false, false);
+        forces_valid = true;
+    }
+    int s = 0;
+    // the first step after a set-up seeds the E-step from the grid search
+    if (!prev_adj_valid_ && s < nsteps) {
+        step_body();
+        for (auto& x : step_h) x++;
+        s++;
+    }
+    for (; s < nsteps; s++) {
+        const int p = cur_;
+        if (!graph_[p]) {
+            const long long l0 = launches, r0 = n_rebuilds;
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+            try {
+                step_body();
+            } catch (...) {
+                cudaStreamEndCapture(stream, &g);
+                if (g) cudaGraphDestroy(g);
+                cur_ = p;
+                throw;
+            }
+            CK(cudaStreamEndCapture(stream, &g));
+            cudaError_t e = cudaGraphInstantiate(&graph_[p], g, 0);
+            cudaGraphDestroy(g);
+            CK(e);
+            // capturing ran no kernel: restore the host-side state it advanced
+            graph_launches_ = launches - l0;
+            launches = l0;
+            n_rebuilds = r0;
+            cur_ = p;
+        }
+        CK(cudaGraphLaunch(graph_[p], stream));
+        cur_ = p ^ 1;   // the step's gather swapped the state buffers
+        launches += graph_launches_;
+        n_rebuilds++;
+        for (auto& x : step_h) x++;
+    }
+    forces_valid = true;
+}
+
+// ---------------------------------------------------------------- arena
+struct ArenaSlot {
+    enum { kFree = 0, kPending = 1, kResident = 2, kDone = 3 };
+    int state = kFree;
+    long long target = 0, done = 0;
+    size_t bytes = 0;       // packed arrays of a batch of one + one snapshot
+    long long n = 0;
+    std::vector<int> bonds;  // host copy of the bond list (ids local to the instance)
+    std::vector<double> r0, kb;
+    std::unique_ptr<Snapshot> snap;   // carried state while pending or finished
+};
+
+class Arena {
+public:
+    Arena(size_t budget, int precision, cudaStream_t st, bool own) :
+        budget_(budget), precision_(precision), stream_(st), own_stream_(own) {}
+    ~Arena() {
+        batch_.reset();
+        slots_.clear();
+        if (own_stream_) cudaStreamDestroy(stream_);
+    }
+
+    size_t reserved() const {
+        size_t s = 0;
+        for (auto& x : slots_) if (x.state != ArenaSlot::kFree) s += x.bytes;
+        return s;
+    }
+
+    int admit(HostInstance& h, long long nsteps) {
+        if (nsteps < 1) throw ArgError("nsteps must be >= 1");
+        if (h.prm.precision != precision_) throw ArgError("instance precision differs from the arena's");
+        if (h.prm.rebuild_every != 1) throw ArgError("arena instances rebuild their cells every step");
+        if (h.prm.n_centroids > (int)h.n) throw ArgError("more centroids than particles");
+        // a batch of one initialises the instance exactly as a plain system does
+        auto snap = std::make_unique<Snapshot>();
+        size_t bytes = 0;
+        {
+            Ensemble e(stream_);
+            e.setup({h});
+            bytes = e.bytes_allocated();
+            if (reserved() + bytes + bytes / 2 > budget_) throw CudaError(cudaErrorMemoryAllocation, "over the HBM budget");
+            e.init_cells();
+            e.compute_forces(false);
+            const unsigned st = e.read_status(true);
+            if (st) throw StateError("instance initialisation flagged status " + std::to_string(st));
+            e.export_instance(0, *snap);
+        }
+        bytes += snap->bytes;
+        if (reserved() + bytes > budget_) throw CudaError(cudaErrorMemoryAllocation, "over the HBM budget");
+        int slot = -1;
+        for (int i = 0; i < (int)slots_.size(); i++)
+            if (slots_[i].state == ArenaSlot::kFree) { slot = i; break; }
+        if (slot < 0) { slots_.emplace_back(); slot = (int)slots_.size() - 1; }
+        ArenaSlot& S = slots_[slot];
+        S.state = ArenaSlot::kPending;
+        S.target = nsteps;
+        S.done = 0;
+        S.bytes = bytes;
+        S.n = h.n;
+        S.snap = std::move(snap);
+        S.bonds = h.bonds;
+        S.r0 = h.r0;
+        S.kb = h.kb;
+        dirty_ = true;
+        return slot;
+    }
+
+    // Steps every resident instance by min(max_steps, fewest steps left).
+    int run(int max_steps, bool graphs) {
+        if (max_steps < 1) throw ArgError("max_steps must be >= 1");
+        if (dirty_) repack();
+        if (!batch_) return 0;
+        long long s = max_steps;
+        for (int slot : batch_slot_) s = std::min(s, slots_[slot].target - slots_[slot].done);
+        if (graphs) batch_->integrate_graph((int)s);
+        else batch_->integrate((int)s);
+        const unsigned st = batch_->read_status(true);
+        if (st) {
+            last_status_ = st;
+            throw StateError("device status " + std::to_string(st));
+        }
+        for (int b = 0; b < (int)batch_slot_.size(); b++) {
+            ArenaSlot& S = slots_[batch_slot_[b]];
+            S.done += s;
+            if (S.done >= S.target) {
+                S.snap = std::make_unique<Snapshot>();
+                batch_->export_instance(b, *S.snap);
+                S.state = ArenaSlot::kDone;
+                dirty_ = true;
+            }
+        }
+        return (int)s;
+    }
+
+    void poll(int* out, int cap, int* ndone) const {
+        int k = 0;
+        for (int i = 0; i < (int)slots_.size(); i++)
+            if (slots_[i].state == ArenaSlot::kDone) {
+                if (out && k < cap) out[k] = i;
+                k++;
+            }
+        *ndone = k;
+    }
+
+    void retire(int slot, double* pos, double* vel, double* ori, double* angvel, long long* step) {
+        if (slot < 0 || slot >= (int)slots_.size() || slots_[slot].state != ArenaSlot::kDone)
+            throw ArgError("slot is not finished");
+        ArenaSlot& S = slots_[slot];
+        const Snapshot& s = *S.snap;
+        const int n = s.n;
+        std::vector<unsigned> ids(n);
+        std::vector<long long> buf((size_t)3 * n);
+        CK(cudaMemcpyAsync(ids.data(), s.id, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, stream_));
+        double* outs[4] = {pos, vel, ori, angvel};
+        for (int q = 0; q < 4; q++) {
+            if (!outs[q]) continue;
+            CK(cudaMemcpyAsync(buf.data(), s.state[q], sizeof(long long) * 3 * n, cudaMemcpyDeviceToHost, stream_));
+            CK(cudaStreamSynchronize(stream_));
+            for (int a = 0; a < 3; a++)
+                for (int i = 0; i < n; i++) outs[q][(size_t)3 * ids[i] + a] = (double)buf[(size_t)a * n + i] * kGridInv;
+        }
+        CK(cudaStreamSynchronize(stream_));
+        if (step) *step = s.step;
+        S.snap.reset();
+        S.state = ArenaSlot::kFree;
+        S.bytes = 0;
+    }
+
+    void info(int* resident, int* pending, int* done, long long* particles, unsigned long long* bytes) const {
+        int r = 0, p = 0, d = 0;
+        long long np = 0;
+        for (auto& x : slots_) {
+            if (x.state == ArenaSlot::kResident) { r++; np += x.n; }
+            if (x.state == ArenaSlot::kPending) p++;
+            if (x.state == ArenaSlot::kDone) d++;
+        }
+        if (resident) *resident = r;
+        if (pending) *pending = p;
+        if (done) *done = d;
+        if (particles) *particles = np;
+        if (bytes) *bytes = (unsigned long long)reserved();
+    }
+
+    long long launches() const { return launches_ + (batch_ ? batch_->launches : 0); }
+    unsigned last_status_ = 0;
+    std::string err;
+
+private:
+    // New batch = unfinished resident instances (carried) + pending ones.
+    void repack() {
+        std::vector<int> members;
+        if (batch_) {
+            for (int b = 0; b < (int)batch_slot_.size(); b++) {
+                ArenaSlot& S = slots_[batch_slot_[b]];
+                if (S.state != ArenaSlot::kResident) continue;
+                S.snap = std::make_unique<Snapshot>();
+                batch_->export_instance(b, *S.snap);
+                members.push_back(batch_slot_[b]);
+            }
+            launches_ += batch_->launches;
+            batch_.reset();
+        }
+        for (int i = 0; i < (int)slots_.size(); i++)
+            if (slots_[i].state == ArenaSlot::kPending) members.push_back(i);
+        batch_slot_.clear();
+        dirty_ = false;
+        if (members.empty()) return;
+        std::vector<const Snapshot*> list;
+        for (int i : members) {
+            Snapshot* sp = slots_[i].snap.get();
+            sp->bonds = slots_[i].bonds;
+            sp->r0 = slots_[i].r0;
+            sp->kb = slots_[i].kb;
+            list.push_back(sp);
+        }
+        auto e = std::make_unique<Ensemble>(stream_);
+        e->setup_from(list);
+        for (int i : members) {
+            slots_[i].state = ArenaSlot::kResident;
+            slots_[i].snap.reset();   // the batch holds the state now
+        }
+        batch_ = std::move(e);
+        batch_slot_ = members;
+    }
+
+    size_t budget_;
+    int precision_;
+    cudaStream_t stream_;
+    bool own_stream_;
+    std::unique_ptr<Ensemble> batch_;
+    std::vector<int> batch_slot_;
+    std::vector<ArenaSlot> slots_;
+    bool dirty_ = false;
+    long long launches_ = 0;
+};
+
+}  // namespace orbc
+
+// ============================================================== C ABI
+using namespace orbc;
+
+struct orbc_arena {
+    Arena* a = nullptr;
+    std::string err;
+};
+
+extern "C" {
+
+int orbc_arena_create(unsigned long long hbm_budget_bytes, orbc_precision precision, void* cuda_stream,
+                      orbc_arena** out) {
+    if (!out) return ORBC_E_ARG;
+    *out = nullptr;
+    if (hbm_budget_bytes == 0 || (precision != ORBC_F32_FORCE_F64_STATE && precision != ORBC_F64_ALL))
+        return ORBC_E_ARG;
+    orbc_arena* h = new (std::nothrow) orbc_arena();
+    if (!h) return ORBC_E_NOMEM;
+    int rc = guarded_call(&h->err, [&] {
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        bool own = false;
+        if (!st) {
+            CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            own = true;
+        }
+        h->a = new Arena((size_t)hbm_budget_bytes, (int)precision, st, own);
+    });
+    if (rc != ORBC_OK) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return ORBC_OK;
+}
+
+int orbc_arena_admit(orbc_arena* h, const orbc_params* params, int n, const double* pos, const double* vel,
+                     const double* ori, const double* angvel, const unsigned char* type, const unsigned* id, int nb,
+                     const int* ij, const double* r0, const double* kb, long long nsteps, int* slot) {
+    if (!h || !params || !slot) return ORBC_E_ARG;
+    *slot = -1;
+    return guarded_call(&h->err, [&] {
+        Params P = to_params(params);
+        check_params(P);
+        HostInstance inst = host_instance(P, n, pos, vel, ori, angvel, type, id);
+        host_bonds(inst, nb, ij, r0, kb);
+        *slot = h->a->admit(inst, nsteps);
+    });
+}
+
+int orbc_arena_run(orbc_arena* h, int max_steps, int use_graphs, int* steps_done) {
+    if (!h) return ORBC_E_ARG;
+    if (steps_done) *steps_done = 0;
+    h->a->last_status_ = 0;
+    int rc = guarded_call(&h->err, [&] {
+        int s = h->a->run(max_steps, use_graphs != 0);
+        if (steps_done) *steps_done = s;
+    });
+    if (rc == ORBC_E_STATE && h->a->last_status_) return status_code(h->a->last_status_);
+    return rc;
+}
+
+int orbc_arena_poll(orbc_arena* h, int* done_slots, int cap, int* ndone) {
+    if (!h || !ndone || cap < 0 || (cap > 0 && !done_slots)) return ORBC_E_ARG;
+    h->a->poll(done_slots, cap, ndone);
+    return ORBC_OK;
+}
+
+int orbc_arena_retire(orbc_arena* h, int slot, double* pos, double* vel, double* ori, double* angvel,
+                      long long* step) {
+    if (!h) return ORBC_E_ARG;
+    return guarded_call(&h->err, [&] { h->a->retire(slot, pos, vel, ori, angvel, step); });
+}
+
+int orbc_arena_info(const orbc_arena* h, int* resident, int* pending, int* done, long long* particles,
+                    unsigned long long* bytes_reserved) {
+    if (!h) return ORBC_E_ARG;
+    h->a->info(resident, pending, done, particles, bytes_reserved);
+    return ORBC_OK;
+}
+
+long long orbc_arena_launch_count(const orbc_arena* h) { return h ? h->a->launches() : -1; }
+
+const char* orbc_arena_last_error(const orbc_arena* h) { return h ? h->err.c_str() : "null handle"; }
+
+void orbc_arena_destroy(orbc_arena* h) {
+    if (!h) return;
+    delete h->a;
+    delete h;
+}
+
+}  // extern "C"

@@ -647,6 +647,9 @@ __global__ void k_estep_fast(View v, const int* __restrict__ cell_old, const int
                 const float cx = __shfl_sync(0xffffffffu, c.x, q);
                 const float cy = __shfl_sync(0xffffffffu, c.y, q);
                 const float cz = __shfl_sync(0xffffffffu, c.z, q);
+                // a warp can straddle two instances of a batch: their cells
+                // live in other coordinates and never compete
+                if ((unsigned)(jq - I.k0) >= (unsigned)I.K) continue;
                 const float dx = axis_dist(p[0], cx, I, 0), dy = axis_dist(p[1], cy, I, 1), dz = axis_dist(p[2], cz, I, 2);
                 const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 if (jq == kn) dself2 = d2;

@@ -59,6 +59,38 @@ struct HostInstance {
     long long step0 = 0;                     // steps already taken
 };
 
+// Bond list of one instance (ids local to the instance).
+struct BondSpec {
+    const std::vector<int>* bonds;
+    const std::vector<double>* r0;
+    const std::vector<double>* kb;
+};
+
+// One instance's carried state in device buffers of its own: what a packed
+// batch needs to continue the instance bit for bit after it is re-packed
+// (state, forces, centroids, cell ownership in the cell-sorted order).
+struct Snapshot {
+    Inst inst;                                // descriptor (p0, k0, g0 of the batch it came from)
+    Params prm;
+    int n = 0, K = 0;
+    long long step = 0;
+    std::vector<int> bonds;                   // host copy of the bond list
+    std::vector<double> r0, kb;
+    long long* state[4] = {nullptr, nullptr, nullptr, nullptr};   // x, v, n, w: [3][n]
+    unsigned char* type = nullptr;
+    unsigned* id = nullptr;
+    int* cell = nullptr;                      // [n], local cell index
+    int* cell_start = nullptr;                // [K + 1], local offsets
+    long long* cq = nullptr;                  // [3][K]
+    long long* F = nullptr;                   // [3][n]
+    long long* T = nullptr;                   // [3][n]
+    void* block = nullptr;                    // one device allocation holding all of the above
+    size_t bytes = 0;
+    void allocate(int n_, int K_);
+    void release();
+    ~Snapshot() { release(); }
+};
+
 class Ensemble {
 public:
     explicit Ensemble(cudaStream_t s);
@@ -68,6 +100,12 @@ public:
 
     // set-up: particles and bonds of every instance; allocates everything
     void setup(const std::vector<HostInstance>& list);
+    // set-up from carried instances: continues each where it stopped
+    void setup_from(const std::vector<const Snapshot*>& list);
+    void export_instance(int b, Snapshot& s);
+    size_t bytes_allocated() const { return bytes_; }
+    // one step captured as a CUDA graph per state-buffer parity, replayed
+    void integrate_graph(int nsteps);
     void init_cells();                       // seeding + Lloyd + reorder
     void rebuild();                          // one EM update + reorder
     void compute_forces(bool energies);
@@ -127,6 +165,12 @@ public:
 
 private:
     void free_all();
+    void alloc_core(const std::vector<int>& p0, const std::vector<int>& k0, bool any_skin);
+    void upload_bonds(const std::vector<BondSpec>& bl, const std::vector<int>& p0);
+    void step_body();
+    size_t bytes_ = 0;
+    cudaGraphExec_t graph_[2] = {nullptr, nullptr};
+    long long graph_launches_ = 0;
     template <typename T> T* alloc(size_t count);
     std::vector<void*> allocs_;
     int cur_ = 0;

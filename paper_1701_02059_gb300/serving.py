@@ -1,0 +1,121 @@
+"""Request loops over the batched arena (continuous batching) and over the
+plain one-system-per-request form, for the ensemble and served-stream
+workloads.  Orchestration only: admission, stepping and retirement are calls
+into the C ABI (orbc_arena_*, orbc_*); no arithmetic of the method runs here.
+
+A job is a dict with ``params`` (orbc_params), ``mem`` (a membrane with the
+host arrays of orbc_set_particles / orbc_set_bonds), ``steps`` and
+``arrival_s`` (seconds after the start of the stream).
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import Arena, OrbcError, System
+from ._native import ORBC_E_NOMEM, F32_FORCE_F64_STATE
+
+
+def _percentiles(lat):
+    lat = np.asarray(lat, float)
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "max_s": float(lat.max()), "mean_s": float(lat.mean())}
+
+
+def serve_batched(jobs, hbm_budget_bytes: int, max_steps: int = 50, graphs: bool = True, keep_states: bool = False,
+                  precision: int = F32_FORCE_F64_STATE, stream: int | None = None):
+    """Continuous batching: requests are admitted as they arrive and as the
+    budget allows, every resident request advances in one batched launch per
+    phase, finished ones are retired.  Returns per-job records (latency =
+    completion time - arrival time) and a summary."""
+    arena = Arena(hbm_budget_bytes, precision, stream)
+    order = sorted(range(len(jobs)), key=lambda i: jobs[i]["arrival_s"])
+    waiting = list(order)
+    slot_job = {}
+    rec = [None] * len(jobs)
+    states = [None] * len(jobs)
+    t0 = time.perf_counter()
+    work = 0
+    while waiting or slot_job:
+        now = time.perf_counter() - t0
+        # admit everything that has arrived, in arrival order, while it fits
+        while waiting and jobs[waiting[0]]["arrival_s"] <= now:
+            i = waiting[0]
+            try:
+                s = arena.admit(jobs[i]["params"], jobs[i]["mem"], jobs[i]["steps"])
+            except OrbcError as e:
+                if e.code != ORBC_E_NOMEM:
+                    raise
+                if not slot_job:
+                    raise RuntimeError(f"request {i} does not fit the HBM budget on an empty GPU") from e
+                break
+            slot_job[s] = i
+            waiting.pop(0)
+            rec[i] = {"arrival_s": jobs[i]["arrival_s"], "admitted_s": time.perf_counter() - t0}
+        if slot_job:
+            arena.run(max_steps, graphs)
+            for s in arena.poll():
+                i = slot_job.pop(s)
+                st = arena.retire(s)
+                if keep_states:
+                    states[i] = st
+                done = time.perf_counter() - t0
+                rec[i]["done_s"] = done
+                rec[i]["latency_s"] = done - jobs[i]["arrival_s"]
+                work += jobs[i]["mem"].n * jobs[i]["steps"]
+        elif waiting:
+            time.sleep(max(0.0, min(0.05, jobs[waiting[0]]["arrival_s"] - (time.perf_counter() - t0))))
+    total = time.perf_counter() - t0
+    launches = arena.launch_count()
+    arena.close()
+    summary = _percentiles([r["latency_s"] for r in rec])
+    summary.update({"makespan_s": total, "particle_steps": work, "particle_steps_per_s": work / total,
+                    "gpu_launches": launches})
+    return rec, summary, states
+
+
+def fifo(services, arrivals):
+    """Completion latencies of a single first-come-first-served server with
+    the given service and arrival times."""
+    order = np.argsort(np.asarray(arrivals, float), kind="stable")
+    clock = 0.0
+    lat = np.zeros(len(services))
+    for i in order:
+        clock = max(clock, arrivals[i]) + services[i]
+        lat[i] = clock - arrivals[i]
+    return lat
+
+
+def serve_plain(jobs, keep_states: bool = False, stream: int | None = None):
+    """The plain form: one system per request, one request at a time, first
+    come first served.  Each request's service time (set-up, k-means
+    initialisation, steps, state read-back) is measured; completion times
+    follow from the arrival times and the FIFO order."""
+    order = sorted(range(len(jobs)), key=lambda i: jobs[i]["arrival_s"])
+    rec = [None] * len(jobs)
+    states = [None] * len(jobs)
+    clock = 0.0
+    busy = 0.0
+    work = 0
+    for i in order:
+        j = jobs[i]
+        t = time.perf_counter()
+        g = System(j["params"], stream=stream)
+        g.load_membrane(j["mem"])
+        g.init_cells()
+        g.integrate(j["steps"])
+        st = g.state()
+        g.close()
+        service = time.perf_counter() - t
+        if keep_states:
+            states[i] = st
+        start = max(clock, j["arrival_s"])
+        clock = start + service
+        busy += service
+        work += j["mem"].n * j["steps"]
+        rec[i] = {"arrival_s": j["arrival_s"], "start_s": start, "done_s": clock, "service_s": service,
+                  "latency_s": clock - j["arrival_s"]}
+    summary = _percentiles([r["latency_s"] for r in rec])
+    summary.update({"makespan_s": clock, "busy_s": busy, "particle_steps": work, "particle_steps_per_s": work / busy})
+    return rec, summary, states

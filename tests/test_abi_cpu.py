@@ -70,3 +70,25 @@ def test_null_handles_are_rejected(lib):
     assert L.orbc_compute_forces(None, None) == _native.ORBC_E_ARG
     assert L.orbc_last_error(None) == b"null handle"
     L.orbc_destroy(None)
+
+
+def test_arena_null_handles_and_arguments_are_rejected(lib):
+    from paper_1701_02059_gb300 import _native
+    L = _native.load()
+    h = C.c_void_p()
+    assert L.orbc_arena_create(0, 0, None, C.byref(h)) == _native.ORBC_E_ARG       # no budget
+    assert L.orbc_arena_create(1 << 30, 7, None, C.byref(h)) == _native.ORBC_E_ARG  # unknown precision
+    assert L.orbc_arena_create(1 << 30, 0, None, None) == _native.ORBC_E_ARG
+    assert not h
+    n = C.c_int(0)
+    assert L.orbc_arena_run(None, 1, 1, C.byref(n)) == _native.ORBC_E_ARG
+    assert L.orbc_arena_poll(None, None, 0, C.byref(n)) == _native.ORBC_E_ARG
+    assert L.orbc_arena_retire(None, 0, None, None, None, None, None) == _native.ORBC_E_ARG
+    slot = C.c_int(5)
+    p = _native.default_params()
+    assert L.orbc_arena_admit(None, C.byref(p), 1, None, None, None, None, None, None, 0, None, None, None, 1,
+                              C.byref(slot)) == _native.ORBC_E_ARG
+    assert L.orbc_arena_info(None, None, None, None, None, None) == _native.ORBC_E_ARG
+    assert L.orbc_arena_launch_count(None) == -1
+    assert L.orbc_arena_last_error(None) == b"null handle"
+    L.orbc_arena_destroy(None)

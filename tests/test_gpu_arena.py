@@ -1,0 +1,149 @@
+"""Batched arena on the GPU: instances of uneven size packed into one batch,
+admitted while others run, stepped by graph replay, retired when done.
+
+The batch only concatenates per-instance work (per-cell kernels, per-
+particle integrator, exact integer force sums, noise keyed by instance, id
+and step), so every instance must come out bit-identical to the same
+membrane run alone through the plain system API for the same number of
+steps.  The plain system itself is held to the FP64 oracle by
+test_gpu_parity.py.
+"""
+import numpy as np
+import pytest
+
+from synth import membranes as M
+
+pytestmark = pytest.mark.gpu
+
+G = pytest.importorskip("paper_1701_02059_gb300")
+from paper_1701_02059_gb300 import _native  # noqa: E402
+
+
+def members():
+    """Three uneven membranes: flat patches and a closed vesicle, each with
+    its own temperature, seed and Philox instance word."""
+    a = M.flat_patch_2304(seed=11)
+    b = M.vesicle(3000, 12, kT=0.15, f=2, chain_beads=5, n_centroids=50)
+    c = M.patch(3, 13, kT=0.25, n_centroids=85)
+    return [a, b, c]
+
+
+def params(mem, i, precision=G.F32_FORCE_F64_STATE):
+    return G.make_params(kT=mem.kT, n_centroids=mem.n_centroids, box=mem.box, periodic=mem.periodic,
+                         seed=1000 + i, instance=i, precision=precision)
+
+
+def alone(mem, i, nsteps, precision=G.F32_FORCE_F64_STATE):
+    g = G.System(params(mem, i, precision))
+    g.load_membrane(mem)
+    g.init_cells()
+    g.integrate(nsteps)
+    st = g.state()
+    g.close()
+    return st
+
+
+def assert_same(a, b):
+    for k in ("pos", "vel", "ori", "angvel"):
+        assert np.array_equal(a[k], b[k]), f"{k}: max |diff| {np.abs(a[k] - b[k]).max()}"
+    assert a["step"] == b["step"]
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_continuous_batching_equals_alone(graphs):
+    mems = members()
+    targets = [7, 12, 20]
+    ar = G.Arena(8 << 30)
+    s0 = ar.admit(params(mems[0], 0), mems[0], targets[0])
+    s1 = ar.admit(params(mems[1], 1), mems[1], targets[1])
+    assert ar.info()["pending"] == 2
+    done = {}
+    # first batch: instances 0 and 1, at most 5 steps per call
+    assert ar.run(5, graphs) == 5
+    assert ar.info()["resident"] == 2
+    # instance 2 arrives while the others are resident
+    s2 = ar.admit(params(mems[2], 2), mems[2], targets[2])
+    slots = {s0: 0, s1: 1, s2: 2}
+    calls = 0
+    while len(done) < 3:
+        ran = ar.run(5, graphs)
+        calls += 1
+        assert calls < 20
+        for s in ar.poll():
+            done[slots[s]] = ar.retire(s)
+        if ran == 0:
+            assert ar.info()["resident"] == 0
+    assert ar.info() == {"resident": 0, "pending": 0, "done": 0, "particles": 0, "bytes": 0}
+    assert ar.launch_count() > 0
+    for i, mem in enumerate(mems):
+        assert done[i]["step"] == targets[i]
+        assert_same(done[i], alone(mem, i, targets[i]))
+    ar.close()
+
+
+def test_fp64_arena_equals_alone():
+    mems = members()[:2]
+    ar = G.Arena(8 << 30, precision=G.F64_ALL)
+    slots = [ar.admit(params(m, i, G.F64_ALL), m, 6) for i, m in enumerate(mems)]
+    assert ar.run(10) == 6
+    got = {s: ar.retire(s) for s in ar.poll()}
+    for i, m in enumerate(mems):
+        assert_same(got[slots[i]], alone(m, i, 6, G.F64_ALL))
+
+
+def test_admission_respects_the_budget():
+    mem = M.flat_patch_2304(seed=3)
+    ar = G.Arena(8 << 30)
+    s = ar.admit(params(mem, 0), mem, 3)
+    per_instance = ar.info()["bytes"]
+    assert per_instance > 0
+    ar.close()
+    # room for one instance only
+    tight = G.Arena(int(per_instance * 1.5))
+    s = tight.admit(params(mem, 0), mem, 3)
+    with pytest.raises(G.OrbcError) as e:
+        tight.admit(params(mem, 1), mem, 3)
+    assert e.value.code == _native.ORBC_E_NOMEM
+    assert tight.run(10) == 3
+    assert tight.poll() == [s]
+    tight.retire(s)
+    # the freed budget admits the next request
+    s2 = tight.admit(params(mem, 1), mem, 2)
+    assert tight.run(10) == 2
+    assert tight.poll() == [s2]
+    tight.close()
+
+
+def test_arena_rejects_invalid_requests():
+    mem = M.flat_patch_2304(seed=4)
+    ar = G.Arena(8 << 30)
+    with pytest.raises(G.OrbcError) as e:
+        ar.admit(params(mem, 0, G.F64_ALL), mem, 3)        # precision differs from the arena's
+    assert e.value.code == _native.ORBC_E_ARG
+    with pytest.raises(G.OrbcError) as e:
+        ar.admit(params(mem, 0), mem, 0)                    # no steps
+    assert e.value.code == _native.ORBC_E_ARG
+    with pytest.raises(G.OrbcError) as e:
+        ar.run(0)
+    assert e.value.code == _native.ORBC_E_ARG
+    with pytest.raises(G.OrbcError) as e:
+        ar.retire(7)                                        # no such finished slot
+    assert e.value.code == _native.ORBC_E_ARG
+    assert ar.run(3) == 0                                   # nothing resident
+    ar.close()
+
+
+def test_overlapping_instances_stay_separate():
+    """Five vesicles of the same radius around the same origin, with
+    instance boundaries inside warps: the batch must never let one
+    instance's particles or cells meet another's."""
+    mems = [M.vesicle(3000, 40 + i, kT=0.2, f=2, chain_beads=5, n_centroids=60) for i in range(5)]
+    assert any(m.n % 32 for m in mems)
+    ar = G.Arena(8 << 30)
+    slots = [ar.admit(params(m, i), m, 8) for i, m in enumerate(mems)]
+    assert ar.run(3) == 3
+    assert ar.run(10) == 5
+    got = {s: ar.retire(s) for s in ar.poll()}
+    for i, m in enumerate(mems):
+        assert_same(got[slots[i]], alone(m, i, 8))
+    ar.close()
