@@ -8,10 +8,14 @@
 //   1. the mirrors of every neighbouring cell (contiguous after the sort) are
 //      staged in shared memory by 1-D bulk async copies (TMA) completing on
 //      an mbarrier, then moved into the cell's own frame: an exact int32
-//      offset (wrap-around arithmetic) and an FP32 copy for filtering;
-//   2. each lane owns one particle i and filters every staged candidate j
-//      with FP32 distances (band 1e-4 sigma), appending hits to a per-lane
-//      queue in shared memory;
+//      offset (wrap-around arithmetic) and an FP32 copy rotated into the
+//      cell's tangent frame (normal = mean lipid director) for filtering;
+//   2. the cell's particles are split into compact groups of <= 32 along
+//      their longer tangent extent; each group's warps cull the staged
+//      particles against the group's bounding box (r_s + band) into a
+//      candidate list, then every lane tests the same candidate at once
+//      (broadcast reads) against its own particle, appending hits to a
+//      per-lane queue in shared memory;
 //   3. queued pairs are evaluated with the exact integer displacement
 //      (2^-26 sigma), the type-pair cutoff decided in FP64 inside a 1e-6 sigma
 //      band, and the FP32 (or FP64) potential; force and torque on i are
@@ -29,9 +33,7 @@ namespace orbc {
 constexpr int kPairThreads = 128;
 constexpr int kStageCap = 544;     // staged particles per pass
 constexpr int kQCap = 32;          // queued hits per lane before a flush
-constexpr int kMaxBins = 512;      // spatial bins of the staged particles (in-CTA counting sort)
-static_assert(kStageCap <= 1024 && kMaxBins <= 8192, "bin and rank packing in the staged record");
-constexpr int kMaxNbr = 64;        // neighbouring cells per pass
+constexpr int kMaxNbr = 32;        // neighbouring cells per pass (one per lane of the set-up warp)
 constexpr float kFilterBand = 1e-4f;
 constexpr float kCutBand = 1e-6f;
 
@@ -319,37 +321,38 @@ __device__ inline T lipid_dispatch(const Inst& I, T dx, T dy, T dz, T r2, T nix,
     }
 }
 
-// reaction of a pair on j (Newton's third law inside the CTA's own cell):
-// exact split integers added to the shared accumulators of j
-__device__ inline void split_parts(float f, int& h, int& l) {
-    const float t = fmaf(f, 4096.0f, kMagic);
-    const float hf = t - kMagic;
-    const float r = fmaf(f, 4096.0f, -hf);
-    const float u = fmaf(r, 1048576.0f, kMagic);
-    h = __float_as_int(t) - kMagicBits;
-    l = __float_as_int(u) - kMagicBits;
-}
+
+// Rotation into the tangent frame of a cell: rows e1, e2, n.
+struct Frame {
+    float r[9];
+    __device__ inline void apply(float x, float y, float z, float& a, float& b, float& c) const {
+        a = fmaf(r[0], x, fmaf(r[1], y, r[2] * z));
+        b = fmaf(r[3], x, fmaf(r[4], y, r[5] * z));
+        c = fmaf(r[6], x, fmaf(r[7], y, r[8] * z));
+    }
+};
 
 template <typename T, bool ENERGY, bool DUMP, int Z>
 __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __restrict__ energy /* [B][8] */,
                                                             unsigned* __restrict__ dump,
                                                             unsigned long long* __restrict__ dump_count,
                                                             long long dump_cap) {
-    // sy: staged mirrors as copied by TMA (int4: x - c at 2^-26 sigma, type)
-    // sY: the same particles in the cell-k frame (float4), counting-sorted by
-    //     spatial bin; w = type | block << 8 | staged index << 14
+    // sy: staged mirrors, after staging in the cell-k frame (exact int32,
+    //     2^-26 sigma), w = type
+    // sY: the same particles in FP32, rotated into the tangent frame
+    // so: directors, w = global slot
     __shared__ alignas(16) int4 sy[kStageCap];
     __shared__ alignas(16) float4 sY[kStageCap];
-    __shared__ alignas(16) float4 so[kStageCap];     // director, w = global slot
-    __shared__ int bstart[kMaxBins + 1];
-    __shared__ int rx[kPairThreads][12];               // Newton-3 reactions on the own cell (split ints)
-    // hit queues during the pair loop; split-combination buffer afterwards
-    __shared__ alignas(16) unsigned char scratch[kPairThreads / 32 * kQCap * 32 * 2];
+    __shared__ alignas(16) float4 so[kStageCap];
+    __shared__ unsigned short cand[kPairThreads / 32][kStageCap];   // per-warp candidate list
+    __shared__ unsigned short qbuf[kPairThreads / 32][kQCap][32];   // per-lane hit queues
     __shared__ NbrInfo nb[kMaxNbr];
+    __shared__ float skey[kPairThreads];
+    __shared__ unsigned char sorder[kPairThreads];
+    __shared__ float sfr[kPairThreads / 32][4];
     __shared__ unsigned long long bar;
-    __shared__ int s_nstage, s_next, s_next_off, s_self, s_self_lo, s_self_hi, s_dim[3];
-    __shared__ float s_lo[3], s_binv;
-    unsigned short (*qbuf)[kQCap][32] = reinterpret_cast<unsigned short (*)[kQCap][32]>(scratch);
+    __shared__ int s_nstage, s_next, s_next_off, s_self, s_self_lo, s_self_hi, s_total;
+    __shared__ Frame s_frame;
 
     const int k = blockIdx.x;
     const int b = find_inst(v.inst_k0, v.B, k);
@@ -365,37 +368,128 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
     const float ll_lo = (rcl - kCutBand) * (rcl - kCutBand), ll_hi = (rcl + kCutBand) * (rcl + kCutBand);
     const float w_lo = (rcw - kCutBand) * (rcw - kCutBand), w_hi = (rcw + kCutBand) * (rcw + kCutBand);
     const float p_lo = (rcp - kCutBand) * (rcp - kCutBand), p_hi = (rcp + kCutBand) * (rcp + kCutBand);
-    const float rmargin = (float)(2.0 * I.skin) + 1e-3f;   // particles lie within R_l (+ skin) of their centroid
     const size_t N = v.N;
     const int zc = (Z > 0) ? Z : I.zeta;
-    const int nk = ce - cs;
     unsigned phase = 0;
     if (tid == 0) mbar_init(&bar, 1);
     __syncthreads();
 
     for (int it0 = cs; it0 < ce; it0 += kPairThreads) {
-        const int nti = min(kPairThreads, ce - it0);           // particles of this i-tile
-        const int groups = (nti + 31) >> 5;                    // warps for one pass over i
+        const int nti = min(kPairThreads, ce - it0);            // particles of this i-tile
+        const int groups = (nti + 31) >> 5;                     // compact groups of <= 32
         const int nsplit = (groups == 1) ? 4 : (groups == 2 ? 2 : 1);
         const int igrp = warp % groups;
         const int jsplit = warp / groups;
         const bool wactive = jsplit < nsplit;
-        const int li = igrp * 32 + lane;
-        const bool ivalid = wactive && li < nti;
-        const int pi = it0 + li;
-        const bool whole_cell = (it0 == cs) && (nti == nk);   // Newton-3 possible inside the own cell
+        const int gs = (nti + groups - 1) / groups;             // balanced group size
+
+        // ---- tangent frame of the tile: normal = mean lipid director
+        {
+            float sx = 0.f, sy_ = 0.f, sz = 0.f;
+            if (tid < nti) {
+                const int4 q = v.mq[it0 + tid];
+                if ((q.w & 0xff) == kLipid) {
+                    const float4 o = v.mo[it0 + tid];
+                    sx = o.x; sy_ = o.y; sz = o.z;
+                }
+            }
+            for (int off = 16; off; off >>= 1) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, off);
+                sy_ += __shfl_xor_sync(0xffffffffu, sy_, off);
+                sz += __shfl_xor_sync(0xffffffffu, sz, off);
+            }
+            if (lane == 0) { sfr[warp][0] = sx; sfr[warp][1] = sy_; sfr[warp][2] = sz; }
+            __syncthreads();
+            if (tid == 0) {
+                float nx = 0.f, ny = 0.f, nz = 0.f;
+                for (int w = 0; w < kPairThreads / 32; w++) { nx += sfr[w][0]; ny += sfr[w][1]; nz += sfr[w][2]; }
+                float nn = sqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+                if (!(nn > 1e-3f)) { nx = 0.f; ny = 0.f; nz = 1.f; nn = 1.f; }
+                nx /= nn; ny /= nn; nz /= nn;
+                // e1 = normalise(n x axis of the smallest |n| component), e2 = n x e1
+                const float ax = fabsf(nx), ay = fabsf(ny), az = fabsf(nz);
+                float ux, uy, uz;
+                if (ax <= ay && ax <= az) { ux = 0.f; uy = nz; uz = -ny; }
+                else if (ay <= az) { ux = -nz; uy = 0.f; uz = nx; }
+                else { ux = ny; uy = -nx; uz = 0.f; }
+                const float un = sqrtf(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+                ux /= un; uy /= un; uz /= un;
+                const float vx = ny * uz - nz * uy, vy = nz * ux - nx * uz, vz = nx * uy - ny * ux;
+                Frame f;
+                f.r[0] = ux; f.r[1] = uy; f.r[2] = uz;
+                f.r[3] = vx; f.r[4] = vy; f.r[5] = vz;
+                f.r[6] = nx; f.r[7] = ny; f.r[8] = nz;
+                s_frame = f;
+            }
+            __syncthreads();
+        }
+        const Frame F = s_frame;
+
+        // ---- compact groups: rank the tile along its longer tangent extent
+        if (groups > 1) {
+            float ya = 0.f, yb = 0.f;
+            if (tid < nti) {
+                const int4 q = v.mq[it0 + tid];
+                float c;
+                F.apply(q.x * kMirrorUnit, q.y * kMirrorUnit, q.z * kMirrorUnit, ya, yb, c);
+            }
+            float lo_a = tid < nti ? ya : 3.0e38f, hi_a = tid < nti ? ya : -3.0e38f;
+            float lo_b = tid < nti ? yb : 3.0e38f, hi_b = tid < nti ? yb : -3.0e38f;
+            for (int off = 16; off; off >>= 1) {
+                lo_a = fminf(lo_a, __shfl_xor_sync(0xffffffffu, lo_a, off));
+                hi_a = fmaxf(hi_a, __shfl_xor_sync(0xffffffffu, hi_a, off));
+                lo_b = fminf(lo_b, __shfl_xor_sync(0xffffffffu, lo_b, off));
+                hi_b = fmaxf(hi_b, __shfl_xor_sync(0xffffffffu, hi_b, off));
+            }
+            if (lane == 0) { sfr[warp][0] = lo_a; sfr[warp][1] = hi_a; sfr[warp][2] = lo_b; sfr[warp][3] = hi_b; }
+            __syncthreads();
+            float ea_lo = 3.0e38f, ea_hi = -3.0e38f, eb_lo = 3.0e38f, eb_hi = -3.0e38f;
+            for (int w = 0; w < kPairThreads / 32; w++) {
+                ea_lo = fminf(ea_lo, sfr[w][0]); ea_hi = fmaxf(ea_hi, sfr[w][1]);
+                eb_lo = fminf(eb_lo, sfr[w][2]); eb_hi = fmaxf(eb_hi, sfr[w][3]);
+            }
+            const bool use_a = (ea_hi - ea_lo) >= (eb_hi - eb_lo);
+            if (tid < nti) skey[tid] = use_a ? ya : yb;
+            __syncthreads();
+            if (tid < nti) {
+                const float kt = skey[tid];
+                int rank = 0;
+                for (int s2 = 0; s2 < nti; s2++) {
+                    const float ks = skey[s2];
+                    rank += (ks < kt || (ks == kt && s2 < tid)) ? 1 : 0;
+                }
+                sorder[rank] = (unsigned char)tid;
+            }
+            __syncthreads();
+        } else {
+            if (tid < nti) sorder[tid] = (unsigned char)tid;
+            __syncthreads();
+        }
+
+        // ---- this lane's particle
+        const int r = igrp * gs + lane;
+        const bool ivalid = wactive && lane < gs && r < nti;
+        int ti = 0, pi = -1;
         int4 qi = make_int4(0, 0, 0, 0);
         float4 oi = make_float4(0, 0, 0, 0);
-        float yix = 0, yiy = 0, yiz = 0;
+        float yix = 0.f, yiy = 0.f, yiz = 0.f;
         unsigned idi = 0;
         if (ivalid) {
+            pi = it0 + sorder[r];
             qi = v.mq[pi];
             oi = v.mo[pi];
-            yix = qi.x * kMirrorUnit; yiy = qi.y * kMirrorUnit; yiz = qi.z * kMirrorUnit;
+            ti = qi.w & 0xff;
+            F.apply(qi.x * kMirrorUnit, qi.y * kMirrorUnit, qi.z * kMirrorUnit, yix, yiy, yiz);
             if (DUMP) idi = v.id[pi];
         }
-        for (int q = tid; q < kPairThreads * 12; q += kPairThreads) (&rx[0][0])[q] = 0;
-        const int ti = qi.w & 0xff;
+        // group bounding box in the tangent frame, widened by the search radius
+        float blo[3] = {ivalid ? yix : 3.0e38f, ivalid ? yiy : 3.0e38f, ivalid ? yiz : 3.0e38f};
+        float bhi[3] = {ivalid ? yix : -3.0e38f, ivalid ? yiy : -3.0e38f, ivalid ? yiz : -3.0e38f};
+        for (int a = 0; a < 3; a++)
+            for (int off = 16; off; off >>= 1) {
+                blo[a] = fminf(blo[a], __shfl_xor_sync(0xffffffffu, blo[a], off));
+                bhi[a] = fmaxf(bhi[a], __shfl_xor_sync(0xffffffffu, bhi[a], off));
+            }
         Acc<T> acc;
         acc.zero();
         T up = 0, vir = 0;
@@ -407,7 +501,7 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
             if (warp == 0) {
                 // one lane per neighbouring cell: counts, offsets, staging slots
                 const int nn = na + lane;
-                const bool has = nn < a1 && lane < kMaxNbr;
+                const bool has = nn < a1;
                 int l = 0, st = 0, c = 0;
                 if (has) {
                     l = v.adj[nn];
@@ -427,31 +521,22 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                 const int m = __popc(fm) + (pm ? 1 : 0);
                 const bool staged = fits || part;
                 const int take = part ? kStageCap - excl : c;
-                float blo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, bhi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
                 if (staged) {
-                    long long dx = minimg_q(v.cq[l] - ckx, I.boxq[0], I.periodic[0]);
-                    long long dy = minimg_q(v.cq[(size_t)v.Ktot + l] - cky, I.boxq[1], I.periodic[1]);
-                    long long dz = minimg_q(v.cq[(size_t)2 * v.Ktot + l] - ckz, I.boxq[2], I.periodic[2]);
-                    long long ox = (dx + (1ll << (kMirrorShift - 1))) >> kMirrorShift;
-                    long long oy = (dy + (1ll << (kMirrorShift - 1))) >> kMirrorShift;
-                    long long oz = (dz + (1ll << (kMirrorShift - 1))) >> kMirrorShift;
+                    const long long dx = minimg_q(v.cq[l] - ckx, I.boxq[0], I.periodic[0]);
+                    const long long dy = minimg_q(v.cq[(size_t)v.Ktot + l] - cky, I.boxq[1], I.periodic[1]);
+                    const long long dz = minimg_q(v.cq[(size_t)2 * v.Ktot + l] - ckz, I.boxq[2], I.periodic[2]);
+                    const long long ox = (dx + (1ll << (kMirrorShift - 1))) >> kMirrorShift;
+                    const long long oy = (dy + (1ll << (kMirrorShift - 1))) >> kMirrorShift;
+                    const long long oz = (dz + (1ll << (kMirrorShift - 1))) >> kMirrorShift;
                     NbrInfo inf;
                     inf.base = excl; inf.cnt = take; inf.start = st;
                     inf.ox = (int)(unsigned)(unsigned long long)ox;
                     inf.oy = (int)(unsigned)(unsigned long long)oy;
                     inf.oz = (int)(unsigned)(unsigned long long)oz;
-                    inf.fx = (float)ox * kMirrorUnit; inf.fy = (float)oy * kMirrorUnit; inf.fz = (float)oz * kMirrorUnit;
+                    inf.fx = 0.f; inf.fy = 0.f; inf.fz = 0.f;
                     nb[lane] = inf;
-                    const float Rl = (float)v.R[l] + rmargin;
-                    blo[0] = inf.fx - Rl; blo[1] = inf.fy - Rl; blo[2] = inf.fz - Rl;
-                    bhi[0] = inf.fx + Rl; bhi[1] = inf.fy + Rl; bhi[2] = inf.fz + Rl;
                 }
                 const unsigned selfm = __ballot_sync(0xffffffffu, staged && l == k);
-                for (int a = 0; a < 3; a++)
-                    for (int off = 16; off; off >>= 1) {
-                        blo[a] = fminf(blo[a], __shfl_xor_sync(0xffffffffu, blo[a], off));
-                        bhi[a] = fmaxf(bhi[a], __shfl_xor_sync(0xffffffffu, bhi[a], off));
-                    }
                 const int total = __shfl_sync(0xffffffffu, excl + take, max(m - 1, 0));
                 // where the next pass starts: after the last fully staged
                 // neighbour, or inside the partially staged one
@@ -476,24 +561,10 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                 }
                 if (lane == 0) {
                     s_nstage = m;
+                    s_total = m > 0 ? total : 0;
                     s_next = nxt;
                     s_next_off = nxo;
                     s_self = sb; s_self_lo = slo; s_self_hi = shi;
-                    float bsz = rs_b * 1.0001f;
-                    int dim[3] = {1, 1, 1};
-                    if (m > 0) {
-                        for (int tries = 0; tries < 40; tries++) {
-                            long long prod = 1;
-                            for (int a = 0; a < 3; a++) {
-                                dim[a] = max(1, min(kMaxBins, (int)floorf((bhi[a] - blo[a]) / bsz) + 1));
-                                prod *= dim[a];
-                            }
-                            if (prod <= kMaxBins) break;
-                            bsz *= 1.25f;
-                        }
-                    }
-                    for (int a = 0; a < 3; a++) { s_lo[a] = blo[a]; s_dim[a] = dim[a]; }
-                    s_binv = 1.0f / bsz;
                 }
                 if (m > 0) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -505,14 +576,12 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                     }
                 }
             }
-            for (int q = tid; q <= kMaxBins; q += kPairThreads) bstart[q] = 0;
             __syncthreads();
             const int m = s_nstage;
+            const int total = s_total;
             const int next = s_next, next_off = s_next_off;
             if (m == 0) { na = next; na_off = next_off; continue; }
             const int sself = s_self, sslo = s_self_lo, sshi = s_self_hi;
-            // Newton-3 inside the own cell when the whole cell is staged and in this i-tile
-            const bool n3 = sizeof(T) == 4 && whole_cell && sslo >= 0 && (sshi - sslo) == nk;
             int selfj = (sslo >= 0 && ivalid) ? sself + (pi - cs) : -1;
             if (selfj < sslo || selfj >= sshi) selfj = -1;
             bool ok = mbar_wait_bounded(&bar, phase, v.status);
@@ -522,80 +591,64 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                 return;
             }
             phase ^= 1u;
-            const float blo0 = s_lo[0], blo1 = s_lo[1], blo2 = s_lo[2], binv = s_binv;
-            const int dim0 = s_dim[0], dim1 = s_dim[1], dim2 = s_dim[2];
 
-            // ---- in-CTA counting sort of the staged particles by spatial bin
+            // ---- staged particles into the cell-k frame (exact) and the
+            //      tangent frame (FP32)
             for (int q = 0; q < m; q++) {
                 const NbrInfo inf = nb[q];
                 for (int j = inf.base + tid; j < inf.base + inf.cnt; j += kPairThreads) {
-                    const int4 r = sy[j];
-                    const float y0 = fmaf((float)r.x, kMirrorUnit, inf.fx), y1 = fmaf((float)r.y, kMirrorUnit, inf.fy),
-                                y2 = fmaf((float)r.z, kMirrorUnit, inf.fz);
-                    const int bx = min(dim0 - 1, max(0, (int)floorf((y0 - blo0) * binv)));
-                    const int by = min(dim1 - 1, max(0, (int)floorf((y1 - blo1) * binv)));
-                    const int bz = min(dim2 - 1, max(0, (int)floorf((y2 - blo2) * binv)));
-                    const int bi = (bz * dim1 + by) * dim0 + bx;
-                    // type | rank in bin << 8 | bin << 18, kept in the staged record
-                    sy[j].w = (r.w & 0xff) | (atomicAdd(&bstart[bi], 1) << 8) | (bi << 18);
-                }
-            }
-            __syncthreads();
-            if (warp == 0) {
-                const int nbins = dim0 * dim1 * dim2;
-                int carry = 0;
-                for (int c0 = 0; c0 < nbins; c0 += 32) {
-                    const int x = (c0 + lane < nbins) ? bstart[c0 + lane] : 0;
-                    int incl = x;
-                    for (int off = 1; off < 32; off <<= 1) {
-                        const int t = __shfl_up_sync(0xffffffffu, incl, off);
-                        if (lane >= off) incl += t;
-                    }
-                    if (c0 + lane < nbins) bstart[c0 + lane] = carry + incl - x;
-                    carry += __shfl_sync(0xffffffffu, incl, 31);
-                }
-                if (lane == 0) bstart[nbins] = carry;
-            }
-            __syncthreads();
-            for (int q = 0; q < m; q++) {
-                const NbrInfo inf = nb[q];
-                for (int j = inf.base + tid; j < inf.base + inf.cnt; j += kPairThreads) {
-                    const int4 r = sy[j];
+                    int4 rj = sy[j];
+                    rj.x = (int)((unsigned)rj.x + (unsigned)inf.ox);
+                    rj.y = (int)((unsigned)rj.y + (unsigned)inf.oy);
+                    rj.z = (int)((unsigned)rj.z + (unsigned)inf.oz);
+                    sy[j] = rj;
                     float4 y;
-                    y.x = fmaf((float)r.x, kMirrorUnit, inf.fx);
-                    y.y = fmaf((float)r.y, kMirrorUnit, inf.fy);
-                    y.z = fmaf((float)r.z, kMirrorUnit, inf.fz);
-                    y.w = __int_as_float((r.w & 0xff) | (q << 8) | (j << 14));
-                    sY[bstart[r.w >> 18] + ((r.w >> 8) & 0x3ff)] = y;
+                    F.apply(rj.x * kMirrorUnit, rj.y * kMirrorUnit, rj.z * kMirrorUnit, y.x, y.y, y.z);
+                    y.w = 0.f;
+                    sY[j] = y;
                 }
             }
             __syncthreads();
 
-            // filter (the 27 bins around i) + evaluate
             if (wactive) {
-                const int ibx = min(dim0 - 1, max(0, (int)floorf((yix - blo0) * binv)));
-                const int iby = min(dim1 - 1, max(0, (int)floorf((yiy - blo1) * binv)));
-                const int ibz = min(dim2 - 1, max(0, (int)floorf((yiz - blo2) * binv)));
-                // candidates of the own cell: with Newton-3 only those after i
-                const int jlo_self = n3 ? selfj + 1 : -1;
+                // ---- candidates: staged particles within r_s (+ band) of the
+                //      group's box; chunks of 32 shared round-robin by the
+                //      warps of the group
+                int cnt = 0;
+                for (int c0 = jsplit * 32; c0 < total; c0 += nsplit * 32) {
+                    const int j = c0 + lane;
+                    bool in = false;
+                    if (j < total) {
+                        const float4 y = sY[j];
+                        const float ex = fmaxf(fmaxf(blo[0] - y.x, y.x - bhi[0]), 0.f);
+                        const float ey = fmaxf(fmaxf(blo[1] - y.y, y.y - bhi[1]), 0.f);
+                        const float ez = fmaxf(fmaxf(blo[2] - y.z, y.z - bhi[2]), 0.f);
+                        in = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < rs2f;
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, in);
+                    if (in) cand[warp][cnt + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)j;
+                    cnt += __popc(bal);
+                }
+                __syncwarp();
+
                 int qn = 0;
                 auto flush = [&]() {
                     int qmax = qn;
                     for (int off = 16; off; off >>= 1) qmax = max(qmax, __shfl_xor_sync(0xffffffffu, qmax, off));
                     for (int t = 0; t < qmax; t++) {
                         if (t >= qn) continue;
-                        const int sp = (int)qbuf[warp][t][lane];
-                        const int wbits = __float_as_int(sY[sp].w);
-                        const int tj = wbits & 0xff, qb = (wbits >> 8) & 0x3f, j = wbits >> 14;
+                        const int j = (int)qbuf[warp][t][lane];
+                        const int4 mj = sy[j];
                         const float4 oj = so[j];
                         const int pj = __float_as_int(oj.w);
-                        const int4 mj = sy[j];
+                        const int tj = mj.w & 0xff;
                         const bool ll = (ti == kLipid) && (tj == kLipid);
                         const int cls = ll ? 0 : ((ti == kLipid || tj == kLipid) ? 1 : 2);
-                        const int dxq = (int)((unsigned)mj.x + (unsigned)nb[qb].ox - (unsigned)qi.x);
-                        const int dyq = (int)((unsigned)mj.y + (unsigned)nb[qb].oy - (unsigned)qi.y);
-                        const int dzq = (int)((unsigned)mj.z + (unsigned)nb[qb].oz - (unsigned)qi.z);
-                        const float dxf = (float)dxq * kMirrorUnit, dyf = (float)dyq * kMirrorUnit, dzf = (float)dzq * kMirrorUnit;
+                        const int dxq = (int)((unsigned)mj.x - (unsigned)qi.x);
+                        const int dyq = (int)((unsigned)mj.y - (unsigned)qi.y);
+                        const int dzq = (int)((unsigned)mj.z - (unsigned)qi.z);
+                        const float dxf = (float)dxq * kMirrorUnit, dyf = (float)dyq * kMirrorUnit,
+                                    dzf = (float)dzq * kMirrorUnit;
                         const float r2f = fmaf(dxf, dxf, fmaf(dyf, dyf, dzf * dzf));
                         const float lo = cls == 0 ? ll_lo : (cls == 1 ? w_lo : p_lo);
                         const float hi = cls == 0 ? ll_hi : (cls == 1 ? w_hi : p_hi);
@@ -604,9 +657,7 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                         if (!in) in = exact_inside(v, I, pi, pj, cls);
                         if (in && cls == 2 && is_excluded(v, I, v.id[pi], v.id[pj])) in = false;
                         if (!in) continue;
-                        const bool react = n3 && j >= sslo && j < sshi;   // j in the own cell: reaction here
                         T fx = 0, fy = 0, fz = 0, tx = 0, ty = 0, tz = 0, U;
-                        T tjv[3] = {0, 0, 0};
                         T dx, dy, dz, r2;
                         if constexpr (sizeof(T) == 4) {
                             dx = dxf; dy = dyf; dz = dzf; r2 = r2f;
@@ -627,78 +678,37 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                                 njz = grid_to_double(v.nq[2 * N + pj]);
                             }
                             U = lipid_dispatch<T>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz, zc,
-                                                  react ? tjv : (T*)nullptr);
+                                                  (T*)nullptr);
                         } else {
                             U = wca_terms<T>(I, cls == 2, dx, dy, dz, r2, fx, fy, fz);
                         }
-                        if (!(fabs(fx) + fabs(fy) + fabs(fz) + fabs(tx) + fabs(ty) + fabs(tz) < (T)3.0e30))
-                            atomicOr(v.status, kStatusNaN);
                         acc.add_pair(v, pi, fx, fy, fz, tx, ty, tz);
-                        if constexpr (sizeof(T) == 4) {
-                            if (react) {
-                                // reaction on j (same cell, same i-tile): -F and tau_j
-                                const int lj = j - sself;
-                                const float fv[6] = {-(float)fx, -(float)fy, -(float)fz,
-                                                     (float)tjv[0], (float)tjv[1], (float)tjv[2]};
-                                for (int h3 = 0; h3 < 2; h3++) {
-                                    const float* w3 = fv + 3 * h3;
-                                    if (fabsf(w3[0]) + fabsf(w3[1]) + fabsf(w3[2]) < 1000.0f) {
-                                        for (int a = 0; a < 3; a++) {
-                                            int hh, ll2;
-                                            split_parts(w3[a], hh, ll2);
-                                            atomicAdd(&rx[lj][6 * h3 + 2 * a], hh);
-                                            atomicAdd(&rx[lj][6 * h3 + 2 * a + 1], ll2);
-                                        }
-                                    } else {
-                                        for (int a = 0; a < 3; a++)
-                                            atomicAdd((unsigned long long*)&v.Fbig[(size_t)(3 * h3 + a) * N + pj],
-                                                      (unsigned long long)__float2ll_rn(w3[a] * 4294967296.0f));
-                                        acc.used_big = true;
-                                    }
-                                }
-                            }
-                        }
                         if (ENERGY) {
-                            const T wgt = react ? (T)1 : (T)0.5;
-                            up += wgt * U;
-                            vir += wgt * -(dx * fx + dy * fy + dz * fz);
+                            up += (T)0.5 * U;
+                            vir += (T)0.5 * -(dx * fx + dy * fy + dz * fz);
                         }
                         if (DUMP) {
                             const unsigned idj = v.id[pj];
-                            if (idi < idj || react) {
-                                const unsigned a_ = min(idi, idj), b_ = max(idi, idj);
+                            if (idi < idj) {
                                 unsigned long long slot = atomicAdd(dump_count, 1ull);
-                                if ((long long)slot < dump_cap) { dump[2 * slot] = a_; dump[2 * slot + 1] = b_; }
+                                if ((long long)slot < dump_cap) { dump[2 * slot] = idi; dump[2 * slot + 1] = idj; }
                             }
                         }
                     }
                     qn = 0;
                     __syncwarp();
                 };
-                // the 27 neighbouring bins, interleaved across the warps sharing
-                // this i-group; a bin is scanned at most 8 candidates per lane
-                // between warp-uniform queue checks
-                for (int o = jsplit; o < 27; o += nsplit) {
-                    const int bx = ibx + (o % 3) - 1, by = iby + ((o / 3) % 3) - 1, bz = ibz + (o / 9) - 1;
-                    int sp = 0, e = 0;
-                    if (ivalid && bx >= 0 && by >= 0 && bz >= 0 && bx < dim0 && by < dim1 && bz < dim2) {
-                        const int bi = (bz * dim1 + by) * dim0 + bx;
-                        sp = bstart[bi];
-                        e = bstart[bi + 1];
-                    }
-                    while (__any_sync(0xffffffffu, sp < e)) {
-                        if (__any_sync(0xffffffffu, qn > kQCap - 8)) flush();
-#pragma unroll 4
-                        for (int u = 0; u < 8; u++) {
-                            if (sp >= e) break;
-                            const float4 y = sY[sp];
+                // ---- every lane tests the same candidate (broadcast reads)
+                for (int c = 0; c < cnt; c += 4) {
+                    if (__any_sync(0xffffffffu, qn > kQCap - 4)) flush();
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        if (c + u < cnt) {
+                            const int j = (int)cand[warp][c + u];
+                            const float4 y = sY[j];
                             const float ex = y.x - yix, ey = y.y - yiy, ez = y.z - yiz;
                             const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                            const int jj = __float_as_int(y.w) >> 14;
-                            const bool self_block = jj >= sslo && jj < sshi;
-                            const bool keep = self_block ? (n3 ? jj >= jlo_self : jj != selfj) : true;
-                            if (d2 < rs2f && keep) { qbuf[warp][qn][lane] = (unsigned short)sp; qn++; }
-                            sp++;
+                            if (ivalid && d2 < rs2f && j != selfj) { qbuf[warp][qn][lane] = (unsigned short)j; qn++; }
                         }
                     }
                 }
@@ -727,9 +737,9 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                     dx = grid_to_double(ddx); dy = grid_to_double(ddy); dz = grid_to_double(ddz);
                     r0 = v.br0_d[q]; kb = v.bkb_d[q];
                 }
-                const T r = sqrt(dx * dx + dy * dy + dz * dz);
-                const T dr = r - r0;
-                const T c = kb * dr / r;
+                const T rr = sqrt(dx * dx + dy * dy + dz * dz);
+                const T dr = rr - r0;
+                const T c = kb * dr / rr;
                 acc.add_bond(v, pi, c * dx, c * dy, c * dz);
                 if (ENERGY) {
                     ub += (T)0.25 * kb * dr * dr;
@@ -738,20 +748,22 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
             }
         }
 
-        // combine the j-splits and the Newton-3 reactions (exact integer sums) and write
+        // combine the warps of a group (exact integer sums) and write; the
+        // slot of a lane's particle in the tile is sorder[r]
         __syncthreads();
+        const int ts = ivalid ? (int)sorder[r] : -1;
         if constexpr (sizeof(T) == 4) {
             int (*red)[14] = reinterpret_cast<int (*)[14]>(&sY[0]);
             for (int q = tid; q < kPairThreads * 14; q += kPairThreads) (&red[0][0])[q] = 0;
             __syncthreads();
             if (ivalid) {
-                atomicAdd(&red[li][0], acc.f[0].h); atomicAdd(&red[li][1], acc.f[0].l);
-                atomicAdd(&red[li][2], acc.f[1].h); atomicAdd(&red[li][3], acc.f[1].l);
-                atomicAdd(&red[li][4], acc.f[2].h); atomicAdd(&red[li][5], acc.f[2].l);
-                atomicAdd(&red[li][6], acc.t[0].h); atomicAdd(&red[li][7], acc.t[0].l);
-                atomicAdd(&red[li][8], acc.t[1].h); atomicAdd(&red[li][9], acc.t[1].l);
-                atomicAdd(&red[li][10], acc.t[2].h); atomicAdd(&red[li][11], acc.t[2].l);
-                atomicAdd(&red[li][12], acc.nf); atomicAdd(&red[li][13], acc.nt);
+                atomicAdd(&red[ts][0], acc.f[0].h); atomicAdd(&red[ts][1], acc.f[0].l);
+                atomicAdd(&red[ts][2], acc.f[1].h); atomicAdd(&red[ts][3], acc.f[1].l);
+                atomicAdd(&red[ts][4], acc.f[2].h); atomicAdd(&red[ts][5], acc.f[2].l);
+                atomicAdd(&red[ts][6], acc.t[0].h); atomicAdd(&red[ts][7], acc.t[0].l);
+                atomicAdd(&red[ts][8], acc.t[1].h); atomicAdd(&red[ts][9], acc.t[1].l);
+                atomicAdd(&red[ts][10], acc.t[2].h); atomicAdd(&red[ts][11], acc.t[2].l);
+                atomicAdd(&red[ts][12], acc.nf); atomicAdd(&red[ts][13], acc.nt);
             }
             const bool any_big = __syncthreads_or(ivalid && acc.used_big);
             if (tid < nti) {
@@ -760,12 +772,11 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                 for (int a = 0; a < 3; a++) {
                     SplitAcc f; f.h = red[tid][2 * a]; f.l = red[tid][2 * a + 1];
                     SplitAcc t; t.h = red[tid][6 + 2 * a]; t.l = red[tid][6 + 2 * a + 1];
-                    long long fb = ((long long)rx[tid][2 * a] << 20) + (long long)rx[tid][2 * a + 1];
-                    long long tb = ((long long)rx[tid][6 + 2 * a] << 20) + (long long)rx[tid][6 + 2 * a + 1];
+                    long long fb = 0, tb = 0;
                     if (any_big) {
                         // written by atomics in L2: read past L1
-                        fb += __ldcg(&v.Fbig[(size_t)a * N + p]);
-                        tb += __ldcg(&v.Fbig[(size_t)(3 + a) * N + p]);
+                        fb = __ldcg(&v.Fbig[(size_t)a * N + p]);
+                        tb = __ldcg(&v.Fbig[(size_t)(3 + a) * N + p]);
                         v.Fbig[(size_t)a * N + p] = 0; v.Fbig[(size_t)(3 + a) * N + p] = 0;
                     }
                     v.F[a * N + p] = f.finish(nfr) + fb;
@@ -778,8 +789,8 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
             __syncthreads();
             if (ivalid)
                 for (int a = 0; a < 3; a++) {
-                    atomicAdd((unsigned long long*)&red64[li][a], (unsigned long long)acc.F(a));
-                    atomicAdd((unsigned long long*)&red64[li][3 + a], (unsigned long long)acc.Tq(a));
+                    atomicAdd((unsigned long long*)&red64[ts][a], (unsigned long long)acc.F(a));
+                    atomicAdd((unsigned long long*)&red64[ts][3 + a], (unsigned long long)acc.Tq(a));
                 }
             __syncthreads();
             if (tid < nti) {
@@ -810,7 +821,6 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
     }
 }
 
-// ---------------------------------------------------------------- host launchers
 // The pair kernel runs five CTAs per SM only with the whole unified L1 /
 // shared memory given to shared memory; ask for that once per process.
 template <typename Kern> static void prefer_shared(Kern k) {
