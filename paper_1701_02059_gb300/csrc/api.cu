@@ -54,7 +54,7 @@ View Ensemble::view() {
     v.type = d_type[cur_]; v.id = d_id[cur_];
     v.cell = d_cell; v.slot_of_id = d_slot_of_id;
     v.F = d_F; v.T = d_T; v.Fbig = d_Fbig;
-    v.mq = d_mq; v.mo = d_mo;
+    v.mq = d_mq; v.mo = d_mo; v.cnorm = d_cnorm; v.grank = d_grank;
     v.cq = d_cq; v.cell_start = d_cell_start; v.R = d_R; v.adj_ptr = d_adj_ptr; v.adj = d_adj; v.adj_cap = adj_cap;
     v.gstart = d_gstart; v.gcent = d_gcent; v.gcf = d_gcf;
     v.bptr = d_bptr; v.bpartner = d_bpartner; v.br0 = d_br0; v.bkb = d_bkb; v.br0_d = d_br0_d; v.bkb_d = d_bkb_d;
@@ -203,6 +203,8 @@ void Ensemble::alloc_core(const std::vector<int>& p0, const std::vector<int>& k0
     d_rmax = alloc<unsigned long long>(B);
     d_rho = alloc<float>(Ktot);
     d_cf = alloc<float4>(Ktot);
+    d_cnorm = alloc<float4>(Ktot);
+    d_grank = alloc<unsigned char>(N);
     d_dmax = alloc<unsigned>(B);
     prev_adj_valid_ = false;
     d_energy = alloc<long long>((size_t)8 * B);
@@ -421,9 +423,7 @@ void Ensemble::init_cells() {
 
 void Ensemble::compute_forces(bool energies) {
     if (!cells_valid) throw StateError("cells not initialised");
-    tic("pairs");
     launch_pairs(energies, false);
-    toc();
     if (energies) launch_kinetic();
     forces_valid = true;
 }
@@ -440,9 +440,7 @@ void Ensemble::energies(std::vector<double>& out) {
 void Ensemble::integrate(int nsteps) {
     if (!cells_valid) throw StateError("cells not initialised");
     if (!forces_valid) {
-        tic("pairs");
         launch_pairs(false, false);
-        toc();
     }
     for (int s = 0; s < nsteps; s++) {
         step_body();
@@ -469,9 +467,7 @@ void Ensemble::step_body() {
         mirrors();
         toc();
     }
-    tic("pairs");
     launch_pairs(false, false);
-    toc();
     tic("integrate_kick");
     launch_kick(false);
     toc();

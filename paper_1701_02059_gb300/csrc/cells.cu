@@ -867,9 +867,16 @@ __global__ void k_mirrors(View v) {
 // definition: FP32 from the exact mirror (error < 1e-6 sigma) finds the
 // candidates within band of the maximum, FP64 decides among them.
 constexpr float kBandR = 1e-5f;
+// Also prepares the pair kernel's per-cell frame and particle groups: the
+// cell normal (mean lipid director, unit; +z when the cell has no lipid
+// direction) and, in each tile of 128 particles, every particle's rank
+// along the tile's longer extent in the tangent plane.  Launched with 256
+// threads (8 warps, one cell each).
 __global__ void k_radius(View v, unsigned long long* __restrict__ rmax_bits /* [B] */) {
+    __shared__ float skey[8][128];
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
+    const int wb = threadIdx.x >> 5;
     if (warp >= v.Ktot) return;
     int k = warp;
     int b = find_inst(v.inst_k0, v.B, k);
@@ -899,6 +906,64 @@ __global__ void k_radius(View v, unsigned long long* __restrict__ rmax_bits /* [
         double R = __dsqrt_rn(best);
         v.R[k] = R;
         atomicMax(&rmax_bits[b], (unsigned long long)__double_as_longlong(R));
+    }
+    // pair-kernel frame
+    float nx = 0.f, ny = 0.f, nz = 0.f;
+    for (int p = s + lane; p < e; p += 32) {
+        if ((v.mq[p].w & 0xff) != kLipid) continue;
+        const float4 o = v.mo[p];
+        nx += o.x; ny += o.y; nz += o.z;
+    }
+    for (int off = 16; off; off >>= 1) {
+        nx += __shfl_xor_sync(0xffffffffu, nx, off);
+        ny += __shfl_xor_sync(0xffffffffu, ny, off);
+        nz += __shfl_xor_sync(0xffffffffu, nz, off);
+    }
+    const float nn = sqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+    if (nn > 1e-3f) { nx /= nn; ny /= nn; nz /= nn; }
+    else { nx = 0.f; ny = 0.f; nz = 1.f; }
+    if (lane == 0) v.cnorm[k] = make_float4(nx, ny, nz, 0.f);
+    const Frame F = tangent_frame(nx, ny, nz);
+    // pair-kernel groups: ranks inside each tile of 128 particles
+    for (int t0 = s; t0 < e; t0 += 128) {
+        const int nt = min(128, e - t0);
+        float ya[4], yb[4];
+        float lo_a = 3.0e38f, hi_a = -3.0e38f, lo_b = 3.0e38f, hi_b = -3.0e38f;
+        for (int u = 0; u < 4; u++) {
+            const int t = lane + 32 * u;
+            ya[u] = 0.f; yb[u] = 0.f;
+            if (t < nt) {
+                const int4 m = v.mq[t0 + t];
+                float c;
+                F.apply(m.x * kMirrorUnit, m.y * kMirrorUnit, m.z * kMirrorUnit, ya[u], yb[u], c);
+                lo_a = fminf(lo_a, ya[u]); hi_a = fmaxf(hi_a, ya[u]);
+                lo_b = fminf(lo_b, yb[u]); hi_b = fmaxf(hi_b, yb[u]);
+            }
+        }
+        for (int off = 16; off; off >>= 1) {
+            lo_a = fminf(lo_a, __shfl_xor_sync(0xffffffffu, lo_a, off));
+            hi_a = fmaxf(hi_a, __shfl_xor_sync(0xffffffffu, hi_a, off));
+            lo_b = fminf(lo_b, __shfl_xor_sync(0xffffffffu, lo_b, off));
+            hi_b = fmaxf(hi_b, __shfl_xor_sync(0xffffffffu, hi_b, off));
+        }
+        const bool use_a = (hi_a - lo_a) >= (hi_b - lo_b);
+        for (int u = 0; u < 4; u++) {
+            const int t = lane + 32 * u;
+            if (t < nt) skey[wb][t] = use_a ? ya[u] : yb[u];
+        }
+        __syncwarp();
+        for (int u = 0; u < 4; u++) {
+            const int t = lane + 32 * u;
+            if (t >= nt) continue;
+            const float kt = skey[wb][t];
+            int rank = 0;
+            for (int s2 = 0; s2 < nt; s2++) {
+                const float ks = skey[wb][s2];
+                rank += (ks < kt || (ks == kt && s2 < t)) ? 1 : 0;
+            }
+            v.grank[t0 + t] = (unsigned char)rank;
+        }
+        __syncwarp();
     }
 }
 

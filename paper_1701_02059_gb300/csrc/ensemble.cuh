@@ -213,6 +213,8 @@ public:
     unsigned long long* d_rmax = nullptr;
     float* d_rho = nullptr;                  // [Ktot] distance to the nearest non-neighbour centroid
     float4* d_cf = nullptr;                  // [Ktot] FP32 centroids by cell
+    float4* d_cnorm = nullptr;               // [Ktot] cell normals (pair-kernel frames)
+    unsigned char* d_grank = nullptr;        // [N] pair-kernel group ranks
     unsigned* d_dmax = nullptr;              // [B] largest centroid move of the last M-step (float bits)
     long long* d_xref = nullptr;
     long long* d_energy = nullptr;           // [B][8] fixed-point sums

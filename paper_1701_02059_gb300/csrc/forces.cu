@@ -322,16 +322,6 @@ __device__ inline T lipid_dispatch(const Inst& I, T dx, T dy, T dz, T r2, T nix,
 }
 
 
-// Rotation into the tangent frame of a cell: rows e1, e2, n.
-struct Frame {
-    float r[9];
-    __device__ inline void apply(float x, float y, float z, float& a, float& b, float& c) const {
-        a = fmaf(r[0], x, fmaf(r[1], y, r[2] * z));
-        b = fmaf(r[3], x, fmaf(r[4], y, r[5] * z));
-        c = fmaf(r[6], x, fmaf(r[7], y, r[8] * z));
-    }
-};
-
 template <typename T, bool ENERGY, bool DUMP, int Z>
 __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __restrict__ energy /* [B][8] */,
                                                             unsigned* __restrict__ dump,
@@ -347,12 +337,9 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
     __shared__ unsigned short cand[kPairThreads / 32][kStageCap];   // per-warp candidate list
     __shared__ unsigned short qbuf[kPairThreads / 32][kQCap][32];   // per-lane hit queues
     __shared__ NbrInfo nb[kMaxNbr];
-    __shared__ float skey[kPairThreads];
     __shared__ unsigned char sorder[kPairThreads];
-    __shared__ float sfr[kPairThreads / 32][4];
     __shared__ unsigned long long bar;
     __shared__ int s_nstage, s_next, s_next_off, s_self, s_self_lo, s_self_hi, s_total;
-    __shared__ Frame s_frame;
 
     const int k = blockIdx.x;
     const int b = find_inst(v.inst_k0, v.B, k);
@@ -383,88 +370,12 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
         const bool wactive = jsplit < nsplit;
         const int gs = (nti + groups - 1) / groups;             // balanced group size
 
-        // ---- tangent frame of the tile: normal = mean lipid director
-        {
-            float sx = 0.f, sy_ = 0.f, sz = 0.f;
-            if (tid < nti) {
-                const int4 q = v.mq[it0 + tid];
-                if ((q.w & 0xff) == kLipid) {
-                    const float4 o = v.mo[it0 + tid];
-                    sx = o.x; sy_ = o.y; sz = o.z;
-                }
-            }
-            for (int off = 16; off; off >>= 1) {
-                sx += __shfl_xor_sync(0xffffffffu, sx, off);
-                sy_ += __shfl_xor_sync(0xffffffffu, sy_, off);
-                sz += __shfl_xor_sync(0xffffffffu, sz, off);
-            }
-            if (lane == 0) { sfr[warp][0] = sx; sfr[warp][1] = sy_; sfr[warp][2] = sz; }
-            __syncthreads();
-            if (tid == 0) {
-                float nx = 0.f, ny = 0.f, nz = 0.f;
-                for (int w = 0; w < kPairThreads / 32; w++) { nx += sfr[w][0]; ny += sfr[w][1]; nz += sfr[w][2]; }
-                float nn = sqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
-                if (!(nn > 1e-3f)) { nx = 0.f; ny = 0.f; nz = 1.f; nn = 1.f; }
-                nx /= nn; ny /= nn; nz /= nn;
-                // e1 = normalise(n x axis of the smallest |n| component), e2 = n x e1
-                const float ax = fabsf(nx), ay = fabsf(ny), az = fabsf(nz);
-                float ux, uy, uz;
-                if (ax <= ay && ax <= az) { ux = 0.f; uy = nz; uz = -ny; }
-                else if (ay <= az) { ux = -nz; uy = 0.f; uz = nx; }
-                else { ux = ny; uy = -nx; uz = 0.f; }
-                const float un = sqrtf(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
-                ux /= un; uy /= un; uz /= un;
-                const float vx = ny * uz - nz * uy, vy = nz * ux - nx * uz, vz = nx * uy - ny * ux;
-                Frame f;
-                f.r[0] = ux; f.r[1] = uy; f.r[2] = uz;
-                f.r[3] = vx; f.r[4] = vy; f.r[5] = vz;
-                f.r[6] = nx; f.r[7] = ny; f.r[8] = nz;
-                s_frame = f;
-            }
-            __syncthreads();
-        }
-        const Frame F = s_frame;
-
-        // ---- compact groups: rank the tile along its longer tangent extent
-        if (groups > 1) {
-            float ya = 0.f, yb = 0.f;
-            if (tid < nti) {
-                const int4 q = v.mq[it0 + tid];
-                float c;
-                F.apply(q.x * kMirrorUnit, q.y * kMirrorUnit, q.z * kMirrorUnit, ya, yb, c);
-            }
-            float lo_a = tid < nti ? ya : 3.0e38f, hi_a = tid < nti ? ya : -3.0e38f;
-            float lo_b = tid < nti ? yb : 3.0e38f, hi_b = tid < nti ? yb : -3.0e38f;
-            for (int off = 16; off; off >>= 1) {
-                lo_a = fminf(lo_a, __shfl_xor_sync(0xffffffffu, lo_a, off));
-                hi_a = fmaxf(hi_a, __shfl_xor_sync(0xffffffffu, hi_a, off));
-                lo_b = fminf(lo_b, __shfl_xor_sync(0xffffffffu, lo_b, off));
-                hi_b = fmaxf(hi_b, __shfl_xor_sync(0xffffffffu, hi_b, off));
-            }
-            if (lane == 0) { sfr[warp][0] = lo_a; sfr[warp][1] = hi_a; sfr[warp][2] = lo_b; sfr[warp][3] = hi_b; }
-            __syncthreads();
-            float ea_lo = 3.0e38f, ea_hi = -3.0e38f, eb_lo = 3.0e38f, eb_hi = -3.0e38f;
-            for (int w = 0; w < kPairThreads / 32; w++) {
-                ea_lo = fminf(ea_lo, sfr[w][0]); ea_hi = fmaxf(ea_hi, sfr[w][1]);
-                eb_lo = fminf(eb_lo, sfr[w][2]); eb_hi = fmaxf(eb_hi, sfr[w][3]);
-            }
-            const bool use_a = (ea_hi - ea_lo) >= (eb_hi - eb_lo);
-            if (tid < nti) skey[tid] = use_a ? ya : yb;
-            __syncthreads();
-            if (tid < nti) {
-                const float kt = skey[tid];
-                int rank = 0;
-                for (int s2 = 0; s2 < nti; s2++) {
-                    const float ks = skey[s2];
-                    rank += (ks < kt || (ks == kt && s2 < tid)) ? 1 : 0;
-                }
-                sorder[rank] = (unsigned char)tid;
-            }
-            __syncthreads();
-        } else {
-            if (tid < nti) sorder[tid] = (unsigned char)tid;
-            __syncthreads();
-        }
+        // ---- tangent frame of the cell and compact groups (ranks along the
+        //      tile's longer tangent extent, prepared with the cell radii)
+        const float4 cn = v.cnorm[k];
+        const Frame F = tangent_frame(cn.x, cn.y, cn.z);
+        if (tid < nti) sorder[groups > 1 ? (int)v.grank[it0 + tid] : tid] = (unsigned char)tid;
+        __syncthreads();
 
         // ---- this lane's particle
         const int r = igrp * gs + lane;
@@ -718,36 +629,6 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
             na_off = next_off;
         }
 
-        // bonds of i (each bond evaluated from both ends)
-        T ub = 0;
-        if (ivalid && jsplit == 0 && ti != kLipid) {
-            const unsigned id = v.id[pi];
-            const int s = v.bptr[I.p0 + id], e = v.bptr[I.p0 + id + 1];
-            for (int q = s; q < e; q++) {
-                const int pj = v.slot_of_id[I.p0 + v.bpartner[q]];
-                const long long ddx = minimg_q(v.xq[pj] - v.xq[pi], I.boxq[0], I.periodic[0]);
-                const long long ddy = minimg_q(v.xq[N + pj] - v.xq[N + pi], I.boxq[1], I.periodic[1]);
-                const long long ddz = minimg_q(v.xq[2 * N + pj] - v.xq[2 * N + pi], I.boxq[2], I.periodic[2]);
-                T dx, dy, dz, r0, kb;
-                if constexpr (sizeof(T) == 4) {
-                    dx = ll_to_float(ddx) * (float)kGridInv; dy = ll_to_float(ddy) * (float)kGridInv;
-                    dz = ll_to_float(ddz) * (float)kGridInv;
-                    r0 = v.br0[q]; kb = v.bkb[q];
-                } else {
-                    dx = grid_to_double(ddx); dy = grid_to_double(ddy); dz = grid_to_double(ddz);
-                    r0 = v.br0_d[q]; kb = v.bkb_d[q];
-                }
-                const T rr = sqrt(dx * dx + dy * dy + dz * dz);
-                const T dr = rr - r0;
-                const T c = kb * dr / rr;
-                acc.add_bond(v, pi, c * dx, c * dy, c * dz);
-                if (ENERGY) {
-                    ub += (T)0.25 * kb * dr * dr;
-                    vir += (T)0.5 * -(c * (dx * dx + dy * dy + dz * dz));
-                }
-            }
-        }
-
         // combine the warps of a group (exact integer sums) and write; the
         // slot of a lane's particle in the tile is sorder[r]
         __syncthreads();
@@ -800,24 +681,92 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
         }
         if (ENERGY) {
             // per-particle energies to fixed point, exact integer sums per instance
-            long long eu = 0, ew = 0, eb = 0;
+            long long eu = 0, ew = 0;
             if (ivalid) {
                 eu = __double2ll_rn((double)up * 4294967296.0);
                 ew = __double2ll_rn((double)vir * 4294967296.0);
-                eb = __double2ll_rn((double)ub * 4294967296.0);
             }
             for (int off = 16; off; off >>= 1) {
                 eu += __shfl_xor_sync(0xffffffffu, eu, off);
                 ew += __shfl_xor_sync(0xffffffffu, ew, off);
-                eb += __shfl_xor_sync(0xffffffffu, eb, off);
             }
             if (lane == 0) {
                 atomicAdd((unsigned long long*)&energy[b * 8 + 0], (unsigned long long)eu);
-                atomicAdd((unsigned long long*)&energy[b * 8 + 1], (unsigned long long)eb);
                 atomicAdd((unsigned long long*)&energy[b * 8 + 4], (unsigned long long)ew);
             }
         }
         __syncthreads();
+    }
+}
+
+// Harmonic bonds ("Force Evaluation": a list of bonds between proteins is
+// maintained): one thread per particle adds its bonds' forces to F, after the
+// pair kernel wrote it.  Each bond is evaluated from both ends; each term is
+// rounded to the 2^-32 grid and added exactly, as the pair terms are.
+template <typename T, bool ENERGY>
+__global__ void k_bonds(View v, long long* __restrict__ energy /* [B][8] */) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool inside = p < v.N;
+    int b = -1;
+    long long eb = 0, ew = 0;
+    if (inside && v.type[p] != kLipid) {
+        b = find_inst(v.inst_p0, v.B, p);
+        const Inst& I = v.inst[b];
+        const size_t N = v.N;
+        const unsigned id = v.id[p];
+        const int s = v.bptr[I.p0 + id], e = v.bptr[I.p0 + id + 1];
+        long long f[3] = {0, 0, 0};
+        T ub = 0, vir = 0;
+        for (int q = s; q < e; q++) {
+            const int pj = v.slot_of_id[I.p0 + v.bpartner[q]];
+            const long long ddx = minimg_q(v.xq[pj] - v.xq[p], I.boxq[0], I.periodic[0]);
+            const long long ddy = minimg_q(v.xq[N + pj] - v.xq[N + p], I.boxq[1], I.periodic[1]);
+            const long long ddz = minimg_q(v.xq[2 * N + pj] - v.xq[2 * N + p], I.boxq[2], I.periodic[2]);
+            T dx, dy, dz, r0, kb;
+            if constexpr (sizeof(T) == 4) {
+                dx = ll_to_float(ddx) * (float)kGridInv; dy = ll_to_float(ddy) * (float)kGridInv;
+                dz = ll_to_float(ddz) * (float)kGridInv;
+                r0 = v.br0[q]; kb = v.bkb[q];
+            } else {
+                dx = grid_to_double(ddx); dy = grid_to_double(ddy); dz = grid_to_double(ddz);
+                r0 = v.br0_d[q]; kb = v.bkb_d[q];
+            }
+            const T r = sqrt(dx * dx + dy * dy + dz * dz);
+            const T dr = r - r0;
+            const T c = kb * dr / r;
+            const T g[3] = {c * dx, c * dy, c * dz};
+            for (int a = 0; a < 3; a++) {
+                if constexpr (sizeof(T) == 4) f[a] += __float2ll_rn(g[a] * 4294967296.0f);
+                else f[a] += __double2ll_rn(g[a] * 4294967296.0);
+                if (!(fabs(g[a]) < (T)1.0e30)) atomicOr(v.status, kStatusNaN);
+            }
+            if (ENERGY) {
+                ub += (T)0.25 * kb * dr * dr;
+                vir += (T)0.5 * -(c * (dx * dx + dy * dy + dz * dz));
+            }
+        }
+        if (e > s)
+            for (int a = 0; a < 3; a++) v.F[a * N + p] += f[a];
+        if (ENERGY) {
+            eb = __double2ll_rn((double)ub * 4294967296.0);
+            ew = __double2ll_rn((double)vir * 4294967296.0);
+        }
+    }
+    if (ENERGY) {
+        // warp-aggregate per instance, then one atomic per instance and warp
+        const unsigned grp = __match_any_sync(0xffffffffu, b);
+        long long sb = 0, sw = 0;
+        unsigned m = grp;
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            sb += __shfl_sync(grp, eb, src);
+            sw += __shfl_sync(grp, ew, src);
+        }
+        if (b >= 0 && (int)(threadIdx.x & 31) == __ffs(grp) - 1) {
+            atomicAdd((unsigned long long*)&energy[b * 8 + 1], (unsigned long long)sb);
+            atomicAdd((unsigned long long*)&energy[b * 8 + 4], (unsigned long long)sw);
+        }
     }
 }
 
@@ -848,6 +797,7 @@ void Ensemble::launch_pairs(bool energies, bool dump) {
     for (auto& I : inst_h) z4 = z4 && I.zeta == 4;
     const dim3 g(Ktot), t(kPairThreads);
     prefer_shared_all();
+    tic("pairs");
     if (precision == 0) {
         if (dump) k_pairs<float, false, true, 0><<<g, t, 0, stream>>>(v, d_energy, d_dump, d_dump_count, dump_cap);
         else if (energies && z4) k_pairs<float, true, false, 4><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
@@ -860,7 +810,19 @@ void Ensemble::launch_pairs(bool energies, bool dump) {
         else k_pairs<double, false, false, 0><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
     }
     launches++;
+    toc();
+    tic("bonds");
+    const int nb = (int)((N + 255) / 256);
+    if (precision == 0) {
+        if (energies) k_bonds<float, true><<<nb, 256, 0, stream>>>(v, d_energy);
+        else k_bonds<float, false><<<nb, 256, 0, stream>>>(v, d_energy);
+    } else {
+        if (energies) k_bonds<double, true><<<nb, 256, 0, stream>>>(v, d_energy);
+        else k_bonds<double, false><<<nb, 256, 0, stream>>>(v, d_energy);
+    }
+    launches++;
     CK(cudaGetLastError());
+    toc();
 }
 
 }  // namespace orbc

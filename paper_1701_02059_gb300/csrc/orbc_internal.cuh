@@ -84,6 +84,9 @@ struct View {
     // mirrors for the pair kernel
     int4* mq;                       // x - c at 2^-26 sigma, w = type
     float4* mo;                     // director, w = slot (int bits)
+    float4* cnorm;                  // [Ktot] unit normal of each cell (mean lipid director)
+    unsigned char* grank;           // [N] rank of each particle in its 128-particle tile along
+                                    //     the tile's longer tangent extent (pair-kernel groups)
     // cells
     long long* cq;                  // [3][Ktot] centroids on the 2^-40 grid
     int* cell_start;                // [Ktot+1]
@@ -260,6 +263,32 @@ __device__ inline int find_inst(const int* off, int B, int x) {   // off[B+1], r
         if (__ldg(off + mid) <= x) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// Orthonormal tangent frame (rows e1, e2, n) of a unit normal n: e1 is n
+// crossed with the coordinate axis least aligned with n.
+struct Frame {
+    float r[9];
+    __device__ inline void apply(float x, float y, float z, float& a, float& b, float& c) const {
+        a = fmaf(r[0], x, fmaf(r[1], y, r[2] * z));
+        b = fmaf(r[3], x, fmaf(r[4], y, r[5] * z));
+        c = fmaf(r[6], x, fmaf(r[7], y, r[8] * z));
+    }
+};
+
+__device__ inline Frame tangent_frame(float nx, float ny, float nz) {
+    const float ax = fabsf(nx), ay = fabsf(ny), az = fabsf(nz);
+    float ux, uy, uz;
+    if (ax <= ay && ax <= az) { ux = 0.f; uy = nz; uz = -ny; }
+    else if (ay <= az) { ux = -nz; uy = 0.f; uz = nx; }
+    else { ux = ny; uy = -nx; uz = 0.f; }
+    const float un = sqrtf(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+    ux /= un; uy /= un; uz /= un;
+    Frame f;
+    f.r[0] = ux; f.r[1] = uy; f.r[2] = uz;
+    f.r[3] = ny * uz - nz * uy; f.r[4] = nz * ux - nx * uz; f.r[5] = nx * uy - ny * ux;
+    f.r[6] = nx; f.r[7] = ny; f.r[8] = nz;
+    return f;
 }
 
 }  // namespace orbc
