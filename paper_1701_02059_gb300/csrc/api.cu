@@ -58,6 +58,7 @@ View Ensemble::view() {
     v.cq = d_cq; v.cell_start = d_cell_start; v.R = d_R; v.adj_ptr = d_adj_ptr; v.adj = d_adj; v.adj_cap = adj_cap;
     v.gstart = d_gstart; v.gcent = d_gcent; v.gcf = d_gcf;
     v.bptr = d_bptr; v.bpartner = d_bpartner; v.br0 = d_br0; v.bkb = d_bkb; v.br0_d = d_br0_d; v.bkb_d = d_bkb_d;
+    v.nbond = nbond; v.bij = d_bij; v.binst = d_binst; v.bkf = d_bkf; v.bkd = d_bkd;
     v.status = d_status;
     return v;
 }
@@ -206,6 +207,8 @@ void Ensemble::alloc_core(const std::vector<int>& p0, const std::vector<int>& k0
     d_cnorm = alloc<float4>(Ktot);
     d_grank = alloc<unsigned char>(N);
     d_dmax = alloc<unsigned>(B);
+    d_fbcount = alloc<int>(1);
+    d_adjpad = alloc<int>((size_t)Ktot * 64);
     prev_adj_valid_ = false;
     d_energy = alloc<long long>((size_t)8 * B);
     d_step = alloc<long long>(B);
@@ -258,6 +261,33 @@ void Ensemble::upload_bonds(const std::vector<BondSpec>& bl, const std::vector<i
         CK(cudaMemcpyAsync(d_bkb, kbf.data(), sizeof(float) * nbe, cudaMemcpyHostToDevice, stream));
         CK(cudaMemcpyAsync(d_br0_d, r0d.data(), sizeof(double) * nbe, cudaMemcpyHostToDevice, stream));
         CK(cudaMemcpyAsync(d_bkb_d, kbd.data(), sizeof(double) * nbe, cudaMemcpyHostToDevice, stream));
+    }
+    // the same bonds once each, for the bond kernel
+    nbond = 0;
+    for (int b = 0; b < B; b++) nbond += (int)bl[b].r0->size();
+    std::vector<int2> bij(std::max(nbond, 1));
+    std::vector<int> binst(std::max(nbond, 1));
+    std::vector<float2> bkf(std::max(nbond, 1));
+    std::vector<double2> bkd(std::max(nbond, 1));
+    for (int b = 0, q0 = 0; b < B; b++) {
+        const int nb = (int)bl[b].r0->size();
+        for (int q = 0; q < nb; q++) {
+            bij[q0 + q] = make_int2(p0[b] + (*bl[b].bonds)[2 * q], p0[b] + (*bl[b].bonds)[2 * q + 1]);
+            binst[q0 + q] = b;
+            bkf[q0 + q] = make_float2((float)(*bl[b].r0)[q], (float)(*bl[b].kb)[q]);
+            bkd[q0 + q] = make_double2((*bl[b].r0)[q], (*bl[b].kb)[q]);
+        }
+        q0 += nb;
+    }
+    d_bij = alloc<int2>(std::max(nbond, 1));
+    d_binst = alloc<int>(std::max(nbond, 1));
+    d_bkf = alloc<float2>(std::max(nbond, 1));
+    d_bkd = alloc<double2>(std::max(nbond, 1));
+    if (nbond > 0) {
+        CK(cudaMemcpyAsync(d_bij, bij.data(), sizeof(int2) * nbond, cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(d_binst, binst.data(), sizeof(int) * nbond, cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(d_bkf, bkf.data(), sizeof(float2) * nbond, cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(d_bkd, bkd.data(), sizeof(double2) * nbond, cudaMemcpyHostToDevice, stream));
     }
     CK(cudaStreamSynchronize(stream));   // the host vectors die here
 }

@@ -594,6 +594,14 @@ __global__ void k_estep(View v, int* __restrict__ cell_out) {
     if (i < v.N) estep_one(v, i, cell_out);
 }
 
+// Grid search for the particles the certified E-step could not decide.
+__global__ void k_estep_list(View v, const int* __restrict__ fb_list, const int* __restrict__ fb_count,
+                             int* __restrict__ cell_out) {
+    const int n = *fb_count;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
+        estep_one(v, fb_list[q], cell_out);
+}
+
 // Rebuild E-step from the previous cell list (the paper's guess from the
 // previous particle, made exact): the candidates are the particle's previous
 // cell and its previous neighbouring cells, renumbered by the Morton
@@ -607,7 +615,8 @@ constexpr float kCertMargin = 4e-3f;
 __global__ void k_estep_fast(View v, const int* __restrict__ cell_old, const int* __restrict__ adj_ptr_old,
                              const int* __restrict__ adj_old, const float* __restrict__ rho_old,
                              const int* __restrict__ new_of_old, const float4* __restrict__ cf,
-                             const unsigned* __restrict__ dmax, int* __restrict__ cell_out) {
+                             const unsigned* __restrict__ dmax, int* __restrict__ cell_out,
+                             int* __restrict__ fb_list, int* __restrict__ fb_count) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const bool valid = i < v.N;
@@ -658,13 +667,22 @@ __global__ void k_estep_fast(View v, const int* __restrict__ cell_old, const int
             }
         }
     }
-    if (!valid) return;
     const float lim = sqrtf(best) + kBandE;
-    const float cert = rho_old[ko] - 2.0f * __uint_as_float(dmax[b]) - sqrtf(dself2) - kCertMargin;
-    if (bk < 0 || dself2 >= 3.0e38f || !(lim < cert)) {
-        estep_one(v, i, cell_out);
-        return;
+    bool fail = false;
+    if (valid) {
+        const float cert = rho_old[ko] - 2.0f * __uint_as_float(dmax[b]) - sqrtf(dself2) - kCertMargin;
+        fail = bk < 0 || dself2 >= 3.0e38f || !(lim < cert);
     }
+    // uncertified particles go to the grid search of k_estep_list (kept out
+    // of this kernel, whose occupancy would otherwise drop to the search's)
+    const unsigned fm = __ballot_sync(0xffffffffu, fail);
+    if (fm) {
+        int base = 0;
+        if (lane == __ffs(fm) - 1) base = atomicAdd(fb_count, __popc(fm));
+        base = __shfl_sync(0xffffffffu, base, __ffs(fm) - 1);
+        if (fail) fb_list[base + __popc(fm & ((1u << lane) - 1u))] = i;
+    }
+    if (!valid || fail) return;
     if (second > lim * lim) { cell_out[i] = bk; return; }
     // tie band among the candidates of the particle's own previous cell: FP64
     double best64 = 1e300;
@@ -687,17 +705,29 @@ __global__ void k_estep_fast(View v, const int* __restrict__ cell_old, const int
 }
 
 // ============================================================== stable counting sort
+// Consecutive particles mostly share a cell: one atomic per distinct cell of
+// a warp (lanes with the same cell found with a match).
 __global__ void k_hist(int N, const int* __restrict__ cell, int* __restrict__ cnt) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) atomicAdd(&cnt[cell[i]], 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (i < N) ? cell[i] : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    const int lane = threadIdx.x & 31;
+    if (c >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[c], __popc(peers));
 }
 
+// Slot of each particle inside its cell's range (in any order across warps;
+// the per-cell sort that follows restores the storage order).
 __global__ void k_scatter(int N, const int* __restrict__ cell, const int* __restrict__ start, int* __restrict__ cursor,
                           int* __restrict__ tmp) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    int c = cell[i];
-    tmp[start[c] + atomicAdd(&cursor[c], 1)] = i;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (i < N) ? cell[i] : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (c >= 0 && lane == leader) base = atomicAdd(&cursor[c], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    if (c >= 0) tmp[start[c] + base + __popc(peers & ((1u << lane) - 1u))] = i;
 }
 
 // Sort each cell's slot list ascending (= old storage order), which makes the
@@ -988,132 +1018,106 @@ __device__ inline bool adj_test(const View& v, const Inst& I, int k, int j, doub
     return d < tt;
 }
 
-__device__ inline void sort_row(int* row, int n) {
-    for (int a = 1; a < n; a++) {
-        int x = row[a];
-        int c = a - 1;
-        while (c >= 0 && row[c] > x) { row[c + 1] = row[c]; c--; }
-        row[c + 1] = x;
-    }
-}
-
-template <bool FILL>
-__device__ void adj_one(const View& v, const unsigned long long* __restrict__ rmax_bits, int* __restrict__ count, int k,
-                        float* __restrict__ rho_out) {
-    int b = find_inst(v.inst_k0, v.B, k);
+// Neighbouring cells, one warp per cell: the lanes share the grid cells of
+// the cube around the cell's own grid cell that the reach
+// R_k + R_max + r_s + 2 skin can touch, test every centroid there with the
+// exact rule, collect the row in shared memory and sort it.  Rows longer than
+// kAdjRow are flagged (kStatusAdjOverflow) and truncated.
+constexpr int kAdjRow = 64;
+__global__ void k_adj_warp(View v, const unsigned long long* __restrict__ rmax_bits, int* __restrict__ count,
+                           float* __restrict__ rho_out, int* __restrict__ pad /* [Ktot][kAdjRow] */) {
+    __shared__ int row[8][kAdjRow];
+    __shared__ int rown[8];
+    const int wb = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= v.Ktot) return;
+    const int b = find_inst(v.inst_k0, v.B, k);
     const Inst& I = v.inst[b];
-    double Rk = v.R[k];
-    double Rmax = __longlong_as_double((long long)rmax_bits[b]);
-    float reach = (float)(Rk + Rmax + I.rs + 2.0 * I.skin) + kBandA;
-    long long cx = v.cq[k], cy = v.cq[(size_t)v.Ktot + k], cz = v.cq[(size_t)2 * v.Ktot + k];
+    const double Rk = v.R[k];
+    const double Rmax = __longlong_as_double((long long)rmax_bits[b]);
+    const float reach = (float)(Rk + Rmax + I.rs + 2.0 * I.skin) + kBandA;
+    const long long cx = v.cq[k], cy = v.cq[(size_t)v.Ktot + k], cz = v.cq[(size_t)2 * v.Ktot + k];
     float p[3];
     int g[3];
     g[0] = grid_coord(cx, I, 0, p[0]);
     g[1] = grid_coord(cy, I, 1, p[1]);
     g[2] = grid_coord(cz, I, 2, p[2]);
-    int n = 0;
-    float rho = reach - kBandA;
-    int out0 = FILL ? v.adj_ptr[k] : 0;
     const double tail = (I.rs) + (I.skin + I.skin);
-    for (int r = 0;; r++) {
-        for_shell(g, r, I, [&](long long gg) {
-            for (int q = v.gstart[gg]; q < v.gstart[gg + 1]; q++) {
-                float4 c = v.gcf[q];
-                int j = __float_as_int(c.w);
-                float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1), dz = axis_dist(p[2], c.z, I, 2);
-                float df = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                bool in = adj_test(v, I, k, j, Rk, df, cx, cy, cz, tail);
-                if (!in) rho = fminf(rho, df);
-                if (in) {
-                    if (FILL) {
-                        if (out0 + n < v.adj_cap) v.adj[out0 + n] = j;
-                        else atomicOr(v.status, kStatusAdjOverflow);
-                    }
-                    n++;
-                }
-            }
-        });
+    // cube radius: the first shell beyond which nothing is within reach
+    int R = 0;
+    for (;; R++) {
         bool ex;
-        float lb = shell_bound(p, g, r, I, ex);
+        const float lb = shell_bound(p, g, R, I, ex);
         if (ex || lb > reach) break;
     }
-    if (!FILL) { count[k] = n; if (rho_out) rho_out[k] = rho; }
-    else {
-        // ascending row (insertion sort, rows are short)
-        if (out0 + n > v.adj_cap) return;
-        sort_row(v.adj + out0, n);
+    int lo[3], ext[3];
+    for (int a = 0; a < 3; a++) {
+        int l, h;
+        if (I.periodic[a]) {
+            if (2 * R + 1 >= I.gdim[a]) { l = 0; h = I.gdim[a] - 1; }
+            else { l = g[a] - R; h = g[a] + R; }
+        } else {
+            l = max(0, g[a] - R);
+            h = min(I.gdim[a] - 1, g[a] + R);
+        }
+        lo[a] = l;
+        ext[a] = h - l + 1;
+    }
+    if (lane == 0) rown[wb] = 0;
+    __syncwarp();
+    float rho = reach - kBandA;
+    const int M = ext[0] * ext[1] * ext[2];
+    for (int t = lane; t < M; t += 32) {
+        const int x = lo[0] + t % ext[0], y = lo[1] + (t / ext[0]) % ext[1], z = lo[2] + t / (ext[0] * ext[1]);
+        const int w0 = I.periodic[0] ? wrap_idx(x, I.gdim[0]) : x;
+        const int w1 = I.periodic[1] ? wrap_idx(y, I.gdim[1]) : y;
+        const int w2 = I.periodic[2] ? wrap_idx(z, I.gdim[2]) : z;
+        const long long gg = I.g0 + ((long long)w2 * I.gdim[1] + w1) * I.gdim[0] + w0;
+        const int q1 = v.gstart[gg + 1];
+        for (int q = v.gstart[gg]; q < q1; q++) {
+            const float4 c = v.gcf[q];
+            const int j = __float_as_int(c.w);
+            const float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1), dz = axis_dist(p[2], c.z, I, 2);
+            const float df = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            if (adj_test(v, I, k, j, Rk, df, cx, cy, cz, tail)) {
+                const int at = atomicAdd(&rown[wb], 1);
+                if (at < kAdjRow) row[wb][at] = j;
+            } else {
+                rho = fminf(rho, df);
+            }
+        }
+    }
+    for (int off = 16; off; off >>= 1) rho = fminf(rho, __shfl_xor_sync(0xffffffffu, rho, off));
+    __syncwarp();
+    int n = rown[wb];
+    if (n > kAdjRow) {
+        if (lane == 0) atomicOr(v.status, kStatusAdjOverflow);
+        n = kAdjRow;
+    }
+    // ascending row: every entry goes to its rank (entries are distinct)
+    int val[2], rk[2] = {0, 0};
+    for (int u = 0; u < 2; u++) val[u] = (lane + 32 * u < n) ? row[wb][lane + 32 * u] : 0;
+    for (int s2 = 0; s2 < n; s2++) {
+        const int o = row[wb][s2];
+        rk[0] += o < val[0];
+        rk[1] += o < val[1];
+    }
+    for (int u = 0; u < 2; u++)
+        if (lane + 32 * u < n) pad[(size_t)k * kAdjRow + rk[u]] = val[u];
+    if (lane == 0) {
+        count[k] = n;
+        rho_out[k] = rho;
     }
 }
 
-
-template <bool FILL>
-__global__ void k_adjacency(View v, const unsigned long long* __restrict__ rmax_bits, int* __restrict__ count,
-                            float* __restrict__ rho_out) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = k < v.Ktot;
-    const int b = valid ? find_inst(v.inst_k0, v.B, k) : -1;
-    const int b0 = __reduce_max_sync(0xffffffffu, b);
-    if (b0 < 0) return;
-    const bool same = __all_sync(0xffffffffu, !valid || b == b0);
-    const Inst& I = v.inst[b0];
-    if (!same || (I.periodic[0] | I.periodic[1] | I.periodic[2])) {
-        if (valid) adj_one<FILL>(v, rmax_bits, count, k, rho_out);
-        return;
-    }
-    // warp-cooperative: 32 consecutive (Morton-ordered) cells share a region
-    const double Rmax = __longlong_as_double((long long)rmax_bits[b0]);
-    const double tail = (I.rs) + (I.skin + I.skin);
-    double Rk = 0;
-    long long cx = 0, cy = 0, cz = 0;
-    float p[3] = {0, 0, 0};
-    int g[3] = {0, 0, 0};
-    float reach = 0;
-    if (valid) {
-        Rk = v.R[k];
-        cx = v.cq[k]; cy = v.cq[(size_t)v.Ktot + k]; cz = v.cq[(size_t)2 * v.Ktot + k];
-        g[0] = grid_coord(cx, I, 0, p[0]);
-        g[1] = grid_coord(cy, I, 1, p[1]);
-        g[2] = grid_coord(cz, I, 2, p[2]);
-        reach = (float)(Rk + Rmax + I.rs + 2.0 * I.skin) + kBandA;
-    }
-    int lo[3], hi[3];
-    warp_box(g, valid, lo, hi);
-    if (hi[0] - lo[0] > 3 || hi[1] - lo[1] > 3 || hi[2] - lo[2] > 3) {
-        if (valid) adj_one<FILL>(v, rmax_bits, count, k, rho_out);
-        return;
-    }
-    int n = 0;
-    float rho = reach - kBandA;
-    const int out0 = (FILL && valid) ? v.adj_ptr[k] : 0;
-    for (int r = 0;; r++) {
-        region_ring(I, lo, hi, r, [&](long long gg) {
-            const int q1 = v.gstart[gg + 1];
-            for (int q = v.gstart[gg]; q < q1; q++) {
-                const float4 c = v.gcf[q];
-                const float dx = p[0] - c.x, dy = p[1] - c.y, dz = p[2] - c.z;
-                const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (valid && d2 <= reach * reach) {
-                    const int j = __float_as_int(c.w);
-                    const float dfj = sqrtf(d2);
-                    const bool in = adj_test(v, I, k, j, Rk, dfj, cx, cy, cz, tail);
-                    if (!in) rho = fminf(rho, dfj);
-                    if (in) {
-                        if (FILL) {
-                            if (out0 + n < v.adj_cap) v.adj[out0 + n] = j;
-                            else atomicOr(v.status, kStatusAdjOverflow);
-                        }
-                        n++;
-                    }
-                }
-            }
-        });
-        bool ex;
-        const float lb = region_bound(I, p, lo, hi, r, ex);
-        if (__all_sync(0xffffffffu, !valid || ex || lb > reach)) break;
-    }
-    if (!valid) return;
-    if (!FILL) { count[k] = n; if (rho_out) rho_out[k] = rho; }
-    else if (out0 + n <= v.adj_cap) sort_row(v.adj + out0, n);
+// CSR rows from the padded rows.
+__global__ void k_adj_compact(View v, const int* __restrict__ pad) {
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= v.Ktot) return;
+    const int a0 = v.adj_ptr[k], n = v.adj_ptr[k + 1] - a0;
+    for (int t = lane; t < n; t += 32)
+        if (a0 + t < v.adj_cap) v.adj[a0 + t] = pad[(size_t)k * kAdjRow + t];
 }
 
 // ============================================================== host side
@@ -1210,9 +1214,11 @@ void Ensemble::finish_cells() {
     morton_relabel();
     build_grid();
     if (prev_adj_valid_) {
+        CK(cudaMemsetAsync(d_fbcount, 0, sizeof(int), stream));
         k_estep_fast<<<nblk(N, 128), 128, 0, stream>>>(v, d_cell, d_adj_ptr, d_adj, d_rho, d_new_of_old, d_cf, d_dmax,
-                                                      d_cell_new);
-        launches++;
+                                                      d_cell_new, d_cell_tmp, d_fbcount);
+        k_estep_list<<<152 * 4, 128, 0, stream>>>(v, d_cell_tmp, d_fbcount, d_cell_new);
+        launches += 2;
         CK(cudaGetLastError());
     } else {
         estep(d_cell_new);
@@ -1246,13 +1252,13 @@ void Ensemble::finish_cells() {
     CK(cudaMemsetAsync(d_rmax, 0, sizeof(unsigned long long) * B, stream));
     k_radius<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(nv, d_rmax);
     launches++;
-    k_adjacency<false><<<nblk(Ktot, 128), 128, 0, stream>>>(nv, d_rmax, d_adjcount, d_rho);
+    k_adj_warp<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(nv, d_rmax, d_adjcount, d_rho, d_adjpad);
     launches++;
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(d_adjcount + Ktot, 0, sizeof(int), stream));
     scan_exclusive(d_adjcount, d_adj_ptr, Ktot + 1);
     nv = view();
-    k_adjacency<true><<<nblk(Ktot, 128), 128, 0, stream>>>(nv, d_rmax, d_adjcount, nullptr);
+    k_adj_compact<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(nv, d_adjpad);
     prev_adj_valid_ = true;
     launches++;
     CK(cudaGetLastError());

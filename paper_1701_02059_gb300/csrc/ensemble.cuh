@@ -202,6 +202,11 @@ public:
     int *d_bptr = nullptr, *d_bpartner = nullptr;
     float *d_br0 = nullptr, *d_bkb = nullptr;
     double *d_br0_d = nullptr, *d_bkb_d = nullptr;
+    int nbond = 0;
+    int2* d_bij = nullptr;
+    int* d_binst = nullptr;
+    float2* d_bkf = nullptr;
+    double2* d_bkd = nullptr;
     unsigned* d_status = nullptr;
     long long* d_S = nullptr;
     int* d_cnt = nullptr;
@@ -216,6 +221,8 @@ public:
     float4* d_cnorm = nullptr;               // [Ktot] cell normals (pair-kernel frames)
     unsigned char* d_grank = nullptr;        // [N] pair-kernel group ranks
     unsigned* d_dmax = nullptr;              // [B] largest centroid move of the last M-step (float bits)
+    int* d_fbcount = nullptr;                // particles the certified E-step left to the grid search
+    int* d_adjpad = nullptr;                 // [Ktot][64] neighbouring-cell rows before compaction
     long long* d_xref = nullptr;
     long long* d_energy = nullptr;           // [B][8] fixed-point sums
     long long* d_step = nullptr;             // [B]

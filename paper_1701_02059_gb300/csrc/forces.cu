@@ -700,56 +700,50 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
 }
 
 // Harmonic bonds ("Force Evaluation": a list of bonds between proteins is
-// maintained): one thread per particle adds its bonds' forces to F, after the
-// pair kernel wrote it.  Each bond is evaluated from both ends; each term is
-// rounded to the 2^-32 grid and added exactly, as the pair terms are.
+// maintained): one thread per bond, after the pair kernel wrote F.  The bond
+// force is rounded to the 2^-32 grid once and added to both ends with
+// opposite signs by 64-bit integer atomics: integer sums do not depend on
+// the order, and the result equals evaluating the bond from each end.
 template <typename T, bool ENERGY>
 __global__ void k_bonds(View v, long long* __restrict__ energy /* [B][8] */) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool inside = p < v.N;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
     int b = -1;
     long long eb = 0, ew = 0;
-    if (inside && v.type[p] != kLipid) {
-        b = find_inst(v.inst_p0, v.B, p);
+    if (q < v.nbond) {
+        b = v.binst[q];
         const Inst& I = v.inst[b];
         const size_t N = v.N;
-        const unsigned id = v.id[p];
-        const int s = v.bptr[I.p0 + id], e = v.bptr[I.p0 + id + 1];
-        long long f[3] = {0, 0, 0};
-        T ub = 0, vir = 0;
-        for (int q = s; q < e; q++) {
-            const int pj = v.slot_of_id[I.p0 + v.bpartner[q]];
-            const long long ddx = minimg_q(v.xq[pj] - v.xq[p], I.boxq[0], I.periodic[0]);
-            const long long ddy = minimg_q(v.xq[N + pj] - v.xq[N + p], I.boxq[1], I.periodic[1]);
-            const long long ddz = minimg_q(v.xq[2 * N + pj] - v.xq[2 * N + p], I.boxq[2], I.periodic[2]);
-            T dx, dy, dz, r0, kb;
-            if constexpr (sizeof(T) == 4) {
-                dx = ll_to_float(ddx) * (float)kGridInv; dy = ll_to_float(ddy) * (float)kGridInv;
-                dz = ll_to_float(ddz) * (float)kGridInv;
-                r0 = v.br0[q]; kb = v.bkb[q];
-            } else {
-                dx = grid_to_double(ddx); dy = grid_to_double(ddy); dz = grid_to_double(ddz);
-                r0 = v.br0_d[q]; kb = v.bkb_d[q];
-            }
-            const T r = sqrt(dx * dx + dy * dy + dz * dz);
-            const T dr = r - r0;
-            const T c = kb * dr / r;
-            const T g[3] = {c * dx, c * dy, c * dz};
-            for (int a = 0; a < 3; a++) {
-                if constexpr (sizeof(T) == 4) f[a] += __float2ll_rn(g[a] * 4294967296.0f);
-                else f[a] += __double2ll_rn(g[a] * 4294967296.0);
-                if (!(fabs(g[a]) < (T)1.0e30)) atomicOr(v.status, kStatusNaN);
-            }
-            if (ENERGY) {
-                ub += (T)0.25 * kb * dr * dr;
-                vir += (T)0.5 * -(c * (dx * dx + dy * dy + dz * dz));
-            }
+        const int2 e = v.bij[q];
+        const int pi = v.slot_of_id[e.x], pj = v.slot_of_id[e.y];
+        const long long ddx = minimg_q(v.xq[pj] - v.xq[pi], I.boxq[0], I.periodic[0]);
+        const long long ddy = minimg_q(v.xq[N + pj] - v.xq[N + pi], I.boxq[1], I.periodic[1]);
+        const long long ddz = minimg_q(v.xq[2 * N + pj] - v.xq[2 * N + pi], I.boxq[2], I.periodic[2]);
+        T dx, dy, dz, r0, kb;
+        if constexpr (sizeof(T) == 4) {
+            dx = ll_to_float(ddx) * (float)kGridInv; dy = ll_to_float(ddy) * (float)kGridInv;
+            dz = ll_to_float(ddz) * (float)kGridInv;
+            const float2 kf = v.bkf[q];
+            r0 = kf.x; kb = kf.y;
+        } else {
+            dx = grid_to_double(ddx); dy = grid_to_double(ddy); dz = grid_to_double(ddz);
+            const double2 kd = v.bkd[q];
+            r0 = kd.x; kb = kd.y;
         }
-        if (e > s)
-            for (int a = 0; a < 3; a++) v.F[a * N + p] += f[a];
+        const T r = sqrt(dx * dx + dy * dy + dz * dz);
+        const T dr = r - r0;
+        const T c = kb * dr / r;
+        const T g[3] = {c * dx, c * dy, c * dz};     // force on the first end
+        for (int a = 0; a < 3; a++) {
+            long long f;
+            if constexpr (sizeof(T) == 4) f = __float2ll_rn(g[a] * 4294967296.0f);
+            else f = __double2ll_rn(g[a] * 4294967296.0);
+            if (!(fabs(g[a]) < (T)1.0e30)) atomicOr(v.status, kStatusNaN);
+            atomicAdd((unsigned long long*)&v.F[a * N + pi], (unsigned long long)f);
+            atomicAdd((unsigned long long*)&v.F[a * N + pj], (unsigned long long)(-f));
+        }
         if (ENERGY) {
-            eb = __double2ll_rn((double)ub * 4294967296.0);
-            ew = __double2ll_rn((double)vir * 4294967296.0);
+            eb = __double2ll_rn((double)((T)0.5 * kb * dr * dr) * 4294967296.0);
+            ew = __double2ll_rn((double)(-(c * (dx * dx + dy * dy + dz * dz))) * 4294967296.0);
         }
     }
     if (ENERGY) {
@@ -812,7 +806,7 @@ void Ensemble::launch_pairs(bool energies, bool dump) {
     launches++;
     toc();
     tic("bonds");
-    const int nb = (int)((N + 255) / 256);
+    const int nb = (int)((std::max(nbond, 1) + 255) / 256);
     if (precision == 0) {
         if (energies) k_bonds<float, true><<<nb, 256, 0, stream>>>(v, d_energy);
         else k_bonds<float, false><<<nb, 256, 0, stream>>>(v, d_energy);

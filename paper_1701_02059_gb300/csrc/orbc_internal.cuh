@@ -105,6 +105,12 @@ struct View {
     float* bkb;
     double* br0_d;
     double* bkb_d;
+    // bonds as a flat list (each once): ends as p0 + id, instance, constants
+    int nbond;
+    const int2* bij;
+    const int* binst;
+    const float2* bkf;              // (r0, kb)
+    const double2* bkd;
     // status word written by kernels (bit flags, see kStatus*)
     unsigned* status;
 };
