@@ -55,7 +55,7 @@ View Ensemble::view() {
     v.cell = d_cell; v.slot_of_id = d_slot_of_id;
     v.F = d_F; v.T = d_T; v.Fbig = d_Fbig;
     v.mq = d_mq; v.mo = d_mo; v.cnorm = d_cnorm; v.grank = d_grank;
-    v.cq = d_cq; v.cell_start = d_cell_start; v.R = d_R; v.adj_ptr = d_adj_ptr; v.adj = d_adj; v.adj_cap = adj_cap;
+    v.cq = d_cq; v.cell_start = d_cell_start; v.R = d_R; v.adj_ptr = d_adj_ptr; v.adj = d_adj; v.adj_cap = adj_cap; v.adjd = d_adjd;
     v.gstart = d_gstart; v.gcent = d_gcent; v.gcf = d_gcf;
     v.bptr = d_bptr; v.bpartner = d_bpartner; v.br0 = d_br0; v.bkb = d_bkb; v.br0_d = d_br0_d; v.bkb_d = d_bkb_d;
     v.nbond = nbond; v.bij = d_bij; v.binst = d_binst; v.bkf = d_bkf; v.bkd = d_bkd;
@@ -209,6 +209,7 @@ void Ensemble::alloc_core(const std::vector<int>& p0, const std::vector<int>& k0
     d_dmax = alloc<unsigned>(B);
     d_fbcount = alloc<int>(1);
     d_adjpad = alloc<int>((size_t)Ktot * 64);
+    d_adjd = alloc<AdjDesc>(adj_cap);
     prev_adj_valid_ = false;
     d_energy = alloc<long long>((size_t)8 * B);
     d_step = alloc<long long>(B);

@@ -1110,14 +1110,31 @@ __global__ void k_adj_warp(View v, const unsigned long long* __restrict__ rmax_b
     }
 }
 
-// CSR rows from the padded rows.
+// CSR rows from the padded rows, with the pair kernel's staging descriptor
+// of every entry (particle range, exact centroid offset at 2^-26 sigma).
 __global__ void k_adj_compact(View v, const int* __restrict__ pad) {
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (k >= v.Ktot) return;
+    const Inst& I = v.inst[find_inst(v.inst_k0, v.B, k)];
+    const long long ckx = v.cq[k], cky = v.cq[(size_t)v.Ktot + k], ckz = v.cq[(size_t)2 * v.Ktot + k];
     const int a0 = v.adj_ptr[k], n = v.adj_ptr[k + 1] - a0;
-    for (int t = lane; t < n; t += 32)
-        if (a0 + t < v.adj_cap) v.adj[a0 + t] = pad[(size_t)k * kAdjRow + t];
+    for (int t = lane; t < n; t += 32) {
+        if (a0 + t >= v.adj_cap) break;
+        const int j = pad[(size_t)k * kAdjRow + t];
+        v.adj[a0 + t] = j;
+        const long long dx = minimg_q(v.cq[j] - ckx, I.boxq[0], I.periodic[0]);
+        const long long dy = minimg_q(v.cq[(size_t)v.Ktot + j] - cky, I.boxq[1], I.periodic[1]);
+        const long long dz = minimg_q(v.cq[(size_t)2 * v.Ktot + j] - ckz, I.boxq[2], I.periodic[2]);
+        AdjDesc d;
+        d.start = v.cell_start[j];
+        d.cnt = v.cell_start[j + 1] - d.start;
+        d.ox = (int)(unsigned)(unsigned long long)((dx + (1ll << (kMirrorShift - 1))) >> kMirrorShift);
+        d.oy = (int)(unsigned)(unsigned long long)((dy + (1ll << (kMirrorShift - 1))) >> kMirrorShift);
+        d.oz = (int)(unsigned)(unsigned long long)((dz + (1ll << (kMirrorShift - 1))) >> kMirrorShift);
+        d.cell = j;
+        v.adjd[a0 + t] = d;
+    }
 }
 
 // ============================================================== host side

@@ -223,6 +223,7 @@ public:
     unsigned* d_dmax = nullptr;              // [B] largest centroid move of the last M-step (float bits)
     int* d_fbcount = nullptr;                // particles the certified E-step left to the grid search
     int* d_adjpad = nullptr;                 // [Ktot][64] neighbouring-cell rows before compaction
+    AdjDesc* d_adjd = nullptr;               // [adj_cap] staging descriptors of the rows
     long long* d_xref = nullptr;
     long long* d_energy = nullptr;           // [B][8] fixed-point sums
     long long* d_step = nullptr;             // [B]

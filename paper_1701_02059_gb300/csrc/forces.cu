@@ -307,7 +307,6 @@ struct NbrInfo {
     int cnt;
     int start;      // global slot of the first particle
     int ox, oy, oz; // exact offset c_l - c_k at 2^-26 sigma (wrap-around int32)
-    float fx, fy, fz;
 };
 
 template <typename T>
@@ -348,7 +347,6 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
     const int cs = v.cell_start[k], ce = v.cell_start[k + 1];
     const int a0 = v.adj_ptr[k];
     const int a1 = (int)min((long long)v.adj_ptr[k + 1], v.adj_cap);   // overflow is flagged by the adjacency pass
-    const long long ckx = v.cq[k], cky = v.cq[(size_t)v.Ktot + k], ckz = v.cq[(size_t)2 * v.Ktot + k];
     const float rs_b = I.rsf + kFilterBand;
     const float rs2f = rs_b * rs_b;
     const float rcl = sqrtf(I.rc2f_ll), rcw = sqrtf(I.rc2f_wca), rcp = sqrtf(I.rc2f_pp);
@@ -369,6 +367,83 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
         const int jsplit = warp / groups;
         const bool wactive = jsplit < nsplit;
         const int gs = (nti + groups - 1) / groups;             // balanced group size
+
+        // staging of one pass (warp 0): neighbour descriptors, bulk copies
+        auto issue = [&](const int na, const int na_off) {
+                if (warp == 0) {
+                    // one lane per neighbouring cell: counts, offsets, staging slots
+                    const int nn = na + lane;
+                    const bool has = nn < a1;
+                    int l = 0, st = 0, c = 0;
+                    AdjDesc d;
+                    if (has) {
+                        d = v.adjd[nn];
+                        l = d.cell;
+                        st = d.start;
+                        c = d.cnt;
+                        if (lane == 0) { st += na_off; c -= na_off; }
+                    }
+                    int incl = c;
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const int t = __shfl_up_sync(0xffffffffu, incl, off);
+                        if (lane >= off) incl += t;
+                    }
+                    const int excl = incl - c;
+                    const bool fits = has && incl <= kStageCap;
+                    const bool part = has && excl < kStageCap && incl > kStageCap;
+                    const unsigned fm = __ballot_sync(0xffffffffu, fits), pm = __ballot_sync(0xffffffffu, part);
+                    const int m = __popc(fm) + (pm ? 1 : 0);
+                    const bool staged = fits || part;
+                    const int take = part ? kStageCap - excl : c;
+                    if (staged) {
+                        NbrInfo inf;
+                        inf.base = excl; inf.cnt = take; inf.start = st;
+                        inf.ox = d.ox; inf.oy = d.oy; inf.oz = d.oz;
+                        nb[lane] = inf;
+                    }
+                    const unsigned selfm = __ballot_sync(0xffffffffu, staged && l == k);
+                    const int total = __shfl_sync(0xffffffffu, excl + take, max(m - 1, 0));
+                    // where the next pass starts: after the last fully staged
+                    // neighbour, or inside the partially staged one
+                    int nxt = na + __popc(fm), nxo = 0;
+                    if (pm) {
+                        const int p = __ffs(pm) - 1;
+                        const int ex_p = __shfl_sync(0xffffffffu, excl, p);
+                        nxt = na + p;
+                        nxo = (p == 0 ? na_off : 0) + (kStageCap - ex_p);
+                    }
+                    // staged range of the own cell, and where its first particle would sit
+                    int slo = -1, shi = -1, sb = 0;
+                    {
+                        const int p = selfm ? __ffs(selfm) - 1 : 0;
+                        const int ex_p = __shfl_sync(0xffffffffu, excl, p);
+                        const int tk_p = __shfl_sync(0xffffffffu, take, p);
+                        if (selfm) {
+                            slo = ex_p;
+                            shi = ex_p + tk_p;
+                            sb = ex_p - ((p == 0) ? na_off : 0);
+                        }
+                    }
+                    if (lane == 0) {
+                        s_nstage = m;
+                        s_total = m > 0 ? total : 0;
+                        s_next = nxt;
+                        s_next_off = nxo;
+                        s_self = sb; s_self_lo = slo; s_self_hi = shi;
+                    }
+                    if (m > 0) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        if (lane == 0) mbar_expect_tx(&bar, (unsigned)total * 32u);
+                        __syncwarp();
+                        if (staged && take > 0) {
+                            bulk_g2s(&sy[excl], v.mq + st, take * 16u, &bar);
+                            bulk_g2s(&so[excl], v.mo + st, take * 16u, &bar);
+                        }
+                    }
+                }
+        };
+        // the first pass's copies are in flight during the tile set-up
+        if (a0 < a1) issue(a0, 0);
 
         // ---- tangent frame of the cell and compact groups (ranks along the
         //      tile's longer tangent extent, prepared with the cell radii)
@@ -407,86 +482,13 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
 
         // passes over chunks of neighbouring cells (a cell larger than the
         // stage is split across passes)
+        bool first_pass = true;
         for (int na = a0, na_off = 0; na < a1;) {
-            __syncthreads();
-            if (warp == 0) {
-                // one lane per neighbouring cell: counts, offsets, staging slots
-                const int nn = na + lane;
-                const bool has = nn < a1;
-                int l = 0, st = 0, c = 0;
-                if (has) {
-                    l = v.adj[nn];
-                    st = v.cell_start[l];
-                    c = v.cell_start[l + 1] - st;
-                    if (lane == 0) { st += na_off; c -= na_off; }
-                }
-                int incl = c;
-                for (int off = 1; off < 32; off <<= 1) {
-                    const int t = __shfl_up_sync(0xffffffffu, incl, off);
-                    if (lane >= off) incl += t;
-                }
-                const int excl = incl - c;
-                const bool fits = has && incl <= kStageCap;
-                const bool part = has && excl < kStageCap && incl > kStageCap;
-                const unsigned fm = __ballot_sync(0xffffffffu, fits), pm = __ballot_sync(0xffffffffu, part);
-                const int m = __popc(fm) + (pm ? 1 : 0);
-                const bool staged = fits || part;
-                const int take = part ? kStageCap - excl : c;
-                if (staged) {
-                    const long long dx = minimg_q(v.cq[l] - ckx, I.boxq[0], I.periodic[0]);
-                    const long long dy = minimg_q(v.cq[(size_t)v.Ktot + l] - cky, I.boxq[1], I.periodic[1]);
-                    const long long dz = minimg_q(v.cq[(size_t)2 * v.Ktot + l] - ckz, I.boxq[2], I.periodic[2]);
-                    const long long ox = (dx + (1ll << (kMirrorShift - 1))) >> kMirrorShift;
-                    const long long oy = (dy + (1ll << (kMirrorShift - 1))) >> kMirrorShift;
-                    const long long oz = (dz + (1ll << (kMirrorShift - 1))) >> kMirrorShift;
-                    NbrInfo inf;
-                    inf.base = excl; inf.cnt = take; inf.start = st;
-                    inf.ox = (int)(unsigned)(unsigned long long)ox;
-                    inf.oy = (int)(unsigned)(unsigned long long)oy;
-                    inf.oz = (int)(unsigned)(unsigned long long)oz;
-                    inf.fx = 0.f; inf.fy = 0.f; inf.fz = 0.f;
-                    nb[lane] = inf;
-                }
-                const unsigned selfm = __ballot_sync(0xffffffffu, staged && l == k);
-                const int total = __shfl_sync(0xffffffffu, excl + take, max(m - 1, 0));
-                // where the next pass starts: after the last fully staged
-                // neighbour, or inside the partially staged one
-                int nxt = na + __popc(fm), nxo = 0;
-                if (pm) {
-                    const int p = __ffs(pm) - 1;
-                    const int ex_p = __shfl_sync(0xffffffffu, excl, p);
-                    nxt = na + p;
-                    nxo = (p == 0 ? na_off : 0) + (kStageCap - ex_p);
-                }
-                // staged range of the own cell, and where its first particle would sit
-                int slo = -1, shi = -1, sb = 0;
-                {
-                    const int p = selfm ? __ffs(selfm) - 1 : 0;
-                    const int ex_p = __shfl_sync(0xffffffffu, excl, p);
-                    const int tk_p = __shfl_sync(0xffffffffu, take, p);
-                    if (selfm) {
-                        slo = ex_p;
-                        shi = ex_p + tk_p;
-                        sb = ex_p - ((p == 0) ? na_off : 0);
-                    }
-                }
-                if (lane == 0) {
-                    s_nstage = m;
-                    s_total = m > 0 ? total : 0;
-                    s_next = nxt;
-                    s_next_off = nxo;
-                    s_self = sb; s_self_lo = slo; s_self_hi = shi;
-                }
-                if (m > 0) {
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    if (lane == 0) mbar_expect_tx(&bar, (unsigned)total * 32u);
-                    __syncwarp();
-                    if (staged && take > 0) {
-                        bulk_g2s(&sy[excl], v.mq + st, take * 16u, &bar);
-                        bulk_g2s(&so[excl], v.mo + st, take * 16u, &bar);
-                    }
-                }
+            if (!first_pass) {
+                __syncthreads();
+                issue(na, na_off);
             }
+            first_pass = false;
             __syncthreads();
             const int m = s_nstage;
             const int total = s_total;

@@ -65,6 +65,15 @@ struct Inst {
 };
 
 // ---------------------------------------------------------------- packed device arrays
+// What the pair kernel needs to stage neighbouring cell l of cell k: its
+// particle range and the exact offset c_l - c_k (minimum image) at the mirror
+// resolution 2^-26 sigma, as wrap-around int32.
+struct AdjDesc {
+    int start, cnt;
+    int ox, oy, oz;
+    int cell;
+};
+
 struct View {
     int B;                      // instances
     int N, Ktot;
@@ -93,6 +102,7 @@ struct View {
     double* R;                      // [Ktot] cell radius
     int* adj_ptr;                   // [Ktot+1]
     int* adj;                       // [adj_cap]
+    struct AdjDesc* adjd;           // [adj_cap] staging descriptor of each neighbouring cell
     long long adj_cap;
     // centroid search grid
     int* gstart;                    // [Gtot+1]
