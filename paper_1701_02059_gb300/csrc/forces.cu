@@ -218,7 +218,9 @@ template <> struct Acc<float> {
     bool used_big;
     __device__ void zero() { for (int a = 0; a < 3; a++) { f[a].zero(); t[a].zero(); } nf = 0; nt = 0; used_big = false; }
     __device__ void add3(const View& v, int p, SplitAcc* s, int& n, int c0, float x, float y, float z) {
-        if (fabsf(x) + fabsf(y) + fabsf(z) < 1000.0f) { s[0].add(x); s[1].add(y); s[2].add(z); n++; return; }
+        const float mag = fabsf(x) + fabsf(y) + fabsf(z);
+        if (mag < 1000.0f) { s[0].add(x); s[1].add(y); s[2].add(z); n++; return; }
+        if (!(mag < 1.0e30f)) atomicOr(v.status, kStatusNaN);    // NaN, infinite or absurd
         const size_t N = v.N;
         atomicAdd((unsigned long long*)&v.Fbig[(size_t)c0 * N + p], (unsigned long long)__float2ll_rn(x * 4294967296.0f));
         atomicAdd((unsigned long long*)&v.Fbig[(size_t)(c0 + 1) * N + p], (unsigned long long)__float2ll_rn(y * 4294967296.0f));
@@ -236,7 +238,8 @@ template <> struct Acc<double> {
     int np, nb;
     __device__ void zero() { for (int a = 0; a < 3; a++) { f[a] = 0; t[a] = 0; } np = 0; nb = 0; }
     __device__ static long long q(double v) { return __double2ll_rn(v * 4294967296.0); }
-    __device__ void add_pair(const View&, int, double fx, double fy, double fz, double tx, double ty, double tz) {
+    __device__ void add_pair(const View& v, int, double fx, double fy, double fz, double tx, double ty, double tz) {
+        if (!(fabs(fx) + fabs(fy) + fabs(fz) + fabs(tx) + fabs(ty) + fabs(tz) < 1.0e30)) atomicOr(v.status, kStatusNaN);
         f[0] += q(fx); f[1] += q(fy); f[2] += q(fz); t[0] += q(tx); t[1] += q(ty); t[2] += q(tz); np++;
     }
     __device__ void add_bond(const View&, int, double fx, double fy, double fz) { f[0] += q(fx); f[1] += q(fy); f[2] += q(fz); nb++; }

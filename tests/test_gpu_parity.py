@@ -297,6 +297,25 @@ def test_nonzero_spontaneous_curvature():
     g.close()
 
 
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_coincident_particles_report_non_finite_forces(precision):
+    """Two lipids at the same point make the pair force non-finite: the
+    kernels flag it and the call returns ORBC_E_NAN (no fault, no silent
+    garbage)."""
+    mem = M.flat_patch_2304(seed=5)
+    pos = mem.pos.copy()
+    pos[1] = pos[0]
+    kw = {"precision": G.F64_ALL} if precision == "f64" else {}
+    g = G.System(gpu_params(mem, **kw))
+    g.set_particles(pos, mem.vel, mem.ori, mem.angvel, mem.type, mem.id)
+    g.set_bonds(mem.bonds, mem.r0, mem.kb)
+    g.init_cells()
+    with pytest.raises(G.OrbcError) as e:
+        g.compute_forces()
+    assert e.value.code == -5
+    g.close()
+
+
 def test_errors_are_reported():
     mem = small_vesicle()
     g = G.System(gpu_params(mem))
