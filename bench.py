@@ -205,6 +205,25 @@ def run_ours(args, rank, world):
     breakdown = {k: round(v["ms"] / max(v["launches"], 1), 4) for k, v in times.items()}
 
     g.close()
+    # the FP64-everywhere variant of the same step (FP64 pair terms and
+    # increments), a few steps on the same workload
+    f64 = None
+    if args.precision == "f32" and not args.no_f64:
+        g64 = G.System(params_for(mem, "f64", G), stream=stream.cuda_stream)
+        g64.load_membrane(mem)
+        g64.init_cells()
+        g64.integrate(2)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n64 = max(2, args.steps // 4)
+        f0.record(stream)
+        g64.integrate(n64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1)
+        f64 = {"value": round(mem.n * n64 / (fms * 1e-3), 1), "unit": UNIT, "steps": n64,
+               "ms_per_step": round(fms / n64, 4), "dtype": "f64"}
+        g64.close()
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -241,9 +260,9 @@ def run_ours(args, rank, world):
                        "precision": ("FP32 forces, int64 fixed-point state (2^-40)" if args.precision == "f32"
                                      else "FP64 forces and increments, int64 fixed-point state"),
                        "rebuild_every": 1, "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (state and mirrors ~0.9 GB)"},
+                       "l2": "inputs larger than L2 (resident state, forces and mirrors ~1.4 GB)"},
             "roofline": roof, "kernel_ms_per_launch": breakdown, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clocks.summary(), "ensemble": ens}
+            "gpu_launches": launches, "clocks": clocks.summary(), "fp64_variant": f64, "ensemble": ens}
     return line
 
 
@@ -388,6 +407,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-vs-plain ensemble comparison")
+    ap.add_argument("--no-f64", action="store_true", help="skip the FP64-everywhere variant")
     ap.add_argument("--ensemble-steps", type=int, default=500)
     ap.add_argument("--requests", type=int, default=32, help="served-stream requests (workload serve)")
     ap.add_argument("--load", type=float, default=0.8, help="arrival rate / plain-form throughput (workload serve)")

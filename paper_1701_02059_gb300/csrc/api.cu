@@ -470,21 +470,25 @@ void Ensemble::energies(std::vector<double>& out) {
 
 void Ensemble::integrate(int nsteps) {
     if (!cells_valid) throw StateError("cells not initialised");
-    if (!forces_valid) {
-        launch_pairs(false, false);
-    }
+    if (!forces_valid) launch_pairs(false, false);
     for (int s = 0; s < nsteps; s++) {
-        step_body();
+        step_body(s > 0);
         for (auto& x : step_h) x++;
+    }
+    if (nsteps > 0) {
+        tic("integrate_kick");
+        launch_kick(false);
+        toc();
     }
     forces_valid = true;
     collect_times(kernel_times);
 }
 
-// One time step: B-A-O-A, cell rebuild (or mirrors), forces, B.
-void Ensemble::step_body() {
+// One time step without its final B: B-A-O-A (after the previous step's
+// final B when fused), cell rebuild (or mirrors), forces.
+void Ensemble::step_body(bool fused) {
     tic("integrate_baoa");
-    launch_integrate_first();
+    launch_integrate_first(fused);
     toc();
     const int re = prm_h[0].rebuild_every;
     bool due = (re <= 1) || ((step_h[0] + 1) % re == 0);
@@ -499,9 +503,6 @@ void Ensemble::step_body() {
         toc();
     }
     launch_pairs(false, false);
-    tic("integrate_kick");
-    launch_kick(false);
-    toc();
 }
 
 // ---------------------------------------------------------------- getters

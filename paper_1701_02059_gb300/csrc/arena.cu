@@ -177,21 +177,19 @@ void Ensemble::integrate_graph(int nsteps) {
         launch_pairs(false, false);
         forces_valid = true;
     }
-    int s = 0;
-    // the first step after a set-up seeds the E-step from the grid search
-    if (!prev_adj_valid_ && s < nsteps) {
-        step_body();
-        for (auto& x : step_h) x++;
-        s++;
-    }
-    for (; s < nsteps; s++) {
+    if (nsteps <= 0) return;
+    // the first step runs eagerly (unfused; after a set-up it also seeds the
+    // E-step from the grid search); the fused steps are graph replays
+    step_body(false);
+    for (auto& x : step_h) x++;
+    for (int s = 1; s < nsteps; s++) {
         const int p = cur_;
         if (!graph_[p]) {
             const long long l0 = launches, r0 = n_rebuilds;
             cudaGraph_t g = nullptr;
             CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
             try {
-                step_body();
+                step_body(true);
             } catch (...) {
                 cudaStreamEndCapture(stream, &g);
                 if (g) cudaGraphDestroy(g);
@@ -214,6 +212,7 @@ void Ensemble::integrate_graph(int nsteps) {
         n_rebuilds++;
         for (auto& x : step_h) x++;
     }
+    launch_kick(false);
     forces_valid = true;
 }
 

@@ -154,7 +154,7 @@ public:
     void morton_relabel();
     void finish_cells();
     void launch_pairs(bool energies, bool dump);
-    void launch_integrate_first();
+    void launch_integrate_first(bool fused);
     void launch_kick(bool energies);
     void mirrors();
 
@@ -167,7 +167,7 @@ private:
     void free_all();
     void alloc_core(const std::vector<int>& p0, const std::vector<int>& k0, bool any_skin);
     void upload_bonds(const std::vector<BondSpec>& bl, const std::vector<int>& p0);
-    void step_body();
+    void step_body(bool fused);   // fused: the previous step's final B is still due
     size_t bytes_ = 0;
     cudaGraphExec_t graph_[2] = {nullptr, nullptr};
     long long graph_launches_ = 0;

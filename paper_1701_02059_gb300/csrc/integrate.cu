@@ -95,8 +95,12 @@ __device__ inline void kick(long long vq[3], long long wq[3], const long long nq
     }
 }
 
-// B A O A of one step (the final B follows the force evaluation).
-template <typename T>
+// B A O A of one step (the final B follows the force evaluation).  FUSED:
+// first the final B of the previous step, whose forces are the same, then
+// this step's B A O A: the same two rounded updates as separate launches,
+// without a second pass over memory.  The previous step is then not yet
+// counted in steps[], so this step's index is steps[b] + 1.
+template <typename T, bool FUSED>
 __global__ void k_baoa(View v, const long long* __restrict__ steps) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= v.N) return;
@@ -109,14 +113,15 @@ __global__ void k_baoa(View v, const long long* __restrict__ steps) {
     long long xq[3], vq[3], nq[3] = {0, 0, 0}, wq[3] = {0, 0, 0};
     for (int a = 0; a < 3; a++) { xq[a] = v.xq[a * N + p]; vq[a] = v.vq[a * N + p]; }
     if (lipid) for (int a = 0; a < 3; a++) { nq[a] = v.nq[a * N + p]; wq[a] = v.wq[a * N + p]; }
-    // B
+    // (final B of the previous step), B
+    if (FUSED) kick<T>(vq, wq, nq, v, p, lipid, C);
     kick<T>(vq, wq, nq, v, p, lipid, C);
     // A
     for (int a = 0; a < 3; a++) xq[a] += V::grid(C.hdt * V::st(vq[a]));
     if (lipid) cayley<T>(nq, wq, C.hdt);
     // O
     const unsigned id = v.id[p];
-    const unsigned long long step = (unsigned long long)steps[b];
+    const unsigned long long step = (unsigned long long)steps[b] + (FUSED ? 1ull : 0ull);
     const uint2 key = make_uint2((unsigned)I.seed, (unsigned)(I.seed >> 32) ^ I.instance);
     uint4 w0 = philox4x32_10(make_uint4(id, (unsigned)step, (unsigned)(step >> 32), 0u), key);
     T xi[3] = { V::noise(w0.x), V::noise(w0.y), V::noise(w0.z) };
@@ -138,6 +143,11 @@ __global__ void k_baoa(View v, const long long* __restrict__ steps) {
     }
     for (int a = 0; a < 3; a++) { v.xq[a * N + p] = xq[a]; v.vq[a * N + p] = vq[a]; }
     if (lipid) for (int a = 0; a < 3; a++) { v.nq[a * N + p] = nq[a]; v.wq[a * N + p] = wq[a]; }
+}
+
+// Counts the previous step after a fused launch read the counters.
+__global__ void k_step_advance(long long* __restrict__ steps, int B) {
+    for (int b = threadIdx.x; b < B; b += blockDim.x) steps[b] += 1;
 }
 
 // Final B of the step; advances the step counter of every instance.
@@ -195,10 +205,19 @@ __global__ void k_kinetic(View v, long long* __restrict__ energy) {
 
 static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
-void Ensemble::launch_integrate_first() {
-    if (precision == 0) k_baoa<float><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
-    else k_baoa<double><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
+void Ensemble::launch_integrate_first(bool fused) {
+    if (precision == 0) {
+        if (fused) k_baoa<float, true><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
+        else k_baoa<float, false><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
+    } else {
+        if (fused) k_baoa<double, true><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
+        else k_baoa<double, false><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
+    }
     launches++;
+    if (fused) {
+        k_step_advance<<<1, 64, 0, stream>>>(d_step, B);
+        launches++;
+    }
     CK(cudaGetLastError());
 }
 
