@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 
 #include "../../include/orbc.h"
@@ -11,14 +12,41 @@
 namespace orbc {
 
 // ============================================================== Ensemble basics
-Ensemble::Ensemble(cudaStream_t s) : stream(s) {}
+// Device memory comes from the stream-ordered pool, which keeps freed blocks
+// for reuse (batches are re-packed while the arena runs); the pool is trimmed
+// when a system or an arena is destroyed.
+static void keep_pool_memory() {
+    static std::mutex mu;
+    static bool done[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); return; }
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        unsigned long long thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done[dev] = true;
+}
+
+void trim_pool() {
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess)
+        cudaMemPoolTrimTo(pool, 0);
+    cudaGetLastError();
+}
+
+Ensemble::Ensemble(cudaStream_t s) : stream(s) { keep_pool_memory(); }
 
 Ensemble::~Ensemble() { free_all(); }
 
 void Ensemble::free_all() {
     for (int q = 0; q < 2; q++)
         if (graph_[q]) { cudaGraphExecDestroy(graph_[q]); graph_[q] = nullptr; }
-    for (void* p : allocs_) cudaFree(p);
+    for (void* p : allocs_) cudaFreeAsync(p, stream);
     allocs_.clear();
     bytes_ = 0;
     for (int* p : scan_tmp_) if (p) cudaFree(p);
@@ -35,7 +63,7 @@ template <typename T>
 T* Ensemble::alloc(size_t count) {
     void* p = nullptr;
     size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-    cudaError_t e = cudaMalloc(&p, bytes);
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         throw CudaError(cudaErrorMemoryAllocation, "device allocation of " + std::to_string(bytes) + " bytes failed");
@@ -209,6 +237,8 @@ void Ensemble::alloc_core(const std::vector<int>& p0, const std::vector<int>& k0
     d_dmax = alloc<unsigned>(B);
     d_fbcount = alloc<int>(1);
     d_adjpad = alloc<int>((size_t)Ktot * 64);
+    d_seglist = alloc<int>((size_t)2 * Ktot);
+    d_seglist_n = alloc<int>(2);
     d_adjd = alloc<AdjDesc>(adj_cap);
     prev_adj_valid_ = false;
     d_energy = alloc<long long>((size_t)8 * B);
@@ -948,6 +978,8 @@ void orbc_destroy(orbc_system* s) {
     if (s->ens) {
         cudaStreamSynchronize(s->stream);
         delete s->ens;
+        cudaStreamSynchronize(s->stream);
+        trim_pool();
     }
     if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;

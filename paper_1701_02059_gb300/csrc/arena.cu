@@ -17,8 +17,9 @@ namespace orbc {
 // ---------------------------------------------------------------- snapshots
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-void Snapshot::allocate(int n_, int K_) {
+void Snapshot::allocate(int n_, int K_, cudaStream_t st) {
     release();
+    stream = st;
     n = n_;
     K = K_;
     const size_t s_state = align256(sizeof(long long) * 3 * (size_t)n);
@@ -27,7 +28,7 @@ void Snapshot::allocate(int n_, int K_) {
     const size_t s_cs = align256(sizeof(int) * ((size_t)K + 1));
     const size_t s_cq = align256(sizeof(long long) * 3 * (size_t)K);
     bytes = 6 * s_state + s_u8 + 2 * s_i32 + s_cs + s_cq;
-    if (cudaMalloc(&block, bytes) != cudaSuccess) {
+    if (cudaMallocAsync(&block, bytes, stream) != cudaSuccess) {
         cudaGetLastError();
         block = nullptr;
         throw CudaError(cudaErrorMemoryAllocation, "snapshot allocation failed");
@@ -44,7 +45,7 @@ void Snapshot::allocate(int n_, int K_) {
 }
 
 void Snapshot::release() {
-    if (block) cudaFree(block);
+    if (block) cudaFreeAsync(block, stream);
     block = nullptr;
     bytes = 0;
 }
@@ -71,7 +72,7 @@ void Ensemble::export_instance(int b, Snapshot& s) {
     if (!cells_valid || !forces_valid) throw StateError("instance has no cell list or forces to carry");
     const Inst& I = inst_h[b];
     const int n = I.n, K = I.K;
-    s.allocate(n, K);
+    s.allocate(n, K, stream);
     s.inst = I;
     s.prm = prm_h[b];
     s.step = step_h[b];
@@ -235,6 +236,8 @@ public:
     ~Arena() {
         batch_.reset();
         slots_.clear();
+        cudaStreamSynchronize(stream_);
+        trim_pool();
         if (own_stream_) cudaStreamDestroy(stream_);
     }
 

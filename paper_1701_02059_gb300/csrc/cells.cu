@@ -824,6 +824,74 @@ __global__ void k_segcopy(int N, const int* __restrict__ cell, const int* __rest
     if (start[c + 1] - start[c] > kSegMax) tmp[q] = src[q];
 }
 
+// Cells that the warp sort cannot take: 128 < n <= kSegMax into list A
+// (block bitonic), n > kSegMax into list B (exact rank); counts in cnt[0..1].
+__global__ void k_seglist(int Ktot, const int* __restrict__ start, int* __restrict__ la, int* __restrict__ lb,
+                          int* __restrict__ cnt) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = (k < Ktot) ? start[k + 1] - start[k] : 0;
+    const bool a = n > 128 && n <= kSegMax, bb = n > kSegMax;
+    const int lane = threadIdx.x & 31;
+    const unsigned ma = __ballot_sync(0xffffffffu, a), mb = __ballot_sync(0xffffffffu, bb);
+    int baseA = 0, baseB = 0;
+    if (ma && lane == __ffs(ma) - 1) baseA = atomicAdd(&cnt[0], __popc(ma));
+    if (mb && lane == __ffs(mb) - 1) baseB = atomicAdd(&cnt[1], __popc(mb));
+    baseA = __shfl_sync(0xffffffffu, baseA, ma ? __ffs(ma) - 1 : 0);
+    baseB = __shfl_sync(0xffffffffu, baseB, mb ? __ffs(mb) - 1 : 0);
+    const unsigned lt = (1u << lane) - 1u;
+    if (a) la[baseA + __popc(ma & lt)] = k;
+    if (bb) lb[baseB + __popc(mb & lt)] = k;
+}
+
+// List A: one block per cell, bitonic sort of its slot list in shared memory.
+__global__ void k_segsort_list(const int* __restrict__ start, const int* __restrict__ la, const int* __restrict__ cnt,
+                               int* __restrict__ tmp) {
+    __shared__ int sh[kSegMax];
+    const int nl = cnt[0];
+    for (int e = blockIdx.x; e < nl; e += gridDim.x) {
+        const int k = la[e];
+        const int s0 = start[k], n = start[k + 1] - s0;
+        int m = 1;
+        while (m < n) m <<= 1;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) sh[t] = (t < n) ? tmp[s0 + t] : 0x7fffffff;
+        __syncthreads();
+        for (int size = 2; size <= m; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                    const int p = t ^ stride;
+                    if (p > t) {
+                        const bool up = (t & size) == 0;
+                        const int a = sh[t], c = sh[p];
+                        if ((c < a) == up) { sh[t] = c; sh[p] = a; }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int t = threadIdx.x; t < n; t += blockDim.x) tmp[s0 + t] = sh[t];
+        __syncthreads();
+    }
+}
+
+// List B: one block per cell; every slot's rank among the cell's slots (they
+// are distinct), written to out, then copied back.
+__global__ void k_segrank_list(const int* __restrict__ start, const int* __restrict__ lb, const int* __restrict__ cnt,
+                               int* __restrict__ tmp, int* __restrict__ out) {
+    const int nl = cnt[1];
+    for (int e = blockIdx.x; e < nl; e += gridDim.x) {
+        const int k = lb[e];
+        const int s0 = start[k], s1 = start[k + 1];
+        for (int q = s0 + threadIdx.x; q < s1; q += blockDim.x) {
+            const int me = tmp[q];
+            int r = 0;
+            for (int t = s0; t < s1; t++) r += (tmp[t] < me);
+            out[s0 + r] = me;
+        }
+        __syncthreads();
+        for (int q = s0 + threadIdx.x; q < s1; q += blockDim.x) tmp[q] = out[q];
+        __syncthreads();
+    }
+}
+
 // ============================================================== gather + mirrors
 __device__ inline int mirror_coord(long long xq, long long cq, const Inst& I, int a, unsigned* status) {
     long long d = minimg_q(xq - cq, I.boxq[a], I.periodic[a]);
@@ -1051,10 +1119,12 @@ __global__ void k_adj_warp(View v, const unsigned long long* __restrict__ rmax_b
         if (ex || lb > reach) break;
     }
     int lo[3], ext[3];
+    bool full[3];
     for (int a = 0; a < 3; a++) {
         int l, h;
+        full[a] = false;
         if (I.periodic[a]) {
-            if (2 * R + 1 >= I.gdim[a]) { l = 0; h = I.gdim[a] - 1; }
+            if (2 * R + 1 >= I.gdim[a]) { l = 0; h = I.gdim[a] - 1; full[a] = true; }
             else { l = g[a] - R; h = g[a] + R; }
         } else {
             l = max(0, g[a] - R);
@@ -1063,12 +1133,27 @@ __global__ void k_adj_warp(View v, const unsigned long long* __restrict__ rmax_b
         lo[a] = l;
         ext[a] = h - l + 1;
     }
+    const float reach2 = reach * reach;
     if (lane == 0) rown[wb] = 0;
     __syncwarp();
     float rho = reach - kBandA;
     const int M = ext[0] * ext[1] * ext[2];
     for (int t = lane; t < M; t += 32) {
         const int x = lo[0] + t % ext[0], y = lo[1] + (t / ext[0]) % ext[1], z = lo[2] + t / (ext[0] * ext[1]);
+        // grid cells entirely beyond the reach hold no candidate (edge cells
+        // of non-periodic axes extend to infinity)
+        {
+            const int u[3] = {x, y, z};
+            float d2 = 0.f;
+            for (int a = 0; a < 3; a++) {
+                if (full[a]) continue;
+                const float cl = (!I.periodic[a] && u[a] == 0) ? -3.0e38f : u[a] * I.gh[a];
+                const float ch = (!I.periodic[a] && u[a] == I.gdim[a] - 1) ? 3.0e38f : (u[a] + 1) * I.gh[a];
+                const float d = fmaxf(fmaxf(cl - p[a], p[a] - ch), 0.f);
+                d2 = fmaf(d, d, d2);
+            }
+            if (d2 > reach2) continue;
+        }
         const int w0 = I.periodic[0] ? wrap_idx(x, I.gdim[0]) : x;
         const int w1 = I.periodic[1] ? wrap_idx(y, I.gdim[1]) : y;
         const int w2 = I.periodic[2] ? wrap_idx(z, I.gdim[2]) : z;
@@ -1249,13 +1334,12 @@ void Ensemble::finish_cells() {
     k_scatter<<<nblk(N, 256), 256, 0, stream>>>(N, d_cell_new, d_cell_start, d_cnt, d_perm);
     launches++;
     k_segsort_warp<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(Ktot, d_cell_start, d_perm);
-    launches++;
-    k_segsort<<<std::min(Ktot, 1024), 256, 0, stream>>>(Ktot, d_cell_start, d_perm, d_status);
-    launches++;
-    k_segrank<<<nblk(N, 256), 256, 0, stream>>>(N, d_cell_new, d_cell_start, d_perm, d_cell_tmp);
-    launches++;
-    k_segcopy<<<nblk(N, 256), 256, 0, stream>>>(N, d_cell_new, d_cell_start, d_cell_tmp, d_perm);
-    launches++;
+    // larger cells (rare) from lists, so that no launch scans every cell or particle
+    CK(cudaMemsetAsync(d_seglist_n, 0, sizeof(int) * 2, stream));
+    k_seglist<<<nblk(Ktot, 256), 256, 0, stream>>>(Ktot, d_cell_start, d_seglist, d_seglist + Ktot, d_seglist_n);
+    k_segsort_list<<<152, 256, 0, stream>>>(d_cell_start, d_seglist, d_seglist_n, d_perm);
+    k_segrank_list<<<152, 256, 0, stream>>>(d_cell_start, d_seglist + Ktot, d_seglist_n, d_perm, d_cell_tmp);
+    launches += 4;
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(d_cnt, 0, sizeof(int) * (Ktot + 1), stream));
     // gather into the second buffer set, then swap

@@ -86,10 +86,15 @@ struct Snapshot {
     long long* T = nullptr;                   // [3][n]
     void* block = nullptr;                    // one device allocation holding all of the above
     size_t bytes = 0;
-    void allocate(int n_, int K_);
+    cudaStream_t stream = nullptr;            // allocation and release are stream-ordered
+    void allocate(int n_, int K_, cudaStream_t st);
     void release();
     ~Snapshot() { release(); }
 };
+
+// Releases the stream-ordered pool's cached blocks (after a system or arena
+// is destroyed).
+void trim_pool();
 
 class Ensemble {
 public:
@@ -223,6 +228,8 @@ public:
     unsigned* d_dmax = nullptr;              // [B] largest centroid move of the last M-step (float bits)
     int* d_fbcount = nullptr;                // particles the certified E-step left to the grid search
     int* d_adjpad = nullptr;                 // [Ktot][64] neighbouring-cell rows before compaction
+    int* d_seglist = nullptr;                // [2][Ktot] cells for the block sort / the rank sort
+    int* d_seglist_n = nullptr;              // [2] their counts
     AdjDesc* d_adjd = nullptr;               // [adj_cap] staging descriptors of the rows
     long long* d_xref = nullptr;
     long long* d_energy = nullptr;           // [B][8] fixed-point sums

@@ -144,6 +144,33 @@ def test_trajectory_100_steps_fp32(name):
     g.close()
 
 
+def test_vesicle_62k_1000_steps():
+    """The vesicle workload for its full 1,000 steps with FP32 forces: the run
+    stays finite, its final cell list is exact for its own state (Voronoi
+    invariant, pair set equal to the O(N^2) brute force), and the Langevin
+    thermostat holds the kinetic temperatures at kT (3/2 kT translational,
+    kT rotational per lipid; statistical over 62k particles)."""
+    mem = M.vesicle_62k()
+    g = G.System(gpu_params(mem))
+    g.load_membrane(mem)
+    g.init_cells()
+    g.integrate(1000)
+    st = g.state()
+    assert st["step"] == 1000
+    assert np.isfinite(st["pos"]).all() and np.isfinite(st["vel"]).all()
+    cg = g.cells()
+    assert np.array_equal(cg["cell_of_id"], oracle.assign_brute(st["pos"], cg["centroids"], mem.box, mem.periodic))
+    m = oracle.model(box=mem.box, periodic=mem.periodic)
+    brute = sorted_pairs(oracle.pairs_brute(m, st["pos"], mem.type, mem.id, mem.bonds))
+    assert np.array_equal(g.pairs(), brute)
+    ke = 0.5 * (st["vel"] ** 2).sum(1).mean()
+    assert abs(ke / (1.5 * mem.kT) - 1.0) < 0.03, ke
+    lip = mem.type == 0
+    kr = 0.5 * (st["angvel"][lip] ** 2).sum(1).mean()
+    assert abs(kr / mem.kT - 1.0) < 0.03, kr
+    g.close()
+
+
 def test_fp64_path_patch_200_steps():
     """The 2,304-particle patch with FP64 forces and increments: forces to
     the fixed-point resolution, 200-step trajectory within 1e-9 sigma RMS."""
