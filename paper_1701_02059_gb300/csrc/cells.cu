@@ -1137,38 +1137,44 @@ __global__ void k_adj_warp(View v, const unsigned long long* __restrict__ rmax_b
     if (lane == 0) rown[wb] = 0;
     __syncwarp();
     float rho = reach - kBandA;
-    const int M = ext[0] * ext[1] * ext[2];
-    for (int t = lane; t < M; t += 32) {
-        const int x = lo[0] + t % ext[0], y = lo[1] + (t / ext[0]) % ext[1], z = lo[2] + t / (ext[0] * ext[1]);
-        // grid cells entirely beyond the reach hold no candidate (edge cells
-        // of non-periodic axes extend to infinity)
-        {
-            const int u[3] = {x, y, z};
-            float d2 = 0.f;
-            for (int a = 0; a < 3; a++) {
-                if (full[a]) continue;
-                const float cl = (!I.periodic[a] && u[a] == 0) ? -3.0e38f : u[a] * I.gh[a];
-                const float ch = (!I.periodic[a] && u[a] == I.gdim[a] - 1) ? 3.0e38f : (u[a] + 1) * I.gh[a];
-                const float d = fmaxf(fmaxf(cl - p[a], p[a] - ch), 0.f);
-                d2 = fmaf(d, d, d2);
-            }
-            if (d2 > reach2) continue;
-        }
-        const int w0 = I.periodic[0] ? wrap_idx(x, I.gdim[0]) : x;
+    // one lane per (y, z) row of the cube: the row's grid cells are
+    // contiguous along x, and so are their centroids in grid order (one or
+    // two segments when a periodic x range wraps)
+    auto axis_gap = [&](int a, int u) {
+        if (full[a]) return 0.f;
+        const float cl = (!I.periodic[a] && u == 0) ? -3.0e38f : u * I.gh[a];
+        const float ch = (!I.periodic[a] && u == I.gdim[a] - 1) ? 3.0e38f : (u + 1) * I.gh[a];
+        return fmaxf(fmaxf(cl - p[a], p[a] - ch), 0.f);
+    };
+    const int rows = ext[1] * ext[2];
+    for (int t = lane; t < rows; t += 32) {
+        const int y = lo[1] + t % ext[1], z = lo[2] + t / ext[1];
+        const float gy = axis_gap(1, y), gz = axis_gap(2, z);
+        if (fmaf(gy, gy, gz * gz) > reach2) continue;      // the whole row is beyond the reach
         const int w1 = I.periodic[1] ? wrap_idx(y, I.gdim[1]) : y;
         const int w2 = I.periodic[2] ? wrap_idx(z, I.gdim[2]) : z;
-        const long long gg = I.g0 + ((long long)w2 * I.gdim[1] + w1) * I.gdim[0] + w0;
-        const int q1 = v.gstart[gg + 1];
-        for (int q = v.gstart[gg]; q < q1; q++) {
-            const float4 c = v.gcf[q];
-            const int j = __float_as_int(c.w);
-            const float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1), dz = axis_dist(p[2], c.z, I, 2);
-            const float df = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-            if (adj_test(v, I, k, j, Rk, df, cx, cy, cz, tail)) {
-                const int at = atomicAdd(&rown[wb], 1);
-                if (at < kAdjRow) row[wb][at] = j;
-            } else {
-                rho = fminf(rho, df);
+        const long long rowbase = I.g0 + ((long long)w2 * I.gdim[1] + w1) * I.gdim[0];
+        int xa[2], xb[2], nseg = 1;
+        xa[0] = lo[0];
+        xb[0] = lo[0] + ext[0] - 1;
+        if (I.periodic[0] && !full[0]) {
+            const int a0 = wrap_idx(xa[0], I.gdim[0]), b0 = wrap_idx(xb[0], I.gdim[0]);
+            if (a0 <= b0) { xa[0] = a0; xb[0] = b0; }
+            else { xa[0] = a0; xb[0] = I.gdim[0] - 1; xa[1] = 0; xb[1] = b0; nseg = 2; }
+        }
+        for (int sg = 0; sg < nseg; sg++) {
+            const int q1 = v.gstart[rowbase + xb[sg] + 1];
+            for (int q = v.gstart[rowbase + xa[sg]]; q < q1; q++) {
+                const float4 c = v.gcf[q];
+                const int j = __float_as_int(c.w);
+                const float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1), dz = axis_dist(p[2], c.z, I, 2);
+                const float df = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                if (adj_test(v, I, k, j, Rk, df, cx, cy, cz, tail)) {
+                    const int at = atomicAdd(&rown[wb], 1);
+                    if (at < kAdjRow) row[wb][at] = j;
+                } else {
+                    rho = fminf(rho, df);
+                }
             }
         }
     }
