@@ -150,6 +150,24 @@ def pairs_traffic(n_particles: int):
     return round(float(m.group(1)) * n_particles)
 
 
+def max_over_ranks(ms: float, world: int) -> float:
+    """The slowest rank's time (replicas run independently; this all-reduce
+    is the only cross-rank exchange, and it happens outside the timed work)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(particles_per_rank: int, steps: int, world: int, ms: float) -> float:
+    """Particle-steps per second of all ranks together over the slowest rank's time."""
+    return particles_per_rank * steps * world / (ms * 1e-3)
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -182,12 +200,8 @@ def run_ours(args, rank, world):
     launches = g.launch_count() - launches0
     times = g.kernel_times()
     g.set_timing(False)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = mem.n * args.steps * world / (ms * 1e-3)
+    ms = max_over_ranks(ms, world)
+    value = whole_job_rate(mem.n, args.steps, world, ms)
 
     # roofline of the dominant kernel (pair forces: plain FP32 ALU work)
     pk = times.get("pairs", {"ms": float("nan"), "launches": 1})
@@ -338,15 +352,24 @@ def ensemble_jobs(n_instances: int, steps: int):
 
 
 def run_ensemble(n_instances=64, steps=500, budget_gb=120.0, max_steps=500):
-    """Batched arena against one-instance-per-launch on the same GPU."""
+    """Batched arena against one-instance-per-launch on the same GPU; the
+    cell size (particles per Voronoi cell) of every member is the one the
+    autotuner picks on the largest member."""
     import torch
+    import paper_1701_02059_gb300 as G
     from paper_1701_02059_gb300 import serving
     jobs = ensemble_jobs(n_instances, steps)
+    big = max(jobs, key=lambda j: j["mem"].n)
+    K, _ = G.autotune(big["params"], big["mem"], steps=10)
+    ppc = big["mem"].n / K
+    for j in jobs:
+        j["params"].n_centroids = max(1, round(j["mem"].n / ppc))
     torch.cuda.synchronize()
     _, sb, _ = serving.serve_batched(jobs, int(budget_gb * 2**30), max_steps=max_steps)
     _, sp, _ = serving.serve_plain(jobs)
     keep = ("p50_s", "p99_s", "makespan_s", "particle_steps_per_s")
     return {"instances": n_instances, "steps": steps, "particles": sum(j["mem"].n for j in jobs),
+            "particles_per_cell": round(ppc, 1),
             "batched": {k: round(sb[k], 4) for k in keep} | {"gpu_launches": sb["gpu_launches"]},
             "plain": {k: round(sp[k], 4) for k in keep},
             "p99_speedup": round(sp["p99_s"] / sb["p99_s"], 3),

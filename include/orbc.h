@@ -225,6 +225,22 @@ ORBC_API int orbc_get_launch_count(orbc_system* s, long long* count);
 ORBC_API const char* orbc_last_error(const orbc_system* s);
 ORBC_API void orbc_destroy(orbc_system* s);
 
+/* Autotuner of the cell-tile shape (no counterpart in the paper, which fixes
+ * the cell count by hand): times the real step ("Spatial Searching
+ * Algorithm" + "Force Evaluation": initialisation, then `steps` timed steps)
+ * of a copy of the given system for several particles-per-cell sizes (32,
+ * 45, 61, 80, 100) and writes the fastest centroid count to
+ * *n_centroids_out (and its ms per step to *ms_per_step_out, nullable).
+ * Arrays as in orbc_set_particles / orbc_set_bonds (host, copied);
+ * params->n_centroids is ignored.  cache_path (nullable): a text file of
+ * "shape K ms" lines; a system of the same shape (counts, periodic box,
+ * precision, extent) is answered from it without timing, and new results
+ * are appended.  Errors: ORBC_E_ARG, ORBC_E_NOMEM, ORBC_E_CUDA, ORBC_E_STATE. */
+ORBC_API int orbc_autotune(const orbc_params* params, int n, const double* pos, const double* vel, const double* ori,
+                           const double* angvel, const unsigned char* type, const unsigned* id, int nb, const int* ij,
+                           const double* r0, const double* kb, int steps, const char* cache_path,
+                           int* n_centroids_out, double* ms_per_step_out);
+
 /* ------------------------------------------------------------------------
  * Batched arena and continuous batching.  The paper runs one membrane per
  * process; these calls have no counterpart in it.  They keep many

@@ -15,7 +15,7 @@ import numpy as np
 from . import _native
 from ._native import F32_FORCE_F64_STATE, F64_ALL, OrbcError, Params, default_params, load
 
-__all__ = ["System", "Arena", "Params", "default_params", "load", "OrbcError", "F32_FORCE_F64_STATE", "F64_ALL"]
+__all__ = ["System", "Arena", "autotune", "Params", "default_params", "load", "OrbcError", "F32_FORCE_F64_STATE", "F64_ALL"]
 
 
 def _p(a):
@@ -48,6 +48,24 @@ def cell_sort(cell, K: int, stream=None):
     if rc != 0:
         raise OrbcError(rc, "orbc_cell_sort")
     return perm, start
+
+
+def autotune(params: Params, mem, steps: int = 10, cache: str | None = None):
+    """orbc_autotune: the centroid count (cell-tile shape) with the fastest
+    step for this membrane; returns (n_centroids, ms_per_step)."""
+    arrs = [np.ascontiguousarray(mem.pos, np.float64), np.ascontiguousarray(mem.vel, np.float64),
+            np.ascontiguousarray(mem.ori, np.float64), np.ascontiguousarray(mem.angvel, np.float64),
+            np.ascontiguousarray(mem.type, np.uint8), np.ascontiguousarray(mem.id, np.uint32)]
+    ij = np.ascontiguousarray(mem.bonds, np.int32)
+    r0 = np.ascontiguousarray(mem.r0, np.float64)
+    kb = np.ascontiguousarray(mem.kb, np.float64)
+    K = C.c_int(0)
+    ms = C.c_double(0.0)
+    rc = load().orbc_autotune(C.byref(params), len(arrs[4]), *[_p(a) for a in arrs], len(r0), _p(ij), _p(r0), _p(kb),
+                              int(steps), cache.encode() if cache else None, C.byref(K), C.byref(ms))
+    if rc != 0:
+        raise OrbcError(rc, "orbc_autotune")
+    return K.value, ms.value
 
 
 class System:

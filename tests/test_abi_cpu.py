@@ -92,3 +92,18 @@ def test_arena_null_handles_and_arguments_are_rejected(lib):
     assert L.orbc_arena_launch_count(None) == -1
     assert L.orbc_arena_last_error(None) == b"null handle"
     L.orbc_arena_destroy(None)
+
+
+def test_autotune_rejects_bad_arguments(lib):
+    from paper_1701_02059_gb300 import _native
+    L = _native.load()
+    p = _native.default_params()
+    K = C.c_int(0)
+    assert L.orbc_autotune(None, 1, None, None, None, None, None, None, 0, None, None, None, 5, None, C.byref(K),
+                           None) == _native.ORBC_E_ARG
+    assert L.orbc_autotune(C.byref(p), 1, None, None, None, None, None, None, 0, None, None, None, 0, None, C.byref(K),
+                           None) == _native.ORBC_E_ARG                # no timed steps
+    assert L.orbc_autotune(C.byref(p), 1, None, None, None, None, None, None, 0, None, None, None, 5, None, None,
+                           None) == _native.ORBC_E_ARG                # no output
+    assert L.orbc_autotune(C.byref(p), 4, None, None, None, None, None, None, 0, None, None, None, 5, None, C.byref(K),
+                           None) == _native.ORBC_E_ARG                # null particle arrays
