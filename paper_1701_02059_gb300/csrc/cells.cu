@@ -900,123 +900,90 @@ __device__ inline int mirror_coord(long long xq, long long cq, const Inst& I, in
     return (int)r;
 }
 
-__global__ void k_gather(View v, View o, const int* __restrict__ perm, const int* __restrict__ cell_new,
-                         long long* __restrict__ xref) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= v.N) return;
-    int s = perm[p];
-    size_t N = v.N;
-    int c = cell_new[s];
-    int b = find_inst(v.inst_p0, v.B, p);
-    const Inst& I = v.inst[b];
-    long long x[3];
-    for (int a = 0; a < 3; a++) {
-        x[a] = o.xq[a * N + s];
-        v.xq[a * N + p] = x[a];
-        v.vq[a * N + p] = o.vq[a * N + s];
-        v.nq[a * N + p] = o.nq[a * N + s];
-        v.wq[a * N + p] = o.wq[a * N + s];
-        if (xref) xref[a * N + p] = x[a];
-    }
-    unsigned char t = o.type[s];
-    unsigned id = o.id[s];
-    v.type[p] = t;
-    v.id[p] = id;
-    v.cell[p] = c;
-    v.slot_of_id[I.p0 + id] = p;
-    int4 m;
-    m.x = mirror_coord(x[0], v.cq[c], I, 0, v.status);
-    m.y = mirror_coord(x[1], v.cq[(size_t)v.Ktot + c], I, 1, v.status);
-    m.z = mirror_coord(x[2], v.cq[(size_t)2 * v.Ktot + c], I, 2, v.status);
-    m.w = t;
-    v.mq[p] = m;
-    float4 no;
-    no.x = ll_to_float(v.nq[p]) * (float)kGridInv;
-    no.y = ll_to_float(v.nq[N + p]) * (float)kGridInv;
-    no.z = ll_to_float(v.nq[2 * N + p]) * (float)kGridInv;
-    no.w = __int_as_float(p);
-    v.mo[p] = no;
-}
-
-// Mirrors of the current order (after integration without a rebuild).
-__global__ void k_mirrors(View v) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= v.N) return;
-    size_t N = v.N;
-    int c = v.cell[p];
-    int b = find_inst(v.inst_p0, v.B, p);
-    const Inst& I = v.inst[b];
-    int4 m;
-    m.x = mirror_coord(v.xq[p], v.cq[c], I, 0, v.status);
-    m.y = mirror_coord(v.xq[N + p], v.cq[(size_t)v.Ktot + c], I, 1, v.status);
-    m.z = mirror_coord(v.xq[2 * N + p], v.cq[(size_t)2 * v.Ktot + c], I, 2, v.status);
-    m.w = v.type[p];
-    v.mq[p] = m;
-    float4 no;
-    no.x = ll_to_float(v.nq[p]) * (float)kGridInv;
-    no.y = ll_to_float(v.nq[N + p]) * (float)kGridInv;
-    no.z = ll_to_float(v.nq[2 * N + p]) * (float)kGridInv;
-    no.w = __int_as_float(p);
-    v.mo[p] = no;
-}
-
-// ============================================================== cell radius
-// R_k = max_i |x_i - c_k| over the cell (all types), equal to the FP64
-// definition: FP32 from the exact mirror (error < 1e-6 sigma) finds the
-// candidates within band of the maximum, FP64 decides among them.
+// Cell radius R_k = max_i |x_i - c_k| over the cell (all types), equal to
+// the FP64 definition: FP32 from the exact mirror (error < 1e-6 sigma) finds
+// the candidates within this band of the maximum, FP64 decides among them.
 constexpr float kBandR = 1e-5f;
-// Also prepares the pair kernel's per-cell frame and particle groups: the
-// cell normal (mean lipid director, unit; +z when the cell has no lipid
-// direction) and, in each tile of 128 particles, every particle's rank
-// along the tile's longer extent in the tangent plane.  Launched with 256
-// threads (8 warps, one cell each).
-__global__ void k_radius(View v, unsigned long long* __restrict__ rmax_bits /* [B] */) {
+
+// Gather of the cell-sorted state, fused with the per-cell quantities that
+// read it back: one warp per new cell moves its particles (state, type, id,
+// slot, mirrors) and computes the cell radius R_k = max |x - c_k| (FP32 with
+// the FP64 definition inside a band), the pair kernel's cell normal (mean
+// lipid director, unit; +z without lipid direction) and, in each tile of 128
+// particles, every particle's rank along the tile's longer tangent extent.
+// Launched with 256 threads (8 warps, one cell each).
+__global__ void k_gather_cells(View v, View o, const int* __restrict__ perm, long long* __restrict__ xref,
+                               unsigned long long* __restrict__ rmax_bits /* [B] */) {
     __shared__ float skey[8][128];
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     const int wb = threadIdx.x >> 5;
-    if (warp >= v.Ktot) return;
-    int k = warp;
-    int b = find_inst(v.inst_k0, v.B, k);
+    if (k >= v.Ktot) return;
+    const int b = find_inst(v.inst_k0, v.B, k);
     const Inst& I = v.inst[b];
-    int s = v.cell_start[k], e = v.cell_start[k + 1];
-    float mx = 0.f;
+    const int s = v.cell_start[k], e = v.cell_start[k + 1];
+    const size_t N = v.N;
+    const long long ck[3] = {v.cq[k], v.cq[(size_t)v.Ktot + k], v.cq[(size_t)2 * v.Ktot + k]};
+    float mx = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
     for (int p = s + lane; p < e; p += 32) {
-        int4 m = v.mq[p];
-        float dx = m.x * kMirrorUnit, dy = m.y * kMirrorUnit, dz = m.z * kMirrorUnit;
+        const int so = perm[p];
+        long long x[3], nq[3];
+        for (int a = 0; a < 3; a++) {
+            x[a] = o.xq[a * N + so];
+            nq[a] = o.nq[a * N + so];
+            v.xq[a * N + p] = x[a];
+            v.vq[a * N + p] = o.vq[a * N + so];
+            v.nq[a * N + p] = nq[a];
+            v.wq[a * N + p] = o.wq[a * N + so];
+            if (xref) xref[a * N + p] = x[a];
+        }
+        const unsigned char t = o.type[so];
+        const unsigned id = o.id[so];
+        v.type[p] = t;
+        v.id[p] = id;
+        v.cell[p] = k;
+        v.slot_of_id[I.p0 + id] = p;
+        int4 m;
+        m.x = mirror_coord(x[0], ck[0], I, 0, v.status);
+        m.y = mirror_coord(x[1], ck[1], I, 1, v.status);
+        m.z = mirror_coord(x[2], ck[2], I, 2, v.status);
+        m.w = t;
+        v.mq[p] = m;
+        float4 no;
+        no.x = ll_to_float(nq[0]) * (float)kGridInv;
+        no.y = ll_to_float(nq[1]) * (float)kGridInv;
+        no.z = ll_to_float(nq[2]) * (float)kGridInv;
+        no.w = __int_as_float(p);
+        v.mo[p] = no;
+        const float dx = m.x * kMirrorUnit, dy = m.y * kMirrorUnit, dz = m.z * kMirrorUnit;
         mx = fmaxf(mx, sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))));
+        if (t == kLipid) { nx += no.x; ny += no.y; nz += no.z; }
     }
-    for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    for (int off = 16; off; off >>= 1) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        nx += __shfl_xor_sync(0xffffffffu, nx, off);
+        ny += __shfl_xor_sync(0xffffffffu, ny, off);
+        nz += __shfl_xor_sync(0xffffffffu, nz, off);
+    }
+    __syncwarp();   // the lanes' writes above are read back below
+    // radius: FP64 definition for the particles within the band of the FP32 max
     double best = 0.0;
-    long long cx = v.cq[k], cy = v.cq[(size_t)v.Ktot + k], cz = v.cq[(size_t)2 * v.Ktot + k];
-    size_t N = v.N;
     for (int p = s + lane; p < e; p += 32) {
-        int4 m = v.mq[p];
-        float dx = m.x * kMirrorUnit, dy = m.y * kMirrorUnit, dz = m.z * kMirrorUnit;
-        float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        const int4 m = v.mq[p];
+        const float dx = m.x * kMirrorUnit, dy = m.y * kMirrorUnit, dz = m.z * kMirrorUnit;
+        const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
         if (d >= mx - kBandR) {
-            double d2 = dist2_grid_d(v.xq[p], v.xq[N + p], v.xq[2 * N + p], cx, cy, cz, I);
+            const double d2 = dist2_grid_d(v.xq[p], v.xq[N + p], v.xq[2 * N + p], ck[0], ck[1], ck[2], I);
             best = fmax(best, d2);
         }
     }
     for (int off = 16; off; off >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, off));
     if (lane == 0) {
-        double R = __dsqrt_rn(best);
+        const double R = __dsqrt_rn(best);
         v.R[k] = R;
         atomicMax(&rmax_bits[b], (unsigned long long)__double_as_longlong(R));
     }
     // pair-kernel frame
-    float nx = 0.f, ny = 0.f, nz = 0.f;
-    for (int p = s + lane; p < e; p += 32) {
-        if ((v.mq[p].w & 0xff) != kLipid) continue;
-        const float4 o = v.mo[p];
-        nx += o.x; ny += o.y; nz += o.z;
-    }
-    for (int off = 16; off; off >>= 1) {
-        nx += __shfl_xor_sync(0xffffffffu, nx, off);
-        ny += __shfl_xor_sync(0xffffffffu, ny, off);
-        nz += __shfl_xor_sync(0xffffffffu, nz, off);
-    }
     const float nn = sqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
     if (nn > 1e-3f) { nx /= nn; ny /= nn; nz /= nn; }
     else { nx = 0.f; ny = 0.f; nz = 1.f; }
@@ -1063,6 +1030,29 @@ __global__ void k_radius(View v, unsigned long long* __restrict__ rmax_bits /* [
         }
         __syncwarp();
     }
+}
+
+
+// Mirrors of the current order (after integration without a rebuild).
+__global__ void k_mirrors(View v) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= v.N) return;
+    size_t N = v.N;
+    int c = v.cell[p];
+    int b = find_inst(v.inst_p0, v.B, p);
+    const Inst& I = v.inst[b];
+    int4 m;
+    m.x = mirror_coord(v.xq[p], v.cq[c], I, 0, v.status);
+    m.y = mirror_coord(v.xq[N + p], v.cq[(size_t)v.Ktot + c], I, 1, v.status);
+    m.z = mirror_coord(v.xq[2 * N + p], v.cq[(size_t)2 * v.Ktot + c], I, 2, v.status);
+    m.w = v.type[p];
+    v.mq[p] = m;
+    float4 no;
+    no.x = ll_to_float(v.nq[p]) * (float)kGridInv;
+    no.y = ll_to_float(v.nq[N + p]) * (float)kGridInv;
+    no.z = ll_to_float(v.nq[2 * N + p]) * (float)kGridInv;
+    no.w = __int_as_float(p);
+    v.mo[p] = no;
 }
 
 // ============================================================== neighbouring cells
@@ -1352,13 +1342,11 @@ void Ensemble::finish_cells() {
     swap_state();
     View nv = view();
     View ov = view_alt();
-    k_gather<<<nblk(N, 256), 256, 0, stream>>>(nv, ov, d_perm, d_cell_new, d_xref);
+    CK(cudaMemsetAsync(d_rmax, 0, sizeof(unsigned long long) * B, stream));
+    k_gather_cells<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(nv, ov, d_perm, d_xref, d_rmax);
     launches++;
     CK(cudaGetLastError());
-    // radii and neighbouring cells
-    CK(cudaMemsetAsync(d_rmax, 0, sizeof(unsigned long long) * B, stream));
-    k_radius<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(nv, d_rmax);
-    launches++;
+    // neighbouring cells
     k_adj_warp<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(nv, d_rmax, d_adjcount, d_rho, d_adjpad);
     launches++;
     CK(cudaGetLastError());
