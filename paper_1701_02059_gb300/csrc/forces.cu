@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
     __shared__ alignas(16) int4 sy[kStageCap];
     __shared__ alignas(16) float4 sY[kStageCap];
     __shared__ alignas(16) float4 so[kStageCap];
-    __shared__ unsigned short cand[kPairThreads / 32][kStageCap];   // per-warp candidate list
+    __shared__ alignas(16) unsigned short cand[kPairThreads / 32][kStageCap];   // per-warp candidate list
     __shared__ unsigned short qbuf[kPairThreads / 32][kQCap][32];   // per-lane hit queues
     __shared__ NbrInfo nb[kMaxNbr];
     __shared__ unsigned char sorder[kPairThreads];
@@ -615,12 +615,15 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                     __syncwarp();
                 };
                 // ---- every lane tests the same candidate (broadcast reads)
-                for (int c = 0; c < cnt; c += 4) {
-                    if (__any_sync(0xffffffffu, qn > kQCap - 4)) flush();
+                static_assert(kStageCap % 8 == 0, "candidate lists are read 8 at a time");
+                for (int c = 0; c < cnt; c += 8) {
+                    if (__any_sync(0xffffffffu, qn > kQCap - 8)) flush();
+                    const uint4 c8 = *reinterpret_cast<const uint4*>(&cand[warp][c]);   // 8 indices, broadcast
+                    const unsigned cw[4] = {c8.x, c8.y, c8.z, c8.w};
 #pragma unroll
-                    for (int u = 0; u < 4; u++) {
+                    for (int u = 0; u < 8; u++) {
                         if (c + u < cnt) {
-                            const int j = (int)cand[warp][c + u];
+                            const int j = (int)((cw[u >> 1] >> (16 * (u & 1))) & 0xffffu);
                             const float4 y = sY[j];
                             const float ex = y.x - yix, ey = y.y - yiy, ez = y.z - yiz;
                             const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
