@@ -70,7 +70,9 @@ __device__ inline float taylor_sin(float x) {
 }
 
 // FP32 lipid pair; Z > 0 fixes zeta at compile time (Z = 0: runtime zeta).
-template <int Z>
+// S0: the spontaneous-curvature term is present (sin theta0 != 0); without
+// it the terms in s0 drop out of a, w and the torque.
+template <int Z, bool S0 = true>
 __device__ inline float lipid_terms_f(const Inst& I, float dx, float dy, float dz, float r2, float nix, float niy,
                                       float niz, float njx, float njy, float njz, float& fx, float& fy, float& fz,
                                       float& tx, float& ty, float& tz, float* tj = nullptr) {
@@ -82,7 +84,7 @@ __device__ inline float lipid_terms_f(const Inst& I, float dx, float dy, float d
     const float nin = fmaf(nix, njx, fmaf(niy, njy, niz * njz));
     const float nir = fmaf(nix, hx, fmaf(niy, hy, niz * hz));
     const float njr = fmaf(njx, hx, fmaf(njy, hy, njz * hz));
-    const float a = fmaf(s0, njr - nir, fmaf(-nir, njr, nin)) - s0 * s0;
+    const float a = S0 ? fmaf(s0, njr - nir, fmaf(-nir, njr, nin)) - s0 * s0 : fmaf(-nir, njr, nin);
     const float phi = fmaf(I.mu, a - 1.0f, 1.0f);
     float f, fp, g, gp;
     if (r < I.rmin) {
@@ -109,9 +111,12 @@ __device__ inline float lipid_terms_f(const Inst& I, float dx, float dy, float d
         gp = I.eps2z_aw * cp * sn;
     }
     const float U = fmaf(g, phi, f);
-    const float wx = fmaf(s0, njx - nix, fmaf(-njr, nix, -nir * njx));
-    const float wy = fmaf(s0, njy - niy, fmaf(-njr, niy, -nir * njy));
-    const float wz = fmaf(s0, njz - niz, fmaf(-njr, niz, -nir * njz));
+    float wx = fmaf(-njr, nix, -nir * njx), wy = fmaf(-njr, niy, -nir * njy), wz = fmaf(-njr, niz, -nir * njz);
+    if (S0) {
+        wx = fmaf(s0, njx - nix, wx);
+        wy = fmaf(s0, njy - niy, wy);
+        wz = fmaf(s0, njz - niz, wz);
+    }
     const float wr = fmaf(wx, hx, fmaf(wy, hy, wz * hz));
     const float radial = fmaf(gp, phi, fp);
     const float gm = g * I.mu;
@@ -120,7 +125,7 @@ __device__ inline float lipid_terms_f(const Inst& I, float dx, float dy, float d
     fy += -radial * hy - gmr * fmaf(-wr, hy, wy);
     fz += -radial * hz - gmr * fmaf(-wr, hz, wz);
     // da/dn_i = n_j - (n_j.rh + s0) rh ; tau_i = -g mu (n_i x da/dn_i)
-    const float js = njr + s0;
+    const float js = S0 ? njr + s0 : njr;
     const float gx = fmaf(-js, hx, njx), gy = fmaf(-js, hy, njy), gz = fmaf(-js, hz, njz);
     tx += -gm * (niy * gz - niz * gy);
     ty += -gm * (niz * gx - nix * gz);
@@ -312,11 +317,12 @@ struct NbrInfo {
     int ox, oy, oz; // exact offset c_l - c_k at 2^-26 sigma (wrap-around int32)
 };
 
-template <typename T>
+template <typename T, bool S0>
 __device__ inline T lipid_dispatch(const Inst& I, T dx, T dy, T dz, T r2, T nix, T niy, T niz, T njx, T njy, T njz,
                                    T& fx, T& fy, T& fz, T& tx, T& ty, T& tz, int zc, T* tj) {
     if constexpr (sizeof(T) == 4) {
-        if (zc == 4) return lipid_terms_f<4>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz, tj);
+        if (zc == 4)
+            return lipid_terms_f<4, S0>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz, tj);
         return lipid_terms_f<0>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz, tj);
     } else {
         return lipid_terms<double>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz, tj);
@@ -324,7 +330,8 @@ __device__ inline T lipid_dispatch(const Inst& I, T dx, T dy, T dz, T r2, T nix,
 }
 
 
-template <typename T, bool ENERGY, bool DUMP, int Z>
+// S0: some instance has a spontaneous-curvature term (s0 != 0).
+template <typename T, bool ENERGY, bool DUMP, int Z, bool S0>
 __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __restrict__ energy /* [B][8] */,
                                                             unsigned* __restrict__ dump,
                                                             unsigned long long* __restrict__ dump_count,
@@ -593,7 +600,7 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                                 njx = grid_to_double(v.nq[pj]); njy = grid_to_double(v.nq[N + pj]);
                                 njz = grid_to_double(v.nq[2 * N + pj]);
                             }
-                            U = lipid_dispatch<T>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz, zc,
+                            U = lipid_dispatch<T, S0>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz, zc,
                                                   (T*)nullptr);
                         } else {
                             U = wca_terms<T>(I, cls == 2, dx, dy, dz, r2, fx, fy, fz);
@@ -781,35 +788,39 @@ template <typename Kern> static void prefer_shared(Kern k) {
 static void prefer_shared_all() {
     static std::once_flag once;
     std::call_once(once, [] {
-        prefer_shared(k_pairs<float, false, true, 0>);
-        prefer_shared(k_pairs<float, true, false, 4>);
-        prefer_shared(k_pairs<float, true, false, 0>);
-        prefer_shared(k_pairs<float, false, false, 4>);
-        prefer_shared(k_pairs<float, false, false, 0>);
-        prefer_shared(k_pairs<double, false, true, 0>);
-        prefer_shared(k_pairs<double, true, false, 0>);
-        prefer_shared(k_pairs<double, false, false, 0>);
+        prefer_shared(k_pairs<float, false, true, 0, true>);
+        prefer_shared(k_pairs<float, true, false, 4, true>);
+        prefer_shared(k_pairs<float, true, false, 4, false>);
+        prefer_shared(k_pairs<float, true, false, 0, true>);
+        prefer_shared(k_pairs<float, false, false, 4, true>);
+        prefer_shared(k_pairs<float, false, false, 4, false>);
+        prefer_shared(k_pairs<float, false, false, 0, true>);
+        prefer_shared(k_pairs<double, false, true, 0, true>);
+        prefer_shared(k_pairs<double, true, false, 0, true>);
+        prefer_shared(k_pairs<double, false, false, 0, true>);
     });
 }
 
 void Ensemble::launch_pairs(bool energies, bool dump) {
     View v = view();
     if (energies) CK(cudaMemsetAsync(d_energy, 0, sizeof(long long) * 8 * B, stream));
-    bool z4 = true;
-    for (auto& I : inst_h) z4 = z4 && I.zeta == 4;
+    bool z4 = true, s0z = true;
+    for (auto& I : inst_h) { z4 = z4 && I.zeta == 4; s0z = s0z && I.s0_d == 0.0; }
     const dim3 g(Ktot), t(kPairThreads);
     prefer_shared_all();
     tic("pairs");
     if (precision == 0) {
-        if (dump) k_pairs<float, false, true, 0><<<g, t, 0, stream>>>(v, d_energy, d_dump, d_dump_count, dump_cap);
-        else if (energies && z4) k_pairs<float, true, false, 4><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
-        else if (energies) k_pairs<float, true, false, 0><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
-        else if (z4) k_pairs<float, false, false, 4><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
-        else k_pairs<float, false, false, 0><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
+        if (dump) k_pairs<float, false, true, 0, true><<<g, t, 0, stream>>>(v, d_energy, d_dump, d_dump_count, dump_cap);
+        else if (energies && z4 && s0z) k_pairs<float, true, false, 4, false><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
+        else if (energies && z4) k_pairs<float, true, false, 4, true><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
+        else if (energies) k_pairs<float, true, false, 0, true><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
+        else if (z4 && s0z) k_pairs<float, false, false, 4, false><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
+        else if (z4) k_pairs<float, false, false, 4, true><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
+        else k_pairs<float, false, false, 0, true><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
     } else {
-        if (dump) k_pairs<double, false, true, 0><<<g, t, 0, stream>>>(v, d_energy, d_dump, d_dump_count, dump_cap);
-        else if (energies) k_pairs<double, true, false, 0><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
-        else k_pairs<double, false, false, 0><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
+        if (dump) k_pairs<double, false, true, 0, true><<<g, t, 0, stream>>>(v, d_energy, d_dump, d_dump_count, dump_cap);
+        else if (energies) k_pairs<double, true, false, 0, true><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
+        else k_pairs<double, false, false, 0, true><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
     }
     launches++;
     toc();
