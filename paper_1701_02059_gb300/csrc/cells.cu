@@ -1012,21 +1012,59 @@ __global__ void k_gather_cells(View v, View o, const int* __restrict__ perm, lon
             hi_b = fmaxf(hi_b, __shfl_xor_sync(0xffffffffu, hi_b, off));
         }
         const bool use_a = (hi_a - lo_a) >= (hi_b - lo_b);
-        for (int u = 0; u < 4; u++) {
-            const int t = lane + 32 * u;
-            if (t < nt) skey[wb][t] = use_a ? ya[u] : yb[u];
-        }
-        __syncwarp();
-        for (int u = 0; u < 4; u++) {
-            const int t = lane + 32 * u;
-            if (t >= nt) continue;
-            const float kt = skey[wb][t];
-            int rank = 0;
-            for (int s2 = 0; s2 < nt; s2++) {
-                const float ks = skey[wb][s2];
-                rank += (ks < kt || (ks == kt && s2 < t)) ? 1 : 0;
+        if (nt <= 64) {
+            // bitonic sort of (key, index) over 64 slots, two per lane; the
+            // rank of a particle is the slot its record ends in
+            unsigned long long r[2];
+            for (int u = 0; u < 2; u++) {
+                const int t = lane + 32 * u;
+                if (t < nt) {
+                    unsigned kb = __float_as_uint(use_a ? ya[u] : yb[u]);
+                    kb ^= (kb >> 31) ? 0xffffffffu : 0x80000000u;      // order-preserving bits
+                    r[u] = ((unsigned long long)kb << 32) | (unsigned)t;
+                } else {
+                    r[u] = ~0ull;
+                }
             }
-            v.grank[t0 + t] = (unsigned char)rank;
+            for (int size = 2; size <= 64; size <<= 1) {
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    if (stride == 32) {
+                        // slots lane and lane + 32 (same lane); both ascending for size 64
+                        const unsigned long long a = r[0], c = r[1];
+                        r[0] = min(a, c);
+                        r[1] = max(a, c);
+                    } else {
+                        for (int u = 0; u < 2; u++) {
+                            const int e = lane + 32 * u;
+                            const unsigned long long o = __shfl_xor_sync(0xffffffffu, r[u], stride);
+                            const bool up = (e & size) == 0;
+                            const bool lower = (e & stride) == 0;
+                            r[u] = (lower == up) ? min(r[u], o) : max(r[u], o);
+                        }
+                    }
+                }
+            }
+            for (int u = 0; u < 2; u++) {
+                const unsigned t = (unsigned)(r[u] & 0xffffffffu);
+                if (r[u] != ~0ull) v.grank[t0 + t] = (unsigned char)(lane + 32 * u);
+            }
+        } else {
+            for (int u = 0; u < 4; u++) {
+                const int t = lane + 32 * u;
+                if (t < nt) skey[wb][t] = use_a ? ya[u] : yb[u];
+            }
+            __syncwarp();
+            for (int u = 0; u < 4; u++) {
+                const int t = lane + 32 * u;
+                if (t >= nt) continue;
+                const float kt = skey[wb][t];
+                int rank = 0;
+                for (int s2 = 0; s2 < nt; s2++) {
+                    const float ks = skey[wb][s2];
+                    rank += (ks < kt || (ks == kt && s2 < t)) ? 1 : 0;
+                }
+                v.grank[t0 + t] = (unsigned char)rank;
+            }
         }
         __syncwarp();
     }

@@ -143,6 +143,7 @@ __host__ __device__ inline long long floor_div_ll(long long a, long long b) {   
 }
 __host__ __device__ inline long long floor_mod_ll(long long a, long long b) { return a - b * floor_div_ll(a, b); }
 
+
 // Minimum image on the 2^-40 grid: d - L * round(d / L), ties rounding up.
 __device__ inline long long minimg_q(long long d, long long L, int per) {
     if (!per) return d;
