@@ -37,14 +37,18 @@ def serve_batched(jobs, hbm_budget_bytes: int, max_steps: int = 50, graphs: bool
     states = [None] * len(jobs)
     t0 = time.perf_counter()
     work = 0
+    spent = {"admit_s": 0.0, "run_s": 0.0, "retire_s": 0.0, "idle_s": 0.0}
     while waiting or slot_job:
         now = time.perf_counter() - t0
         # admit everything that has arrived, in arrival order, while it fits
         while waiting and jobs[waiting[0]]["arrival_s"] <= now:
             i = waiting[0]
+            ta = time.perf_counter()
             try:
                 s = arena.admit(jobs[i]["params"], jobs[i]["mem"], jobs[i]["steps"])
+                spent["admit_s"] += time.perf_counter() - ta
             except OrbcError as e:
+                spent["admit_s"] += time.perf_counter() - ta
                 if e.code != ORBC_E_NOMEM:
                     raise
                 if not slot_job:
@@ -54,10 +58,14 @@ def serve_batched(jobs, hbm_budget_bytes: int, max_steps: int = 50, graphs: bool
             waiting.pop(0)
             rec[i] = {"arrival_s": jobs[i]["arrival_s"], "admitted_s": time.perf_counter() - t0}
         if slot_job:
+            tr = time.perf_counter()
             arena.run(max_steps, graphs)
+            spent["run_s"] += time.perf_counter() - tr
             for s in arena.poll():
                 i = slot_job.pop(s)
+                tt = time.perf_counter()
                 st = arena.retire(s)
+                spent["retire_s"] += time.perf_counter() - tt
                 if keep_states:
                     states[i] = st
                 done = time.perf_counter() - t0
@@ -65,13 +73,16 @@ def serve_batched(jobs, hbm_budget_bytes: int, max_steps: int = 50, graphs: bool
                 rec[i]["latency_s"] = done - jobs[i]["arrival_s"]
                 work += jobs[i]["mem"].n * jobs[i]["steps"]
         elif waiting:
+            ti = time.perf_counter()
             time.sleep(max(0.0, min(0.05, jobs[waiting[0]]["arrival_s"] - (time.perf_counter() - t0))))
+            spent["idle_s"] += time.perf_counter() - ti
     total = time.perf_counter() - t0
     launches = arena.launch_count()
     arena.close()
     summary = _percentiles([r["latency_s"] for r in rec])
     summary.update({"makespan_s": total, "particle_steps": work, "particle_steps_per_s": work / total,
                     "gpu_launches": launches})
+    summary.update({k: round(v, 3) for k, v in spent.items()})
     return rec, summary, states
 
 
