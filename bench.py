@@ -407,7 +407,8 @@ def run_serving(args):
     plain = {"p50_s": round(float(np.percentile(lat_p, 50)), 4), "p99_s": round(float(np.percentile(lat_p, 99)), 4),
              "particle_steps_per_s": round(C, 1)}
     batched = {k: round(sb[k], 4) for k in ("p50_s", "p99_s", "makespan_s", "particle_steps_per_s",
-                                           "admit_s", "run_s", "retire_s", "idle_s")}
+                                           "admit_s", "run_s", "retire_s", "idle_s", "repack_s", "repacks",
+                                           "batched_steps")}
     return {"metric": "p99 completion latency of a served request stream", "value": batched["p99_s"], "unit": "s",
             "n_gpus": 1, "steps": None, "warmup": 0, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -302,6 +302,12 @@ ORBC_API int orbc_arena_info(const orbc_arena* a, int* resident, int* pending, i
 /* Kernels the arena has launched so far (graph replays count each kernel). */
 ORBC_API long long orbc_arena_launch_count(const orbc_arena* a);
 
+/* Host wall time spent re-packing the batch and stepping it (including the
+ * export of finished instances), the number of re-packs and of batched steps
+ * so far; each output nullable.  Errors: ORBC_E_ARG. */
+ORBC_API int orbc_arena_stats(const orbc_arena* a, double* repack_s, double* step_s, long long* repacks,
+                              long long* steps);
+
 /* Message of the last failed arena call ("" if none). */
 ORBC_API const char* orbc_arena_last_error(const orbc_arena* a);
 

@@ -271,3 +271,10 @@ class Arena:
 
     def launch_count(self) -> int:
         return int(self._L.orbc_arena_launch_count(self._h))
+
+    def stats(self):
+        rp, st = C.c_double(0.0), C.c_double(0.0)
+        nr, ns = C.c_longlong(0), C.c_longlong(0)
+        self._check(self._L.orbc_arena_stats(self._h, C.byref(rp), C.byref(st), C.byref(nr), C.byref(ns)),
+                    "orbc_arena_stats")
+        return {"repack_s": rp.value, "step_s": st.value, "repacks": nr.value, "steps": ns.value}

@@ -10,6 +10,7 @@
 #include "abi_common.cuh"
 
 #include <algorithm>
+#include <chrono>
 #include <memory>
 
 namespace orbc {
@@ -289,7 +290,13 @@ public:
     // Steps every resident instance by min(max_steps, fewest steps left).
     int run(int max_steps, bool graphs) {
         if (max_steps < 1) throw ArgError("max_steps must be >= 1");
-        if (dirty_) repack();
+        const auto t0 = std::chrono::steady_clock::now();
+        if (dirty_) {
+            repack();
+            repacks_++;
+        }
+        const auto t1 = std::chrono::steady_clock::now();
+        repack_s_ += std::chrono::duration<double>(t1 - t0).count();
         if (!batch_) return 0;
         long long s = max_steps;
         for (int slot : batch_slot_) s = std::min(s, slots_[slot].target - slots_[slot].done);
@@ -310,7 +317,16 @@ public:
                 dirty_ = true;
             }
         }
+        step_s_ += std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
+        steps_ += s;
         return (int)s;
+    }
+
+    void stats(double* repack_s, double* step_s, long long* repacks, long long* steps) const {
+        if (repack_s) *repack_s = repack_s_;
+        if (step_s) *step_s = step_s_;
+        if (repacks) *repacks = repacks_;
+        if (steps) *steps = steps_;
     }
 
     void poll(int* out, int cap, int* ndone) const {
@@ -413,6 +429,8 @@ private:
     std::vector<ArenaSlot> slots_;
     bool dirty_ = false;
     long long launches_ = 0;
+    double repack_s_ = 0.0, step_s_ = 0.0;    // host wall time inside re-packing / stepping
+    long long repacks_ = 0, steps_ = 0;
 };
 
 }  // namespace orbc
@@ -498,6 +516,12 @@ int orbc_arena_info(const orbc_arena* h, int* resident, int* pending, int* done,
 }
 
 long long orbc_arena_launch_count(const orbc_arena* h) { return h ? h->a->launches() : -1; }
+
+int orbc_arena_stats(const orbc_arena* h, double* repack_s, double* step_s, long long* repacks, long long* steps) {
+    if (!h) return ORBC_E_ARG;
+    h->a->stats(repack_s, step_s, repacks, steps);
+    return ORBC_OK;
+}
 
 const char* orbc_arena_last_error(const orbc_arena* h) { return h ? h->err.c_str() : "null handle"; }
 

@@ -78,11 +78,14 @@ def serve_batched(jobs, hbm_budget_bytes: int, max_steps: int = 50, graphs: bool
             spent["idle_s"] += time.perf_counter() - ti
     total = time.perf_counter() - t0
     launches = arena.launch_count()
+    inner = arena.stats()
     arena.close()
     summary = _percentiles([r["latency_s"] for r in rec])
     summary.update({"makespan_s": total, "particle_steps": work, "particle_steps_per_s": work / total,
                     "gpu_launches": launches})
     summary.update({k: round(v, 3) for k, v in spent.items()})
+    summary.update({"repack_s": round(inner["repack_s"], 3), "repacks": inner["repacks"],
+                    "batched_steps": inner["steps"]})
     return rec, summary, states
 
 

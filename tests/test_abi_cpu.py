@@ -90,6 +90,7 @@ def test_arena_null_handles_and_arguments_are_rejected(lib):
                               C.byref(slot)) == _native.ORBC_E_ARG
     assert L.orbc_arena_info(None, None, None, None, None, None) == _native.ORBC_E_ARG
     assert L.orbc_arena_launch_count(None) == -1
+    assert L.orbc_arena_stats(None, None, None, None, None) == _native.ORBC_E_ARG
     assert L.orbc_arena_last_error(None) == b"null handle"
     L.orbc_arena_destroy(None)
 
