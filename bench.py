@@ -38,6 +38,12 @@ MAX_SM_MHZ = 2070.0
 # candidate test), counted from the pair expression
 FLOP_PER_PAIR = 100.0
 FLOP_PER_CANDIDATE = 9.0
+# algorithmic HBM bytes of one step per particle (cells rebuilt every step):
+# B-A-O-A 240, M-step 24, E-step 32, histogram/scatter/per-cell order 16,
+# gather 238 (state in and out, mirrors, slot), pair kernel 80 (mirrors in,
+# force and torque out); the final half kick runs once per integrate call
+STEP_BYTES_PER_PARTICLE = 630.0
+PAIR_BYTES_PER_PARTICLE = 80.0
 
 
 def workload(name: str):
@@ -217,6 +223,15 @@ def run_ours(args, rank, world):
             "flops_per_launch": flops, "half_list_pairs": npairs, "half_list_candidates": ncand,
             "kernel_ms": round(pair_ms, 4)}
     breakdown = {k: round(v["ms"] / max(v["launches"], 1), 4) for k, v in times.items()}
+    # step roofline: every kernel at the HBM bound except the pair kernel,
+    # which is bound by the larger of its bytes and its FP32 work
+    pk_meas, src = peaks()
+    hbm = float(pk_meas.get("hbm_gbs", 6800.0)) * 1e9
+    t_rest = (STEP_BYTES_PER_PARTICLE - PAIR_BYTES_PER_PARTICLE) * mem.n / hbm
+    t_pair = max(PAIR_BYTES_PER_PARTICLE * mem.n / hbm, flops / (peak_tflops * 1e12))
+    step_roof = {"t_roof_ms": round((t_rest + t_pair) * 1e3, 4), "t_measured_ms": round(ms / args.steps, 4),
+                 "frac": round((t_rest + t_pair) * 1e3 / (ms / args.steps), 4), "hbm_gbs": hbm / 1e9,
+                 "hbm_source": src, "bytes_per_particle": STEP_BYTES_PER_PARTICLE}
 
     g.close()
     # the FP64-everywhere variant of the same step (FP64 pair terms and
@@ -276,7 +291,7 @@ def run_ours(args, rank, world):
                        "rebuild_every": 1, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (resident state, forces and mirrors ~1.4 GB)"},
             "roofline": roof, "kernel_ms_per_launch": breakdown, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clocks.summary(), "fp64_variant": f64, "ensemble": ens}
+            "gpu_launches": launches, "clocks": clocks.summary(), "step_roofline": step_roof, "fp64_variant": f64, "ensemble": ens}
     return line
 
 
