@@ -240,6 +240,7 @@ void Ensemble::alloc_core(const std::vector<int>& p0, const std::vector<int>& k0
     d_seglist = alloc<int>((size_t)2 * Ktot);
     d_seglist_n = alloc<int>(2);
     d_adjd = alloc<AdjDesc>(adj_cap);
+    d_candrows = alloc<float4>(adj_cap);
     prev_adj_valid_ = false;
     d_energy = alloc<long long>((size_t)8 * B);
     d_step = alloc<long long>(B);

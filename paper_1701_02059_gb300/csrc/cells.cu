@@ -612,11 +612,25 @@ __global__ void k_estep_list(View v, const int* __restrict__ fb_list, const int*
 //   sqrt(best) + band < rho_k - 2 dmax - |x - c_k|   (FP32 with margins).
 // Particles that fail the test take the grid search.
 constexpr float kCertMargin = 4e-3f;
+// The previous rows with their cells renumbered and the renumbered cells'
+// FP32 centroids (w = new index), so the E-step reads one record per
+// candidate instead of three dependent loads.
+__global__ void k_cand_rows(const int* __restrict__ adj_ptr_old, int Ktot, const int* __restrict__ adj_old,
+                            const int* __restrict__ new_of_old, const float4* __restrict__ cf, long long cap,
+                            float4* __restrict__ rows) {
+    const long long n = min((long long)adj_ptr_old[Ktot], cap);
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int j = new_of_old[adj_old[q]];
+        float4 c = cf[j];
+        c.w = __int_as_float(j);
+        rows[q] = c;
+    }
+}
+
 __global__ void k_estep_fast(View v, const int* __restrict__ cell_old, const int* __restrict__ adj_ptr_old,
-                             const int* __restrict__ adj_old, const float* __restrict__ rho_old,
-                             const int* __restrict__ new_of_old, const float4* __restrict__ cf,
-                             const unsigned* __restrict__ dmax, int* __restrict__ cell_out,
-                             int* __restrict__ fb_list, int* __restrict__ fb_count) {
+                             const float4* __restrict__ rows, const float* __restrict__ rho_old,
+                             const int* __restrict__ new_of_old, const unsigned* __restrict__ dmax,
+                             int* __restrict__ cell_out, int* __restrict__ fb_list, int* __restrict__ fb_count) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const bool valid = i < v.N;
@@ -647,8 +661,8 @@ __global__ void k_estep_fast(View v, const int* __restrict__ cell_old, const int
             int j = -1;
             float4 c = make_float4(0, 0, 0, 0);
             if (c0 + lane < len) {
-                j = new_of_old[adj_old[a0 + c0 + lane]];
-                c = cf[j];
+                c = rows[a0 + c0 + lane];
+                j = __float_as_int(c.w);
             }
             const int cnt = min(32, len - c0);
             for (int q = 0; q < cnt; q++) {
@@ -689,8 +703,8 @@ __global__ void k_estep_fast(View v, const int* __restrict__ cell_old, const int
     int bk64 = -1;
     const int a0 = adj_ptr_old[ko], a1 = adj_ptr_old[ko + 1];
     for (int q = a0; q < a1; q++) {
-        const int j = new_of_old[adj_old[q]];
-        const float4 c = cf[j];
+        const float4 c = rows[q];
+        const int j = __float_as_int(c.w);
         const float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1), dz = axis_dist(p[2], c.z, I, 2);
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         if (d2 <= lim * lim) {
@@ -1351,10 +1365,11 @@ void Ensemble::finish_cells() {
     build_grid();
     if (prev_adj_valid_) {
         CK(cudaMemsetAsync(d_fbcount, 0, sizeof(int), stream));
-        k_estep_fast<<<nblk(N, 128), 128, 0, stream>>>(v, d_cell, d_adj_ptr, d_adj, d_rho, d_new_of_old, d_cf, d_dmax,
+        k_cand_rows<<<152 * 8, 256, 0, stream>>>(d_adj_ptr, Ktot, d_adj, d_new_of_old, d_cf, adj_cap, d_candrows);
+        k_estep_fast<<<nblk(N, 128), 128, 0, stream>>>(v, d_cell, d_adj_ptr, d_candrows, d_rho, d_new_of_old, d_dmax,
                                                       d_cell_new, d_cell_tmp, d_fbcount);
         k_estep_list<<<152 * 4, 128, 0, stream>>>(v, d_cell_tmp, d_fbcount, d_cell_new);
-        launches += 2;
+        launches += 3;
         CK(cudaGetLastError());
     } else {
         estep(d_cell_new);

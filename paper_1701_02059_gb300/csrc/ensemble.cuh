@@ -231,6 +231,7 @@ public:
     int* d_seglist = nullptr;                // [2][Ktot] cells for the block sort / the rank sort
     int* d_seglist_n = nullptr;              // [2] their counts
     AdjDesc* d_adjd = nullptr;               // [adj_cap] staging descriptors of the rows
+    float4* d_candrows = nullptr;            // [adj_cap] previous rows renumbered, with centroids (E-step)
     long long* d_xref = nullptr;
     long long* d_energy = nullptr;           // [B][8] fixed-point sums
     long long* d_step = nullptr;             // [B]
