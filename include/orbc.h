@@ -174,6 +174,18 @@ ORBC_API int orbc_get_state(orbc_system* s, double* pos, double* vel, double* or
 /* Forces and torques of the last force evaluation, in id order. */
 ORBC_API int orbc_get_forces(orbc_system* s, double* force, double* torque);
 
+/* Device-pointer variants (for callers whose arrays live on the GPU, e.g.
+ * torch tensors; all on the handle's stream, which the call synchronises).
+ * orbc_get_state_device / orbc_get_forces_device write [n][3] FP64 arrays
+ * in id order with a kernel (no host round trip); any pointer may be NULL.
+ * orbc_set_particles_device takes the arrays of orbc_set_particles in device
+ * memory; they are read back once for the host-side validation and set-up
+ * (a set-up cost, not a per-step one).  Errors as the host variants. */
+ORBC_API int orbc_set_particles_device(orbc_system* s, int n, const double* pos, const double* vel, const double* ori,
+                                       const double* angvel, const unsigned char* type, const unsigned* id);
+ORBC_API int orbc_get_state_device(orbc_system* s, double* pos, double* vel, double* ori, double* angvel);
+ORBC_API int orbc_get_forces_device(orbc_system* s, double* force, double* torque);
+
 /* Cell list: cell_of_id [n]; slot_ids [n] (id stored at each storage slot,
  * the particle reorder); centroids [K][3]; cell_start [K+1]; radius [K];
  * adj_ptr [K+1] and adj [adj_len] (neighbouring cells, ascending, CSR).

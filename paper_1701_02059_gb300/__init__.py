@@ -145,6 +145,34 @@ class System:
         self._check(self._L.orbc_get_state(self._h, _p(pos), _p(vel), _p(ori), _p(w), C.byref(step)), "orbc_get_state")
         return {"pos": pos, "vel": vel, "ori": ori, "angvel": w, "step": step.value}
 
+    # -------------------------------------------------------------- device tensors
+    def set_particles_tensors(self, pos, vel, ori, angvel, typ, ids):
+        """orbc_set_particles_device from CUDA tensors (float64 [n,3] x4,
+        uint8 [n], int32/uint32 [n]), on the system's stream."""
+        ts = [pos, vel, ori, angvel, typ, ids]
+        for t in ts:
+            assert t.is_cuda and t.is_contiguous()
+        self.n = int(typ.numel())
+        self._check(self._L.orbc_set_particles_device(self._h, self.n, *[C.c_void_p(t.data_ptr()) for t in ts]),
+                    "orbc_set_particles_device")
+
+    def state_tensors(self, device=None):
+        """orbc_get_state_device: the state in id order as CUDA float64 tensors."""
+        import torch
+        out = [torch.empty((self.n, 3), dtype=torch.float64, device=device or "cuda") for _ in range(4)]
+        self._check(self._L.orbc_get_state_device(self._h, *[C.c_void_p(t.data_ptr()) for t in out]),
+                    "orbc_get_state_device")
+        return dict(zip(("pos", "vel", "ori", "angvel"), out))
+
+    def force_tensors(self, device=None):
+        """orbc_get_forces_device: forces and torques in id order as CUDA tensors."""
+        import torch
+        F = torch.empty((self.n, 3), dtype=torch.float64, device=device or "cuda")
+        T = torch.empty((self.n, 3), dtype=torch.float64, device=device or "cuda")
+        self._check(self._L.orbc_get_forces_device(self._h, C.c_void_p(F.data_ptr()), C.c_void_p(T.data_ptr())),
+                    "orbc_get_forces_device")
+        return F, T
+
     def forces(self):
         F, T = np.zeros((self.n, 3)), np.zeros((self.n, 3))
         self._check(self._L.orbc_get_forces(self._h, _p(F), _p(T)), "orbc_get_forces")

@@ -23,7 +23,8 @@ EXPORTS = [
     "orbc_get_launch_count", "orbc_last_error", "orbc_destroy", "orbc_cell_sort", "orbc_cell_sort_noalloc",
     "orbc_arena_create", "orbc_arena_admit", "orbc_arena_run", "orbc_arena_poll", "orbc_arena_retire",
     "orbc_arena_info", "orbc_arena_launch_count", "orbc_arena_last_error", "orbc_arena_destroy",
-    "orbc_autotune", "orbc_arena_stats",
+    "orbc_autotune", "orbc_arena_stats", "orbc_set_particles_device", "orbc_get_state_device",
+    "orbc_get_forces_device",
 ]
 _NOT_INT = {"orbc_default_params": None, "orbc_last_error": C.c_char_p, "orbc_destroy": None,
             "orbc_arena_launch_count": C.c_longlong, "orbc_arena_last_error": C.c_char_p, "orbc_arena_destroy": None}
@@ -94,6 +95,9 @@ def load(path: str | None = None):
     L.orbc_arena_launch_count.argtypes = [V]
     L.orbc_arena_last_error.argtypes = [V]
     L.orbc_arena_destroy.argtypes = [V]
+    L.orbc_set_particles_device.argtypes = [V, C.c_int, V, V, V, V, V, V]
+    L.orbc_get_state_device.argtypes = [V, V, V, V, V]
+    L.orbc_get_forces_device.argtypes = [V, V, V]
     L.orbc_arena_stats.argtypes = [V, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                                    C.POINTER(C.c_longlong)]
     L.orbc_autotune.argtypes = [C.POINTER(Params), C.c_int, V, V, V, V, V, V, C.c_int, V, V, V, C.c_int, C.c_char_p,

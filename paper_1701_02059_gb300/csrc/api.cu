@@ -660,6 +660,43 @@ long long Ensemble::dump_pairs(int b, long long cap, unsigned* pairs) {
     return (long long)cnt;
 }
 
+// Per-slot int64 fixed-point arrays of instance b to FP64 [n][3] in id order.
+__global__ void k_to_id_order(const unsigned* __restrict__ id, const long long* __restrict__ q, size_t N, int p0, int n,
+                              double unit, double* __restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int p = p0 + t;
+    const unsigned i = id[p];
+    for (int a = 0; a < 3; a++) out[(size_t)3 * i + a] = __ll2double_rn(q[(size_t)a * N + p]) * unit;
+}
+
+void Ensemble::get_state_device(int b, double* pos, double* vel, double* ori, double* angvel) {
+    const Inst& I = inst_h[b];
+    double* outs[4] = {pos, vel, ori, angvel};
+    for (int q = 0; q < 4; q++) {
+        if (!outs[q]) continue;
+        k_to_id_order<<<(I.n + 255) / 256, 256, 0, stream>>>(d_id[cur_], d_state[cur_][q], (size_t)N, I.p0, I.n,
+                                                             kGridInv, outs[q]);
+        launches++;
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(stream));
+}
+
+void Ensemble::get_forces_device(int b, double* f, double* t) {
+    const Inst& I = inst_h[b];
+    long long* src[2] = {d_F, d_T};
+    double* outs[2] = {f, t};
+    for (int q = 0; q < 2; q++) {
+        if (!outs[q]) continue;
+        k_to_id_order<<<(I.n + 255) / 256, 256, 0, stream>>>(d_id[cur_], src[q], (size_t)N, I.p0, I.n, kForceUnit,
+                                                             outs[q]);
+        launches++;
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(stream));
+}
+
 }  // namespace orbc
 
 // ============================================================== C ABI
@@ -909,6 +946,43 @@ int orbc_get_state(orbc_system* s, double* pos, double* vel, double* ori, double
     return guarded(s, [&] {
         if (!s->have_particles) throw StateError("no particles");
         s->ens->get_state(0, pos, vel, ori, angvel, step);
+    });
+}
+
+int orbc_set_particles_device(orbc_system* s, int n, const double* pos, const double* vel, const double* ori,
+                              const double* angvel, const unsigned char* type, const unsigned* id) {
+    if (!s) return ORBC_E_ARG;
+    return guarded(s, [&] {
+        if (n < 1 || !pos || !vel || !ori || !angvel || !type || !id) throw ArgError("null pointer or n < 1");
+        std::vector<double> hp((size_t)3 * n), hv((size_t)3 * n), ho((size_t)3 * n), hw((size_t)3 * n);
+        std::vector<unsigned char> ht(n);
+        std::vector<unsigned> hi(n);
+        const double* src[4] = {pos, vel, ori, angvel};
+        double* dst[4] = {hp.data(), hv.data(), ho.data(), hw.data()};
+        for (int q = 0; q < 4; q++)
+            CK(cudaMemcpyAsync(dst[q], src[q], sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaMemcpyAsync(ht.data(), type, (size_t)n, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaMemcpyAsync(hi.data(), id, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        s->host = host_instance(s->prm, n, hp.data(), hv.data(), ho.data(), hw.data(), ht.data(), hi.data());
+        s->have_particles = true;
+        s->ens->setup({s->host});
+    });
+}
+
+int orbc_get_state_device(orbc_system* s, double* pos, double* vel, double* ori, double* angvel) {
+    if (!s) return ORBC_E_ARG;
+    return guarded(s, [&] {
+        if (!s->have_particles) throw StateError("no particles");
+        s->ens->get_state_device(0, pos, vel, ori, angvel);
+    });
+}
+
+int orbc_get_forces_device(orbc_system* s, double* force, double* torque) {
+    if (!s) return ORBC_E_ARG;
+    return guarded(s, [&] {
+        if (!s->ens->forces_valid) throw StateError("forces not computed");
+        s->ens->get_forces_device(0, force, torque);
     });
 }
 

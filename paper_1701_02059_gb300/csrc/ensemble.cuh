@@ -120,6 +120,8 @@ public:
     // host copies (instance b, id order)
     void get_state(int b, double* pos, double* vel, double* ori, double* angvel, long long* step);
     void get_forces(int b, double* f, double* t);
+    void get_state_device(int b, double* pos, double* vel, double* ori, double* angvel);
+    void get_forces_device(int b, double* f, double* t);
     void get_cells(int b, int* cell_of_id, unsigned* slot_ids, double* centroids, int* cell_start, double* radius,
                    int* adj_ptr, int* adj);
     long long adjacency_len(int b);

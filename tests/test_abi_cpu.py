@@ -68,6 +68,9 @@ def test_null_handles_are_rejected(lib):
     assert L.orbc_create(None, None, None) == _native.ORBC_E_ARG
     assert L.orbc_integrate(None, 1) == _native.ORBC_E_ARG
     assert L.orbc_compute_forces(None, None) == _native.ORBC_E_ARG
+    assert L.orbc_set_particles_device(None, 1, None, None, None, None, None, None) == _native.ORBC_E_ARG
+    assert L.orbc_get_state_device(None, None, None, None, None) == _native.ORBC_E_ARG
+    assert L.orbc_get_forces_device(None, None, None) == _native.ORBC_E_ARG
     assert L.orbc_last_error(None) == b"null handle"
     L.orbc_destroy(None)
 
