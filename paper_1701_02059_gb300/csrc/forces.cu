@@ -478,6 +478,8 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
             F.apply(qi.x * kMirrorUnit, qi.y * kMirrorUnit, qi.z * kMirrorUnit, yix, yiy, yiz);
             if (DUMP) idi = v.id[pi];
         }
+        // a lane without a particle sits far away: it passes no distance test
+        if (!ivalid) { yix = 1.0e18f; yiy = 1.0e18f; yiz = 1.0e18f; }
         // group bounding box in the tangent frame, widened by the search radius
         float blo[3] = {ivalid ? yix : 3.0e38f, ivalid ? yiy : 3.0e38f, ivalid ? yiz : 3.0e38f};
         float bhi[3] = {ivalid ? yix : -3.0e38f, ivalid ? yiy : -3.0e38f, ivalid ? yiz : -3.0e38f};
@@ -535,11 +537,13 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
 
             if (wactive) {
                 // ---- candidates: staged particles within r_s (+ band) of the
-                //      group's box; chunks of 32 shared round-robin by the
-                //      warps of the group
+                //      group's box; the warps of a group take every nsplit-th
+                //      staged particle, so that their shares of the candidates
+                //      and hits stay even (whole chunks per warp left them
+                //      waiting on each other at the next barrier)
                 int cnt = 0;
-                for (int c0 = jsplit * 32; c0 < total; c0 += nsplit * 32) {
-                    const int j = c0 + lane;
+                for (int c0 = 0; c0 < total; c0 += nsplit * 32) {
+                    const int j = c0 + lane * nsplit + jsplit;
                     bool in = false;
                     if (j < total) {
                         const float4 y = sY[j];
@@ -634,7 +638,7 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                             const float4 y = sY[j];
                             const float ex = y.x - yix, ey = y.y - yiy, ez = y.z - yiz;
                             const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                            if (ivalid && d2 < rs2f && j != selfj) { qbuf[warp][qn][lane] = (unsigned short)j; qn++; }
+                            if (d2 < rs2f && j != selfj) { qbuf[warp][qn][lane] = (unsigned short)j; qn++; }
                         }
                     }
                 }
