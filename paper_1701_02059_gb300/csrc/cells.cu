@@ -627,7 +627,7 @@ __global__ void k_cand_rows(const int* __restrict__ adj_ptr_old, int Ktot, const
     }
 }
 
-__global__ void k_estep_fast(View v, const int* __restrict__ cell_old, const int* __restrict__ adj_ptr_old,
+__global__ void __launch_bounds__(128, 12) k_estep_fast(View v, const int* __restrict__ cell_old, const int* __restrict__ adj_ptr_old,
                              const float4* __restrict__ rows, const float* __restrict__ rho_old,
                              const int* __restrict__ new_of_old, const unsigned* __restrict__ dmax,
                              int* __restrict__ cell_out, int* __restrict__ fb_list, int* __restrict__ fb_count) {
@@ -919,15 +919,57 @@ __device__ inline int mirror_coord(long long xq, long long cq, const Inst& I, in
 // the candidates within this band of the maximum, FP64 decides among them.
 constexpr float kBandR = 1e-5f;
 
-// Gather of the cell-sorted state, fused with the per-cell quantities that
-// read it back: one warp per new cell moves its particles (state, type, id,
-// slot, mirrors) and computes the cell radius R_k = max |x - c_k| (FP32 with
-// the FP64 definition inside a band), the pair kernel's cell normal (mean
-// lipid director, unit; +z without lipid direction) and, in each tile of 128
+// Gather of the cell-sorted state, one thread per new slot p: the particle
+// of old slot perm[p] moves with its state, type and id, learns its new cell
+// (the E-step's result for the old slot) and gets its exact mirror relative
+// to that cell's centroid.
+__global__ void __launch_bounds__(256) k_gather_particles(View v, View o, const int* __restrict__ perm,
+                                                          const int* __restrict__ cell_new,
+                                                          long long* __restrict__ xref) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= v.N) return;
+    const size_t N = v.N;
+    const int so = perm[p];
+    const int k = cell_new[so];
+    const int b = find_inst(v.inst_p0, v.B, p);
+    const Inst& I = v.inst[b];
+    long long x[3], nq[3];
+    for (int a = 0; a < 3; a++) {
+        x[a] = o.xq[a * N + so];
+        nq[a] = o.nq[a * N + so];
+        v.xq[a * N + p] = x[a];
+        v.vq[a * N + p] = o.vq[a * N + so];
+        v.nq[a * N + p] = nq[a];
+        v.wq[a * N + p] = o.wq[a * N + so];
+        if (xref) xref[a * N + p] = x[a];
+    }
+    const unsigned char t = o.type[so];
+    const unsigned id = o.id[so];
+    v.type[p] = t;
+    v.id[p] = id;
+    v.cell[p] = k;
+    v.slot_of_id[I.p0 + id] = p;
+    int4 m;
+    m.x = mirror_coord(x[0], v.cq[k], I, 0, v.status);
+    m.y = mirror_coord(x[1], v.cq[(size_t)v.Ktot + k], I, 1, v.status);
+    m.z = mirror_coord(x[2], v.cq[(size_t)2 * v.Ktot + k], I, 2, v.status);
+    m.w = t;
+    v.mq[p] = m;
+    float4 no;
+    no.x = ll_to_float(nq[0]) * (float)kGridInv;
+    no.y = ll_to_float(nq[1]) * (float)kGridInv;
+    no.z = ll_to_float(nq[2]) * (float)kGridInv;
+    no.w = __int_as_float(p);
+    v.mo[p] = no;
+}
+
+// Per-cell quantities read back from the gathered mirrors: one warp per cell
+// computes the cell radius R_k = max |x - c_k| (FP32 with the FP64
+// definition inside a band), the pair kernel's cell normal (mean lipid
+// director, unit; +z without lipid direction) and, in each tile of 128
 // particles, every particle's rank along the tile's longer tangent extent.
 // Launched with 256 threads (8 warps, one cell each).
-__global__ void k_gather_cells(View v, View o, const int* __restrict__ perm, long long* __restrict__ xref,
-                               unsigned long long* __restrict__ rmax_bits /* [B] */) {
+__global__ void __launch_bounds__(256, 6) k_cell_props(View v, unsigned long long* __restrict__ rmax_bits /* [B] */) {
     __shared__ float skey[8][128];
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -940,38 +982,11 @@ __global__ void k_gather_cells(View v, View o, const int* __restrict__ perm, lon
     const long long ck[3] = {v.cq[k], v.cq[(size_t)v.Ktot + k], v.cq[(size_t)2 * v.Ktot + k]};
     float mx = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
     for (int p = s + lane; p < e; p += 32) {
-        const int so = perm[p];
-        long long x[3], nq[3];
-        for (int a = 0; a < 3; a++) {
-            x[a] = o.xq[a * N + so];
-            nq[a] = o.nq[a * N + so];
-            v.xq[a * N + p] = x[a];
-            v.vq[a * N + p] = o.vq[a * N + so];
-            v.nq[a * N + p] = nq[a];
-            v.wq[a * N + p] = o.wq[a * N + so];
-            if (xref) xref[a * N + p] = x[a];
-        }
-        const unsigned char t = o.type[so];
-        const unsigned id = o.id[so];
-        v.type[p] = t;
-        v.id[p] = id;
-        v.cell[p] = k;
-        v.slot_of_id[I.p0 + id] = p;
-        int4 m;
-        m.x = mirror_coord(x[0], ck[0], I, 0, v.status);
-        m.y = mirror_coord(x[1], ck[1], I, 1, v.status);
-        m.z = mirror_coord(x[2], ck[2], I, 2, v.status);
-        m.w = t;
-        v.mq[p] = m;
-        float4 no;
-        no.x = ll_to_float(nq[0]) * (float)kGridInv;
-        no.y = ll_to_float(nq[1]) * (float)kGridInv;
-        no.z = ll_to_float(nq[2]) * (float)kGridInv;
-        no.w = __int_as_float(p);
-        v.mo[p] = no;
+        const int4 m = v.mq[p];
+        const float4 no = v.mo[p];
         const float dx = m.x * kMirrorUnit, dy = m.y * kMirrorUnit, dz = m.z * kMirrorUnit;
         mx = fmaxf(mx, sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))));
-        if (t == kLipid) { nx += no.x; ny += no.y; nz += no.z; }
+        if ((m.w & 0xff) == kLipid) { nx += no.x; ny += no.y; nz += no.z; }
     }
     for (int off = 16; off; off >>= 1) {
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
@@ -979,7 +994,6 @@ __global__ void k_gather_cells(View v, View o, const int* __restrict__ perm, lon
         ny += __shfl_xor_sync(0xffffffffu, ny, off);
         nz += __shfl_xor_sync(0xffffffffu, nz, off);
     }
-    __syncwarp();   // the lanes' writes above are read back below
     // radius: FP64 definition for the particles within the band of the FP32 max
     double best = 0.0;
     for (int p = s + lane; p < e; p += 32) {
@@ -1134,7 +1148,7 @@ __device__ inline bool adj_test(const View& v, const Inst& I, int k, int j, doub
 // exact rule, collect the row in shared memory and sort it.  Rows longer than
 // kAdjRow are flagged (kStatusAdjOverflow) and truncated.
 constexpr int kAdjRow = 64;
-__global__ void k_adj_warp(View v, const unsigned long long* __restrict__ rmax_bits, int* __restrict__ count,
+__global__ void __launch_bounds__(256, 6) k_adj_warp(View v, const unsigned long long* __restrict__ rmax_bits, int* __restrict__ count,
                            float* __restrict__ rho_out, int* __restrict__ pad /* [Ktot][kAdjRow] */) {
     __shared__ int row[8][kAdjRow];
     __shared__ int rown[8];
@@ -1396,8 +1410,9 @@ void Ensemble::finish_cells() {
     View nv = view();
     View ov = view_alt();
     CK(cudaMemsetAsync(d_rmax, 0, sizeof(unsigned long long) * B, stream));
-    k_gather_cells<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(nv, ov, d_perm, d_xref, d_rmax);
-    launches++;
+    k_gather_particles<<<nblk(N, 256), 256, 0, stream>>>(nv, ov, d_perm, d_cell_new, d_xref);
+    k_cell_props<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(nv, d_rmax);
+    launches += 2;
     CK(cudaGetLastError());
     // neighbouring cells
     k_adj_warp<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(nv, d_rmax, d_adjcount, d_rho, d_adjpad);

@@ -31,7 +31,7 @@
 namespace orbc {
 
 constexpr int kPairThreads = 128;
-constexpr int kStageCap = 544;     // staged particles per pass
+constexpr int kStageCap = 624;     // staged particles per pass
 constexpr int kQCap = 32;          // queued hits per lane before a flush
 constexpr int kMaxNbr = 32;        // neighbouring cells per pass (one per lane of the set-up warp)
 constexpr float kFilterBand = 1e-4f;
@@ -649,38 +649,46 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
         }
 
         // combine the warps of a group (exact integer sums) and write; the
-        // slot of a lane's particle in the tile is sorder[r]
+        // slot of a lane's particle in the tile is sorder[r].  The red rows
+        // of the later splits ((nsplit - 1) x nti <= 96 rows of 56 bytes)
+        // fit in sY, which no warp reads any more.
         __syncthreads();
         const int ts = ivalid ? (int)sorder[r] : -1;
         if constexpr (sizeof(T) == 4) {
+            // the warps of a group hold partial sums of the same particles:
+            // the later splits hand theirs over by plain stores, split 0 adds
+            // them and writes the particle
+            static_assert(3 * 32 * 14 * sizeof(int) <= kStageCap * sizeof(float4), "split rows must fit in sY");
             int (*red)[14] = reinterpret_cast<int (*)[14]>(&sY[0]);
-            for (int q = tid; q < kPairThreads * 14; q += kPairThreads) (&red[0][0])[q] = 0;
-            __syncthreads();
-            if (ivalid) {
-                atomicAdd(&red[ts][0], acc.f[0].h); atomicAdd(&red[ts][1], acc.f[0].l);
-                atomicAdd(&red[ts][2], acc.f[1].h); atomicAdd(&red[ts][3], acc.f[1].l);
-                atomicAdd(&red[ts][4], acc.f[2].h); atomicAdd(&red[ts][5], acc.f[2].l);
-                atomicAdd(&red[ts][6], acc.t[0].h); atomicAdd(&red[ts][7], acc.t[0].l);
-                atomicAdd(&red[ts][8], acc.t[1].h); atomicAdd(&red[ts][9], acc.t[1].l);
-                atomicAdd(&red[ts][10], acc.t[2].h); atomicAdd(&red[ts][11], acc.t[2].l);
-                atomicAdd(&red[ts][12], acc.nf); atomicAdd(&red[ts][13], acc.nt);
+            if (ivalid && jsplit > 0) {
+                int* d = red[(jsplit - 1) * nti + ts];
+                d[0] = acc.f[0].h; d[1] = acc.f[0].l; d[2] = acc.f[1].h; d[3] = acc.f[1].l;
+                d[4] = acc.f[2].h; d[5] = acc.f[2].l; d[6] = acc.t[0].h; d[7] = acc.t[0].l;
+                d[8] = acc.t[1].h; d[9] = acc.t[1].l; d[10] = acc.t[2].h; d[11] = acc.t[2].l;
+                d[12] = acc.nf; d[13] = acc.nt;
             }
             const bool any_big = __syncthreads_or(ivalid && acc.used_big);
-            if (tid < nti) {
-                const int nfr = red[tid][12], ntr = red[tid][13];
-                const int p = it0 + tid;
+            if (ivalid && jsplit == 0) {
+                int sm[14] = {acc.f[0].h, acc.f[0].l, acc.f[1].h, acc.f[1].l, acc.f[2].h, acc.f[2].l,
+                              acc.t[0].h, acc.t[0].l, acc.t[1].h, acc.t[1].l, acc.t[2].h, acc.t[2].l, acc.nf, acc.nt};
+                for (int q = 1; q < nsplit; q++) {
+                    const int* d = red[(q - 1) * nti + ts];
+#pragma unroll
+                    for (int c = 0; c < 14; c++) sm[c] += d[c];
+                }
+                const int p = it0 + ts;
+#pragma unroll
                 for (int a = 0; a < 3; a++) {
-                    SplitAcc f; f.h = red[tid][2 * a]; f.l = red[tid][2 * a + 1];
-                    SplitAcc t; t.h = red[tid][6 + 2 * a]; t.l = red[tid][6 + 2 * a + 1];
+                    SplitAcc f; f.h = sm[2 * a]; f.l = sm[2 * a + 1];
+                    SplitAcc t; t.h = sm[6 + 2 * a]; t.l = sm[6 + 2 * a + 1];
                     long long fb = 0, tb = 0;
                     if (any_big) {
-                        // written by atomics in L2: read past L1
                         fb = __ldcg(&v.Fbig[(size_t)a * N + p]);
                         tb = __ldcg(&v.Fbig[(size_t)(3 + a) * N + p]);
                         v.Fbig[(size_t)a * N + p] = 0; v.Fbig[(size_t)(3 + a) * N + p] = 0;
                     }
-                    v.F[a * N + p] = f.finish(nfr) + fb;
-                    v.T[a * N + p] = t.finish(ntr) + tb;
+                    v.F[a * N + p] = f.finish(sm[12]) + fb;
+                    v.T[a * N + p] = t.finish(sm[13]) + tb;
                 }
             }
         } else {
