@@ -221,6 +221,8 @@ void Ensemble::alloc_core(const std::vector<int>& p0, const std::vector<int>& k0
     d_gidx = alloc<int>(Ktot);
     d_status = alloc<unsigned>(1);
     d_S = alloc<long long>((size_t)3 * Ktot);
+    d_msum = alloc<long long>((size_t)3 * Ktot);   // zeroed by alloc, re-zeroed by each use
+    d_mcnt = alloc<int>(Ktot);
     d_cnt = alloc<int>(Ktot + 1);
     d_bbox = alloc<long long>((size_t)6 * B);
     d_keys = alloc<unsigned long long>(Ktot);
@@ -518,15 +520,18 @@ void Ensemble::integrate(int nsteps) {
 // One time step without its final B: B-A-O-A (after the previous step's
 // final B when fused), cell rebuild (or mirrors), forces.
 void Ensemble::step_body(bool fused) {
-    tic("integrate_baoa");
-    launch_integrate_first(fused);
-    toc();
+    // rebuilding every step: the B-A-O-A launch also sums the M-step's
+    // per-cell lipid displacements
     const int re = prm_h[0].rebuild_every;
+    const bool every = re <= 1 && !d_xref;
+    tic("integrate_baoa");
+    launch_integrate_first(fused, every);
+    toc();
     bool due = (re <= 1) || ((step_h[0] + 1) % re == 0);
     if (!due && d_xref) due = displacement_exceeds_skin();
     if (due) {
         tic("rebuild");
-        rebuild();
+        rebuild(every);
         toc();
     } else {
         tic("mirrors");

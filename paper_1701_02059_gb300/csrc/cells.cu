@@ -141,6 +141,49 @@ __global__ void k_mstep_sorted(View v, long long* __restrict__ bb, unsigned* __r
     }
 }
 
+// M-step from the sums the B-A-O-A launch accumulated (same terms as
+// k_mstep_sorted, so the same centroids): one thread per cell updates c_k,
+// clears the sums for the next step and folds the centroid into the
+// instance's bounding box and its largest move (warp-reduced before the
+// atomics).
+__global__ void __launch_bounds__(256) k_mstep_apply(View v, long long* __restrict__ S, int* __restrict__ cnt,
+                                                     long long* __restrict__ bb, unsigned* __restrict__ dmax) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= v.Ktot) return;
+    const size_t K = v.Ktot;
+    const int b = find_inst(v.inst_k0, v.B, k);
+    const Inst& I = v.inst[b];
+    const int n = cnt[k];
+    long long c[3];
+    float mv2 = 0.f;
+    for (int a = 0; a < 3; a++) {
+        c[a] = v.cq[a * K + k];
+        long long step = 0;
+        if (n > 0) step = floor_div_ll(2 * S[a * K + k] + n, 2 * (long long)n);
+        const float sf = ll_to_float(step) * (float)kGridInv;
+        mv2 = fmaf(sf, sf, mv2);
+        c[a] += step;
+        if (I.periodic[a]) c[a] = floor_mod_ll(c[a], I.boxq[a]);
+        v.cq[a * K + k] = c[a];
+        S[a * K + k] = 0;
+    }
+    cnt[k] = 0;
+    const unsigned grp = __match_any_sync(__activemask(), b);
+    const unsigned mv = __reduce_max_sync(grp, __float_as_uint(sqrtf(mv2) * 1.0001f + 1e-6f));
+    long long mn[3] = {c[0], c[1], c[2]}, mx[3] = {c[0], c[1], c[2]};
+    if (grp == 0xffffffffu) {
+        for (int off = 16; off; off >>= 1)
+            for (int a = 0; a < 3; a++) {
+                mn[a] = min(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], off));
+                mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], off));
+            }
+    }
+    const bool leader = (int)(threadIdx.x & 31) == __ffs(grp) - 1;
+    if (leader && dmax) atomicMax(&dmax[b], mv);
+    if (grp != 0xffffffffu || leader)
+        for (int a = 0; a < 3; a++) { atomicMin(&bb[b * 6 + a], mn[a]); atomicMax(&bb[b * 6 + 3 + a], mx[a]); }
+}
+
 // ============================================================== Morton relabel
 __global__ void k_fill_bbox(long long* bb, int B) {
     for (int t = threadIdx.x; t < B * 6; t += blockDim.x) bb[t] = ((t % 6) < 3) ? 0x7fffffffffffffffll : (-0x7fffffffffffffffll - 1);
@@ -1430,12 +1473,13 @@ void Ensemble::finish_cells() {
     n_rebuilds++;
 }
 
-void Ensemble::rebuild() {
+void Ensemble::rebuild(bool sums_ready) {
     // M-step on the cell-sorted particles, fused with the centroid bounding box
     k_fill_bbox<<<1, 64, 0, stream>>>(d_bbox, B);
     launches++;
     CK(cudaMemsetAsync(d_dmax, 0, sizeof(unsigned) * B, stream));
-    k_mstep_sorted<<<nblk(Ktot, 8), 256, 0, stream>>>(view(), d_bbox, d_dmax);
+    if (sums_ready) k_mstep_apply<<<nblk(Ktot, 256), 256, 0, stream>>>(view(), d_msum, d_mcnt, d_bbox, d_dmax);
+    else k_mstep_sorted<<<nblk(Ktot, 8), 256, 0, stream>>>(view(), d_bbox, d_dmax);
     launches++;
     CK(cudaGetLastError());
     bbox_ready_ = true;

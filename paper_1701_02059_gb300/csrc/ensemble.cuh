@@ -112,7 +112,9 @@ public:
     // one step captured as a CUDA graph per state-buffer parity, replayed
     void integrate_graph(int nsteps);
     void init_cells();                       // seeding + Lloyd + reorder
-    void rebuild();                          // one EM update + reorder
+    // one EM update + reorder; sums_ready: the B-A-O-A launch before it
+    // already summed each cell's lipid displacements (d_msum, d_mcnt)
+    void rebuild(bool sums_ready = false);
     void compute_forces(bool energies);
     void integrate(int nsteps);
     void energies(std::vector<double>& out); // [B][5] after compute_forces(true)
@@ -161,7 +163,7 @@ public:
     void morton_relabel();
     void finish_cells();
     void launch_pairs(bool energies, bool dump);
-    void launch_integrate_first(bool fused);
+    void launch_integrate_first(bool fused, bool msums = false);
     void launch_kick(bool energies);
     void mirrors();
 
@@ -216,6 +218,8 @@ public:
     double2* d_bkd = nullptr;
     unsigned* d_status = nullptr;
     long long* d_S = nullptr;
+    long long* d_msum = nullptr;   // [3][Ktot] M-step sums from the B-A-O-A launch (zero between uses)
+    int* d_mcnt = nullptr;         // [Ktot] lipids per cell, same
     int* d_cnt = nullptr;
     long long* d_bbox = nullptr;
     unsigned long long* d_keys = nullptr;

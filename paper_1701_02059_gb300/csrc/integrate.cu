@@ -100,8 +100,37 @@ __device__ inline void kick(long long vq[3], long long wq[3], const long long nq
 // this step's B A O A: the same two rounded updates as separate launches,
 // without a second pass over memory.  The previous step is then not yet
 // counted in steps[], so this step's index is steps[b] + 1.
+// The M-step's sums for the rebuild that follows (the "Spatial Searching
+// Algorithm" update of each centroid from its lipids at the new positions):
+// lipid i of cell k adds minimg(x_i - c_k) on the 2^-40 grid, exactly.  The
+// lanes of a warp that share a cell add up a 24-bit low part and the high
+// part separately in 32 bits, exact while |x_i - c_k| < 1024 sigma (the
+// mirrors already flag anything beyond 32 sigma); one lane per cell adds the
+// int64 totals.
+__device__ inline void mstep_sums(const View& v, const Inst& I, int p, bool lipid, const long long* xq,
+                                  long long* __restrict__ msum, int* __restrict__ mcnt) {
+    const int k = v.cell[p];
+    const size_t K = v.Ktot;
+    long long d[3] = {0, 0, 0};
+    if (lipid)
+        for (int a = 0; a < 3; a++) d[a] = minimg_q(xq[a] - v.cq[a * K + k], I.boxq[a], I.periodic[a]);
+    const unsigned grp = __match_any_sync(__activemask(), k);
+    const unsigned n = __reduce_add_sync(grp, lipid ? 1u : 0u);
+    long long tot[3];
+    for (int a = 0; a < 3; a++) {
+        const unsigned lo = __reduce_add_sync(grp, (unsigned)(d[a] & 0xffffff));
+        const int hi = (int)__reduce_add_sync(grp, (unsigned)(int)(d[a] >> 24));
+        tot[a] = (long long)hi * 16777216ll + (long long)lo;
+    }
+    if ((int)(threadIdx.x & 31) == __ffs(grp) - 1 && n > 0) {
+        for (int a = 0; a < 3; a++) atomicAdd((unsigned long long*)&msum[a * K + k], (unsigned long long)tot[a]);
+        atomicAdd(&mcnt[k], (int)n);
+    }
+}
+
 template <typename T, bool FUSED>
-__global__ void k_baoa(View v, const long long* __restrict__ steps) {
+__global__ void __launch_bounds__(256, 4) k_baoa(View v, const long long* __restrict__ steps,
+                                                 long long* __restrict__ msum, int* __restrict__ mcnt) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= v.N) return;
     using V = Num<T>;
@@ -143,6 +172,7 @@ __global__ void k_baoa(View v, const long long* __restrict__ steps) {
     }
     for (int a = 0; a < 3; a++) { v.xq[a * N + p] = xq[a]; v.vq[a * N + p] = vq[a]; }
     if (lipid) for (int a = 0; a < 3; a++) { v.nq[a * N + p] = nq[a]; v.wq[a * N + p] = wq[a]; }
+    if (msum) mstep_sums(v, I, p, lipid, xq, msum, mcnt);
 }
 
 // Counts the previous step after a fused launch read the counters.
@@ -205,13 +235,15 @@ __global__ void k_kinetic(View v, long long* __restrict__ energy) {
 
 static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
-void Ensemble::launch_integrate_first(bool fused) {
+void Ensemble::launch_integrate_first(bool fused, bool msums) {
+    long long* ms = msums ? d_msum : nullptr;
+    int* mc = msums ? d_mcnt : nullptr;
     if (precision == 0) {
-        if (fused) k_baoa<float, true><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
-        else k_baoa<float, false><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
+        if (fused) k_baoa<float, true><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step, ms, mc);
+        else k_baoa<float, false><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step, ms, mc);
     } else {
-        if (fused) k_baoa<double, true><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
-        else k_baoa<double, false><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
+        if (fused) k_baoa<double, true><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step, ms, mc);
+        else k_baoa<double, false><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step, ms, mc);
     }
     launches++;
     if (fused) {
