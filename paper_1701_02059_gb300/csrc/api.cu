@@ -82,7 +82,7 @@ View Ensemble::view() {
     v.type = d_type[cur_]; v.id = d_id[cur_];
     v.cell = d_cell; v.slot_of_id = d_slot_of_id;
     v.F = d_F; v.T = d_T; v.Fbig = d_Fbig;
-    v.mq = d_mq; v.mo = d_mo; v.cnorm = d_cnorm; v.grank = d_grank;
+    v.mq = d_mq; v.mo = d_mo; v.mqr = d_mqr; v.mor = d_mor; v.cnorm = d_cnorm; v.grank = d_grank;
     v.cq = d_cq; v.cell_start = d_cell_start; v.R = d_R; v.adj_ptr = d_adj_ptr; v.adj = d_adj; v.adj_cap = adj_cap; v.adjd = d_adjd;
     v.gstart = d_gstart; v.gcent = d_gcent; v.gcf = d_gcf;
     v.bptr = d_bptr; v.bpartner = d_bpartner; v.br0 = d_br0; v.bkb = d_bkb; v.br0_d = d_br0_d; v.bkb_d = d_bkb_d;
@@ -208,6 +208,8 @@ void Ensemble::alloc_core(const std::vector<int>& p0, const std::vector<int>& k0
     d_Fbig = alloc<long long>((size_t)6 * N);
     d_mq = alloc<int4>(N);
     d_mo = alloc<float4>(N);
+    d_mqr = alloc<int4>(N);
+    d_mor = alloc<float4>(N);
     d_cq = alloc<long long>((size_t)3 * Ktot);
     d_cq_tmp = alloc<long long>((size_t)3 * Ktot);
     d_cell_start = alloc<int>(Ktot + 1);

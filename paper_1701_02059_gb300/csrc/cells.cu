@@ -1117,7 +1117,12 @@ __global__ void __launch_bounds__(256, 6) k_cell_props(View v, unsigned long lon
             }
             for (int u = 0; u < 2; u++) {
                 const unsigned t = (unsigned)(r[u] & 0xffffffffu);
-                if (r[u] != ~0ull) v.grank[t0 + t] = (unsigned char)(lane + 32 * u);
+                if (r[u] != ~0ull) {
+                    const int q = lane + 32 * u;
+                    v.grank[t0 + t] = (unsigned char)q;
+                    v.mqr[t0 + q] = v.mq[t0 + t];
+                    v.mor[t0 + q] = v.mo[t0 + t];
+                }
             }
         } else {
             for (int u = 0; u < 4; u++) {
@@ -1135,6 +1140,8 @@ __global__ void __launch_bounds__(256, 6) k_cell_props(View v, unsigned long lon
                     rank += (ks < kt || (ks == kt && s2 < t)) ? 1 : 0;
                 }
                 v.grank[t0 + t] = (unsigned char)rank;
+                v.mqr[t0 + rank] = v.mq[t0 + t];
+                v.mor[t0 + rank] = v.mo[t0 + t];
             }
         }
         __syncwarp();
@@ -1142,7 +1149,9 @@ __global__ void __launch_bounds__(256, 6) k_cell_props(View v, unsigned long lon
 }
 
 
-// Mirrors of the current order (after integration without a rebuild).
+// Mirrors of the current order (after integration without a rebuild),
+// written where the pair kernel reads them: slot p of its cell's tile of 128
+// goes to the tile's position grank[p].
 __global__ void k_mirrors(View v) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= v.N) return;
@@ -1155,13 +1164,15 @@ __global__ void k_mirrors(View v) {
     m.y = mirror_coord(v.xq[N + p], v.cq[(size_t)v.Ktot + c], I, 1, v.status);
     m.z = mirror_coord(v.xq[2 * N + p], v.cq[(size_t)2 * v.Ktot + c], I, 2, v.status);
     m.w = v.type[p];
-    v.mq[p] = m;
     float4 no;
     no.x = ll_to_float(v.nq[p]) * (float)kGridInv;
     no.y = ll_to_float(v.nq[N + p]) * (float)kGridInv;
     no.z = ll_to_float(v.nq[2 * N + p]) * (float)kGridInv;
     no.w = __int_as_float(p);
-    v.mo[p] = no;
+    const int cs = v.cell_start[c];
+    const int q = cs + ((p - cs) & ~127) + (int)v.grank[p];
+    v.mqr[q] = m;
+    v.mor[q] = no;
 }
 
 // ============================================================== neighbouring cells

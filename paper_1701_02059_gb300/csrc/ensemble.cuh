@@ -201,6 +201,8 @@ public:
     long long *d_F = nullptr, *d_T = nullptr, *d_Fbig = nullptr;
     int4* d_mq = nullptr;
     float4* d_mo = nullptr;
+    int4* d_mqr = nullptr;     // mirrors in group-rank order (read by the pair kernel)
+    float4* d_mor = nullptr;
     long long *d_cq = nullptr, *d_cq_tmp = nullptr;
     int* d_cell_start = nullptr;
     double* d_R = nullptr;

@@ -346,7 +346,6 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
     __shared__ alignas(16) unsigned short cand[kPairThreads / 32][kStageCap];   // per-warp candidate list
     __shared__ unsigned short qbuf[kPairThreads / 32][kQCap][32];   // per-lane hit queues
     __shared__ NbrInfo nb[kMaxNbr];
-    __shared__ unsigned char sorder[kPairThreads];
     __shared__ unsigned long long bar;
     __shared__ int s_nstage, s_next, s_next_off, s_self, s_self_lo, s_self_hi, s_total;
 
@@ -446,8 +445,8 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                         if (lane == 0) mbar_expect_tx(&bar, (unsigned)total * 32u);
                         __syncwarp();
                         if (staged && take > 0) {
-                            bulk_g2s(&sy[excl], v.mq + st, take * 16u, &bar);
-                            bulk_g2s(&so[excl], v.mo + st, take * 16u, &bar);
+                            bulk_g2s(&sy[excl], v.mqr + st, take * 16u, &bar);
+                            bulk_g2s(&so[excl], v.mor + st, take * 16u, &bar);
                         }
                     }
                 }
@@ -455,14 +454,14 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
         // the first pass's copies are in flight during the tile set-up
         if (a0 < a1) issue(a0, 0);
 
-        // ---- tangent frame of the cell and compact groups (ranks along the
-        //      tile's longer tangent extent, prepared with the cell radii)
+        // ---- tangent frame of the cell; the mirrors of each tile of 128 are
+        //      stored in the order of their rank along the tile's longer
+        //      tangent extent (prepared with the cell radii), so that the
+        //      group of rank range [g gs, (g + 1) gs) is compact
         const float4 cn = v.cnorm[k];
         const Frame F = tangent_frame(cn.x, cn.y, cn.z);
-        if (tid < nti) sorder[groups > 1 ? (int)v.grank[it0 + tid] : tid] = (unsigned char)tid;
-        __syncthreads();
 
-        // ---- this lane's particle
+        // ---- this lane's particle: rank r of the tile, slot pi
         const int r = igrp * gs + lane;
         const bool ivalid = wactive && lane < gs && r < nti;
         int ti = 0, pi = -1;
@@ -471,9 +470,9 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
         float yix = 0.f, yiy = 0.f, yiz = 0.f;
         unsigned idi = 0;
         if (ivalid) {
-            pi = it0 + sorder[r];
-            qi = v.mq[pi];
-            oi = v.mo[pi];
+            qi = v.mqr[it0 + r];
+            oi = v.mor[it0 + r];
+            pi = __float_as_int(oi.w);
             ti = qi.w & 0xff;
             F.apply(qi.x * kMirrorUnit, qi.y * kMirrorUnit, qi.z * kMirrorUnit, yix, yiy, yiz);
             if (DUMP) idi = v.id[pi];
@@ -507,7 +506,7 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
             const int next = s_next, next_off = s_next_off;
             if (m == 0) { na = next; na_off = next_off; continue; }
             const int sself = s_self, sslo = s_self_lo, sshi = s_self_hi;
-            int selfj = (sslo >= 0 && ivalid) ? sself + (pi - cs) : -1;
+            int selfj = (sslo >= 0 && ivalid) ? sself + (it0 + r - cs) : -1;
             if (selfj < sslo || selfj >= sshi) selfj = -1;
             bool ok = mbar_wait_bounded(&bar, phase, v.status);
             if (__syncthreads_or(!ok)) {
@@ -648,12 +647,11 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
             na_off = next_off;
         }
 
-        // combine the warps of a group (exact integer sums) and write; the
-        // slot of a lane's particle in the tile is sorder[r].  The red rows
-        // of the later splits ((nsplit - 1) x nti <= 96 rows of 56 bytes)
-        // fit in sY, which no warp reads any more.
+        // combine the warps of a group (exact integer sums) and write; rows
+        // are indexed by the rank r.  The red rows of the later splits
+        // ((nsplit - 1) x nti <= 96 rows of 56 bytes) fit in sY, which no
+        // warp reads any more.
         __syncthreads();
-        const int ts = ivalid ? (int)sorder[r] : -1;
         if constexpr (sizeof(T) == 4) {
             // the warps of a group hold partial sums of the same particles:
             // the later splits hand theirs over by plain stores, split 0 adds
@@ -661,7 +659,7 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
             static_assert(3 * 32 * 14 * sizeof(int) <= kStageCap * sizeof(float4), "split rows must fit in sY");
             int (*red)[14] = reinterpret_cast<int (*)[14]>(&sY[0]);
             if (ivalid && jsplit > 0) {
-                int* d = red[(jsplit - 1) * nti + ts];
+                int* d = red[(jsplit - 1) * nti + r];
                 d[0] = acc.f[0].h; d[1] = acc.f[0].l; d[2] = acc.f[1].h; d[3] = acc.f[1].l;
                 d[4] = acc.f[2].h; d[5] = acc.f[2].l; d[6] = acc.t[0].h; d[7] = acc.t[0].l;
                 d[8] = acc.t[1].h; d[9] = acc.t[1].l; d[10] = acc.t[2].h; d[11] = acc.t[2].l;
@@ -672,11 +670,11 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                 int sm[14] = {acc.f[0].h, acc.f[0].l, acc.f[1].h, acc.f[1].l, acc.f[2].h, acc.f[2].l,
                               acc.t[0].h, acc.t[0].l, acc.t[1].h, acc.t[1].l, acc.t[2].h, acc.t[2].l, acc.nf, acc.nt};
                 for (int q = 1; q < nsplit; q++) {
-                    const int* d = red[(q - 1) * nti + ts];
+                    const int* d = red[(q - 1) * nti + r];
 #pragma unroll
                     for (int c = 0; c < 14; c++) sm[c] += d[c];
                 }
-                const int p = it0 + ts;
+                const int p = pi;
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
                     SplitAcc f; f.h = sm[2 * a]; f.l = sm[2 * a + 1];
@@ -697,12 +695,12 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
             __syncthreads();
             if (ivalid)
                 for (int a = 0; a < 3; a++) {
-                    atomicAdd((unsigned long long*)&red64[ts][a], (unsigned long long)acc.F(a));
-                    atomicAdd((unsigned long long*)&red64[ts][3 + a], (unsigned long long)acc.Tq(a));
+                    atomicAdd((unsigned long long*)&red64[r][a], (unsigned long long)acc.F(a));
+                    atomicAdd((unsigned long long*)&red64[r][3 + a], (unsigned long long)acc.Tq(a));
                 }
             __syncthreads();
             if (tid < nti) {
-                const int p = it0 + tid;
+                const int p = __float_as_int(v.mor[it0 + tid].w);   // slot of rank tid
                 for (int a = 0; a < 3; a++) { v.F[a * N + p] = red64[tid][a]; v.T[a * N + p] = red64[tid][3 + a]; }
             }
         }

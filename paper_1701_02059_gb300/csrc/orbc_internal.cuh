@@ -93,6 +93,8 @@ struct View {
     // mirrors for the pair kernel
     int4* mq;                       // x - c at 2^-26 sigma, w = type
     float4* mo;                     // director, w = slot (int bits)
+    int4* mqr;                      // the same two, each tile of 128 particles of a cell
+    float4* mor;                    // in the order of the pair kernel's group ranks
     float4* cnorm;                  // [Ktot] unit normal of each cell (mean lipid director)
     unsigned char* grank;           // [N] rank of each particle in its 128-particle tile along
                                     //     the tile's longer tangent extent (pair-kernel groups)
