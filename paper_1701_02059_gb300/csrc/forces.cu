@@ -97,13 +97,21 @@ __device__ inline float lipid_terms_f(const Inst& I, float dx, float dy, float d
     } else {
         const float th = I.aw * (r - I.rmin);
         const float c = taylor_cos(th), sn = taylor_sin(th);
-        float cp;                                   // c^(2 zeta - 1)
+        // c^(2 zeta - 1) by binary powering from the low bits: the general
+        // path forms the same products in the same order as the zeta = 4
+        // one, so an instance gives the same bits in a batch that mixes
+        // exponents (which takes the general path) as alone
+        float cp;
         if (Z == 4) {
             const float c2 = c * c, c4 = c2 * c2;
-            cp = c4 * c2 * c;
+            cp = (c * c2) * c4;
         } else {
             cp = 1.0f;
-            for (int k = 0; k < 2 * I.zeta - 1; k++) cp *= c;
+            float bp = c;
+            for (int e = 2 * I.zeta - 1; e > 0; e >>= 1) {
+                if (e & 1) cp *= bp;
+                bp *= bp;
+            }
         }
         f = 0.0f;
         fp = 0.0f;

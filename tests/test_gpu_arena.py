@@ -91,6 +91,31 @@ def test_fp64_arena_equals_alone():
         assert_same(got[slots[i]], alone(m, i, 6, G.F64_ALL))
 
 
+def test_mixed_potentials_in_one_batch_equal_alone():
+    """Instances with other constants of the potential (zeta, mu, sin theta0)
+    share a batch: the batch takes the kernels' general paths, which must
+    reproduce each instance's own specialised run bit for bit."""
+    mems = members()[:2]
+    extra = [{}, dict(zeta=2, mu=2.5, sin_theta0=0.05)]
+
+    def prm(i):
+        return G.make_params(kT=mems[i].kT, n_centroids=mems[i].n_centroids, box=mems[i].box,
+                             periodic=mems[i].periodic, seed=1000 + i, instance=i, **extra[i])
+
+    ar = G.Arena(8 << 30)
+    slots = [ar.admit(prm(i), m, 6) for i, m in enumerate(mems)]
+    assert ar.run(10) == 6
+    got = {s: ar.retire(s) for s in ar.poll()}
+    ar.close()
+    for i, m in enumerate(mems):
+        g = G.System(prm(i))
+        g.load_membrane(m)
+        g.init_cells()
+        g.integrate(6)
+        assert_same(got[slots[i]], g.state())
+        g.close()
+
+
 def test_admission_respects_the_budget():
     mem = M.flat_patch_2304(seed=3)
     ar = G.Arena(8 << 30)

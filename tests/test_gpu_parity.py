@@ -324,6 +324,44 @@ def test_nonzero_spontaneous_curvature():
     g.close()
 
 
+POTENTIALS = {
+    # zeta = 2 and 3 take the kernels' general exponent path; a shorter
+    # lipid cutoff and wider proteins change the search radius and the WCA
+    # bands; a nonzero sin(theta0) adds the spontaneous-curvature terms
+    "zeta2": dict(zeta=2, mu=2.0, eps=1.3, rc_lipid=2.5, sigma_wca=0.95, sigma_wca_pp=0.6),
+    "zeta3-s0": dict(zeta=3, mu=4.0, eps=0.8, rc_lipid=2.7, sin_theta0=0.05),
+}
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", list(POTENTIALS))
+def test_other_potential_parameters(name, precision):
+    """Other constants of the potential (the model's parameters are inputs):
+    pair set bit-exact, forces and torques within the path's tolerance."""
+    kw = POTENTIALS[name]
+    mem = small_vesicle()
+    g = G.System(gpu_params(mem, precision=precision, **kw))
+    g.load_membrane(mem)
+    okw = dict(kw)
+    okw["rc"] = okw.pop("rc_lipid")
+    if "sigma_wca_pp" in okw:
+        okw["sigma_pp"] = okw.pop("sigma_wca_pp")
+    o = oracle.OracleSystem(oracle.model(box=mem.box, periodic=mem.periodic, **okw),
+                            oracle.run(kT=mem.kT, n_centroids=mem.n_centroids, seed=0))
+    o.load(mem)
+    g.init_cells()
+    o.init_cells()
+    assert_cells_equal(g, o)
+    assert np.array_equal(g.pairs(), o.pairs())
+    g.compute_forces()
+    o.compute_forces()
+    tol = 1e-5 if precision == 0 else 1e-8
+    ef, frms = force_error(g.forces()[0], o.forces()[0])
+    assert ef <= tol, ef
+    assert torque_error(g.forces()[1], o.forces()[1], frms) <= tol
+    g.close()
+
+
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 def test_coincident_particles_report_non_finite_forces(precision):
     """Two lipids at the same point make the pair force non-finite: the
