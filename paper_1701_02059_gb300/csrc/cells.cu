@@ -670,95 +670,79 @@ __global__ void k_cand_rows(const int* __restrict__ adj_ptr_old, int Ktot, const
     }
 }
 
-__global__ void __launch_bounds__(128, 12) k_estep_fast(View v, const int* __restrict__ cell_old, const int* __restrict__ adj_ptr_old,
-                             const float4* __restrict__ rows, const float* __restrict__ rho_old,
-                             const int* __restrict__ new_of_old, const unsigned* __restrict__ dmax,
-                             int* __restrict__ cell_out, int* __restrict__ fb_list, int* __restrict__ fb_count) {
+// Rebuild E-step from the previous cell list (the paper's guess from the
+// previous particle, made exact), one thread per particle: the candidates
+// are the particle's previous cell and its previous neighbouring cells (one
+// row; the lanes of a warp mostly share it), renumbered by the Morton
+// relabel.  Every centroid outside the row was at least rho_k from the old
+// centroid c_k when the list was built (rho_k: distance to the nearest
+// non-neighbour), and every centroid has since moved at most dmax, so none
+// of them is within best + band of the particle when
+//   sqrt(best) + band < rho_k - 2 dmax - |x - c_k|   (FP32 with margins).
+// Particles that fail the test take the grid search.
+__global__ void __launch_bounds__(128) k_estep_rows(View v, const int* __restrict__ cell_old,
+                                                    const int* __restrict__ adj_ptr_old, const float4* __restrict__ rows,
+                                                    const float* __restrict__ rho_old, const int* __restrict__ new_of_old,
+                                                    const unsigned* __restrict__ dmax, int* __restrict__ cell_out,
+                                                    int* __restrict__ fb_list, int* __restrict__ fb_count) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    const bool valid = i < v.N;
-    int b = 0, ko = -1, kn = -1;
-    long long xq[3] = {0, 0, 0};
-    float p[3] = {0, 0, 0};
-    if (valid) {
-        b = find_inst(v.inst_p0, v.B, i);
-        xq[0] = v.xq[i]; xq[1] = v.xq[(size_t)v.N + i]; xq[2] = v.xq[(size_t)2 * v.N + i];
-        for (int a = 0; a < 3; a++) grid_coord(xq[a], v.inst[b], a, p[a]);
-        ko = cell_old[i];
-        kn = new_of_old[ko];
-    }
-    const Inst& I = v.inst[b];
-    float best = 3.0e38f, second = 3.0e38f, dself2 = 3.0e38f;
-    int bk = -1;
-    // the warp walks the distinct previous cells of its lanes (usually one or
-    // two); each cell's candidate row is loaded once, one candidate per lane,
-    // and broadcast; every lane scores every candidate of the union
-    unsigned todo = __ballot_sync(0xffffffffu, valid);
-    while (todo) {
-        const int leader = __ffs(todo) - 1;
-        const int kc = __shfl_sync(0xffffffffu, ko, leader);
-        const unsigned grp = __ballot_sync(0xffffffffu, valid && ko == kc);
-        todo &= ~grp;
-        const int a0 = adj_ptr_old[kc], len = adj_ptr_old[kc + 1] - a0;
-        for (int c0 = 0; c0 < len; c0 += 32) {
-            int j = -1;
-            float4 c = make_float4(0, 0, 0, 0);
-            if (c0 + lane < len) {
-                c = rows[a0 + c0 + lane];
-                j = __float_as_int(c.w);
-            }
-            const int cnt = min(32, len - c0);
-            for (int q = 0; q < cnt; q++) {
-                const int jq = __shfl_sync(0xffffffffu, j, q);
-                const float cx = __shfl_sync(0xffffffffu, c.x, q);
-                const float cy = __shfl_sync(0xffffffffu, c.y, q);
-                const float cz = __shfl_sync(0xffffffffu, c.z, q);
-                // a warp can straddle two instances of a batch: their cells
-                // live in other coordinates and never compete
-                if ((unsigned)(jq - I.k0) >= (unsigned)I.K) continue;
-                const float dx = axis_dist(p[0], cx, I, 0), dy = axis_dist(p[1], cy, I, 1), dz = axis_dist(p[2], cz, I, 2);
-                const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (jq == kn) dself2 = d2;
-                if (d2 < best || (d2 == best && jq < bk)) { second = best; best = d2; bk = jq; }
-                else if (d2 < second) second = d2;
-            }
-        }
-    }
-    const float lim = sqrtf(best) + kBandE;
     bool fail = false;
-    if (valid) {
+    if (i < v.N) {
+        const int b = find_inst(v.inst_p0, v.B, i);
+        const Inst& I = v.inst[b];
+        long long xq[3];
+        float p[3];
+        for (int a = 0; a < 3; a++) {
+            xq[a] = v.xq[(size_t)a * v.N + i];
+            grid_coord(xq[a], I, a, p[a]);
+        }
+        const int ko = cell_old[i], kn = new_of_old[ko];
+        const int a0 = adj_ptr_old[ko], a1 = adj_ptr_old[ko + 1];
+        float best = 3.0e38f, second = 3.0e38f, dself2 = 3.0e38f;
+        int bk = -1;
+        for (int r = a0; r < a1; r++) {
+            const float4 c = rows[r];
+            const int j = __float_as_int(c.w);
+            const float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1), dz = axis_dist(p[2], c.z, I, 2);
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (j == kn) dself2 = d2;
+            if (d2 < best || (d2 == best && j < bk)) { second = best; best = d2; bk = j; }
+            else if (d2 < second) second = d2;
+        }
+        const float lim = sqrtf(best) + kBandE;
         const float cert = rho_old[ko] - 2.0f * __uint_as_float(dmax[b]) - sqrtf(dself2) - kCertMargin;
         fail = bk < 0 || dself2 >= 3.0e38f || !(lim < cert);
-    }
-    // uncertified particles go to the grid search of k_estep_list (kept out
-    // of this kernel, whose occupancy would otherwise drop to the search's)
-    const unsigned fm = __ballot_sync(0xffffffffu, fail);
-    if (fm) {
-        int base = 0;
-        if (lane == __ffs(fm) - 1) base = atomicAdd(fb_count, __popc(fm));
-        base = __shfl_sync(0xffffffffu, base, __ffs(fm) - 1);
-        if (fail) fb_list[base + __popc(fm & ((1u << lane) - 1u))] = i;
-    }
-    if (!valid || fail) return;
-    if (second > lim * lim) { cell_out[i] = bk; return; }
-    // tie band among the candidates of the particle's own previous cell: FP64
-    double best64 = 1e300;
-    int bk64 = -1;
-    const int a0 = adj_ptr_old[ko], a1 = adj_ptr_old[ko + 1];
-    for (int q = a0; q < a1; q++) {
-        const float4 c = rows[q];
-        const int j = __float_as_int(c.w);
-        const float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1), dz = axis_dist(p[2], c.z, I, 2);
-        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (d2 <= lim * lim) {
-            const double d64 = dist2_grid_d(xq[0], xq[1], xq[2], v.cq[j], v.cq[(size_t)v.Ktot + j],
-                                            v.cq[(size_t)2 * v.Ktot + j], I);
-            if (d64 < best64 || (d64 == best64 && j < bk64)) { best64 = d64; bk64 = j; }
+        if (!fail) {
+            if (second > lim * lim) {
+                cell_out[i] = bk;
+            } else {
+                // tie band: FP64 among the row's candidates within it
+                double best64 = 1e300;
+                int bk64 = -1;
+                for (int r = a0; r < a1; r++) {
+                    const float4 c = rows[r];
+                    const int j = __float_as_int(c.w);
+                    const float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1),
+                                dz = axis_dist(p[2], c.z, I, 2);
+                    if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim) {
+                        const double d64 = dist2_grid_d(xq[0], xq[1], xq[2], v.cq[j], v.cq[(size_t)v.Ktot + j],
+                                                        v.cq[(size_t)2 * v.Ktot + j], I);
+                        if (d64 < best64 || (d64 == best64 && j < bk64)) { best64 = d64; bk64 = j; }
+                    }
+                }
+                cell_out[i] = bk64;
+            }
         }
     }
-    // candidates of other lanes' cells within the band are not in this row:
-    // the certificate excludes them (they are farther than best + band)
-    cell_out[i] = bk64;
+    // the rare failures to the grid search's list, one atomic per warp
+    const unsigned m = __ballot_sync(0xffffffffu, fail);
+    if (m) {
+        const int lane = threadIdx.x & 31, first = __ffs(m) - 1;
+        int base = 0;
+        if (lane == first) base = atomicAdd(fb_count, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, first);
+        if (fail) fb_list[base + __popc(m & ((1u << lane) - 1u))] = i;
+    }
 }
 
 // ============================================================== stable counting sort
@@ -1434,7 +1418,7 @@ void Ensemble::finish_cells() {
     if (prev_adj_valid_) {
         CK(cudaMemsetAsync(d_fbcount, 0, sizeof(int), stream));
         k_cand_rows<<<152 * 8, 256, 0, stream>>>(d_adj_ptr, Ktot, d_adj, d_new_of_old, d_cf, adj_cap, d_candrows);
-        k_estep_fast<<<nblk(N, 128), 128, 0, stream>>>(v, d_cell, d_adj_ptr, d_candrows, d_rho, d_new_of_old, d_dmax,
+        k_estep_rows<<<nblk(N, 128), 128, 0, stream>>>(v, d_cell, d_adj_ptr, d_candrows, d_rho, d_new_of_old, d_dmax,
                                                       d_cell_new, d_cell_tmp, d_fbcount);
         k_estep_list<<<152 * 4, 128, 0, stream>>>(v, d_cell_tmp, d_fbcount, d_cell_new);
         launches += 3;
