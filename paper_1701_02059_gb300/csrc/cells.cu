@@ -261,38 +261,62 @@ __device__ inline bool rec_less(const SortRec& a, const SortRec& b) {
     return a.idx < b.idx;
 }
 
-__global__ void k_tile_sort(View v, const unsigned long long* __restrict__ key, SortRec* __restrict__ out) {
+// One tile of kTile records sorted by a block of kTile threads (bitonic):
+// exchanges across warps go through shared memory, the strides below 32
+// through shuffles.
+__device__ inline SortRec shfl_rec(const SortRec& r, int m) {
+    SortRec o;
+    o.key = __shfl_xor_sync(0xffffffffu, r.key, m);
+    o.idx = __shfl_xor_sync(0xffffffffu, r.idx, m);
+    o.inst = __shfl_xor_sync(0xffffffffu, r.inst, m);
+    return o;
+}
+
+__global__ void __launch_bounds__(kTile) k_tile_sort(View v, const unsigned long long* __restrict__ key,
+                                                    SortRec* __restrict__ out) {
     __shared__ SortRec sh[kTile];
-    int base = blockIdx.x * kTile;
-    for (int t = threadIdx.x; t < kTile; t += blockDim.x) {
-        int k = base + t;
-        SortRec r;
-        if (k < v.Ktot) { r.key = key[k]; r.idx = k; r.inst = find_inst(v.inst_k0, v.B, k); }
-        else { r.key = ~0ull; r.idx = 0x7fffffff; r.inst = 0x7fffffff; }
-        sh[t] = r;
-    }
-    __syncthreads();
+    const int t = threadIdx.x;
+    const int k = blockIdx.x * kTile + t;
+    SortRec r;
+    if (k < v.Ktot) { r.key = key[k]; r.idx = k; r.inst = find_inst(v.inst_k0, v.B, k); }
+    else { r.key = ~0ull; r.idx = 0x7fffffff; r.inst = 0x7fffffff; }
     for (int size = 2; size <= kTile; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = threadIdx.x; t < kTile; t += blockDim.x) {
-                int p = t ^ stride;
-                if (p > t) {
-                    bool up = (t & size) == 0;
-                    SortRec a = sh[t], c = sh[p];
-                    if (rec_less(c, a) == up) { sh[t] = c; sh[p] = a; }
-                }
+            SortRec o;
+            if (stride >= 32) {
+                sh[t] = r;
+                __syncthreads();
+                o = sh[t ^ stride];
+                __syncthreads();
+            } else {
+                o = shfl_rec(r, stride);
             }
-            __syncthreads();
+            // the lower slot of an ascending pair keeps the smaller record
+            const bool up = (t & size) == 0, lower = (t & stride) == 0;
+            const bool take = (lower == up) ? rec_less(o, r) : rec_less(r, o);
+            if (take) r = o;
         }
     }
-    for (int t = threadIdx.x; t < kTile; t += blockDim.x) out[base + t] = sh[t];
+    out[blockIdx.x * kTile + t] = r;
 }
 
 // rank -> new cell index; writes order[new] = old and the permuted centroids.
 // Tiles wholly below or above a record need no search (nearly sorted keys
 // between rebuilds make this the common case).
+constexpr int kBoundTiles = 1024;   // tiles whose bounds a block keeps in shared memory
+
 __global__ void k_rank_scatter(View v, const SortRec* __restrict__ tiles, int ntiles, const long long* __restrict__ cq_old,
                                int* __restrict__ new_of_old) {
+    // first and last record of every tile (most tiles lie wholly below or
+    // above a record, which these settle without a search)
+    __shared__ SortRec tb[2][kBoundTiles];
+    const bool cached = ntiles <= kBoundTiles;
+    if (cached)
+        for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+            tb[0][t] = tiles[(size_t)t * kTile];
+            tb[1][t] = tiles[(size_t)t * kTile + kTile - 1];
+        }
+    __syncthreads();
     int pos = blockIdx.x * blockDim.x + threadIdx.x;   // position in the tiled array
     if (pos >= ntiles * kTile) return;
     SortRec me = tiles[pos];
@@ -306,7 +330,7 @@ __global__ void k_rank_scatter(View v, const SortRec* __restrict__ tiles, int nt
     int t0 = I.k0 / kTile, t1 = (I.k0 + I.K - 1) / kTile;
     for (int t = t0; t <= t1; t++) {
         const SortRec* T = tiles + (size_t)t * kTile;
-        const SortRec tmin = T[0], tmax = T[kTile - 1];
+        const SortRec tmin = cached ? tb[0][t] : T[0], tmax = cached ? tb[1][t] : T[kTile - 1];
         int lo, lo2;
         if (rec_less(tmax, me)) lo = kTile;
         else if (!rec_less(tmin, me)) lo = 0;
@@ -1402,7 +1426,7 @@ void Ensemble::morton_relabel() {
     k_morton_keys<<<nblk(Ktot, 256), 256, 0, stream>>>(v, d_bbox, d_keys);
     launches++;
     int ntiles = nblk(Ktot, kTile);
-    k_tile_sort<<<ntiles, 256, 0, stream>>>(v, d_keys, (SortRec*)d_sortrec);
+    k_tile_sort<<<ntiles, kTile, 0, stream>>>(v, d_keys, (SortRec*)d_sortrec);
     launches++;
     CK(cudaMemcpyAsync(d_cq_tmp, d_cq, sizeof(long long) * 3 * Ktot, cudaMemcpyDeviceToDevice, stream));
     k_rank_scatter<<<nblk((long long)ntiles * kTile, 256), 256, 0, stream>>>(v, (const SortRec*)d_sortrec, ntiles, d_cq_tmp,
