@@ -1014,6 +1014,39 @@ __global__ void __launch_bounds__(256) k_gather_particles(View v, View o, const 
     v.mo[p] = no;
 }
 
+// Bitonic sort of 32 * NE records over a warp, slot lane + 32 u held in
+// r[u] (records of r beyond NE untouched); slots at a distance >= 32 are
+// exchanged inside a lane.
+template <int NE>
+__device__ inline void warp_bitonic_u32(unsigned (&r)[4], int lane) {
+#pragma unroll
+    for (int size = 2; size <= 32 * NE; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+                const int du = stride >> 5;
+#pragma unroll
+                for (int u = 0; u < NE; u++) {
+                    if (u & du) continue;
+                    const bool up = ((lane + 32 * u) & size) == 0;
+                    const unsigned x = r[u], y = r[u + du];
+                    r[u] = up ? min(x, y) : max(x, y);
+                    r[u + du] = up ? max(x, y) : min(x, y);
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < NE; u++) {
+                    const int e = lane + 32 * u;
+                    const unsigned o = __shfl_xor_sync(0xffffffffu, r[u], stride);
+                    const bool up = (e & size) == 0;
+                    const bool lower = (e & stride) == 0;
+                    r[u] = (lower == up) ? min(r[u], o) : max(r[u], o);
+                }
+            }
+        }
+    }
+}
+
 // Per-cell quantities read back from the gathered mirrors: one warp per cell
 // computes the cell radius R_k = max |x - c_k| (FP32 with the FP64
 // definition inside a band), the pair kernel's cell normal (mean lipid
@@ -1021,10 +1054,8 @@ __global__ void __launch_bounds__(256) k_gather_particles(View v, View o, const 
 // particles, every particle's rank along the tile's longer tangent extent.
 // Launched with 256 threads (8 warps, one cell each).
 __global__ void __launch_bounds__(256, 6) k_cell_props(View v, unsigned long long* __restrict__ rmax_bits /* [B] */) {
-    __shared__ float skey[8][128];
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    const int wb = threadIdx.x >> 5;
     if (k >= v.Ktot) return;
     const int b = find_inst(v.inst_k0, v.B, k);
     const Inst& I = v.inst[b];
@@ -1091,66 +1122,26 @@ __global__ void __launch_bounds__(256, 6) k_cell_props(View v, unsigned long lon
             hi_b = fmaxf(hi_b, __shfl_xor_sync(0xffffffffu, hi_b, off));
         }
         const bool use_a = (hi_a - lo_a) >= (hi_b - lo_b);
-        if (nt <= 64) {
-            // bitonic sort of (key, index) over 64 slots, two per lane; the
-            // rank of a particle is the slot its record ends in
-            unsigned long long r[2];
-            for (int u = 0; u < 2; u++) {
-                const int t = lane + 32 * u;
-                if (t < nt) {
-                    unsigned kb = __float_as_uint(use_a ? ya[u] : yb[u]);
-                    kb ^= (kb >> 31) ? 0xffffffffu : 0x80000000u;      // order-preserving bits
-                    r[u] = ((unsigned long long)kb << 32) | (unsigned)t;
-                } else {
-                    r[u] = ~0ull;
-                }
-            }
-            for (int size = 2; size <= 64; size <<= 1) {
-                for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    if (stride == 32) {
-                        // slots lane and lane + 32 (same lane); both ascending for size 64
-                        const unsigned long long a = r[0], c = r[1];
-                        r[0] = min(a, c);
-                        r[1] = max(a, c);
-                    } else {
-                        for (int u = 0; u < 2; u++) {
-                            const int e = lane + 32 * u;
-                            const unsigned long long o = __shfl_xor_sync(0xffffffffu, r[u], stride);
-                            const bool up = (e & size) == 0;
-                            const bool lower = (e & stride) == 0;
-                            r[u] = (lower == up) ? min(r[u], o) : max(r[u], o);
-                        }
-                    }
-                }
-            }
-            for (int u = 0; u < 2; u++) {
-                const unsigned t = (unsigned)(r[u] & 0xffffffffu);
-                if (r[u] != ~0ull) {
-                    const int q = lane + 32 * u;
-                    v.grank[t0 + t] = (unsigned char)q;
-                    v.mqr[t0 + q] = v.mq[t0 + t];
-                    v.mor[t0 + q] = v.mo[t0 + t];
-                }
-            }
-        } else {
-            for (int u = 0; u < 4; u++) {
-                const int t = lane + 32 * u;
-                if (t < nt) skey[wb][t] = use_a ? ya[u] : yb[u];
-            }
-            __syncwarp();
-            for (int u = 0; u < 4; u++) {
-                const int t = lane + 32 * u;
-                if (t >= nt) continue;
-                const float kt = skey[wb][t];
-                int rank = 0;
-                for (int s2 = 0; s2 < nt; s2++) {
-                    const float ks = skey[wb][s2];
-                    rank += (ks < kt || (ks == kt && s2 < t)) ? 1 : 0;
-                }
-                v.grank[t0 + t] = (unsigned char)rank;
-                v.mqr[t0 + rank] = v.mq[t0 + t];
-                v.mor[t0 + rank] = v.mo[t0 + t];
-            }
+        // 32-bit records: the key quantised to 24 bits over the tile's
+        // extent (monotone), the tile index in the low 7 bits (equal keys
+        // go by index); the rank of a particle is the slot its record ends
+        // in after a warp bitonic sort
+        const float klo = use_a ? lo_a : lo_b, kext = use_a ? hi_a - lo_a : hi_b - lo_b;
+        const float ksc = kext > 0.f ? 16777215.0f / kext : 0.f;
+        unsigned r[4];
+        for (int u = 0; u < 4; u++) {
+            const int t = lane + 32 * u;
+            const float y = use_a ? ya[u] : yb[u];
+            r[u] = (t < nt) ? (min(16777215u, (unsigned)((y - klo) * ksc)) << 7) | (unsigned)t : 0xffffffffu;
+        }
+        if (nt <= 64) warp_bitonic_u32<2>(r, lane);
+        else warp_bitonic_u32<4>(r, lane);
+        for (int u = 0; u < 4; u++) {
+            if (r[u] == 0xffffffffu) continue;
+            const int t = (int)(r[u] & 127u), q = lane + 32 * u;
+            v.grank[t0 + t] = (unsigned char)q;
+            v.mqr[t0 + q] = v.mq[t0 + t];
+            v.mor[t0 + q] = v.mo[t0 + t];
         }
         __syncwarp();
     }
