@@ -4,8 +4,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <mutex>
 #include <numeric>
+#include <thread>
 
 #include "../../include/orbc.h"
 
@@ -367,8 +369,11 @@ void Ensemble::setup(const std::vector<HostInstance>& list) {
         for (int b = 0; b < B; b++) {
             const HostInstance& h = list[b];
             const std::vector<long long>& src = h.*fields[q];
-            for (int i = 0; i < h.n; i++)
-                for (int a = 0; a < 3; a++) ax[(size_t)a * N + p0[b] + i] = src[(size_t)3 * i + a];
+            const int pb = p0[b];
+            parallel_for(h.n, [&](long long i0, long long i1) {
+                for (long long i = i0; i < i1; i++)
+                    for (int a = 0; a < 3; a++) ax[(size_t)a * N + pb + i] = src[(size_t)3 * i + a];
+            });
         }
         CK(cudaMemcpyAsync(d_state[0][q], ax.data(), sizeof(long long) * 3 * N, cudaMemcpyHostToDevice, stream));
         CK(cudaStreamSynchronize(stream));
@@ -544,49 +549,46 @@ void Ensemble::step_body(bool fused) {
 }
 
 // ---------------------------------------------------------------- getters
+// Host copies in id order: converted on the device (k_to_id_order), then one
+// copy per array.
 void Ensemble::get_state(int b, double* pos, double* vel, double* ori, double* angvel, long long* step) {
     const Inst& I = inst_h[b];
-    const int n = I.n;
-    std::vector<long long> buf((size_t)n);
-    std::vector<unsigned> ids(n);
-    CK(cudaMemcpyAsync(ids.data(), d_id[cur_] + I.p0, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, stream));
+    double* tmp = nullptr;
+    CK(cudaMallocAsync(&tmp, sizeof(double) * 3 * (size_t)std::max(I.n, 1), stream));
     double* outs[4] = {pos, vel, ori, angvel};
-    for (int q = 0; q < 4; q++) {
-        if (!outs[q]) continue;
-        for (int a = 0; a < 3; a++) {
-            CK(cudaMemcpyAsync(buf.data(), d_state[cur_][q] + (size_t)a * N + I.p0, sizeof(long long) * n,
-                               cudaMemcpyDeviceToHost, stream));
-            CK(cudaStreamSynchronize(stream));
-            for (int i = 0; i < n; i++) outs[q][(size_t)3 * ids[i] + a] = (double)buf[i] * kGridInv;
+    try {
+        for (int q = 0; q < 4; q++) {
+            if (!outs[q]) continue;
+            to_id_order(b, d_state[cur_][q], kGridInv, tmp);
+            CK(cudaMemcpyAsync(outs[q], tmp, sizeof(double) * 3 * (size_t)I.n, cudaMemcpyDeviceToHost, stream));
         }
-    }
-    if (step) {
-        long long s = 0;
-        CK(cudaMemcpyAsync(&s, d_step + b, sizeof(long long), cudaMemcpyDeviceToHost, stream));
+        if (step) CK(cudaMemcpyAsync(step, d_step + b, sizeof(long long), cudaMemcpyDeviceToHost, stream));
         CK(cudaStreamSynchronize(stream));
-        *step = s;
+    } catch (...) {
+        cudaFreeAsync(tmp, stream);
+        throw;
     }
-    CK(cudaStreamSynchronize(stream));
+    CK(cudaFreeAsync(tmp, stream));
 }
 
 void Ensemble::get_forces(int b, double* f, double* t) {
     const Inst& I = inst_h[b];
-    const int n = I.n;
-    std::vector<long long> buf((size_t)n);
-    std::vector<unsigned> ids(n);
-    CK(cudaMemcpyAsync(ids.data(), d_id[cur_] + I.p0, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, stream));
+    double* tmp = nullptr;
+    CK(cudaMallocAsync(&tmp, sizeof(double) * 3 * (size_t)std::max(I.n, 1), stream));
     long long* src[2] = {d_F, d_T};
     double* outs[2] = {f, t};
-    for (int q = 0; q < 2; q++) {
-        if (!outs[q]) continue;
-        for (int a = 0; a < 3; a++) {
-            CK(cudaMemcpyAsync(buf.data(), src[q] + (size_t)a * N + I.p0, sizeof(long long) * n, cudaMemcpyDeviceToHost,
-                               stream));
-            CK(cudaStreamSynchronize(stream));
-            for (int i = 0; i < n; i++) outs[q][(size_t)3 * ids[i] + a] = (double)buf[i] * kForceUnit;
+    try {
+        for (int q = 0; q < 2; q++) {
+            if (!outs[q]) continue;
+            to_id_order(b, src[q], kForceUnit, tmp);
+            CK(cudaMemcpyAsync(outs[q], tmp, sizeof(double) * 3 * (size_t)I.n, cudaMemcpyDeviceToHost, stream));
         }
+        CK(cudaStreamSynchronize(stream));
+    } catch (...) {
+        cudaFreeAsync(tmp, stream);
+        throw;
     }
-    CK(cudaStreamSynchronize(stream));
+    CK(cudaFreeAsync(tmp, stream));
 }
 
 void Ensemble::get_cells(int b, int* cell_of_id, unsigned* slot_ids, double* centroids, int* cell_start,
@@ -677,30 +679,23 @@ __global__ void k_to_id_order(const unsigned* __restrict__ id, const long long* 
     for (int a = 0; a < 3; a++) out[(size_t)3 * i + a] = __ll2double_rn(q[(size_t)a * N + p]) * unit;
 }
 
-void Ensemble::get_state_device(int b, double* pos, double* vel, double* ori, double* angvel) {
+void Ensemble::to_id_order(int b, const long long* q, double unit, double* out) {
     const Inst& I = inst_h[b];
-    double* outs[4] = {pos, vel, ori, angvel};
-    for (int q = 0; q < 4; q++) {
-        if (!outs[q]) continue;
-        k_to_id_order<<<(I.n + 255) / 256, 256, 0, stream>>>(d_id[cur_], d_state[cur_][q], (size_t)N, I.p0, I.n,
-                                                             kGridInv, outs[q]);
-        launches++;
-    }
+    k_to_id_order<<<(I.n + 255) / 256, 256, 0, stream>>>(d_id[cur_], q, (size_t)N, I.p0, I.n, unit, out);
+    launches++;
     CK(cudaGetLastError());
+}
+
+void Ensemble::get_state_device(int b, double* pos, double* vel, double* ori, double* angvel) {
+    double* outs[4] = {pos, vel, ori, angvel};
+    for (int q = 0; q < 4; q++)
+        if (outs[q]) to_id_order(b, d_state[cur_][q], kGridInv, outs[q]);
     CK(cudaStreamSynchronize(stream));
 }
 
 void Ensemble::get_forces_device(int b, double* f, double* t) {
-    const Inst& I = inst_h[b];
-    long long* src[2] = {d_F, d_T};
-    double* outs[2] = {f, t};
-    for (int q = 0; q < 2; q++) {
-        if (!outs[q]) continue;
-        k_to_id_order<<<(I.n + 255) / 256, 256, 0, stream>>>(d_id[cur_], src[q], (size_t)N, I.p0, I.n, kForceUnit,
-                                                             outs[q]);
-        launches++;
-    }
-    CK(cudaGetLastError());
+    if (f) to_id_order(b, d_F, kForceUnit, f);
+    if (t) to_id_order(b, d_T, kForceUnit, t);
     CK(cudaStreamSynchronize(stream));
 }
 
@@ -716,8 +711,20 @@ struct orbc_system {
     Ensemble* ens = nullptr;
     HostInstance host;
     bool have_particles = false;
+    bool dirty = false;        // the host copy is newer than the device (set-up pending)
+    bool host_stale = false;   // the device has stepped past the host copy
     std::string err;
 };
+
+static void pull_state(orbc_system* s);
+
+// The device set-up runs once, when a call first needs the device after the
+// particles or bonds changed.
+static void sync_device(orbc_system* s) {
+    if (!s->dirty) return;
+    s->ens->setup({s->host});
+    s->dirty = false;
+}
 
 // Current device state back into the host copy (exact: grid values), so a
 // re-setup keeps the trajectory.
@@ -731,13 +738,14 @@ static void pull_state(orbc_system* s) {
     for (int i = 0; i < n; i++) ids[i] = (unsigned)i;
     std::vector<unsigned char> ty(n);
     for (int i = 0; i < n; i++) ty[h.id[i]] = h.type[i];
-    for (int i = 0; i < n; i++)
-        for (int a = 0; a < 3; a++) {
-            h.xq[(size_t)3 * i + a] = llrint(pos[(size_t)3 * i + a] * kGrid);
-            h.vq[(size_t)3 * i + a] = llrint(vel[(size_t)3 * i + a] * kGrid);
-            h.nq[(size_t)3 * i + a] = llrint(ori[(size_t)3 * i + a] * kGrid);
-            h.wq[(size_t)3 * i + a] = llrint(w[(size_t)3 * i + a] * kGrid);
+    parallel_for((long long)3 * n, [&](long long q0, long long q1) {
+        for (long long q = q0; q < q1; q++) {
+            h.xq[q] = llrint(pos[q] * kGrid);
+            h.vq[q] = llrint(vel[q] * kGrid);
+            h.nq[q] = llrint(ori[q] * kGrid);
+            h.wq[q] = llrint(w[q] * kGrid);
         }
+    });
     h.id = ids;
     h.type = ty;
     h.step0 = step;
@@ -785,6 +793,27 @@ void orbc::check_params(const Params& P) {
 }
 
 
+void orbc::parallel_for(long long n, const std::function<void(long long, long long)>& f) {
+    if (n <= 0) return;
+    const long long nt = std::min<long long>({16, std::max(1u, std::thread::hardware_concurrency()), (n + 65535) / 65536});
+    if (nt <= 1) { f(0, n); return; }
+    std::vector<std::thread> th;
+    std::vector<std::exception_ptr> err((size_t)nt);
+    const long long chunk = (n + nt - 1) / nt;
+    for (long long t = 0; t < nt; t++)
+        th.emplace_back([&, t] {
+            try {
+                const long long b = t * chunk, e = std::min(n, b + chunk);
+                if (b < e) f(b, e);
+            } catch (...) {
+                err[(size_t)t] = std::current_exception();
+            }
+        });
+    for (auto& x : th) x.join();
+    for (auto& e : err)
+        if (e) std::rethrow_exception(e);
+}
+
 HostInstance orbc::host_instance(const Params& prm, int n, const double* pos, const double* vel, const double* ori,
                                  const double* angvel, const unsigned char* type, const unsigned* id) {
     if (n < 1 || !pos || !vel || !ori || !angvel || !type || !id) throw ArgError("null pointer or n < 1");
@@ -799,27 +828,31 @@ HostInstance orbc::host_instance(const Params& prm, int n, const double* pos, co
         if (id[i] >= (unsigned)n || seen[id[i]]) throw ArgError("ids must be a permutation of 0..n-1");
         seen[id[i]] = 1;
         if (type[i] > 2) throw ArgError("unknown particle type");
-        for (int a = 0; a < 3; a++) {
-            double x = pos[3 * i + a], v = vel[3 * i + a];
-            if (!std::isfinite(x) || !std::isfinite(v)) throw ArgError("non-finite position or velocity");
-            if (std::fabs(x) >= 4096.0) throw ArgError("|position| must be < 4096 sigma");
-            if (std::fabs(v) >= 1e6) throw ArgError("|velocity| too large");
-            h.xq[(size_t)3 * i + a] = llrint(x * kGrid);
-            h.vq[(size_t)3 * i + a] = llrint(v * kGrid);
-        }
-        if (type[i] == kLipid) {
-            double o[3], w[3];
-            for (int a = 0; a < 3; a++) { o[a] = ori[3 * i + a]; w[a] = angvel[3 * i + a]; }
-            for (int a = 0; a < 3; a++)
-                if (!std::isfinite(o[a]) || !std::isfinite(w[a])) throw ArgError("non-finite orientation");
-            double nn = std::sqrt(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]);
-            if (std::fabs(nn - 1.0) > 1e-6) throw ArgError("lipid orientation must be a unit vector");
+    }
+    parallel_for(n, [&](long long i0, long long i1) {
+        for (long long i = i0; i < i1; i++) {
             for (int a = 0; a < 3; a++) {
-                h.nq[(size_t)3 * i + a] = llrint(o[a] * kGrid);
-                h.wq[(size_t)3 * i + a] = llrint(w[a] * kGrid);
+                double x = pos[3 * i + a], v = vel[3 * i + a];
+                if (!std::isfinite(x) || !std::isfinite(v)) throw ArgError("non-finite position or velocity");
+                if (std::fabs(x) >= 4096.0) throw ArgError("|position| must be < 4096 sigma");
+                if (std::fabs(v) >= 1e6) throw ArgError("|velocity| too large");
+                h.xq[(size_t)3 * i + a] = llrint(x * kGrid);
+                h.vq[(size_t)3 * i + a] = llrint(v * kGrid);
+            }
+            if (type[i] == kLipid) {
+                double o[3], w[3];
+                for (int a = 0; a < 3; a++) { o[a] = ori[3 * i + a]; w[a] = angvel[3 * i + a]; }
+                for (int a = 0; a < 3; a++)
+                    if (!std::isfinite(o[a]) || !std::isfinite(w[a])) throw ArgError("non-finite orientation");
+                double nn = std::sqrt(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]);
+                if (std::fabs(nn - 1.0) > 1e-6) throw ArgError("lipid orientation must be a unit vector");
+                for (int a = 0; a < 3; a++) {
+                    h.nq[(size_t)3 * i + a] = llrint(o[a] * kGrid);
+                    h.wq[(size_t)3 * i + a] = llrint(w[a] * kGrid);
+                }
             }
         }
-    }
+    });
     return h;
 }
 
@@ -880,7 +913,8 @@ int orbc_set_particles(orbc_system* s, int n, const double* pos, const double* v
     return guarded(s, [&] {
         s->host = host_instance(s->prm, n, pos, vel, ori, angvel, type, id);
         s->have_particles = true;
-        s->ens->setup({s->host});
+        s->dirty = true;
+        s->host_stale = false;
     });
 }
 
@@ -888,8 +922,10 @@ int orbc_set_bonds(orbc_system* s, int nb, const int* ij, const double* r0, cons
     if (!s) return ORBC_E_ARG;
     return guarded(s, [&] {
         if (!s->have_particles) throw StateError("set particles before bonds");
+        if (s->host_stale) pull_state(s);
         host_bonds(s->host, nb, ij, r0, kb);
-        s->ens->setup({s->host});
+        s->dirty = true;
+        s->host_stale = false;
     });
 }
 
@@ -897,7 +933,7 @@ int orbc_init_cells(orbc_system* s, const double* centroids) {
     if (!s) return ORBC_E_ARG;
     return guarded(s, [&] {
         if (!s->have_particles) throw StateError("no particles");
-        if (s->ens->B == 1) pull_state(s);
+        if (s->host_stale) pull_state(s);
         if (centroids) {
             for (int q = 0; q < 3 * s->prm.n_centroids; q++)
                 if (!std::isfinite(centroids[q]) || std::fabs(centroids[q]) >= 4096.0) throw ArgError("invalid centroid");
@@ -906,6 +942,8 @@ int orbc_init_cells(orbc_system* s, const double* centroids) {
             s->host.centroids.clear();
         }
         s->ens->setup({s->host});
+        s->dirty = false;
+        s->host_stale = false;
         s->ens->init_cells();
     });
 }
@@ -913,6 +951,7 @@ int orbc_init_cells(orbc_system* s, const double* centroids) {
 int orbc_rebuild_cells(orbc_system* s) {
     if (!s) return ORBC_E_ARG;
     return guarded(s, [&] {
+        sync_device(s);
         if (!s->ens->cells_valid) throw StateError("cells not initialised");
         s->ens->rebuild();
         unsigned st = s->ens->read_status(true);
@@ -924,6 +963,7 @@ int orbc_compute_forces(orbc_system* s, double* energies_out) {
     if (!s) return ORBC_E_ARG;
     unsigned st = 0;
     int rc = guarded(s, [&] {
+        sync_device(s);
         s->ens->compute_forces(energies_out != nullptr);
         st = s->ens->read_status(true);
         if (!st && energies_out) {
@@ -941,6 +981,8 @@ int orbc_integrate(orbc_system* s, int nsteps) {
     if (nsteps < 0) return fail(s, ORBC_E_ARG, "nsteps < 0");
     unsigned st = 0;
     int rc = guarded(s, [&] {
+        sync_device(s);
+        s->host_stale = true;
         s->ens->integrate(nsteps);
         st = s->ens->read_status(true);
     });
@@ -952,6 +994,7 @@ int orbc_get_state(orbc_system* s, double* pos, double* vel, double* ori, double
     if (!s) return ORBC_E_ARG;
     return guarded(s, [&] {
         if (!s->have_particles) throw StateError("no particles");
+        sync_device(s);
         s->ens->get_state(0, pos, vel, ori, angvel, step);
     });
 }
@@ -973,7 +1016,8 @@ int orbc_set_particles_device(orbc_system* s, int n, const double* pos, const do
         CK(cudaStreamSynchronize(s->stream));
         s->host = host_instance(s->prm, n, hp.data(), hv.data(), ho.data(), hw.data(), ht.data(), hi.data());
         s->have_particles = true;
-        s->ens->setup({s->host});
+        s->dirty = true;
+        s->host_stale = false;
     });
 }
 
@@ -981,6 +1025,7 @@ int orbc_get_state_device(orbc_system* s, double* pos, double* vel, double* ori,
     if (!s) return ORBC_E_ARG;
     return guarded(s, [&] {
         if (!s->have_particles) throw StateError("no particles");
+        sync_device(s);
         s->ens->get_state_device(0, pos, vel, ori, angvel);
     });
 }
@@ -988,6 +1033,7 @@ int orbc_get_state_device(orbc_system* s, double* pos, double* vel, double* ori,
 int orbc_get_forces_device(orbc_system* s, double* force, double* torque) {
     if (!s) return ORBC_E_ARG;
     return guarded(s, [&] {
+        sync_device(s);
         if (!s->ens->forces_valid) throw StateError("forces not computed");
         s->ens->get_forces_device(0, force, torque);
     });
@@ -996,6 +1042,7 @@ int orbc_get_forces_device(orbc_system* s, double* force, double* torque) {
 int orbc_get_forces(orbc_system* s, double* force, double* torque) {
     if (!s) return ORBC_E_ARG;
     return guarded(s, [&] {
+        sync_device(s);
         if (!s->ens->forces_valid) throw StateError("forces not computed");
         s->ens->get_forces(0, force, torque);
     });
@@ -1005,6 +1052,7 @@ int orbc_get_cells(orbc_system* s, int* cell_of_id, unsigned* slot_ids, double* 
                    double* radius, int* adj_ptr, int* adj) {
     if (!s) return ORBC_E_ARG;
     return guarded(s, [&] {
+        sync_device(s);
         if (!s->ens->cells_valid) throw StateError("cells not initialised");
         s->ens->get_cells(0, cell_of_id, slot_ids, centroids, cell_start, radius, adj_ptr, adj);
     });
@@ -1013,6 +1061,7 @@ int orbc_get_cells(orbc_system* s, int* cell_of_id, unsigned* slot_ids, double* 
 int orbc_get_adjacency_len(orbc_system* s, long long* len) {
     if (!s || !len) return ORBC_E_ARG;
     return guarded(s, [&] {
+        sync_device(s);
         if (!s->ens->cells_valid) throw StateError("cells not initialised");
         *len = s->ens->adjacency_len(0);
     });
@@ -1020,7 +1069,10 @@ int orbc_get_adjacency_len(orbc_system* s, long long* len) {
 
 int orbc_dump_pairs(orbc_system* s, long long cap, unsigned* pairs, long long* npairs) {
     if (!s || !npairs || cap < 0) return ORBC_E_ARG;
-    return guarded(s, [&] { *npairs = s->ens->dump_pairs(0, cap, pairs); });
+    return guarded(s, [&] {
+        sync_device(s);
+        *npairs = s->ens->dump_pairs(0, cap, pairs);
+    });
 }
 
 int orbc_set_timing(orbc_system* s, int on) {

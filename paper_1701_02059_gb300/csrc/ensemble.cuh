@@ -123,6 +123,8 @@ public:
     void get_state(int b, double* pos, double* vel, double* ori, double* angvel, long long* step);
     void get_forces(int b, double* f, double* t);
     void get_state_device(int b, double* pos, double* vel, double* ori, double* angvel);
+    // per-slot int64 array q of instance b to FP64 [n][3] in id order (device)
+    void to_id_order(int b, const long long* q, double unit, double* out);
     void get_forces_device(int b, double* f, double* t);
     void get_cells(int b, int* cell_of_id, unsigned* slot_ids, double* centroids, int* cell_start, double* radius,
                    int* adj_ptr, int* adj);
