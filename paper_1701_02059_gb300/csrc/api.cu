@@ -330,17 +330,17 @@ void Ensemble::upload_bonds(const std::vector<BondSpec>& bl, const std::vector<i
     CK(cudaStreamSynchronize(stream));   // the host vectors die here
 }
 
-void Ensemble::setup(const std::vector<HostInstance>& list) {
+void Ensemble::setup(const std::vector<const HostInstance*>& list) {
     free_all();
     B = (int)list.size();
     if (B < 1) throw ArgError("no instance");
-    precision = list[0].prm.precision;
+    precision = list[0]->prm.precision;
     N = 0; Ktot = 0;
     inst_h.assign(B, Inst());
     prm_h.clear();
     std::vector<int> p0(B + 1, 0), k0(B + 1, 0);
     for (int b = 0; b < B; b++) {
-        const HostInstance& h = list[b];
+        const HostInstance& h = *list[b];
         if (h.prm.precision != precision) throw ArgError("all instances of a batch need the same precision");
         inst_h[b] = make_inst(h.prm);
         inst_h[b].p0 = N; inst_h[b].n = h.n;
@@ -353,9 +353,9 @@ void Ensemble::setup(const std::vector<HostInstance>& list) {
         k0[b + 1] = Ktot;
     }
     step_h.assign(B, 0);
-    for (int b = 0; b < B; b++) step_h[b] = list[b].step0;
+    for (int b = 0; b < B; b++) step_h[b] = list[b]->step0;
     bool any_skin = false;
-    for (auto& h : list) any_skin |= (h.prm.rebuild_every > 1);
+    for (const HostInstance* hp : list) any_skin |= (hp->prm.rebuild_every > 1);
     alloc_core(p0, k0, any_skin);
 
     // state, axis-major
@@ -367,7 +367,7 @@ void Ensemble::setup(const std::vector<HostInstance>& list) {
                                                                &HostInstance::wq};
     for (int q = 0; q < 4; q++) {
         for (int b = 0; b < B; b++) {
-            const HostInstance& h = list[b];
+            const HostInstance& h = *list[b];
             const std::vector<long long>& src = h.*fields[q];
             const int pb = p0[b];
             parallel_for(h.n, [&](long long i0, long long i1) {
@@ -379,12 +379,15 @@ void Ensemble::setup(const std::vector<HostInstance>& list) {
         CK(cudaStreamSynchronize(stream));
     }
     for (int b = 0; b < B; b++) {
-        const HostInstance& h = list[b];
-        for (int i = 0; i < h.n; i++) {
-            ty[p0[b] + i] = h.type[i];
-            ids[p0[b] + i] = h.id[i];
-            slot[p0[b] + h.id[i]] = p0[b] + i;
-        }
+        const HostInstance& h = *list[b];
+        const int pb = p0[b];
+        parallel_for(h.n, [&](long long i0, long long i1) {   // ids are a permutation: no write conflicts
+            for (long long i = i0; i < i1; i++) {
+                ty[pb + i] = h.type[i];
+                ids[pb + i] = h.id[i];
+                slot[pb + h.id[i]] = pb + (int)i;
+            }
+        });
     }
     CK(cudaMemcpyAsync(d_type[0], ty.data(), N, cudaMemcpyHostToDevice, stream));
     CK(cudaMemcpyAsync(d_id[0], ids.data(), sizeof(unsigned) * N, cudaMemcpyHostToDevice, stream));
@@ -392,14 +395,14 @@ void Ensemble::setup(const std::vector<HostInstance>& list) {
 
     // bonds
     std::vector<BondSpec> bl(B);
-    for (int b = 0; b < B; b++) bl[b] = BondSpec{&list[b].bonds, &list[b].r0, &list[b].kb};
+    for (int b = 0; b < B; b++) bl[b] = BondSpec{&list[b]->bonds, &list[b]->r0, &list[b]->kb};
     upload_bonds(bl, p0);
 
     // initial centroids (host) and the centroid-grid geometry of each instance
     std::vector<long long> c0((size_t)3 * Ktot);
     Gtot = 0;
     for (int b = 0; b < B; b++) {
-        const HostInstance& h = list[b];
+        const HostInstance& h = *list[b];
         Inst& I = inst_h[b];
         const int K = I.K;
         std::vector<long long> c((size_t)3 * K);
@@ -467,10 +470,12 @@ void Ensemble::setup(const std::vector<HostInstance>& list) {
     scan_exclusive(d_cnt, d_cell_start, Ktot + 1);
     CK(cudaStreamSynchronize(stream));
     n_lloyd_.clear();
-    for (auto& h : list) n_lloyd_.push_back(h.prm.n_lloyd_init);
+    for (const HostInstance* hp : list) n_lloyd_.push_back(hp->prm.n_lloyd_init);
     cells_valid = false;
     forces_valid = false;
 }
+
+void Ensemble::setup(const HostInstance& h) { setup(std::vector<const HostInstance*>{&h}); }
 
 void Ensemble::init_cells() {
     int iters = 0;
@@ -722,7 +727,7 @@ static void pull_state(orbc_system* s);
 // particles or bonds changed.
 static void sync_device(orbc_system* s) {
     if (!s->dirty) return;
-    s->ens->setup({s->host});
+    s->ens->setup(s->host);
     s->dirty = false;
 }
 
@@ -941,7 +946,7 @@ int orbc_init_cells(orbc_system* s, const double* centroids) {
         } else {
             s->host.centroids.clear();
         }
-        s->ens->setup({s->host});
+        s->ens->setup(s->host);
         s->dirty = false;
         s->host_stale = false;
         s->ens->init_cells();

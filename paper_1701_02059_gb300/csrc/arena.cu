@@ -258,7 +258,7 @@ public:
         size_t bytes = 0;
         {
             Ensemble e(stream_);
-            e.setup({h});
+            e.setup(h);
             bytes = e.bytes_allocated();
             if (reserved() + bytes + bytes / 2 > budget_) throw CudaError(cudaErrorMemoryAllocation, "over the HBM budget");
             e.init_cells();

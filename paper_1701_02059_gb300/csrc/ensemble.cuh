@@ -104,7 +104,8 @@ public:
     Ensemble& operator=(const Ensemble&) = delete;
 
     // set-up: particles and bonds of every instance; allocates everything
-    void setup(const std::vector<HostInstance>& list);
+    void setup(const std::vector<const HostInstance*>& list);
+    void setup(const HostInstance& h);
     // set-up from carried instances: continues each where it stopped
     void setup_from(const std::vector<const Snapshot*>& list);
     void export_instance(int b, Snapshot& s);

@@ -70,7 +70,7 @@ static double time_tile(const HostInstance& h, int K, int steps, cudaStream_t st
     c.prm.n_centroids = K;
     c.centroids.clear();
     Ensemble e(st);
-    e.setup({c});
+    e.setup(c);
     e.init_cells();
     e.integrate(2);
     cudaEvent_t a, b;
