@@ -81,8 +81,11 @@ def serve_batched(jobs, hbm_budget_bytes: int, max_steps: int = 50, graphs: bool
     inner = arena.stats()
     arena.close()
     summary = _percentiles([r["latency_s"] for r in rec])
-    summary.update({"makespan_s": total, "particle_steps": work, "particle_steps_per_s": work / total,
-                    "gpu_launches": launches})
+    busy = spent["admit_s"] + spent["run_s"] + spent["retire_s"]
+    # the same two throughputs as the plain form: over the makespan (arrival
+    # gaps included) and over the time the server was busy
+    summary.update({"makespan_s": total, "busy_s": busy, "particle_steps": work, "particle_steps_per_s": work / total,
+                    "busy_particle_steps_per_s": work / busy if busy > 0 else 0.0, "gpu_launches": launches})
     summary.update({k: round(v, 3) for k, v in spent.items()})
     summary.update({"repack_s": round(inner["repack_s"], 3), "repacks": inner["repacks"],
                     "batched_steps": inner["steps"]})
@@ -131,5 +134,6 @@ def serve_plain(jobs, keep_states: bool = False, stream: int | None = None):
         rec[i] = {"arrival_s": j["arrival_s"], "start_s": start, "done_s": clock, "service_s": service,
                   "latency_s": clock - j["arrival_s"]}
     summary = _percentiles([r["latency_s"] for r in rec])
-    summary.update({"makespan_s": clock, "busy_s": busy, "particle_steps": work, "particle_steps_per_s": work / busy})
+    summary.update({"makespan_s": clock, "busy_s": busy, "particle_steps": work, "particle_steps_per_s": work / clock,
+                    "busy_particle_steps_per_s": work / busy})
     return rec, summary, states
