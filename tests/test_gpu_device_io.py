@@ -60,3 +60,26 @@ def test_device_getters_need_state():
     with pytest.raises(RuntimeError):
         g.force_tensors()
     g.close()
+
+
+def test_lazy_setup_keeps_the_trajectory():
+    """The device set-up is deferred to the first call that needs it: the
+    state reads back right after set_particles, and setting the bonds again
+    after some steps keeps the stepped state (the host copy is refreshed
+    from the device first)."""
+    mem = M.flat_patch_2304()
+    g = G.System(params(mem))
+    g.set_particles(mem.pos, mem.vel, mem.ori, mem.angvel, mem.type, mem.id)
+    st0 = g.state()
+    assert np.array_equal(st0["pos"], np.rint(mem.pos * 2.0 ** 40) / 2.0 ** 40)
+    g.set_bonds(mem.bonds, mem.r0, mem.kb)
+    g.init_cells()
+    g.integrate(5)
+    st5 = g.state()
+    g.set_bonds(mem.bonds, mem.r0, mem.kb)
+    g.init_cells()
+    st5b = g.state()
+    for k in ("pos", "vel", "ori", "angvel"):
+        assert np.array_equal(st5[k], st5b[k]), k
+    assert st5b["step"] == 5
+    g.close()
