@@ -704,7 +704,7 @@ __global__ void k_cand_rows(const int* __restrict__ adj_ptr_old, int Ktot, const
 // of them is within best + band of the particle when
 //   sqrt(best) + band < rho_k - 2 dmax - |x - c_k|   (FP32 with margins).
 // Particles that fail the test take the grid search.
-__global__ void __launch_bounds__(128) k_estep_rows(View v, const int* __restrict__ cell_old,
+__global__ void __launch_bounds__(128, 16) k_estep_rows(View v, const int* __restrict__ cell_old,
                                                     const int* __restrict__ adj_ptr_old, const float4* __restrict__ rows,
                                                     const float* __restrict__ rho_old, const int* __restrict__ new_of_old,
                                                     const unsigned* __restrict__ dmax, int* __restrict__ cell_out,
