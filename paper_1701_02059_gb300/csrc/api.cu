@@ -86,6 +86,7 @@ View Ensemble::view() {
     v.F = d_F; v.T = d_T; v.Fbig = d_Fbig;
     v.mq = d_mq; v.mo = d_mo; v.mqr = d_mqr; v.mor = d_mor; v.cnorm = d_cnorm; v.grank = d_grank;
     v.cq = d_cq; v.cell_start = d_cell_start; v.R = d_R; v.adj_ptr = d_adj_ptr; v.adj = d_adj; v.adj_cap = adj_cap; v.adjd = d_adjd;
+    v.adjn = d_adjcount;
     v.gstart = d_gstart; v.gcent = d_gcent; v.gcf = d_gcf;
     v.bptr = d_bptr; v.bpartner = d_bpartner; v.br0 = d_br0; v.bkb = d_bkb; v.br0_d = d_br0_d; v.bkb_d = d_bkb_d;
     v.nbond = nbond; v.bij = d_bij; v.binst = d_binst; v.bkf = d_bkf; v.bkd = d_bkd;
@@ -598,6 +599,7 @@ void Ensemble::get_forces(int b, double* f, double* t) {
 
 void Ensemble::get_cells(int b, int* cell_of_id, unsigned* slot_ids, double* centroids, int* cell_start,
                          double* radius, int* adj_ptr, int* adj) {
+    adjacency_csr();
     const Inst& I = inst_h[b];
     const int n = I.n, K = I.K;
     std::vector<unsigned> ids(n);
@@ -635,6 +637,7 @@ void Ensemble::get_cells(int b, int* cell_of_id, unsigned* slot_ids, double* cen
 }
 
 long long Ensemble::adjacency_len(int b) {
+    adjacency_csr();
     const Inst& I = inst_h[b];
     int ap[2];
     CK(cudaMemcpyAsync(&ap[0], d_adj_ptr + I.k0, sizeof(int), cudaMemcpyDeviceToHost, stream));

@@ -682,12 +682,13 @@ constexpr float kCertMargin = 4e-3f;
 // The previous rows with their cells renumbered and the renumbered cells'
 // FP32 centroids (w = new index), so the E-step reads one record per
 // candidate instead of three dependent loads.
-__global__ void k_cand_rows(const int* __restrict__ adj_ptr_old, int Ktot, const int* __restrict__ adj_old,
-                            const int* __restrict__ new_of_old, const float4* __restrict__ cf, long long cap,
+__global__ void k_cand_rows(const int* __restrict__ cnt_old, int Ktot, const int* __restrict__ pad_old,
+                            const int* __restrict__ new_of_old, const float4* __restrict__ cf,
                             float4* __restrict__ rows) {
-    const long long n = min((long long)adj_ptr_old[Ktot], cap);
+    const long long n = (long long)Ktot * kAdjRow;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        const int j = new_of_old[adj_old[q]];
+        if ((int)(q % kAdjRow) >= cnt_old[q / kAdjRow]) continue;
+        const int j = new_of_old[pad_old[q]];
         float4 c = cf[j];
         c.w = __int_as_float(j);
         rows[q] = c;
@@ -705,7 +706,7 @@ __global__ void k_cand_rows(const int* __restrict__ adj_ptr_old, int Ktot, const
 //   sqrt(best) + band < rho_k - 2 dmax - |x - c_k|   (FP32 with margins).
 // Particles that fail the test take the grid search.
 __global__ void __launch_bounds__(128, 16) k_estep_rows(View v, const int* __restrict__ cell_old,
-                                                    const int* __restrict__ adj_ptr_old, const float4* __restrict__ rows,
+                                                    const int* __restrict__ cnt_old, const float4* __restrict__ rows,
                                                     const float* __restrict__ rho_old, const int* __restrict__ new_of_old,
                                                     const unsigned* __restrict__ dmax, int* __restrict__ cell_out,
                                                     int* __restrict__ fb_list, int* __restrict__ fb_count) {
@@ -721,7 +722,7 @@ __global__ void __launch_bounds__(128, 16) k_estep_rows(View v, const int* __res
             grid_coord(xq[a], I, a, p[a]);
         }
         const int ko = cell_old[i], kn = new_of_old[ko];
-        const int a0 = adj_ptr_old[ko], a1 = adj_ptr_old[ko + 1];
+        const int a0 = ko * kAdjRow, a1 = a0 + min(cnt_old[ko], kAdjRow);
         float best = 3.0e38f, second = 3.0e38f, dself2 = 3.0e38f;
         int bk = -1;
         for (int r = a0; r < a1; r++) {
@@ -1199,8 +1200,9 @@ __device__ inline bool adj_test(const View& v, const Inst& I, int k, int j, doub
 // the cube around the cell's own grid cell that the reach
 // R_k + R_max + r_s + 2 skin can touch, test every centroid there with the
 // exact rule, collect the row in shared memory and sort it.  Rows longer than
-// kAdjRow are flagged (kStatusAdjOverflow) and truncated.
-constexpr int kAdjRow = 64;
+// kAdjRow are flagged (kStatusAdjOverflow) and truncated. Each entry gets
+// the pair kernel's staging descriptor (particle range, exact centroid
+// offset at 2^-26 sigma) in the same fixed-stride row.
 __global__ void __launch_bounds__(256, 6) k_adj_warp(View v, const unsigned long long* __restrict__ rmax_bits, int* __restrict__ count,
                            float* __restrict__ rho_out, int* __restrict__ pad /* [Ktot][kAdjRow] */) {
     __shared__ int row[8][kAdjRow];
@@ -1302,30 +1304,13 @@ __global__ void __launch_bounds__(256, 6) k_adj_warp(View v, const unsigned long
         rk[0] += o < val[0];
         rk[1] += o < val[1];
     }
-    for (int u = 0; u < 2; u++)
-        if (lane + 32 * u < n) pad[(size_t)k * kAdjRow + rk[u]] = val[u];
-    if (lane == 0) {
-        count[k] = n;
-        rho_out[k] = rho;
-    }
-}
-
-// CSR rows from the padded rows, with the pair kernel's staging descriptor
-// of every entry (particle range, exact centroid offset at 2^-26 sigma).
-__global__ void k_adj_compact(View v, const int* __restrict__ pad) {
-    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (k >= v.Ktot) return;
-    const Inst& I = v.inst[find_inst(v.inst_k0, v.B, k)];
-    const long long ckx = v.cq[k], cky = v.cq[(size_t)v.Ktot + k], ckz = v.cq[(size_t)2 * v.Ktot + k];
-    const int a0 = v.adj_ptr[k], n = v.adj_ptr[k + 1] - a0;
-    for (int t = lane; t < n; t += 32) {
-        if (a0 + t >= v.adj_cap) break;
-        const int j = pad[(size_t)k * kAdjRow + t];
-        v.adj[a0 + t] = j;
-        const long long dx = minimg_q(v.cq[j] - ckx, I.boxq[0], I.periodic[0]);
-        const long long dy = minimg_q(v.cq[(size_t)v.Ktot + j] - cky, I.boxq[1], I.periodic[1]);
-        const long long dz = minimg_q(v.cq[(size_t)2 * v.Ktot + j] - ckz, I.boxq[2], I.periodic[2]);
+    for (int u = 0; u < 2; u++) {
+        if (lane + 32 * u >= n) continue;
+        const int j = val[u];
+        pad[(size_t)k * kAdjRow + rk[u]] = j;
+        const long long dx = minimg_q(v.cq[j] - cx, I.boxq[0], I.periodic[0]);
+        const long long dy = minimg_q(v.cq[(size_t)v.Ktot + j] - cy, I.boxq[1], I.periodic[1]);
+        const long long dz = minimg_q(v.cq[(size_t)2 * v.Ktot + j] - cz, I.boxq[2], I.periodic[2]);
         AdjDesc d;
         d.start = v.cell_start[j];
         d.cnt = v.cell_start[j + 1] - d.start;
@@ -1333,8 +1318,21 @@ __global__ void k_adj_compact(View v, const int* __restrict__ pad) {
         d.oy = (int)(unsigned)(unsigned long long)((dy + (1ll << (kMirrorShift - 1))) >> kMirrorShift);
         d.oz = (int)(unsigned)(unsigned long long)((dz + (1ll << (kMirrorShift - 1))) >> kMirrorShift);
         d.cell = j;
-        v.adjd[a0 + t] = d;
+        v.adjd[(size_t)k * kAdjRow + rk[u]] = d;
     }
+    if (lane == 0) {
+        count[k] = n;
+        rho_out[k] = rho;
+    }
+}
+
+// CSR rows from the fixed-stride rows (for the getters).
+__global__ void k_adj_csr(View v, const int* __restrict__ pad) {
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= v.Ktot) return;
+    const int a0 = v.adj_ptr[k], n = v.adj_ptr[k + 1] - a0;
+    for (int t = lane; t < n && a0 + t < v.adj_cap; t += 32) v.adj[a0 + t] = pad[(size_t)k * kAdjRow + t];
 }
 
 // ============================================================== host side
@@ -1432,8 +1430,8 @@ void Ensemble::finish_cells() {
     build_grid();
     if (prev_adj_valid_) {
         CK(cudaMemsetAsync(d_fbcount, 0, sizeof(int), stream));
-        k_cand_rows<<<152 * 8, 256, 0, stream>>>(d_adj_ptr, Ktot, d_adj, d_new_of_old, d_cf, adj_cap, d_candrows);
-        k_estep_rows<<<nblk(N, 128), 128, 0, stream>>>(v, d_cell, d_adj_ptr, d_candrows, d_rho, d_new_of_old, d_dmax,
+        k_cand_rows<<<152 * 8, 256, 0, stream>>>(d_adjcount, Ktot, d_adjpad, d_new_of_old, d_cf, d_candrows);
+        k_estep_rows<<<nblk(N, 128), 128, 0, stream>>>(v, d_cell, d_adjcount, d_candrows, d_rho, d_new_of_old, d_dmax,
                                                       d_cell_new, d_cell_tmp, d_fbcount);
         k_estep_list<<<152 * 4, 128, 0, stream>>>(v, d_cell_tmp, d_fbcount, d_cell_new);
         launches += 3;
@@ -1471,16 +1469,21 @@ void Ensemble::finish_cells() {
     k_adj_warp<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(nv, d_rmax, d_adjcount, d_rho, d_adjpad);
     launches++;
     CK(cudaGetLastError());
-    CK(cudaMemsetAsync(d_adjcount + Ktot, 0, sizeof(int), stream));
-    scan_exclusive(d_adjcount, d_adj_ptr, Ktot + 1);
-    nv = view();
-    k_adj_compact<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(nv, d_adjpad);
     prev_adj_valid_ = true;
-    launches++;
-    CK(cudaGetLastError());
+    csr_valid_ = false;
     cells_valid = true;
     forces_valid = false;
     n_rebuilds++;
+}
+
+void Ensemble::adjacency_csr() {
+    if (csr_valid_ || !cells_valid) return;
+    CK(cudaMemsetAsync(d_adjcount + Ktot, 0, sizeof(int), stream));
+    scan_exclusive(d_adjcount, d_adj_ptr, Ktot + 1);
+    k_adj_csr<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(view(), d_adjpad);
+    launches++;
+    CK(cudaGetLastError());
+    csr_valid_ = true;
 }
 
 void Ensemble::rebuild(bool sums_ready) {

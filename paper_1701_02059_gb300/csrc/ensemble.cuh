@@ -130,6 +130,8 @@ public:
     void get_cells(int b, int* cell_of_id, unsigned* slot_ids, double* centroids, int* cell_start, double* radius,
                    int* adj_ptr, int* adj);
     long long adjacency_len(int b);
+    // the neighbour rows as CSR (adj_ptr, adj), built on demand for the getters
+    void adjacency_csr();
     long long dump_pairs(int b, long long cap, unsigned* pairs);
     unsigned read_status(bool clear);
     void sync();
@@ -187,6 +189,7 @@ private:
     std::vector<void*> allocs_;
     int cur_ = 0;
     bool bbox_ready_ = false;   // set by the fused M-step of a rebuild
+    bool csr_valid_ = false;        // d_adj_ptr / d_adj hold the current rows as CSR
     bool prev_adj_valid_ = false;   // the cell list of the previous rebuild can seed the E-step
     // timing state
     cudaEvent_t ev0_ = nullptr, ev1_ = nullptr;

@@ -362,8 +362,11 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
     const Inst& I = v.inst[b];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int cs = v.cell_start[k], ce = v.cell_start[k + 1];
-    const int a0 = v.adj_ptr[k];
-    const int a1 = (int)min((long long)v.adj_ptr[k + 1], v.adj_cap);   // overflow is flagged by the adjacency pass
+    // the cell's neighbour row (fixed stride; rows longer than kAdjRow are
+    // flagged by the adjacency pass)
+    const AdjDesc* __restrict__ row = v.adjd + (size_t)k * kAdjRow;
+    const int a0 = 0;
+    const int a1 = min(v.adjn[k], kAdjRow);
     const float rs_b = I.rsf + kFilterBand;
     const float rs2f = rs_b * rs_b;
     const float rcl = sqrtf(I.rc2f_ll), rcw = sqrtf(I.rc2f_wca), rcp = sqrtf(I.rc2f_pp);
@@ -394,7 +397,7 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                     int l = 0, st = 0, c = 0;
                     AdjDesc d;
                     if (has) {
-                        d = v.adjd[nn];
+                        d = row[nn];
                         l = d.cell;
                         st = d.start;
                         c = d.cnt;

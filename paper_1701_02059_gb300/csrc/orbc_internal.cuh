@@ -68,6 +68,9 @@ struct Inst {
 // What the pair kernel needs to stage neighbouring cell l of cell k: its
 // particle range and the exact offset c_l - c_k (minimum image) at the mirror
 // resolution 2^-26 sigma, as wrap-around int32.
+// Longest row of neighbouring cells; rows are stored at this fixed stride.
+constexpr int kAdjRow = 64;
+
 struct AdjDesc {
     int start, cnt;
     int ox, oy, oz;
@@ -104,7 +107,8 @@ struct View {
     double* R;                      // [Ktot] cell radius
     int* adj_ptr;                   // [Ktot+1]
     int* adj;                       // [adj_cap]
-    struct AdjDesc* adjd;           // [adj_cap] staging descriptor of each neighbouring cell
+    struct AdjDesc* adjd;           // [Ktot][kAdjRow] staging descriptors, row k ascending by cell
+    const int* adjn;                // [Ktot] row lengths
     long long adj_cap;
     // centroid search grid
     int* gstart;                    // [Gtot+1]
