@@ -238,6 +238,7 @@ void Ensemble::alloc_core(const std::vector<int>& p0, const std::vector<int>& k0
     d_cell_tmp = alloc<int>(N);
     d_rmax = alloc<unsigned long long>(B);
     d_rho = alloc<float>(Ktot);
+    d_lbound = alloc<float>(N);
     d_cf = alloc<float4>(Ktot);
     d_cnorm = alloc<float4>(Ktot);
     d_grank = alloc<unsigned char>(N);
@@ -485,11 +486,15 @@ void Ensemble::init_cells() {
         tic("grid");
         build_grid();
         toc();
+        // the first round searches every particle and records a lower bound
+        // on its second-nearest centroid; later rounds search only the
+        // particles whose bound no longer certifies their centroid
         tic("estep");
-        estep(d_cell);
+        if (it == 0) estep(d_cell, d_lbound);
+        else estep_bounded(d_cell);
         toc();
         tic("mstep");
-        mstep_iter(d_cell, it);
+        mstep_iter(d_cell, it, d_dmax);
         toc();
     }
     finish_cells();

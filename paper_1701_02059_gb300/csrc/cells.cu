@@ -57,20 +57,33 @@ __global__ void k_mstep_accum(View v, const int* __restrict__ cell_of, long long
 }
 
 // c_k <- c_k + floor((2 S_k + n_k) / (2 n_k)); periodic axes wrap into [0, L).
-__global__ void k_mstep_finish(View v, long long* __restrict__ S, int* __restrict__ cnt, int iter) {
+// dmax (nullable): the largest move of an instance's centroids, as FP32 bits
+// rounded up (warp-reduced before the atomics).
+__global__ void k_mstep_finish(View v, long long* __restrict__ S, int* __restrict__ cnt, int iter,
+                               unsigned* __restrict__ dmax) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= v.Ktot) return;
     int b = find_inst(v.inst_k0, v.B, k);
     const Inst& I = v.inst[b];
     int n = (iter < 0 || iter < I.n_lloyd) ? cnt[k] : 0;   // instances past their k-means rounds keep c
+    float mv2 = 0.f;
     for (int a = 0; a < 3; a++) {
         long long c = v.cq[(size_t)a * v.Ktot + k];
-        if (n > 0) c += floor_div_ll(2 * S[(size_t)a * v.Ktot + k] + n, 2 * (long long)n);
+        long long step = 0;
+        if (n > 0) step = floor_div_ll(2 * S[(size_t)a * v.Ktot + k] + n, 2 * (long long)n);
+        const float sf = ll_to_float(step) * (float)kGridInv;
+        mv2 = fmaf(sf, sf, mv2);
+        c += step;
         if (I.periodic[a]) c = floor_mod_ll(c, I.boxq[a]);
         v.cq[(size_t)a * v.Ktot + k] = c;
         S[(size_t)a * v.Ktot + k] = 0;
     }
     cnt[k] = 0;
+    if (dmax) {
+        const unsigned grp = __match_any_sync(__activemask(), b);
+        const unsigned mv = __reduce_max_sync(grp, __float_as_uint(sqrtf(mv2) * 1.0001f + 1e-6f));
+        if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicMax(&dmax[b], mv);
+    }
 }
 
 // Rebuild M-step on cell-sorted particles: one warp per cell sums its lipids'
@@ -410,6 +423,8 @@ __global__ void k_grid_fill(View v, const int* __restrict__ gidx, int* __restric
 // definition's operation order.  A single candidate in the band is the
 // exact answer without FP64.
 constexpr float kBandE = 2e-3f;
+// margin of the FP32 certificates of the E-steps (coordinates up to ~2000 sigma)
+constexpr float kCertMargin = 4e-3f;
 
 __device__ inline float axis_dist(float p, float c, const Inst& I, int a) {
     float d = p - c;
@@ -477,14 +492,19 @@ __device__ inline float shell_bound(const float p[3], const int g[3], int r, con
     return lb;
 }
 
-__device__ void estep_one(const View& v, int i, int* __restrict__ cell_out) {
+// lbound (nullable) receives a lower bound on the distance from the particle
+// to every centroid but the one it is assigned: the second-best scanned
+// distance or the bound on the unscanned shells, whichever is smaller (0
+// when the winner was decided inside the tie band).
+__device__ void estep_one(const View& v, int i, int* __restrict__ cell_out, float* __restrict__ lbound = nullptr) {
     int b = find_inst(v.inst_p0, v.B, i);
     const Inst& I = v.inst[b];
     long long xq[3] = { v.xq[i], v.xq[(size_t)v.N + i], v.xq[(size_t)2 * v.N + i] };
     float p[3];
     int g[3];
     for (int a = 0; a < 3; a++) g[a] = grid_coord(xq[a], I, a, p[a]);
-    float best = 3.0e38f;     // FP32 distance squared
+    float best = 3.0e38f, second = 3.0e38f;     // FP32 distances squared
+    float lbx = 3.0e38f;                         // bound on the unscanned shells
     int r = 0;
     const int rmax = max(I.gdim[0], max(I.gdim[1], I.gdim[2]));
     for (;; r++) {
@@ -493,13 +513,14 @@ __device__ void estep_one(const View& v, int i, int* __restrict__ cell_out) {
                 float4 c = v.gcf[q];
                 float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1), dz = axis_dist(p[2], c.z, I, 2);
                 float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                second = fminf(second, fmaxf(best, d2));
                 best = fminf(best, d2);
             }
         });
         bool ex;
         float lb = shell_bound(p, g, r, I, ex);
         if (ex || r >= rmax) break;
-        if (best < 3.0e38f && lb > sqrtf(best) + kBandE) break;
+        if (best < 3.0e38f && lb > sqrtf(best) + kBandE) { lbx = lb; break; }
     }
     // second pass over the searched cube: candidates within the band
     float lim = sqrtf(best) + kBandE;
@@ -531,9 +552,11 @@ __device__ void estep_one(const View& v, int i, int* __restrict__ cell_out) {
     if (ncand == 0) {   // unreachable for finite input: the search covers every centroid
         atomicOr(v.status, kStatusGridRange);
         cell_out[i] = I.k0;
+        if (lbound) lbound[i] = 0.f;
         return;
     }
     cell_out[i] = (ncand == 1) ? k1 : bestk;
+    if (lbound) lbound[i] = (ncand == 1) ? fminf(sqrtf(second), lbx) : 0.f;
 }
 
 // ---- warp-cooperative search for instances without periodic axes: the
@@ -578,9 +601,13 @@ __device__ inline void warp_box(const int g[3], bool valid, int lo[3], int hi[3]
     }
 }
 
-__global__ void k_estep_warp(View v, int* __restrict__ cell_out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = i < v.N;
+// list (nullable): search only the *count particles listed (in list order,
+// which keeps the lanes of a warp close in space)
+__global__ void k_estep_warp(View v, int* __restrict__ cell_out, float* __restrict__ lbound,
+                             const int* __restrict__ list, const int* __restrict__ count) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = list ? q < *count : q < v.N;
+    const int i = valid ? (list ? list[q] : q) : 0;
     const int b = valid ? find_inst(v.inst_p0, v.B, i) : -1;
     int b0 = __shfl_sync(0xffffffffu, b, 0);
     const int bfirst = __reduce_max_sync(0xffffffffu, valid ? b : -1);
@@ -591,7 +618,7 @@ __global__ void k_estep_warp(View v, int* __restrict__ cell_out) {
     const bool periodic = I.periodic[0] | I.periodic[1] | I.periodic[2];
     if (!same || periodic) {
         // mixed instances or periodic axes: per-thread shell search
-        if (valid) estep_one(v, i, cell_out);
+        if (valid) estep_one(v, i, cell_out, lbound);
         return;
     }
     long long xq[3] = {0, 0, 0};
@@ -605,10 +632,11 @@ __global__ void k_estep_warp(View v, int* __restrict__ cell_out) {
     warp_box(g, valid, lo, hi);
     if (hi[0] - lo[0] > 2 || hi[1] - lo[1] > 2 || hi[2] - lo[2] > 2) {
         // queries not clustered in space (e.g. input order): per-thread search
-        if (valid) estep_one(v, i, cell_out);
+        if (valid) estep_one(v, i, cell_out, lbound);
         return;
     }
     float best = 3.0e38f, second = 3.0e38f;
+    float lbr = 3.0e38f;    // bound on the unscanned region after the last ring
     int bk = -1;
     int r = 0;
     for (;; r++) {
@@ -624,6 +652,7 @@ __global__ void k_estep_warp(View v, int* __restrict__ cell_out) {
         });
         bool ex;
         const float lb = region_bound(I, p, lo, hi, r, ex);
+        lbr = ex ? 3.0e38f : lb;
         const bool done = !valid || ex || (best < 3.0e38f && lb > sqrtf(best) + kBandE);
         if (__all_sync(0xffffffffu, done)) break;
     }
@@ -653,6 +682,7 @@ __global__ void k_estep_warp(View v, int* __restrict__ cell_out) {
     if (valid) {
         if (bk < 0) { atomicOr(v.status, kStatusGridRange); bk = I.k0; }
         cell_out[i] = bk;
+        if (lbound) lbound[i] = amb ? 0.f : fminf(sqrtf(second), lbr);
     }
 }
 
@@ -663,22 +693,47 @@ __global__ void k_estep(View v, int* __restrict__ cell_out) {
 
 // Grid search for the particles the certified E-step could not decide.
 __global__ void k_estep_list(View v, const int* __restrict__ fb_list, const int* __restrict__ fb_count,
-                             int* __restrict__ cell_out) {
+                             int* __restrict__ cell_out, float* __restrict__ lbound = nullptr) {
     const int n = *fb_count;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
-        estep_one(v, fb_list[q], cell_out);
+        estep_one(v, fb_list[q], cell_out, lbound);
 }
 
-// Rebuild E-step from the previous cell list (the paper's guess from the
-// previous particle, made exact): the candidates are the particle's previous
-// cell and its previous neighbouring cells, renumbered by the Morton
-// relabel.  Every centroid outside that set was at least rho_k from the old
-// centroid c_k when the list was built (rho_k: distance to the nearest
-// non-neighbour), and every centroid has since moved at most dmax, so none
-// of them is within best + band of the particle when
-//   sqrt(best) + band < rho_k - 2 dmax - |x - c_k|   (FP32 with margins).
-// Particles that fail the test take the grid search.
-constexpr float kCertMargin = 4e-3f;
+// k-means E-step after the first round (Hamerly's bound): the particle's
+// centroid of the previous round is still its nearest when the distance to
+// it is below the previous lower bound on every other centroid, less the
+// largest move of the M-step in between (FP32 with a margin); the bound is
+// carried on, the others are listed for the grid search.
+__global__ void __launch_bounds__(256) k_estep_bound(View v, const int* __restrict__ cell, float* __restrict__ lbound,
+                                                     const float4* __restrict__ cf, const unsigned* __restrict__ dmax,
+                                                     int* __restrict__ list, int* __restrict__ count) {
+    __shared__ int wcount[8], wbase[8], bbase;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    bool need = false;
+    if (i < v.N) {
+        const int b = find_inst(v.inst_p0, v.B, i);
+        const Inst& I = v.inst[b];
+        float p[3];
+        for (int a = 0; a < 3; a++) grid_coord(v.xq[(size_t)a * v.N + i], I, a, p[a]);
+        const float4 c = cf[cell[i]];
+        const float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1), dz = axis_dist(p[2], c.z, I, 2);
+        const float l = lbound[i] - __uint_as_float(dmax[b]);
+        if (sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + kCertMargin < l) lbound[i] = l;
+        else need = true;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    if (lane == 0) wcount[warp] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < 8; w++) { wbase[w] = tot; tot += wcount[w]; }
+        bbase = tot ? atomicAdd(count, tot) : 0;
+    }
+    __syncthreads();
+    if (need) list[bbase + wbase[warp] + __popc(m & ((1u << lane) - 1u))] = i;
+}
+
 // The previous rows with their cells renumbered and the renumbered cells'
 // FP32 centroids (w = new index), so the E-step reads one record per
 // candidate instead of three dependent loads.
@@ -1351,12 +1406,13 @@ void Ensemble::build_grid() {
     CK(cudaGetLastError());
 }
 
-void Ensemble::mstep_iter(const int* cell_of, int iter) {
+void Ensemble::mstep_iter(const int* cell_of, int iter, unsigned* dmax) {
     View v = view();
     k_mstep_accum<<<nblk(N, 256), 256, 0, stream>>>(v, cell_of, d_S, d_cnt);
     launches++;
     CK(cudaGetLastError());
-    k_mstep_finish<<<nblk(Ktot, 256), 256, 0, stream>>>(v, d_S, d_cnt, iter);
+    if (dmax) CK(cudaMemsetAsync(dmax, 0, sizeof(unsigned) * B, stream));
+    k_mstep_finish<<<nblk(Ktot, 256), 256, 0, stream>>>(v, d_S, d_cnt, iter, dmax);
     launches++;
     CK(cudaGetLastError());
 }
@@ -1396,9 +1452,17 @@ bool Ensemble::displacement_exceeds_skin() {
     return f != 0;
 }
 
-void Ensemble::estep(int* cell_out) {
-    k_estep_warp<<<nblk(N, 128), 128, 0, stream>>>(view(), cell_out);
+void Ensemble::estep(int* cell_out, float* lbound) {
+    k_estep_warp<<<nblk(N, 128), 128, 0, stream>>>(view(), cell_out, lbound, nullptr, nullptr);
     launches++;
+    CK(cudaGetLastError());
+}
+
+void Ensemble::estep_bounded(int* cell) {
+    CK(cudaMemsetAsync(d_fbcount, 0, sizeof(int), stream));
+    k_estep_bound<<<nblk(N, 256), 256, 0, stream>>>(view(), cell, d_lbound, d_cf, d_dmax, d_cell_tmp, d_fbcount);
+    k_estep_warp<<<nblk(N, 128), 128, 0, stream>>>(view(), cell, d_lbound, d_cell_tmp, d_fbcount);
+    launches += 2;
     CK(cudaGetLastError());
 }
 
@@ -1437,7 +1501,7 @@ void Ensemble::finish_cells() {
         launches += 3;
         CK(cudaGetLastError());
     } else {
-        estep(d_cell_new);
+        estep(d_cell_new, nullptr);
     }
     // stable counting sort
     CK(cudaMemsetAsync(d_cnt, 0, sizeof(int) * (Ktot + 1), stream));

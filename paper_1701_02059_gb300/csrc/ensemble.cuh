@@ -161,10 +161,12 @@ public:
     // phases
     void build_grid();
     void mstep(const int* cell_of) { mstep_iter(cell_of, -1); }
-    void mstep_iter(const int* cell_of, int iter);   // iter < 0: every instance updates
+    // iter < 0: every instance updates; dmax (nullable): largest centroid move per instance
+    void mstep_iter(const int* cell_of, int iter, unsigned* dmax = nullptr);
     bool displacement_exceeds_skin();
     void launch_kinetic();
-    void estep(int* cell_out);
+    void estep(int* cell_out, float* lbound);       // grid search; lbound: second-nearest bounds
+    void estep_bounded(int* cell);                  // k-means rounds after the first (bounds in d_lbound)
     void morton_relabel();
     void finish_cells();
     void launch_pairs(bool energies, bool dump);
@@ -236,6 +238,7 @@ public:
     int *d_cell_new = nullptr, *d_perm = nullptr, *d_cell_tmp = nullptr;
     unsigned long long* d_rmax = nullptr;
     float* d_rho = nullptr;                  // [Ktot] distance to the nearest non-neighbour centroid
+    float* d_lbound = nullptr;               // [N] k-means: lower bound on the second-nearest centroid
     float4* d_cf = nullptr;                  // [Ktot] FP32 centroids by cell
     float4* d_cnorm = nullptr;               // [Ktot] cell normals (pair-kernel frames)
     unsigned char* d_grank = nullptr;        // [N] pair-kernel group ranks
