@@ -88,7 +88,7 @@ View Ensemble::view() {
     v.cq = d_cq; v.cell_start = d_cell_start; v.R = d_R; v.adj_ptr = d_adj_ptr; v.adj = d_adj; v.adj_cap = adj_cap; v.adjd = d_adjd;
     v.adjn = d_adjcount;
     v.gstart = d_gstart; v.gcent = d_gcent; v.gcf = d_gcf;
-    v.bptr = d_bptr; v.bpartner = d_bpartner; v.br0 = d_br0; v.bkb = d_bkb; v.br0_d = d_br0_d; v.bkb_d = d_bkb_d;
+    v.bptr = d_bptr; v.bpartner = d_bpartner;
     v.nbond = nbond; v.bij = d_bij; v.binst = d_binst; v.bkf = d_bkf; v.bkd = d_bkd;
     v.status = d_status;
     return v;
@@ -257,52 +257,42 @@ void Ensemble::alloc_core(const std::vector<int>& p0, const std::vector<int>& k0
 }
 
 // Bond CSR by (p0 + id), both directions; r0 and kb per entry in FP32 and FP64.
+// Bond partner lists on the device, keyed by p0 + id: counts, scan, fill,
+// then each (short) list sorted so the order does not depend on the atomics.
+__global__ void k_bond_count(int nbond, const int2* __restrict__ bij, int* __restrict__ cnt,
+                             unsigned* __restrict__ status) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nbond; q += gridDim.x * blockDim.x) {
+        const int2 e = bij[q];
+        const int ci = atomicAdd(&cnt[e.x], 1), cj = atomicAdd(&cnt[e.y], 1);
+        if (ci >= kMaxBondsPerParticle || cj >= kMaxBondsPerParticle) atomicOr(status, 1u);
+    }
+}
+
+__global__ void k_bond_fill(int nbond, const int2* __restrict__ bij, const int* __restrict__ binst,
+                            const int* __restrict__ p0, const int* __restrict__ bptr, int* __restrict__ fill,
+                            int* __restrict__ partner) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nbond; q += gridDim.x * blockDim.x) {
+        const int2 e = bij[q];
+        const int base = p0[binst[q]];
+        partner[bptr[e.x] + atomicAdd(&fill[e.x], 1)] = e.y - base;
+        partner[bptr[e.y] + atomicAdd(&fill[e.y], 1)] = e.x - base;
+    }
+}
+
+__global__ void k_bond_sort(int N, const int* __restrict__ bptr, int* __restrict__ partner) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int s = bptr[i], e = bptr[i + 1];
+    for (int x = s + 1; x < e; x++) {
+        const int t = partner[x];
+        int y = x - 1;
+        while (y >= s && partner[y] > t) { partner[y + 1] = partner[y]; y--; }
+        partner[y + 1] = t;
+    }
+}
+
 void Ensemble::upload_bonds(const std::vector<BondSpec>& bl, const std::vector<int>& p0) {
-    std::vector<int> bptr(N + 1, 0);
-    for (int b = 0; b < B; b++) {
-        const int nb = (int)bl[b].r0->size();
-        for (int q = 0; q < nb; q++) {
-            bptr[p0[b] + (*bl[b].bonds)[2 * q] + 1]++;
-            bptr[p0[b] + (*bl[b].bonds)[2 * q + 1] + 1]++;
-        }
-    }
-    for (int i = 0; i < N; i++) {
-        if (bptr[i + 1] > kMaxBondsPerParticle) throw ArgError("more than 8 bonds on one particle");
-        bptr[i + 1] += bptr[i];
-    }
-    const int nbe = bptr[N];
-    std::vector<int> part(std::max(nbe, 1));
-    std::vector<float> r0f(std::max(nbe, 1)), kbf(std::max(nbe, 1));
-    std::vector<double> r0d(std::max(nbe, 1)), kbd(std::max(nbe, 1));
-    std::vector<int> fill(N, 0);
-    for (int b = 0; b < B; b++) {
-        const int nb = (int)bl[b].r0->size();
-        for (int q = 0; q < nb; q++) {
-            const int i = (*bl[b].bonds)[2 * q], j = (*bl[b].bonds)[2 * q + 1];
-            const int gi = p0[b] + i, gj = p0[b] + j;
-            const int si = bptr[gi] + fill[gi]++, sj = bptr[gj] + fill[gj]++;
-            part[si] = j; part[sj] = i;
-            r0f[si] = r0f[sj] = (float)(*bl[b].r0)[q];
-            kbf[si] = kbf[sj] = (float)(*bl[b].kb)[q];
-            r0d[si] = r0d[sj] = (*bl[b].r0)[q];
-            kbd[si] = kbd[sj] = (*bl[b].kb)[q];
-        }
-    }
-    d_bptr = alloc<int>(N + 1);
-    d_bpartner = alloc<int>(std::max(nbe, 1));
-    d_br0 = alloc<float>(std::max(nbe, 1));
-    d_bkb = alloc<float>(std::max(nbe, 1));
-    d_br0_d = alloc<double>(std::max(nbe, 1));
-    d_bkb_d = alloc<double>(std::max(nbe, 1));
-    CK(cudaMemcpyAsync(d_bptr, bptr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, stream));
-    if (nbe > 0) {
-        CK(cudaMemcpyAsync(d_bpartner, part.data(), sizeof(int) * nbe, cudaMemcpyHostToDevice, stream));
-        CK(cudaMemcpyAsync(d_br0, r0f.data(), sizeof(float) * nbe, cudaMemcpyHostToDevice, stream));
-        CK(cudaMemcpyAsync(d_bkb, kbf.data(), sizeof(float) * nbe, cudaMemcpyHostToDevice, stream));
-        CK(cudaMemcpyAsync(d_br0_d, r0d.data(), sizeof(double) * nbe, cudaMemcpyHostToDevice, stream));
-        CK(cudaMemcpyAsync(d_bkb_d, kbd.data(), sizeof(double) * nbe, cudaMemcpyHostToDevice, stream));
-    }
-    // the same bonds once each, for the bond kernel
+    // the bonds once each (for the bond kernel), keys p0 + id
     nbond = 0;
     for (int b = 0; b < B; b++) nbond += (int)bl[b].r0->size();
     std::vector<int2> bij(std::max(nbond, 1));
@@ -329,7 +319,27 @@ void Ensemble::upload_bonds(const std::vector<BondSpec>& bl, const std::vector<i
         CK(cudaMemcpyAsync(d_bkf, bkf.data(), sizeof(float2) * nbond, cudaMemcpyHostToDevice, stream));
         CK(cudaMemcpyAsync(d_bkd, bkd.data(), sizeof(double2) * nbond, cudaMemcpyHostToDevice, stream));
     }
+    // partner lists (CSR by p0 + id) for the exclusions of the pair kernel
+    d_bptr = alloc<int>(N + 1);
+    d_bpartner = alloc<int>(std::max(2 * nbond, 1));
+    int* cnt = alloc<int>(N + 1);    // zeroed
+    int* fill = alloc<int>(N);
+    unsigned* flag = alloc<unsigned>(1);
+    if (nbond > 0) {
+        k_bond_count<<<152 * 8, 256, 0, stream>>>(nbond, d_bij, cnt, flag);
+        launches++;
+    }
+    scan_exclusive(cnt, d_bptr, N + 1);
+    if (nbond > 0) {
+        k_bond_fill<<<152 * 8, 256, 0, stream>>>(nbond, d_bij, d_binst, d_p0, d_bptr, fill, d_bpartner);
+        k_bond_sort<<<(N + 255) / 256, 256, 0, stream>>>(N, d_bptr, d_bpartner);
+        launches += 2;
+    }
+    CK(cudaGetLastError());
+    unsigned over = 0;
+    CK(cudaMemcpyAsync(&over, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));   // the host vectors die here
+    if (over) throw ArgError("more than 8 bonds on one particle");
 }
 
 void Ensemble::setup(const std::vector<const HostInstance*>& list) {

@@ -219,8 +219,6 @@ public:
     int *d_gstart = nullptr, *d_gcount = nullptr, *d_gcent = nullptr, *d_gidx = nullptr;
     float4* d_gcf = nullptr;
     int *d_bptr = nullptr, *d_bpartner = nullptr;
-    float *d_br0 = nullptr, *d_bkb = nullptr;
-    double *d_br0_d = nullptr, *d_bkb_d = nullptr;
     int nbond = 0;
     int2* d_bij = nullptr;
     int* d_binst = nullptr;

@@ -116,11 +116,7 @@ struct View {
     float4* gcf;                    // [Ktot] centroid xyz rel. to grid origin, w = id bits
     // bonds: CSR by (p0 + id)
     int* bptr;                      // [N+1]
-    int* bpartner;                  // partner id (instance-local)
-    float* br0;
-    float* bkb;
-    double* br0_d;
-    double* bkb_d;
+    int* bpartner;                  // partner id (instance-local), ascending per particle
     // bonds as a flat list (each once): ends as p0 + id, instance, constants
     int nbond;
     const int2* bij;

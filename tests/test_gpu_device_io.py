@@ -83,3 +83,18 @@ def test_lazy_setup_keeps_the_trajectory():
         assert np.array_equal(st5[k], st5b[k]), k
     assert st5b["step"] == 5
     g.close()
+
+
+def test_too_many_bonds_on_one_particle_is_rejected():
+    """A particle with more than 8 bonds is refused when the device lists are
+    built (the first call that needs the device), with ORBC_E_ARG."""
+    mem = M.flat_patch_2304()
+    g = G.System(params(mem))
+    g.set_particles(mem.pos, mem.vel, mem.ori, mem.angvel, mem.type, mem.id)
+    hub = 0
+    ij = np.array([[hub, j] for j in range(1, 11)], np.int32)
+    g.set_bonds(ij, np.ones(len(ij)), np.ones(len(ij)))
+    with pytest.raises(G.OrbcError) as e:
+        g.init_cells()
+    assert e.value.code == -1
+    g.close()
