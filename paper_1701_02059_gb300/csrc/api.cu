@@ -4,7 +4,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <exception>
+#include <memory>
 #include <mutex>
 #include <numeric>
 #include <thread>
@@ -375,12 +377,12 @@ void Ensemble::setup(const std::vector<const HostInstance*>& list) {
     std::vector<unsigned char> ty(N);
     std::vector<unsigned> ids(N);
     std::vector<int> slot(N);
-    const std::vector<long long> HostInstance::*fields[4] = {&HostInstance::xq, &HostInstance::vq, &HostInstance::nq,
-                                                               &HostInstance::wq};
+    const GridVec HostInstance::*fields[4] = {&HostInstance::xq, &HostInstance::vq, &HostInstance::nq,
+                                              &HostInstance::wq};
     for (int q = 0; q < 4; q++) {
         for (int b = 0; b < B; b++) {
             const HostInstance& h = *list[b];
-            const std::vector<long long>& src = h.*fields[q];
+            const GridVec& src = h.*fields[q];
             const int pb = p0[b];
             parallel_for(h.n, [&](long long i0, long long i1) {
                 for (long long i = i0; i < i1; i++)
@@ -843,15 +845,22 @@ HostInstance orbc::host_instance(const Params& prm, int n, const double* pos, co
     HostInstance h;
     h.prm = prm;
     h.n = n;
-    h.xq.resize((size_t)3 * n); h.vq.resize((size_t)3 * n); h.nq.assign((size_t)3 * n, 0); h.wq.assign((size_t)3 * n, 0);
+    // sized without zero-filling: every entry is written below
+    h.xq.resize((size_t)3 * n); h.vq.resize((size_t)3 * n); h.nq.resize((size_t)3 * n); h.wq.resize((size_t)3 * n);
     h.type.assign(type, type + n);
     h.id.assign(id, id + n);
-    std::vector<char> seen(n, 0);
-    for (int i = 0; i < n; i++) {
-        if (id[i] >= (unsigned)n || seen[id[i]]) throw ArgError("ids must be a permutation of 0..n-1");
-        seen[id[i]] = 1;
-        if (type[i] > 2) throw ArgError("unknown particle type");
-    }
+    // ids a permutation of 0..n-1 (each marked once), types known
+    std::unique_ptr<std::atomic<unsigned char>[]> seen(new std::atomic<unsigned char>[n]);
+    parallel_for(n, [&](long long i0, long long i1) {
+        for (long long i = i0; i < i1; i++) seen[i].store(0, std::memory_order_relaxed);
+    });
+    parallel_for(n, [&](long long i0, long long i1) {
+        for (long long i = i0; i < i1; i++) {
+            if (id[i] >= (unsigned)n || seen[id[i]].exchange(1, std::memory_order_relaxed))
+                throw ArgError("ids must be a permutation of 0..n-1");
+            if (type[i] > 2) throw ArgError("unknown particle type");
+        }
+    });
     parallel_for(n, [&](long long i0, long long i1) {
         for (long long i = i0; i < i1; i++) {
             for (int a = 0; a < 3; a++) {
@@ -873,6 +882,8 @@ HostInstance orbc::host_instance(const Params& prm, int n, const double* pos, co
                     h.nq[(size_t)3 * i + a] = llrint(o[a] * kGrid);
                     h.wq[(size_t)3 * i + a] = llrint(w[a] * kGrid);
                 }
+            } else {
+                for (int a = 0; a < 3; a++) { h.nq[(size_t)3 * i + a] = 0; h.wq[(size_t)3 * i + a] = 0; }
             }
         }
     });

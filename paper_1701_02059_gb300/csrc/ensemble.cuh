@@ -47,10 +47,26 @@ struct Params {
 };
 
 // One instance as given by the caller (host memory, id order not required).
+// Allocator that leaves scalars uninitialised on resize: large host arrays
+// that are filled right after they are sized.
+template <typename T>
+struct NoInitAlloc : std::allocator<T> {
+    template <typename U>
+    struct rebind { using other = NoInitAlloc<U>; };
+    NoInitAlloc() = default;
+    template <typename U>
+    NoInitAlloc(const NoInitAlloc<U>&) {}
+    template <typename U>
+    void construct(U* p) noexcept { ::new ((void*)p) U; }
+    template <typename U, typename... A>
+    void construct(U* p, A&&... a) { ::new ((void*)p) U(std::forward<A>(a)...); }
+};
+using GridVec = std::vector<long long, NoInitAlloc<long long>>;
+
 struct HostInstance {
     Params prm;
     int n = 0;
-    std::vector<long long> xq, vq, nq, wq;   // [n][3] on the 2^-40 grid
+    GridVec xq, vq, nq, wq;                  // [n][3] on the 2^-40 grid
     std::vector<unsigned char> type;
     std::vector<unsigned> id;
     std::vector<int> bonds;                  // [nb][2] ids
