@@ -21,9 +21,9 @@ HostInstance host_instance(const Params& prm, int n, const double* pos, const do
 void host_bonds(HostInstance& h, int nb, const int* ij, const double* r0, const double* kb);
 // Device status flags to an orbc_status.
 int status_code(unsigned st);
-// Runs f(begin, end) over chunks of [0, n) on up to 16 host threads; the
-// first exception a chunk throws is rethrown here.
-void parallel_for(long long n, const std::function<void(long long, long long)>& f);
+// Runs f(begin, end) over chunks of [0, n) (at least grain items each) on up
+// to 16 host threads; the first exception a chunk throws is rethrown here.
+void parallel_for(long long n, const std::function<void(long long, long long)>& f, long long grain = 65536);
 
 // Runs f, turning exceptions into status codes and recording the message.
 template <typename F>

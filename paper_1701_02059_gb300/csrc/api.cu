@@ -259,6 +259,13 @@ void Ensemble::alloc_core(const std::vector<int>& p0, const std::vector<int>& k0
 }
 
 // Bond CSR by (p0 + id), both directions; r0 and kb per entry in FP32 and FP64.
+// [n][3] to axis-major [3][n].
+__global__ void k_aos_to_soa(const long long* __restrict__ aos, int n, long long* __restrict__ soa) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int a = 0; a < 3; a++) soa[(size_t)a * n + i] = aos[(size_t)3 * i + a];
+}
+
 // Bond partner lists on the device, keyed by p0 + id: counts, scan, fill,
 // then each (short) list sorted so the order does not depend on the atomics.
 __global__ void k_bond_count(int nbond, const int2* __restrict__ bij, int* __restrict__ cnt,
@@ -372,25 +379,27 @@ void Ensemble::setup(const std::vector<const HostInstance*>& list) {
     for (const HostInstance* hp : list) any_skin |= (hp->prm.rebuild_every > 1);
     alloc_core(p0, k0, any_skin);
 
-    // state, axis-major
-    std::vector<long long> ax((size_t)3 * N);
+    // state: the host's [n][3] arrays are copied as they are and made
+    // axis-major on the device
     std::vector<unsigned char> ty(N);
     std::vector<unsigned> ids(N);
     std::vector<int> slot(N);
     const GridVec HostInstance::*fields[4] = {&HostInstance::xq, &HostInstance::vq, &HostInstance::nq,
                                               &HostInstance::wq};
-    for (int q = 0; q < 4; q++) {
-        for (int b = 0; b < B; b++) {
-            const HostInstance& h = *list[b];
-            const GridVec& src = h.*fields[q];
-            const int pb = p0[b];
-            parallel_for(h.n, [&](long long i0, long long i1) {
-                for (long long i = i0; i < i1; i++)
-                    for (int a = 0; a < 3; a++) ax[(size_t)a * N + pb + i] = src[(size_t)3 * i + a];
-            });
+    {
+        long long* aos = nullptr;
+        CK(cudaMallocAsync(&aos, sizeof(long long) * 3 * (size_t)N, stream));
+        for (int q = 0; q < 4; q++) {
+            for (int b = 0; b < B; b++) {
+                const GridVec& src = (*list[b]).*fields[q];
+                CK(cudaMemcpyAsync(aos + (size_t)3 * p0[b], src.data(), sizeof(long long) * 3 * (size_t)list[b]->n,
+                                   cudaMemcpyHostToDevice, stream));
+            }
+            k_aos_to_soa<<<(N + 255) / 256, 256, 0, stream>>>(aos, N, d_state[0][q]);
+            launches++;
         }
-        CK(cudaMemcpyAsync(d_state[0][q], ax.data(), sizeof(long long) * 3 * N, cudaMemcpyHostToDevice, stream));
-        CK(cudaStreamSynchronize(stream));
+        CK(cudaGetLastError());
+        CK(cudaFreeAsync(aos, stream));
     }
     for (int b = 0; b < B; b++) {
         const HostInstance& h = *list[b];
@@ -425,11 +434,27 @@ void Ensemble::setup(const std::vector<const HostInstance*>& list) {
         } else {
             // lipids in id order, centroid k = lipid floor(k N_L / K)
             std::vector<int> by_id(h.n);
-            for (int i = 0; i < h.n; i++) by_id[h.id[i]] = i;
-            std::vector<int> lip;
-            lip.reserve(h.n);
-            for (int idv = 0; idv < h.n; idv++)
-                if (h.type[by_id[idv]] == kLipid) lip.push_back(by_id[idv]);
+            parallel_for(h.n, [&](long long i0, long long i1) {
+                for (long long i = i0; i < i1; i++) by_id[h.id[i]] = (int)i;
+            });
+            // the lipid slots in id order: counts per chunk of ids, then fill
+            const int nch = 64;
+            const long long per = ((long long)h.n + nch - 1) / nch;
+            std::vector<long long> cnt(nch + 1, 0);
+            parallel_for(nch, [&](long long c0, long long c1) {
+                for (long long ch = c0; ch < c1; ch++)
+                    for (long long idv = ch * per; idv < std::min<long long>(h.n, (ch + 1) * per); idv++)
+                        cnt[ch + 1] += h.type[by_id[idv]] == kLipid;
+            }, 1);
+            for (int ch = 0; ch < nch; ch++) cnt[ch + 1] += cnt[ch];
+            std::vector<int> lip((size_t)cnt[nch]);
+            parallel_for(nch, [&](long long c0, long long c1) {
+                for (long long ch = c0; ch < c1; ch++) {
+                    long long o = cnt[ch];
+                    for (long long idv = ch * per; idv < std::min<long long>(h.n, (ch + 1) * per); idv++)
+                        if (h.type[by_id[idv]] == kLipid) lip[(size_t)o++] = by_id[idv];
+                }
+            }, 1);
             if ((int)lip.size() < K) throw ArgError("more centroids than lipids");
             for (int k = 0; k < K; k++) {
                 int s = lip[(size_t)((long long)k * (long long)lip.size() / K)];
@@ -818,9 +843,10 @@ void orbc::check_params(const Params& P) {
 }
 
 
-void orbc::parallel_for(long long n, const std::function<void(long long, long long)>& f) {
+void orbc::parallel_for(long long n, const std::function<void(long long, long long)>& f, long long grain) {
     if (n <= 0) return;
-    const long long nt = std::min<long long>({16, std::max(1u, std::thread::hardware_concurrency()), (n + 65535) / 65536});
+    grain = std::max(1ll, grain);
+    const long long nt = std::min<long long>({16, std::max(1u, std::thread::hardware_concurrency()), (n + grain - 1) / grain});
     if (nt <= 1) { f(0, n); return; }
     std::vector<std::thread> th;
     std::vector<std::exception_ptr> err((size_t)nt);
