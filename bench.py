@@ -349,7 +349,7 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-KERNEL_REV = "pairs-v11"
+KERNEL_REV = "pairs-v12"
 
 
 def ensemble_jobs(n_instances: int, steps: int):
