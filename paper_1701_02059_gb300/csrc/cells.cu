@@ -740,14 +740,12 @@ __global__ void __launch_bounds__(256) k_estep_bound(View v, const int* __restri
 __global__ void k_cand_rows(const int* __restrict__ cnt_old, int Ktot, const int* __restrict__ pad_old,
                             const int* __restrict__ new_of_old, const float4* __restrict__ cf,
                             float4* __restrict__ rows) {
-    const long long n = (long long)Ktot * kAdjRow;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        if ((int)(q % kAdjRow) >= cnt_old[q / kAdjRow]) continue;
-        const int j = new_of_old[pad_old[q]];
-        float4 c = cf[j];
-        c.w = __int_as_float(j);
-        rows[q] = c;
-    }
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // one thread per row slot
+    if (q >= (long long)Ktot * kAdjRow || (int)(q % kAdjRow) >= cnt_old[q / kAdjRow]) return;
+    const int j = new_of_old[pad_old[q]];
+    float4 c = cf[j];
+    c.w = __int_as_float(j);
+    rows[q] = c;
 }
 
 // Rebuild E-step from the previous cell list (the paper's guess from the
@@ -1494,7 +1492,8 @@ void Ensemble::finish_cells() {
     build_grid();
     if (prev_adj_valid_) {
         CK(cudaMemsetAsync(d_fbcount, 0, sizeof(int), stream));
-        k_cand_rows<<<152 * 8, 256, 0, stream>>>(d_adjcount, Ktot, d_adjpad, d_new_of_old, d_cf, d_candrows);
+        k_cand_rows<<<nblk((long long)Ktot * kAdjRow, 256), 256, 0, stream>>>(d_adjcount, Ktot, d_adjpad, d_new_of_old, d_cf,
+                                                                          d_candrows);
         k_estep_rows<<<nblk(N, 128), 128, 0, stream>>>(v, d_cell, d_adjcount, d_candrows, d_rho, d_new_of_old, d_dmax,
                                                       d_cell_new, d_cell_tmp, d_fbcount);
         k_estep_list<<<152 * 4, 128, 0, stream>>>(v, d_cell_tmp, d_fbcount, d_cell_new);
