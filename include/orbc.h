@@ -125,16 +125,23 @@ ORBC_API int orbc_create(const orbc_params* params, void* cuda_stream, orbc_syst
  * system's particles with their types).  pos, vel: [n][3]; ori, angvel:
  * [n][3], read for lipids only (ori must be unit, angvel is projected
  * perpendicular to it); type: [n] (ORBC_LIPID/JUNCTION/SPECTRIN); id: [n],
- * a permutation of 0..n-1.  Invalidates cells and forces.
+ * a permutation of 0..n-1.  The arrays are validated and copied on the host;
+ * the device set-up (allocation, upload, bond lists) runs at the first call
+ * that needs the device, which then reports its errors (ORBC_E_NOMEM,
+ * ORBC_E_CUDA, and the bond limit of orbc_set_bonds as ORBC_E_ARG).
+ * Invalidates cells and forces.
  * Errors: ORBC_E_ARG (null pointer, n < 1, non-finite value, |x| >= 4096
- * sigma, unknown type, ids not a permutation), ORBC_E_NOMEM, ORBC_E_CUDA. */
+ * sigma, unknown type, ids not a permutation), ORBC_E_NOMEM. */
 ORBC_API int orbc_set_particles(orbc_system* s, int n, const double* pos, const double* vel, const double* ori,
                        const double* angvel, const unsigned char* type, const unsigned* id);
 
 /* Harmonic bonds 1/2 kb (r - r0)^2 between particle ids ("Force
  * Evaluation": a list of bonds between proteins is maintained).  ij: [nb][2]
- * ids; r0, kb: [nb].  At most 8 bonds per particle.  Call after
- * orbc_set_particles.  Errors: ORBC_E_ARG, ORBC_E_STATE, ORBC_E_NOMEM. */
+ * ids; r0, kb: [nb].  At most 8 bonds per particle (checked when the device
+ * lists are built, see orbc_set_particles).  Call after orbc_set_particles;
+ * after steps the stepped state is kept.  Errors: ORBC_E_ARG (ids out of
+ * range, a particle bonded to itself, negative or non-finite constants),
+ * ORBC_E_STATE (no particles), ORBC_E_NOMEM. */
 ORBC_API int orbc_set_bonds(orbc_system* s, int nb, const int* ij, const double* r0, const double* kb);
 
 /* Initial k-means clustering ("Spatial Searching Algorithm"): centroids
