@@ -241,6 +241,7 @@ void Ensemble::alloc_core(const std::vector<int>& p0, const std::vector<int>& k0
     d_rmax = alloc<unsigned long long>(B);
     d_rho = alloc<float>(Ktot);
     d_lbound = alloc<float>(N);
+    d_cmove = alloc<float>(Ktot);
     d_cf = alloc<float4>(Ktot);
     d_cnorm = alloc<float4>(Ktot);
     d_grank = alloc<unsigned char>(N);
@@ -502,6 +503,7 @@ void Ensemble::setup(const std::vector<const HostInstance*>& list) {
         Gtot += (long long)I.gdim[0] * I.gdim[1] * I.gdim[2];
     }
     d_gstart = alloc<int>(Gtot + 1);
+    d_gmove = alloc<unsigned>(Gtot);
     d_gcount = alloc<int>(Gtot + 1);
     CK(cudaMemcpyAsync(d_cq, c0.data(), sizeof(long long) * 3 * Ktot, cudaMemcpyHostToDevice, stream));
     CK(cudaMemcpyAsync(d_inst, inst_h.data(), sizeof(Inst) * B, cudaMemcpyHostToDevice, stream));

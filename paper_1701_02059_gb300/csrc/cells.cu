@@ -60,7 +60,7 @@ __global__ void k_mstep_accum(View v, const int* __restrict__ cell_of, long long
 // dmax (nullable): the largest move of an instance's centroids, as FP32 bits
 // rounded up (warp-reduced before the atomics).
 __global__ void k_mstep_finish(View v, long long* __restrict__ S, int* __restrict__ cnt, int iter,
-                               unsigned* __restrict__ dmax) {
+                               unsigned* __restrict__ dmax, float* __restrict__ cmove) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= v.Ktot) return;
     int b = find_inst(v.inst_k0, v.B, k);
@@ -79,6 +79,7 @@ __global__ void k_mstep_finish(View v, long long* __restrict__ S, int* __restric
         S[(size_t)a * v.Ktot + k] = 0;
     }
     cnt[k] = 0;
+    if (cmove) cmove[k] = sqrtf(mv2) * 1.0001f + 1e-6f;
     if (dmax) {
         const unsigned grp = __match_any_sync(__activemask(), b);
         const unsigned mv = __reduce_max_sync(grp, __float_as_uint(sqrtf(mv2) * 1.0001f + 1e-6f));
@@ -699,14 +700,26 @@ __global__ void k_estep_list(View v, const int* __restrict__ fb_list, const int*
         estep_one(v, fb_list[q], cell_out, lbound);
 }
 
+// Largest move of the centroids now in each grid cell (FP32 bits:
+// non-negative floats order like their bit patterns).
+__global__ void k_grid_move(View v, const int* __restrict__ gidx, const float* __restrict__ cmove,
+                            unsigned* __restrict__ gmove) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < v.Ktot) atomicMax(&gmove[gidx[k]], __float_as_uint(cmove[k]));
+}
+
 // k-means E-step after the first round (Hamerly's bound): the particle's
 // centroid of the previous round is still its nearest when the distance to
 // it is below the previous lower bound on every other centroid, less the
 // largest move of the M-step in between (FP32 with a margin); the bound is
-// carried on, the others are listed for the grid search.
+// carried on, the others are listed for the grid search.  When the bound is
+// below the grid edge, every centroid that could now be nearer lies in the
+// 27 grid cells around the particle, and the largest move among those
+// replaces the instance's largest move.
 __global__ void __launch_bounds__(256) k_estep_bound(View v, const int* __restrict__ cell, float* __restrict__ lbound,
                                                      const float4* __restrict__ cf, const unsigned* __restrict__ dmax,
-                                                     int* __restrict__ list, int* __restrict__ count) {
+                                                     const unsigned* __restrict__ gmove, int* __restrict__ list,
+                                                     int* __restrict__ count) {
     __shared__ int wcount[8], wbase[8], bbase;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -715,10 +728,25 @@ __global__ void __launch_bounds__(256) k_estep_bound(View v, const int* __restri
         const int b = find_inst(v.inst_p0, v.B, i);
         const Inst& I = v.inst[b];
         float p[3];
-        for (int a = 0; a < 3; a++) grid_coord(v.xq[(size_t)a * v.N + i], I, a, p[a]);
+        int g[3];
+        for (int a = 0; a < 3; a++) g[a] = grid_coord(v.xq[(size_t)a * v.N + i], I, a, p[a]);
         const float4 c = cf[cell[i]];
         const float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1), dz = axis_dist(p[2], c.z, I, 2);
-        const float l = lbound[i] - __uint_as_float(dmax[b]);
+        const float l0 = lbound[i];
+        float dm = __uint_as_float(dmax[b]);
+        if (gmove && l0 <= fminf(I.gh[0], fminf(I.gh[1], I.gh[2]))) {
+            unsigned m = 0;
+            for (int zz = -1; zz <= 1; zz++)
+                for (int yy = -1; yy <= 1; yy++)
+                    for (int xx = -1; xx <= 1; xx++) {
+                        int w[3] = {g[0] + xx, g[1] + yy, g[2] + zz};
+                        for (int a = 0; a < 3; a++)
+                            w[a] = I.periodic[a] ? wrap_idx(w[a], I.gdim[a]) : min(max(w[a], 0), I.gdim[a] - 1);
+                        m = max(m, gmove[I.g0 + ((long long)w[2] * I.gdim[1] + w[1]) * I.gdim[0] + w[0]]);
+                    }
+            dm = __uint_as_float(m);
+        }
+        const float l = l0 - dm;
         if (sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + kCertMargin < l) lbound[i] = l;
         else need = true;
     }
@@ -1410,7 +1438,7 @@ void Ensemble::mstep_iter(const int* cell_of, int iter, unsigned* dmax) {
     launches++;
     CK(cudaGetLastError());
     if (dmax) CK(cudaMemsetAsync(dmax, 0, sizeof(unsigned) * B, stream));
-    k_mstep_finish<<<nblk(Ktot, 256), 256, 0, stream>>>(v, d_S, d_cnt, iter, dmax);
+    k_mstep_finish<<<nblk(Ktot, 256), 256, 0, stream>>>(v, d_S, d_cnt, iter, dmax, dmax ? d_cmove : nullptr);
     launches++;
     CK(cudaGetLastError());
 }
@@ -1458,7 +1486,10 @@ void Ensemble::estep(int* cell_out, float* lbound) {
 
 void Ensemble::estep_bounded(int* cell) {
     CK(cudaMemsetAsync(d_fbcount, 0, sizeof(int), stream));
-    k_estep_bound<<<nblk(N, 256), 256, 0, stream>>>(view(), cell, d_lbound, d_cf, d_dmax, d_cell_tmp, d_fbcount);
+    CK(cudaMemsetAsync(d_gmove, 0, sizeof(unsigned) * Gtot, stream));
+    k_grid_move<<<nblk(Ktot, 256), 256, 0, stream>>>(view(), d_gidx, d_cmove, d_gmove);
+    k_estep_bound<<<nblk(N, 256), 256, 0, stream>>>(view(), cell, d_lbound, d_cf, d_dmax, d_gmove, d_cell_tmp,
+                                                    d_fbcount);
     k_estep_warp<<<nblk(N, 128), 128, 0, stream>>>(view(), cell, d_lbound, d_cell_tmp, d_fbcount);
     launches += 2;
     CK(cudaGetLastError());

@@ -252,7 +252,9 @@ public:
     int *d_cell_new = nullptr, *d_perm = nullptr, *d_cell_tmp = nullptr;
     unsigned long long* d_rmax = nullptr;
     float* d_rho = nullptr;                  // [Ktot] distance to the nearest non-neighbour centroid
-    float* d_lbound = nullptr;               // [N] k-means: lower bound on the second-nearest centroid
+    float* d_lbound = nullptr;
+    float* d_cmove = nullptr;                // [Ktot] k-means: move of each centroid in the last M-step
+    unsigned* d_gmove = nullptr;             // [Gtot] k-means: largest move of the centroids in a grid cell               // [N] k-means: lower bound on the second-nearest centroid
     float4* d_cf = nullptr;                  // [Ktot] FP32 centroids by cell
     float4* d_cnorm = nullptr;               // [Ktot] cell normals (pair-kernel frames)
     unsigned char* d_grank = nullptr;        // [N] pair-kernel group ranks
