@@ -138,9 +138,19 @@ class System:
         self._check(self._L.orbc_integrate(self._h, int(nsteps)), "orbc_integrate")
 
     # -------------------------------------------------------------- getters
-    def state(self):
+    def state(self, out=None):
+        """orbc_get_state: positions, velocities, directors and angular
+        velocities in id order. ``out`` (optional) maps those four names to
+        caller-owned C-contiguous float64 [n, 3] arrays (pinned memory makes
+        the copy run at the link's full rate); they are filled and returned."""
         n = self.n
-        pos, vel, ori, w = (np.zeros((n, 3)) for _ in range(4))
+        if out is None:
+            pos, vel, ori, w = (np.empty((n, 3)) for _ in range(4))
+        else:
+            pos, vel, ori, w = (out[k] for k in ("pos", "vel", "ori", "angvel"))
+            for a in (pos, vel, ori, w):
+                if a.dtype != np.float64 or a.shape != (n, 3) or not a.flags.c_contiguous or not a.flags.writeable:
+                    raise ValueError("state(out=...) wants writeable C-contiguous float64 [n, 3] arrays")
         step = C.c_longlong(0)
         self._check(self._L.orbc_get_state(self._h, _p(pos), _p(vel), _p(ori), _p(w), C.byref(step)), "orbc_get_state")
         return {"pos": pos, "vel": vel, "ori": ori, "angvel": w, "step": step.value}

@@ -98,3 +98,36 @@ def test_too_many_bonds_on_one_particle_is_rejected():
         g.init_cells()
     assert e.value.code == -1
     g.close()
+
+
+def test_pinned_host_buffers_match_pageable():
+    """Page-locked inputs and caller-owned page-locked outputs give the same
+    trajectory and state as ordinary numpy arrays."""
+    import dataclasses
+    mem = M.flat_patch_2304()
+
+    def pinned(a):
+        a = np.ascontiguousarray(a)
+        buf = torch.empty(max(a.nbytes, 1), dtype=torch.uint8, pin_memory=True).numpy()
+        out = buf[:a.nbytes].view(a.dtype).reshape(a.shape)
+        out[...] = a
+        return out
+
+    pm = dataclasses.replace(mem, **{k: pinned(getattr(mem, k))
+                                     for k in ("pos", "vel", "ori", "angvel", "type", "id", "bonds", "r0", "kb")})
+    out = {k: pinned(np.full((mem.n, 3), np.nan)) for k in ("pos", "vel", "ori", "angvel")}
+    a, b = G.System(params(mem)), G.System(params(mem))
+    a.load_membrane(mem)
+    b.load_membrane(pm)
+    for g in (a, b):
+        g.init_cells()
+        g.integrate(10)
+    sa, sb = a.state(), b.state(out=out)
+    assert sb["step"] == sa["step"] == 10
+    for k in ("pos", "vel", "ori", "angvel"):
+        assert sb[k] is out[k]
+        assert np.array_equal(sa[k], out[k]), k
+    with pytest.raises(ValueError):
+        b.state(out={k: np.empty((mem.n, 3), np.float32) for k in out})
+    a.close()
+    b.close()
