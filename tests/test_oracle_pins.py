@@ -477,6 +477,47 @@ def test_langevin_equipartition():
     assert np.mean(kr) == pytest.approx(0.2, rel=0.06)
 
 
+def _rodrigues(n, axis, theta):
+    u = unit(axis)
+    return n * math.cos(theta) + np.cross(u, n) * math.sin(theta) + u * np.dot(u, n) * (1.0 - math.cos(theta))
+
+
+def test_free_lipids_drift_and_rotate_in_closed_form():
+    """Two lipids farther apart than the cutoff, kT = 0 and no friction: no
+    force, torque or noise acts, so each step moves x by dt v and turns n
+    about omega (right-handed, dn/dt = omega x n) through twice the angle
+    of one half-step Cayley map with a = (dt/2) omega / 2, i.e. by
+    4 atan(dt |omega| / 4); v and omega stay constant."""
+    d = [unit([0.0, 0.0, 1.0]), unit([1.0, 2.0, -0.5])]
+    w = [np.array([1.5, -0.7, 0.0]), 0.0 * d[1]]
+    w[1] = np.cross(d[1], unit([0.3, -1.0, 2.0])) * 2.2          # perpendicular to its director
+    mem = M.Membrane(pos=np.array([[0.0, 0.0, 0.0], [9.0, -4.0, 3.0]]), vel=np.array([[0.3, -0.2, 0.1], [-0.4, 0.0, 0.25]]),
+                     ori=np.array(d), angvel=np.array(w), type=np.zeros(2, np.uint8), id=np.array([0, 1], np.uint32),
+                     bonds=np.zeros((0, 2), np.int32), r0=np.zeros(0), kb=np.zeros(0),
+                     box=np.array([100.0, 100.0, 100.0]), periodic=np.zeros(3, np.int32), n_centroids=2, kT=0.0)
+    dt, steps = 0.01, 60
+    _, s = make_sys(mem, dt=dt, kT=0.0, gamma_t=0.0, gamma_r=0.0)
+    s.init_cells()
+    s0 = s.state()
+    e = s.compute_forces()
+    assert e[0] == 0.0 and e[1] == 0.0          # no pair or bond energy: nothing in range
+    s.integrate(steps)
+    st = s.state()
+    assert st["step"] == steps
+    assert np.abs(st["pos"] - (s0["pos"] + steps * dt * s0["vel"])).max() < 1e-12
+    assert np.abs(st["vel"] - s0["vel"]).max() < 1e-15
+    for i in range(2):
+        om = s0["angvel"][i]
+        theta = steps * 4.0 * math.atan(dt * np.linalg.norm(om) / 4.0)
+        expect = _rodrigues(unit(s0["ori"][i]), om, theta)
+        assert np.abs(st["ori"][i] - expect).max() < 1e-10, i
+        assert np.abs(st["angvel"][i] - om).max() < 1e-10, i
+    # the turn is not the small-angle one: the Cayley angle differs from |omega| t
+    om = s0["angvel"][0]
+    naive = _rodrigues(unit(s0["ori"][0]), om, steps * dt * np.linalg.norm(om))
+    assert np.abs(st["ori"][0] - naive).max() > 1e-8
+
+
 def test_directors_stay_unit_and_angular_velocity_perpendicular():
     mem = tiny_patch()
     _, s = make_sys(mem)
