@@ -518,6 +518,37 @@ def test_free_lipids_drift_and_rotate_in_closed_form():
     assert np.abs(st["ori"][0] - naive).max() > 1e-8
 
 
+def test_free_lipids_relax_at_the_friction_rate():
+    """kT = 0 with friction: the O step multiplies v by exp(-gamma_t dt) and
+    omega by exp(-gamma_r dt) once per step, so v and omega decay as
+    exp(-gamma t); x gains (dt/2)(v_j + v_j+1) and n turns through the two
+    half-step Cayley angles of omega before and after that step's O."""
+    dn = unit([0.2, -0.4, 1.0])
+    om0 = np.cross(dn, unit([1.0, 0.5, 0.0])) * 1.8
+    mem = M.Membrane(pos=np.array([[1.0, 2.0, -3.0]]), vel=np.array([[0.5, -0.25, 0.75]]), ori=dn[None, :],
+                     angvel=om0[None, :], type=np.zeros(1, np.uint8), id=np.array([0], np.uint32),
+                     bonds=np.zeros((0, 2), np.int32), r0=np.zeros(0), kb=np.zeros(0),
+                     box=np.array([100.0, 100.0, 100.0]), periodic=np.zeros(3, np.int32), n_centroids=1, kT=0.0)
+    dt, steps, gt, gr = 0.01, 40, 1.5, 4.0
+    _, s = make_sys(mem, dt=dt, kT=0.0, gamma_t=gt, gamma_r=gr)
+    s.init_cells()
+    s0 = s.state()
+    s.integrate(steps)
+    st = s.state()
+    ct, cr = math.exp(-gt * dt), math.exp(-gr * dt)
+    v0, w0 = s0["vel"][0], s0["angvel"][0]
+    assert np.abs(st["vel"][0] - ct ** steps * v0).max() < 1e-13
+    assert np.abs(st["angvel"][0] - cr ** steps * w0).max() < 1e-10
+    x = s0["pos"][0] + 0.5 * dt * sum(ct ** j + ct ** (j + 1) for j in range(steps)) * v0
+    assert np.abs(st["pos"][0] - x).max() < 1e-12
+    wn = np.linalg.norm(w0)
+    theta = sum(2.0 * math.atan(0.25 * dt * wn * cr ** j) + 2.0 * math.atan(0.25 * dt * wn * cr ** (j + 1))
+                for j in range(steps))
+    assert np.abs(st["ori"][0] - _rodrigues(unit(s0["ori"][0]), w0, theta)).max() < 1e-10
+    # exp(-gamma dt / 2) per step would leave v visibly larger
+    assert np.abs(st["vel"][0] - math.exp(-0.5 * gt * dt) ** steps * v0).max() > 1e-3
+
+
 def test_directors_stay_unit_and_angular_velocity_perpendicular():
     mem = tiny_patch()
     _, s = make_sys(mem)
