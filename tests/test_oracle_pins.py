@@ -288,6 +288,30 @@ def test_system_forces_finite_difference():
             assert fd == pytest.approx(T[i, k], abs=1e-5 * (1 + abs(T[i, k])))
 
 
+def test_virial_is_minus_the_dilation_derivative():
+    """Under x -> lambda x with the directors held, dU/dlambda at 1 is
+    sum_i x_i . grad_i U = -sum_i x_i . F_i, so the reported virial W (pairs
+    and bonds) equals minus the central difference of U in lambda."""
+    mem = tiny_vesicle(n_lipids=300, f=1, beads=2)
+    m, s = make_sys(mem)
+    s.init_cells()
+    e = s.compute_forces()
+    st = s.state()
+
+    def energy(lam):
+        t = oracle.OracleSystem(m, s.r)
+        t.set_particles(lam * st["pos"], mem.vel, st["ori"], mem.angvel, mem.type, mem.id)
+        t.set_bonds(mem.bonds, mem.r0, mem.kb)
+        t.init_cells()
+        u = t.compute_forces()
+        return u[0] + u[1]
+
+    h = 1e-6
+    w_fd = -(energy(1.0 + h) - energy(1.0 - h)) / (2 * h)
+    assert abs(e[4]) > 1.0
+    assert w_fd == pytest.approx(e[4], rel=1e-5, abs=1e-6)
+
+
 # --------------------------------------------------------------------------- Voronoi cells
 
 def _random_points(rng, n, L):
