@@ -72,32 +72,52 @@ def oracle_params(mem, oracle):
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock and throttle reasons during the timed
+    region. ``start`` returns once the sampler has produced its first row, so
+    it is already running when the region opens; ``region`` brackets the
+    region in host time; the summary takes the rows that arrived inside it
+    (with the rows just before and after for the throttle reasons)."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, exe: str = "nvidia-smi"):
         self.gpu = gpu_index
-        self.rows = []
+        self.exe = exe
+        self.rows = []          # (host time of arrival, fields)
         self.proc = None
+        self.t0 = self.t1 = None
 
-    def start(self):
+    def start(self, wait_s: float = 5.0):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+            self.proc = subprocess.Popen([self.exe, f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
             self.proc = None
+            return
+        t = time.perf_counter()
+        while not self.rows and self.proc.poll() is None and time.perf_counter() - t < wait_s:
+            time.sleep(0.005)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([t.strip() for t in line.split(",")])
+            self.rows.append((time.perf_counter(), [t.strip() for t in line.split(",")]))
+
+    def region(self, begin: bool):
+        if begin:
+            self.t0 = time.perf_counter()
+        else:
+            self.t1 = time.perf_counter()
 
     def stop(self):
         if self.proc:
+            # one more interval so that a row taken at the region's end arrives
+            time.sleep(self.INTERVAL_MS * 1.5e-3)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -105,18 +125,26 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        if not self.rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = sorted(float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit())
-        mx = max((float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()), default=None)
+        rows = list(self.rows)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        t0 = self.t0 if self.t0 is not None else rows[0][0]
+        t1 = self.t1 if self.t1 is not None else rows[-1][0]
+        inside = [r for t, r in rows if t0 <= t <= t1]
+        before = [r for t, r in rows if t < t0][-1:]
+        after = [r for t, r in rows if t > t1][:1]
+        # a region shorter than the sampling interval: the nearest row after it
+        use = inside or after or before
+        num = lambda x: x.replace(".", "").isdigit()
+        sm = sorted(float(r[1]) for r in use if len(r) > 1 and num(r[1]))
+        mx = max((float(r[2]) for r in use if len(r) > 2 and num(r[2])), default=None)
         reasons = set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
-            for q, nm in enumerate(names):
+        for r in before + inside + after:
+            for q, nm in enumerate(self.REASONS):
                 if len(r) > 5 + q and r[5 + q].lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(self.rows)}
+                "samples": len(inside), "interval_ms": self.INTERVAL_MS}
 
 
 def peaks():
@@ -191,17 +219,19 @@ def run_ours(args, rank, world):
     # per-kernel timing (CUDA events recorded by the library on its stream)
     g.set_timing(True)
     clocks = ClockSampler(dev)
+    clocks.start()              # running before the ranks meet at the barrier
     launches0 = g.launch_count()
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks.start()
+    clocks.region(True)
     ev0.record(stream)
     g.integrate(args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
+    clocks.region(False)
     clocks.stop()
     ms = ev0.elapsed_time(ev1)
     launches = g.launch_count() - launches0
