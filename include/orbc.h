@@ -150,7 +150,11 @@ ORBC_API int orbc_set_bonds(orbc_system* s, int nb, const int* ij, const double*
  * nearest-centroid assignment and centroid update; then the two-level
  * reorder (centroids along a Morton curve, particles stably by cell) and the
  * neighbouring-cell lists.  Errors: ORBC_E_ARG (more centroids than lipids),
- * ORBC_E_STATE (no particles), ORBC_E_NOMEM, ORBC_E_CUDA. */
+ * ORBC_E_STATE (no particles, or a cell with more than 64 neighbouring cells:
+ * each cell's row is held at a fixed stride of 64, which a membrane with
+ * about 60 particles per cell fills to about 8; a particle cloud in 3-D or a
+ * large skin can exceed it, and fewer, larger cells bring it back),
+ * ORBC_E_NOMEM, ORBC_E_CUDA. */
 ORBC_API int orbc_init_cells(orbc_system* s, const double* centroids);
 
 /* One update of the Voronoi cells ("Spatial Searching Algorithm": online EM
@@ -158,7 +162,8 @@ ORBC_API int orbc_init_cells(orbc_system* s, const double* centroids);
  * reorder): centroid M-step from the current ownership, Morton relabel,
  * exact nearest-centroid E-step, stable counting sort of the particles and
  * their state, cell radii and neighbouring-cell lists.
- * Errors: ORBC_E_STATE (cells not initialised), ORBC_E_CUDA. */
+ * Errors: ORBC_E_STATE (cells not initialised, or a cell with more than 64
+ * neighbouring cells, as for orbc_init_cells), ORBC_E_CUDA. */
 ORBC_API int orbc_rebuild_cells(orbc_system* s);
 
 /* Forces and torques on every particle through the quad loop over cells,
@@ -171,7 +176,9 @@ ORBC_API int orbc_compute_forces(orbc_system* s, double* energies_out);
 /* Advances nsteps BAOAB steps ("Software Overview": force and torque, then
  * position and orientation update), rebuilding the cells every
  * rebuild_every steps or when a particle has moved more than the skin.
- * Errors: ORBC_E_ARG (nsteps < 0), ORBC_E_STATE, ORBC_E_NAN, ORBC_E_CUDA. */
+ * Errors: ORBC_E_ARG (nsteps < 0), ORBC_E_STATE (cells not initialised, or a
+ * rebuild found a cell with more than 64 neighbouring cells), ORBC_E_NAN,
+ * ORBC_E_CUDA. */
 ORBC_API int orbc_integrate(orbc_system* s, int nsteps);
 
 /* Host copies of the state in id order; any pointer may be NULL.  step:
