@@ -414,6 +414,27 @@ def test_errors_are_reported():
         h.init_cells()
 
 
+def test_neighbour_row_limit_is_reported():
+    """Each cell's neighbouring cells are held in a row of 64.  512 cells on
+    the 2,304-particle patch with a 5 sigma skin put about 170 centroids
+    within R_k + R_j + r_s + 2 skin of each other: the initialisation
+    reports ORBC_E_STATE instead of dropping neighbours.  Without the skin
+    the rows hold about 20 cells and the same system initialises."""
+    mem = M.flat_patch_2304()
+    g = G.System(gpu_params(mem, n_centroids=512, skin=5.0))
+    g.load_membrane(mem)
+    with pytest.raises(G.OrbcError) as e:
+        g.init_cells()
+    assert e.value.code == -4
+    g.close()
+    h = G.System(gpu_params(mem, n_centroids=512))
+    h.load_membrane(mem)
+    h.init_cells()
+    c = h.cells()
+    assert np.diff(c["adj_ptr"]).max() <= 64
+    h.close()
+
+
 # --------------------------------------------------------------------------- full-size 4M cell, sampled
 
 @pytest.fixture(scope="module")
