@@ -176,6 +176,14 @@ def pair_terms(m: Model, ti, tj, d, ni, nj):
     return U, Fi, Ti, Tj
 
 
+def bond_pair(d, kb, r0):
+    """Harmonic bond term; d = x_b - x_a.  Returns (U, force on a)."""
+    d = _c(d, np.float64)
+    Fa = np.zeros(3)
+    U = lib().or_bond_pair(_p(d), float(kb), float(r0), _p(Fa))
+    return U, Fa
+
+
 def pairs_brute(m: Model, x, typ, ids, bonds=None):
     x = _c(x, np.float64)
     typ = _c(typ, np.uint8)

@@ -87,6 +87,76 @@ def test_lipid_pair_antiparallel_tilted_phi():
     assert U == pytest.approx(m.mu - 1.0, abs=1e-13)
 
 
+@pytest.mark.parametrize("zeta", [2, 3, 4])
+def test_lipid_pair_attractive_tail_interior_closed_form(zeta):
+    """Inside the attractive well, with aligned normals perpendicular to the
+    separation (a = 1, phi = 1), U = -eps cos^(2 zeta)(theta) with
+    theta = (pi/2)(r - r_min)/(r_c - r_min).  Halfway between r_min and r_c
+    theta = pi/4, so U = -eps 2^-zeta; one third of the way theta = pi/6, so
+    U = -eps (3/4)^zeta.  The radial force is -dU/dr =
+    -eps 2 zeta cos^(2 zeta - 1) sin (pi/2)/(r_c - r_min), pulling i towards
+    j.  A wrong exponent (cos^zeta, cos^(2 zeta - 2)) or a wrong width
+    ((pi/2)/r_c) moves every one of these values."""
+    eps, rc = 1.5, 2.6
+    m = oracle.model(eps=eps, rc=rc, zeta=zeta)
+    w = (math.pi / 2.0) / (rc - RMIN)
+    for frac, c, s in ((0.5, math.sqrt(0.5), math.sqrt(0.5)), (1.0 / 3.0, math.sqrt(3.0) / 2.0, 0.5)):
+        r = RMIN + frac * (rc - RMIN)
+        # j sits at +x from i; normals along z, perpendicular to the separation
+        U, F, Ti, Tj = oracle.lipid_pair(m, [r, 0, 0], [0, 0, 1], [0, 0, 1])
+        assert U == pytest.approx(-eps * c ** (2 * zeta), rel=1e-13)
+        fr = eps * 2 * zeta * c ** (2 * zeta - 1) * s * w
+        assert F[0] == pytest.approx(fr, rel=1e-12)       # attractive: towards +x
+        assert abs(F[1]) < 1e-14 and abs(F[2]) < 1e-14
+        assert np.abs(Ti).max() < 1e-14 and np.abs(Tj).max() < 1e-14
+    # halfway, the energy is exactly -eps 2^-zeta
+    U, _, _, _ = oracle.lipid_pair(m, [0, 0.5 * (RMIN + rc), 0], [1, 0, 0], [1, 0, 0])
+    assert U == pytest.approx(-eps * 2.0 ** -zeta, rel=1e-13)
+
+
+def test_lipid_pair_attractive_tail_scales_with_phi():
+    """Halfway through the well, a tilt that lowers a scales the tail by
+    phi = 1 + mu (a - 1) and adds the angular force and torques: with n_i
+    along z and n_j tilted by alpha about the separation axis x, rh = -x and
+    a = cos(alpha), so U = -eps 2^-zeta (1 + mu (cos(alpha) - 1))."""
+    m = oracle.model()
+    r = 0.5 * (RMIN + m.rc)
+    for alpha in (0.1, 0.4, 1.0):
+        nj = [0.0, -math.sin(alpha), math.cos(alpha)]
+        U, _, Ti, Tj = oracle.lipid_pair(m, [r, 0, 0], [0, 0, 1], nj)
+        phi = 1.0 + m.mu * (math.cos(alpha) - 1.0)
+        assert U == pytest.approx(-(2.0 ** -m.zeta) * phi, rel=1e-12)
+        # the torques twist the directors back towards each other about x
+        g = -(2.0 ** -m.zeta)
+        assert Ti[0] == pytest.approx(-g * m.mu * math.sin(alpha), rel=1e-12)
+        assert Tj[0] == pytest.approx(g * m.mu * math.sin(alpha), rel=1e-12)
+
+
+@pytest.mark.parametrize("delta", [0.1, -0.05])
+def test_bond_closed_form(delta):
+    """One harmonic bond stretched (or compressed) by delta from its rest
+    length: U = kb delta^2 / 2 and the force on each end has magnitude
+    kb |delta|, pulling the ends together when stretched.  Checked on the
+    term itself and through the system force routine (both ends, energy,
+    virial W = -kb delta r)."""
+    kb, r0 = 100.0, 0.57
+    r = r0 + delta
+    u = unit([0.3, -0.4, 1.2])
+    U, Fa = oracle.bond_pair(u * r, kb, r0)
+    assert U == pytest.approx(0.5 * kb * delta * delta, rel=1e-13)
+    np.testing.assert_allclose(Fa, kb * delta * u, rtol=1e-12, atol=1e-14)
+    m = oracle.model()
+    x = np.array([[1.0, 2.0, 3.0], [1.0, 2.0, 3.0] + u * r])
+    typ = np.array([2, 2], np.uint8)
+    F, T, e = oracle.forces_from_pairs(m, x, np.zeros((2, 3)), typ, np.zeros((0, 2), np.int32),
+                                       bond_idx=np.array([[0, 1]]), r0=np.array([r0]), kb=np.array([kb]))
+    np.testing.assert_allclose(F[0], kb * delta * u, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(F[1], -kb * delta * u, rtol=1e-12, atol=1e-14)
+    assert e[1] == pytest.approx(0.5 * kb * delta * delta, rel=1e-13)
+    assert e[4] == pytest.approx(-kb * delta * r, rel=1e-12)
+    assert np.abs(T).max() == 0.0
+
+
 def test_wca_textbook_points():
     """WCA at r = s: LJ is 0 so U = eps, and the force is 24 eps/s; at
     r = 2^(1/6) s both vanish (LJ minimum).  s = sigma_wca for a
@@ -584,7 +654,7 @@ def test_directors_stay_unit_and_angular_velocity_perpendicular():
     assert np.abs(np.sum(st["ori"][lip] * st["angvel"][lip], axis=1)).max() < 1e-14
 
 
-def test_trajectory_is_deterministic_and_restartable():
+def test_trajectory_is_deterministic():
     mem = tiny_patch()
     _, a = make_sys(mem)
     a.init_cells()
