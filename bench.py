@@ -61,9 +61,16 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+PRECISION = {"f32": ("F32_FORCE_F64_STATE", "FP32 pair/bond forces; FP64 integrator increments and energy/virial "
+                                             "partials; int64 fixed-point state (2^-40) and force sums (2^-32)"),
+             "f64": ("F64_ALL", "FP64 pair/bond forces and integrator increments; int64 fixed-point state"),
+             "f32step": ("F32_FORCE_F32_STEP", "FP32 pair/bond forces and FP32 integrator increments; int64 "
+                                               "fixed-point state")}
+
+
 def params_for(mem, precision: str, G):
     return G.make_params(kT=mem.kT, n_centroids=mem.n_centroids, box=mem.box, periodic=mem.periodic,
-                         seed=2, precision=G.F64_ALL if precision == "f64" else G.F32_FORCE_F64_STATE)
+                         seed=2, precision=getattr(G, PRECISION[precision][0]))
 
 
 def oracle_params(mem, oracle):
@@ -265,25 +272,35 @@ def run_ours(args, rank, world):
                  "hbm_source": src, "bytes_per_particle": STEP_BYTES_PER_PARTICLE}
 
     g.close()
-    # the FP64-everywhere variant of the same step (FP64 pair terms and
-    # increments), a few steps on the same workload
-    f64 = None
-    if args.precision == "f32" and not args.no_f64:
-        g64 = G.System(params_for(mem, "f64", G), stream=stream.cuda_stream)
-        g64.load_membrane(mem)
-        g64.init_cells()
-        g64.integrate(2)
+
+    def variant(prec, nsteps):
+        """The same step in another precision mode, a few steps on the same workload."""
+        gv = G.System(params_for(mem, prec, G), stream=stream.cuda_stream)
+        gv.load_membrane(mem)
+        gv.init_cells()
+        gv.integrate(3)
+        gv.set_timing(True)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        n64 = max(2, args.steps // 4)
         f0.record(stream)
-        g64.integrate(n64)
+        gv.integrate(nsteps)
         f1.record(stream)
         torch.cuda.synchronize()
         fms = f0.elapsed_time(f1)
-        f64 = {"value": round(mem.n * n64 / (fms * 1e-3), 1), "unit": UNIT, "steps": n64,
-               "ms_per_step": round(fms / n64, 4), "dtype": "f64"}
-        g64.close()
+        kt = {k: round(v["ms"] / max(v["launches"], 1), 4) for k, v in gv.kernel_times().items()}
+        gv.close()
+        return {"value": round(mem.n * nsteps / (fms * 1e-3), 1), "unit": UNIT, "steps": nsteps,
+                "ms_per_step": round(fms / nsteps, 4), "precision": PRECISION[prec][1],
+                "kernel_ms_per_launch": kt}
+
+    # the FP64-everywhere variant (FP64 pair terms and increments) and the
+    # FP32-increment variant of the same step
+    f64 = f32step = None
+    if args.precision == "f32" and not args.no_f64:
+        f64 = variant("f64", max(2, args.steps // 4)) | {"dtype": "f64"}
+    if args.precision == "f32" and not args.no_variants:
+        f32step = variant("f32step", args.steps) | {"dtype": "f32"}
+        f32step["cost_of_fp64_increments_ms_per_step"] = round(ms / args.steps - f32step["ms_per_step"], 4)
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -327,14 +344,14 @@ def run_ours(args, rank, world):
     line = {"metric": METRIC if args.workload == "rbc-4m" else f"particle-steps/s at {args.workload}",
             "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.precision == "f32" else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "f64" else "f32", "data": "synthetic",
             "config": {"workload": args.workload, "particles": mem.n, "voronoi_cells": mem.n_centroids,
-                       "precision": ("FP32 forces, int64 fixed-point state (2^-40)" if args.precision == "f32"
-                                     else "FP64 forces and increments, int64 fixed-point state"),
+                       "precision": PRECISION[args.precision][1],
                        "rebuild_every": 1, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (resident state, forces and mirrors ~1.4 GB)"},
             "roofline": roof, "kernel_ms_per_launch": breakdown, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clocks.summary(), "step_roofline": step_roof, "fp64_variant": f64, "ensemble": ens}
+            "gpu_launches": launches, "clocks": clocks.summary(), "step_roofline": step_roof, "fp64_variant": f64, "f32_increment_variant": f32step,
+            "ensemble": ens}
     return line
 
 
@@ -489,12 +506,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="rbc-4m")
-    ap.add_argument("--precision", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--precision", choices=list(PRECISION), default="f32")
     ap.add_argument("--cpu-budget", type=float, default=25.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-vs-plain ensemble comparison")
     ap.add_argument("--no-f64", action="store_true", help="skip the FP64-everywhere variant")
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP32-increment variant")
     ap.add_argument("--ensemble-steps", type=int, default=500)
     ap.add_argument("--requests", type=int, default=32, help="served-stream requests (workload serve)")
     ap.add_argument("--load", type=float, default=0.8, help="arrival rate / plain-form throughput (workload serve)")

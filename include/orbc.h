@@ -50,13 +50,22 @@ typedef enum {
     ORBC_E_NOMEM = -2,     /* device allocation failed or HBM budget exceeded   */
     ORBC_E_CUDA = -3,      /* CUDA runtime error                                */
     ORBC_E_STATE = -4,     /* call out of order, or the device state is invalid */
-    ORBC_E_NAN = -5,       /* non-finite force or state detected on the device  */
+    ORBC_E_NAN = -5,       /* non-finite force or state detected on the device, or a
+                              pair/bond term of 2^24 eps/sigma or more (beyond the
+                              range of the 2^-32 fixed-point force sums)          */
     ORBC_E_TIMEOUT = -6    /* a bounded device wait gave up                     */
 } orbc_status;
 
+/* Arithmetic of the time step.  In every mode the state (x, v, n, w) is held
+ * as int64 on the 2^-40 grid and forces, torques and energies are summed as
+ * exact 2^-32 fixed point, so sums do not depend on the order of the terms. */
 typedef enum {
-    ORBC_F32_FORCE_F64_STATE = 0,  /* FP32 pair/bond forces, exact fixed-point accumulation and state */
-    ORBC_F64_ALL = 1               /* FP64 pair/bond forces and FP64 integrator increments             */
+    ORBC_F32_FORCE_F64_STATE = 0,  /* FP32 pair/bond forces; FP64 integrator increments (kicks, drifts,
+                                      Ornstein-Uhlenbeck update, Cayley map, renormalisation) and FP64
+                                      per-particle energy/virial partials                               */
+    ORBC_F64_ALL = 1,              /* FP64 pair/bond forces and FP64 integrator increments             */
+    ORBC_F32_FORCE_F32_STEP = 2    /* FP32 pair/bond forces and FP32 integrator increments (rounded onto
+                                      the same int64 grid): the narrowest, fastest variant             */
 } orbc_precision;
 
 /* Particle types of the two-component red-cell model ("Initial structure
@@ -236,12 +245,17 @@ ORBC_API int orbc_cell_sort(const int* d_cell, int n, int K, int* d_perm, int* d
  * no allocator.  Its scratch is one fixed array of about 4.7 MB in the
  * library's device memory, present on every device that loads the library
  * until the process exits, which bounds the sizes: n <= 1,048,576 and
- * K <= 65,536, larger requests return ORBC_E_NOMEM.  The first call on each
- * device looks up the array's device address with that device current
- * (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  Every call reuses the same array and zeroes what must start at
- * zero; calls that overlap on the GPU (other streams, other threads) race
- * on it and must be serialised by the caller.  Synchronises the stream. */
+ * K <= 65,536, larger requests return ORBC_E_NOMEM.  Every call made while
+ * its stream is not capturing looks up the array's device address with the
+ * current device (cudaGetSymbolAddress), so a device reset or a new context
+ * between calls is followed; make the first call on each device before any
+ * stream capture.  A call made while its stream is capturing does not look
+ * the address up: it reuses the one found by the last call on that device
+ * (ORBC_E_CUDA if there was none), which is stale if the context was reset
+ * or replaced since.  Every call reuses the same array
+ * and zeroes what must start at zero; calls that overlap on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller.
+ * Synchronises the stream. */
 ORBC_API int orbc_cell_sort_noalloc(const int* d_cell, int n, int K, int* d_perm, int* d_cell_start,
                                     void* cuda_stream);
 
@@ -284,7 +298,8 @@ typedef struct orbc_arena orbc_arena;   /* opaque; owns its device memory */
 
 /* hbm_budget_bytes bounds the device memory reserved by admitted instances
  * (packed arrays plus one carried copy each, which a re-pack needs).  All
- * instances share one precision.  cuda_stream as in orbc_create.
+ * instances share one precision (any orbc_precision).  cuda_stream as in
+ * orbc_create.
  * Errors: ORBC_E_ARG (budget 0, unknown precision, null out), ORBC_E_CUDA. */
 ORBC_API int orbc_arena_create(unsigned long long hbm_budget_bytes, orbc_precision precision, void* cuda_stream,
                                orbc_arena** out);

@@ -13,9 +13,10 @@ import ctypes as C
 import numpy as np
 
 from . import _native
-from ._native import F32_FORCE_F64_STATE, F64_ALL, OrbcError, Params, default_params, load
+from ._native import F32_FORCE_F32_STEP, F32_FORCE_F64_STATE, F64_ALL, OrbcError, Params, default_params, load
 
-__all__ = ["System", "Arena", "autotune", "Params", "default_params", "load", "OrbcError", "F32_FORCE_F64_STATE", "F64_ALL"]
+__all__ = ["System", "Arena", "autotune", "Params", "default_params", "load", "OrbcError", "F32_FORCE_F64_STATE", "F64_ALL",
+           "F32_FORCE_F32_STEP"]
 
 
 def _p(a):

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liborbc.so")
 
 ORBC_OK, ORBC_E_ARG, ORBC_E_NOMEM, ORBC_E_CUDA, ORBC_E_STATE, ORBC_E_NAN, ORBC_E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
-F32_FORCE_F64_STATE, F64_ALL = 0, 1
+F32_FORCE_F64_STATE, F64_ALL, F32_FORCE_F32_STEP = 0, 1, 2
 STATUS_NAMES = {0: "ORBC_OK", -1: "ORBC_E_ARG", -2: "ORBC_E_NOMEM", -3: "ORBC_E_CUDA", -4: "ORBC_E_STATE",
                 -5: "ORBC_E_NAN", -6: "ORBC_E_TIMEOUT"}
 

@@ -842,7 +842,7 @@ void orbc::check_params(const Params& P) {
     if (P.rebuild_every < 1) throw ArgError("rebuild_every must be >= 1");
     if (P.rebuild_every > 1 && !(P.skin > 0)) throw ArgError("rebuild_every > 1 needs a positive skin");
     if (!(P.skin >= 0 && fin(P.skin)) || !(P.grid_h >= 0 && fin(P.grid_h))) throw ArgError("invalid skin or grid_h");
-    if (P.precision != 0 && P.precision != 1) throw ArgError("unknown precision");
+    if (P.precision < 0 || P.precision > 2) throw ArgError("unknown precision");
 }
 
 

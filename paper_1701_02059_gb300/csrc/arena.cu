@@ -449,7 +449,8 @@ int orbc_arena_create(unsigned long long hbm_budget_bytes, orbc_precision precis
                       orbc_arena** out) {
     if (!out) return ORBC_E_ARG;
     *out = nullptr;
-    if (hbm_budget_bytes == 0 || (precision != ORBC_F32_FORCE_F64_STATE && precision != ORBC_F64_ALL))
+    if (hbm_budget_bytes == 0 || (precision != ORBC_F32_FORCE_F64_STATE && precision != ORBC_F64_ALL &&
+                                  precision != ORBC_F32_FORCE_F32_STEP))
         return ORBC_E_ARG;
     orbc_arena* h = new (std::nothrow) orbc_arena();
     if (!h) return ORBC_E_NOMEM;

@@ -122,15 +122,23 @@ constexpr size_t kStaticInts = 2 * ((size_t)kStaticMaxCells + 1) + (size_t)kStat
 static __device__ __align__(256) int g_cell_sort_scratch[kStaticInts];   // ~4.7 MB per device
 
 // Host code may not use g_cell_sort_scratch as a device address: its host
-// name is only a stand-in.  The device address is looked up once per device
-// (with that device current) and cached.
+// name is only a stand-in.  The device address is looked up with the device
+// current (cudaGetSymbolAddress) on every call made outside stream capture,
+// so a context that was reset or replaced since the last call is picked up;
+// inside a capture the lookup may not run, and the address found by the last
+// call outside capture on the same device is used.
 static std::mutex g_scratch_mu;
 static int* g_scratch_addr[64] = {nullptr};
 
-static int* static_scratch(int dev) {
-    std::lock_guard<std::mutex> lk(g_scratch_mu);
+static int* static_scratch(int dev, cudaStream_t st) {
     if (dev < 0 || dev >= 64) return nullptr;
-    if (!g_scratch_addr[dev]) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (cap == cudaStreamCaptureStatusNone) {
         int* p = nullptr;
         if (cudaGetSymbolAddress((void**)&p, g_cell_sort_scratch) != cudaSuccess) {
             cudaGetLastError();
@@ -150,7 +158,7 @@ extern "C" int orbc_cell_sort_noalloc(const int* d_cell, int n, int K, int* d_pe
     cudaStream_t st = (cudaStream_t)cuda_stream;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return ORBC_E_CUDA; }
-    int* base = static_scratch(dev);
+    int* base = static_scratch(dev, st);
     if (!base) return ORBC_E_CUDA;
     try {
         int* counts = base;

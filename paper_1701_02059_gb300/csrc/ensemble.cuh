@@ -43,7 +43,7 @@ struct Params {
     double skin = 0, grid_h = 0;
     unsigned long long seed = 0;
     unsigned instance = 0;
-    int precision = 0;   // 0 = FP32 forces, 1 = FP64 everywhere
+    int precision = 0;   // 0 = FP32 forces, FP64 increments; 1 = FP64 everywhere; 2 = FP32 forces and increments
 };
 
 // One instance as given by the caller (host memory, id order not required).
@@ -168,6 +168,10 @@ public:
     std::vector<long long> step_h;
     cudaStream_t stream;
     int precision = 0;
+    // pair and bond terms in FP64 (ORBC_F64_ALL), integrator increments in
+    // FP32 (ORBC_F32_FORCE_F32_STEP)
+    bool force_f64() const { return precision == 1; }
+    bool step_f32() const { return precision == 2; }
 
     View view();
     View view_alt();

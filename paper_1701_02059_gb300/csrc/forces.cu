@@ -36,6 +36,10 @@ constexpr int kQCap = 32;          // queued hits per lane before a flush
 constexpr int kMaxNbr = 32;        // neighbouring cells per pass (one per lane of the set-up warp)
 constexpr float kFilterBand = 1e-4f;
 constexpr float kCutBand = 1e-6f;
+// Largest magnitude of one pair or bond term (force or torque component,
+// eps/sigma or eps): 2^24, so that a particle's 2^-32 fixed-point sum of a
+// few hundred terms stays inside int64.
+constexpr float kMaxTerm = 16777216.0f;
 
 // ---------------------------------------------------------------- pair terms
 // Lipid pair (see the header of orbc.h for the potential).  d = x_j - x_i.
@@ -233,7 +237,9 @@ template <> struct Acc<float> {
     __device__ void add3(const View& v, int p, SplitAcc* s, int& n, int c0, float x, float y, float z) {
         const float mag = fabsf(x) + fabsf(y) + fabsf(z);
         if (mag < 1000.0f) { s[0].add(x); s[1].add(y); s[2].add(z); n++; return; }
-        if (!(mag < 1.0e30f)) atomicOr(v.status, kStatusNaN);    // NaN, infinite or absurd
+        // NaN, infinite, or a term beyond the range the 2^-32 fixed-point
+        // sums hold (|component| < 2^31 after a few hundred terms)
+        if (!(mag < kMaxTerm)) atomicOr(v.status, (mag == mag) ? kStatusPairForceRange : kStatusNaN);
         const size_t N = v.N;
         atomicAdd((unsigned long long*)&v.Fbig[(size_t)c0 * N + p], (unsigned long long)__float2ll_rn(x * 4294967296.0f));
         atomicAdd((unsigned long long*)&v.Fbig[(size_t)(c0 + 1) * N + p], (unsigned long long)__float2ll_rn(y * 4294967296.0f));
@@ -252,7 +258,8 @@ template <> struct Acc<double> {
     __device__ void zero() { for (int a = 0; a < 3; a++) { f[a] = 0; t[a] = 0; } np = 0; nb = 0; }
     __device__ static long long q(double v) { return __double2ll_rn(v * 4294967296.0); }
     __device__ void add_pair(const View& v, int, double fx, double fy, double fz, double tx, double ty, double tz) {
-        if (!(fabs(fx) + fabs(fy) + fabs(fz) + fabs(tx) + fabs(ty) + fabs(tz) < 1.0e30)) atomicOr(v.status, kStatusNaN);
+        const double mag = fabs(fx) + fabs(fy) + fabs(fz) + fabs(tx) + fabs(ty) + fabs(tz);
+        if (!(mag < (double)kMaxTerm)) atomicOr(v.status, (mag == mag) ? kStatusPairForceRange : kStatusNaN);
         f[0] += q(fx); f[1] += q(fy); f[2] += q(fz); t[0] += q(tx); t[1] += q(ty); t[2] += q(tz); np++;
     }
     __device__ void add_bond(const View&, int, double fx, double fy, double fz) { f[0] += q(fx); f[1] += q(fy); f[2] += q(fz); nb++; }
@@ -500,7 +507,7 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
             }
         Acc<T> acc;
         acc.zero();
-        T up = 0, vir = 0;
+        double up = 0, vir = 0;     // per-particle energy and virial partials, FP64 in every mode
 
         // passes over chunks of neighbouring cells (a cell larger than the
         // stage is split across passes)
@@ -621,8 +628,8 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                         }
                         acc.add_pair(v, pi, fx, fy, fz, tx, ty, tz);
                         if (ENERGY) {
-                            up += (T)0.5 * U;
-                            vir += (T)0.5 * -(dx * fx + dy * fy + dz * fz);
+                            up += 0.5 * (double)U;
+                            vir += -0.5 * ((double)dx * (double)fx + (double)dy * (double)fy + (double)dz * (double)fz);
                         }
                         if (DUMP) {
                             const unsigned idj = v.id[pj];
@@ -719,8 +726,8 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
             // per-particle energies to fixed point, exact integer sums per instance
             long long eu = 0, ew = 0;
             if (ivalid) {
-                eu = __double2ll_rn((double)up * 4294967296.0);
-                ew = __double2ll_rn((double)vir * 4294967296.0);
+                eu = __double2ll_rn(up * 4294967296.0);
+                ew = __double2ll_rn(vir * 4294967296.0);
             }
             for (int off = 16; off; off >>= 1) {
                 eu += __shfl_xor_sync(0xffffffffu, eu, off);
@@ -773,13 +780,19 @@ __global__ void k_bonds(View v, long long* __restrict__ energy /* [B][8] */) {
             long long f;
             if constexpr (sizeof(T) == 4) f = __float2ll_rn(g[a] * 4294967296.0f);
             else f = __double2ll_rn(g[a] * 4294967296.0);
-            if (!(fabs(g[a]) < (T)1.0e30)) atomicOr(v.status, kStatusNaN);
+            if (!(fabs(g[a]) < (T)kMaxTerm)) atomicOr(v.status, (g[a] == g[a]) ? kStatusPairForceRange : kStatusNaN);
             atomicAdd((unsigned long long*)&v.F[a * N + pi], (unsigned long long)f);
             atomicAdd((unsigned long long*)&v.F[a * N + pj], (unsigned long long)(-f));
         }
         if (ENERGY) {
-            eb = __double2ll_rn((double)((T)0.5 * kb * dr * dr) * 4294967296.0);
-            ew = __double2ll_rn((double)(-(c * (dx * dx + dy * dy + dz * dz))) * 4294967296.0);
+            // energy and virial partials in FP64 from the exact displacement
+            const double ex = grid_to_double(ddx), ey = grid_to_double(ddy), ez = grid_to_double(ddz);
+            const double r2d = ex * ex + ey * ey + ez * ez;
+            const double rd = sqrt(r2d);
+            const double r0d = (double)r0, kbd = (double)kb;
+            const double drd = rd - r0d;
+            eb = __double2ll_rn(0.5 * kbd * drd * drd * 4294967296.0);
+            ew = __double2ll_rn(-(kbd * drd * rd) * 4294967296.0);
         }
     }
     if (ENERGY) {
@@ -830,7 +843,7 @@ void Ensemble::launch_pairs(bool energies, bool dump) {
     const dim3 g(Ktot), t(kPairThreads);
     prefer_shared_all();
     tic("pairs");
-    if (precision == 0) {
+    if (!force_f64()) {
         if (dump) k_pairs<float, false, true, 0, true><<<g, t, 0, stream>>>(v, d_energy, d_dump, d_dump_count, dump_cap);
         else if (energies && z4 && s0z) k_pairs<float, true, false, 4, false><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
         else if (energies && z4) k_pairs<float, true, false, 4, true><<<g, t, 0, stream>>>(v, d_energy, nullptr, nullptr, 0);
@@ -847,7 +860,7 @@ void Ensemble::launch_pairs(bool energies, bool dump) {
     toc();
     tic("bonds");
     const int nb = (int)((std::max(nbond, 1) + 255) / 256);
-    if (precision == 0) {
+    if (!force_f64()) {
         if (energies) k_bonds<float, true><<<nb, 256, 0, stream>>>(v, d_energy);
         else k_bonds<float, false><<<nb, 256, 0, stream>>>(v, d_energy);
     } else {

@@ -5,8 +5,8 @@
 // Philox4x32-10 keyed by (seed, instance; id, step, substream).
 //
 // State is int64 on the 2^-40 grid; every update is an increment computed in
-// FP32 (FP64 for ORBC_F64_ALL) and rounded onto the grid, so accumulation is
-// exact integer arithmetic and no FP64 operation runs in the FP32 path.
+// FP64 (FP32 for ORBC_F32_FORCE_F32_STEP) and rounded onto the grid, so
+// accumulation is exact integer arithmetic.
 #include "ensemble.cuh"
 
 namespace orbc {
@@ -22,7 +22,12 @@ template <> struct Num<double> {
     static __device__ double st(long long q) { return grid_to_double(q); }
     static __device__ double frc(long long q) { return __ll2double_rn(q) * kForceUnit; }
     static __device__ long long grid(double x) { return double_to_grid(x); }
-    static __device__ double noise(unsigned w) { return noise_d(w); }
+    // sqrt(12) ((w + 1/2) 2^-32 - 1/2) = sqrt(12) 2^-33 (2 (w - 2^31) + 1): the
+    // integer is exact and the product is rounded once, as in the definition
+    static __device__ double noise(unsigned w) {
+        const long long s = 2 * (long long)(int)(w ^ 0x80000000u) + 1;   // |s| < 2^32, exact
+        return (3.4641016151377544 * 1.16415321826934814453125e-10) * (double)s;
+    }
 };
 
 template <typename T> struct Consts;
@@ -79,19 +84,22 @@ __device__ inline void renormalise(long long nq[3], double) {
     nq[2] -= double_to_grid(n2 * 0.5 * delta);
 }
 
+// Half kick of v and w with the current force and torque (torque projected
+// perpendicular to n); reps = 2 applies the same rounded increments twice
+// (the final B of the previous step and this step's B share their forces).
 template <typename T>
 __device__ inline void kick(long long vq[3], long long wq[3], const long long nq[3], const View& v, int p, bool lipid,
-                            const Consts<T>& C) {
+                            const Consts<T>& C, int reps = 1) {
     using V = Num<T>;
     const size_t N = v.N;
-    for (int a = 0; a < 3; a++) vq[a] += V::grid(C.hm * V::frc(v.F[a * N + p]));
+    for (int a = 0; a < 3; a++) vq[a] += reps * V::grid(C.hm * V::frc(v.F[a * N + p]));
     if (lipid) {
         T t0 = V::frc(v.T[p]), t1 = V::frc(v.T[N + p]), t2 = V::frc(v.T[2 * N + p]);
         T n0 = V::st(nq[0]), n1 = V::st(nq[1]), n2 = V::st(nq[2]);
         T tn = t0 * n0 + t1 * n1 + t2 * n2;
-        wq[0] += V::grid(C.hi * (t0 - tn * n0));
-        wq[1] += V::grid(C.hi * (t1 - tn * n1));
-        wq[2] += V::grid(C.hi * (t2 - tn * n2));
+        wq[0] += reps * V::grid(C.hi * (t0 - tn * n0));
+        wq[1] += reps * V::grid(C.hi * (t1 - tn * n1));
+        wq[2] += reps * V::grid(C.hi * (t2 - tn * n2));
     }
 }
 
@@ -129,7 +137,7 @@ __device__ inline void mstep_sums(const View& v, const Inst& I, int p, bool lipi
 }
 
 template <typename T, bool FUSED>
-__global__ void __launch_bounds__(256, 4) k_baoa(View v, const long long* __restrict__ steps,
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 4) k_baoa(View v, const long long* __restrict__ steps,
                                                  long long* __restrict__ msum, int* __restrict__ mcnt) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= v.N) return;
@@ -143,10 +151,13 @@ __global__ void __launch_bounds__(256, 4) k_baoa(View v, const long long* __rest
     for (int a = 0; a < 3; a++) { xq[a] = v.xq[a * N + p]; vq[a] = v.vq[a * N + p]; }
     if (lipid) for (int a = 0; a < 3; a++) { nq[a] = v.nq[a * N + p]; wq[a] = v.wq[a * N + p]; }
     // (final B of the previous step), B
-    if (FUSED) kick<T>(vq, wq, nq, v, p, lipid, C);
-    kick<T>(vq, wq, nq, v, p, lipid, C);
+    kick<T>(vq, wq, nq, v, p, lipid, C, FUSED ? 2 : 1);
     // A
-    for (int a = 0; a < 3; a++) xq[a] += V::grid(C.hdt * V::st(vq[a]));
+    T vd[3];
+    for (int a = 0; a < 3; a++) {
+        vd[a] = V::st(vq[a]);
+        xq[a] += V::grid(C.hdt * vd[a]);
+    }
     if (lipid) cayley<T>(nq, wq, C.hdt);
     // O
     const unsigned id = v.id[p];
@@ -154,7 +165,7 @@ __global__ void __launch_bounds__(256, 4) k_baoa(View v, const long long* __rest
     const uint2 key = make_uint2((unsigned)I.seed, (unsigned)(I.seed >> 32) ^ I.instance);
     uint4 w0 = philox4x32_10(make_uint4(id, (unsigned)step, (unsigned)(step >> 32), 0u), key);
     T xi[3] = { V::noise(w0.x), V::noise(w0.y), V::noise(w0.z) };
-    for (int a = 0; a < 3; a++) vq[a] += V::grid(C.ctm1 * V::st(vq[a]) + C.st * xi[a]);
+    for (int a = 0; a < 3; a++) vq[a] += V::grid(C.ctm1 * vd[a] + C.st * xi[a]);
     if (lipid) {
         uint4 w1 = philox4x32_10(make_uint4(id, (unsigned)step, (unsigned)(step >> 32), 1u), key);
         T r0 = V::noise(w1.x), r1 = V::noise(w1.y), r2 = V::noise(w1.z);
@@ -238,7 +249,7 @@ static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 void Ensemble::launch_integrate_first(bool fused, bool msums) {
     long long* ms = msums ? d_msum : nullptr;
     int* mc = msums ? d_mcnt : nullptr;
-    if (precision == 0) {
+    if (step_f32()) {
         if (fused) k_baoa<float, true><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step, ms, mc);
         else k_baoa<float, false><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step, ms, mc);
     } else {
@@ -254,7 +265,7 @@ void Ensemble::launch_integrate_first(bool fused, bool msums) {
 }
 
 void Ensemble::launch_kick(bool energies) {
-    if (precision == 0) k_kick<float><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
+    if (step_f32()) k_kick<float><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
     else k_kick<double><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
     launches++;
     CK(cudaGetLastError());

@@ -122,10 +122,13 @@ def test_rebuilds_bit_exact(initialised):
         assert_cells_equal(g, o)
 
 
+@pytest.mark.parametrize("precision", [G.F32_FORCE_F64_STATE, G.F32_FORCE_F32_STEP])
 @pytest.mark.parametrize("name", ["patch-2304", "vesicle-3.6k", "vesicle-62k"])
-def test_trajectory_100_steps_fp32(name):
+def test_trajectory_100_steps_fp32(name, precision):
+    """FP32 forces with FP64 or FP32 integrator increments: 100 steps within
+    1e-5 sigma RMS of the oracle's trajectory."""
     mem = WORKLOADS[name]()
-    g, m, o = pair(mem)
+    g, m, o = pair(mem, gkw={"precision": precision})
     g.init_cells()
     o.init_cells()
     g.integrate(100)
