@@ -252,6 +252,7 @@ void Ensemble::alloc_core(const std::vector<int>& p0, const std::vector<int>& k0
     d_seglist_n = alloc<int>(2);
     d_adjd = alloc<AdjDesc>(adj_cap);
     d_candrows = alloc<float4>(adj_cap);
+    alloc_lists();
     prev_adj_valid_ = false;
     csr_valid_ = false;
     d_energy = alloc<long long>((size_t)8 * B);

@@ -165,6 +165,7 @@ void Ensemble::setup_from(const std::vector<const Snapshot*>& list) {
     // recomputes the mirrors, radii and neighbouring cells
     cells_valid = true;
     forces_valid = true;
+    list_valid = false;
 }
 
 // ---------------------------------------------------------------- graphs

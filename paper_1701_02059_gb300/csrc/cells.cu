@@ -1567,6 +1567,7 @@ void Ensemble::finish_cells() {
     csr_valid_ = false;
     cells_valid = true;
     forces_valid = false;
+    list_valid = false;
     n_rebuilds++;
 }
 

@@ -190,6 +190,7 @@ public:
     void morton_relabel();
     void finish_cells();
     void launch_pairs(bool energies, bool dump);
+    void alloc_lists();
     void launch_integrate_first(bool fused, bool msums = false);
     void launch_kick(bool energies);
     void mirrors();
@@ -269,6 +270,14 @@ public:
     int* d_seglist_n = nullptr;              // [2] their counts
     AdjDesc* d_adjd = nullptr;               // [adj_cap] staging descriptors of the rows
     float4* d_candrows = nullptr;            // [adj_cap] previous rows renumbered, with centroids (E-step)
+    // neighbour lists of the split pair path (valid until the next reorder)
+    int* d_nlist = nullptr;                  // [list_cap][N] entries (row << 26 | q), t-major
+    int* d_ncnt = nullptr;                   // [N] listed pairs per particle (rank order)
+    int2* d_novf = nullptr;                  // [ovf_cap] (q, entry) beyond list_cap
+    int* d_novf_n = nullptr;                 // their count
+    int4* d_rowoff = nullptr;                // [adj_cap] exact offset c_l - c_k of each row entry
+    int list_cap = 0, ovf_cap = 0;
+    bool list_valid = false;
     long long* d_xref = nullptr;
     long long* d_energy = nullptr;           // [B][8] fixed-point sums
     long long* d_step = nullptr;             // [B]

@@ -76,8 +76,8 @@ __device__ inline float taylor_sin(float x) {
 // FP32 lipid pair; Z > 0 fixes zeta at compile time (Z = 0: runtime zeta).
 // S0: the spontaneous-curvature term is present (sin theta0 != 0); without
 // it the terms in s0 drop out of a, w and the torque.
-template <int Z, bool S0 = true>
-__device__ inline float lipid_terms_f(const Inst& I, float dx, float dy, float dz, float r2, float nix, float niy,
+template <int Z, bool S0 = true, typename IC = Inst>
+__device__ inline float lipid_terms_f(const IC& I, float dx, float dy, float dz, float r2, float nix, float niy,
                                       float niz, float njx, float njy, float njz, float& fx, float& fy, float& fz,
                                       float& tx, float& ty, float& tz, float* tj = nullptr) {
     const float rinv = rsqrtf(r2);
@@ -742,6 +742,438 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
     }
 }
 
+// ================================================================ split pair path
+// The quad loop in two launches: a per-cell search that lists, for every
+// particle, the staged particles of its neighbouring cells within its
+// type-pair cutoff (+ two skins + a rounding band), and an evaluation with
+// one thread per particle over its list, which takes the exact inclusion
+// decision and the pair terms.  The search keeps only what the filter needs
+// (no evaluation, queues or combine), so it runs with more resident warps;
+// the evaluation has no barriers and full lanes.  Forces are the same exact
+// integer sums as in the one-launch kernel, whatever order the list holds.
+//
+// List entry: (row << 26) | q, where q indexes the rank-ordered mirrors and
+// row is the neighbouring cell's place in the row of the particle's cell,
+// whose exact offset c_l - c_k the search writes to rowoff.  Lists hold
+// kListCap entries per particle (t-major: entry t of particle q at t N + q);
+// further entries go to an overflow list evaluated with integer atomics.
+constexpr int kSearchStage = 768;
+constexpr int kListCap = 32;
+constexpr int kRowShift = 26;
+
+struct SNbr {
+    int base, cnt, start, row;
+    int ox, oy, oz;
+};
+
+__global__ void __launch_bounds__(kPairThreads, 7)
+    k_pair_search(View v, int* __restrict__ nlist, int* __restrict__ ncnt, int cap, int2* __restrict__ ovf,
+                  int* __restrict__ novf, int ovf_cap, int4* __restrict__ rowoff) {
+    // sY: staged mirrors (int4 by the bulk copy), then in the tangent frame
+    //     (FP32), w = 0 for a lipid and 1 for a protein
+    // sQ: the list entry of each staged particle
+    __shared__ alignas(16) float4 sY[kSearchStage];
+    __shared__ int sQ[kSearchStage];
+    __shared__ alignas(16) unsigned short cand[kPairThreads / 32][kSearchStage];
+    __shared__ SNbr nb[kMaxNbr];
+    __shared__ int s_cnt[kPairThreads];
+    __shared__ unsigned long long bar;
+    __shared__ int s_nstage, s_next, s_next_off, s_self, s_self_lo, s_self_hi, s_total;
+
+    const int k = blockIdx.x;
+    const int b = find_inst(v.inst_k0, v.B, k);
+    const Inst& I = v.inst[b];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cs = v.cell_start[k], ce = v.cell_start[k + 1];
+    const AdjDesc* __restrict__ row = v.adjd + (size_t)k * kAdjRow;
+    const int a1 = min(v.adjn[k], kAdjRow);
+    const size_t N = v.N;
+    const float sk = 2.0f * (float)I.skin + kFilterBand;
+    const float rsb = I.rsf + sk, rs2f = rsb * rsb;
+    const float cl = sqrtf(I.rc2f_ll) + sk, cw = sqrtf(I.rc2f_wca) + sk, cp = sqrtf(I.rc2f_pp) + sk;
+    unsigned phase = 0;
+    if (tid == 0) mbar_init(&bar, 1);
+    __syncthreads();
+
+    for (int it0 = cs; it0 < ce; it0 += kPairThreads) {
+        const int nti = min(kPairThreads, ce - it0);
+        const int groups = (nti + 31) >> 5;
+        const int nsplit = (groups == 1) ? 4 : (groups == 2 ? 2 : 1);
+        const int igrp = warp % groups;
+        const int jsplit = warp / groups;
+        const bool wactive = jsplit < nsplit;
+        const int gs = (nti + groups - 1) / groups;
+        s_cnt[tid] = 0;
+
+        auto issue = [&](const int na, const int na_off) {
+            if (warp == 0) {
+                const int nn = na + lane;
+                const bool has = nn < a1;
+                int l = 0, st = 0, c = 0;
+                AdjDesc d;
+                if (has) {
+                    d = row[nn];
+                    l = d.cell;
+                    st = d.start;
+                    c = d.cnt;
+                    if (na_off == 0 && it0 == cs) rowoff[(size_t)k * kAdjRow + nn] = make_int4(d.ox, d.oy, d.oz, 0);
+                    if (lane == 0) { st += na_off; c -= na_off; }
+                }
+                int incl = c;
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, incl, off);
+                    if (lane >= off) incl += t;
+                }
+                const int excl = incl - c;
+                const bool fits = has && incl <= kSearchStage;
+                const bool part = has && excl < kSearchStage && incl > kSearchStage;
+                const unsigned fm = __ballot_sync(0xffffffffu, fits), pm = __ballot_sync(0xffffffffu, part);
+                const int m = __popc(fm) + (pm ? 1 : 0);
+                const bool staged = fits || part;
+                const int take = part ? kSearchStage - excl : c;
+                if (staged) {
+                    SNbr inf;
+                    inf.base = excl; inf.cnt = take; inf.start = st; inf.row = nn;
+                    inf.ox = d.ox; inf.oy = d.oy; inf.oz = d.oz;
+                    nb[lane] = inf;
+                }
+                const unsigned selfm = __ballot_sync(0xffffffffu, staged && l == k);
+                const int total = __shfl_sync(0xffffffffu, excl + take, max(m - 1, 0));
+                int nxt = na + __popc(fm), nxo = 0;
+                if (pm) {
+                    const int p = __ffs(pm) - 1;
+                    const int ex_p = __shfl_sync(0xffffffffu, excl, p);
+                    nxt = na + p;
+                    nxo = (p == 0 ? na_off : 0) + (kSearchStage - ex_p);
+                }
+                int slo = -1, shi = -1, sb = 0;
+                {
+                    const int p = selfm ? __ffs(selfm) - 1 : 0;
+                    const int ex_p = __shfl_sync(0xffffffffu, excl, p);
+                    const int tk_p = __shfl_sync(0xffffffffu, take, p);
+                    if (selfm) {
+                        slo = ex_p;
+                        shi = ex_p + tk_p;
+                        sb = ex_p - ((p == 0) ? na_off : 0);
+                    }
+                }
+                if (lane == 0) {
+                    s_nstage = m;
+                    s_total = m > 0 ? total : 0;
+                    s_next = nxt;
+                    s_next_off = nxo;
+                    s_self = sb; s_self_lo = slo; s_self_hi = shi;
+                }
+                if (m > 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    if (lane == 0) mbar_expect_tx(&bar, (unsigned)total * 16u);
+                    __syncwarp();
+                    if (staged && take > 0) bulk_g2s(&sY[excl], v.mqr + st, take * 16u, &bar);
+                }
+            }
+        };
+        if (0 < a1) issue(0, 0);
+
+        const float4 cn = v.cnorm[k];
+        const Frame F = tangent_frame(cn.x, cn.y, cn.z);
+        const int r = igrp * gs + lane;
+        const bool ivalid = wactive && lane < gs && r < nti;
+        int ti = 0;
+        float yix = 1.0e18f, yiy = 1.0e18f, yiz = 1.0e18f;
+        if (ivalid) {
+            const int4 qi = v.mqr[it0 + r];
+            ti = qi.w & 0xff;
+            F.apply(qi.x * kMirrorUnit, qi.y * kMirrorUnit, qi.z * kMirrorUnit, yix, yiy, yiz);
+        }
+        // squared search radius for a lipid and for a protein partner
+        const float cutL = ti == kLipid ? cl * cl : cw * cw;
+        const float cutP = ti == kLipid ? cw * cw : cp * cp;
+        const float cutD = cutP - cutL;
+        float blo[3] = {ivalid ? yix : 3.0e38f, ivalid ? yiy : 3.0e38f, ivalid ? yiz : 3.0e38f};
+        float bhi[3] = {ivalid ? yix : -3.0e38f, ivalid ? yiy : -3.0e38f, ivalid ? yiz : -3.0e38f};
+        for (int a = 0; a < 3; a++)
+            for (int off = 16; off; off >>= 1) {
+                blo[a] = fminf(blo[a], __shfl_xor_sync(0xffffffffu, blo[a], off));
+                bhi[a] = fmaxf(bhi[a], __shfl_xor_sync(0xffffffffu, bhi[a], off));
+            }
+        const int qi_idx = it0 + r;
+
+        bool first_pass = true;
+        for (int na = 0, na_off = 0; na < a1;) {
+            if (!first_pass) {
+                __syncthreads();
+                issue(na, na_off);
+            }
+            first_pass = false;
+            __syncthreads();
+            const int m = s_nstage;
+            const int total = s_total;
+            const int next = s_next, next_off = s_next_off;
+            if (m == 0) { na = next; na_off = next_off; continue; }
+            const int sself = s_self, sslo = s_self_lo, sshi = s_self_hi;
+            int selfj = (sslo >= 0 && ivalid) ? sself + (it0 + r - cs) : -1;
+            if (selfj < sslo || selfj >= sshi) selfj = -1;
+            bool ok = mbar_wait_bounded(&bar, phase, v.status);
+            if (__syncthreads_or(!ok)) {
+                if (ok == false) mbar_wait_bounded(&bar, phase, v.status);
+                return;
+            }
+            phase ^= 1u;
+            // staged particles into the cell's frame (exact) and the tangent
+            // frame (FP32), with their list entries
+            for (int q = 0; q < m; q++) {
+                const SNbr inf = nb[q];
+                for (int j = inf.base + tid; j < inf.base + inf.cnt; j += kPairThreads) {
+                    const int4 rj = reinterpret_cast<const int4*>(sY)[j];
+                    const int x = (int)((unsigned)rj.x + (unsigned)inf.ox);
+                    const int y = (int)((unsigned)rj.y + (unsigned)inf.oy);
+                    const int z = (int)((unsigned)rj.z + (unsigned)inf.oz);
+                    float4 w;
+                    F.apply(x * kMirrorUnit, y * kMirrorUnit, z * kMirrorUnit, w.x, w.y, w.z);
+                    w.w = ((rj.w & 0xff) == kLipid) ? 0.0f : 1.0f;
+                    sY[j] = w;
+                    sQ[j] = (inf.row << kRowShift) | (inf.start + (j - inf.base));
+                }
+            }
+            __syncthreads();
+
+            if (wactive) {
+                int cnt = 0;
+                for (int c0 = 0; c0 < total; c0 += nsplit * 32) {
+                    const int j = c0 + lane * nsplit + jsplit;
+                    bool in = false;
+                    if (j < total) {
+                        const float4 y = sY[j];
+                        const float ex = fmaxf(fmaxf(blo[0] - y.x, y.x - bhi[0]), 0.f);
+                        const float ey = fmaxf(fmaxf(blo[1] - y.y, y.y - bhi[1]), 0.f);
+                        const float ez = fmaxf(fmaxf(blo[2] - y.z, y.z - bhi[2]), 0.f);
+                        in = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < rs2f;
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, in);
+                    if (in) cand[warp][cnt + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)j;
+                    cnt += __popc(bal);
+                }
+                // pad to a multiple of 32 with a valid staged index
+                if (cnt + lane < ((cnt + 31) & ~31)) cand[warp][cnt + lane] = 0;
+                __syncwarp();
+                // every lane tests the same 32 candidates (broadcast reads)
+                // into a bit mask, then writes its hits; the padding of the
+                // candidate list past cnt is never read as a hit
+                static_assert(kSearchStage % 32 == 0, "candidate lists are read 32 at a time");
+                for (int c0 = 0; c0 < cnt; c0 += 32) {
+                    unsigned hits = 0u;
+#pragma unroll
+                    for (int h = 0; h < 4; h++) {
+                        const uint4 c8 = *reinterpret_cast<const uint4*>(&cand[warp][c0 + 8 * h]);
+                        const unsigned cw8[4] = {c8.x, c8.y, c8.z, c8.w};
+#pragma unroll
+                        for (int u = 0; u < 8; u++) {
+                            const int j = (int)((cw8[u >> 1] >> (16 * (u & 1))) & 0xffffu);
+                            const float4 y = sY[j];
+                            const float ex = y.x - yix, ey = y.y - yiy, ez = y.z - yiz;
+                            const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                            if (d2 < fmaf(y.w, cutD, cutL) && j != selfj) hits |= 1u << (8 * h + u);
+                        }
+                    }
+                    if (cnt - c0 < 32) hits &= (1u << (cnt - c0)) - 1u;
+                    while (hits) {
+                        const int u = __ffs(hits) - 1;
+                        hits &= hits - 1u;
+                        const int e = sQ[cand[warp][c0 + u]];
+                        const int pos = atomicAdd(&s_cnt[r], 1);
+                        if (pos < cap) {
+                            nlist[(size_t)pos * N + qi_idx] = e;
+                        } else {
+                            const int o = atomicAdd(novf, 1);
+                            if (o < ovf_cap) ovf[o] = make_int2(qi_idx, e);
+                            else atomicOr(v.status, kStatusListOverflow);
+                        }
+                    }
+                }
+            }
+            na = next;
+            na_off = next_off;
+        }
+        __syncthreads();
+        if (tid < nti) ncnt[it0 + tid] = s_cnt[tid];
+        __syncthreads();
+    }
+}
+
+// One listed pair: exact integer displacement (2^-26 sigma), the type-pair
+// cutoff decided in FP32 outside a 1e-6 sigma band and in FP64 inside it,
+// bonded exclusions, then the FP32 pair terms.  Returns false when the pair
+// does not interact.
+template <int Z, bool S0>
+__device__ inline bool listed_pair(const View& v, const Inst& I, int zc, int pi, int ti, int4 qi, float4 oi, int4 mj,
+                                   float4 oj, int4 o, float ll_lo, float ll_hi, float w_lo, float w_hi, float p_lo,
+                                   float p_hi, float& fx, float& fy, float& fz, float& tx, float& ty, float& tz) {
+    const int pj = __float_as_int(oj.w);
+    const int tj = mj.w & 0xff;
+    const bool ll = (ti == kLipid) && (tj == kLipid);
+    const int cls = ll ? 0 : ((ti == kLipid || tj == kLipid) ? 1 : 2);
+    const int dxq = (int)((unsigned)mj.x + (unsigned)o.x - (unsigned)qi.x);
+    const int dyq = (int)((unsigned)mj.y + (unsigned)o.y - (unsigned)qi.y);
+    const int dzq = (int)((unsigned)mj.z + (unsigned)o.z - (unsigned)qi.z);
+    const float dx = (float)dxq * kMirrorUnit, dy = (float)dyq * kMirrorUnit, dz = (float)dzq * kMirrorUnit;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float lo = cls == 0 ? ll_lo : (cls == 1 ? w_lo : p_lo);
+    const float hi = cls == 0 ? ll_hi : (cls == 1 ? w_hi : p_hi);
+    if (r2 >= hi) return false;
+    bool in = r2 < lo;
+    if (!in) in = exact_inside(v, I, pi, pj, cls);
+    if (in && cls == 2 && is_excluded(v, I, v.id[pi], v.id[pj])) in = false;
+    if (!in) return false;
+    if (ll)
+        lipid_dispatch<float, S0>(I, dx, dy, dz, r2, oi.x, oi.y, oi.z, oj.x, oj.y, oj.z, fx, fy, fz, tx, ty, tz, zc,
+                                  (float*)nullptr);
+    else
+        wca_terms<float>(I, cls == 2, dx, dy, dz, r2, fx, fy, fz);
+    return true;
+}
+
+// The FP32 constants of the pair terms, held in registers by the evaluation.
+struct PairC {
+    float eps, rmin, mu, s0, aw, eps2z_aw, eps_wca, sig_wca, sig_pp;
+    int zeta;
+    float ll_lo, ll_hi, w_lo, w_hi, p_lo, p_hi;   // squared cutoffs -+ the FP64 decision band
+    __device__ explicit PairC(const Inst& I)
+        : eps(I.eps), rmin(I.rmin), mu(I.mu), s0(I.s0), aw(I.aw), eps2z_aw(I.eps2z_aw), eps_wca(I.eps_wca),
+          sig_wca(I.sig_wca), sig_pp(I.sig_pp), zeta(I.zeta) {
+        const float rcl = sqrtf(I.rc2f_ll), rcw = sqrtf(I.rc2f_wca), rcp = sqrtf(I.rc2f_pp);
+        ll_lo = (rcl - kCutBand) * (rcl - kCutBand); ll_hi = (rcl + kCutBand) * (rcl + kCutBand);
+        w_lo = (rcw - kCutBand) * (rcw - kCutBand); w_hi = (rcw + kCutBand) * (rcw + kCutBand);
+        p_lo = (rcp - kCutBand) * (rcp - kCutBand); p_hi = (rcp + kCutBand) * (rcp + kCutBand);
+    }
+};
+
+// Evaluation: one thread per particle (rank order) over its list, reading
+// the listed particles' mirrors from global memory (L1/L2), the constants of
+// the pair terms in registers, the force and torque summed as exact split
+// integers.  (Measured on the 4M cell: evaluating from mirrors staged in
+// shared memory per cell, with each list split over two or four threads,
+// took 1.31 ms against 1.06 ms for this kernel.)
+template <int Z, bool S0>
+__global__ void __launch_bounds__(128, 5)
+    k_pair_eval(View v, const int* __restrict__ nlist, const int* __restrict__ ncnt, int cap,
+                const int4* __restrict__ rowoff) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= v.N) return;
+    const size_t N = v.N;
+    const int4 qi = v.mqr[q];
+    const float4 oi = v.mor[q];
+    const int pi = __float_as_int(oi.w);
+    const int ti = qi.w & 0xff;
+    const int k = v.cell[pi];
+    const int b = find_inst(v.inst_p0, v.B, pi);
+    const Inst& I = v.inst[b];
+    const PairC C(I);
+    const int zc = (Z > 0) ? Z : C.zeta;
+    const int4* __restrict__ ro = rowoff + (size_t)k * kAdjRow;
+    const int n = min(ncnt[q], cap);
+    SplitAcc af[3], at[3];
+    for (int a = 0; a < 3; a++) { af[a].zero(); at[a].zero(); }
+    int nterm = 0;
+    bool big = false;
+    for (int t = 0; t < n; t++) {
+        const int e = __ldcs(nlist + (size_t)t * N + q);
+        const int qj = e & ((1 << kRowShift) - 1);
+        const int4 o = ro[(unsigned)e >> kRowShift];
+        const int4 mj = v.mqr[qj];
+        const float4 oj = v.mor[qj];
+        const int tj = mj.w & 0xff;
+        const bool ll = (ti == kLipid) && (tj == kLipid);
+        const int cls = ll ? 0 : ((ti == kLipid || tj == kLipid) ? 1 : 2);
+        const int dxq = (int)((unsigned)mj.x + (unsigned)o.x - (unsigned)qi.x);
+        const int dyq = (int)((unsigned)mj.y + (unsigned)o.y - (unsigned)qi.y);
+        const int dzq = (int)((unsigned)mj.z + (unsigned)o.z - (unsigned)qi.z);
+        const float dx = (float)dxq * kMirrorUnit, dy = (float)dyq * kMirrorUnit, dz = (float)dzq * kMirrorUnit;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float lo = cls == 0 ? C.ll_lo : (cls == 1 ? C.w_lo : C.p_lo);
+        const float hi = cls == 0 ? C.ll_hi : (cls == 1 ? C.w_hi : C.p_hi);
+        if (r2 >= hi) continue;
+        if (!(r2 < lo) && !exact_inside(v, I, pi, __float_as_int(oj.w), cls)) continue;
+        if (cls == 2 && is_excluded(v, I, v.id[pi], v.id[__float_as_int(oj.w)])) continue;
+        float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (ll) {
+            if (zc == 4)
+                lipid_terms_f<4, S0>(C, dx, dy, dz, r2, oi.x, oi.y, oi.z, oj.x, oj.y, oj.z, f[0], f[1], f[2], f[3],
+                                     f[4], f[5]);
+            else
+                lipid_terms_f<0, true>(C, dx, dy, dz, r2, oi.x, oi.y, oi.z, oj.x, oj.y, oj.z, f[0], f[1], f[2], f[3],
+                                       f[4], f[5]);
+        } else {
+            const float sig = cls == 2 ? C.sig_pp : C.sig_wca;
+            const float s2 = sig * sig / r2;
+            const float s6 = s2 * s2 * s2;
+            const float s12 = s6 * s6;
+            const float fr = 4.0f * C.eps_wca * (12.0f * s12 - 6.0f * s6) / r2;
+            f[0] = -fr * dx; f[1] = -fr * dy; f[2] = -fr * dz;
+        }
+        const float mag = fabsf(f[0]) + fabsf(f[1]) + fabsf(f[2]) + fabsf(f[3]) + fabsf(f[4]) + fabsf(f[5]);
+        if (mag < 1000.0f) {
+            for (int a = 0; a < 3; a++) { af[a].add(f[a]); at[a].add(f[3 + a]); }
+            nterm++;
+        } else {
+            // terms of 1000 or more go to the int64 side array (exact, rare)
+            if (!(mag < kMaxTerm)) atomicOr(v.status, (mag == mag) ? kStatusPairForceRange : kStatusNaN);
+            for (int a = 0; a < 6; a++)
+                atomicAdd((unsigned long long*)&v.Fbig[(size_t)a * N + pi],
+                          (unsigned long long)__float2ll_rn(f[a] * 4294967296.0f));
+            big = true;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        long long fb = 0, tb = 0;
+        if (big) {
+            fb = __ldcg(&v.Fbig[(size_t)a * N + pi]);
+            tb = __ldcg(&v.Fbig[(size_t)(3 + a) * N + pi]);
+            v.Fbig[(size_t)a * N + pi] = 0;
+            v.Fbig[(size_t)(3 + a) * N + pi] = 0;
+        }
+        v.F[a * N + pi] = af[a].finish(nterm) + fb;
+        v.T[a * N + pi] = at[a].finish(nterm) + tb;
+    }
+}
+
+// Listed pairs beyond kListCap: the same terms, added to F and T by 64-bit
+// integer atomics (each term rounded to 2^-32 exactly as the split sums do,
+// so the totals are the same integers).
+template <int Z, bool S0>
+__global__ void k_pair_overflow(View v, const int2* __restrict__ ovf, const int* __restrict__ novf, int ovf_cap,
+                                const int4* __restrict__ rowoff) {
+    const int n = min(*novf, ovf_cap);
+    const size_t N = v.N;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        const int2 pr = ovf[x];
+        const int q = pr.x, e = pr.y;
+        const int4 qi = v.mqr[q];
+        const float4 oi = v.mor[q];
+        const int pi = __float_as_int(oi.w);
+        const int ti = qi.w & 0xff;
+        const int k = v.cell[pi];
+        const int b = find_inst(v.inst_p0, v.B, pi);
+        const Inst& I = v.inst[b];
+        const int zc = (Z > 0) ? Z : I.zeta;
+        const float rcl = sqrtf(I.rc2f_ll), rcw = sqrtf(I.rc2f_wca), rcp = sqrtf(I.rc2f_pp);
+        const int qj = e & ((1 << kRowShift) - 1);
+        const int4 o = rowoff[(size_t)k * kAdjRow + ((unsigned)e >> kRowShift)];
+        float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (!listed_pair<Z, S0>(v, I, zc, pi, ti, qi, oi, v.mqr[qj], v.mor[qj], o, (rcl - kCutBand) * (rcl - kCutBand),
+                                (rcl + kCutBand) * (rcl + kCutBand), (rcw - kCutBand) * (rcw - kCutBand),
+                                (rcw + kCutBand) * (rcw + kCutBand), (rcp - kCutBand) * (rcp - kCutBand),
+                                (rcp + kCutBand) * (rcp + kCutBand), f[0], f[1], f[2], f[3], f[4], f[5]))
+            continue;
+        const float mag = fabsf(f[0]) + fabsf(f[1]) + fabsf(f[2]) + fabsf(f[3]) + fabsf(f[4]) + fabsf(f[5]);
+        if (!(mag < kMaxTerm)) atomicOr(v.status, (mag == mag) ? kStatusPairForceRange : kStatusNaN);
+        for (int a = 0; a < 3; a++) {
+            atomicAdd((unsigned long long*)&v.F[a * N + pi], (unsigned long long)__float2ll_rn(f[a] * 4294967296.0f));
+            atomicAdd((unsigned long long*)&v.T[a * N + pi], (unsigned long long)__float2ll_rn(f[3 + a] * 4294967296.0f));
+        }
+    }
+}
+
 // Harmonic bonds ("Force Evaluation": a list of bonds between proteins is
 // maintained): one thread per bond, after the pair kernel wrote F.  The bond
 // force is rounded to the 2^-32 grid once and added to both ends with
@@ -835,6 +1267,17 @@ static void prefer_shared_all() {
     });
 }
 
+void Ensemble::alloc_lists() {
+    list_cap = kListCap;
+    ovf_cap = std::max(N / 4, 4096);
+    d_nlist = alloc<int>((size_t)list_cap * N);
+    d_ncnt = alloc<int>(N);
+    d_novf = alloc<int2>(ovf_cap);
+    d_novf_n = alloc<int>(1);
+    d_rowoff = alloc<int4>(adj_cap);
+    list_valid = false;
+}
+
 void Ensemble::launch_pairs(bool energies, bool dump) {
     View v = view();
     if (energies) CK(cudaMemsetAsync(d_energy, 0, sizeof(long long) * 8 * B, stream));
@@ -842,6 +1285,34 @@ void Ensemble::launch_pairs(bool energies, bool dump) {
     for (auto& I : inst_h) { z4 = z4 && I.zeta == 4; s0z = s0z && I.s0_d == 0.0; }
     const dim3 g(Ktot), t(kPairThreads);
     prefer_shared_all();
+    if (!force_f64() && !energies && !dump) {
+        // split path: neighbour lists (once per cell reorder), evaluation,
+        // listed pairs beyond the lists' capacity
+        if (!list_valid) {
+            tic("pair_search");
+            CK(cudaMemsetAsync(d_novf_n, 0, sizeof(int), stream));
+            k_pair_search<<<g, t, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_novf, d_novf_n, ovf_cap, d_rowoff);
+            launches++;
+            CK(cudaGetLastError());
+            toc();
+            list_valid = true;
+        }
+        tic("pairs");
+        const int ng = (int)((N + 127) / 128);
+        if (z4 && s0z) {
+            k_pair_eval<4, false><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);
+            k_pair_overflow<4, false><<<152, 128, 0, stream>>>(v, d_novf, d_novf_n, ovf_cap, d_rowoff);
+        } else if (z4) {
+            k_pair_eval<4, true><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);
+            k_pair_overflow<4, true><<<152, 128, 0, stream>>>(v, d_novf, d_novf_n, ovf_cap, d_rowoff);
+        } else {
+            k_pair_eval<0, true><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);
+            k_pair_overflow<0, true><<<152, 128, 0, stream>>>(v, d_novf, d_novf_n, ovf_cap, d_rowoff);
+        }
+        launches += 2;
+        CK(cudaGetLastError());
+        toc();
+    } else {
     tic("pairs");
     if (!force_f64()) {
         if (dump) k_pairs<float, false, true, 0, true><<<g, t, 0, stream>>>(v, d_energy, d_dump, d_dump_count, dump_cap);
@@ -858,6 +1329,7 @@ void Ensemble::launch_pairs(bool energies, bool dump) {
     }
     launches++;
     toc();
+    }
     tic("bonds");
     const int nb = (int)((std::max(nbond, 1) + 255) / 256);
     if (!force_f64()) {

@@ -135,6 +135,7 @@ enum : unsigned {
     kStatusPairForceRange = 16u,
     kStatusTimeout = 32u,
     kStatusGridRange = 64u,
+    kStatusListOverflow = 128u,   // more listed pairs than the neighbour lists and their overflow hold
 };
 
 // ---------------------------------------------------------------- small helpers

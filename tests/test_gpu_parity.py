@@ -114,6 +114,20 @@ def test_forces_energies_fp32(initialised):
     assert abs(eg[4] - eo[4]) <= 1e-5 * max(abs(eo[4]), abs(eo[0]))
 
 
+def test_split_pair_path_equals_one_launch_path(initialised):
+    """The step's pair forces come from a per-cell search that writes
+    neighbour lists and a per-particle evaluation of them; energies and the
+    pair dump come from the one-launch quad-loop kernel.  Both add the same
+    FP32 pair terms as exact 2^-32 integers, so forces and torques agree bit
+    for bit."""
+    _, mem, g, m, o = initialised
+    g.compute_forces(energies=True)
+    F1, T1 = g.forces()
+    g.compute_forces()
+    F2, T2 = g.forces()
+    assert np.array_equal(F1, F2) and np.array_equal(T1, T2)
+
+
 def test_rebuilds_bit_exact(initialised):
     _, mem, g, m, o = initialised
     for _ in range(3):
