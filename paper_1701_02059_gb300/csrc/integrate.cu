@@ -186,6 +186,134 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 4) k_baoa(View v, co
     if (msum) mstep_sums(v, I, p, lipid, xq, msum, mcnt);
 }
 
+// ---------------------------------------------------------------- FP64 increments in grid units
+// GB300 runs FP64 arithmetic and int64 <-> FP64 conversions at a few
+// operations per clock per SM, so the FP64 B-A-O-A holds every state value
+// as an integer-valued double in grid units (exact below 2^53) and folds the
+// 2^40 and 2^-32 scale factors into host-computed constants: the same
+// roundings as the computation in sigma units (power-of-two scaling commutes
+// with rounding), about half the FP64 operations.  Values that do not change
+// between phases are converted once.
+__device__ inline double gd(long long q) { return __ll2double_rn(q); }
+__device__ inline long long rg(double x) { return __double2ll_rn(x); }
+
+// Half kick(s): v += round(h_m 2^8 F), w += round(h_i 2^8 (T - (T.n) n)) in
+// grid units, with N the director in grid units.
+__device__ inline void kick_grid(long long vq[3], long long wq[3], const double N[3], const View& v, int p,
+                                 bool lipid, const Inst& I, int reps) {
+    const size_t NN = v.N;
+    for (int a = 0; a < 3; a++) vq[a] += reps * rg(I.hm8_d * gd(v.F[a * NN + p]));
+    if (lipid) {
+        const double T0 = gd(v.T[p]), T1 = gd(v.T[NN + p]), T2 = gd(v.T[2 * NN + p]);
+        const double u = (T0 * N[0] + T1 * N[1] + T2 * N[2]) * 8.271806125530277e-25;   // (T.N) 2^-80
+        wq[0] += reps * rg(I.hi8_d * (T0 - u * N[0]));
+        wq[1] += reps * rg(I.hi8_d * (T1 - u * N[1]));
+        wq[2] += reps * rg(I.hi8_d * (T2 - u * N[2]));
+    }
+}
+
+// Cayley increment of the director in grid units: a = (dt/4 2^-40) W,
+// B = a x N, C = a x B, delta = round(2/(1 + |a|^2) (B + C)).
+__device__ inline void cayley_grid(const double N[3], const double W[3], const Inst& I, long long d[3]) {
+    const double a0 = I.ca_d * W[0], a1 = I.ca_d * W[1], a2 = I.ca_d * W[2];
+    const double aa = a0 * a0 + a1 * a1 + a2 * a2;
+    const double k = 2.0 / (1.0 + aa);
+    const double b0 = a1 * N[2] - a2 * N[1], b1 = a2 * N[0] - a0 * N[2], b2 = a0 * N[1] - a1 * N[0];
+    const double c0 = a1 * b2 - a2 * b1, c1 = a2 * b0 - a0 * b2, c2 = a0 * b1 - a1 * b0;
+    d[0] = rg(k * (b0 + c0));
+    d[1] = rg(k * (b1 + c1));
+    d[2] = rg(k * (b2 + c2));
+}
+
+// Noise in grid-unit form: sqrt(12) 2^-33 (2 (w - 2^31) + 1), exact integer,
+// one rounding.
+__device__ inline double noise_grid(unsigned w) {
+    const long long s = 2 * (long long)(int)(w ^ 0x80000000u) + 1;
+    return (3.4641016151377544 * 1.16415321826934814453125e-10) * (double)s;
+}
+
+template <bool FUSED>
+__global__ void __launch_bounds__(256, 2) k_baoa_d(View v, const long long* __restrict__ steps,
+                                                   long long* __restrict__ msum, int* __restrict__ mcnt) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= v.N) return;
+    const int b = find_inst(v.inst_p0, v.B, p);
+    const Inst& I = v.inst[b];
+    const size_t N = v.N;
+    const bool lipid = v.type[p] == kLipid;
+    long long xq[3], vq[3], nq[3] = {0, 0, 0}, wq[3] = {0, 0, 0};
+    for (int a = 0; a < 3; a++) { xq[a] = v.xq[a * N + p]; vq[a] = v.vq[a * N + p]; }
+    if (lipid) for (int a = 0; a < 3; a++) { nq[a] = v.nq[a * N + p]; wq[a] = v.wq[a * N + p]; }
+    double Nd[3] = {0.0, 0.0, 0.0};
+    if (lipid) for (int a = 0; a < 3; a++) Nd[a] = gd(nq[a]);
+    // (final B of the previous step), B
+    kick_grid(vq, wq, Nd, v, p, lipid, I, FUSED ? 2 : 1);
+    // A
+    double Vd[3], Wd[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < 3; a++) {
+        Vd[a] = gd(vq[a]);
+        xq[a] += rg(I.hdt_d * Vd[a]);
+    }
+    if (lipid) {
+        for (int a = 0; a < 3; a++) Wd[a] = gd(wq[a]);
+        long long d[3];
+        cayley_grid(Nd, Wd, I, d);
+        for (int a = 0; a < 3; a++) { nq[a] += d[a]; Nd[a] = gd(nq[a]); }
+    }
+    // O
+    const unsigned id = v.id[p];
+    const unsigned long long step = (unsigned long long)steps[b] + (FUSED ? 1ull : 0ull);
+    const uint2 key = make_uint2((unsigned)I.seed, (unsigned)(I.seed >> 32) ^ I.instance);
+    const uint4 w0 = philox4x32_10(make_uint4(id, (unsigned)step, (unsigned)(step >> 32), 0u), key);
+    const double xi[3] = {noise_grid(w0.x), noise_grid(w0.y), noise_grid(w0.z)};
+    for (int a = 0; a < 3; a++) {
+        const long long d = rg(I.ct_m1_d * Vd[a] + I.st40_d * xi[a]);
+        vq[a] += d;
+        Vd[a] = gd(vq[a]);
+    }
+    if (lipid) {
+        const uint4 w1 = philox4x32_10(make_uint4(id, (unsigned)step, (unsigned)(step >> 32), 1u), key);
+        const double r0 = noise_grid(w1.x), r1 = noise_grid(w1.y), r2 = noise_grid(w1.z);
+        const double u = (r0 * Nd[0] + r1 * Nd[1] + r2 * Nd[2]) * 8.271806125530277e-25;   // (r.N) 2^-80
+        const double rp[3] = {r0 - u * Nd[0], r1 - u * Nd[1], r2 - u * Nd[2]};
+        for (int a = 0; a < 3; a++) {
+            const long long d = rg(I.cr_m1_d * Wd[a] + I.sr40_d * rp[a]);
+            wq[a] += d;
+            Wd[a] = gd(wq[a]);
+        }
+    }
+    // A
+    for (int a = 0; a < 3; a++) xq[a] += rg(I.hdt_d * Vd[a]);
+    if (lipid) {
+        long long d[3];
+        cayley_grid(Nd, Wd, I, d);
+        for (int a = 0; a < 3; a++) { nq[a] += d[a]; Nd[a] = gd(nq[a]); }
+        // unit-norm correction n <- n (1 - delta/2), delta = |n|^2 - 1
+        const double delta = (Nd[0] * Nd[0] + Nd[1] * Nd[1] + Nd[2] * Nd[2]) * 8.271806125530277e-25 - 1.0;
+        for (int a = 0; a < 3; a++) nq[a] -= rg(Nd[a] * 0.5 * delta);
+    }
+    for (int a = 0; a < 3; a++) { v.xq[a * N + p] = xq[a]; v.vq[a * N + p] = vq[a]; }
+    if (lipid) for (int a = 0; a < 3; a++) { v.nq[a * N + p] = nq[a]; v.wq[a * N + p] = wq[a]; }
+    if (msum) mstep_sums(v, I, p, lipid, xq, msum, mcnt);
+}
+
+__global__ void k_kick_d(View v, long long* __restrict__ steps) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= v.N) return;
+    const int b = find_inst(v.inst_p0, v.B, p);
+    const Inst& I = v.inst[b];
+    const size_t N = v.N;
+    const bool lipid = v.type[p] == kLipid;
+    long long vq[3], wq[3] = {0, 0, 0};
+    double Nd[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < 3; a++) vq[a] = v.vq[a * N + p];
+    if (lipid) for (int a = 0; a < 3; a++) { Nd[a] = gd(v.nq[a * N + p]); wq[a] = v.wq[a * N + p]; }
+    kick_grid(vq, wq, Nd, v, p, lipid, I, 1);
+    for (int a = 0; a < 3; a++) v.vq[a * N + p] = vq[a];
+    if (lipid) for (int a = 0; a < 3; a++) v.wq[a * N + p] = wq[a];
+    if (p == I.p0) steps[b] += 1;
+}
+
 // Counts the previous step after a fused launch read the counters.
 __global__ void k_step_advance(long long* __restrict__ steps, int B) {
     for (int b = threadIdx.x; b < B; b += blockDim.x) steps[b] += 1;
@@ -253,8 +381,8 @@ void Ensemble::launch_integrate_first(bool fused, bool msums) {
         if (fused) k_baoa<float, true><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step, ms, mc);
         else k_baoa<float, false><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step, ms, mc);
     } else {
-        if (fused) k_baoa<double, true><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step, ms, mc);
-        else k_baoa<double, false><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step, ms, mc);
+        if (fused) k_baoa_d<true><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step, ms, mc);
+        else k_baoa_d<false><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step, ms, mc);
     }
     launches++;
     if (fused) {
@@ -266,7 +394,7 @@ void Ensemble::launch_integrate_first(bool fused, bool msums) {
 
 void Ensemble::launch_kick(bool energies) {
     if (step_f32()) k_kick<float><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
-    else k_kick<double><<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
+    else k_kick_d<<<nblk(N, 256), 256, 0, stream>>>(view(), d_step);
     launches++;
     CK(cudaGetLastError());
     (void)energies;

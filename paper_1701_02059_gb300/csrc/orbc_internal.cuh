@@ -57,6 +57,11 @@ struct Inst {
     float hdt;                  // dt/2
     float ct_m1, st, cr_m1, sr; // exp(-g dt) - 1 and noise amplitudes
     double h_m_d, h_i_d, hdt_d, ct_m1_d, st_d, cr_m1_d, sr_d;
+    // the same, scaled by powers of two for FP64 increments in grid units
+    // (state as integer-valued doubles): h_m 2^8 and h_i 2^8 (force and
+    // torque at 2^-32 to a grid increment at 2^-40), st 2^40 and sr 2^40,
+    // and dt/4 2^-40 (half the Cayley rotation vector from w in grid units)
+    double hm8_d, hi8_d, st40_d, sr40_d, ca_d;
     double mass, inertia;
     unsigned long long seed;
     unsigned instance;
