@@ -39,12 +39,23 @@ MAX_SM_MHZ = 2070.0
 # candidate test), counted from the pair expression
 FLOP_PER_PAIR = 100.0
 FLOP_PER_CANDIDATE = 9.0
+# FP64 work of one B-A-O-A step (both half kicks, both drifts with their
+# Cayley rotations, the Ornstein-Uhlenbeck update and its noise scaling),
+# counted from the integrator's expressions with FMA = 2: per lipid and per
+# point particle
+FLOP64_PER_LIPID_STEP = 225.0
+FLOP64_PER_BEAD_STEP = 45.0
+# FP64 peak: the recipe's nominal GB300 figure (no measured FP64 peak exists)
+FP64_TFLOPS = 1.25
 # algorithmic HBM bytes of one step per particle (cells rebuilt every step):
 # B-A-O-A 240, M-step 24, E-step 32, histogram/scatter/per-cell order 16,
 # gather 238 (state in and out, mirrors, slot), pair kernel 80 (mirrors in,
 # force and torque out); the final half kick runs once per integrate call
 STEP_BYTES_PER_PARTICLE = 630.0
 PAIR_BYTES_PER_PARTICLE = 80.0
+# cell-list cadence of the skin variant
+CADENCE_EVERY = 10
+CADENCE_SKIN = 0.3
 
 
 def workload(name: str):
@@ -177,17 +188,18 @@ def algorithmic_work(g, mem):
     return npairs, cand
 
 
-def pairs_traffic(n_particles: int):
-    """DRAM bytes per pair-kernel launch, from the committed ncu summary of
-    the same kernel revision: bytes per particle measured on the 1M-particle
-    cell, scaled by the particles one launch processes.  None when the
-    summary belongs to another revision of the kernel."""
+def kernel_traffic(kernel: str, n_particles: int):
+    """DRAM bytes per launch of a kernel, from the committed ncu summary of
+    the same kernel revision (profiles/<kernel>_rbc-1m.md, a line
+    "traffic_bytes_per_particle: X (kernel REV)"): bytes per particle
+    measured on the 1M-particle cell, scaled by the particles one launch
+    processes.  None when there is no summary of this revision."""
     import re
-    path = os.path.join(ROOT, "profiles", "k_pairs_rbc-1m_full.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_rbc-1m.md")
     if not os.path.exists(path):
         return None
     m = re.search(r"^traffic_bytes_per_particle:\s*([0-9.eE+]+)\s*\(kernel (\S+)\)", open(path).read(), re.M)
-    if not m or m.group(2) != KERNEL_REV:
+    if not m or m.group(2) != KERNEL_REV.get(kernel):
         return None
     return round(float(m.group(1)) * n_particles)
 
@@ -247,35 +259,73 @@ def run_ours(args, rank, world):
     ms = max_over_ranks(ms, world)
     value = whole_job_rate(mem.n, args.steps, world, ms)
 
-    # roofline of the dominant kernel (pair forces: plain FP32 ALU work)
-    pk = times.get("pairs", {"ms": float("nan"), "launches": 1})
+    # work counts of the step: half-list pairs and quad-loop candidate tests
+    # (counted from the cell list), lipids and point particles
     npairs, ncand = algorithmic_work(g, mem)
-    flops = npairs * FLOP_PER_PAIR + ncand * FLOP_PER_CANDIDATE
-    pair_ms = pk["ms"] / max(pk["launches"], 1)
-    peak_tflops = SM_COUNT * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
-    achieved = flops / (pair_ms * 1e-3) / 1e12
-    traffic = pairs_traffic(mem.n)
-    roof = {"bound": "alu", "kernel": "k_pairs", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
-            "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": traffic,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-            "flops_per_launch": flops, "half_list_pairs": npairs, "half_list_candidates": ncand,
-            "kernel_ms": round(pair_ms, 4)}
-    breakdown = {k: round(v["ms"] / max(v["launches"], 1), 4) for k, v in times.items()}
-    # step roofline: every kernel at the HBM bound except the pair kernel,
-    # which is bound by the larger of its bytes and its FP32 work
+    n_lip = int((mem.type == 0).sum())
+    n_bead = mem.n - n_lip
+    peak32 = SM_COUNT * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
     pk_meas, src = peaks()
     hbm = float(pk_meas.get("hbm_gbs", 6800.0)) * 1e9
-    t_rest = (STEP_BYTES_PER_PARTICLE - PAIR_BYTES_PER_PARTICLE) * mem.n / hbm
-    t_pair = max(PAIR_BYTES_PER_PARTICLE * mem.n / hbm, flops / (peak_tflops * 1e12))
-    step_roof = {"t_roof_ms": round((t_rest + t_pair) * 1e3, 4), "t_measured_ms": round(ms / args.steps, 4),
-                 "frac": round((t_rest + t_pair) * 1e3 / (ms / args.steps), 4), "hbm_gbs": hbm / 1e9,
-                 "hbm_source": src, "bytes_per_particle": STEP_BYTES_PER_PARTICLE}
+    f64_step = args.precision in ("f32", "f64")
+    per = lambda name: times.get(name, {"ms": 0.0, "launches": 1})["ms"] / max(times.get(name, {}).get("launches", 1), 1)
+    flops_pair = npairs * FLOP_PER_PAIR
+    flops_search = ncand * FLOP_PER_CANDIDATE
+    flops64 = n_lip * FLOP64_PER_LIPID_STEP + n_bead * FLOP64_PER_BEAD_STEP
+    # candidates for the dominant single kernel: the list search, the pair
+    # evaluation and the B-A-O-A update, each against its own bound
+    cands = {
+        "k_pair_search": {"ms": per("pair_search"), "bound": "alu", "unit": "TFLOP/s", "work": flops_search,
+                          "peak": peak32, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+        "k_pair_eval": {"ms": per("pairs"), "bound": "alu", "unit": "TFLOP/s", "work": flops_pair, "peak": peak32,
+                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+    }
+    if f64_step:
+        cands["k_baoa_d"] = {"ms": per("integrate_baoa"), "bound": "alu", "unit": "TFLOP/s", "work": flops64,
+                             "peak": FP64_TFLOPS, "peak_source": "nominal GB300 FP64 (no measured FP64 peak)",
+                             "dtype": "f64"}
+    else:
+        cands["k_baoa"] = {"ms": per("integrate_baoa"), "bound": "hbm", "unit": "GB/s",
+                           "work": 240.0 * mem.n, "peak": hbm / 1e9, "peak_source": f"{src} copy bandwidth"}
+    dom = max(cands, key=lambda k: cands[k]["ms"])
+    d = cands[dom]
+    achieved = d["work"] / (d["ms"] * 1e-3) / (1e12 if d["unit"] == "TFLOP/s" else 1e9)
+    roof = {"bound": d["bound"], "kernel": dom, "achieved": round(achieved, 3), "peak": round(d["peak"], 2),
+            "unit": d["unit"], "frac": round(achieved / d["peak"], 4), "traffic": kernel_traffic(dom, mem.n),
+            "peak_source": d["peak_source"], "work_per_launch": d["work"], "kernel_ms": round(d["ms"], 4)}
+    # the pair stage (list search + evaluation) against the FP32 peak
+    pair_ms = per("pair_search") + per("pairs")
+    pair_roof = {"kernels": ["k_pair_search", "k_pair_eval"], "ms": round(pair_ms, 4),
+                 "flops_per_step": flops_pair + flops_search, "half_list_pairs": npairs,
+                 "half_list_candidates": ncand,
+                 "achieved_tflops": round((flops_pair + flops_search) / (pair_ms * 1e-3) / 1e12, 3),
+                 "peak_tflops": round(peak32, 2),
+                 "frac": round((flops_pair + flops_search) / (pair_ms * 1e-3) / 1e12 / peak32, 4),
+                 "eval_frac": round(flops_pair / (per("pairs") * 1e-3) / 1e12 / peak32, 4)}
+    breakdown = {k: round(v["ms"] / max(v["launches"], 1), 4) for k, v in times.items()}
+    # step roofline: each phase at the larger of its HBM time and its
+    # arithmetic time (FP32 pair work; FP64 integrator work when the step
+    # computes its increments in FP64)
+    t_int = max(240.0 * mem.n / hbm, flops64 / (FP64_TFLOPS * 1e12) if f64_step else 0.0)
+    t_rest = (STEP_BYTES_PER_PARTICLE - 240.0 - PAIR_BYTES_PER_PARTICLE) * mem.n / hbm
+    t_pair = max(PAIR_BYTES_PER_PARTICLE * mem.n / hbm, (flops_pair + flops_search) / (peak32 * 1e12))
+    t_roof = t_int + t_rest + t_pair
+    step_roof = {"t_roof_ms": round(t_roof * 1e3, 4), "t_measured_ms": round(ms / args.steps, 4),
+                 "frac": round(t_roof * 1e3 / (ms / args.steps), 4), "hbm_gbs": hbm / 1e9, "hbm_source": src,
+                 "bytes_per_particle": STEP_BYTES_PER_PARTICLE,
+                 "phases_ms": {"integrator": round(t_int * 1e3, 4), "rebuild": round(t_rest * 1e3, 4),
+                               "pairs": round(t_pair * 1e3, 4)},
+                 "fp64_tflops": FP64_TFLOPS if f64_step else None}
 
     g.close()
 
-    def variant(prec, nsteps):
-        """The same step in another precision mode, a few steps on the same workload."""
-        gv = G.System(params_for(mem, prec, G), stream=stream.cuda_stream)
+    def variant(prec, nsteps, **kw):
+        """The same step in another precision mode (or cell-list cadence), a
+        few steps on the same workload."""
+        pv = params_for(mem, prec, G)
+        for k, val in kw.items():
+            setattr(pv, k, val)
+        gv = G.System(pv, stream=stream.cuda_stream)
         gv.load_membrane(mem)
         gv.init_cells()
         gv.integrate(3)
@@ -298,9 +348,18 @@ def run_ours(args, rank, world):
     f64 = f32step = None
     if args.precision == "f32" and not args.no_f64:
         f64 = variant("f64", max(2, args.steps // 4)) | {"dtype": "f64"}
+    cadence = None
     if args.precision == "f32" and not args.no_variants:
         f32step = variant("f32step", args.steps) | {"dtype": "f32"}
         f32step["cost_of_fp64_increments_ms_per_step"] = round(ms / args.steps - f32step["ms_per_step"], 4)
+        # the cell list rebuilt every 10 steps or as soon as a particle has
+        # moved more than the skin (the neighbour lists are searched with the
+        # cutoff plus two skins, so the pair set stays exact); the search runs
+        # only with the rebuild
+        cadence = variant(args.precision, 4 * args.steps, rebuild_every=CADENCE_EVERY, skin=CADENCE_SKIN) | {
+            "rebuild_every": CADENCE_EVERY, "skin_sigma": CADENCE_SKIN, "dtype": "f32",
+            "speedup_over_every_step": None}
+        cadence["speedup_over_every_step"] = round((ms / args.steps) / cadence["ms_per_step"], 3)
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -340,6 +399,9 @@ def run_ours(args, rank, world):
     ens = None
     if rank == 0 and world == 1 and not args.no_ensemble and args.workload == "rbc-4m":
         ens = run_ensemble(steps=args.ensemble_steps, budget_gb=args.budget_gb)
+    serve = None
+    if rank == 0 and world == 1 and not args.no_serve and args.workload == "rbc-4m":
+        serve = serve_leg(args.serve_requests, args.load, args.budget_gb, args.max_steps)
 
     line = {"metric": METRIC if args.workload == "rbc-4m" else f"particle-steps/s at {args.workload}",
             "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -350,8 +412,8 @@ def run_ours(args, rank, world):
                        "rebuild_every": 1, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (resident state, forces and mirrors ~1.4 GB)"},
             "roofline": roof, "kernel_ms_per_launch": breakdown, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clocks.summary(), "step_roofline": step_roof, "fp64_variant": f64, "f32_increment_variant": f32step,
-            "ensemble": ens}
+            "gpu_launches": launches, "clocks": clocks.summary(), "step_roofline": step_roof, "pair_roofline": pair_roof, "fp64_variant": f64,
+            "f32_increment_variant": f32step, "skin_cadence_variant": cadence, "ensemble": ens, "serve": serve}
     return line
 
 
@@ -409,7 +471,8 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-KERNEL_REV = "pairs-v12"
+# revisions of the kernels whose ncu summaries are committed under profiles/
+KERNEL_REV = {"k_pair_search": "search-v1", "k_pair_eval": "eval-v1", "k_baoa_d": "baoa-d-v1"}
 
 
 def ensemble_jobs(n_instances: int, steps: int):
@@ -457,16 +520,8 @@ def run_serving(args):
     """Served request stream: Poisson arrivals at load x the plain form's
     measured throughput, continuous batching against FIFO one-at-a-time."""
     import numpy as np
-    import paper_1701_02059_gb300 as G
     from paper_1701_02059_gb300 import serving
-    from synth import membranes as M
-    reqs = M.request_stream(n_requests=args.requests, rate_per_s=1.0, seed=4)
-    jobs = []
-    for i, r in enumerate(reqs):
-        m = r["build"]()
-        p = G.make_params(kT=m.kT, n_centroids=m.n_centroids, box=m.box, periodic=m.periodic, seed=40_000 + i,
-                          instance=i)
-        jobs.append({"params": p, "mem": m, "steps": r["steps"], "arrival_s": 0.0})
+    reqs, jobs = serve_jobs(args.requests)
     # plain form: measured service times, then FIFO against the arrivals
     recp, sp, _ = serving.serve_plain(jobs)
     services = [r["service_s"] for r in recp]
@@ -499,6 +554,63 @@ def run_serving(args):
             "gpu_launches": sb["gpu_launches"]}
 
 
+def serve_jobs(n_requests: int):
+    """The served-stream requests (Poisson order, sizes log-uniform in
+    [10k, 1M] particles, steps in {100..2000})."""
+    import paper_1701_02059_gb300 as G
+    from synth import membranes as M
+    reqs = M.request_stream(n_requests=n_requests, rate_per_s=1.0, seed=4)
+    jobs = []
+    for i, r in enumerate(reqs):
+        m = r["build"]()
+        p = G.make_params(kT=m.kT, n_centroids=m.n_centroids, box=m.box, periodic=m.periodic, seed=40_000 + i,
+                          instance=i)
+        jobs.append({"params": p, "mem": m, "steps": r["steps"], "arrival_s": 0.0})
+    return reqs, jobs
+
+
+def serve_leg(n_requests: int, load: float, budget_gb: float, max_steps: int):
+    """Served stream inside the default run: Poisson arrivals at load x the
+    plain form's measured throughput; continuous batching at the full HBM
+    budget and at a budget below the resident peak that pass reached (so
+    that admission waits for memory), against the first-come-first-served
+    plain server."""
+    import numpy as np
+    from paper_1701_02059_gb300 import serving
+    reqs, jobs = serve_jobs(n_requests)
+    recp, sp, _ = serving.serve_plain(jobs)
+    services = [r["service_s"] for r in recp]
+    C = sp["particle_steps_per_s"]
+    mean_work = float(np.mean([j["mem"].n * j["steps"] for j in jobs]))
+    rate = load * C / mean_work
+    arrivals = [r["arrival_s"] / rate for r in reqs]
+    for j, a in zip(jobs, arrivals):
+        j["arrival_s"] = a
+    lat_p = serving.fifo(services, arrivals)
+    span_p = float(np.max(np.asarray(arrivals) + lat_p))
+    work = sum(j["mem"].n * j["steps"] for j in jobs)
+    keep = ("p50_s", "p99_s", "makespan_s", "particle_steps_per_s", "busy_particle_steps_per_s", "repacks",
+            "batched_steps", "peak_reserved_bytes", "largest_request_bytes", "budget_refusals")
+    _, full, _ = serving.serve_batched(jobs, int(budget_gb * 2**30), max_steps=max_steps)
+    # a budget that binds: half the resident peak of the first pass, and no
+    # less than twice the largest request (admission reserves an instance's
+    # arrays, half as much again for its set-up, and its carried copy)
+    tight = max(int(0.5 * full["peak_reserved_bytes"]), int(2.0 * full["largest_request_bytes"]))
+    _, bound, _ = serving.serve_batched(jobs, tight, max_steps=max_steps)
+    plain = {"p50_s": round(float(np.percentile(lat_p, 50)), 4), "p99_s": round(float(np.percentile(lat_p, 99)), 4),
+             "makespan_s": round(span_p, 4), "particle_steps_per_s": round(work / span_p, 1),
+             "busy_particle_steps_per_s": round(C, 1)}
+    rnd = lambda d: {k: (round(d[k], 4) if isinstance(d[k], float) else d[k]) for k in keep}
+    return {"requests": len(jobs), "particles": sum(j["mem"].n for j in jobs), "particle_steps": work,
+            "rate_per_s": round(rate, 4), "load": load, "max_steps_per_launch": max_steps,
+            "batched": rnd(full) | {"hbm_budget_gb": budget_gb},
+            "batched_tight": rnd(bound) | {"hbm_budget_gb": round(tight / 2**30, 3),
+                                           "budget_bound": bool(bound["budget_refusals"] > 0)},
+            "plain_fifo": plain,
+            "p99_speedup": round(plain["p99_s"] / full["p99_s"], 3),
+            "timing": "wall clock from arrival to retirement, host arrays in and out"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -512,7 +624,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-vs-plain ensemble comparison")
     ap.add_argument("--no-f64", action="store_true", help="skip the FP64-everywhere variant")
-    ap.add_argument("--no-variants", action="store_true", help="skip the FP32-increment variant")
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP32-increment and skin-cadence variants")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-stream leg")
+    ap.add_argument("--serve-requests", type=int, default=32, help="requests of the served-stream leg")
     ap.add_argument("--ensemble-steps", type=int, default=500)
     ap.add_argument("--requests", type=int, default=32, help="served-stream requests (workload serve)")
     ap.add_argument("--load", type=float, default=0.8, help="arrival rate / plain-form throughput (workload serve)")

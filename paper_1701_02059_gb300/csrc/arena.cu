@@ -231,6 +231,19 @@ struct ArenaSlot {
     std::unique_ptr<Snapshot> snap;   // carried state while pending or finished
 };
 
+// Device bytes that the set-up of one instance in a batch of one allocates
+// whatever its geometry: per particle the state in two buffers (192),
+// types and ids (10), cell and slot maps (8), forces, torques and the wide
+// side array (96), mirrors (64), sort scratch, bounds and ranks (17) and the
+// neighbour lists (132); per cell the neighbour rows at their fixed stride
+// of 64 (4,096) and the per-cell arrays (258).  A lower bound of
+// Ensemble::bytes_allocated(): the centroid grid, the bond lists and
+// allocation rounding come on top.
+static size_t instance_bytes_lower_bound(const HostInstance& h) {
+    const size_t n = (size_t)h.n, K = (size_t)std::max(h.prm.n_centroids, 1);
+    return n * 519 + K * 4354;
+}
+
 class Arena {
 public:
     Arena(size_t budget, int precision, cudaStream_t st, bool own) :
@@ -254,6 +267,12 @@ public:
         if (h.prm.precision != precision_) throw ArgError("instance precision differs from the arena's");
         if (h.prm.rebuild_every != 1) throw ArgError("arena instances rebuild their cells every step");
         if (h.prm.n_centroids > (int)h.n) throw ArgError("more centroids than particles");
+        // refuse from the sizes alone, before any device allocation, when the
+        // arrays every set-up allocates already exceed the budget (the same
+        // test as after the set-up, on a lower bound of its bytes); the exact
+        // check follows the set-up
+        const size_t lb = instance_bytes_lower_bound(h);
+        if (reserved() + lb + lb / 2 > budget_) throw CudaError(cudaErrorMemoryAllocation, "over the HBM budget");
         // a batch of one initialises the instance exactly as a plain system does
         auto snap = std::make_unique<Snapshot>();
         size_t bytes = 0;

@@ -816,7 +816,11 @@ __global__ void __launch_bounds__(kPairThreads, 7)
                     l = d.cell;
                     st = d.start;
                     c = d.cnt;
-                    if (na_off == 0 && it0 == cs) rowoff[(size_t)k * kAdjRow + nn] = make_int4(d.ox, d.oy, d.oz, 0);
+                    // each row's exact offset, written where the row is first
+                    // staged (lane 0 of a pass that continues a split row
+                    // was written in the pass before)
+                    if (it0 == cs && !(lane == 0 && na_off > 0))
+                        rowoff[(size_t)k * kAdjRow + nn] = make_int4(d.ox, d.oy, d.oz, 0);
                     if (lane == 0) { st += na_off; c -= na_off; }
                 }
                 int incl = c;

@@ -38,12 +38,14 @@ def serve_batched(jobs, hbm_budget_bytes: int, max_steps: int = 50, graphs: bool
     t0 = time.perf_counter()
     work = 0
     spent = {"admit_s": 0.0, "run_s": 0.0, "retire_s": 0.0, "idle_s": 0.0}
+    mem_stats = {"peak_reserved_bytes": 0, "largest_request_bytes": 0, "budget_refusals": 0}
     while waiting or slot_job:
         now = time.perf_counter() - t0
         # admit everything that has arrived, in arrival order, while it fits
         while waiting and jobs[waiting[0]]["arrival_s"] <= now:
             i = waiting[0]
             ta = time.perf_counter()
+            before = arena.info()["bytes"]
             try:
                 s = arena.admit(jobs[i]["params"], jobs[i]["mem"], jobs[i]["steps"])
                 spent["admit_s"] += time.perf_counter() - ta
@@ -51,9 +53,13 @@ def serve_batched(jobs, hbm_budget_bytes: int, max_steps: int = 50, graphs: bool
                 spent["admit_s"] += time.perf_counter() - ta
                 if e.code != ORBC_E_NOMEM:
                     raise
+                mem_stats["budget_refusals"] += 1
                 if not slot_job:
                     raise RuntimeError(f"request {i} does not fit the HBM budget on an empty GPU") from e
                 break
+            after = arena.info()["bytes"]
+            mem_stats["peak_reserved_bytes"] = max(mem_stats["peak_reserved_bytes"], after)
+            mem_stats["largest_request_bytes"] = max(mem_stats["largest_request_bytes"], after - before)
             slot_job[s] = i
             waiting.pop(0)
             rec[i] = {"arrival_s": jobs[i]["arrival_s"], "admitted_s": time.perf_counter() - t0}
@@ -89,6 +95,7 @@ def serve_batched(jobs, hbm_budget_bytes: int, max_steps: int = 50, graphs: bool
     summary.update({k: round(v, 3) for k, v in spent.items()})
     summary.update({"repack_s": round(inner["repack_s"], 3), "repacks": inner["repacks"],
                     "batched_steps": inner["steps"]})
+    summary.update(mem_stats)
     return rec, summary, states
 
 

@@ -128,6 +128,27 @@ def test_split_pair_path_equals_one_launch_path(initialised):
     assert np.array_equal(F1, F2) and np.array_equal(T1, T2)
 
 
+@pytest.mark.parametrize("K", [6, 12])
+def test_split_pair_path_with_split_staging(K):
+    """Few, large cells (about 300-600 particles each) make every
+    neighbourhood larger than the search and evaluation stages, so rows are
+    staged over several passes, some split between two passes: forces from
+    the split path equal the one-launch kernel's bit for bit, and stay so
+    over rebuilding steps."""
+    mem = M.vesicle(3000, 5, f=2, chain_beads=5, n_centroids=K)
+    g = G.System(gpu_params(mem))
+    g.load_membrane(mem)
+    g.init_cells()
+    for _ in range(3):
+        g.compute_forces(energies=True)
+        F1, T1 = g.forces()
+        g.compute_forces()
+        F2, T2 = g.forces()
+        assert np.array_equal(F1, F2) and np.array_equal(T1, T2)
+        g.integrate(5)
+    g.close()
+
+
 def test_rebuilds_bit_exact(initialised):
     _, mem, g, m, o = initialised
     for _ in range(3):

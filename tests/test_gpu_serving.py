@@ -41,14 +41,20 @@ def test_served_results_equal_alone():
 
 def test_tight_budget_queues_requests_and_still_serves_them():
     js = jobs()
-    # room for the largest request and a little more: the others wait for it
+    # room for the largest request and a little more (admission reserves
+    # an instance's arrays half as much again for its set-up): the others
+    # wait for it
     probe = G.Arena(8 << 30)
     need = []
     for j in js:
         s = probe.admit(j["params"], j["mem"], 1)
         need.append(probe.info()["bytes"] - sum(need))
     probe.close()
-    rec, summary, states = serving.serve_batched(js, int(max(need) * 1.2), max_steps=4, keep_states=True)
+    budget = int(max(need) * 1.6)
+    assert budget < sum(need)
+    for j in js:
+        j["arrival_s"] = 0.0     # all at once: only the budget holds them back
+    rec, summary, states = serving.serve_batched(js, budget, max_steps=4, keep_states=True)
     _, _, alone = serving.serve_plain(js, keep_states=True)
     for i in range(len(js)):
         assert np.array_equal(states[i]["pos"], alone[i]["pos"])
@@ -56,3 +62,4 @@ def test_tight_budget_queues_requests_and_still_serves_them():
     # after an earlier one had finished and freed its memory
     first_done = min(r["done_s"] for r in rec)
     assert sum(r["admitted_s"] < first_done for r in rec) < len(js)
+    assert summary["budget_refusals"] >= 1 and summary["peak_reserved_bytes"] <= budget

@@ -70,6 +70,9 @@ class _FakeArena:
     def launch_count(self):
         return 0
 
+    def info(self):
+        return {"resident": len(self.left), "pending": 0, "done": 0, "particles": 0, "bytes": self.used}
+
     def stats(self):
         return {"repack_s": 0.0, "repacks": 0, "steps": 0}
 
@@ -99,6 +102,11 @@ def test_batched_loop_under_a_binding_budget(monkeypatch):
     # admissions after the first two wait for a retirement
     first_retire = next(k for k, e in enumerate(_FakeArena.log) if e[0] == "retire")
     assert sum(1 for e in _FakeArena.log[:first_retire] if e[0] == "admit") == 2
+    # the summary reports the budget binding: refused admissions, the peak
+    # reserved bytes at the budget and the largest single request
+    assert summary["budget_refusals"] >= 1
+    assert summary["peak_reserved_bytes"] == 2 * per
+    assert summary["largest_request_bytes"] == per
 
 
 def test_request_larger_than_the_budget_is_refused(monkeypatch):
