@@ -1079,12 +1079,16 @@ __global__ void __launch_bounds__(128, 5)
     for (int a = 0; a < 3; a++) { af[a].zero(); at[a].zero(); }
     int nterm = 0;
     bool big = false;
+    // the next list entry is in flight while a pair is evaluated; the
+    // mirrors are read through the read-only data path
+    int e_next = n > 0 ? __ldcs(nlist + q) : 0;
     for (int t = 0; t < n; t++) {
-        const int e = __ldcs(nlist + (size_t)t * N + q);
+        const int e = e_next;
+        if (t + 1 < n) e_next = __ldcs(nlist + (size_t)(t + 1) * N + q);
         const int qj = e & ((1 << kRowShift) - 1);
-        const int4 o = ro[(unsigned)e >> kRowShift];
-        const int4 mj = v.mqr[qj];
-        const float4 oj = v.mor[qj];
+        const int4 o = __ldg(ro + ((unsigned)e >> kRowShift));
+        const int4 mj = __ldg(v.mqr + qj);
+        const float4 oj = __ldg(v.mor + qj);
         const int tj = mj.w & 0xff;
         const bool ll = (ti == kLipid) && (tj == kLipid);
         const int cls = ll ? 0 : ((ti == kLipid || tj == kLipid) ? 1 : 2);
