@@ -259,6 +259,19 @@ ORBC_API int orbc_cell_sort(const int* d_cell, int n, int K, int* d_perm, int* d
 ORBC_API int orbc_cell_sort_noalloc(const int* d_cell, int n, int K, int* d_perm, int* d_cell_start,
                                     void* cuda_stream);
 
+/* Test of the bounded waits (no counterpart in the paper).  Every wait of a
+ * kernel on its shared-memory staging barrier gives up after a number of
+ * polls (2^22 by default, well over a second), records a timeout that the
+ * call returns as ORBC_E_TIMEOUT, waits (bounded again) for its copies and
+ * leaves the kernel.  extra_tx_bytes (a multiple of 16, at most 4096; 0 in
+ * normal use) makes each staging barrier expect that many bytes more than
+ * the copies bring, so every copy lands but the barrier never completes and
+ * the wait runs out; max_polls (1 .. 2^22) sets the limit.  The pair kernels
+ * of the handle's next calls use these settings; orbc_set_wait_test(s, 0,
+ * 1 << 22) restores normal operation.  A call that timed out leaves the
+ * forces of that call invalid and the handle usable.  Errors: ORBC_E_ARG. */
+ORBC_API int orbc_set_wait_test(orbc_system* s, unsigned extra_tx_bytes, unsigned max_polls);
+
 /* Number of CUDA kernels this handle has launched since creation. */
 ORBC_API int orbc_get_launch_count(orbc_system* s, long long* count);
 
@@ -321,16 +334,26 @@ ORBC_API int orbc_arena_admit(orbc_arena* a, const orbc_params* params, int n, c
  * left) steps (use_graphs != 0: replay of a captured step).  Instances that
  * reach their step count leave the batch and become finished.  *steps_done
  * (nullable) receives s (0 when nothing is resident).
- * Errors: ORBC_E_NAN / ORBC_E_TIMEOUT from the device status, ORBC_E_ARG
- * (max_steps < 1), ORBC_E_STATE, ORBC_E_CUDA. */
+ * An instance whose own data raises a device flag during the call (non-
+ * finite or out-of-range pair or bond terms, a particle beyond the mirror
+ * range of its cell, a cell with more than 64 neighbouring cells) fails
+ * alone: it is reported by orbc_arena_poll, leaves the batch, and
+ * orbc_arena_retire returns its error; the other instances advance exactly
+ * as they would alone and the call returns ORBC_OK.  Failures are detected
+ * at the end of the call, so a failed instance may have stepped on garbage
+ * for up to max_steps steps; a small max_steps narrows that.
+ * Errors: ORBC_E_TIMEOUT and the shared neighbour-list overflow (ORBC_E_STATE)
+ * fail the whole call; ORBC_E_ARG (max_steps < 1), ORBC_E_CUDA. */
 ORBC_API int orbc_arena_run(orbc_arena* a, int max_steps, int use_graphs, int* steps_done);
 
-/* Finished slots: up to cap slot numbers into done_slots, their count into
- * *ndone.  Errors: ORBC_E_ARG. */
+/* Finished or failed slots: up to cap slot numbers into done_slots, their
+ * count into *ndone.  Errors: ORBC_E_ARG. */
 ORBC_API int orbc_arena_poll(orbc_arena* a, int* done_slots, int cap, int* ndone);
 
 /* Copies a finished instance's state out in id order (pos, vel, ori, angvel:
- * [n][3], each nullable; step: nullable) and frees its slot and memory.
+ * [n][3], each nullable; step: nullable) and frees its slot and memory.  For
+ * a failed slot it copies nothing, frees the slot and returns the failure
+ * (ORBC_E_NAN for non-finite or out-of-range terms, ORBC_E_STATE otherwise).
  * Errors: ORBC_E_ARG (slot not finished), ORBC_E_CUDA. */
 ORBC_API int orbc_arena_retire(orbc_arena* a, int slot, double* pos, double* vel, double* ori, double* angvel,
                                long long* step);

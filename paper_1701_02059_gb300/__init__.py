@@ -220,6 +220,11 @@ class System:
     def set_timing(self, on: bool):
         self._check(self._L.orbc_set_timing(self._h, 1 if on else 0), "orbc_set_timing")
 
+    def set_wait_test(self, extra_tx_bytes: int = 0, max_polls: int = 1 << 22):
+        """orbc_set_wait_test: make the staging waits run out (test of the
+        bounded waits); (0, 1 << 22) is normal operation."""
+        self._check(self._L.orbc_set_wait_test(self._h, int(extra_tx_bytes), int(max_polls)), "orbc_set_wait_test")
+
     def launch_count(self) -> int:
         c = C.c_longlong(0)
         self._check(self._L.orbc_get_launch_count(self._h, C.byref(c)), "orbc_get_launch_count")

@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "ORBC_OK", -1: "ORBC_E_ARG", -2: "ORBC_E_NOMEM", -3: "ORBC_E_
 EXPORTS = [
     "orbc_default_params", "orbc_create", "orbc_set_particles", "orbc_set_bonds", "orbc_init_cells",
     "orbc_rebuild_cells", "orbc_compute_forces", "orbc_integrate", "orbc_get_state", "orbc_get_forces",
-    "orbc_get_cells", "orbc_get_adjacency_len", "orbc_dump_pairs", "orbc_set_timing", "orbc_get_kernel_times",
+    "orbc_get_cells", "orbc_get_adjacency_len", "orbc_dump_pairs", "orbc_set_timing", "orbc_set_wait_test", "orbc_get_kernel_times",
     "orbc_get_launch_count", "orbc_last_error", "orbc_destroy", "orbc_cell_sort", "orbc_cell_sort_noalloc",
     "orbc_arena_create", "orbc_arena_admit", "orbc_arena_run", "orbc_arena_poll", "orbc_arena_retire",
     "orbc_arena_info", "orbc_arena_launch_count", "orbc_arena_last_error", "orbc_arena_destroy",
@@ -77,6 +77,7 @@ def load(path: str | None = None):
     L.orbc_get_adjacency_len.argtypes = [V, C.POINTER(C.c_longlong)]
     L.orbc_dump_pairs.argtypes = [V, C.c_longlong, V, C.POINTER(C.c_longlong)]
     L.orbc_set_timing.argtypes = [V, C.c_int]
+    L.orbc_set_wait_test.argtypes = [V, C.c_uint, C.c_uint]
     L.orbc_get_kernel_times.argtypes = [V, C.c_char_p, C.c_int, V, C.c_int, C.POINTER(C.c_int)]
     L.orbc_get_launch_count.argtypes = [V, C.POINTER(C.c_longlong)]
     L.orbc_cell_sort.argtypes = [V, C.c_int, C.c_int, V, V, V]

@@ -93,6 +93,9 @@ View Ensemble::view() {
     v.bptr = d_bptr; v.bpartner = d_bpartner;
     v.nbond = nbond; v.bij = d_bij; v.binst = d_binst; v.bkf = d_bkf; v.bkd = d_bkd;
     v.status = d_status;
+    v.istatus = d_istatus;
+    v.wait_polls = wait_polls;
+    v.extra_tx = extra_tx;
     return v;
 }
 
@@ -107,10 +110,21 @@ void Ensemble::swap_state() { cur_ ^= 1; }
 
 void Ensemble::sync() { CK(cudaStreamSynchronize(stream)); }
 
+// Per-instance flags of the launches since the last clear.
+std::vector<unsigned> Ensemble::read_instance_status(bool clear) {
+    std::vector<unsigned> s(B, 0u);
+    CK(cudaMemcpyAsync(s.data(), d_istatus, sizeof(unsigned) * B, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    if (clear) CK(cudaMemsetAsync(d_istatus, 0, sizeof(unsigned) * B, stream));
+    return s;
+}
+
 unsigned Ensemble::read_status(bool clear) {
     unsigned s = 0;
     CK(cudaMemcpyAsync(&s, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
+    // a flagged launch may have left the neighbour lists partial
+    if (s) list_valid = false;
     if (clear && s) CK(cudaMemsetAsync(d_status, 0, sizeof(unsigned), stream));
     return s;
 }
@@ -229,6 +243,7 @@ void Ensemble::alloc_core(const std::vector<int>& p0, const std::vector<int>& k0
     d_gcf = alloc<float4>(Ktot);
     d_gidx = alloc<int>(Ktot);
     d_status = alloc<unsigned>(1);
+    d_istatus = alloc<unsigned>(B);
     d_S = alloc<long long>((size_t)3 * Ktot);
     d_msum = alloc<long long>((size_t)3 * Ktot);   // zeroed by alloc, re-zeroed by each use
     d_mcnt = alloc<int>(Ktot);
@@ -1032,6 +1047,7 @@ int orbc_compute_forces(orbc_system* s, double* energies_out) {
         sync_device(s);
         s->ens->compute_forces(energies_out != nullptr);
         st = s->ens->read_status(true);
+        if (st) s->ens->forces_valid = false;
         if (!st && energies_out) {
             std::vector<double> e;
             s->ens->energies(e);
@@ -1051,6 +1067,7 @@ int orbc_integrate(orbc_system* s, int nsteps) {
         s->host_stale = true;
         s->ens->integrate(nsteps);
         st = s->ens->read_status(true);
+        if (st) s->ens->forces_valid = false;
     });
     if (rc == ORBC_OK && st) return fail(s, status_code(st), "device status " + std::to_string(st));
     return rc;
@@ -1139,6 +1156,14 @@ int orbc_dump_pairs(orbc_system* s, long long cap, unsigned* pairs, long long* n
         sync_device(s);
         *npairs = s->ens->dump_pairs(0, cap, pairs);
     });
+}
+
+int orbc_set_wait_test(orbc_system* s, unsigned extra_tx_bytes, unsigned max_polls) {
+    if (!s || max_polls < 1 || max_polls > (1u << 22) || extra_tx_bytes > 4096 || (extra_tx_bytes % 16) != 0)
+        return ORBC_E_ARG;
+    s->ens->extra_tx = extra_tx_bytes;
+    s->ens->wait_polls = max_polls;
+    return ORBC_OK;
 }
 
 int orbc_set_timing(orbc_system* s, int on) {

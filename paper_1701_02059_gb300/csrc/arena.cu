@@ -221,8 +221,12 @@ void Ensemble::integrate_graph(int nsteps) {
 
 // ---------------------------------------------------------------- arena
 struct ArenaSlot {
-    enum { kFree = 0, kPending = 1, kResident = 2, kDone = 3 };
+    // kFailed: the instance's own data raised a device flag (non-finite or
+    // out-of-range forces, a particle beyond its cell's mirror range, ...);
+    // it left the batch, the others continue
+    enum { kFree = 0, kPending = 1, kResident = 2, kDone = 3, kFailed = 4 };
     int state = kFree;
+    unsigned status = 0;     // the flags that failed it
     long long target = 0, done = 0;
     size_t bytes = 0;       // packed arrays of a batch of one + one snapshot
     long long n = 0;
@@ -324,11 +328,28 @@ public:
         else batch_->integrate((int)s);
         const unsigned st = batch_->read_status(true);
         if (st) {
-            last_status_ = st;
-            throw StateError("device status " + std::to_string(st));
+            // flags that belong to single instances fail those instances
+            // only: they leave the batch at the next re-pack and the others,
+            // which never read another instance's data, have advanced
+            // exactly as alone; anything else fails the whole call
+            const std::vector<unsigned> ist = batch_->read_instance_status(true);
+            bool attributed = false;
+            for (unsigned x : ist) attributed |= (x != 0u);
+            if ((st & ~kStatusPerInstance) || !attributed) {
+                last_status_ = st;
+                throw StateError("device status " + std::to_string(st));
+            }
+            for (int b = 0; b < (int)batch_slot_.size(); b++)
+                if (ist[b]) {
+                    ArenaSlot& S = slots_[batch_slot_[b]];
+                    S.state = ArenaSlot::kFailed;
+                    S.status = ist[b];
+                    dirty_ = true;
+                }
         }
         for (int b = 0; b < (int)batch_slot_.size(); b++) {
             ArenaSlot& S = slots_[batch_slot_[b]];
+            if (S.state == ArenaSlot::kFailed) continue;
             S.done += s;
             if (S.done >= S.target) {
                 S.snap = std::make_unique<Snapshot>();
@@ -352,7 +373,7 @@ public:
     void poll(int* out, int cap, int* ndone) const {
         int k = 0;
         for (int i = 0; i < (int)slots_.size(); i++)
-            if (slots_[i].state == ArenaSlot::kDone) {
+            if (slots_[i].state == ArenaSlot::kDone || slots_[i].state == ArenaSlot::kFailed) {
                 if (out && k < cap) out[k] = i;
                 k++;
             }
@@ -360,6 +381,18 @@ public:
     }
 
     void retire(int slot, double* pos, double* vel, double* ori, double* angvel, long long* step) {
+        if (slot >= 0 && slot < (int)slots_.size() && slots_[slot].state == ArenaSlot::kFailed) {
+            // a failed instance has no state to copy out: free its slot and
+            // report its flags
+            ArenaSlot& S = slots_[slot];
+            const unsigned st = S.status;
+            S.snap.reset();
+            S.state = ArenaSlot::kFree;
+            S.bytes = 0;
+            S.status = 0;
+            last_status_ = st;
+            throw StateError("instance failed with device status " + std::to_string(st));
+        }
         if (slot < 0 || slot >= (int)slots_.size() || slots_[slot].state != ArenaSlot::kDone)
             throw ArgError("slot is not finished");
         ArenaSlot& S = slots_[slot];
@@ -389,7 +422,7 @@ public:
         for (auto& x : slots_) {
             if (x.state == ArenaSlot::kResident) { r++; np += x.n; }
             if (x.state == ArenaSlot::kPending) p++;
-            if (x.state == ArenaSlot::kDone) d++;
+            if (x.state == ArenaSlot::kDone || x.state == ArenaSlot::kFailed) d++;
         }
         if (resident) *resident = r;
         if (pending) *pending = p;
@@ -526,7 +559,10 @@ int orbc_arena_poll(orbc_arena* h, int* done_slots, int cap, int* ndone) {
 int orbc_arena_retire(orbc_arena* h, int slot, double* pos, double* vel, double* ori, double* angvel,
                       long long* step) {
     if (!h) return ORBC_E_ARG;
-    return guarded_call(&h->err, [&] { h->a->retire(slot, pos, vel, ori, angvel, step); });
+    h->a->last_status_ = 0;
+    int rc = guarded_call(&h->err, [&] { h->a->retire(slot, pos, vel, ori, angvel, step); });
+    if (rc == ORBC_E_STATE && h->a->last_status_) return status_code(h->a->last_status_);
+    return rc;
 }
 
 int orbc_arena_info(const orbc_arena* h, int* resident, int* pending, int* done, long long* particles,

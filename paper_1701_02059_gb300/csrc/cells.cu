@@ -551,7 +551,7 @@ __device__ void estep_one(const View& v, int i, int* __restrict__ cell_out, floa
         });
     }
     if (ncand == 0) {   // unreachable for finite input: the search covers every centroid
-        atomicOr(v.status, kStatusGridRange);
+        flag_inst(v, I, kStatusGridRange);
         cell_out[i] = I.k0;
         if (lbound) lbound[i] = 0.f;
         return;
@@ -681,7 +681,7 @@ __global__ void k_estep_warp(View v, int* __restrict__ cell_out, float* __restri
         if (amb) bk = bk64;
     }
     if (valid) {
-        if (bk < 0) { atomicOr(v.status, kStatusGridRange); bk = I.k0; }
+        if (bk < 0) { flag_inst(v, I, kStatusGridRange); bk = I.k0; }
         cell_out[i] = bk;
         if (lbound) lbound[i] = amb ? 0.f : fminf(sqrtf(second), lbr);
     }
@@ -1040,10 +1040,19 @@ __global__ void k_segrank_list(const int* __restrict__ start, const int* __restr
 }
 
 // ============================================================== gather + mirrors
-__device__ inline int mirror_coord(long long xq, long long cq, const Inst& I, int a, unsigned* status) {
-    long long d = minimg_q(xq - cq, I.boxq[a], I.periodic[a]);
+// The mirrors hold x - c~ at 2^-26 sigma, where c~ is the centroid rounded to
+// a multiple of 2^-26 sigma: then round(x - c~) = round(x) - c~ exactly, and
+// a pair's integer displacement m_j + (c~_l - c~_k) - m_i depends on the two
+// positions alone (and, on a periodic axis, on the image), not on which
+// cells hold them, so FP32 pair forces do not change when the cell list is
+// rebuilt.
+__device__ inline long long mirror_ref(long long c) {
+    return ((c + (1ll << (kMirrorShift - 1))) >> kMirrorShift) << kMirrorShift;
+}
+__device__ inline int mirror_coord(long long xq, long long cq, const Inst& I, int a, const View& v) {
+    long long d = minimg_q(xq - mirror_ref(cq), I.boxq[a], I.periodic[a]);
     long long r = (d + (1ll << (kMirrorShift - 1))) >> kMirrorShift;
-    if (r > 2147483647ll || r < -2147483647ll) { atomicOr(status, kStatusMirrorRange); r = 0; }
+    if (r > 2147483647ll || r < -2147483647ll) { flag_inst(v, I, kStatusMirrorRange); r = 0; }
     return (int)r;
 }
 
@@ -1083,9 +1092,9 @@ __global__ void __launch_bounds__(256) k_gather_particles(View v, View o, const 
     v.cell[p] = k;
     v.slot_of_id[I.p0 + id] = p;
     int4 m;
-    m.x = mirror_coord(x[0], v.cq[k], I, 0, v.status);
-    m.y = mirror_coord(x[1], v.cq[(size_t)v.Ktot + k], I, 1, v.status);
-    m.z = mirror_coord(x[2], v.cq[(size_t)2 * v.Ktot + k], I, 2, v.status);
+    m.x = mirror_coord(x[0], v.cq[k], I, 0, v);
+    m.y = mirror_coord(x[1], v.cq[(size_t)v.Ktot + k], I, 1, v);
+    m.z = mirror_coord(x[2], v.cq[(size_t)2 * v.Ktot + k], I, 2, v);
     m.w = t;
     v.mq[p] = m;
     float4 no;
@@ -1241,9 +1250,9 @@ __global__ void k_mirrors(View v) {
     int b = find_inst(v.inst_p0, v.B, p);
     const Inst& I = v.inst[b];
     int4 m;
-    m.x = mirror_coord(v.xq[p], v.cq[c], I, 0, v.status);
-    m.y = mirror_coord(v.xq[N + p], v.cq[(size_t)v.Ktot + c], I, 1, v.status);
-    m.z = mirror_coord(v.xq[2 * N + p], v.cq[(size_t)2 * v.Ktot + c], I, 2, v.status);
+    m.x = mirror_coord(v.xq[p], v.cq[c], I, 0, v);
+    m.y = mirror_coord(v.xq[N + p], v.cq[(size_t)v.Ktot + c], I, 1, v);
+    m.z = mirror_coord(v.xq[2 * N + p], v.cq[(size_t)2 * v.Ktot + c], I, 2, v);
     m.w = v.type[p];
     float4 no;
     no.x = ll_to_float(v.nq[p]) * (float)kGridInv;
@@ -1374,7 +1383,7 @@ __global__ void __launch_bounds__(256, 6) k_adj_warp(View v, const unsigned long
     __syncwarp();
     int n = rown[wb];
     if (n > kAdjRow) {
-        if (lane == 0) atomicOr(v.status, kStatusAdjOverflow);
+        if (lane == 0) flag_inst(v, I, kStatusAdjOverflow);
         n = kAdjRow;
     }
     // ascending row: every entry goes to its rank (entries are distinct)
@@ -1389,9 +1398,11 @@ __global__ void __launch_bounds__(256, 6) k_adj_warp(View v, const unsigned long
         if (lane + 32 * u >= n) continue;
         const int j = val[u];
         pad[(size_t)k * kAdjRow + rk[u]] = j;
-        const long long dx = minimg_q(v.cq[j] - cx, I.boxq[0], I.periodic[0]);
-        const long long dy = minimg_q(v.cq[(size_t)v.Ktot + j] - cy, I.boxq[1], I.periodic[1]);
-        const long long dz = minimg_q(v.cq[(size_t)2 * v.Ktot + j] - cz, I.boxq[2], I.periodic[2]);
+        // exact offset between the mirrors' reference points (multiples of
+        // 2^-26 sigma; on a periodic axis less the image)
+        const long long dx = minimg_q(mirror_ref(v.cq[j]) - mirror_ref(cx), I.boxq[0], I.periodic[0]);
+        const long long dy = minimg_q(mirror_ref(v.cq[(size_t)v.Ktot + j]) - mirror_ref(cy), I.boxq[1], I.periodic[1]);
+        const long long dz = minimg_q(mirror_ref(v.cq[(size_t)2 * v.Ktot + j]) - mirror_ref(cz), I.boxq[2], I.periodic[2]);
         AdjDesc d;
         d.start = v.cell_start[j];
         d.cnt = v.cell_start[j + 1] - d.start;

@@ -150,6 +150,7 @@ public:
     void adjacency_csr();
     long long dump_pairs(int b, long long cap, unsigned* pairs);
     unsigned read_status(bool clear);
+    std::vector<unsigned> read_instance_status(bool clear);
     void sync();
 
     // timing of individual kernels (CUDA events on the stream)
@@ -245,7 +246,10 @@ public:
     int* d_binst = nullptr;
     float2* d_bkf = nullptr;
     double2* d_bkd = nullptr;
+    unsigned wait_polls = 1u << 22;          // bounded staging waits (see View)
+    unsigned extra_tx = 0;
     unsigned* d_status = nullptr;
+    unsigned* d_istatus = nullptr;           // [B] flags raised by one instance's data
     long long* d_S = nullptr;
     long long* d_msum = nullptr;   // [3][Ktot] M-step sums from the B-A-O-A launch (zero between uses)
     int* d_mcnt = nullptr;         // [Ktot] lipids per cell, same

@@ -239,7 +239,8 @@ template <> struct Acc<float> {
         if (mag < 1000.0f) { s[0].add(x); s[1].add(y); s[2].add(z); n++; return; }
         // NaN, infinite, or a term beyond the range the 2^-32 fixed-point
         // sums hold (|component| < 2^31 after a few hundred terms)
-        if (!(mag < kMaxTerm)) atomicOr(v.status, (mag == mag) ? kStatusPairForceRange : kStatusNaN);
+        if (!(mag < kMaxTerm))
+            flag_inst(v, v.inst[find_inst(v.inst_p0, v.B, p)], (mag == mag) ? kStatusPairForceRange : kStatusNaN);
         const size_t N = v.N;
         atomicAdd((unsigned long long*)&v.Fbig[(size_t)c0 * N + p], (unsigned long long)__float2ll_rn(x * 4294967296.0f));
         atomicAdd((unsigned long long*)&v.Fbig[(size_t)(c0 + 1) * N + p], (unsigned long long)__float2ll_rn(y * 4294967296.0f));
@@ -257,9 +258,10 @@ template <> struct Acc<double> {
     int np, nb;
     __device__ void zero() { for (int a = 0; a < 3; a++) { f[a] = 0; t[a] = 0; } np = 0; nb = 0; }
     __device__ static long long q(double v) { return __double2ll_rn(v * 4294967296.0); }
-    __device__ void add_pair(const View& v, int, double fx, double fy, double fz, double tx, double ty, double tz) {
+    __device__ void add_pair(const View& v, int p, double fx, double fy, double fz, double tx, double ty, double tz) {
         const double mag = fabs(fx) + fabs(fy) + fabs(fz) + fabs(tx) + fabs(ty) + fabs(tz);
-        if (!(mag < (double)kMaxTerm)) atomicOr(v.status, (mag == mag) ? kStatusPairForceRange : kStatusNaN);
+        if (!(mag < (double)kMaxTerm))
+            flag_inst(v, v.inst[find_inst(v.inst_p0, v.B, p)], (mag == mag) ? kStatusPairForceRange : kStatusNaN);
         f[0] += q(fx); f[1] += q(fy); f[2] += q(fz); t[0] += q(tx); t[1] += q(ty); t[2] += q(tz); np++;
     }
     __device__ void add_bond(const View&, int, double fx, double fy, double fz) { f[0] += q(fx); f[1] += q(fy); f[2] += q(fz); nb++; }
@@ -313,10 +315,12 @@ __device__ inline bool mbar_try_wait(unsigned long long* bar, unsigned phase) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: gives up after ~2^22 polls (with back-off, well over a
-// second), records a timeout in the status word and returns false.
-__device__ inline bool mbar_wait_bounded(unsigned long long* bar, unsigned phase, unsigned* status) {
-    for (unsigned it = 0; it < (1u << 22); it++) {
+// Bounded wait: gives up after `polls` polls (2^22 by default: with the
+// back-off, well over a second), records a timeout in the status word and
+// returns false.
+__device__ inline bool mbar_wait_bounded(unsigned long long* bar, unsigned phase, unsigned* status,
+                                         unsigned polls) {
+    for (unsigned it = 0; it < polls; it++) {
         if (mbar_try_wait(bar, phase)) return true;
         if (it > 64) __nanosleep(256);
     }
@@ -460,7 +464,7 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                     }
                     if (m > 0) {
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        if (lane == 0) mbar_expect_tx(&bar, (unsigned)total * 32u);
+                        if (lane == 0) mbar_expect_tx(&bar, (unsigned)total * 32u + v.extra_tx);
                         __syncwarp();
                         if (staged && take > 0) {
                             bulk_g2s(&sy[excl], v.mqr + st, take * 16u, &bar);
@@ -526,10 +530,10 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
             const int sself = s_self, sslo = s_self_lo, sshi = s_self_hi;
             int selfj = (sslo >= 0 && ivalid) ? sself + (it0 + r - cs) : -1;
             if (selfj < sslo || selfj >= sshi) selfj = -1;
-            bool ok = mbar_wait_bounded(&bar, phase, v.status);
+            bool ok = mbar_wait_bounded(&bar, phase, v.status, v.wait_polls);
             if (__syncthreads_or(!ok)) {
                 // give the copies in flight a second bounded wait, then leave
-                if (ok == false) mbar_wait_bounded(&bar, phase, v.status);
+                if (ok == false) mbar_wait_bounded(&bar, phase, v.status, v.wait_polls);
                 return;
             }
             phase ^= 1u;
@@ -870,7 +874,7 @@ __global__ void __launch_bounds__(kPairThreads, 7)
                 }
                 if (m > 0) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    if (lane == 0) mbar_expect_tx(&bar, (unsigned)total * 16u);
+                    if (lane == 0) mbar_expect_tx(&bar, (unsigned)total * 16u + v.extra_tx);
                     __syncwarp();
                     if (staged && take > 0) bulk_g2s(&sY[excl], v.mqr + st, take * 16u, &bar);
                 }
@@ -917,9 +921,9 @@ __global__ void __launch_bounds__(kPairThreads, 7)
             const int sself = s_self, sslo = s_self_lo, sshi = s_self_hi;
             int selfj = (sslo >= 0 && ivalid) ? sself + (it0 + r - cs) : -1;
             if (selfj < sslo || selfj >= sshi) selfj = -1;
-            bool ok = mbar_wait_bounded(&bar, phase, v.status);
+            bool ok = mbar_wait_bounded(&bar, phase, v.status, v.wait_polls);
             if (__syncthreads_or(!ok)) {
-                if (ok == false) mbar_wait_bounded(&bar, phase, v.status);
+                if (ok == false) mbar_wait_bounded(&bar, phase, v.status, v.wait_polls);
                 return;
             }
             phase ^= 1u;
@@ -1124,7 +1128,7 @@ __global__ void __launch_bounds__(128, 5)
             nterm++;
         } else {
             // terms of 1000 or more go to the int64 side array (exact, rare)
-            if (!(mag < kMaxTerm)) atomicOr(v.status, (mag == mag) ? kStatusPairForceRange : kStatusNaN);
+            if (!(mag < kMaxTerm)) flag_inst(v, I, (mag == mag) ? kStatusPairForceRange : kStatusNaN);
             for (int a = 0; a < 6; a++)
                 atomicAdd((unsigned long long*)&v.Fbig[(size_t)a * N + pi],
                           (unsigned long long)__float2ll_rn(f[a] * 4294967296.0f));
@@ -1174,7 +1178,7 @@ __global__ void k_pair_overflow(View v, const int2* __restrict__ ovf, const int*
                                 (rcp + kCutBand) * (rcp + kCutBand), f[0], f[1], f[2], f[3], f[4], f[5]))
             continue;
         const float mag = fabsf(f[0]) + fabsf(f[1]) + fabsf(f[2]) + fabsf(f[3]) + fabsf(f[4]) + fabsf(f[5]);
-        if (!(mag < kMaxTerm)) atomicOr(v.status, (mag == mag) ? kStatusPairForceRange : kStatusNaN);
+        if (!(mag < kMaxTerm)) flag_inst(v, I, (mag == mag) ? kStatusPairForceRange : kStatusNaN);
         for (int a = 0; a < 3; a++) {
             atomicAdd((unsigned long long*)&v.F[a * N + pi], (unsigned long long)__float2ll_rn(f[a] * 4294967296.0f));
             atomicAdd((unsigned long long*)&v.T[a * N + pi], (unsigned long long)__float2ll_rn(f[3 + a] * 4294967296.0f));
@@ -1220,7 +1224,7 @@ __global__ void k_bonds(View v, long long* __restrict__ energy /* [B][8] */) {
             long long f;
             if constexpr (sizeof(T) == 4) f = __float2ll_rn(g[a] * 4294967296.0f);
             else f = __double2ll_rn(g[a] * 4294967296.0);
-            if (!(fabs(g[a]) < (T)kMaxTerm)) atomicOr(v.status, (g[a] == g[a]) ? kStatusPairForceRange : kStatusNaN);
+            if (!(fabs(g[a]) < (T)kMaxTerm)) flag_inst(v, I, (g[a] == g[a]) ? kStatusPairForceRange : kStatusNaN);
             atomicAdd((unsigned long long*)&v.F[a * N + pi], (unsigned long long)f);
             atomicAdd((unsigned long long*)&v.F[a * N + pj], (unsigned long long)(-f));
         }

@@ -128,8 +128,15 @@ struct View {
     const int* binst;
     const float2* bkf;              // (r0, kb)
     const double2* bkd;
-    // status word written by kernels (bit flags, see kStatus*)
+    // status word written by kernels (bit flags, see kStatus*), and one per
+    // instance for the flags that belong to one instance (nullable)
     unsigned* status;
+    unsigned* istatus;              // [B]
+    // bounded waits: polls before a staging barrier gives up, and bytes a
+    // barrier expects beyond those issued (0; a test sets it to make the
+    // wait run out while every copy still lands)
+    unsigned wait_polls;
+    unsigned extra_tx;
 };
 
 enum : unsigned {
@@ -142,6 +149,11 @@ enum : unsigned {
     kStatusGridRange = 64u,
     kStatusListOverflow = 128u,   // more listed pairs than the neighbour lists and their overflow hold
 };
+// Flags raised by the data of one instance (its state, forces or cells);
+// the others (a wait that timed out, the shared overflow list) concern the
+// whole launch.
+constexpr unsigned kStatusPerInstance =
+    kStatusNaN | kStatusAdjOverflow | kStatusMirrorRange | kStatusPairForceRange | kStatusGridRange;
 
 // ---------------------------------------------------------------- small helpers
 __host__ __device__ inline long long floor_div_ll(long long a, long long b) {   // b > 0
@@ -314,6 +326,13 @@ __device__ inline Frame tangent_frame(float nx, float ny, float nz) {
     f.r[3] = ny * uz - nz * uy; f.r[4] = nz * ux - nx * uz; f.r[5] = nx * uy - ny * ux;
     f.r[6] = nx; f.r[7] = ny; f.r[8] = nz;
     return f;
+}
+
+// Raises status bits for the launch and for the instance I (a reference
+// into v.inst).
+__device__ inline void flag_inst(const View& v, const Inst& I, unsigned bits) {
+    atomicOr(v.status, bits);
+    if (v.istatus) atomicOr(v.istatus + (&I - v.inst), bits);
 }
 
 }  // namespace orbc

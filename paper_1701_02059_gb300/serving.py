@@ -70,14 +70,21 @@ def serve_batched(jobs, hbm_budget_bytes: int, max_steps: int = 50, graphs: bool
             for s in arena.poll():
                 i = slot_job.pop(s)
                 tt = time.perf_counter()
-                st = arena.retire(s)
+                try:
+                    st = arena.retire(s)
+                except OrbcError as e:
+                    # the request failed alone (its own data raised a device
+                    # flag); the others carry on
+                    st = None
+                    rec[i]["error"] = e.code
                 spent["retire_s"] += time.perf_counter() - tt
                 if keep_states:
                     states[i] = st
                 done = time.perf_counter() - t0
                 rec[i]["done_s"] = done
                 rec[i]["latency_s"] = done - jobs[i]["arrival_s"]
-                work += jobs[i]["mem"].n * jobs[i]["steps"]
+                if st is not None:
+                    work += jobs[i]["mem"].n * jobs[i]["steps"]
         elif waiting:
             ti = time.perf_counter()
             time.sleep(max(0.0, min(0.05, jobs[waiting[0]]["arrival_s"] - (time.perf_counter() - t0))))
@@ -96,6 +103,7 @@ def serve_batched(jobs, hbm_budget_bytes: int, max_steps: int = 50, graphs: bool
     summary.update({"repack_s": round(inner["repack_s"], 3), "repacks": inner["repacks"],
                     "batched_steps": inner["steps"]})
     summary.update(mem_stats)
+    summary["failed"] = sum(1 for r in rec if "error" in r)
     return rec, summary, states
 
 

@@ -172,3 +172,54 @@ def test_overlapping_instances_stay_separate():
     for i, m in enumerate(mems):
         assert_same(got[slots[i]], alone(m, i, 8))
     ar.close()
+
+
+def runaway_patch(seed=31):
+    """A 2,304-particle patch with one spectrin bond made stiff (k_b = 10^6)
+    and stretched 0.01 sigma past its rest length: admissible (a 10^4 force
+    at admission), but the two beads overshoot each other with growing
+    amplitude and the bond force passes the 2^24 range limit within a few
+    steps."""
+    m = M.flat_patch_2304(seed=seed)
+    i, j = (int(x) for x in m.bonds[0])
+    r = float(np.linalg.norm(m.pos[j] - m.pos[i]))
+    m.kb = m.kb.copy()
+    m.r0 = m.r0.copy()
+    m.kb[0] = 1.0e6
+    m.r0[0] = r - 0.01
+    return m
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_failing_instance_is_isolated(graphs):
+    """One instance that blows up fails alone: poll reports it, retire
+    returns ORBC_E_NAN for it, and the others finish bit-identical to their
+    runs alone."""
+    mems = members()
+    bad = runaway_patch()
+    steps = 12
+    ar = G.Arena(8 << 30)
+    slots = [ar.admit(params(m, i), m, steps) for i, m in enumerate(mems)]
+    sbad = ar.admit(params(bad, 9), bad, steps)
+    got, failed = {}, {}
+    for _ in range(20):
+        ar.run(2, graphs)
+        for s in ar.poll():
+            try:
+                got[s] = ar.retire(s)
+            except G.OrbcError as e:
+                failed[s] = e.code
+        if len(got) + len(failed) == 4:
+            break
+    assert failed == {sbad: _native.ORBC_E_NAN}
+    for i, m in enumerate(mems):
+        assert_same(got[slots[i]], alone(m, i, steps))
+    ar.close()
+    # the runaway instance alone fails the plain system with the same code
+    g = G.System(params(bad, 9))
+    g.load_membrane(bad)
+    g.init_cells()
+    with pytest.raises(G.OrbcError) as e:
+        g.integrate(steps)
+    assert e.value.code == _native.ORBC_E_NAN
+    g.close()
