@@ -18,6 +18,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "orbc_oracle.c")
+SRC_MESH = os.path.join(HERE, "orbc_oracle_mesh.c")
 LIB = os.path.join(HERE, "liborbc_oracle.so")
 
 _lock = threading.Lock()
@@ -26,10 +27,11 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile the oracle shared library in place; returns its path."""
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+    stale = not os.path.exists(LIB) or any(os.path.getmtime(LIB) < os.path.getmtime(x) for x in (SRC, SRC_MESH))
+    if force or stale:
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
-               "-shared", "-o", tmp, SRC, "-lm"]
+               "-shared", "-o", tmp, SRC, SRC_MESH, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, LIB)
     return LIB
@@ -87,6 +89,10 @@ def lib():
             L.or_sys_rebuild.argtypes = [P]
             L.or_sys_compute_forces.argtypes = [P, P]
             L.or_sys_integrate.argtypes = [P, C.c_int]
+            L.or_sys_quench.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_double, P]
+            L.or_mesh_build.argtypes = [C.c_int, P, C.c_int, P, C.c_double, C.c_int, C.c_double, C.c_double,
+                                        C.c_double, C.c_double, C.c_double, C.c_ulonglong, C.c_longlong, P, P, P, P,
+                                        C.c_longlong, P, P, P, P]
             L.or_sys_get_state.argtypes = [P, P, P, P, P, P]
             L.or_sys_get_forces.argtypes = [P, P, P]
             L.or_sys_get_cells.argtypes = [P, P, P, P, P, P, P, P]
@@ -182,6 +188,25 @@ def bond_pair(d, kb, r0):
     Fa = np.zeros(3)
     U = lib().or_bond_pair(_p(d), float(kb), float(r0), _p(Fa))
     return U, Fa
+
+
+def mesh_build(verts, faces, spacing=1.12, beads=4, slack=1.03, kb=100.0, offset=1.0, d_min=0.8, d_ll=0.2, seed=0):
+    """Particles and bonds of a triangular mesh (readings M1-M6 of
+    orbc_oracle_mesh.c): returns dict(pos, ori, type, bonds, r0, kb)."""
+    v = _c(verts, np.float64)
+    f = _c(faces, np.int32)
+    n, nb = C.c_longlong(0), C.c_longlong(0)
+    args = (len(v), _p(v), len(f), _p(f), float(spacing), int(beads), float(slack), float(kb), float(offset),
+            float(d_min), float(d_ll), int(seed))
+    if lib().or_mesh_build(*args, 0, None, None, None, C.byref(n), 0, None, None, None, C.byref(nb)) != 0:
+        raise ValueError("invalid mesh")
+    pos, ori = np.zeros((n.value, 3)), np.zeros((n.value, 3))
+    typ = np.zeros(n.value, np.uint8)
+    bonds = np.zeros((nb.value, 2), np.int32)
+    r0, kbo = np.zeros(nb.value), np.zeros(nb.value)
+    lib().or_mesh_build(*args, n.value, _p(pos), _p(ori), _p(typ), C.byref(n), nb.value, _p(bonds), _p(r0),
+                        _p(kbo), C.byref(nb))
+    return {"pos": pos, "ori": ori, "type": typ, "bonds": bonds, "r0": r0, "kb": kbo}
 
 
 def pairs_brute(m: Model, x, typ, ids, bonds=None):
@@ -342,6 +367,13 @@ class OracleSystem:
     def integrate(self, nsteps):
         if lib().or_sys_integrate(self._h, int(nsteps)) != 0:
             raise RuntimeError("oracle integrate failed")
+
+    def quench(self, nsteps, dt, max_move=0.02, max_turn=0.05):
+        """Velocity quench (reading M7); returns the largest |F| at the end."""
+        fm = np.zeros(1)
+        if lib().or_sys_quench(self._h, int(nsteps), float(dt), float(max_move), float(max_turn), _p(fm)) != 0:
+            raise RuntimeError("oracle quench failed")
+        return float(fm[0])
 
     def state(self):
         n = self.n

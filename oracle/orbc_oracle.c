@@ -1197,6 +1197,63 @@ int or_sys_integrate(or_sys* s, int nsteps)
     return 0;
 }
 
+/* Velocity quench ("Initial structure generation": the generated system is
+ * optimised by velocity quenching to remove collisions; reading M7 of the
+ * mesh oracle): per step, with the current forces,
+ *   v += dt F/m, then v <- (v.F) F / |F|^2 when v.F > 0, else v <- 0,
+ *   scaled down so that |dt v| <= max_move; x += dt v;
+ *   for lipids w += dt tau_perp / I with tau_perp = tau - (tau.n) n, then
+ *   w <- (w.tau_perp) tau_perp / |tau_perp|^2 when positive, else 0,
+ *   scaled down so that |dt w| <= max_turn; n rotated by dt w (Cayley map,
+ *   renormalised);
+ * then the cells are rebuilt and the forces evaluated.  Velocities and
+ * angular velocities are zero at the end; the step counter does not move.
+ * fmax (nullable): the largest |F| after the last step. */
+int or_sys_quench(or_sys* s, int nsteps, double dt, double max_move, double max_turn, double* fmax)
+{
+    if (!s->cells_valid) return -1;
+    if (!s->forces_valid) or_compute(s);
+    for (int it = 0; it < nsteps; it++) {
+        for (int i = 0; i < s->n; i++) {
+            double* v = s->v + 3 * i;
+            const double* F = s->F + 3 * i;
+            for (int c = 0; c < 3; c++) v[c] = v[c] + dt * F[c] / s->r.mass;
+            const double vf = dot3(v, F), ff = dot3(F, F);
+            for (int c = 0; c < 3; c++) v[c] = (vf > 0.0 && ff > 0.0) ? (vf / ff) * F[c] : 0.0;
+            const double mv = dt * sqrt(dot3(v, v));
+            if (mv > max_move)
+                for (int c = 0; c < 3; c++) v[c] = v[c] * (max_move / mv);
+            for (int c = 0; c < 3; c++) s->x[3 * i + c] = s->x[3 * i + c] + dt * v[c];
+            if (s->type[i] == OR_LIPID) {
+                double* w = s->w + 3 * i;
+                double* nn = s->n_ + 3 * i;
+                const double* t = s->T + 3 * i;
+                const double tn = dot3(t, nn);
+                double tp[3];
+                for (int c = 0; c < 3; c++) tp[c] = t[c] - tn * nn[c];
+                for (int c = 0; c < 3; c++) w[c] = w[c] + dt * tp[c] / s->r.inertia;
+                const double wt = dot3(w, tp), tt = dot3(tp, tp);
+                for (int c = 0; c < 3; c++) w[c] = (wt > 0.0 && tt > 0.0) ? (wt / tt) * tp[c] : 0.0;
+                const double mw = dt * sqrt(dot3(w, w));
+                if (mw > max_turn)
+                    for (int c = 0; c < 3; c++) w[c] = w[c] * (max_turn / mw);
+                double th[3] = { dt * w[0], dt * w[1], dt * w[2] };
+                or_cayley(nn, th);
+            }
+        }
+        or_sys_rebuild(s);
+        or_compute(s);
+    }
+    double m = 0.0;
+    for (int i = 0; i < s->n; i++) {
+        double f = sqrt(dot3(s->F + 3 * i, s->F + 3 * i));
+        if (f > m) m = f;
+        for (int c = 0; c < 3; c++) { s->v[3 * i + c] = 0.0; s->w[3 * i + c] = 0.0; }
+    }
+    if (fmax) *fmax = m;
+    return 0;
+}
+
 /* ---------------------------------------------------------------- getters (id order) */
 
 int or_sys_n(const or_sys* s) { return s->n; }

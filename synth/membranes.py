@@ -260,6 +260,58 @@ def icosphere(f: int):
     return np.asarray(verts), np.asarray(sorted(edges), dtype=np.int64)
 
 
+def icosphere_mesh(f: int, radius: float = 1.0):
+    """Frequency-f geodesic icosphere as a triangle mesh: vertices on the
+    sphere of the given radius and faces wound counter-clockwise seen from
+    outside (V = 10 f^2 + 2, F = 20 f^2)."""
+    p = (1.0 + math.sqrt(5.0)) / 2.0
+    v0 = np.array([[-1, p, 0], [1, p, 0], [-1, -p, 0], [1, -p, 0], [0, -1, p], [0, 1, p],
+                   [0, -1, -p], [0, 1, -p], [p, 0, -1], [p, 0, 1], [-p, 0, -1], [-p, 0, 1]],
+                  dtype=np.float64)
+    base = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4),
+            (11, 10, 2), (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8),
+            (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    key_of, verts, faces = {}, [], []
+
+    def vertex(pnt):
+        q = pnt / np.linalg.norm(pnt)
+        key = tuple(np.round(q, 9))
+        if key not in key_of:
+            key_of[key] = len(verts)
+            verts.append(q)
+        return key_of[key]
+
+    for (a, b, c) in base:
+        A, B, C = v0[a], v0[b], v0[c]
+        if np.dot(np.cross(B - A, C - A), A + B + C) < 0:      # wind outward
+            B, C = C, B
+        P = {}
+        for i in range(f + 1):
+            for j in range(f + 1 - i):
+                P[(i, j)] = vertex((i * A + j * B + (f - i - j) * C) / f)
+        for i in range(f):
+            for j in range(f - i):
+                faces.append((P[(i, j)], P[(i + 1, j)], P[(i, j + 1)]))
+                if i + j <= f - 2:
+                    faces.append((P[(i + 1, j + 1)], P[(i, j + 1)], P[(i + 1, j)]))
+    return np.asarray(verts) * radius, np.asarray(faces, dtype=np.int32)
+
+
+def biconcave_mesh(n_vertices: int, n_lipids: int = 3_571_024):
+    """Triangulated biconcave red-cell surface (Evans-Fung profile) at the
+    lipid scale of biconcave(): n_vertices points spread by area, joined by
+    the convex hull of their unit-sphere images, faces wound outward."""
+    from scipy.spatial import ConvexHull
+    cdf = _AreaCDF()
+    scale = math.sqrt(n_lipids * AREA_PER_LIPID / cdf.total)
+    pos, _, sph = _ef_points(n_vertices, cdf, scale)
+    faces = ConvexHull(sph).simplices.astype(np.int32)
+    a, b, c = sph[faces[:, 0]], sph[faces[:, 1]], sph[faces[:, 2]]
+    inward = np.einsum("ij,ij->i", np.cross(b - a, c - a), a + b + c) < 0
+    faces[inward] = faces[inward][:, [0, 2, 1]]
+    return pos, faces
+
+
 def vesicle(n_lipids: int, seed: int, kT: float = 0.2, f: int | None = None,
             chain_beads: int = 20, slack: float = 0.03, kb: float = 100.0,
             n_centroids: int | None = None, jitter: float = 0.05, name: str = "vesicle") -> Membrane:
