@@ -272,6 +272,66 @@ ORBC_API int orbc_cell_sort_noalloc(const int* d_cell, int n, int K, int* d_perm
  * forces of that call invalid and the handle usable.  Errors: ORBC_E_ARG. */
 ORBC_API int orbc_set_wait_test(orbc_system* s, unsigned extra_tx_bytes, unsigned max_polls);
 
+/* ------------------------------------------------------------------------
+ * Initial structure ("Initial structure generation": a two-component system
+ * generated from a triangular mesh -- actin/glycophorin particles on the
+ * vertices, spectrin along the edges, lipids placed at random on each face by
+ * uniform sampling of the triangle, a minimum inter-particle distance, then
+ * a velocity quench that removes collisions).
+ */
+typedef struct {
+    double spacing;             /* lipid spacing s: one lipid per (sqrt(3)/2) s^2 of face area      */
+    double slack;               /* chain bond rest length = slack |J_b - J_a| / (beads + 1)          */
+    double kb;                  /* chain bond constant                                               */
+    double offset;              /* protein network this far inside the surface (along vertex normals) */
+    double d_min;               /* lipid candidates closer than this to a protein particle dropped   */
+    double d_ll;                /* ... and closer than this to an earlier lipid candidate            */
+    int beads;                  /* spectrin particles per mesh edge (0 .. 64)                         */
+    int pad0;
+    unsigned long long seed;    /* Philox key of the face counts and samples                          */
+} orbc_mesh_params;
+
+/* Fills mp with spacing 1.12, slack 1.03, kb 100, offset 1, d_min 0.8,
+ * d_ll 0.2, beads 4, seed 0. */
+ORBC_API void orbc_default_mesh_params(orbc_mesh_params* mp);
+
+/* Builds the particles and bonds of a membrane on a triangular mesh, on the
+ * GPU: verts [nv][3], faces [nf][3] vertex indices wound counter-clockwise
+ * seen from outside (host arrays, copied).  Face f holds floor(A_f / a) +
+ * [u < frac(A_f / a)] lipid candidates (a = (sqrt(3)/2) spacing^2, u a
+ * Philox4x32-10 variate at counter (f, 0, 0, 2)); candidate k of face f is
+ * ((1 - sqrt r1) p_a + sqrt r1 (1 - r2) p_b) + sqrt r1 r2 p_c with r1, r2
+ * from counter (f, k, 0, 3), its director the face's unit normal.  Junctions
+ * sit at v - offset n_v (n_v the normalised exact sum of the vertex's face
+ * cross products); each undirected edge carries `beads` spectrin particles
+ * evenly spaced between its junctions, chained by harmonic bonds.  A
+ * candidate closer than d_min to a protein particle or closer than d_ll to
+ * an earlier candidate is dropped.  Output (host, id order): the kept
+ * lipids, then the junctions (vertex order), then the spectrin (edge order):
+ * pos, ori [n][3] (ori zero for proteins), type [n]; bonds [nb][2] ids, r0,
+ * kb [nb].  *n_out and *nb_out always receive the totals; the arrays are
+ * written when cap >= n and bond_cap >= nb (pass 0 to query the sizes).
+ * The result does not depend on the launch shape.  cuda_stream: as in
+ * orbc_cell_sort; the call synchronises it and frees its scratch.
+ * Errors: ORBC_E_ARG (null pointer, vertex index out of range, a degenerate
+ * face, non-finite or |x| >= 4096 coordinates, invalid parameters, or a
+ * nonzero capacity smaller than the totals), ORBC_E_NOMEM, ORBC_E_CUDA. */
+ORBC_API int orbc_mesh_build(const orbc_mesh_params* mp, int nv, const double* verts, int nf, const int* faces,
+                             long long cap, double* pos, double* ori, unsigned char* type, long long* n_out,
+                             long long bond_cap, int* bonds, double* r0, double* kb, long long* nb_out,
+                             void* cuda_stream);
+
+/* Velocity quench of the handle's system (after orbc_init_cells): nsteps
+ * steps of v += dt F/m, v replaced by its component along F (zero when it
+ * points against F) and limited to |dt v| <= max_move, x += dt v; for lipids
+ * the same with w, the torque's part normal to the director and max_turn,
+ * the director turned by the Cayley map of dt w; cells rebuilt and forces
+ * evaluated every step.  Velocities and angular velocities are zero at the
+ * end and the step counter does not move.  fmax_out (nullable): the largest
+ * |F| after the last step.  Errors: ORBC_E_ARG (nsteps < 0, non-positive dt
+ * or limits), ORBC_E_STATE (cells not initialised), ORBC_E_NAN, ORBC_E_CUDA. */
+ORBC_API int orbc_quench(orbc_system* s, int nsteps, double dt, double max_move, double max_turn, double* fmax_out);
+
 /* Number of CUDA kernels this handle has launched since creation. */
 ORBC_API int orbc_get_launch_count(orbc_system* s, long long* count);
 

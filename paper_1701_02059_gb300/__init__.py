@@ -35,6 +35,34 @@ def make_params(**kw) -> Params:
     return p
 
 
+def mesh_build(verts, faces, stream=None, **kw):
+    """orbc_mesh_build: particles and bonds of a membrane on a triangular
+    mesh (keywords: the orbc_mesh_params fields).  Returns dict(pos, ori,
+    type, bonds, r0, kb) in id order."""
+    from ._native import MeshParams
+    L = load()
+    mp = MeshParams()
+    L.orbc_default_mesh_params(C.byref(mp))
+    for k, v in kw.items():
+        setattr(mp, k, v)
+    v = np.ascontiguousarray(verts, np.float64)
+    f = np.ascontiguousarray(faces, np.int32)
+    n, nb = C.c_longlong(0), C.c_longlong(0)
+    st = C.c_void_p(stream) if stream else None
+    rc = L.orbc_mesh_build(C.byref(mp), len(v), _p(v), len(f), _p(f), 0, None, None, None, C.byref(n), 0, None, None,
+                           None, C.byref(nb), st)
+    if rc != 0:
+        raise OrbcError(rc, "orbc_mesh_build")
+    out = {"pos": np.zeros((n.value, 3)), "ori": np.zeros((n.value, 3)), "type": np.zeros(n.value, np.uint8),
+           "bonds": np.zeros((nb.value, 2), np.int32), "r0": np.zeros(nb.value), "kb": np.zeros(nb.value)}
+    rc = L.orbc_mesh_build(C.byref(mp), len(v), _p(v), len(f), _p(f), n.value, _p(out["pos"]), _p(out["ori"]),
+                           _p(out["type"]), C.byref(n), nb.value, _p(out["bonds"]), _p(out["r0"]), _p(out["kb"]),
+                           C.byref(nb), st)
+    if rc != 0:
+        raise OrbcError(rc, "orbc_mesh_build")
+    return out
+
+
 def cell_sort(cell, K: int, stream=None):
     """Stable sort of device int32 cell ids (torch tensor on CUDA) through
     orbc_cell_sort; returns (perm, cell_start) as device tensors."""
@@ -137,6 +165,13 @@ class System:
 
     def integrate(self, nsteps: int):
         self._check(self._L.orbc_integrate(self._h, int(nsteps)), "orbc_integrate")
+
+    def quench(self, nsteps: int, dt: float, max_move: float = 0.02, max_turn: float = 0.05) -> float:
+        """orbc_quench: velocity quench; returns the largest |F| at the end."""
+        fm = C.c_double(0.0)
+        self._check(self._L.orbc_quench(self._h, int(nsteps), float(dt), float(max_move), float(max_turn),
+                                        C.byref(fm)), "orbc_quench")
+        return fm.value
 
     # -------------------------------------------------------------- getters
     def state(self, out=None):

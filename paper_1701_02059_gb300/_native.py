@@ -24,9 +24,9 @@ EXPORTS = [
     "orbc_arena_create", "orbc_arena_admit", "orbc_arena_run", "orbc_arena_poll", "orbc_arena_retire",
     "orbc_arena_info", "orbc_arena_launch_count", "orbc_arena_last_error", "orbc_arena_destroy",
     "orbc_autotune", "orbc_arena_stats", "orbc_set_particles_device", "orbc_get_state_device",
-    "orbc_get_forces_device",
+    "orbc_get_forces_device", "orbc_default_mesh_params", "orbc_mesh_build", "orbc_quench",
 ]
-_NOT_INT = {"orbc_default_params": None, "orbc_last_error": C.c_char_p, "orbc_destroy": None,
+_NOT_INT = {"orbc_default_params": None, "orbc_default_mesh_params": None, "orbc_last_error": C.c_char_p, "orbc_destroy": None,
             "orbc_arena_launch_count": C.c_longlong, "orbc_arena_last_error": C.c_char_p, "orbc_arena_destroy": None}
 
 
@@ -41,6 +41,13 @@ class Params(C.Structure):
                 ("n_centroids", C.c_int), ("n_lloyd_init", C.c_int), ("rebuild_every", C.c_int),
                 ("skin", C.c_double), ("grid_h", C.c_double), ("seed", C.c_ulonglong), ("instance", C.c_uint),
                 ("precision", C.c_int)]
+
+
+class MeshParams(C.Structure):
+    """Mirror of orbc_mesh_params."""
+    _fields_ = [("spacing", C.c_double), ("slack", C.c_double), ("kb", C.c_double), ("offset", C.c_double),
+                ("d_min", C.c_double), ("d_ll", C.c_double), ("beads", C.c_int), ("pad0", C.c_int),
+                ("seed", C.c_ulonglong)]
 
 
 class OrbcError(RuntimeError):
@@ -78,6 +85,9 @@ def load(path: str | None = None):
     L.orbc_dump_pairs.argtypes = [V, C.c_longlong, V, C.POINTER(C.c_longlong)]
     L.orbc_set_timing.argtypes = [V, C.c_int]
     L.orbc_set_wait_test.argtypes = [V, C.c_uint, C.c_uint]
+    L.orbc_default_mesh_params.argtypes = [V]
+    L.orbc_mesh_build.argtypes = [V, C.c_int, V, C.c_int, V, C.c_longlong, V, V, V, V, C.c_longlong, V, V, V, V, V]
+    L.orbc_quench.argtypes = [V, C.c_int, C.c_double, C.c_double, C.c_double, V]
     L.orbc_get_kernel_times.argtypes = [V, C.c_char_p, C.c_int, V, C.c_int, C.POINTER(C.c_int)]
     L.orbc_get_launch_count.argtypes = [V, C.POINTER(C.c_longlong)]
     L.orbc_cell_sort.argtypes = [V, C.c_int, C.c_int, V, V, V]

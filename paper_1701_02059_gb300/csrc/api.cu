@@ -1158,6 +1158,31 @@ int orbc_dump_pairs(orbc_system* s, long long cap, unsigned* pairs, long long* n
     });
 }
 
+void orbc_default_mesh_params(orbc_mesh_params* mp) {
+    if (!mp) return;
+    std::memset(mp, 0, sizeof(*mp));
+    mp->spacing = 1.12; mp->slack = 1.03; mp->kb = 100.0; mp->offset = 1.0; mp->d_min = 0.8; mp->d_ll = 0.2;
+    mp->beads = 4; mp->seed = 0;
+}
+
+int orbc_quench(orbc_system* s, int nsteps, double dt, double max_move, double max_turn, double* fmax_out) {
+    if (!s) return ORBC_E_ARG;
+    if (nsteps < 0 || !(dt > 0) || !(max_move > 0) || !(max_turn > 0)) return fail(s, ORBC_E_ARG, "invalid quench");
+    unsigned st = 0;
+    double fm = 0.0;
+    int rc = guarded(s, [&] {
+        sync_device(s);
+        if (!s->ens->cells_valid) throw StateError("cells not initialised");
+        s->host_stale = true;
+        fm = s->ens->quench(nsteps, dt, max_move, max_turn);
+        st = s->ens->read_status(true);
+        if (st) s->ens->forces_valid = false;
+    });
+    if (rc == ORBC_OK && st) return fail(s, status_code(st), "device status " + std::to_string(st));
+    if (rc == ORBC_OK && fmax_out) *fmax_out = fm;
+    return rc;
+}
+
 int orbc_set_wait_test(orbc_system* s, unsigned extra_tx_bytes, unsigned max_polls) {
     if (!s || max_polls < 1 || max_polls > (1u << 22) || extra_tx_bytes > 4096 || (extra_tx_bytes % 16) != 0)
         return ORBC_E_ARG;

@@ -134,6 +134,8 @@ public:
     void rebuild(bool sums_ready = false);
     void compute_forces(bool energies);
     void integrate(int nsteps);
+    // velocity quench; returns the largest |F| at the end
+    double quench(int nsteps, double dt, double max_move, double max_turn);
     void energies(std::vector<double>& out); // [B][5] after compute_forces(true)
 
     // host copies (instance b, id order)

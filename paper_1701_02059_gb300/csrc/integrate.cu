@@ -9,6 +9,8 @@
 // accumulation is exact integer arithmetic.
 #include "ensemble.cuh"
 
+#include <cstring>
+
 namespace orbc {
 
 template <typename T> struct Num;
@@ -372,6 +374,73 @@ __global__ void k_kinetic(View v, long long* __restrict__ energy) {
     }
 }
 
+// Velocity quench ("Initial structure generation": the generated system is
+// optimised by velocity quenching to remove collisions between particles;
+// the paper names no scheme, the reading is quick-min with rotations): with
+// the current force, v += dt F/m, then v is replaced by its component along
+// F (zero when it points against F) and scaled down so that |dt v| <=
+// max_move; x += dt v.  Lipids likewise with w, the torque's part normal to
+// the director and max_turn, the director turned by the Cayley map of dt w.
+// FP64 increments rounded onto the grid.
+__global__ void k_quench(View v, double dt, double max_move, double max_turn) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= v.N) return;
+    using V = Num<double>;
+    const int b = find_inst(v.inst_p0, v.B, p);
+    const Inst& I = v.inst[b];
+    const size_t N = v.N;
+    double F[3], u[3];
+    for (int a = 0; a < 3; a++) {
+        F[a] = V::frc(v.F[a * N + p]);
+        u[a] = V::st(v.vq[a * N + p]) + dt * F[a] / I.mass;
+    }
+    const double vf = u[0] * F[0] + u[1] * F[1] + u[2] * F[2], ff = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
+    for (int a = 0; a < 3; a++) u[a] = (vf > 0.0 && ff > 0.0) ? (vf / ff) * F[a] : 0.0;
+    const double mv = dt * sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    if (mv > max_move)
+        for (int a = 0; a < 3; a++) u[a] *= max_move / mv;
+    for (int a = 0; a < 3; a++) {
+        v.xq[a * N + p] += V::grid(dt * u[a]);
+        v.vq[a * N + p] = V::grid(u[a]);
+    }
+    if (v.type[p] != kLipid) return;
+    long long nq[3], wq[3];
+    double n[3], t[3], w[3];
+    for (int a = 0; a < 3; a++) {
+        nq[a] = v.nq[a * N + p];
+        n[a] = V::st(nq[a]);
+        t[a] = V::frc(v.T[a * N + p]);
+    }
+    const double tn = t[0] * n[0] + t[1] * n[1] + t[2] * n[2];
+    for (int a = 0; a < 3; a++) {
+        t[a] -= tn * n[a];
+        w[a] = V::st(v.wq[a * N + p]) + dt * t[a] / I.inertia;
+    }
+    const double wt = w[0] * t[0] + w[1] * t[1] + w[2] * t[2], tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    for (int a = 0; a < 3; a++) w[a] = (wt > 0.0 && tt > 0.0) ? (wt / tt) * t[a] : 0.0;
+    const double mw = dt * sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    if (mw > max_turn)
+        for (int a = 0; a < 3; a++) w[a] *= max_turn / mw;
+    for (int a = 0; a < 3; a++) wq[a] = V::grid(w[a]);
+    cayley<double>(nq, wq, dt);
+    renormalise(nq, 0.0);
+    for (int a = 0; a < 3; a++) { v.nq[a * N + p] = nq[a]; v.wq[a * N + p] = wq[a]; }
+}
+
+// Largest |F| over the particles, as the bits of a positive double.
+__global__ void k_fmax(View v, unsigned long long* __restrict__ out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    double f = 0.0;
+    if (p < v.N) {
+        const size_t N = v.N;
+        double s = 0.0;
+        for (int a = 0; a < 3; a++) { const double x = Num<double>::frc(v.F[a * N + p]); s += x * x; }
+        f = sqrt(s);
+    }
+    for (int off = 16; off; off >>= 1) f = fmax(f, __shfl_xor_sync(0xffffffffu, f, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(f));
+}
+
 static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
 void Ensemble::launch_integrate_first(bool fused, bool msums) {
@@ -398,6 +467,34 @@ void Ensemble::launch_kick(bool energies) {
     launches++;
     CK(cudaGetLastError());
     (void)energies;
+}
+
+double Ensemble::quench(int nsteps, double dt, double max_move, double max_turn) {
+    if (!cells_valid) throw StateError("cells not initialised");
+    if (!forces_valid) launch_pairs(false, false);
+    for (int s = 0; s < nsteps; s++) {
+        k_quench<<<nblk(N, 256), 256, 0, stream>>>(view(), dt, max_move, max_turn);
+        launches++;
+        CK(cudaGetLastError());
+        rebuild(false);
+        launch_pairs(false, false);
+    }
+    forces_valid = true;
+    // velocities and angular velocities zero at the end
+    CK(cudaMemsetAsync(d_state[cur_][1], 0, sizeof(long long) * 3 * (size_t)N, stream));
+    CK(cudaMemsetAsync(d_state[cur_][3], 0, sizeof(long long) * 3 * (size_t)N, stream));
+    unsigned long long* d = nullptr;
+    CK(cudaMallocAsync(&d, sizeof(unsigned long long), stream));
+    CK(cudaMemsetAsync(d, 0, sizeof(unsigned long long), stream));
+    k_fmax<<<nblk(N, 256), 256, 0, stream>>>(view(), d);
+    launches++;
+    unsigned long long bits = 0;
+    CK(cudaMemcpyAsync(&bits, d, sizeof(bits), cudaMemcpyDeviceToHost, stream));
+    CK(cudaFreeAsync(d, stream));
+    CK(cudaStreamSynchronize(stream));
+    double fm;
+    std::memcpy(&fm, &bits, sizeof(fm));
+    return fm;
 }
 
 void Ensemble::launch_kinetic() {
