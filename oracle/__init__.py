@@ -89,6 +89,11 @@ def lib():
             L.or_sys_rebuild.argtypes = [P]
             L.or_sys_compute_forces.argtypes = [P, P]
             L.or_sys_integrate.argtypes = [P, C.c_int]
+            L.or_sys_set_volume.argtypes = [P, C.c_double, C.c_double, C.c_double, P]
+            L.or_sys_volume.restype = C.c_double
+            L.or_sys_volume.argtypes = [P, C.c_double, P]
+            L.or_height_map.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
+                                        C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, P, P]
             L.or_sys_quench.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_double, P]
             L.or_mesh_build.argtypes = [C.c_int, P, C.c_int, P, C.c_double, C.c_int, C.c_double, C.c_double,
                                         C.c_double, C.c_double, C.c_double, C.c_ulonglong, C.c_longlong, P, P, P, P,
@@ -367,6 +372,22 @@ class OracleSystem:
     def integrate(self, nsteps):
         if lib().or_sys_integrate(self._h, int(nsteps)) != 0:
             raise RuntimeError("oracle integrate failed")
+
+    def set_volume(self, kv, v0, area, center):
+        """Harmonic volume constraint (readings V1-V2); kv = 0 switches it off."""
+        c = _c(center, np.float64)
+        lib().or_sys_set_volume(self._h, float(kv), float(v0), float(area), _p(c))
+
+    def volume(self, area, center):
+        c = _c(center, np.float64)
+        return lib().or_sys_volume(self._h, float(area), _p(c))
+
+    def height_map(self, x0, y0, dx, dy, nx, ny, z_min, axis, rho_in, rho_out):
+        """Mean z per (x, y) bin of the upper-rim lipids (reading H1)."""
+        h, cnt = np.zeros(nx * ny), np.zeros(nx * ny, np.int32)
+        lib().or_height_map(self._h, float(x0), float(y0), float(dx), float(dy), int(nx), int(ny), float(z_min),
+                            float(axis[0]), float(axis[1]), float(rho_in), float(rho_out), _p(h), _p(cnt))
+        return h.reshape(ny, nx), cnt.reshape(ny, nx)
 
     def quench(self, nsteps, dt, max_move=0.02, max_turn=0.05):
         """Velocity quench (reading M7); returns the largest |F| at the end."""

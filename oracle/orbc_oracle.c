@@ -29,6 +29,9 @@
  *     can check they agree.
  *   - Time stepping: force and torque, then position and orientation update
  *     ("Software Overview", flow chart).
+ *   - Harmonic volume constraint and the upper-rim height map for the
+ *     membrane fluctuation ("Validation and Benchmark", the whole-cell run):
+ *     readings V1, V2 and H1 beside the code.
  *
  * Readings where the paper is silent (pair potential, integrator, cell
  * adjacency rule, tie-breaks, fixed-point scales) are stated beside the code
@@ -830,6 +833,10 @@ typedef struct {
     long long step;
     int cells_valid;
     long long n_rebuilds;
+    /* harmonic volume constraint (reading V1-V2) */
+    int vol_on;
+    double kv, v0, a_vol, xc[3];
+    double vol, u_vol;
 } or_sys;
 
 or_sys* or_sys_create(const or_model* m, const or_run* r)
@@ -1068,6 +1075,39 @@ static void or_compute(or_sys* s)
             wb += -d[k] * Fa[k];
         }
     }
+    /* harmonic volume constraint ("Validation and Benchmark": a harmonic
+     * volume constraint keeps the cell's surface-to-volume ratio; reading
+     * V1: the enclosed volume of a particle membrane by the divergence
+     * theorem over the lipids' area elements, V = (1/3) sum a (x_i - x_c).n_i,
+     * a the area per lipid, x_c a fixed reference point inside; V2:
+     * U_V = k_V (V - V0)^2 / 2, so with g = k_V (V - V0) a / 3 every lipid
+     * gets F -= g n_i and, from dU/dn_i = g (x_i - x_c), the torque
+     * n_i x (-g (x_i - x_c)); U_V is reported with the bond energy and
+     * adds nothing to the virial) */
+    s->vol = 0.0;
+    s->u_vol = 0.0;
+    if (s->vol_on) {
+        double V = 0.0;
+        for (int i = 0; i < n; i++) {
+            if (s->type[i] != OR_LIPID) continue;
+            double d[3] = { s->x[3 * i] - s->xc[0], s->x[3 * i + 1] - s->xc[1], s->x[3 * i + 2] - s->xc[2] };
+            V += s->a_vol * dot3(d, s->n_ + 3 * i) / 3.0;
+        }
+        const double g = s->kv * (V - s->v0) * s->a_vol / 3.0;
+        for (int i = 0; i < n; i++) {
+            if (s->type[i] != OR_LIPID) continue;
+            double d[3] = { s->x[3 * i] - s->xc[0], s->x[3 * i + 1] - s->xc[1], s->x[3 * i + 2] - s->xc[2] };
+            double gd[3] = { -g * d[0], -g * d[1], -g * d[2] }, t[3];
+            cross3(s->n_ + 3 * i, gd, t);
+            for (int c = 0; c < 3; c++) {
+                s->F[3 * i + c] -= g * s->n_[3 * i + c];
+                s->T[3 * i + c] += t[c];
+            }
+        }
+        s->vol = V;
+        s->u_vol = 0.5 * s->kv * (V - s->v0) * (V - s->v0);
+        ub += s->u_vol;
+    }
     double U = 0.0, W = 0.0, kt = 0.0, kr = 0.0;
     for (int i = 0; i < n; i++) {
         U += up[i];
@@ -1082,6 +1122,57 @@ static void or_compute(or_sys* s)
     s->energies[4] = W + wb;
     free(up); free(wp);
     s->forces_valid = 1;
+}
+
+void or_sys_set_volume(or_sys* s, double kv, double v0, double area, const double* xc)
+{
+    s->vol_on = kv > 0.0;
+    s->kv = kv;
+    s->v0 = v0;
+    s->a_vol = area;
+    for (int c = 0; c < 3; c++) s->xc[c] = xc[c];
+    s->forces_valid = 0;
+}
+
+/* The enclosed volume (reading V1) of the current state, whether or not the
+ * constraint acts. */
+double or_sys_volume(or_sys* s, double area, const double* xc)
+{
+    double V = 0.0;
+    for (int i = 0; i < s->n; i++) {
+        if (s->type[i] != OR_LIPID) continue;
+        double d[3] = { s->x[3 * i] - xc[0], s->x[3 * i + 1] - xc[1], s->x[3 * i + 2] - xc[2] };
+        V += area * dot3(d, s->n_ + 3 * i) / 3.0;
+    }
+    return V;
+}
+
+/* Height map for the membrane fluctuation measurement ("Validation and
+ * Benchmark": the instantaneous vertical fluctuation dh(x, y) along the
+ * upper rim of a fixed cell; reading H1): lipids above z_min whose distance
+ * rho from the axis through (ax, ay) lies in [rho_in, rho_out) are binned on
+ * the grid [x0 + i dx, x0 + (i + 1) dx) x [y0 + j dy, ...), i < nx, j < ny;
+ * h[j nx + i] = their mean z (0 where the bin is empty), count = their
+ * number.  dh over time is h(t) minus its time mean, bin by bin. */
+void or_height_map(const or_sys* s, double x0, double y0, double dx, double dy, int nx, int ny, double z_min,
+                   double ax, double ay, double rho_in, double rho_out, double* h, int* count)
+{
+    for (int q = 0; q < nx * ny; q++) { h[q] = 0.0; count[q] = 0; }
+    for (int i = 0; i < s->n; i++) {
+        if (s->type[i] != OR_LIPID) continue;
+        const double* x = s->x + 3 * i;
+        if (!(x[2] > z_min)) continue;
+        const double rx = x[0] - ax, ry = x[1] - ay;
+        const double rho = sqrt(rx * rx + ry * ry);
+        if (!(rho >= rho_in && rho < rho_out)) continue;
+        const double fx = floor((x[0] - x0) / dx), fy = floor((x[1] - y0) / dy);
+        if (fx < 0.0 || fy < 0.0 || fx >= nx || fy >= ny) continue;
+        const int q = (int)fy * nx + (int)fx;
+        h[q] += x[2];
+        count[q]++;
+    }
+    for (int q = 0; q < nx * ny; q++)
+        if (count[q] > 0) h[q] /= count[q];
 }
 
 int or_sys_compute_forces(or_sys* s, double* energies)
