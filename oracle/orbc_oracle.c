@@ -1166,7 +1166,7 @@ void or_height_map(const or_sys* s, double x0, double y0, double dx, double dy, 
         const double rho = sqrt(rx * rx + ry * ry);
         if (!(rho >= rho_in && rho < rho_out)) continue;
         const double fx = floor((x[0] - x0) / dx), fy = floor((x[1] - y0) / dy);
-        if (fx < 0.0 || fy < 0.0 || fx >= nx || fy >= ny) continue;
+        if (!(fx >= 0.0 && fy >= 0.0 && fx < nx && fy < ny)) continue;
         const int q = (int)fy * nx + (int)fx;
         h[q] += x[2];
         count[q]++;
