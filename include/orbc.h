@@ -332,6 +332,47 @@ ORBC_API int orbc_mesh_build(const orbc_mesh_params* mp, int nv, const double* v
  * or limits), ORBC_E_STATE (cells not initialised), ORBC_E_NAN, ORBC_E_CUDA. */
 ORBC_API int orbc_quench(orbc_system* s, int nsteps, double dt, double max_move, double max_turn, double* fmax_out);
 
+/* Harmonic volume constraint on the handle's membrane ("Validation and
+ * Benchmark": the whole-cell run holds its surface-to-volume ratio by a
+ * harmonic volume constraint; the paper states no functional form, so the
+ * enclosed volume is taken from the lipids by the divergence theorem with
+ * each lipid's director as its surface normal):
+ *   V = sum over lipids of (a / 3) (x_i - c) . n_i,   U_V = k_V (V - V0)^2 / 2,
+ * a = area_per_lipid (sigma^2), c = center (sigma, a fixed point inside the
+ * membrane).  With g = k_V (V - V0) a / 3 each lipid gets the force -g n_i
+ * and the torque n_i x (-g (x_i - c)); U_V is added to the bond energy
+ * (energies[1]) and nothing to the virial.  Each term of V is rounded to
+ * 2^-48 sigma^3 before an exact integer sum, so V does not depend on the
+ * order; (x_i - c).n_i is FP32 in the FP32-force modes and FP64 otherwise,
+ * the factor a/3 and everything after the sum FP64.  kv = 0 switches the
+ * constraint off; the setting survives later orbc_set_particles calls.
+ * Errors: ORBC_E_ARG (null center, kv < 0, non-finite values, a
+ * non-positive area with kv > 0, a periodic axis with kv > 0), ORBC_E_CUDA. */
+ORBC_API int orbc_set_volume_constraint(orbc_system* s, double kv, double v0, double area_per_lipid,
+                                        const double* center);
+
+/* The enclosed volume V of the current state (the sum above) for the given
+ * area per lipid and center, whether or not the constraint acts.
+ * Errors: ORBC_E_ARG (null pointer, non-finite values), ORBC_E_STATE (no
+ * particles), ORBC_E_CUDA. */
+ORBC_API int orbc_get_volume(orbc_system* s, double area_per_lipid, const double* center, double* volume_out);
+
+/* Height map of the membrane's upper rim for the fluctuation measurement
+ * ("Validation and Benchmark": the instantaneous vertical fluctuation
+ * dh(x, y) along the upper rim of a cell held in place): the lipids with
+ * z > z_min whose distance rho from the vertical axis through (axis[0],
+ * axis[1]) lies in [rho_in, rho_out) are binned on the grid
+ * x in [x0 + i dx, x0 + (i + 1) dx), y in [y0 + j dy, ...), i < nx, j < ny;
+ * h_out[j nx + i] = their mean z (0 for an empty bin), count_out[j nx + i]
+ * their number (both host arrays of nx ny).  Every selection and bin index
+ * is decided in FP64 from the exact state with correctly rounded operations;
+ * z is summed exactly as an integer on the state grid.  dh over time is h
+ * minus its time mean, bin by bin.  Errors: ORBC_E_ARG (null pointer,
+ * nx or ny < 1, nx ny > 2^24, non-positive dx or dy, non-finite values),
+ * ORBC_E_STATE (no particles), ORBC_E_CUDA. */
+ORBC_API int orbc_height_map(orbc_system* s, double x0, double y0, double dx, double dy, int nx, int ny, double z_min,
+                             const double* axis, double rho_in, double rho_out, double* h_out, int* count_out);
+
 /* Number of CUDA kernels this handle has launched since creation. */
 ORBC_API int orbc_get_launch_count(orbc_system* s, long long* count);
 

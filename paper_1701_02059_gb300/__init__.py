@@ -173,6 +173,30 @@ class System:
                                         C.byref(fm)), "orbc_quench")
         return fm.value
 
+    def set_volume_constraint(self, kv: float, v0: float, area_per_lipid: float, center=(0.0, 0.0, 0.0)):
+        """orbc_set_volume_constraint: U_V = kv (V - v0)^2 / 2 on the lipid
+        volume V (kv = 0 switches it off)."""
+        c = np.ascontiguousarray(center, np.float64)
+        self._check(self._L.orbc_set_volume_constraint(self._h, float(kv), float(v0), float(area_per_lipid), _p(c)),
+                    "orbc_set_volume_constraint")
+
+    def volume(self, area_per_lipid: float, center=(0.0, 0.0, 0.0)) -> float:
+        """orbc_get_volume: the enclosed lipid volume of the current state."""
+        c = np.ascontiguousarray(center, np.float64)
+        V = C.c_double(0.0)
+        self._check(self._L.orbc_get_volume(self._h, float(area_per_lipid), _p(c), C.byref(V)), "orbc_get_volume")
+        return V.value
+
+    def height_map(self, x0, y0, dx, dy, nx, ny, z_min, axis=(0.0, 0.0), rho_in=0.0, rho_out=float("inf")):
+        """orbc_height_map: mean z and count per (x, y) bin of the lipids
+        above z_min in the annulus rho_in <= rho < rho_out; arrays [ny, nx]."""
+        a = np.ascontiguousarray(axis, np.float64)
+        h, cnt = np.zeros(nx * ny), np.zeros(nx * ny, np.int32)
+        self._check(self._L.orbc_height_map(self._h, float(x0), float(y0), float(dx), float(dy), int(nx), int(ny),
+                                            float(z_min), _p(a), float(rho_in), float(rho_out), _p(h), _p(cnt)),
+                    "orbc_height_map")
+        return h.reshape(ny, nx), cnt.reshape(ny, nx)
+
     # -------------------------------------------------------------- getters
     def state(self, out=None):
         """orbc_get_state: positions, velocities, directors and angular

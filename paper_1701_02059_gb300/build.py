@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liborbc.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["api.cu", "arena.cu", "cells.cu", "cellsort.cu", "forces.cu", "integrate.cu", "mesh.cu", "scan.cu",
-           "tune.cu"]
+           "tune.cu", "volume.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

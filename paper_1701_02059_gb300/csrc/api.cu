@@ -96,6 +96,7 @@ View Ensemble::view() {
     v.istatus = d_istatus;
     v.wait_polls = wait_polls;
     v.extra_tx = extra_tx;
+    v.vol = d_vol;
     return v;
 }
 
@@ -273,6 +274,9 @@ void Ensemble::alloc_core(const std::vector<int>& p0, const std::vector<int>& k0
     prev_adj_valid_ = false;
     csr_valid_ = false;
     d_energy = alloc<long long>((size_t)8 * B);
+    d_vol = alloc<long long>((size_t)2 * B);
+    vol_any = false;
+    for (const Inst& I : inst_h) vol_any = vol_any || I.vol_on;
     d_step = alloc<long long>(B);
     CK(cudaMemcpyAsync(d_step, step_h.data(), sizeof(long long) * B, cudaMemcpyHostToDevice, stream));
     d_xref = any_skin ? alloc<long long>((size_t)3 * N) : nullptr;
@@ -387,6 +391,11 @@ void Ensemble::setup(const std::vector<const HostInstance*>& list) {
         inst_h[b].p0 = N; inst_h[b].n = h.n;
         inst_h[b].k0 = Ktot; inst_h[b].K = h.prm.n_centroids;
         inst_h[b].nlip = (int)std::count(h.type.begin(), h.type.end(), (unsigned char)kLipid);
+        inst_h[b].vol_on = h.vol_kv > 0.0;
+        inst_h[b].kv = h.vol_kv;
+        inst_h[b].v0 = h.vol_v0;
+        inst_h[b].a3 = h.vol_area / 3.0;
+        for (int a = 0; a < 3; a++) inst_h[b].xcq[a] = llrint(h.vol_xc[a] * kGrid);
         prm_h.push_back(h.prm);
         N += h.n;
         Ktot += h.prm.n_centroids;
@@ -992,7 +1001,13 @@ int orbc_set_particles(orbc_system* s, int n, const double* pos, const double* v
                        const double* angvel, const unsigned char* type, const unsigned* id) {
     if (!s) return ORBC_E_ARG;
     return guarded(s, [&] {
-        s->host = host_instance(s->prm, n, pos, vel, ori, angvel, type, id);
+        HostInstance h = host_instance(s->prm, n, pos, vel, ori, angvel, type, id);
+        // the volume constraint belongs to the handle, not to the particles
+        h.vol_kv = s->host.vol_kv;
+        h.vol_v0 = s->host.vol_v0;
+        h.vol_area = s->host.vol_area;
+        for (int a = 0; a < 3; a++) h.vol_xc[a] = s->host.vol_xc[a];
+        s->host = std::move(h);
         s->have_particles = true;
         s->dirty = true;
         s->host_stale = false;
@@ -1181,6 +1196,59 @@ int orbc_quench(orbc_system* s, int nsteps, double dt, double max_move, double m
     if (rc == ORBC_OK && st) return fail(s, status_code(st), "device status " + std::to_string(st));
     if (rc == ORBC_OK && fmax_out) *fmax_out = fm;
     return rc;
+}
+
+int orbc_set_volume_constraint(orbc_system* s, double kv, double v0, double area_per_lipid, const double* center) {
+    if (!s) return ORBC_E_ARG;
+    if (!center || !(kv >= 0) || !std::isfinite(kv) || !std::isfinite(v0) || !std::isfinite(area_per_lipid) ||
+        !std::isfinite(center[0]) || !std::isfinite(center[1]) || !std::isfinite(center[2]))
+        return fail(s, ORBC_E_ARG, "invalid volume constraint");
+    if (kv > 0 && !(area_per_lipid > 0)) return fail(s, ORBC_E_ARG, "volume constraint needs a positive area per lipid");
+    if (kv > 0 && (s->prm.periodic[0] || s->prm.periodic[1] || s->prm.periodic[2]))
+        return fail(s, ORBC_E_ARG, "volume constraint needs a non-periodic box");
+    for (int a = 0; a < 3; a++)
+        if (!(std::fabs(center[a]) < 4096.0)) return fail(s, ORBC_E_ARG, "volume centre out of range");
+    return guarded(s, [&] {
+        HostInstance& h = s->host;
+        h.vol_kv = kv;
+        h.vol_v0 = v0;
+        h.vol_area = area_per_lipid;
+        for (int a = 0; a < 3; a++) h.vol_xc[a] = center[a];
+        if (s->have_particles && !s->dirty) s->ens->set_volume(0, kv, v0, area_per_lipid, center);
+    });
+}
+
+int orbc_get_volume(orbc_system* s, double area_per_lipid, const double* center, double* volume_out) {
+    if (!s) return ORBC_E_ARG;
+    if (!center || !volume_out || !std::isfinite(area_per_lipid)) return fail(s, ORBC_E_ARG, "invalid volume query");
+    for (int a = 0; a < 3; a++)
+        if (!(std::fabs(center[a]) < 4096.0)) return fail(s, ORBC_E_ARG, "volume centre out of range");
+    if (!s->have_particles) return fail(s, ORBC_E_STATE, "no particles");
+    double V = 0.0;
+    unsigned st = 0;
+    int rc = guarded(s, [&] {
+        sync_device(s);
+        V = s->ens->volume(0, area_per_lipid, center);
+        st = s->ens->read_status(true);
+    });
+    if (rc == ORBC_OK && st) return fail(s, status_code(st), "device status " + std::to_string(st));
+    if (rc == ORBC_OK) *volume_out = V;
+    return rc;
+}
+
+int orbc_height_map(orbc_system* s, double x0, double y0, double dx, double dy, int nx, int ny, double z_min,
+                    const double* axis, double rho_in, double rho_out, double* h_out, int* count_out) {
+    if (!s) return ORBC_E_ARG;
+    auto fin = [](double x) { return std::isfinite(x); };
+    if (!axis || !h_out || !count_out || nx < 1 || ny < 1 || (long long)nx * ny > (1ll << 24) || !(dx > 0) ||
+        !(dy > 0) || !fin(x0) || !fin(y0) || !fin(dx) || !fin(dy) || !fin(z_min) || !fin(axis[0]) || !fin(axis[1]) ||
+        std::isnan(rho_in) || std::isnan(rho_out))
+        return fail(s, ORBC_E_ARG, "invalid height map");
+    if (!s->have_particles) return fail(s, ORBC_E_STATE, "no particles");
+    return guarded(s, [&] {
+        sync_device(s);
+        s->ens->height_map(0, x0, y0, dx, dy, nx, ny, z_min, axis, rho_in, rho_out, h_out, count_out);
+    });
 }
 
 int orbc_set_wait_test(orbc_system* s, unsigned extra_tx_bytes, unsigned max_polls) {

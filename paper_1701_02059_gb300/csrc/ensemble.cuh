@@ -73,6 +73,8 @@ struct HostInstance {
     std::vector<double> r0, kb;
     std::vector<double> centroids;           // optional initial centroids [K][3]
     long long step0 = 0;                     // steps already taken
+    // harmonic volume constraint (kv = 0: off)
+    double vol_kv = 0.0, vol_v0 = 0.0, vol_area = 0.0, vol_xc[3] = {0.0, 0.0, 0.0};
 };
 
 // Bond list of one instance (ids local to the instance).
@@ -137,6 +139,13 @@ public:
     // velocity quench; returns the largest |F| at the end
     double quench(int nsteps, double dt, double max_move, double max_turn);
     void energies(std::vector<double>& out); // [B][5] after compute_forces(true)
+    // volume constraint of instance b (kv = 0: off); forces become stale
+    void set_volume(int b, double kv, double v0, double area, const double xc[3]);
+    // enclosed volume of instance b for the given area per lipid and centre
+    double volume(int b, double area, const double xc[3]);
+    // upper-rim height map of instance b (host outputs of nx * ny)
+    void height_map(int b, double x0, double y0, double dx, double dy, int nx, int ny, double z_min,
+                    const double axis[2], double rho_in, double rho_out, double* h, int* count);
 
     // host copies (instance b, id order)
     void get_state(int b, double* pos, double* vel, double* ori, double* angvel, long long* step);
@@ -193,6 +202,7 @@ public:
     void morton_relabel();
     void finish_cells();
     void launch_pairs(bool energies, bool dump);
+    void launch_volume(bool energies);       // after the pair and bond forces
     void alloc_lists();
     void launch_integrate_first(bool fused, bool msums = false);
     void launch_kick(bool energies);
@@ -286,6 +296,8 @@ public:
     bool list_valid = false;
     long long* d_xref = nullptr;
     long long* d_energy = nullptr;           // [B][8] fixed-point sums
+    long long* d_vol = nullptr;              // [B][2] enclosed volume (floors at 2^-24, remainders at 2^-48)
+    bool vol_any = false;                    // some instance has the volume constraint on
     long long* d_step = nullptr;             // [B]
     unsigned* d_dump = nullptr;
     unsigned long long* d_dump_count = nullptr;

@@ -36,10 +36,6 @@ constexpr int kQCap = 32;          // queued hits per lane before a flush
 constexpr int kMaxNbr = 32;        // neighbouring cells per pass (one per lane of the set-up warp)
 constexpr float kFilterBand = 1e-4f;
 constexpr float kCutBand = 1e-6f;
-// Largest magnitude of one pair or bond term (force or torque component,
-// eps/sigma or eps): 2^24, so that a particle's 2^-32 fixed-point sum of a
-// few hundred terms stays inside int64.
-constexpr float kMaxTerm = 16777216.0f;
 
 // ---------------------------------------------------------------- pair terms
 // Lipid pair (see the header of orbc.h for the potential).  d = x_j - x_i.
@@ -1354,6 +1350,7 @@ void Ensemble::launch_pairs(bool energies, bool dump) {
     launches++;
     CK(cudaGetLastError());
     toc();
+    if (!dump) launch_volume(energies);
 }
 
 }  // namespace orbc

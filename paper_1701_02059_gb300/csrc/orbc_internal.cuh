@@ -28,6 +28,10 @@ constexpr float kMagic = 12582912.0f;                // 1.5 * 2^23
 constexpr int kMagicBits = 0x4B400000;
 constexpr int kMaxBondsPerParticle = 8;
 constexpr int kLipid = 0;
+// Largest magnitude of one pair, bond or constraint term (force or torque
+// component, eps/sigma or eps; a volume term in sigma^3): 2^24, so that a
+// particle's 2^-32 fixed-point sum of a few hundred terms stays inside int64.
+constexpr float kMaxTerm = 16777216.0f;
 
 // ---------------------------------------------------------------- per-instance descriptor
 struct Inst {
@@ -67,6 +71,11 @@ struct Inst {
     unsigned instance;
     int rebuild_every;
     int n_lloyd;        // k-means rounds at initialisation
+    // harmonic volume constraint (off when vol_on == 0): k_V, V0, a/3 and
+    // the reference point on the 2^-40 grid
+    int vol_on;
+    double kv, v0, a3;
+    long long xcq[3];
 };
 
 // ---------------------------------------------------------------- packed device arrays
@@ -137,6 +146,9 @@ struct View {
     // wait run out while every copy still lands)
     unsigned wait_polls;
     unsigned extra_tx;
+    // [B][2] enclosed volume: sums of the 2^-24 sigma^3 floors and of the
+    // 2^-48 remainders of its terms (volume constraint)
+    long long* vol;
 };
 
 enum : unsigned {
