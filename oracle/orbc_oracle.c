@@ -1076,14 +1076,16 @@ static void or_compute(or_sys* s)
         }
     }
     /* harmonic volume constraint ("Validation and Benchmark": a harmonic
-     * volume constraint keeps the cell's surface-to-volume ratio; reading
-     * V1: the enclosed volume of a particle membrane by the divergence
-     * theorem over the lipids' area elements, V = (1/3) sum a (x_i - x_c).n_i,
-     * a the area per lipid, x_c a fixed reference point inside; V2:
-     * U_V = k_V (V - V0)^2 / 2, so with g = k_V (V - V0) a / 3 every lipid
-     * gets F -= g n_i and, from dU/dn_i = g (x_i - x_c), the torque
-     * n_i x (-g (x_i - x_c)); U_V is reported with the bond energy and
-     * adds nothing to the virial) */
+     * volume constraint keeps the cell's surface-to-volume ratio; the form
+     * is not given).  Reading V1: the enclosed volume of a particle
+     * membrane by the divergence theorem over the lipids' area elements,
+     * V = (1/3) sum a (x_i - x_c).n_i, a the area per lipid, x_c a fixed
+     * reference point inside.  Reading V2: U_V = k_V (V - V0)^2 / 2 acts as
+     * the uniform pressure P = -k_V (V - V0) on each lipid's area element,
+     * F_i += P a n_i (moving one element by delta along its normal changes
+     * the enclosed volume by a delta), and exerts no torque (a uniform
+     * pressure has no moment about the element's own centre).  U_V is
+     * reported with the bond energy and adds nothing to the virial. */
     s->vol = 0.0;
     s->u_vol = 0.0;
     if (s->vol_on) {
@@ -1093,16 +1095,10 @@ static void or_compute(or_sys* s)
             double d[3] = { s->x[3 * i] - s->xc[0], s->x[3 * i + 1] - s->xc[1], s->x[3 * i + 2] - s->xc[2] };
             V += s->a_vol * dot3(d, s->n_ + 3 * i) / 3.0;
         }
-        const double g = s->kv * (V - s->v0) * s->a_vol / 3.0;
+        const double Pa = -s->kv * (V - s->v0) * s->a_vol;
         for (int i = 0; i < n; i++) {
             if (s->type[i] != OR_LIPID) continue;
-            double d[3] = { s->x[3 * i] - s->xc[0], s->x[3 * i + 1] - s->xc[1], s->x[3 * i + 2] - s->xc[2] };
-            double gd[3] = { -g * d[0], -g * d[1], -g * d[2] }, t[3];
-            cross3(s->n_ + 3 * i, gd, t);
-            for (int c = 0; c < 3; c++) {
-                s->F[3 * i + c] -= g * s->n_[3 * i + c];
-                s->T[3 * i + c] += t[c];
-            }
+            for (int c = 0; c < 3; c++) s->F[3 * i + c] += Pa * s->n_[3 * i + c];
         }
         s->vol = V;
         s->u_vol = 0.5 * s->kv * (V - s->v0) * (V - s->v0);

@@ -3,8 +3,9 @@
 surface-to-volume ratio; the fluctuation dh(x, y) is read along the upper rim
 of the cell), checked by routes other than the oracle's own formulas: the
 volume of a sphere and of a polyhedron in closed form, invariance under the
-reference point for a centrally symmetric surface, central differences of
-the total energy, and numpy's weighted 2-D histogram and a sine's bin means.
+reference point for a centrally symmetric surface, the virtual work of a
+dilation against the closed-form volume change, and numpy's weighted 2-D
+histogram and a sine's bin means.
 """
 import math
 
@@ -77,8 +78,8 @@ def test_volume_of_an_ellipsoidal_polyhedron():
 
 def test_constraint_energy_closed_form_and_inactive_for_proteins():
     """U_V = k_V (V - V0)^2 / 2 with V = 4/3 pi R^3 (the sphere's closed
-    form, not the oracle's sum); the constraint acts on lipids only, so a
-    protein's force is unchanged by it."""
+    form, not the oracle's sum); the constraint acts on lipids only and
+    exerts no torque, so every torque and a protein's force are unchanged."""
     R = 12.0
     pos, ori, typ, a = lipid_sphere(6, R)
     # one protein at the centre, far from every lipid
@@ -95,12 +96,11 @@ def test_constraint_energy_closed_form_and_inactive_for_proteins():
     F1, T1 = s.forces()
     assert e1[1] - e0[1] == pytest.approx(0.5 * kv * (Vs - V0) ** 2, rel=1e-11)
     assert e1[0] == e0[0] and e1[4] == e0[4]                 # pair energy and virial untouched
-    assert np.array_equal(F1[-1], F0[-1]) and np.array_equal(T1[-1], T0[-1])
-    # V > V0 pushes every lipid inward along its director, with no torque
-    # (the lever arm is parallel to the director)
+    assert np.array_equal(F1[-1], F0[-1]) and np.array_equal(T1, T0)
+    # V > V0 pushes every lipid inward along its director
     dF = F1[:-1] - F0[:-1]
     assert (np.einsum("ij,ij->i", dF, ori[:-1]) < 0).all()
-    assert np.abs(T1[:-1] - T0[:-1]).max() < 1e-9 * np.abs(dF).max() * R
+    assert np.abs(np.cross(dF, ori[:-1])).max() < 1e-12 * np.abs(dF).max()
     # switching it off restores the forces exactly
     s.set_volume(0.0, V0, a, [0.0, 0.0, 0.0])
     s.compute_forces()
@@ -108,61 +108,43 @@ def test_constraint_energy_closed_form_and_inactive_for_proteins():
     assert np.array_equal(F2, F0) and np.array_equal(T2, T0)
 
 
-def _rotate(n, axis, ang):
-    axis = np.asarray(axis, float)
-    return n * math.cos(ang) + np.cross(axis, n) * math.sin(ang) + axis * np.dot(axis, n) * (1 - math.cos(ang))
+def _ellipsoid_lipids(seed=3):
+    v, f = M.icosphere_mesh(6, 1.0)
+    v = v * np.array([30.0, 22.0, 12.0])
+    out = oracle.mesh_build(v, f, beads=1, d_min=0.0, d_ll=0.0, seed=seed)
+    lip = out["type"] == 0
+    tri = v[f]
+    V_poly = np.einsum("ij,ij->i", tri[:, 0], np.cross(tri[:, 1], tri[:, 2])).sum() / 6.0
+    A = 0.5 * np.linalg.norm(np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0]), axis=1).sum()
+    return out["pos"][lip], out["ori"][lip], V_poly, A
 
 
-def test_constraint_forces_and_torques_finite_difference():
-    """Central differences of the total energy (pairs + bonds + U_V) of a
-    small vesicle whose reference point is off centre: the forces and the
-    director torques are the energy's derivatives."""
-    mem = M.vesicle(300, 5, kT=0.2, f=1, chain_beads=2, n_centroids=12)
-    m = oracle.model()
-    r = oracle.run(kT=mem.kT, n_centroids=mem.n_centroids, seed=0)
-    lip = np.flatnonzero(mem.type == 0)
-    R = mem.meta["R"]
-    a = 4.0 * math.pi * R * R / len(lip)
-    xc = [1.3, -0.7, 0.4]
-    kv = 0.05
-
-    def system(pos, ori):
-        t = oracle.OracleSystem(m, r)
-        t.set_particles(pos, mem.vel, ori, mem.angvel, mem.type, mem.id)
-        t.set_bonds(mem.bonds, mem.r0, mem.kb)
-        t.init_cells()
-        return t
-
-    s = system(mem.pos, mem.ori)
-    V = s.volume(a, xc)
-    s.set_volume(kv, 0.9 * V, a, xc)
+def test_constraint_force_does_the_virtual_work_of_a_dilation():
+    """Under the dilation x -> x_c + (1 + e)(x - x_c) the enclosed volume of
+    any shape grows by 3 e V, so the work of forces that derive from
+    U_V(true volume) is -k_V (V - V0) 3 e V_poly: checked against the
+    polyhedron's closed-form volume, and a uniform translation (no volume
+    change) does no work.  A force of a/3 per lipid, a sign error or a
+    dropped term fails."""
+    pos, ori, V_poly, A = _ellipsoid_lipids()
+    s = make(pos, ori, np.zeros(len(pos), np.uint8), n_centroids=32)
+    a = A / len(pos)
+    xc = np.array([5.0, -3.0, 2.0])
     s.compute_forces()
-    F, T = s.forces()
-    st = s.state()
-
-    def energy(pos, ori):
-        t = system(pos, ori)
-        t.set_volume(kv, 0.9 * V, a, xc)
-        e = t.compute_forces()
-        return e[0] + e[1]
-
-    h = 1e-5
-    rng = np.random.default_rng(8)
-    for i in rng.choice(lip, 5, replace=False):
-        for k in range(3):
-            p1, p2 = st["pos"].copy(), st["pos"].copy()
-            p1[i, k] += h
-            p2[i, k] -= h
-            fd = -(energy(p1, st["ori"]) - energy(p2, st["ori"])) / (2 * h)
-            assert fd == pytest.approx(F[i, k], abs=2e-5 * (1 + abs(F[i, k])))
-    for i in rng.choice(lip, 4, replace=False):
-        for k in range(3):
-            ax = np.eye(3)[k]
-            o1, o2 = st["ori"].copy(), st["ori"].copy()
-            o1[i] = _rotate(o1[i], ax, h)
-            o2[i] = _rotate(o2[i], ax, -h)
-            fd = -(energy(st["pos"], o1) - energy(st["pos"], o2)) / (2 * h)
-            assert fd == pytest.approx(T[i, k], abs=2e-5 * (1 + abs(T[i, k])))
+    F0, T0 = s.forces()
+    kv, V0 = 1e-3, 0.9 * V_poly
+    s.set_volume(kv, V0, a, xc)
+    s.compute_forces()
+    F1, T1 = s.forces()
+    dF = F1 - F0
+    V = s.volume(a, xc)
+    x = s.state()["pos"]
+    work = np.einsum("ij,ij->", dF, x - xc)                    # per unit e
+    assert work == pytest.approx(-kv * (V - V0) * 3.0 * V_poly, rel=5e-3)
+    # a translation does no work up to the face counts' rounding (a closed
+    # polyhedron's area-weighted normals sum to zero)
+    assert np.linalg.norm(dF.sum(0)) < 2e-3 * np.linalg.norm(dF, axis=1).sum()
+    assert np.array_equal(T1, T0)
 
 
 def test_constraint_drives_the_volume_toward_v0():
