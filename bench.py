@@ -56,6 +56,10 @@ PAIR_BYTES_PER_PARTICLE = 80.0
 # cell-list cadence of the skin variant
 CADENCE_EVERY = 10
 CADENCE_SKIN = 0.3
+# harmonic volume constraint of the constrained variant: k_V (eps/sigma^6),
+# V0 = the cell's initial volume; the upper-rim height map on a 32 x 32 grid
+# of 0.25 um bins over the annulus 2.5-3.9 um, upper half
+VOL_KV = 1e-6
 
 
 def workload(name: str):
@@ -319,14 +323,16 @@ def run_ours(args, rank, world):
 
     g.close()
 
-    def variant(prec, nsteps, **kw):
-        """The same step in another precision mode (or cell-list cadence), a
-        few steps on the same workload."""
+    def variant(prec, nsteps, setup=None, **kw):
+        """The same step in another precision mode (or cell-list cadence, or
+        with the volume constraint), a few steps on the same workload."""
         pv = params_for(mem, prec, G)
         for k, val in kw.items():
             setattr(pv, k, val)
         gv = G.System(pv, stream=stream.cuda_stream)
         gv.load_membrane(mem)
+        if setup is not None:
+            setup(gv)
         gv.init_cells()
         gv.integrate(3)
         gv.set_timing(True)
@@ -360,6 +366,9 @@ def run_ours(args, rank, world):
             "rebuild_every": CADENCE_EVERY, "skin_sigma": CADENCE_SKIN, "dtype": "f32",
             "speedup_over_every_step": None}
         cadence["speedup_over_every_step"] = round((ms / args.steps) / cadence["ms_per_step"], 3)
+    volume = None
+    if args.precision == "f32" and not args.no_variants and args.workload == "rbc-4m":
+        volume = volume_variant(mem, G, torch, stream, variant, args.steps, ms / args.steps)
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -413,8 +422,41 @@ def run_ours(args, rank, world):
                        "l2": "inputs larger than L2 (resident state, forces and mirrors ~1.4 GB)"},
             "roofline": roof, "kernel_ms_per_launch": breakdown, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks.summary(), "step_roofline": step_roof, "pair_roofline": pair_roof, "fp64_variant": f64,
-            "f32_increment_variant": f32step, "skin_cadence_variant": cadence, "ensemble": ens, "serve": serve}
+            "f32_increment_variant": f32step, "skin_cadence_variant": cadence, "volume_variant": volume,
+            "ensemble": ens, "serve": serve}
     return line
+
+
+def volume_variant(mem, G, torch, stream, variant, steps, plain_ms):
+    """The headline step with the harmonic volume constraint on (V0 = the
+    initial volume), and the cost of one upper-rim height map."""
+    from synth.membranes import AREA_PER_LIPID
+    a = float(AREA_PER_LIPID)
+    s = float(mem.meta["sigma_per_um"])
+
+    def on(gv):
+        gv.set_volume_constraint(VOL_KV, gv.volume(a, (0.0, 0.0, 0.0)), a, (0.0, 0.0, 0.0))
+
+    out = variant("f32", steps, setup=on) | {"dtype": "f32", "kv": VOL_KV, "v0": "initial volume",
+                                              "area_per_lipid": a}
+    out["cost_of_constraint_ms_per_step"] = round(out["ms_per_step"] - plain_ms, 4)
+    # height map: time a few calls on the same stream
+    pv = params_for(mem, "f32", G)
+    gv = G.System(pv, stream=stream.cuda_stream)
+    gv.load_membrane(mem)
+    gv.init_cells()
+    rim = (-4.0 * s, -4.0 * s, 0.25 * s, 0.25 * s, 32, 32, 0.0, (0.0, 0.0), 2.5 * s, 3.9 * s)
+    gv.height_map(*rim)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = 10
+    for _ in range(reps):
+        h, c = gv.height_map(*rim)
+    t1 = time.perf_counter()
+    gv.close()
+    out["height_map"] = {"ms_per_call": round((t1 - t0) * 1e3 / reps, 4), "bins": "32 x 32, 0.25 um",
+                         "lipids_binned": int(c.sum()), "includes": "launch, scratch, copy back, host means"}
+    return out
 
 
 def cpu_baseline(mem, budget_s=30.0, steps=None):
@@ -472,7 +514,7 @@ def run_reference(args, rank, world):
 
 
 # revisions of the kernels whose ncu summaries are committed under profiles/
-KERNEL_REV = {"k_pair_search": "search-v1", "k_pair_eval": "eval-v1", "k_baoa_d": "baoa-d-v1"}
+KERNEL_REV = {"k_pair_search": "search-v2", "k_pair_eval": "eval-v2", "k_baoa_d": "baoa-d-v2"}
 
 
 def ensemble_jobs(n_instances: int, steps: int):

@@ -339,12 +339,15 @@ ORBC_API int orbc_quench(orbc_system* s, int nsteps, double dt, double max_move,
  * each lipid's director as its surface normal):
  *   V = sum over lipids of (a / 3) (x_i - c) . n_i,   U_V = k_V (V - V0)^2 / 2,
  * a = area_per_lipid (sigma^2), c = center (sigma, a fixed point inside the
- * membrane).  With g = k_V (V - V0) a / 3 each lipid gets the force -g n_i
- * and the torque n_i x (-g (x_i - c)); U_V is added to the bond energy
- * (energies[1]) and nothing to the virial.  Each term of V is rounded to
- * 2^-48 sigma^3 before an exact integer sum, so V does not depend on the
- * order; (x_i - c).n_i is FP32 in the FP32-force modes and FP64 otherwise,
- * the factor a/3 and everything after the sum FP64.  kv = 0 switches the
+ * membrane).  U_V acts as the uniform pressure P = -k_V (V - V0) on each
+ * lipid's area element: the force P a n_i and no torque (moving one element
+ * by delta along its normal changes the enclosed volume by a delta; a
+ * uniform pressure has no moment about the element).  U_V is added to the
+ * bond energy (energies[1]) and nothing to the virial.  Each (x_i - c).n_i
+ * is rounded to 2^-48 sigma before an exact integer sum, so V does not
+ * depend on the order; (x_i - c).n_i is FP32 in the FP32-force modes and
+ * FP64 otherwise (and in orbc_get_volume), the factor a/3 and the pressure
+ * FP64, the force P a n_i FP32 or FP64 as the pair forces.  kv = 0 switches the
  * constraint off; the setting survives later orbc_set_particles calls.
  * Errors: ORBC_E_ARG (null center, kv < 0, non-finite values, a
  * non-positive area with kv > 0, a periodic axis with kv > 0), ORBC_E_CUDA. */

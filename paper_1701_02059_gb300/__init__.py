@@ -4,7 +4,8 @@ pair forces, spectrin bonds and a BAOAB Langevin integrator, all in CUDA
 kernels for sm_103a behind the C ABI of include/orbc.h.
 
 ``System`` is a thin wrapper over that ABI (host numpy arrays in, host numpy
-arrays out); it does no arithmetic of its own.
+arrays out); it does no arithmetic of its own.  ``fluctuation`` holds the
+host-side analysis of a series of height maps.
 """
 from __future__ import annotations
 

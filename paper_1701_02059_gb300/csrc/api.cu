@@ -394,6 +394,7 @@ void Ensemble::setup(const std::vector<const HostInstance*>& list) {
         inst_h[b].vol_on = h.vol_kv > 0.0;
         inst_h[b].kv = h.vol_kv;
         inst_h[b].v0 = h.vol_v0;
+        inst_h[b].avol = h.vol_area;
         inst_h[b].a3 = h.vol_area / 3.0;
         for (int a = 0; a < 3; a++) inst_h[b].xcq[a] = llrint(h.vol_xc[a] * kGrid);
         prm_h.push_back(h.prm);

@@ -296,7 +296,7 @@ public:
     bool list_valid = false;
     long long* d_xref = nullptr;
     long long* d_energy = nullptr;           // [B][8] fixed-point sums
-    long long* d_vol = nullptr;              // [B][2] enclosed volume (floors at 2^-24, remainders at 2^-48)
+    long long* d_vol = nullptr;              // [B][2] sum of (x - c).n (floors at 2^-24, remainders at 2^-48)
     bool vol_any = false;                    // some instance has the volume constraint on
     long long* d_step = nullptr;             // [B]
     unsigned* d_dump = nullptr;

@@ -71,10 +71,10 @@ struct Inst {
     unsigned instance;
     int rebuild_every;
     int n_lloyd;        // k-means rounds at initialisation
-    // harmonic volume constraint (off when vol_on == 0): k_V, V0, a/3 and
-    // the reference point on the 2^-40 grid
+    // harmonic volume constraint (off when vol_on == 0): k_V, V0, the area
+    // per lipid a, a/3 and the reference point on the 2^-40 grid
     int vol_on;
-    double kv, v0, a3;
+    double kv, v0, avol, a3;
     long long xcq[3];
 };
 
@@ -146,8 +146,9 @@ struct View {
     // wait run out while every copy still lands)
     unsigned wait_polls;
     unsigned extra_tx;
-    // [B][2] enclosed volume: sums of the 2^-24 sigma^3 floors and of the
-    // 2^-48 remainders of its terms (volume constraint)
+    // [B][2] sum of (x - c).n over the lipids (the enclosed volume is a/3
+    // times it): sums of the 2^-24 sigma floors and of the 2^-48 remainders
+    // of its terms (volume constraint)
     long long* vol;
 };
 

@@ -3,14 +3,16 @@
 //
 // Volume: V = sum over lipids of (a/3) (x_i - c) . n_i (the divergence
 // theorem with each lipid's director as its surface normal), U_V =
-// k_V (V - V0)^2 / 2.  Two launches after the pair and bond forces: the sum
-// (each term split into its 2^-24 sigma^3 floor and the remainder at
-// 2^-48, two integer sums by atomics, so V does not depend on the order),
-// then per lipid F -= g n and T += n x (-g (x - c)),
-// g = k_V (V - V0) a/3, rounded to the 2^-32 force grid and added in place.
-// FP32 terms in the FP32-force modes, FP64 when every force is FP64.  Both
-// launches read the lipids' state once: they are bound by HBM bandwidth
-// (49 and 145 bytes per lipid).
+// k_V (V - V0)^2 / 2, acting as the uniform pressure P = -k_V (V - V0) on
+// each lipid's area element: F_i += P a n_i, no torque (a uniform pressure
+// has no moment about the element's centre).  Two launches after the pair
+// and bond forces: the sum D of (x - c).n (each term split into its 2^-24
+// sigma floor and the remainder at 2^-48, two integer sums by atomics, so D
+// does not depend on the order; V = (a/3) D in FP64), then the per-lipid
+// force rounded to the 2^-32 force grid and added in place.  (x - c).n and the force are FP32 in the
+// FP32-force modes and FP64 when every force is FP64.  Both launches touch
+// each lipid once and are bound by HBM bandwidth: 49 bytes per lipid for
+// the sum (type, x, n), 73 for the force (type, n, F read and written).
 //
 // Height map: the lipids above z_min inside an annulus about a vertical
 // axis, binned on an (x, y) grid; every decision in FP64 with correctly
@@ -20,11 +22,12 @@
 
 namespace orbc {
 
-constexpr double kVolUnit = 16777216.0;                 // 2^24: volume fixed point 2^-24 sigma^3
+constexpr double kVolUnit = 16777216.0;                 // 2^24: fixed point of (x - c).n, 2^-24 sigma
 constexpr double kVolUnitInv = 5.9604644775390625e-08;  // 2^-24
 constexpr double kVolFineInv = 3.552713678800501e-15;   // 2^-48: the remainders' unit
 
-// V from its two integer sums (the 2^-24 floors and the 2^-48 remainders).
+// D = sum of (x - c).n from its two integer sums (the 2^-24 floors and the
+// 2^-48 remainders).
 __host__ __device__ inline double volume_of(long long hi, long long lo) {
     return (double)hi * kVolUnitInv + (double)lo * kVolFineInv;
 }
@@ -54,13 +57,29 @@ __device__ inline void warp_flush(long long h, long long l, int b, long long* ou
     }
 }
 
-// V per instance.  b_only < 0: every instance with the constraint on, with
-// its own a/3 and centre; b_only >= 0: that instance alone, with a3 and xc
-// given (the volume query, summed into out[0..1]).
+// One lipid's (x - c).n split exactly into its floor at 2^-24 sigma and the
+// remainder rounded at 2^-48 (integer sums of both do not depend on the
+// order; they wrap harmlessly in int64 as long as the final sum stays below
+// 2^39 sigma).  In FP32 the scaled value is an integer already when
+// |(x - c).n| >= 1, and the remainder is exact in both precisions.
+__device__ inline void split_term(float dn, long long& th, long long& tl) {
+    const float s = dn * 16777216.0f, fl = floorf(s);
+    th = __float2ll_rn(fl);
+    tl = __float2ll_rn((s - fl) * 16777216.0f);
+}
+__device__ inline void split_term(double dn, long long& th, long long& tl) {
+    const double s = dn * kVolUnit, fl = floor(s);
+    th = __double2ll_rn(fl);
+    tl = __double2ll_rn((s - fl) * kVolUnit);
+}
+
+// D = sum over lipids of (x - c).n per instance; V = (a/3) D.  b_only < 0:
+// every instance with the constraint on, with its own centre; b_only >= 0:
+// that instance alone with the centre given (the volume query, summed into
+// out[0..1]).
 template <typename T>
-__global__ void __launch_bounds__(kVolThreads) k_volume_sum(View v, int b_only, double a3_q, long long xc0,
-                                                            long long xc1, long long xc2,
-                                                            long long* __restrict__ out) {
+__global__ void __launch_bounds__(kVolThreads) k_volume_sum(View v, int b_only, long long xc0, long long xc1,
+                                                            long long xc2, long long* __restrict__ out) {
     const size_t N = v.N;
     const int stride = gridDim.x * blockDim.x;
     int cur = -1;
@@ -78,23 +97,12 @@ __global__ void __launch_bounds__(kVolThreads) k_volume_sum(View v, int b_only, 
             if (b_only >= 0 ? bi == b_only : I.vol_on != 0) {
                 const long long c[3] = {b_only >= 0 ? xc0 : I.xcq[0], b_only >= 0 ? xc1 : I.xcq[1],
                                         b_only >= 0 ? xc2 : I.xcq[2]};
-                // (x - c).n in T, the factor a/3 in FP64 (a bias in a/3
-                // would shift every term the same way)
                 T dn = 0;
                 for (int a = 0; a < 3; a++)
                     dn += to_sigma<T>(v.xq[a * N + p] - c[a]) * to_sigma<T>(v.nq[a * N + p]);
-                const double term = (b_only >= 0 ? a3_q : I.a3) * (double)dn;
-                if (!(fabs(term) < (double)kMaxTerm)) {
-                    flag_inst(v, I, term == term ? kStatusPairForceRange : kStatusNaN);
-                } else {
-                    // the floor at 2^-24 sigma^3, and the remainder (exact in
-                    // FP64) rounded at 2^-48; the int64 sums wrap harmlessly
-                    // as long as the final V stays below 2^39 sigma^3
-                    const double s = term * kVolUnit, fl = floor(s);
-                    th = (long long)fl;
-                    tl = __double2ll_rn((s - fl) * kVolUnit);
-                }
-                b = b_only >= 0 ? 0 : bi;        // the query sums into out[0]
+                if (!(fabs(dn) < (T)kMaxTerm)) flag_inst(v, I, dn == dn ? kStatusPairForceRange : kStatusNaN);
+                else split_term(dn, th, tl);
+                b = b_only >= 0 ? 0 : bi;
             }
         }
         // flush when this lane's instance changes
@@ -110,51 +118,44 @@ __global__ void __launch_bounds__(kVolThreads) k_volume_sum(View v, int b_only, 
     warp_flush(acc_h, acc_l, cur, out);
 }
 
-// Constraint forces and torques, added to F and T in place; with ENERGY the
-// constraint energy joins the bond energy.
+// Constraint forces, added to F in place; with ENERGY the constraint energy
+// joins the bond energy.
 template <typename T, bool ENERGY>
 __global__ void __launch_bounds__(kVolThreads) k_volume_apply(View v, const long long* __restrict__ vol,
                                                               long long* __restrict__ energy /* [B][8] */) {
     const size_t N = v.N;
     const int stride = gridDim.x * blockDim.x;
+    int bc = -1;
+    T pa = 0;                                      // P a of instance bc
+    bool on = false;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < (int)N; p += stride) {
         if (v.type[p] != kLipid) continue;
         const int b = find_inst(v.inst_p0, v.B, p);
         const Inst& I = v.inst[b];
-        if (!I.vol_on) continue;
-        const double Vd = volume_of(__ldg(&vol[2 * b]), __ldg(&vol[2 * b + 1]));
-        const T g = (T)(I.kv * (Vd - I.v0) * I.a3);
-        T d[3], n[3];
-        for (int a = 0; a < 3; a++) {
-            d[a] = to_sigma<T>(v.xq[a * N + p] - I.xcq[a]);
-            n[a] = to_sigma<T>(v.nq[a * N + p]);
+        if (b != bc) {
+            bc = b;
+            on = I.vol_on != 0;
+            const double V = I.a3 * volume_of(__ldg(&vol[2 * b]), __ldg(&vol[2 * b + 1]));
+            pa = (T)(-I.kv * (V - I.v0) * I.avol);
         }
-        const T f[3] = {-g * n[0], -g * n[1], -g * n[2]};
-        // n x (-g d)
-        const T tq[3] = {-g * (n[1] * d[2] - n[2] * d[1]), -g * (n[2] * d[0] - n[0] * d[2]),
-                         -g * (n[0] * d[1] - n[1] * d[0])};
+        if (!on) continue;
         for (int a = 0; a < 3; a++) {
-            if (!(fabs(f[a]) < (T)kMaxTerm) || !(fabs(tq[a]) < (T)kMaxTerm)) {
-                flag_inst(v, I, (f[a] == f[a] && tq[a] == tq[a]) ? kStatusPairForceRange : kStatusNaN);
+            const T f = pa * to_sigma<T>(v.nq[a * N + p]);
+            if (!(fabs(f) < (T)kMaxTerm)) {
+                flag_inst(v, I, f == f ? kStatusPairForceRange : kStatusNaN);
                 continue;
             }
-            long long fq, tqq;
-            if constexpr (sizeof(T) == 4) {
-                fq = __float2ll_rn(f[a] * 4294967296.0f);
-                tqq = __float2ll_rn(tq[a] * 4294967296.0f);
-            } else {
-                fq = __double2ll_rn(f[a] * 4294967296.0);
-                tqq = __double2ll_rn(tq[a] * 4294967296.0);
-            }
+            long long fq;
+            if constexpr (sizeof(T) == 4) fq = __float2ll_rn(f * 4294967296.0f);
+            else fq = __double2ll_rn(f * 4294967296.0);
             v.F[a * N + p] += fq;
-            v.T[a * N + p] += tqq;
         }
     }
     if (ENERGY && blockIdx.x == 0) {
         for (int b = threadIdx.x; b < v.B; b += blockDim.x) {
             const Inst& I = v.inst[b];
             if (!I.vol_on) continue;
-            const double dV = volume_of(vol[2 * b], vol[2 * b + 1]) - I.v0;
+            const double dV = I.a3 * volume_of(vol[2 * b], vol[2 * b + 1]) - I.v0;
             const double u = 0.5 * I.kv * dV * dV;
             if (!(u < 1073741824.0)) {          // 2^30: the 2^-32 sum stays inside int64
                 flag_inst(v, I, u == u ? kStatusPairForceRange : kStatusNaN);
@@ -179,11 +180,11 @@ void Ensemble::launch_volume(bool energies) {
     tic("volume");
     CK(cudaMemsetAsync(d_vol, 0, sizeof(long long) * 2 * B, stream));
     if (force_f64()) {
-        k_volume_sum<double><<<g, kVolThreads, 0, stream>>>(v, -1, 0.0, 0, 0, 0, d_vol);
+        k_volume_sum<double><<<g, kVolThreads, 0, stream>>>(v, -1, 0, 0, 0, d_vol);
         if (energies) k_volume_apply<double, true><<<g, kVolThreads, 0, stream>>>(v, d_vol, d_energy);
         else k_volume_apply<double, false><<<g, kVolThreads, 0, stream>>>(v, d_vol, d_energy);
     } else {
-        k_volume_sum<float><<<g, kVolThreads, 0, stream>>>(v, -1, 0.0, 0, 0, 0, d_vol);
+        k_volume_sum<float><<<g, kVolThreads, 0, stream>>>(v, -1, 0, 0, 0, d_vol);
         if (energies) k_volume_apply<float, true><<<g, kVolThreads, 0, stream>>>(v, d_vol, d_energy);
         else k_volume_apply<float, false><<<g, kVolThreads, 0, stream>>>(v, d_vol, d_energy);
     }
@@ -197,6 +198,7 @@ void Ensemble::set_volume(int b, double kv, double v0, double area, const double
     I.vol_on = kv > 0.0;
     I.kv = kv;
     I.v0 = v0;
+    I.avol = area;
     I.a3 = area / 3.0;
     for (int a = 0; a < 3; a++) I.xcq[a] = llrint(xc[a] * kGrid);
     CK(cudaMemcpyAsync(d_inst + b, &I, sizeof(Inst), cudaMemcpyHostToDevice, stream));
@@ -220,7 +222,7 @@ double Ensemble::volume(int b, double area, const double xc[3]) {
     try {
         CK(cudaMemsetAsync(d, 0, sizeof(long long) * 2, stream));
         k_volume_sum<double><<<volume_grid(N), kVolThreads, 0, stream>>>(
-            v, b, area / 3.0, llrint(xc[0] * kGrid), llrint(xc[1] * kGrid), llrint(xc[2] * kGrid), d);
+            v, b, llrint(xc[0] * kGrid), llrint(xc[1] * kGrid), llrint(xc[2] * kGrid), d);
         launches++;
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(h, d, sizeof(long long) * 2, cudaMemcpyDeviceToHost, stream));
@@ -230,7 +232,7 @@ double Ensemble::volume(int b, double area, const double xc[3]) {
         throw;
     }
     CK(cudaFreeAsync(d, stream));
-    return volume_of(h[0], h[1]);
+    return area / 3.0 * volume_of(h[0], h[1]);
 }
 
 // ---------------------------------------------------------------- height map
