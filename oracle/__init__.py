@@ -48,7 +48,7 @@ class Run(C.Structure):
     _fields_ = [("dt", C.c_double), ("kT", C.c_double), ("gamma_t", C.c_double), ("gamma_r", C.c_double),
                 ("mass", C.c_double), ("inertia", C.c_double), ("skin", C.c_double),
                 ("seed", C.c_ulonglong), ("instance", C.c_uint), ("rebuild_every", C.c_int),
-                ("n_centroids", C.c_int), ("n_lloyd_init", C.c_int)]
+                ("n_centroids", C.c_int), ("n_lloyd_init", C.c_int), ("n_protein_centroids", C.c_int)]
 
 
 TWO_SIXTH = 2.0 ** (1.0 / 6.0)
@@ -66,10 +66,11 @@ def model(eps=1.0, sigma=1.0, rc=2.6, zeta=4, mu=3.0, sin_theta0=0.0, eps_wca=1.
 
 
 def run(dt=0.01, kT=0.2, gamma_t=1.0, gamma_r=1.0, mass=1.0, inertia=1.0, skin=0.0, seed=0, instance=0,
-        rebuild_every=1, n_centroids=64, n_lloyd_init=10) -> Run:
+        rebuild_every=1, n_centroids=64, n_lloyd_init=10, n_protein_centroids=0) -> Run:
     r = Run()
     r.dt, r.kT, r.gamma_t, r.gamma_r, r.mass, r.inertia, r.skin = dt, kT, gamma_t, gamma_r, mass, inertia, skin
     r.seed, r.instance, r.rebuild_every, r.n_centroids, r.n_lloyd_init = seed, instance, rebuild_every, n_centroids, n_lloyd_init
+    r.n_protein_centroids = n_protein_centroids
     return r
 
 

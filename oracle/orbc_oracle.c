@@ -803,6 +803,7 @@ typedef struct {
     int rebuild_every;
     int n_centroids;
     int n_lloyd_init;
+    int n_protein_centroids;   /* > 0: a separate cell set for the proteins (reading D1) */
 } or_run;
 
 typedef struct {
@@ -944,17 +945,78 @@ static void or_permute(or_sys* s, const int* perm)
     for (int p = 0; p < n; p++) s->slot_of_id[s->id[p]] = p;
 }
 
+/* Separate protein cells ("Force Evaluation": for a cell whose cytoskeleton
+ * is partly or fully detached, the proteins get a Voronoi cell set of their
+ * own).  Reading D1: with K_P = n_protein_centroids > 0, cells 0..K_L-1
+ * cluster the lipids and K_L..K_L+K_P-1 the proteins; each particle belongs
+ * to the nearest centroid of its own set, and each centroid moves to the
+ * mean of its own members.  Reading D2: the neighbouring-cell rule is the
+ * same over both sets together, so the quad loop over a cell and its
+ * neighbours finds lipid-lipid, lipid-protein and protein-protein pairs.
+ * Reading D3: each set is numbered along its own Morton curve (the box of
+ * its own centroids), lipid cells first. */
+static int or_kp(const or_sys* s) { return s->r.n_protein_centroids > 0 ? s->r.n_protein_centroids : 0; }
+
+/* E-step: the nearest centroid of each particle's own set. */
+static void or_assign_sets(or_sys* s)
+{
+    const int KP = or_kp(s), KL = s->K - KP, n = s->n;
+    if (KP == 0) {
+        or_assign_kdtree(n, s->x, s->K, s->c, s->m.box, s->m.periodic, s->cell);
+        return;
+    }
+    double* xs = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    int* idx = (int*)malloc(sizeof(int) * (size_t)n);
+    int* cs = (int*)malloc(sizeof(int) * (size_t)n);
+    for (int set = 0; set < 2; set++) {
+        int m = 0;
+        for (int i = 0; i < n; i++) {
+            if ((s->type[i] != OR_LIPID) != set) continue;
+            for (int a = 0; a < 3; a++) xs[3 * m + a] = s->x[3 * i + a];
+            idx[m++] = i;
+        }
+        const int Ks = set ? KP : KL, k0 = set ? KL : 0;
+        if (m > 0) or_assign_kdtree(m, xs, Ks, s->c + 3 * (size_t)k0, s->m.box, s->m.periodic, cs);
+        for (int q = 0; q < m; q++) s->cell[idx[q]] = k0 + cs[q];
+    }
+    free(xs); free(idx); free(cs);
+}
+
+/* M-step: lipids only for the shared cells; with separate sets every
+ * particle is a member of its own set's cell. */
+static void or_mstep_sets(or_sys* s, double* c_out)
+{
+    if (or_kp(s) == 0) {
+        or_lloyd(s->n, s->x, s->type, s->cell, s->K, s->c, c_out, s->m.box, s->m.periodic);
+        return;
+    }
+    unsigned char* all = (unsigned char*)calloc((size_t)s->n, 1);   /* every particle counted */
+    or_lloyd(s->n, s->x, all, s->cell, s->K, s->c, c_out, s->m.box, s->m.periodic);
+    free(all);
+}
+
+/* Morton order of each set's centroids, order[new] = old. */
+static void or_morton_sets(const or_sys* s, int* order)
+{
+    const int KP = or_kp(s), KL = s->K - KP;
+    or_morton_order(KL, s->c, order);
+    if (KP > 0) {
+        or_morton_order(KP, s->c + 3 * (size_t)KL, order + KL);
+        for (int k = KL; k < s->K; k++) order[k] += KL;
+    }
+}
+
 /* Morton relabel of the centroids, E-step, stable sort, radii, adjacency. */
 static int or_finish_cells(or_sys* s)
 {
     int K = s->K, n = s->n;
     int* order = (int*)malloc(sizeof(int) * (size_t)K);
-    or_morton_order(K, s->c, order);
+    or_morton_sets(s, order);
     double* cn = (double*)malloc(sizeof(double) * 3 * (size_t)K);
     for (int k = 0; k < K; k++) for (int a = 0; a < 3; a++) cn[3 * k + a] = s->c[3 * order[k] + a];
     memcpy(s->c, cn, sizeof(double) * 3 * (size_t)K);
     free(cn); free(order);
-    or_assign_kdtree(n, s->x, K, s->c, s->m.box, s->m.periodic, s->cell);
+    or_assign_sets(s);
     int* perm = (int*)malloc(sizeof(int) * (size_t)n);
     or_counting_sort(n, s->cell, K, perm, s->start);
     or_permute(s, perm);
@@ -972,13 +1034,36 @@ static int or_finish_cells(or_sys* s)
     return 0;
 }
 
+/* Seeds centroids c[0..K) from the particles of one set in id order
+ * (c_k = member floor(k M / K)). */
+static int or_seed_set(or_sys* s, int proteins, int K, double* c)
+{
+    int m = 0;
+    for (int i = 0; i < s->n; i++) if ((s->type[i] != OR_LIPID) == proteins) m++;
+    if (m < K) return -1;
+    int* mem = (int*)malloc(sizeof(int) * (size_t)(m > 0 ? m : 1));
+    int q = 0;
+    for (int idv = 0; idv <= s->max_id; idv++) {
+        int slot = s->slot_of_id[idv];
+        if (slot >= 0 && (s->type[slot] != OR_LIPID) == proteins) mem[q++] = slot;
+    }
+    for (int k = 0; k < K; k++) {
+        long long pick = ((long long)k * m) / K;
+        for (int a = 0; a < 3; a++) c[3 * k + a] = s->x[3 * mem[pick] + a];
+    }
+    free(mem);
+    return 0;
+}
+
 /* Initial k-means: centroids given, or seeded from the lipids in id order
- * (c_k = lipid floor(k N_L / K)); then n_lloyd_init rounds of [E-step over
- * all particles, M-step over lipids]; then the two-level reorder. */
+ * (c_k = lipid floor(k N_L / K)), with separate protein cells the protein
+ * centroids likewise from the proteins; then n_lloyd_init rounds of
+ * [E-step, M-step] (shared cells: E over all particles, M over lipids);
+ * then the two-level reorder. */
 int or_sys_init_cells(or_sys* s, const double* centroids)
 {
-    int K = s->r.n_centroids, n = s->n;
-    if (K <= 0) return -1;
+    int K = s->r.n_centroids + or_kp(s), n = s->n;
+    if (s->r.n_centroids <= 0) return -1;
     s->K = K;
     free(s->c); free(s->R); free(s->start); free(s->adj_ptr);
     s->c = (double*)malloc(sizeof(double) * 3 * (size_t)K);
@@ -988,30 +1073,18 @@ int or_sys_init_cells(or_sys* s, const double* centroids)
     if (centroids) {
         memcpy(s->c, centroids, sizeof(double) * 3 * (size_t)K);
     } else {
-        /* lipids in id order */
-        int nl = 0;
-        for (int i = 0; i < n; i++) if (s->type[i] == OR_LIPID) nl++;
-        if (nl < K) return -1;
-        int* lip = (int*)malloc(sizeof(int) * (size_t)nl);
-        int q = 0;
-        for (int idv = 0; idv <= s->max_id; idv++) {
-            int slot = s->slot_of_id[idv];
-            if (slot >= 0 && s->type[slot] == OR_LIPID) lip[q++] = slot;
-        }
-        for (int k = 0; k < K; k++) {
-            long long pick = ((long long)k * nl) / K;
-            for (int a = 0; a < 3; a++) s->c[3 * k + a] = s->x[3 * lip[pick] + a];
-        }
-        free(lip);
+        if (or_seed_set(s, 0, s->r.n_centroids, s->c) != 0) return -1;
+        if (or_kp(s) > 0 && or_seed_set(s, 1, or_kp(s), s->c + 3 * (size_t)s->r.n_centroids) != 0) return -1;
     }
     for (int k = 0; k < K; k++) for (int a = 0; a < 3; a++)
         s->c[3 * k + a] = or_centroid_on_grid(s->c[3 * k + a], s->m.box[a], s->m.periodic[a]);
     double* cn = (double*)malloc(sizeof(double) * 3 * (size_t)K);
     for (int it = 0; it < s->r.n_lloyd_init; it++) {
-        or_assign_kdtree(n, s->x, K, s->c, s->m.box, s->m.periodic, s->cell);
-        or_lloyd(n, s->x, s->type, s->cell, K, s->c, cn, s->m.box, s->m.periodic);
+        or_assign_sets(s);
+        or_mstep_sets(s, cn);
         memcpy(s->c, cn, sizeof(double) * 3 * (size_t)K);
     }
+    (void)n;
     free(cn);
     return or_finish_cells(s);
 }
@@ -1022,7 +1095,7 @@ int or_sys_rebuild(or_sys* s)
 {
     if (!s->cells_valid) return -1;
     double* cn = (double*)malloc(sizeof(double) * 3 * (size_t)s->K);
-    or_lloyd(s->n, s->x, s->type, s->cell, s->K, s->c, cn, s->m.box, s->m.periodic);
+    or_mstep_sets(s, cn);
     memcpy(s->c, cn, sizeof(double) * 3 * (size_t)s->K);
     free(cn);
     return or_finish_cells(s);

@@ -314,9 +314,13 @@ def biconcave_mesh(n_vertices: int, n_lipids: int = 3_571_024):
 
 def vesicle(n_lipids: int, seed: int, kT: float = 0.2, f: int | None = None,
             chain_beads: int = 20, slack: float = 0.03, kb: float = 100.0,
-            n_centroids: int | None = None, jitter: float = 0.05, name: str = "vesicle") -> Membrane:
+            n_centroids: int | None = None, jitter: float = 0.05, name: str = "vesicle",
+            net_offset: float = 1.0, detach_upper: float = 0.0) -> Membrane:
     """Closed vesicle: Fibonacci-sphere lipids at 1.12 sigma spacing with
-    outward orientations; icosphere spectrin network 1 sigma inside."""
+    outward orientations; icosphere spectrin network net_offset sigma inside
+    (1 sigma: attached).  detach_upper > 0 moves the junctions of the upper
+    hemisphere (z > 0) that much further in (a partly detached network; its
+    chains then run straight between their junctions)."""
     rng = _rng(seed)
     R = math.sqrt(n_lipids * AREA_PER_LIPID / (4.0 * math.pi))
     u = fibonacci_sphere(n_lipids)
@@ -327,12 +331,15 @@ def vesicle(n_lipids: int, seed: int, kT: float = 0.2, f: int | None = None,
     lo = lp / np.linalg.norm(lp, axis=1, keepdims=True)
     if f is None:
         f = max(1, round(math.sqrt(n_lipids / 1105.0)))
-    Rn = R - 1.0
+    Rn = R - net_offset
     vj, edges = icosphere(f)
     jp = vj * Rn
+    if detach_upper > 0.0:
+        jp[vj[:, 2] > 0.0] *= (Rn - detach_upper) / Rn
     beads, bonds, r0, kbs = _chains(jp, edges, chain_beads, n_lipids, n_lipids + len(jp),
                                     lambda L: (1.0 + slack) * L / (chain_beads + 1), kb,
-                                    project=lambda q: q * (Rn / np.linalg.norm(q, axis=1, keepdims=True)))
+                                    project=None if detach_upper > 0.0 else
+                                    (lambda q: q * (Rn / np.linalg.norm(q, axis=1, keepdims=True))))
     if n_centroids is None:
         n_centroids = max(1, round((n_lipids + len(jp) + len(beads)) / 61))
     return _assemble(name, lp, lo, jp, beads, bonds, r0, kbs, [0.0, 0.0, 0.0], [0, 0, 0],
@@ -395,11 +402,13 @@ def _ef_points(n, cdf, scale):
 
 def biconcave(n_lipids: int = 3_571_024, n_junctions: int = 33_000, seed: int = 2,
               kT: float = 0.2, chain_beads: int = 4, slack: float = 0.03, kb: float = 100.0,
-              n_centroids: int = 65_536, jitter: float = 0.05, name: str = "rbc") -> Membrane:
+              n_centroids: int = 65_536, jitter: float = 0.05, name: str = "rbc",
+              net_offset: float = 1.0) -> Membrane:
     """Whole biconcave red cell (Evans-Fung profile, diameter 7.82 um) mapped
     to reduced units so the lipid area per particle is that of a 1.12 sigma
     hexagonal packing.  Junctions form a triangulated network 1 sigma inside
-    the lipid surface; every network edge carries `chain_beads` beads."""
+    the lipid surface (net_offset sigma: 1 is attached, more is a detached
+    network); every network edge carries `chain_beads` beads."""
     from scipy.spatial import ConvexHull
 
     rng = _rng(seed)
@@ -410,7 +419,7 @@ def biconcave(n_lipids: int = 3_571_024, n_junctions: int = 33_000, seed: int = 
     noise -= np.sum(noise * lo, axis=1, keepdims=True) * lo
     lp = lp + noise
     jpos, jn, jsph = _ef_points(n_junctions, cdf, scale)
-    jpos = jpos - jn                                                # 1 sigma inside
+    jpos = jpos - net_offset * jn                                   # net_offset sigma inside
     hull = ConvexHull(jsph)
     e = np.concatenate([hull.simplices[:, [0, 1]], hull.simplices[:, [1, 2]], hull.simplices[:, [2, 0]]])
     e.sort(axis=1)
@@ -440,6 +449,12 @@ def rbc_4m(seed: int = 2) -> Membrane:
     """4,000,000-particle biconcave red cell: 3,571,024 lipids, 33,000
     junctions, 98,994 four-bead chains, 65,536 Voronoi centroids."""
     return biconcave(seed=seed)
+
+
+def rbc_4m_detached(seed: int = 2, depth: float = 6.0) -> Membrane:
+    """The 4,000,000-particle cell with its whole protein network detached:
+    the junctions `depth` sigma inside the lipid surface instead of 1."""
+    return biconcave(seed=seed, net_offset=depth, name="rbc-detached")
 
 
 def ensemble_member(i: int) -> Membrane:
