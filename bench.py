@@ -60,6 +60,10 @@ CADENCE_SKIN = 0.3
 # V0 = the cell's initial volume; the upper-rim height map on a 32 x 32 grid
 # of 0.25 um bins over the annulus 2.5-3.9 um, upper half
 VOL_KV = 1e-6
+# the detached-network variant: the 4M cell with its junctions 6 sigma inside
+# the lipid surface, run with the lipid cells shared and with a protein cell
+# set of its own (about 52 proteins per cell)
+DETACHED_KP = 8192
 
 
 def workload(name: str):
@@ -366,9 +370,10 @@ def run_ours(args, rank, world):
             "rebuild_every": CADENCE_EVERY, "skin_sigma": CADENCE_SKIN, "dtype": "f32",
             "speedup_over_every_step": None}
         cadence["speedup_over_every_step"] = round((ms / args.steps) / cadence["ms_per_step"], 3)
-    volume = None
+    volume = detached = None
     if args.precision == "f32" and not args.no_variants and args.workload == "rbc-4m":
         volume = volume_variant(mem, G, torch, stream, variant, args.steps, ms / args.steps)
+        detached = detached_variant(G, torch, stream, args.steps)
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -423,8 +428,42 @@ def run_ours(args, rank, world):
             "roofline": roof, "kernel_ms_per_launch": breakdown, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks.summary(), "step_roofline": step_roof, "pair_roofline": pair_roof, "fp64_variant": f64,
             "f32_increment_variant": f32step, "skin_cadence_variant": cadence, "volume_variant": volume,
+            "detached_variant": detached,
             "ensemble": ens, "serve": serve}
     return line
+
+
+def detached_variant(G, torch, stream, steps):
+    """The 4M cell with a detached protein network, every step rebuilt, with
+    the lipid cells shared by the proteins and with a protein cell set of
+    its own (the same trajectory bit for bit)."""
+    from synth import membranes as M
+    mem = M.rbc_4m_detached()
+    out = {"workload": "rbc-4m, junctions 6 sigma inside the lipid surface", "particles": mem.n,
+           "lipid_cells": mem.n_centroids, "protein_cells": DETACHED_KP}
+    for name, kp in (("shared_cells", 0), ("separate_cells", DETACHED_KP)):
+        p = params_for(mem, "f32", G)
+        p.n_protein_centroids = kp
+        g = G.System(p, stream=stream.cuda_stream)
+        g.load_membrane(mem)
+        g.init_cells()
+        g.integrate(3)
+        g.set_timing(True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.integrate(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        kt = {k: round(v["ms"] / max(v["launches"], 1), 4) for k, v in g.kernel_times().items()}
+        R = g.cells()["radius"]
+        g.close()
+        out[name] = {"value": round(mem.n * steps / (t * 1e-3), 1), "unit": UNIT, "ms_per_step": round(t / steps, 4),
+                     "largest_lipid_cell_radius": round(float(R[:mem.n_centroids].max()), 3),
+                     "kernel_ms_per_launch": kt}
+    out["speedup_of_separate_cells"] = round(out["shared_cells"]["ms_per_step"] / out["separate_cells"]["ms_per_step"], 3)
+    return out
 
 
 def volume_variant(mem, G, torch, stream, variant, steps, plain_ms):

@@ -111,6 +111,8 @@ typedef struct {
     unsigned long long seed;
     unsigned instance;                             /* Philox key word, per ensemble member */
     orbc_precision precision;
+    int n_protein_centroids;                       /* > 0: a separate cell set for the     */
+                                                   /* proteins (detached cytoskeleton)     */
 } orbc_params;
 
 typedef struct orbc_system orbc_system;   /* opaque; owns its device memory */
@@ -120,7 +122,19 @@ typedef struct orbc_system orbc_system;   /* opaque; owns its device memory */
  * dt = 0.01, kT = 0.2,
  * gamma_t = gamma_r = 1, mass = inertia = 1, no periodic axis,
  * n_centroids = 64, n_lloyd_init = 10, rebuild_every = 1, skin = 0,
- * grid_h = 0, seed = 0, instance = 0, ORBC_F32_FORCE_F64_STATE. */
+ * grid_h = 0, seed = 0, instance = 0, ORBC_F32_FORCE_F64_STATE,
+ * n_protein_centroids = 0.
+ *
+ * Separate protein cells ("Force Evaluation": a cell whose cytoskeleton is
+ * partly or fully detached from the bilayer gets a separate set of Voronoi
+ * cells for its proteins): with n_protein_centroids = K_P > 0, cells
+ * 0..K_L-1 (K_L = n_centroids) cluster the lipids and K_L..K_L+K_P-1 the
+ * proteins; each particle belongs to the nearest centroid of its own set,
+ * each centroid is the mean of its own members, each set is numbered along
+ * its own Morton curve, and the neighbouring-cell rule runs over both sets
+ * together, so the pair search finds every type pair.  The ids must then be
+ * type-major (the lipids hold ids 0..N_L-1) and every bond joins two
+ * proteins; the arena does not take such systems. */
 ORBC_API void orbc_default_params(orbc_params* p);
 
 /* Creates a handle.  cuda_stream is a cudaStream_t (NULL = the library's own

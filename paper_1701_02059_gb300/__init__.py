@@ -108,7 +108,7 @@ class System:
                     "orbc_create")
         self.params = params
         self.n = 0
-        self.K = params.n_centroids
+        self.K = params.n_centroids + params.n_protein_centroids   # lipid cells, then protein cells
 
     def _check(self, rc, what):
         if rc != 0:

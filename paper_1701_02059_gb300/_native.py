@@ -41,7 +41,7 @@ class Params(C.Structure):
                 ("box", C.c_double * 3), ("periodic", C.c_int * 3),
                 ("n_centroids", C.c_int), ("n_lloyd_init", C.c_int), ("rebuild_every", C.c_int),
                 ("skin", C.c_double), ("grid_h", C.c_double), ("seed", C.c_ulonglong), ("instance", C.c_uint),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("n_protein_centroids", C.c_int)]
 
 
 class MeshParams(C.Structure):

@@ -390,7 +390,11 @@ void Ensemble::setup(const std::vector<const HostInstance*>& list) {
         inst_h[b] = make_inst(h.prm);
         inst_h[b].p0 = N; inst_h[b].n = h.n;
         inst_h[b].k0 = Ktot; inst_h[b].K = h.prm.n_centroids;
-        inst_h[b].nlip = (int)std::count(h.type.begin(), h.type.end(), (unsigned char)kLipid);
+        inst_h[b].partner = h.partner;
+        inst_h[b].id_base = h.id_base;
+        inst_h[b].all_members = h.all_members;
+        // centroid members: the lipids, or every particle of a protein cell set
+        inst_h[b].nlip = h.all_members ? h.n : (int)std::count(h.type.begin(), h.type.end(), (unsigned char)kLipid);
         inst_h[b].vol_on = h.vol_kv > 0.0;
         inst_h[b].kv = h.vol_kv;
         inst_h[b].v0 = h.vol_v0;
@@ -462,7 +466,8 @@ void Ensemble::setup(const std::vector<const HostInstance*>& list) {
         if (!h.centroids.empty()) {
             for (int q = 0; q < 3 * K; q++) c[q] = llrint(h.centroids[q] * kGrid);
         } else {
-            // lipids in id order, centroid k = lipid floor(k N_L / K)
+            // members (lipids, or every particle of a protein cell set) in
+            // id order, centroid k = member floor(k M / K)
             std::vector<int> by_id(h.n);
             parallel_for(h.n, [&](long long i0, long long i1) {
                 for (long long i = i0; i < i1; i++) by_id[h.id[i]] = (int)i;
@@ -474,7 +479,7 @@ void Ensemble::setup(const std::vector<const HostInstance*>& list) {
             parallel_for(nch, [&](long long c0, long long c1) {
                 for (long long ch = c0; ch < c1; ch++)
                     for (long long idv = ch * per; idv < std::min<long long>(h.n, (ch + 1) * per); idv++)
-                        cnt[ch + 1] += h.type[by_id[idv]] == kLipid;
+                        cnt[ch + 1] += h.all_members || h.type[by_id[idv]] == kLipid;
             }, 1);
             for (int ch = 0; ch < nch; ch++) cnt[ch + 1] += cnt[ch];
             std::vector<int> lip((size_t)cnt[nch]);
@@ -482,10 +487,11 @@ void Ensemble::setup(const std::vector<const HostInstance*>& list) {
                 for (long long ch = c0; ch < c1; ch++) {
                     long long o = cnt[ch];
                     for (long long idv = ch * per; idv < std::min<long long>(h.n, (ch + 1) * per); idv++)
-                        if (h.type[by_id[idv]] == kLipid) lip[(size_t)o++] = by_id[idv];
+                        if (h.all_members || h.type[by_id[idv]] == kLipid) lip[(size_t)o++] = by_id[idv];
                 }
             }, 1);
-            if ((int)lip.size() < K) throw ArgError("more centroids than lipids");
+            if ((int)lip.size() < K)
+                throw ArgError(h.all_members ? "more protein centroids than proteins" : "more centroids than lipids");
             for (int k = 0; k < K; k++) {
                 int s = lip[(size_t)((long long)k * (long long)lip.size() / K)];
                 for (int a = 0; a < 3; a++) c[(size_t)3 * k + a] = h.xq[(size_t)3 * s + a];
@@ -496,8 +502,11 @@ void Ensemble::setup(const std::vector<const HostInstance*>& list) {
                 if (I.periodic[a]) c[(size_t)3 * k + a] = floor_mod_ll(c[(size_t)3 * k + a], I.boxq[a]);
         for (int k = 0; k < K; k++)
             for (int a = 0; a < 3; a++) c0[(size_t)a * Ktot + I.k0 + k] = c[(size_t)3 * k + a];
-        // grid: edge ~ centroid spacing on a membrane of this many lipids
-        double hgrid = h.prm.grid_h > 0 ? h.prm.grid_h : std::sqrt(1.0863 * std::max(I.nlip, 1) / (double)K);
+        // grid: edge ~ centroid spacing on a membrane of this many lipids (a
+        // protein cell set spreads its K centroids over its partner's
+        // membrane: the lipid count measures the area)
+        const int area_n = (I.all_members && I.partner >= 0) ? inst_h[I.partner].nlip : I.nlip;
+        double hgrid = h.prm.grid_h > 0 ? h.prm.grid_h : std::sqrt(1.0863 * std::max(area_n, 1) / (double)K);
         hgrid = std::max(hgrid, 1.0);
         double lo[3], hi[3];
         for (int a = 0; a < 3; a++) {
@@ -709,6 +718,52 @@ void Ensemble::get_cells(int b, int* cell_of_id, unsigned* slot_ids, double* cen
     }
 }
 
+// The cells of every instance of the batch as one list (global cell
+// numbers, ids offset by each instance's id_base): a membrane with separate
+// protein cells, or a single instance.
+void Ensemble::get_cells_all(int* cell_of_id, unsigned* slot_ids, double* centroids, int* cell_start, double* radius,
+                             int* adj_ptr, int* adj) {
+    adjacency_csr();
+    std::vector<unsigned> ids(N);
+    std::vector<int> cl(N);
+    CK(cudaMemcpyAsync(ids.data(), d_id[cur_], sizeof(unsigned) * N, cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(cl.data(), d_cell, sizeof(int) * N, cudaMemcpyDeviceToHost, stream));
+    std::vector<int> cs(Ktot + 1), ap(Ktot + 1);
+    CK(cudaMemcpyAsync(cs.data(), d_cell_start, sizeof(int) * (Ktot + 1), cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(ap.data(), d_adj_ptr, sizeof(int) * (Ktot + 1), cudaMemcpyDeviceToHost, stream));
+    std::vector<double> R(Ktot);
+    CK(cudaMemcpyAsync(R.data(), d_R, sizeof(double) * Ktot, cudaMemcpyDeviceToHost, stream));
+    std::vector<long long> c((size_t)3 * Ktot);
+    CK(cudaMemcpyAsync(c.data(), d_cq, sizeof(long long) * 3 * Ktot, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    for (int b = 0; b < B; b++)
+        for (int i = inst_h[b].p0; i < inst_h[b].p0 + inst_h[b].n; i++) ids[i] += (unsigned)inst_h[b].id_base;
+    for (int i = 0; i < N; i++) {
+        if (cell_of_id) cell_of_id[ids[i]] = cl[i];
+        if (slot_ids) slot_ids[i] = ids[i];
+    }
+    if (centroids)
+        for (int k = 0; k < Ktot; k++)
+            for (int a = 0; a < 3; a++) centroids[(size_t)3 * k + a] = (double)c[(size_t)a * Ktot + k] * kGridInv;
+    if (cell_start) std::copy(cs.begin(), cs.end(), cell_start);
+    if (radius) std::copy(R.begin(), R.end(), radius);
+    if (adj_ptr) for (int k = 0; k <= Ktot; k++) adj_ptr[k] = ap[k] - ap[0];
+    if (adj) {
+        const long long L = ap[Ktot] - ap[0];
+        if (L > 0) CK(cudaMemcpyAsync(adj, d_adj + ap[0], sizeof(int) * L, cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+    }
+}
+
+long long Ensemble::adjacency_len_all() {
+    adjacency_csr();
+    int ap[2];
+    CK(cudaMemcpyAsync(&ap[0], d_adj_ptr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(&ap[1], d_adj_ptr + Ktot, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    return ap[1] - ap[0];
+}
+
 long long Ensemble::adjacency_len(int b) {
     adjacency_csr();
     const Inst& I = inst_h[b];
@@ -721,7 +776,8 @@ long long Ensemble::adjacency_len(int b) {
 
 long long Ensemble::dump_pairs(int b, long long cap, unsigned* pairs) {
     if (!cells_valid) throw StateError("cells not initialised");
-    if (B != 1) throw ArgError("pair dump is available for single-instance systems");
+    if (B != 1 && !(B == 2 && inst_h[0].partner == 1))
+        throw ArgError("pair dump is available for single-membrane systems");
     (void)b;
     // cap == 0 or no output: count only
     long long want = pairs ? cap : 0;
@@ -791,6 +847,7 @@ struct orbc_system {
     bool own_stream = false;
     Ensemble* ens = nullptr;
     HostInstance host;
+    HostInstance parts[2];     // the lipid and protein cell sets while they are set up
     bool have_particles = false;
     bool dirty = false;        // the host copy is newer than the device (set-up pending)
     bool host_stale = false;   // the device has stepped past the host copy
@@ -799,12 +856,92 @@ struct orbc_system {
 
 static void pull_state(orbc_system* s);
 
+// Separate protein cells: the membrane runs as two instances of one batch,
+// its lipids (the lipid cell set) and its proteins (the protein cell set),
+// each the other's partner: their neighbour rows hold the cells of both
+// sets, and the proteins' ids, Philox counters and pair dumps are offset by
+// N_L.  Type-major ids keep every particle's id.
+static void split_sets(const HostInstance& h, HostInstance& L, HostInstance& P) {
+    const int n = h.n;
+    const int nl = (int)std::count(h.type.begin(), h.type.end(), (unsigned char)kLipid);
+    for (int i = 0; i < n; i++)
+        if ((h.type[i] == kLipid) != ((int)h.id[i] < nl))
+            throw ArgError("separate protein cells need type-major ids (the lipids hold ids 0..N_L-1)");
+    if (nl < 1 || nl == n) throw ArgError("separate protein cells need lipids and proteins");
+    L = HostInstance();
+    P = HostInstance();
+    L.prm = h.prm;
+    L.prm.n_protein_centroids = 0;
+    P.prm = h.prm;
+    P.prm.n_centroids = h.prm.n_protein_centroids;
+    P.prm.n_protein_centroids = 0;
+    L.n = nl;
+    P.n = n - nl;
+    HostInstance* to[2] = {&L, &P};
+    for (HostInstance* t : to) {
+        t->xq.resize((size_t)3 * t->n); t->vq.resize((size_t)3 * t->n);
+        t->nq.resize((size_t)3 * t->n); t->wq.resize((size_t)3 * t->n);
+        t->type.reserve(t->n); t->id.reserve(t->n);
+    }
+    int o[2] = {0, 0};
+    for (int i = 0; i < n; i++) {
+        const int w = h.type[i] == kLipid ? 0 : 1;
+        HostInstance& t = *to[w];
+        for (int a = 0; a < 3; a++) {
+            t.xq[(size_t)3 * o[w] + a] = h.xq[(size_t)3 * i + a];
+            t.vq[(size_t)3 * o[w] + a] = h.vq[(size_t)3 * i + a];
+            t.nq[(size_t)3 * o[w] + a] = h.nq[(size_t)3 * i + a];
+            t.wq[(size_t)3 * o[w] + a] = h.wq[(size_t)3 * i + a];
+        }
+        t.type.push_back(h.type[i]);
+        t.id.push_back(w ? h.id[i] - (unsigned)nl : h.id[i]);
+        o[w]++;
+    }
+    for (size_t q = 0; q < h.r0.size(); q++) {
+        const int a = h.bonds[2 * q], b = h.bonds[2 * q + 1];
+        if (a < nl || b < nl) throw ArgError("with separate protein cells every bond joins two proteins");
+        P.bonds.push_back(a - nl);
+        P.bonds.push_back(b - nl);
+        P.r0.push_back(h.r0[q]);
+        P.kb.push_back(h.kb[q]);
+    }
+    if (!h.centroids.empty()) {
+        const size_t kl = (size_t)3 * h.prm.n_centroids;
+        L.centroids.assign(h.centroids.begin(), h.centroids.begin() + kl);
+        P.centroids.assign(h.centroids.begin() + kl, h.centroids.end());
+    }
+    L.step0 = P.step0 = h.step0;
+    L.vol_kv = h.vol_kv; L.vol_v0 = h.vol_v0; L.vol_area = h.vol_area;
+    for (int a = 0; a < 3; a++) L.vol_xc[a] = h.vol_xc[a];
+    L.partner = 1; P.partner = 0;
+    P.id_base = nl;
+    P.all_members = 1;
+}
+
 // The device set-up runs once, when a call first needs the device after the
 // particles or bonds changed.
 static void sync_device(orbc_system* s) {
     if (!s->dirty) return;
-    s->ens->setup(s->host);
+    if (s->prm.n_protein_centroids > 0) {
+        split_sets(s->host, s->parts[0], s->parts[1]);
+        s->ens->setup(std::vector<const HostInstance*>{&s->parts[0], &s->parts[1]});
+        s->parts[0] = HostInstance();
+        s->parts[1] = HostInstance();
+    } else {
+        s->ens->setup(s->host);
+    }
     s->dirty = false;
+}
+
+// The handle's membrane from every instance of its batch, in id order (each
+// instance's ids start at its id_base).
+static void sys_get_state(orbc_system* s, double* pos, double* vel, double* ori, double* angvel, long long* step) {
+    Ensemble& e = *s->ens;
+    for (int b = 0; b < e.B; b++) {
+        const size_t o = (size_t)3 * e.inst_h[b].id_base;
+        e.get_state(b, pos ? pos + o : nullptr, vel ? vel + o : nullptr, ori ? ori + o : nullptr,
+                    angvel ? angvel + o : nullptr, b == 0 ? step : nullptr);
+    }
 }
 
 // Current device state back into the host copy (exact: grid values), so a
@@ -814,7 +951,7 @@ static void pull_state(orbc_system* s) {
     const int n = h.n;
     std::vector<double> pos((size_t)3 * n), vel((size_t)3 * n), ori((size_t)3 * n), w((size_t)3 * n);
     long long step = 0;
-    s->ens->get_state(0, pos.data(), vel.data(), ori.data(), w.data(), &step);
+    sys_get_state(s, pos.data(), vel.data(), ori.data(), w.data(), &step);
     std::vector<unsigned> ids(n);
     for (int i = 0; i < n; i++) ids[i] = (unsigned)i;
     std::vector<unsigned char> ty(n);
@@ -851,6 +988,7 @@ Params orbc::to_params(const orbc_params* p) {
     P.n_centroids = p->n_centroids; P.n_lloyd_init = p->n_lloyd_init; P.rebuild_every = p->rebuild_every;
     P.skin = p->skin; P.grid_h = p->grid_h; P.seed = p->seed; P.instance = p->instance;
     P.precision = (int)p->precision;
+    P.n_protein_centroids = p->n_protein_centroids;
     return P;
 }
 
@@ -871,6 +1009,7 @@ void orbc::check_params(const Params& P) {
     if (P.rebuild_every > 1 && !(P.skin > 0)) throw ArgError("rebuild_every > 1 needs a positive skin");
     if (!(P.skin >= 0 && fin(P.skin)) || !(P.grid_h >= 0 && fin(P.grid_h))) throw ArgError("invalid skin or grid_h");
     if (P.precision < 0 || P.precision > 2) throw ArgError("unknown precision");
+    if (P.n_protein_centroids < 0) throw ArgError("n_protein_centroids must be >= 0");
 }
 
 
@@ -976,6 +1115,7 @@ void orbc_default_params(orbc_params* p) {
     p->dt = 0.01; p->kT = 0.2; p->gamma_t = 1.0; p->gamma_r = 1.0; p->mass = 1.0; p->inertia = 1.0;
     p->n_centroids = 64; p->n_lloyd_init = 10; p->rebuild_every = 1; p->skin = 0.0; p->grid_h = 0.0;
     p->seed = 0; p->instance = 0; p->precision = ORBC_F32_FORCE_F64_STATE;
+    p->n_protein_centroids = 0;
 }
 
 int orbc_create(const orbc_params* params, void* cuda_stream, orbc_system** out) {
@@ -1031,15 +1171,16 @@ int orbc_init_cells(orbc_system* s, const double* centroids) {
     return guarded(s, [&] {
         if (!s->have_particles) throw StateError("no particles");
         if (s->host_stale) pull_state(s);
+        const int K = s->prm.n_centroids + s->prm.n_protein_centroids;
         if (centroids) {
-            for (int q = 0; q < 3 * s->prm.n_centroids; q++)
+            for (int q = 0; q < 3 * K; q++)
                 if (!std::isfinite(centroids[q]) || std::fabs(centroids[q]) >= 4096.0) throw ArgError("invalid centroid");
-            s->host.centroids.assign(centroids, centroids + 3 * (size_t)s->prm.n_centroids);
+            s->host.centroids.assign(centroids, centroids + 3 * (size_t)K);
         } else {
             s->host.centroids.clear();
         }
-        s->ens->setup(s->host);
-        s->dirty = false;
+        s->dirty = true;
+        sync_device(s);
         s->host_stale = false;
         s->ens->init_cells();
     });
@@ -1067,7 +1208,11 @@ int orbc_compute_forces(orbc_system* s, double* energies_out) {
         if (!st && energies_out) {
             std::vector<double> e;
             s->ens->energies(e);
-            for (int q = 0; q < 5; q++) energies_out[q] = e[q];
+            // the membrane's totals over the instances of its batch
+            for (int q = 0; q < 5; q++) {
+                energies_out[q] = 0.0;
+                for (int b = 0; b < s->ens->B; b++) energies_out[q] += e[(size_t)5 * b + q];
+            }
         }
     });
     if (rc == ORBC_OK && st) return fail(s, status_code(st), "device status " + std::to_string(st));
@@ -1094,7 +1239,7 @@ int orbc_get_state(orbc_system* s, double* pos, double* vel, double* ori, double
     return guarded(s, [&] {
         if (!s->have_particles) throw StateError("no particles");
         sync_device(s);
-        s->ens->get_state(0, pos, vel, ori, angvel, step);
+        sys_get_state(s, pos, vel, ori, angvel, step);
     });
 }
 
@@ -1125,7 +1270,11 @@ int orbc_get_state_device(orbc_system* s, double* pos, double* vel, double* ori,
     return guarded(s, [&] {
         if (!s->have_particles) throw StateError("no particles");
         sync_device(s);
-        s->ens->get_state_device(0, pos, vel, ori, angvel);
+        for (int b = 0; b < s->ens->B; b++) {
+            const size_t o = (size_t)3 * s->ens->inst_h[b].id_base;
+            s->ens->get_state_device(b, pos ? pos + o : nullptr, vel ? vel + o : nullptr, ori ? ori + o : nullptr,
+                                     angvel ? angvel + o : nullptr);
+        }
     });
 }
 
@@ -1134,7 +1283,10 @@ int orbc_get_forces_device(orbc_system* s, double* force, double* torque) {
     return guarded(s, [&] {
         sync_device(s);
         if (!s->ens->forces_valid) throw StateError("forces not computed");
-        s->ens->get_forces_device(0, force, torque);
+        for (int b = 0; b < s->ens->B; b++) {
+            const size_t o = (size_t)3 * s->ens->inst_h[b].id_base;
+            s->ens->get_forces_device(b, force ? force + o : nullptr, torque ? torque + o : nullptr);
+        }
     });
 }
 
@@ -1143,7 +1295,10 @@ int orbc_get_forces(orbc_system* s, double* force, double* torque) {
     return guarded(s, [&] {
         sync_device(s);
         if (!s->ens->forces_valid) throw StateError("forces not computed");
-        s->ens->get_forces(0, force, torque);
+        for (int b = 0; b < s->ens->B; b++) {
+            const size_t o = (size_t)3 * s->ens->inst_h[b].id_base;
+            s->ens->get_forces(b, force ? force + o : nullptr, torque ? torque + o : nullptr);
+        }
     });
 }
 
@@ -1153,7 +1308,7 @@ int orbc_get_cells(orbc_system* s, int* cell_of_id, unsigned* slot_ids, double* 
     return guarded(s, [&] {
         sync_device(s);
         if (!s->ens->cells_valid) throw StateError("cells not initialised");
-        s->ens->get_cells(0, cell_of_id, slot_ids, centroids, cell_start, radius, adj_ptr, adj);
+        s->ens->get_cells_all(cell_of_id, slot_ids, centroids, cell_start, radius, adj_ptr, adj);
     });
 }
 
@@ -1162,7 +1317,7 @@ int orbc_get_adjacency_len(orbc_system* s, long long* len) {
     return guarded(s, [&] {
         sync_device(s);
         if (!s->ens->cells_valid) throw StateError("cells not initialised");
-        *len = s->ens->adjacency_len(0);
+        *len = s->ens->adjacency_len_all();
     });
 }
 

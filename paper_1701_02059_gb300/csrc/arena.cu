@@ -532,6 +532,7 @@ int orbc_arena_admit(orbc_arena* h, const orbc_params* params, int n, const doub
     return guarded_call(&h->err, [&] {
         Params P = to_params(params);
         check_params(P);
+        if (P.n_protein_centroids > 0) throw ArgError("the arena takes no separate protein cells");
         HostInstance inst = host_instance(P, n, pos, vel, ori, angvel, type, id);
         host_bonds(inst, nb, ij, r0, kb);
         *slot = h->a->admit(inst, nsteps);

@@ -15,20 +15,23 @@
 namespace orbc {
 
 // ============================================================== M-step
-// S_k = sum over lipids of minimg(x_i - c_k) on the 2^-40 grid (int64, exact,
-// order-independent), n_k = lipid count.  Warp-aggregated 64-bit atomics.
+// S_k = sum over the members (lipids; every particle of a protein cell set)
+// of minimg(x_i - c_k) on the 2^-40 grid (int64, exact, order-independent),
+// n_k = their count.  Warp-aggregated 64-bit atomics.
 __global__ void k_mstep_accum(View v, const int* __restrict__ cell_of, long long* __restrict__ S,
                               int* __restrict__ cnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool act = i < v.N;
     int c = -1;
     long long d[3] = {0, 0, 0};
-    if (act && v.type[i] == kLipid) {
-        c = cell_of[i];
-        int b = find_inst(v.inst_k0, v.B, c);
-        const Inst& I = v.inst[b];
-        for (int a = 0; a < 3; a++)
-            d[a] = minimg_q(v.xq[(size_t)a * v.N + i] - v.cq[(size_t)a * v.Ktot + c], I.boxq[a], I.periodic[a]);
+    if (act) {
+        const int ci = cell_of[i];
+        const Inst& I = v.inst[find_inst(v.inst_k0, v.B, ci)];
+        if (centroid_member(I, v.type[i])) {
+            c = ci;
+            for (int a = 0; a < 3; a++)
+                d[a] = minimg_q(v.xq[(size_t)a * v.N + i] - v.cq[(size_t)a * v.Ktot + c], I.boxq[a], I.periodic[a]);
+        }
     }
     const unsigned full = 0xffffffffu;   // every lane of the warp reaches this point
     unsigned grp = __match_any_sync(full, c);
@@ -87,7 +90,7 @@ __global__ void k_mstep_finish(View v, long long* __restrict__ S, int* __restric
     }
 }
 
-// Rebuild M-step on cell-sorted particles: one warp per cell sums its lipids'
+// Rebuild M-step on cell-sorted particles: one warp per cell sums its members'
 // grid displacements (exact int64, shuffles), updates the centroid and
 // folds it into the instance bounding box (block-level, then atomics).
 __global__ void k_mstep_sorted(View v, long long* __restrict__ bb, unsigned* __restrict__ dmax) {
@@ -106,7 +109,7 @@ __global__ void k_mstep_sorted(View v, long long* __restrict__ bb, unsigned* __r
         int n = 0;
         const size_t N = v.N;
         for (int p = s + lane; p < e; p += 32) {
-            if (v.type[p] != kLipid) continue;
+            if (!centroid_member(I, v.type[p])) continue;
             S0 += minimg_q(v.xq[p] - c[0], I.boxq[0], I.periodic[0]);
             S1 += minimg_q(v.xq[N + p] - c[1], I.boxq[1], I.periodic[1]);
             S2 += minimg_q(v.xq[2 * N + p] - c[2], I.boxq[2], I.periodic[2]);
@@ -809,6 +812,7 @@ __global__ void __launch_bounds__(128, 16) k_estep_rows(View v, const int* __res
         for (int r = a0; r < a1; r++) {
             const float4 c = rows[r];
             const int j = __float_as_int(c.w);
+            if (j < I.k0 || j >= I.k0 + I.K) continue;    // a cell of the other set
             const float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1), dz = axis_dist(p[2], c.z, I, 2);
             const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             if (j == kn) dself2 = d2;
@@ -828,6 +832,7 @@ __global__ void __launch_bounds__(128, 16) k_estep_rows(View v, const int* __res
                 for (int r = a0; r < a1; r++) {
                     const float4 c = rows[r];
                     const int j = __float_as_int(c.w);
+                    if (j < I.k0 || j >= I.k0 + I.K) continue;
                     const float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1),
                                 dz = axis_dist(p[2], c.z, I, 2);
                     if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim) {
@@ -1289,7 +1294,9 @@ __device__ inline bool adj_test(const View& v, const Inst& I, int k, int j, doub
 // Neighbouring cells, one warp per cell: the lanes share the grid cells of
 // the cube around the cell's own grid cell that the reach
 // R_k + R_max + r_s + 2 skin can touch, test every centroid there with the
-// exact rule, collect the row in shared memory and sort it.  Rows longer than
+// exact rule, collect the row in shared memory and sort it.  A membrane
+// whose proteins have a cell set of their own searches that set's grid too,
+// so that its rows hold the neighbouring cells of both sets.  Rows longer than
 // kAdjRow are flagged (kStatusAdjOverflow) and truncated. Each entry gets
 // the pair kernel's staging descriptor (particle range, exact centroid
 // offset at 2^-26 sigma) in the same fixed-stride row.
@@ -1303,82 +1310,92 @@ __global__ void __launch_bounds__(256, 6) k_adj_warp(View v, const unsigned long
     const int b = find_inst(v.inst_k0, v.B, k);
     const Inst& I = v.inst[b];
     const double Rk = v.R[k];
-    const double Rmax = __longlong_as_double((long long)rmax_bits[b]);
-    const float reach = (float)(Rk + Rmax + I.rs + 2.0 * I.skin) + kBandA;
     const long long cx = v.cq[k], cy = v.cq[(size_t)v.Ktot + k], cz = v.cq[(size_t)2 * v.Ktot + k];
-    float p[3];
-    int g[3];
-    g[0] = grid_coord(cx, I, 0, p[0]);
-    g[1] = grid_coord(cy, I, 1, p[1]);
-    g[2] = grid_coord(cz, I, 2, p[2]);
     const double tail = (I.rs) + (I.skin + I.skin);
-    // cube radius: the first shell beyond which nothing is within reach
-    int R = 0;
-    for (;; R++) {
-        bool ex;
-        const float lb = shell_bound(p, g, R, I, ex);
-        if (ex || lb > reach) break;
-    }
-    int lo[3], ext[3];
-    bool full[3];
-    for (int a = 0; a < 3; a++) {
-        int l, h;
-        full[a] = false;
-        if (I.periodic[a]) {
-            if (2 * R + 1 >= I.gdim[a]) { l = 0; h = I.gdim[a] - 1; full[a] = true; }
-            else { l = g[a] - R; h = g[a] + R; }
-        } else {
-            l = max(0, g[a] - R);
-            h = min(I.gdim[a] - 1, g[a] + R);
-        }
-        lo[a] = l;
-        ext[a] = h - l + 1;
-    }
-    const float reach2 = reach * reach;
     if (lane == 0) rown[wb] = 0;
     __syncwarp();
-    float rho = reach - kBandA;
-    // one lane per (y, z) row of the cube: the row's grid cells are
-    // contiguous along x, and so are their centroids in grid order (one or
-    // two segments when a periodic x range wraps)
-    auto axis_gap = [&](int a, int u) {
-        if (full[a]) return 0.f;
-        const float cl = (!I.periodic[a] && u == 0) ? -3.0e38f : u * I.gh[a];
-        const float ch = (!I.periodic[a] && u == I.gdim[a] - 1) ? 3.0e38f : (u + 1) * I.gh[a];
-        return fmaxf(fmaxf(cl - p[a], p[a] - ch), 0.f);
-    };
-    const int rows = ext[1] * ext[2];
-    for (int t = lane; t < rows; t += 32) {
-        const int y = lo[1] + t % ext[1], z = lo[2] + t / ext[1];
-        const float gy = axis_gap(1, y), gz = axis_gap(2, z);
-        if (fmaf(gy, gy, gz * gz) > reach2) continue;      // the whole row is beyond the reach
-        const int w1 = I.periodic[1] ? wrap_idx(y, I.gdim[1]) : y;
-        const int w2 = I.periodic[2] ? wrap_idx(z, I.gdim[2]) : z;
-        const long long rowbase = I.g0 + ((long long)w2 * I.gdim[1] + w1) * I.gdim[0];
-        int xa[2], xb[2], nseg = 1;
-        xa[0] = lo[0];
-        xb[0] = lo[0] + ext[0] - 1;
-        if (I.periodic[0] && !full[0]) {
-            const int a0 = wrap_idx(xa[0], I.gdim[0]), b0 = wrap_idx(xb[0], I.gdim[0]);
-            if (a0 <= b0) { xa[0] = a0; xb[0] = b0; }
-            else { xa[0] = a0; xb[0] = I.gdim[0] - 1; xa[1] = 0; xb[1] = b0; nseg = 2; }
+    const float reach_own = (float)(Rk + __longlong_as_double((long long)rmax_bits[b]) + I.rs + 2.0 * I.skin) + kBandA;
+    float rho = reach_own - kBandA;
+    // the centroids of one set through its own grid G: every centroid within
+    // the reach R_k + R_max(G) + r_s + 2 skin is tested with the exact rule;
+    // own: the set of cell k, whose nearest non-neighbour bounds the
+    // E-step's certificate (the other set's cells join the row only)
+    auto scan = [&](const Inst& G, double Rmax, bool own) {
+        const float reach = (float)(Rk + Rmax + I.rs + 2.0 * I.skin) + kBandA;
+        float p[3];
+        int g[3];
+        g[0] = grid_coord(cx, G, 0, p[0]);
+        g[1] = grid_coord(cy, G, 1, p[1]);
+        g[2] = grid_coord(cz, G, 2, p[2]);
+        // cube radius: the first shell beyond which nothing is within reach
+        int R = 0;
+        for (;; R++) {
+            bool ex;
+            const float lb = shell_bound(p, g, R, G, ex);
+            if (ex || lb > reach) break;
         }
-        for (int sg = 0; sg < nseg; sg++) {
-            const int q1 = v.gstart[rowbase + xb[sg] + 1];
-            for (int q = v.gstart[rowbase + xa[sg]]; q < q1; q++) {
-                const float4 c = v.gcf[q];
-                const int j = __float_as_int(c.w);
-                const float dx = axis_dist(p[0], c.x, I, 0), dy = axis_dist(p[1], c.y, I, 1), dz = axis_dist(p[2], c.z, I, 2);
-                const float df = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                if (adj_test(v, I, k, j, Rk, df, cx, cy, cz, tail)) {
-                    const int at = atomicAdd(&rown[wb], 1);
-                    if (at < kAdjRow) row[wb][at] = j;
-                } else {
-                    rho = fminf(rho, df);
+        int lo[3], ext[3];
+        bool full[3];
+        for (int a = 0; a < 3; a++) {
+            int l, h;
+            full[a] = false;
+            if (G.periodic[a]) {
+                if (2 * R + 1 >= G.gdim[a]) { l = 0; h = G.gdim[a] - 1; full[a] = true; }
+                else { l = g[a] - R; h = g[a] + R; }
+            } else {
+                l = max(0, g[a] - R);
+                h = min(G.gdim[a] - 1, g[a] + R);
+            }
+            lo[a] = l;
+            ext[a] = h - l + 1;
+        }
+        const float reach2 = reach * reach;
+        // one lane per (y, z) row of the cube: the row's grid cells are
+        // contiguous along x, and so are their centroids in grid order (one
+        // or two segments when a periodic x range wraps)
+        auto axis_gap = [&](int a, int u) {
+            if (full[a]) return 0.f;
+            const float cl = (!G.periodic[a] && u == 0) ? -3.0e38f : u * G.gh[a];
+            const float ch = (!G.periodic[a] && u == G.gdim[a] - 1) ? 3.0e38f : (u + 1) * G.gh[a];
+            return fmaxf(fmaxf(cl - p[a], p[a] - ch), 0.f);
+        };
+        const int rows = ext[1] * ext[2];
+        for (int t = lane; t < rows; t += 32) {
+            const int y = lo[1] + t % ext[1], z = lo[2] + t / ext[1];
+            const float gy = axis_gap(1, y), gz = axis_gap(2, z);
+            if (fmaf(gy, gy, gz * gz) > reach2) continue;      // the whole row is beyond the reach
+            const int w1 = G.periodic[1] ? wrap_idx(y, G.gdim[1]) : y;
+            const int w2 = G.periodic[2] ? wrap_idx(z, G.gdim[2]) : z;
+            const long long rowbase = G.g0 + ((long long)w2 * G.gdim[1] + w1) * G.gdim[0];
+            int xa[2], xb[2], nseg = 1;
+            xa[0] = lo[0];
+            xb[0] = lo[0] + ext[0] - 1;
+            if (G.periodic[0] && !full[0]) {
+                const int a0 = wrap_idx(xa[0], G.gdim[0]), b0 = wrap_idx(xb[0], G.gdim[0]);
+                if (a0 <= b0) { xa[0] = a0; xb[0] = b0; }
+                else { xa[0] = a0; xb[0] = G.gdim[0] - 1; xa[1] = 0; xb[1] = b0; nseg = 2; }
+            }
+            for (int sg = 0; sg < nseg; sg++) {
+                const int q1 = v.gstart[rowbase + xb[sg] + 1];
+                for (int q = v.gstart[rowbase + xa[sg]]; q < q1; q++) {
+                    const float4 c = v.gcf[q];
+                    const int j = __float_as_int(c.w);
+                    const float dx = axis_dist(p[0], c.x, G, 0), dy = axis_dist(p[1], c.y, G, 1),
+                                dz = axis_dist(p[2], c.z, G, 2);
+                    const float df = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                    if (adj_test(v, I, k, j, Rk, df, cx, cy, cz, tail)) {
+                        const int at = atomicAdd(&rown[wb], 1);
+                        if (at < kAdjRow) row[wb][at] = j;
+                    } else if (own) {
+                        rho = fminf(rho, df);
+                    }
                 }
             }
         }
-    }
+    };
+    scan(I, __longlong_as_double((long long)rmax_bits[b]), true);
+    if (I.partner >= 0)
+        scan(v.inst[I.partner], __longlong_as_double((long long)rmax_bits[I.partner]), false);
     for (int off = 16; off; off >>= 1) rho = fminf(rho, __shfl_xor_sync(0xffffffffu, rho, off));
     __syncwarp();
     int n = rown[wb];

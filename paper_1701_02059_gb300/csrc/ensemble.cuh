@@ -44,6 +44,7 @@ struct Params {
     unsigned long long seed = 0;
     unsigned instance = 0;
     int precision = 0;   // 0 = FP32 forces, FP64 increments; 1 = FP64 everywhere; 2 = FP32 forces and increments
+    int n_protein_centroids = 0;   // > 0: the proteins get a cell set of their own
 };
 
 // One instance as given by the caller (host memory, id order not required).
@@ -75,6 +76,11 @@ struct HostInstance {
     long long step0 = 0;                     // steps already taken
     // harmonic volume constraint (kv = 0: off)
     double vol_kv = 0.0, vol_v0 = 0.0, vol_area = 0.0, vol_xc[3] = {0.0, 0.0, 0.0};
+    // one cell set of a membrane split into lipid and protein cell sets:
+    // the batch index of the other set (-1: none), the ids' offset in the
+    // membrane, and whether every particle (not only the lipids) moves the
+    // centroids
+    int partner = -1, id_base = 0, all_members = 0;
 };
 
 // Bond list of one instance (ids local to the instance).
@@ -157,6 +163,10 @@ public:
     void get_cells(int b, int* cell_of_id, unsigned* slot_ids, double* centroids, int* cell_start, double* radius,
                    int* adj_ptr, int* adj);
     long long adjacency_len(int b);
+    // every instance of the batch as one list (global cell numbers, ids offset by id_base)
+    void get_cells_all(int* cell_of_id, unsigned* slot_ids, double* centroids, int* cell_start, double* radius,
+                       int* adj_ptr, int* adj);
+    long long adjacency_len_all();
     // the neighbour rows as CSR (adj_ptr, adj), built on demand for the getters
     void adjacency_csr();
     long long dump_pairs(int b, long long cap, unsigned* pairs);

@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
             pi = __float_as_int(oi.w);
             ti = qi.w & 0xff;
             F.apply(qi.x * kMirrorUnit, qi.y * kMirrorUnit, qi.z * kMirrorUnit, yix, yiy, yiz);
-            if (DUMP) idi = v.id[pi];
+            if (DUMP) idi = (unsigned)I.id_base + v.id[pi];
         }
         // a lane without a particle sits far away: it passes no distance test
         if (!ivalid) { yix = 1.0e18f; yiy = 1.0e18f; yiz = 1.0e18f; }
@@ -632,7 +632,8 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                             vir += -0.5 * ((double)dx * (double)fx + (double)dy * (double)fy + (double)dz * (double)fz);
                         }
                         if (DUMP) {
-                            const unsigned idj = v.id[pj];
+                            const unsigned idj =
+                                (unsigned)v.inst[find_inst(v.inst_p0, v.B, pj)].id_base + v.id[pj];
                             if (idi < idj) {
                                 unsigned long long slot = atomicAdd(dump_count, 1ull);
                                 if ((long long)slot < dump_cap) { dump[2 * slot] = idi; dump[2 * slot + 1] = idj; }
@@ -893,6 +894,10 @@ __global__ void __launch_bounds__(kPairThreads, 7)
         const float cutL = ti == kLipid ? cl * cl : cw * cw;
         const float cutP = ti == kLipid ? cw * cw : cp * cp;
         const float cutD = cutP - cutL;
+        // the group box's cull radius: the search cutoff, or for a group
+        // without lipids (a protein cell) the larger of its two cutoffs
+        const bool glip = __any_sync(0xffffffffu, ivalid && ti == kLipid);
+        const float rcull2 = glip ? rs2f : fmaxf(cw, cp) * fmaxf(cw, cp);
         float blo[3] = {ivalid ? yix : 3.0e38f, ivalid ? yiy : 3.0e38f, ivalid ? yiz : 3.0e38f};
         float bhi[3] = {ivalid ? yix : -3.0e38f, ivalid ? yiy : -3.0e38f, ivalid ? yiz : -3.0e38f};
         for (int a = 0; a < 3; a++)
@@ -951,7 +956,7 @@ __global__ void __launch_bounds__(kPairThreads, 7)
                         const float ex = fmaxf(fmaxf(blo[0] - y.x, y.x - bhi[0]), 0.f);
                         const float ey = fmaxf(fmaxf(blo[1] - y.y, y.y - bhi[1]), 0.f);
                         const float ez = fmaxf(fmaxf(blo[2] - y.z, y.z - bhi[2]), 0.f);
-                        in = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < rs2f;
+                        in = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < rcull2;
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, in);
                     if (in) cand[warp][cnt + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)j;

@@ -112,20 +112,21 @@ __device__ inline void kick(long long vq[3], long long wq[3], const long long nq
 // counted in steps[], so this step's index is steps[b] + 1.
 // The M-step's sums for the rebuild that follows (the "Spatial Searching
 // Algorithm" update of each centroid from its lipids at the new positions):
-// lipid i of cell k adds minimg(x_i - c_k) on the 2^-40 grid, exactly.  The
+// member i of cell k (a lipid, or any particle of a protein cell set) adds
+// minimg(x_i - c_k) on the 2^-40 grid, exactly.  The
 // lanes of a warp that share a cell add up a 24-bit low part and the high
 // part separately in 32 bits, exact while |x_i - c_k| < 1024 sigma (the
 // mirrors already flag anything beyond 32 sigma); one lane per cell adds the
 // int64 totals.
-__device__ inline void mstep_sums(const View& v, const Inst& I, int p, bool lipid, const long long* xq,
+__device__ inline void mstep_sums(const View& v, const Inst& I, int p, bool member, const long long* xq,
                                   long long* __restrict__ msum, int* __restrict__ mcnt) {
     const int k = v.cell[p];
     const size_t K = v.Ktot;
     long long d[3] = {0, 0, 0};
-    if (lipid)
+    if (member)
         for (int a = 0; a < 3; a++) d[a] = minimg_q(xq[a] - v.cq[a * K + k], I.boxq[a], I.periodic[a]);
     const unsigned grp = __match_any_sync(__activemask(), k);
-    const unsigned n = __reduce_add_sync(grp, lipid ? 1u : 0u);
+    const unsigned n = __reduce_add_sync(grp, member ? 1u : 0u);
     long long tot[3];
     for (int a = 0; a < 3; a++) {
         const unsigned lo = __reduce_add_sync(grp, (unsigned)(d[a] & 0xffffff));
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 4) k_baoa(View v, co
     }
     if (lipid) cayley<T>(nq, wq, C.hdt);
     // O
-    const unsigned id = v.id[p];
+    const unsigned id = (unsigned)I.id_base + v.id[p];   // the id in the membrane
     const unsigned long long step = (unsigned long long)steps[b] + (FUSED ? 1ull : 0ull);
     const uint2 key = make_uint2((unsigned)I.seed, (unsigned)(I.seed >> 32) ^ I.instance);
     uint4 w0 = philox4x32_10(make_uint4(id, (unsigned)step, (unsigned)(step >> 32), 0u), key);
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 4) k_baoa(View v, co
     }
     for (int a = 0; a < 3; a++) { v.xq[a * N + p] = xq[a]; v.vq[a * N + p] = vq[a]; }
     if (lipid) for (int a = 0; a < 3; a++) { v.nq[a * N + p] = nq[a]; v.wq[a * N + p] = wq[a]; }
-    if (msum) mstep_sums(v, I, p, lipid, xq, msum, mcnt);
+    if (msum) mstep_sums(v, I, p, centroid_member(I, v.type[p]), xq, msum, mcnt);
 }
 
 // ---------------------------------------------------------------- FP64 increments in grid units
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(256, 2) k_baoa_d(View v, const long long* __re
         for (int a = 0; a < 3; a++) { nq[a] += d[a]; Nd[a] = gd(nq[a]); }
     }
     // O
-    const unsigned id = v.id[p];
+    const unsigned id = (unsigned)I.id_base + v.id[p];   // the id in the membrane
     const unsigned long long step = (unsigned long long)steps[b] + (FUSED ? 1ull : 0ull);
     const uint2 key = make_uint2((unsigned)I.seed, (unsigned)(I.seed >> 32) ^ I.instance);
     const uint4 w0 = philox4x32_10(make_uint4(id, (unsigned)step, (unsigned)(step >> 32), 0u), key);
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(256, 2) k_baoa_d(View v, const long long* __re
     }
     for (int a = 0; a < 3; a++) { v.xq[a * N + p] = xq[a]; v.vq[a * N + p] = vq[a]; }
     if (lipid) for (int a = 0; a < 3; a++) { v.nq[a * N + p] = nq[a]; v.wq[a * N + p] = wq[a]; }
-    if (msum) mstep_sums(v, I, p, lipid, xq, msum, mcnt);
+    if (msum) mstep_sums(v, I, p, centroid_member(I, v.type[p]), xq, msum, mcnt);
 }
 
 __global__ void k_kick_d(View v, long long* __restrict__ steps) {

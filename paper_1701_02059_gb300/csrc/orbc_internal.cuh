@@ -76,6 +76,11 @@ struct Inst {
     int vol_on;
     double kv, v0, avol, a3;
     long long xcq[3];
+    // separate cell sets of one membrane: the batch index of the other set
+    // (-1: none; its cells join this set's neighbour rows), the offset of
+    // this set's ids in the membrane (Philox counters, pair dumps), and
+    // whether every particle is a centroid member (else only the lipids)
+    int partner, id_base, all_members;
 };
 
 // ---------------------------------------------------------------- packed device arrays
@@ -339,6 +344,12 @@ __device__ inline Frame tangent_frame(float nx, float ny, float nz) {
     f.r[3] = ny * uz - nz * uy; f.r[4] = nz * ux - nx * uz; f.r[5] = nx * uy - ny * ux;
     f.r[6] = nx; f.r[7] = ny; f.r[8] = nz;
     return f;
+}
+
+// A particle that moves its cell's centroid (the M-step): the lipids, or
+// every particle of a protein cell set.
+__host__ __device__ inline bool centroid_member(const Inst& I, unsigned char type) {
+    return I.all_members || type == kLipid;
 }
 
 // Raises status bits for the launch and for the instance I (a reference

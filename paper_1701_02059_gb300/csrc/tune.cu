@@ -102,6 +102,7 @@ extern "C" int orbc_autotune(const orbc_params* params, int n, const double* pos
     return guarded_call(&err, [&] {
         Params P = to_params(params);
         check_params(P);
+        if (P.n_protein_centroids > 0) throw ArgError("the autotuner takes no separate protein cells");
         HostInstance h = host_instance(P, n, pos, vel, ori, angvel, type, id);
         host_bonds(h, nb, ij, r0, kb);
         const std::string key = tune_key(h);
