@@ -346,6 +346,15 @@ ORBC_API int orbc_mesh_build(const orbc_mesh_params* mp, int nv, const double* v
  * or limits), ORBC_E_STATE (cells not initialised), ORBC_E_NAN, ORBC_E_CUDA. */
 ORBC_API int orbc_quench(orbc_system* s, int nsteps, double dt, double max_move, double max_turn, double* fmax_out);
 
+/* Whether each step's force launch also runs the next step's B-A-O-A update
+ * in its epilogue (on = 1; FP32-force modes; default 0, separate launches).
+ * Every particle's update needs only its own force, so the update could
+ * overlap the pair evaluation of the other particles; on GB300 the fused
+ * launch is slower (its state loads, permuted within the cell tiles, wait
+ * with few resident warps).  Both settings give the same trajectory bit for
+ * bit.  Errors: ORBC_E_ARG (null handle). */
+ORBC_API int orbc_set_step_fusion(orbc_system* s, int on);
+
 /* Harmonic volume constraint on the handle's membrane ("Validation and
  * Benchmark": the whole-cell run holds its surface-to-volume ratio by a
  * harmonic volume constraint; the paper states no functional form, so the

@@ -174,6 +174,11 @@ class System:
                                         C.byref(fm)), "orbc_quench")
         return fm.value
 
+    def set_step_fusion(self, on: bool):
+        """orbc_set_step_fusion: run each step's update in the previous force
+        launch's epilogue, or as a launch of its own (the default)."""
+        self._check(self._L.orbc_set_step_fusion(self._h, int(bool(on))), "orbc_set_step_fusion")
+
     def set_volume_constraint(self, kv: float, v0: float, area_per_lipid: float, center=(0.0, 0.0, 0.0)):
         """orbc_set_volume_constraint: U_V = kv (V - v0)^2 / 2 on the lipid
         volume V (kv = 0 switches it off)."""

@@ -25,7 +25,7 @@ EXPORTS = [
     "orbc_arena_info", "orbc_arena_launch_count", "orbc_arena_last_error", "orbc_arena_destroy",
     "orbc_autotune", "orbc_arena_stats", "orbc_set_particles_device", "orbc_get_state_device",
     "orbc_get_forces_device", "orbc_default_mesh_params", "orbc_mesh_build", "orbc_quench",
-    "orbc_set_volume_constraint", "orbc_get_volume", "orbc_height_map",
+    "orbc_set_volume_constraint", "orbc_get_volume", "orbc_height_map", "orbc_set_step_fusion",
 ]
 _NOT_INT = {"orbc_default_params": None, "orbc_default_mesh_params": None, "orbc_last_error": C.c_char_p, "orbc_destroy": None,
             "orbc_arena_launch_count": C.c_longlong, "orbc_arena_last_error": C.c_char_p, "orbc_arena_destroy": None}
@@ -90,6 +90,7 @@ def load(path: str | None = None):
     L.orbc_mesh_build.argtypes = [V, C.c_int, V, C.c_int, V, C.c_longlong, V, V, V, V, C.c_longlong, V, V, V, V, V]
     L.orbc_quench.argtypes = [V, C.c_int, C.c_double, C.c_double, C.c_double, V]
     L.orbc_set_volume_constraint.argtypes = [V, C.c_double, C.c_double, C.c_double, V]
+    L.orbc_set_step_fusion.argtypes = [V, C.c_int]
     L.orbc_get_volume.argtypes = [V, C.c_double, V, C.POINTER(C.c_double)]
     L.orbc_height_map.argtypes = [V, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_double,
                                   V, C.c_double, C.c_double, V, V]

@@ -599,8 +599,11 @@ void Ensemble::energies(std::vector<double>& out) {
 void Ensemble::integrate(int nsteps) {
     if (!cells_valid) throw StateError("cells not initialised");
     if (!forces_valid) launch_pairs(false, false);
+    // with FP32 forces, each step's force launch also runs the next step's
+    // B-A-O-A (the last step's forces are evaluated alone, before the final B)
+    const bool fuse = fuse_steps && !force_f64();
     for (int s = 0; s < nsteps; s++) {
-        step_body(s > 0);
+        step_body(s > 0, fuse && s > 0, fuse && s + 1 < nsteps);
         for (auto& x : step_h) x++;
     }
     if (nsteps > 0) {
@@ -614,14 +617,16 @@ void Ensemble::integrate(int nsteps) {
 
 // One time step without its final B: B-A-O-A (after the previous step's
 // final B when fused), cell rebuild (or mirrors), forces.
-void Ensemble::step_body(bool fused) {
+void Ensemble::step_body(bool fused, bool baoa_done, bool eval_step) {
     // rebuilding every step: the B-A-O-A launch also sums the M-step's
-    // per-cell lipid displacements
+    // per-cell displacements of the centroid members
     const int re = prm_h[0].rebuild_every;
     const bool every = re <= 1 && !d_xref;
-    tic("integrate_baoa");
-    launch_integrate_first(fused, every);
-    toc();
+    if (!baoa_done) {
+        tic("integrate_baoa");
+        launch_integrate_first(fused, every);
+        toc();
+    }
     bool due = (re <= 1) || ((step_h[0] + 1) % re == 0);
     if (!due && d_xref) due = displacement_exceeds_skin();
     if (due) {
@@ -633,7 +638,8 @@ void Ensemble::step_body(bool fused) {
         mirrors();
         toc();
     }
-    launch_pairs(false, false);
+    if (eval_step) launch_pairs_step(every);
+    else launch_pairs(false, false);
 }
 
 // ---------------------------------------------------------------- getters
@@ -1405,6 +1411,12 @@ int orbc_height_map(orbc_system* s, double x0, double y0, double dx, double dy, 
         sync_device(s);
         s->ens->height_map(0, x0, y0, dx, dy, nx, ny, z_min, axis, rho_in, rho_out, h_out, count_out);
     });
+}
+
+int orbc_set_step_fusion(orbc_system* s, int on) {
+    if (!s) return ORBC_E_ARG;
+    s->ens->fuse_steps = on != 0;
+    return ORBC_OK;
 }
 
 int orbc_set_wait_test(orbc_system* s, unsigned extra_tx_bytes, unsigned max_polls) {

@@ -212,6 +212,13 @@ public:
     void morton_relabel();
     void finish_cells();
     void launch_pairs(bool energies, bool dump);
+    // the forces of the current positions with the next step's B-A-O-A (after
+    // this step's final B) in the evaluation's epilogue; the new state lands
+    // in the other buffer, which becomes current; msums: the epilogue takes
+    // the M-step's sums for the next rebuild
+    void launch_pairs_step(bool msums);
+    void launch_volume_sum();                // D of every constrained instance into d_vol
+    bool fuse_steps = false;                 // run each step's B-A-O-A in the previous step's force launch
     void launch_volume(bool energies);       // after the pair and bond forces
     void alloc_lists();
     void launch_integrate_first(bool fused, bool msums = false);
@@ -227,7 +234,10 @@ private:
     void free_all();
     void alloc_core(const std::vector<int>& p0, const std::vector<int>& k0, bool any_skin);
     void upload_bonds(const std::vector<BondSpec>& bl, const std::vector<int>& p0);
-    void step_body(bool fused);   // fused: the previous step's final B is still due
+    // fused: the previous step's final B is still due; baoa_done: this step's
+    // B-A-O-A already ran in the previous step's force launch; eval_step: the
+    // force launch also runs the next step's B-A-O-A
+    void step_body(bool fused, bool baoa_done = false, bool eval_step = false);
     size_t bytes_ = 0;
     cudaGraphExec_t graph_[2] = {nullptr, nullptr};
     long long graph_launches_ = 0;
@@ -301,6 +311,7 @@ public:
     int* d_ncnt = nullptr;                   // [N] listed pairs per particle (rank order)
     int2* d_novf = nullptr;                  // [ovf_cap] (q, entry) beyond list_cap
     int* d_novf_n = nullptr;                 // their count
+    unsigned char* d_sflag = nullptr;        // [N] side-array contributions pending for the particle
     int4* d_rowoff = nullptr;                // [adj_cap] exact offset c_l - c_k of each row entry
     int list_cap = 0, ovf_cap = 0;
     bool list_valid = false;

@@ -24,7 +24,7 @@
 //   4. every pair is computed from both sides (no atomics to other cells, as
 //      the paper does across patch boundaries); bonds of i are added in the
 //      epilogue.
-#include "ensemble.cuh"
+#include "integrator.cuh"
 
 #include <mutex>
 
@@ -1056,22 +1056,19 @@ struct PairC {
     }
 };
 
-// Evaluation: one thread per particle (rank order) over its list, reading
-// the listed particles' mirrors from global memory (L1/L2), the constants of
-// the pair terms in registers, the force and torque summed as exact split
-// integers.  (Measured on the 4M cell: evaluating from mirrors staged in
-// shared memory per cell, with each list split over two or four threads,
-// took 1.31 ms against 1.06 ms for this kernel.)
+// One particle's list (the thread of rank q): the listed particles' mirrors
+// read from global memory (L1/L2), the constants of the pair terms in
+// registers, the force and torque summed as exact split integers; terms of
+// 1000 or more go to the int64 side array (big = true).
 template <int Z, bool S0>
-__global__ void __launch_bounds__(128, 5)
-    k_pair_eval(View v, const int* __restrict__ nlist, const int* __restrict__ ncnt, int cap,
-                const int4* __restrict__ rowoff) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= v.N) return;
+__device__ __forceinline__ void eval_list(const View& v, int q, const int* __restrict__ nlist,
+                                          const int* __restrict__ ncnt, int cap, const int4* __restrict__ rowoff,
+                                          SplitAcc af[3], SplitAcc at[3], int& nterm, bool& big, int& pi_out) {
     const size_t N = v.N;
     const int4 qi = v.mqr[q];
     const float4 oi = v.mor[q];
     const int pi = __float_as_int(oi.w);
+    pi_out = pi;
     const int ti = qi.w & 0xff;
     const int k = v.cell[pi];
     const int b = find_inst(v.inst_p0, v.B, pi);
@@ -1080,10 +1077,9 @@ __global__ void __launch_bounds__(128, 5)
     const int zc = (Z > 0) ? Z : C.zeta;
     const int4* __restrict__ ro = rowoff + (size_t)k * kAdjRow;
     const int n = min(ncnt[q], cap);
-    SplitAcc af[3], at[3];
     for (int a = 0; a < 3; a++) { af[a].zero(); at[a].zero(); }
-    int nterm = 0;
-    bool big = false;
+    nterm = 0;
+    big = false;
     // the next list entry is in flight while a pair is evaluated; the
     // mirrors are read through the read-only data path
     int e_next = n > 0 ? __ldcs(nlist + q) : 0;
@@ -1136,6 +1132,23 @@ __global__ void __launch_bounds__(128, 5)
             big = true;
         }
     }
+}
+
+// Evaluation: one thread per particle (rank order) over its list (see
+// eval_list).  (Measured on the 4M cell: evaluating from mirrors staged in
+// shared memory per cell, with each list split over two or four threads,
+// took 1.31 ms against 1.06 ms for this kernel.)
+template <int Z, bool S0>
+__global__ void __launch_bounds__(128, 5)
+    k_pair_eval(View v, const int* __restrict__ nlist, const int* __restrict__ ncnt, int cap,
+                const int4* __restrict__ rowoff) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= v.N) return;
+    const size_t N = v.N;
+    SplitAcc af[3], at[3];
+    int nterm, pi;
+    bool big;
+    eval_list<Z, S0>(v, q, nlist, ncnt, cap, rowoff, af, at, nterm, big, pi);
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         long long fb = 0, tb = 0;
@@ -1150,12 +1163,69 @@ __global__ void __launch_bounds__(128, 5)
     }
 }
 
+// The evaluation of one step with the next step's update in its epilogue:
+// each particle's force and torque are complete once its own list is done
+// (the bonds, the listed pairs beyond the lists' capacity and the large
+// terms were added beforehand to the side array, flagged per particle; the
+// volume constraint's pressure is added here), and its B-A-O-A update (with
+// the final B of this step) needs nothing else, so the FP64 update of one
+// warp overlaps the FP32 pair terms of the others.  The updated state goes
+// to the other state buffer (o): the exact inclusion decisions of the other
+// threads still read this step's positions.  D: FP64 increments.
+template <int Z, bool S0, bool D>
+__global__ void __launch_bounds__(128, 4)
+    k_pair_eval_step(View v, View o, const int* __restrict__ nlist, const int* __restrict__ ncnt, int cap,
+                     const int4* __restrict__ rowoff, unsigned char* __restrict__ sflag,
+                     const long long* __restrict__ steps, long long* __restrict__ msum, int* __restrict__ mcnt) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned live = __ballot_sync(0xffffffffu, q < v.N);
+    if (q >= v.N) return;
+    const size_t N = v.N;
+    SplitAcc af[3], at[3];
+    int nterm, pi;
+    bool big;
+    eval_list<Z, S0>(v, q, nlist, ncnt, cap, rowoff, af, at, nterm, big, pi);
+    const bool side = big || sflag[pi];
+    long long F[3], Tq[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        long long fb = 0, tb = 0;
+        if (side) {
+            fb = __ldcg(&v.Fbig[(size_t)a * N + pi]);
+            tb = __ldcg(&v.Fbig[(size_t)(3 + a) * N + pi]);
+            v.Fbig[(size_t)a * N + pi] = 0;
+            v.Fbig[(size_t)(3 + a) * N + pi] = 0;
+        }
+        F[a] = af[a].finish(nterm) + fb;
+        Tq[a] = at[a].finish(nterm) + tb;
+    }
+    if (side) sflag[pi] = 0;
+    const Inst& I = v.inst[find_inst(v.inst_p0, v.B, pi)];
+    if (I.vol_on && v.type[pi] == kLipid) {
+        // the volume constraint's pressure on the lipid's area element, as
+        // the constraint's own launch computes it
+        const double V = I.a3 * volume_of(__ldg(&v.vol[2 * (&I - v.inst)]), __ldg(&v.vol[2 * (&I - v.inst) + 1]));
+        const float pa = (float)(-I.kv * (V - I.v0) * I.avol);
+        for (int a = 0; a < 3; a++) {
+            const float f = pa * (ll_to_float(v.nq[a * N + pi]) * (float)kGridInv);
+            if (!(fabsf(f) < kMaxTerm)) flag_inst(v, I, f == f ? kStatusPairForceRange : kStatusNaN);
+            else F[a] += __float2ll_rn(f * 4294967296.0f);
+        }
+    }
+    for (int a = 0; a < 3; a++) { v.F[a * N + pi] = F[a]; v.T[a * N + pi] = Tq[a]; }
+    __syncwarp(live);
+    if (D) baoa_d_body<true>(v, o, pi, F, Tq, steps, msum, mcnt, live, true);
+    else baoa_body<float, true>(v, o, pi, F, Tq, steps, msum, mcnt, live, true);
+}
+
 // Listed pairs beyond kListCap: the same terms, added to F and T by 64-bit
 // integer atomics (each term rounded to 2^-32 exactly as the split sums do,
 // so the totals are the same integers).
+// sflag (nullable): add to the side array instead, and flag the particle
+// (the evaluation with the update in its epilogue collects it).
 template <int Z, bool S0>
 __global__ void k_pair_overflow(View v, const int2* __restrict__ ovf, const int* __restrict__ novf, int ovf_cap,
-                                const int4* __restrict__ rowoff) {
+                                const int4* __restrict__ rowoff, unsigned char* __restrict__ sflag) {
     const int n = min(*novf, ovf_cap);
     const size_t N = v.N;
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
@@ -1180,10 +1250,13 @@ __global__ void k_pair_overflow(View v, const int2* __restrict__ ovf, const int*
             continue;
         const float mag = fabsf(f[0]) + fabsf(f[1]) + fabsf(f[2]) + fabsf(f[3]) + fabsf(f[4]) + fabsf(f[5]);
         if (!(mag < kMaxTerm)) flag_inst(v, I, (mag == mag) ? kStatusPairForceRange : kStatusNaN);
+        long long* const Ft = sflag ? v.Fbig : v.F;
+        long long* const Tt = sflag ? v.Fbig + 3 * N : v.T;
         for (int a = 0; a < 3; a++) {
-            atomicAdd((unsigned long long*)&v.F[a * N + pi], (unsigned long long)__float2ll_rn(f[a] * 4294967296.0f));
-            atomicAdd((unsigned long long*)&v.T[a * N + pi], (unsigned long long)__float2ll_rn(f[3 + a] * 4294967296.0f));
+            atomicAdd((unsigned long long*)&Ft[a * N + pi], (unsigned long long)__float2ll_rn(f[a] * 4294967296.0f));
+            atomicAdd((unsigned long long*)&Tt[a * N + pi], (unsigned long long)__float2ll_rn(f[3 + a] * 4294967296.0f));
         }
+        if (sflag) sflag[pi] = 1;
     }
 }
 
@@ -1192,8 +1265,9 @@ __global__ void k_pair_overflow(View v, const int2* __restrict__ ovf, const int*
 // force is rounded to the 2^-32 grid once and added to both ends with
 // opposite signs by 64-bit integer atomics: integer sums do not depend on
 // the order, and the result equals evaluating the bond from each end.
+// sflag (nullable): add to the side array instead, and flag both ends.
 template <typename T, bool ENERGY>
-__global__ void k_bonds(View v, long long* __restrict__ energy /* [B][8] */) {
+__global__ void k_bonds(View v, long long* __restrict__ energy /* [B][8] */, unsigned char* __restrict__ sflag) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     int b = -1;
     long long eb = 0, ew = 0;
@@ -1226,9 +1300,11 @@ __global__ void k_bonds(View v, long long* __restrict__ energy /* [B][8] */) {
             if constexpr (sizeof(T) == 4) f = __float2ll_rn(g[a] * 4294967296.0f);
             else f = __double2ll_rn(g[a] * 4294967296.0);
             if (!(fabs(g[a]) < (T)kMaxTerm)) flag_inst(v, I, (g[a] == g[a]) ? kStatusPairForceRange : kStatusNaN);
-            atomicAdd((unsigned long long*)&v.F[a * N + pi], (unsigned long long)f);
-            atomicAdd((unsigned long long*)&v.F[a * N + pj], (unsigned long long)(-f));
+            long long* const Ft = sflag ? v.Fbig : v.F;
+            atomicAdd((unsigned long long*)&Ft[a * N + pi], (unsigned long long)f);
+            atomicAdd((unsigned long long*)&Ft[a * N + pj], (unsigned long long)(-f));
         }
+        if (sflag) { sflag[pi] = 1; sflag[pj] = 1; }
         if (ENERGY) {
             // energy and virial partials in FP64 from the exact displacement
             const double ex = grid_to_double(ddx), ey = grid_to_double(ddy), ez = grid_to_double(ddz);
@@ -1288,6 +1364,7 @@ void Ensemble::alloc_lists() {
     d_novf = alloc<int2>(ovf_cap);
     d_novf_n = alloc<int>(1);
     d_rowoff = alloc<int4>(adj_cap);
+    d_sflag = alloc<unsigned char>(N);
     list_valid = false;
 }
 
@@ -1314,13 +1391,13 @@ void Ensemble::launch_pairs(bool energies, bool dump) {
         const int ng = (int)((N + 127) / 128);
         if (z4 && s0z) {
             k_pair_eval<4, false><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);
-            k_pair_overflow<4, false><<<152, 128, 0, stream>>>(v, d_novf, d_novf_n, ovf_cap, d_rowoff);
+            k_pair_overflow<4, false><<<152, 128, 0, stream>>>(v, d_novf, d_novf_n, ovf_cap, d_rowoff, nullptr);
         } else if (z4) {
             k_pair_eval<4, true><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);
-            k_pair_overflow<4, true><<<152, 128, 0, stream>>>(v, d_novf, d_novf_n, ovf_cap, d_rowoff);
+            k_pair_overflow<4, true><<<152, 128, 0, stream>>>(v, d_novf, d_novf_n, ovf_cap, d_rowoff, nullptr);
         } else {
             k_pair_eval<0, true><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);
-            k_pair_overflow<0, true><<<152, 128, 0, stream>>>(v, d_novf, d_novf_n, ovf_cap, d_rowoff);
+            k_pair_overflow<0, true><<<152, 128, 0, stream>>>(v, d_novf, d_novf_n, ovf_cap, d_rowoff, nullptr);
         }
         launches += 2;
         CK(cudaGetLastError());
@@ -1346,16 +1423,62 @@ void Ensemble::launch_pairs(bool energies, bool dump) {
     tic("bonds");
     const int nb = (int)((std::max(nbond, 1) + 255) / 256);
     if (!force_f64()) {
-        if (energies) k_bonds<float, true><<<nb, 256, 0, stream>>>(v, d_energy);
-        else k_bonds<float, false><<<nb, 256, 0, stream>>>(v, d_energy);
+        if (energies) k_bonds<float, true><<<nb, 256, 0, stream>>>(v, d_energy, nullptr);
+        else k_bonds<float, false><<<nb, 256, 0, stream>>>(v, d_energy, nullptr);
     } else {
-        if (energies) k_bonds<double, true><<<nb, 256, 0, stream>>>(v, d_energy);
-        else k_bonds<double, false><<<nb, 256, 0, stream>>>(v, d_energy);
+        if (energies) k_bonds<double, true><<<nb, 256, 0, stream>>>(v, d_energy, nullptr);
+        else k_bonds<double, false><<<nb, 256, 0, stream>>>(v, d_energy, nullptr);
     }
     launches++;
     CK(cudaGetLastError());
     toc();
     if (!dump) launch_volume(energies);
+}
+
+void Ensemble::launch_pairs_step(bool msums) {
+    View v = view();
+    bool z4 = true, s0z = true;
+    for (auto& I : inst_h) { z4 = z4 && I.zeta == 4; s0z = s0z && I.s0_d == 0.0; }
+    prefer_shared_all();
+    if (!list_valid) {
+        tic("pair_search");
+        CK(cudaMemsetAsync(d_novf_n, 0, sizeof(int), stream));
+        k_pair_search<<<Ktot, kPairThreads, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_novf, d_novf_n, ovf_cap, d_rowoff);
+        launches++;
+        CK(cudaGetLastError());
+        toc();
+        list_valid = true;
+    }
+    tic("pairs_step");
+    // what the epilogue cannot compute from a particle's own list goes to
+    // the side array first: bonds, listed pairs beyond the lists' capacity;
+    // then the constrained volume
+    const int nb = (int)((std::max(nbond, 1) + 255) / 256);
+    k_bonds<float, false><<<nb, 256, 0, stream>>>(v, d_energy, d_sflag);
+    if (z4 && s0z) k_pair_overflow<4, false><<<152, 128, 0, stream>>>(v, d_novf, d_novf_n, ovf_cap, d_rowoff, d_sflag);
+    else if (z4) k_pair_overflow<4, true><<<152, 128, 0, stream>>>(v, d_novf, d_novf_n, ovf_cap, d_rowoff, d_sflag);
+    else k_pair_overflow<0, true><<<152, 128, 0, stream>>>(v, d_novf, d_novf_n, ovf_cap, d_rowoff, d_sflag);
+    launches += 2;
+    launch_volume_sum();
+    long long* ms = msums ? d_msum : nullptr;
+    int* mc = msums ? d_mcnt : nullptr;
+    const View o = view_alt();
+    const int ng = (int)((N + 127) / 128);
+    const bool d = !step_f32();
+#define ORBC_EVAL_STEP(Z, S, D) \
+    k_pair_eval_step<Z, S, D><<<ng, 128, 0, stream>>>(v, o, d_nlist, d_ncnt, list_cap, d_rowoff, d_sflag, d_step, ms, mc)
+    if (z4 && s0z) { if (d) ORBC_EVAL_STEP(4, false, true); else ORBC_EVAL_STEP(4, false, false); }
+    else if (z4) { if (d) ORBC_EVAL_STEP(4, true, true); else ORBC_EVAL_STEP(4, true, false); }
+    else { if (d) ORBC_EVAL_STEP(0, true, true); else ORBC_EVAL_STEP(0, true, false); }
+#undef ORBC_EVAL_STEP
+    launches++;
+    CK(cudaGetLastError());
+    toc();
+    swap_state();
+    k_step_advance<<<1, 64, 0, stream>>>(d_step, B);
+    launches++;
+    CK(cudaGetLastError());
+    forces_valid = false;   // F and T belong to the positions before the update
 }
 
 }  // namespace orbc

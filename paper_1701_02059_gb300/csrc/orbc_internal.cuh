@@ -346,6 +346,16 @@ __device__ inline Frame tangent_frame(float nx, float ny, float nz) {
     return f;
 }
 
+// Volume constraint: the sum D of (x - c).n over the lipids is kept as two
+// integer sums, of the terms' floors at 2^-24 sigma and of their remainders
+// at 2^-48; the enclosed volume is (a/3) D.
+constexpr double kVolUnit = 16777216.0;                 // 2^24: fixed point of (x - c).n, 2^-24 sigma
+constexpr double kVolUnitInv = 5.9604644775390625e-08;  // 2^-24
+constexpr double kVolFineInv = 3.552713678800501e-15;   // 2^-48: the remainders' unit
+__host__ __device__ inline double volume_of(long long hi, long long lo) {
+    return (double)hi * kVolUnitInv + (double)lo * kVolFineInv;
+}
+
 // A particle that moves its cell's centroid (the M-step): the lipids, or
 // every particle of a protein cell set.
 __host__ __device__ inline bool centroid_member(const Inst& I, unsigned char type) {

@@ -22,15 +22,6 @@
 
 namespace orbc {
 
-constexpr double kVolUnit = 16777216.0;                 // 2^24: fixed point of (x - c).n, 2^-24 sigma
-constexpr double kVolUnitInv = 5.9604644775390625e-08;  // 2^-24
-constexpr double kVolFineInv = 3.552713678800501e-15;   // 2^-48: the remainders' unit
-
-// D = sum of (x - c).n from its two integer sums (the 2^-24 floors and the
-// 2^-48 remainders).
-__host__ __device__ inline double volume_of(long long hi, long long lo) {
-    return (double)hi * kVolUnitInv + (double)lo * kVolFineInv;
-}
 constexpr int kVolThreads = 256;
 
 template <typename T> __device__ inline T to_sigma(long long q);
@@ -171,6 +162,15 @@ static int volume_grid(int N) {
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int need = (N + kVolThreads - 1) / kVolThreads;
     return std::max(1, std::min(need, sms * 8));
+}
+
+void Ensemble::launch_volume_sum() {
+    if (!vol_any) return;
+    CK(cudaMemsetAsync(d_vol, 0, sizeof(long long) * 2 * B, stream));
+    if (force_f64()) k_volume_sum<double><<<volume_grid(N), kVolThreads, 0, stream>>>(view(), -1, 0, 0, 0, d_vol);
+    else k_volume_sum<float><<<volume_grid(N), kVolThreads, 0, stream>>>(view(), -1, 0, 0, 0, d_vol);
+    launches++;
+    CK(cudaGetLastError());
 }
 
 void Ensemble::launch_volume(bool energies) {
