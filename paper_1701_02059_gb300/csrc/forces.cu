@@ -767,7 +767,8 @@ struct SNbr {
     int ox, oy, oz;
 };
 
-__global__ void __launch_bounds__(kPairThreads, 7)
+// Eight CTAs per SM (the shared-memory limit): 0.833 against 0.863 ms at seven.
+__global__ void __launch_bounds__(kPairThreads, 8)
     k_pair_search(View v, int* __restrict__ nlist, int* __restrict__ ncnt, int cap, int2* __restrict__ ovf,
                   int* __restrict__ novf, int ovf_cap, int4* __restrict__ rowoff) {
     // sY: staged mirrors (int4 by the bulk copy), then in the tangent frame
@@ -1138,8 +1139,10 @@ __device__ __forceinline__ void eval_list(const View& v, int q, const int* __res
 // eval_list).  (Measured on the 4M cell: evaluating from mirrors staged in
 // shared memory per cell, with each list split over two or four threads,
 // took 1.31 ms against 1.06 ms for this kernel.)
+// Seven CTAs per SM (72 registers, a few spilled) hide more of the gathers'
+// latency than five without spills: 0.785 against 0.857 ms on the 4M cell.
 template <int Z, bool S0>
-__global__ void __launch_bounds__(128, 5)
+__global__ void __launch_bounds__(128, 7)
     k_pair_eval(View v, const int* __restrict__ nlist, const int* __restrict__ ncnt, int cap,
                 const int4* __restrict__ rowoff) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
