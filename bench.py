@@ -553,7 +553,7 @@ def run_reference(args, rank, world):
 
 
 # revisions of the kernels whose ncu summaries are committed under profiles/
-KERNEL_REV = {"k_pair_search": "search-v3", "k_pair_eval": "eval-v3", "k_baoa_d": "baoa-d-v2"}
+KERNEL_REV = {"k_pair_search": "search-v3", "k_pair_eval": "eval-v3", "k_baoa_d": "baoa-d-v3"}
 
 
 def ensemble_jobs(n_instances: int, steps: int):

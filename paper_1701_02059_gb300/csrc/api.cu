@@ -201,6 +201,9 @@ static Inst make_inst(const Params& P) {
     I.sr_d = std::sqrt(std::max(0.0, (1.0 - cr * cr) * P.kT / P.inertia));
     I.hm8_d = std::ldexp(I.h_m_d, 8); I.hi8_d = std::ldexp(I.h_i_d, 8);
     I.st40_d = std::ldexp(I.st_d, 40); I.sr40_d = std::ldexp(I.sr_d, 40); I.ca_d = std::ldexp(0.5 * h, -40);
+    const double noise_scale = 3.4641016151377544 * 1.16415321826934814453125e-10;   // sqrt(12) 2^-33
+    I.stn_d = I.st40_d * noise_scale;
+    I.srn_d = I.sr40_d * noise_scale;
     I.h_m = (float)I.h_m_d; I.h_i = (float)I.h_i_d; I.hdt = (float)I.hdt_d;
     I.ct_m1 = (float)I.ct_m1_d; I.cr_m1 = (float)I.cr_m1_d; I.st = (float)I.st_d; I.sr = (float)I.sr_d;
     I.mass = P.mass; I.inertia = P.inertia;

@@ -217,23 +217,24 @@ __device__ inline void kick_grid(long long vq[3], long long wq[3], const double 
 }
 
 // Cayley increment of the director in grid units: a = (dt/4 2^-40) W,
-// B = a x N, C = a x B, delta = round(2/(1 + |a|^2) (B + C)).
+// B = a x N, delta = round(2/(1 + |a|^2) (B + a x B)).  The angular
+// velocity stays perpendicular to the director (the kicks and the noise are
+// projected onto the plane normal to it, and each rotation turns the
+// director about it), so a x B = a (a.N) - |a|^2 N = -|a|^2 N up to rounding.
 __device__ inline void cayley_grid(const double N[3], const double W[3], const Inst& I, long long d[3]) {
     const double a0 = I.ca_d * W[0], a1 = I.ca_d * W[1], a2 = I.ca_d * W[2];
     const double aa = a0 * a0 + a1 * a1 + a2 * a2;
     const double k = 2.0 / (1.0 + aa);
     const double b0 = a1 * N[2] - a2 * N[1], b1 = a2 * N[0] - a0 * N[2], b2 = a0 * N[1] - a1 * N[0];
-    const double c0 = a1 * b2 - a2 * b1, c1 = a2 * b0 - a0 * b2, c2 = a0 * b1 - a1 * b0;
-    d[0] = rg(k * (b0 + c0));
-    d[1] = rg(k * (b1 + c1));
-    d[2] = rg(k * (b2 + c2));
+    d[0] = rg(k * fma(-aa, N[0], b0));
+    d[1] = rg(k * fma(-aa, N[1], b1));
+    d[2] = rg(k * fma(-aa, N[2], b2));
 }
 
-// Noise in grid-unit form: sqrt(12) 2^-33 (2 (w - 2^31) + 1), exact integer,
-// one rounding.
-__device__ inline double noise_grid(unsigned w) {
-    const long long s = 2 * (long long)(int)(w ^ 0x80000000u) + 1;
-    return (3.4641016151377544 * 1.16415321826934814453125e-10) * (double)s;
+// The noise's integer part 2 (w - 2^31) + 1 (exact); the factor
+// sqrt(12) 2^-33 is folded into the host constants stn_d and srn_d.
+__device__ inline double noise_int(unsigned w) {
+    return (double)(2 * (long long)(int)(w ^ 0x80000000u) + 1);
 }
 
 // The same with FP64 increments in grid units.
@@ -270,19 +271,20 @@ __device__ inline void baoa_d_body(const View& v, const View& o, int p, const lo
     const unsigned long long step = (unsigned long long)steps[b] + (FUSED ? 1ull : 0ull);
     const uint2 key = make_uint2((unsigned)I.seed, (unsigned)(I.seed >> 32) ^ I.instance);
     const uint4 w0 = philox4x32_10(make_uint4(id, (unsigned)step, (unsigned)(step >> 32), 0u), key);
-    const double xi[3] = {noise_grid(w0.x), noise_grid(w0.y), noise_grid(w0.z)};
+    const double xi[3] = {noise_int(w0.x), noise_int(w0.y), noise_int(w0.z)};
     for (int a = 0; a < 3; a++) {
-        const long long d = rg(I.ct_m1_d * Vd[a] + I.st40_d * xi[a]);
+        const long long d = rg(fma(I.ct_m1_d, Vd[a], I.stn_d * xi[a]));
         vq[a] += d;
         Vd[a] = gd(vq[a]);
     }
     if (lipid) {
         const uint4 w1 = philox4x32_10(make_uint4(id, (unsigned)step, (unsigned)(step >> 32), 1u), key);
-        const double r0 = noise_grid(w1.x), r1 = noise_grid(w1.y), r2 = noise_grid(w1.z);
+        // the noise scaled by sr first: its projection is linear
+        const double r0 = I.srn_d * noise_int(w1.x), r1 = I.srn_d * noise_int(w1.y), r2 = I.srn_d * noise_int(w1.z);
         const double u = (r0 * Nd[0] + r1 * Nd[1] + r2 * Nd[2]) * 8.271806125530277e-25;   // (r.N) 2^-80
         const double rp[3] = {r0 - u * Nd[0], r1 - u * Nd[1], r2 - u * Nd[2]};
         for (int a = 0; a < 3; a++) {
-            const long long d = rg(I.cr_m1_d * Wd[a] + I.sr40_d * rp[a]);
+            const long long d = rg(fma(I.cr_m1_d, Wd[a], rp[a]));
             wq[a] += d;
             Wd[a] = gd(wq[a]);
         }
@@ -294,8 +296,8 @@ __device__ inline void baoa_d_body(const View& v, const View& o, int p, const lo
         cayley_grid(Nd, Wd, I, d);
         for (int a = 0; a < 3; a++) { nq[a] += d[a]; Nd[a] = gd(nq[a]); }
         // unit-norm correction n <- n (1 - delta/2), delta = |n|^2 - 1
-        const double delta = (Nd[0] * Nd[0] + Nd[1] * Nd[1] + Nd[2] * Nd[2]) * 8.271806125530277e-25 - 1.0;
-        for (int a = 0; a < 3; a++) nq[a] -= rg(Nd[a] * 0.5 * delta);
+        const double hdelta = 0.5 * ((Nd[0] * Nd[0] + Nd[1] * Nd[1] + Nd[2] * Nd[2]) * 8.271806125530277e-25 - 1.0);
+        for (int a = 0; a < 3; a++) nq[a] -= rg(Nd[a] * hdelta);
     }
     for (int a = 0; a < 3; a++) { o.xq[a * N + p] = xq[a]; o.vq[a * N + p] = vq[a]; }
     // in place a protein's (zero) director and angular velocity need no

@@ -66,6 +66,9 @@ struct Inst {
     // torque at 2^-32 to a grid increment at 2^-40), st 2^40 and sr 2^40,
     // and dt/4 2^-40 (half the Cayley rotation vector from w in grid units)
     double hm8_d, hi8_d, st40_d, sr40_d, ca_d;
+    // st and sr 2^40 times the noise's scale sqrt(12) 2^-33 (multiplying the
+    // noise's exact integer part)
+    double stn_d, srn_d;
     double mass, inertia;
     unsigned long long seed;
     unsigned instance;
