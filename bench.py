@@ -39,12 +39,15 @@ MAX_SM_MHZ = 2070.0
 # candidate test), counted from the pair expression
 FLOP_PER_PAIR = 100.0
 FLOP_PER_CANDIDATE = 9.0
-# FP64 work of one B-A-O-A step (both half kicks, both drifts with their
-# Cayley rotations, the Ornstein-Uhlenbeck update and its noise scaling),
-# counted from the integrator's expressions with FMA = 2: per lipid and per
-# point particle
-FLOP64_PER_LIPID_STEP = 225.0
-FLOP64_PER_BEAD_STEP = 45.0
+# FP64 arithmetic of the integrator's B-A-O-A per step (both half kicks, both
+# drifts with their Cayley maps and the renormalisation, the
+# Ornstein-Uhlenbeck update with its noise scaling), counted from the
+# kernel's expressions with FMA = 2 and a division as 1: per lipid (kick 18,
+# first drift 31, O 30, second drift 42) and per point particle (3 + 3 + 9
+# + 3).  The int64 <-> FP64 conversions (about 60 per lipid) use the same
+# pipe but are not counted.
+FLOP64_PER_LIPID_STEP = 121.0
+FLOP64_PER_BEAD_STEP = 18.0
 # FP64 peak: the recipe's nominal GB300 figure (no measured FP64 peak exists)
 FP64_TFLOPS = 1.25
 # algorithmic HBM bytes of one step per particle (cells rebuilt every step):
