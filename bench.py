@@ -573,25 +573,38 @@ def ensemble_jobs(n_instances: int, steps: int):
     return jobs
 
 
+# size classes of the ensemble's members for the autotuner (particles)
+SIZE_CLASSES = (20_000, 80_000)
+
+
 def run_ensemble(n_instances=64, steps=500, budget_gb=120.0, max_steps=500):
     """Batched arena against one-instance-per-launch on the same GPU; the
-    cell size (particles per Voronoi cell) of every member is the one the
-    autotuner picks on the largest member."""
+    cell size (particles per Voronoi cell) and the pair evaluation's CTAs per
+    SM are the autotuner's choice for the largest member of each size class
+    (below 20k, 20k-80k, above 80k particles)."""
     import torch
     import paper_1701_02059_gb300 as G
     from paper_1701_02059_gb300 import serving
     jobs = ensemble_jobs(n_instances, steps)
-    big = max(jobs, key=lambda j: j["mem"].n)
-    K, _ = G.autotune(big["params"], big["mem"], steps=10)
-    ppc = big["mem"].n / K
+    cls = lambda n: sum(n >= c for c in SIZE_CLASSES)
+    tuned = {}
+    for c in sorted({cls(j["mem"].n) for j in jobs}):
+        big = max((j for j in jobs if cls(j["mem"].n) == c), key=lambda j: j["mem"].n)
+        K, ctas, _ = G.autotune(big["params"], big["mem"], steps=10)
+        tuned[c] = (big["mem"].n / K, ctas)
     for j in jobs:
+        ppc, ctas = tuned[cls(j["mem"].n)]
         j["params"].n_centroids = max(1, round(j["mem"].n / ppc))
+        j["params"].eval_ctas = ctas
+    ppc = sum(j["mem"].n for j in jobs) / sum(j["params"].n_centroids for j in jobs)
     torch.cuda.synchronize()
     _, sb, _ = serving.serve_batched(jobs, int(budget_gb * 2**30), max_steps=max_steps)
     _, sp, _ = serving.serve_plain(jobs)
     keep = ("p50_s", "p99_s", "makespan_s", "particle_steps_per_s")
     return {"instances": n_instances, "steps": steps, "particles": sum(j["mem"].n for j in jobs),
             "particles_per_cell": round(ppc, 1),
+            "tuned_per_size_class": {f"class {c}": {"particles_per_cell": round(v[0], 1), "eval_ctas": v[1]}
+                                     for c, v in sorted(tuned.items())},
             "batched": {k: round(sb[k], 4) for k in keep} | {"gpu_launches": sb["gpu_launches"]},
             "plain": {k: round(sp[k], 4) for k in keep},
             "p99_speedup": round(sp["p99_s"] / sb["p99_s"], 3),

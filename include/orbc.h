@@ -113,6 +113,8 @@ typedef struct {
     orbc_precision precision;
     int n_protein_centroids;                       /* > 0: a separate cell set for the     */
                                                    /* proteins (detached cytoskeleton)     */
+    int eval_ctas;                                 /* pair evaluation CTAs per SM: 5 or 7, */
+                                                   /* 0 = 7 (launch shape; results equal)  */
 } orbc_params;
 
 typedef struct orbc_system orbc_system;   /* opaque; owns its device memory */
@@ -123,7 +125,7 @@ typedef struct orbc_system orbc_system;   /* opaque; owns its device memory */
  * gamma_t = gamma_r = 1, mass = inertia = 1, no periodic axis,
  * n_centroids = 64, n_lloyd_init = 10, rebuild_every = 1, skin = 0,
  * grid_h = 0, seed = 0, instance = 0, ORBC_F32_FORCE_F64_STATE,
- * n_protein_centroids = 0.
+ * n_protein_centroids = 0, eval_ctas = 0.
  *
  * Separate protein cells ("Force Evaluation": a cell whose cytoskeleton is
  * partly or fully detached from the bilayer gets a separate set of Voronoi
@@ -405,21 +407,24 @@ ORBC_API int orbc_get_launch_count(orbc_system* s, long long* count);
 ORBC_API const char* orbc_last_error(const orbc_system* s);
 ORBC_API void orbc_destroy(orbc_system* s);
 
-/* Autotuner of the cell-tile shape (no counterpart in the paper, which fixes
- * the cell count by hand): times the real step ("Spatial Searching
- * Algorithm" + "Force Evaluation": initialisation, then `steps` timed steps)
- * of a copy of the given system for several particles-per-cell sizes (32,
- * 45, 61, 80, 100) and writes the fastest centroid count to
- * *n_centroids_out (and its ms per step to *ms_per_step_out, nullable).
- * Arrays as in orbc_set_particles / orbc_set_bonds (host, copied);
- * params->n_centroids is ignored.  cache_path (nullable): a text file of
- * "shape K ms" lines; a system of the same shape (counts, periodic box,
- * precision, extent) is answered from it without timing, and new results
- * are appended.  Errors: ORBC_E_ARG, ORBC_E_NOMEM, ORBC_E_CUDA, ORBC_E_STATE. */
+/* Autotuner of the cell-tile shape and the pair evaluation's launch shape
+ * (no counterpart in the paper, which fixes the cell count by hand): times
+ * the real step ("Spatial Searching Algorithm" + "Force Evaluation":
+ * initialisation, then `steps` timed steps) of a copy of the given system
+ * for each particles-per-cell size (32, 45, 61, 80, 100) and each pair
+ * evaluation occupancy (5 or 7 CTAs per SM, compiled instances of the
+ * kernel), and writes the fastest centroid count to *n_centroids_out, its
+ * CTAs per SM to *eval_ctas_out (nullable) and its ms per step to
+ * *ms_per_step_out (nullable).  Arrays as in orbc_set_particles /
+ * orbc_set_bonds (host, copied); params->n_centroids and ->eval_ctas are
+ * ignored.  cache_path (nullable): a text file of "shape K ctas ms" lines; a
+ * system of the same shape (counts, periodic box, precision, extent) is
+ * answered from it without timing, and new results are appended.
+ * Errors: ORBC_E_ARG, ORBC_E_NOMEM, ORBC_E_CUDA, ORBC_E_STATE. */
 ORBC_API int orbc_autotune(const orbc_params* params, int n, const double* pos, const double* vel, const double* ori,
                            const double* angvel, const unsigned char* type, const unsigned* id, int nb, const int* ij,
                            const double* r0, const double* kb, int steps, const char* cache_path,
-                           int* n_centroids_out, double* ms_per_step_out);
+                           int* n_centroids_out, int* eval_ctas_out, double* ms_per_step_out);
 
 /* ------------------------------------------------------------------------
  * Batched arena and continuous batching.  The paper runs one membrane per

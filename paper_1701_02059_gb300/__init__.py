@@ -81,8 +81,9 @@ def cell_sort(cell, K: int, stream=None):
 
 
 def autotune(params: Params, mem, steps: int = 10, cache: str | None = None):
-    """orbc_autotune: the centroid count (cell-tile shape) with the fastest
-    step for this membrane; returns (n_centroids, ms_per_step)."""
+    """orbc_autotune: the centroid count (cell-tile shape) and the pair
+    evaluation's CTAs per SM with the fastest step for this membrane;
+    returns (n_centroids, eval_ctas, ms_per_step)."""
     arrs = [np.ascontiguousarray(mem.pos, np.float64), np.ascontiguousarray(mem.vel, np.float64),
             np.ascontiguousarray(mem.ori, np.float64), np.ascontiguousarray(mem.angvel, np.float64),
             np.ascontiguousarray(mem.type, np.uint8), np.ascontiguousarray(mem.id, np.uint32)]
@@ -90,12 +91,13 @@ def autotune(params: Params, mem, steps: int = 10, cache: str | None = None):
     r0 = np.ascontiguousarray(mem.r0, np.float64)
     kb = np.ascontiguousarray(mem.kb, np.float64)
     K = C.c_int(0)
+    ctas = C.c_int(0)
     ms = C.c_double(0.0)
     rc = load().orbc_autotune(C.byref(params), len(arrs[4]), *[_p(a) for a in arrs], len(r0), _p(ij), _p(r0), _p(kb),
-                              int(steps), cache.encode() if cache else None, C.byref(K), C.byref(ms))
+                              int(steps), cache.encode() if cache else None, C.byref(K), C.byref(ctas), C.byref(ms))
     if rc != 0:
         raise OrbcError(rc, "orbc_autotune")
-    return K.value, ms.value
+    return K.value, ctas.value, ms.value
 
 
 class System:

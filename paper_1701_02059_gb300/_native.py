@@ -41,7 +41,7 @@ class Params(C.Structure):
                 ("box", C.c_double * 3), ("periodic", C.c_int * 3),
                 ("n_centroids", C.c_int), ("n_lloyd_init", C.c_int), ("rebuild_every", C.c_int),
                 ("skin", C.c_double), ("grid_h", C.c_double), ("seed", C.c_ulonglong), ("instance", C.c_uint),
-                ("precision", C.c_int), ("n_protein_centroids", C.c_int)]
+                ("precision", C.c_int), ("n_protein_centroids", C.c_int), ("eval_ctas", C.c_int)]
 
 
 class MeshParams(C.Structure):
@@ -118,7 +118,7 @@ def load(path: str | None = None):
     L.orbc_arena_stats.argtypes = [V, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                                    C.POINTER(C.c_longlong)]
     L.orbc_autotune.argtypes = [C.POINTER(Params), C.c_int, V, V, V, V, V, V, C.c_int, V, V, V, C.c_int, C.c_char_p,
-                                C.POINTER(C.c_int), C.POINTER(C.c_double)]
+                                C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
     for name in EXPORTS:
         getattr(L, name).restype = _NOT_INT.get(name, C.c_int) if name in _NOT_INT else C.c_int
     _lib = L

@@ -998,6 +998,7 @@ Params orbc::to_params(const orbc_params* p) {
     P.skin = p->skin; P.grid_h = p->grid_h; P.seed = p->seed; P.instance = p->instance;
     P.precision = (int)p->precision;
     P.n_protein_centroids = p->n_protein_centroids;
+    P.eval_ctas = p->eval_ctas == 0 ? 7 : p->eval_ctas;
     return P;
 }
 
@@ -1019,6 +1020,7 @@ void orbc::check_params(const Params& P) {
     if (!(P.skin >= 0 && fin(P.skin)) || !(P.grid_h >= 0 && fin(P.grid_h))) throw ArgError("invalid skin or grid_h");
     if (P.precision < 0 || P.precision > 2) throw ArgError("unknown precision");
     if (P.n_protein_centroids < 0) throw ArgError("n_protein_centroids must be >= 0");
+    if (P.eval_ctas != 5 && P.eval_ctas != 7) throw ArgError("eval_ctas must be 0, 5 or 7");
 }
 
 
@@ -1125,6 +1127,7 @@ void orbc_default_params(orbc_params* p) {
     p->n_centroids = 64; p->n_lloyd_init = 10; p->rebuild_every = 1; p->skin = 0.0; p->grid_h = 0.0;
     p->seed = 0; p->instance = 0; p->precision = ORBC_F32_FORCE_F64_STATE;
     p->n_protein_centroids = 0;
+    p->eval_ctas = 0;
 }
 
 int orbc_create(const orbc_params* params, void* cuda_stream, orbc_system** out) {

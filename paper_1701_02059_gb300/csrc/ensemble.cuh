@@ -45,6 +45,7 @@ struct Params {
     unsigned instance = 0;
     int precision = 0;   // 0 = FP32 forces, FP64 increments; 1 = FP64 everywhere; 2 = FP32 forces and increments
     int n_protein_centroids = 0;   // > 0: the proteins get a cell set of their own
+    int eval_ctas = 7;             // pair evaluation launched for 5 or 7 CTAs per SM
 };
 
 // One instance as given by the caller (host memory, id order not required).

@@ -1139,10 +1139,11 @@ __device__ __forceinline__ void eval_list(const View& v, int q, const int* __res
 // eval_list).  (Measured on the 4M cell: evaluating from mirrors staged in
 // shared memory per cell, with each list split over two or four threads,
 // took 1.31 ms against 1.06 ms for this kernel.)
-// Seven CTAs per SM (72 registers, a few spilled) hide more of the gathers'
-// latency than five without spills: 0.785 against 0.857 ms on the 4M cell.
-template <int Z, bool S0>
-__global__ void __launch_bounds__(128, 7)
+// Compiled for 5 and 7 CTAs per SM (the autotuner's second dimension):
+// seven (72 registers, a few spilled) hide more of the gathers' latency than
+// five without spills, 0.785 against 0.857 ms on the 4M cell.
+template <int Z, bool S0, int MINB>
+__global__ void __launch_bounds__(128, MINB)
     k_pair_eval(View v, const int* __restrict__ nlist, const int* __restrict__ ncnt, int cap,
                 const int4* __restrict__ rowoff) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1392,16 +1393,26 @@ void Ensemble::launch_pairs(bool energies, bool dump) {
         }
         tic("pairs");
         const int ng = (int)((N + 127) / 128);
+        // the batch's launch shape: the choice of its largest instance
+        int ctas = prm_h[0].eval_ctas, nmax = -1;
+        for (int b = 0; b < B; b++)
+            if (inst_h[b].n > nmax) { nmax = inst_h[b].n; ctas = prm_h[b].eval_ctas; }
+#define ORBC_EVAL(Z, S)                                                                                    \
+    do {                                                                                                   \
+        if (ctas == 5) k_pair_eval<Z, S, 5><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff); \
+        else k_pair_eval<Z, S, 7><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);          \
+    } while (0)
         if (z4 && s0z) {
-            k_pair_eval<4, false><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);
+            ORBC_EVAL(4, false);
             k_pair_overflow<4, false><<<152, 128, 0, stream>>>(v, d_novf, d_novf_n, ovf_cap, d_rowoff, nullptr);
         } else if (z4) {
-            k_pair_eval<4, true><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);
+            ORBC_EVAL(4, true);
             k_pair_overflow<4, true><<<152, 128, 0, stream>>>(v, d_novf, d_novf_n, ovf_cap, d_rowoff, nullptr);
         } else {
-            k_pair_eval<0, true><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);
+            ORBC_EVAL(0, true);
             k_pair_overflow<0, true><<<152, 128, 0, stream>>>(v, d_novf, d_novf_n, ovf_cap, d_rowoff, nullptr);
         }
+#undef ORBC_EVAL
         launches += 2;
         CK(cudaGetLastError());
         toc();

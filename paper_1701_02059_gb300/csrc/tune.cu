@@ -1,13 +1,17 @@
-// Autotuner of the cell-tile shape: the number of particles per Voronoi cell
-// (hence the number of centroids).  A cell is the pair kernel's tile: one CTA
-// stages its neighbouring cells and evaluates its particles in groups of 32,
-// and the rebuild's per-cell kernels work one warp per cell, so the cell size
-// trades staging and search overheads against candidate counts.  Every
-// candidate size runs the real step (k-means initialisation, then timed
-// steps) on a copy of the caller's system; the fastest is returned and, with
-// a cache path, remembered for systems of the same shape.  The pair set and
-// the FP64 results do not depend on the cell size; the FP32 forces change
-// only at the rounding level (the mirrors are relative to the centroids).
+// Autotuner of the cell-tile shape and of the pair evaluation's launch
+// shape.  The tile is the number of particles per Voronoi cell (hence the
+// number of centroids): a cell is the list search's CTA, which stages its
+// neighbouring cells and searches its particles in groups of 32, and the
+// rebuild's per-cell kernels work one warp per cell, so the cell size trades
+// staging and search overheads against candidate counts.  The launch shape
+// is the evaluation's occupancy, 5 or 7 CTAs per SM (compiled instances:
+// more resident warps against a few spilled registers).  Every combination
+// runs the real step (k-means initialisation, then timed steps) on a copy of
+// the caller's system; the fastest is returned and, with a cache path,
+// remembered for systems of the same shape.  The pair set does not depend on
+// either choice, nor do the forces on the launch shape; with FP32 forces
+// they do not depend on the cell size either (the mirrors' reference points
+// are the centroids rounded to the mirror grid).
 #include "abi_common.cuh"
 
 #include <algorithm>
@@ -20,6 +24,7 @@
 namespace orbc {
 
 static const int kTileCandidates[] = {32, 45, 61, 80, 100};
+static const int kEvalCtas[] = {5, 7};
 
 // Shape of a system for the cache: particle, lipid and bond counts, periodic
 // axes and box, precision, and the extent of the particles (rounded).
@@ -42,7 +47,8 @@ static std::string tune_key(const HostInstance& h) {
 
 static std::mutex g_tune_mu;
 
-static bool cache_lookup(const char* path, const std::string& key, int& K, double& ms) {
+// "shape K ctas ms" lines (the last entry of a shape wins).
+static bool cache_lookup(const char* path, const std::string& key, int& K, int& ctas, double& ms) {
     if (!path) return false;
     std::ifstream f(path);
     std::string line;
@@ -50,24 +56,26 @@ static bool cache_lookup(const char* path, const std::string& key, int& K, doubl
     while (std::getline(f, line)) {
         std::istringstream ls(line);
         std::string k;
-        int kk;
+        int kk, cc;
         double m;
-        if (ls >> k >> kk >> m && k == key) { K = kk; ms = m; found = true; }   // the last entry wins
+        if (ls >> k >> kk >> cc >> m && k == key && (cc == 5 || cc == 7)) { K = kk; ctas = cc; ms = m; found = true; }
     }
     return found;
 }
 
-static void cache_store(const char* path, const std::string& key, int K, double ms) {
+static void cache_store(const char* path, const std::string& key, int K, int ctas, double ms) {
     if (!path) return;
     std::ofstream f(path, std::ios::app);
-    if (f) f << key << " " << K << " " << ms << "\n";
+    if (f) f << key << " " << K << " " << ctas << " " << ms << "\n";
 }
 
-// Milliseconds per step of h with K centroids: initialisation and two warm-up
-// steps untimed, then `steps` steps timed with events on the stream.
-static double time_tile(const HostInstance& h, int K, int steps, cudaStream_t st) {
+// Milliseconds per step of h with K centroids and the evaluation at ctas
+// CTAs per SM: initialisation and two warm-up steps untimed, then `steps`
+// steps timed with events on the stream.
+static double time_tile(const HostInstance& h, int K, int ctas, int steps, cudaStream_t st) {
     HostInstance c = h;
     c.prm.n_centroids = K;
+    c.prm.eval_ctas = ctas;
     c.centroids.clear();
     Ensemble e(st);
     e.setup(c);
@@ -96,7 +104,7 @@ using namespace orbc;
 extern "C" int orbc_autotune(const orbc_params* params, int n, const double* pos, const double* vel, const double* ori,
                              const double* angvel, const unsigned char* type, const unsigned* id, int nb, const int* ij,
                              const double* r0, const double* kb, int steps, const char* cache_path,
-                             int* n_centroids_out, double* ms_per_step_out) {
+                             int* n_centroids_out, int* eval_ctas_out, double* ms_per_step_out) {
     if (!params || !n_centroids_out || steps < 1) return ORBC_E_ARG;
     std::string err;
     return guarded_call(&err, [&] {
@@ -108,10 +116,11 @@ extern "C" int orbc_autotune(const orbc_params* params, int n, const double* pos
         const std::string key = tune_key(h);
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
-            int K = 0;
+            int K = 0, ctas = 7;
             double ms = 0;
-            if (cache_lookup(cache_path, key, K, ms)) {
+            if (cache_lookup(cache_path, key, K, ctas, ms)) {
                 *n_centroids_out = K;
+                if (eval_ctas_out) *eval_ctas_out = ctas;
                 if (ms_per_step_out) *ms_per_step_out = ms;
                 return;
             }
@@ -119,15 +128,17 @@ extern "C" int orbc_autotune(const orbc_params* params, int n, const double* pos
         const int nl = (int)std::count(h.type.begin(), h.type.end(), (unsigned char)kLipid);
         cudaStream_t st;
         CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-        int bestK = -1, lastK = -1;
+        int bestK = -1, bestC = 7, lastK = -1;
         double best = 1e300;
         try {
             for (int ppc : kTileCandidates) {
                 const int K = std::max(1, std::min(nl, (int)std::lround((double)n / ppc)));
                 if (K == lastK) continue;        // small systems: sizes that round to the same count
                 lastK = K;
-                const double ms = time_tile(h, K, steps, st);
-                if (ms < best) { best = ms; bestK = K; }
+                for (int ctas : kEvalCtas) {
+                    const double ms = time_tile(h, K, ctas, steps, st);
+                    if (ms < best) { best = ms; bestK = K; bestC = ctas; }
+                }
             }
         } catch (...) {
             cudaStreamDestroy(st);
@@ -138,9 +149,10 @@ extern "C" int orbc_autotune(const orbc_params* params, int n, const double* pos
         if (bestK < 1) throw ArgError("no lipid to seed a cell");
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
-            cache_store(cache_path, key, bestK, best);
+            cache_store(cache_path, key, bestK, bestC, best);
         }
         *n_centroids_out = bestK;
+        if (eval_ctas_out) *eval_ctas_out = bestC;
         if (ms_per_step_out) *ms_per_step_out = best;
     });
 }

@@ -104,10 +104,10 @@ def test_autotune_rejects_bad_arguments(lib):
     p = _native.default_params()
     K = C.c_int(0)
     assert L.orbc_autotune(None, 1, None, None, None, None, None, None, 0, None, None, None, 5, None, C.byref(K),
-                           None) == _native.ORBC_E_ARG
+                           None, None) == _native.ORBC_E_ARG
     assert L.orbc_autotune(C.byref(p), 1, None, None, None, None, None, None, 0, None, None, None, 0, None, C.byref(K),
-                           None) == _native.ORBC_E_ARG                # no timed steps
+                           None, None) == _native.ORBC_E_ARG                # no timed steps
     assert L.orbc_autotune(C.byref(p), 1, None, None, None, None, None, None, 0, None, None, None, 5, None, None,
-                           None) == _native.ORBC_E_ARG                # no output
+                           None, None) == _native.ORBC_E_ARG                # no output
     assert L.orbc_autotune(C.byref(p), 4, None, None, None, None, None, None, 0, None, None, None, 5, None, C.byref(K),
-                           None) == _native.ORBC_E_ARG                # null particle arrays
+                           None, None) == _native.ORBC_E_ARG                # null particle arrays
