@@ -87,7 +87,7 @@ View Ensemble::view() {
     v.cell = d_cell; v.slot_of_id = d_slot_of_id;
     v.F = d_F; v.T = d_T; v.Fbig = d_Fbig;
     v.mq = d_mq; v.mo = d_mo; v.mqr = d_mqr; v.mor = d_mor; v.cnorm = d_cnorm; v.grank = d_grank;
-    v.cq = d_cq; v.cell_start = d_cell_start; v.R = d_R; v.adj_ptr = d_adj_ptr; v.adj = d_adj; v.adj_cap = adj_cap; v.adjd = d_adjd;
+    v.cq = d_cq; v.cell_start = d_cell_start; v.R = d_R; v.Rf = d_Rf; v.adj_ptr = d_adj_ptr; v.adj = d_adj; v.adj_cap = adj_cap; v.adjd = d_adjd;
     v.adjn = d_adjcount;
     v.gstart = d_gstart; v.gcent = d_gcent; v.gcf = d_gcf;
     v.bptr = d_bptr; v.bpartner = d_bpartner;
@@ -239,6 +239,7 @@ void Ensemble::alloc_core(const std::vector<int>& p0, const std::vector<int>& k0
     d_cq_tmp = alloc<long long>((size_t)3 * Ktot);
     d_cell_start = alloc<int>(Ktot + 1);
     d_R = alloc<double>(Ktot);
+    d_Rf = alloc<float>(Ktot);
     d_adj_ptr = alloc<int>(Ktot + 1);
     d_adjcount = alloc<int>(Ktot + 1);
     adj_cap = (long long)Ktot * 64;

@@ -1183,10 +1183,15 @@ __global__ void __launch_bounds__(256, 6) k_cell_props(View v, unsigned long lon
             best = fmax(best, d2);
         }
     }
-    for (int off = 16; off; off >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, off));
+    // the max over the lanes on the bit patterns (a non-negative double's
+    // bits order like its value): integer operations, not the FP64 pipe
+    unsigned long long bb = (unsigned long long)__double_as_longlong(best);
+    for (int off = 16; off; off >>= 1) bb = max(bb, (unsigned long long)__shfl_xor_sync(0xffffffffu, bb, off));
+    best = __longlong_as_double((long long)bb);
     if (lane == 0) {
         const double R = __dsqrt_rn(best);
         v.R[k] = R;
+        v.Rf[k] = (float)R;
         atomicMax(&rmax_bits[b], (unsigned long long)__double_as_longlong(R));
     }
     // pair-kernel frame
@@ -1278,10 +1283,11 @@ constexpr float kBandA = 2e-3f;
 
 // exact neighbouring-cell test of (k, j), FP32 with a margin outside the
 // band and the definition's FP64 operations inside it
-__device__ inline bool adj_test(const View& v, const Inst& I, int k, int j, double Rk, float df, long long cx,
-                                long long cy, long long cz, double tail) {
-    const double t = __dadd_rn(__dadd_rn(Rk, v.R[j]), tail);
-    const float tf = (float)t;
+__device__ inline bool adj_test(const View& v, const Inst& I, int k, int j, double Rk, float Rkf, float df,
+                                long long cx, long long cy, long long cz, double tail, float tailf) {
+    // FP32 prefilter: radii rounded to FP32 differ from the definition's
+    // FP64 sum by far less than the band
+    const float tf = (Rkf + v.Rf[j]) + tailf;
     if (df < tf - kBandA) return true;
     if (df > tf + kBandA) return false;
     const double d = __dsqrt_rn(dist2_grid_d(cx, cy, cz, v.cq[j], v.cq[(size_t)v.Ktot + j], v.cq[(size_t)2 * v.Ktot + j], I));
@@ -1310,8 +1316,10 @@ __global__ void __launch_bounds__(256, 6) k_adj_warp(View v, const unsigned long
     const int b = find_inst(v.inst_k0, v.B, k);
     const Inst& I = v.inst[b];
     const double Rk = v.R[k];
+    const float Rkf = v.Rf[k];
     const long long cx = v.cq[k], cy = v.cq[(size_t)v.Ktot + k], cz = v.cq[(size_t)2 * v.Ktot + k];
     const double tail = (I.rs) + (I.skin + I.skin);
+    const float tailf = (float)tail;
     if (lane == 0) rown[wb] = 0;
     __syncwarp();
     const float reach_own = (float)(Rk + __longlong_as_double((long long)rmax_bits[b]) + I.rs + 2.0 * I.skin) + kBandA;
@@ -1383,7 +1391,7 @@ __global__ void __launch_bounds__(256, 6) k_adj_warp(View v, const unsigned long
                     const float dx = axis_dist(p[0], c.x, G, 0), dy = axis_dist(p[1], c.y, G, 1),
                                 dz = axis_dist(p[2], c.z, G, 2);
                     const float df = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                    if (adj_test(v, I, k, j, Rk, df, cx, cy, cz, tail)) {
+                    if (adj_test(v, I, k, j, Rk, Rkf, df, cx, cy, cz, tail, tailf)) {
                         const int at = atomicAdd(&rown[wb], 1);
                         if (at < kAdjRow) row[wb][at] = j;
                     } else if (own) {

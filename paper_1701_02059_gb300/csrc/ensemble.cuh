@@ -269,6 +269,7 @@ public:
     long long *d_cq = nullptr, *d_cq_tmp = nullptr;
     int* d_cell_start = nullptr;
     double* d_R = nullptr;
+    float* d_Rf = nullptr;
     int *d_adj_ptr = nullptr, *d_adj = nullptr, *d_adjcount = nullptr;
     long long adj_cap = 0;
     int *d_gstart = nullptr, *d_gcount = nullptr, *d_gcent = nullptr, *d_gidx = nullptr;

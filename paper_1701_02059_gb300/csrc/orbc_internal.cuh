@@ -127,6 +127,7 @@ struct View {
     long long* cq;                  // [3][Ktot] centroids on the 2^-40 grid
     int* cell_start;                // [Ktot+1]
     double* R;                      // [Ktot] cell radius
+    float* Rf;                      // [Ktot] the same rounded to FP32 (the neighbour rule's prefilter)
     int* adj_ptr;                   // [Ktot+1]
     int* adj;                       // [adj_cap]
     struct AdjDesc* adjd;           // [Ktot][kAdjRow] staging descriptors, row k ascending by cell
