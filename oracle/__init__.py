@@ -41,7 +41,8 @@ class Model(C.Structure):
     _fields_ = [("eps", C.c_double), ("rmin", C.c_double), ("rc", C.c_double), ("mu", C.c_double),
                 ("sin_theta0", C.c_double), ("zeta", C.c_int), ("pad0", C.c_int),
                 ("eps_wca", C.c_double), ("sigma_wca", C.c_double), ("sigma_pp", C.c_double),
-                ("box", C.c_double * 3), ("periodic", C.c_int * 3), ("pad1", C.c_int)]
+                ("box", C.c_double * 3), ("periodic", C.c_int * 3), ("pad1", C.c_int),
+                ("mem_eps", C.c_double * 9), ("mem_rc", C.c_double * 9)]
 
 
 class Run(C.Structure):
@@ -55,13 +56,24 @@ TWO_SIXTH = 2.0 ** (1.0 / 6.0)
 
 
 def model(eps=1.0, sigma=1.0, rc=2.6, zeta=4, mu=3.0, sin_theta0=0.0, eps_wca=1.0, sigma_wca=1.0, sigma_pp=0.5,
-          box=(0.0, 0.0, 0.0), periodic=(0, 0, 0)) -> Model:
+          box=(0.0, 0.0, 0.0), periodic=(0, 0, 0), mem_eps=None, mem_rc=None) -> Model:
+    """mem_eps, mem_rc: symmetric 3 x 3 tables over the bilayer species
+    (lipid, band-3, glycophorin) of the lipid potential's well depth and
+    cutoff; an entry of 0 (or no table) takes the lipid-lipid value, and the
+    lipid-lipid entry is always (eps, rc)."""
     m = Model()
     m.eps, m.rmin, m.rc, m.mu, m.sin_theta0, m.zeta = eps, TWO_SIXTH * sigma, rc, mu, sin_theta0, zeta
     m.eps_wca, m.sigma_wca, m.sigma_pp = eps_wca, sigma_wca, sigma_pp
     for k in range(3):
         m.box[k] = float(box[k])
         m.periodic[k] = int(periodic[k])
+    te = np.zeros((3, 3)) if mem_eps is None else np.asarray(mem_eps, float).reshape(3, 3)
+    tr = np.zeros((3, 3)) if mem_rc is None else np.asarray(mem_rc, float).reshape(3, 3)
+    for a in range(3):
+        for b in range(3):
+            lip = a == 0 and b == 0
+            m.mem_eps[3 * a + b] = eps if (lip or te[a, b] == 0) else float(te[a, b])
+            m.mem_rc[3 * a + b] = rc if (lip or tr[a, b] == 0) else float(tr[a, b])
     return m
 
 

@@ -47,6 +47,19 @@
 #endif
 
 #define OR_LIPID 0
+#define OR_BAND3 3
+#define OR_GLYCOPHORIN 4
+
+/* Reading P1 (the two-component model's membrane proteins: the paper places
+ * band-3 and glycophorin particles in the membrane, "Initial structure
+ * generation", but prints none of the cited model's constants): band-3 and
+ * glycophorin sit in the bilayer and carry a director like the lipids; any
+ * two bilayer particles interact through the lipid potential with the well
+ * depth and cutoff of their species pair (lipid, band-3, glycophorin), all
+ * other constants shared.  With every pair at the lipid-lipid values a
+ * membrane protein is a lipid with another label. */
+static inline int or_membrane(int t) { return t == OR_LIPID || t == OR_BAND3 || t == OR_GLYCOPHORIN; }
+static inline int or_species(int t) { return t == OR_BAND3 ? 1 : (t == OR_GLYCOPHORIN ? 2 : 0); }
 
 /* ---------------------------------------------------------------- model */
 
@@ -64,6 +77,8 @@ typedef struct {
     double box[3];
     int    periodic[3];
     int    pad1;
+    double mem_eps[9];   /* bilayer species pairs [3 s_i + s_j]: well depth */
+    double mem_rc[9];    /* ... and cutoff (the lipid-lipid pair: eps, rc)  */
 } or_model;
 
 /* 2^(1/6), correctly rounded. */
@@ -77,7 +92,9 @@ double or_search_cutoff(const or_model* m)
 {
     double a = m->rc, b = or_wca_cut(m), c = or_wca_pp_cut(m);
     double r = a > b ? a : b;
-    return r > c ? r : c;
+    r = r > c ? r : c;
+    for (int q = 0; q < 9; q++) r = m->mem_rc[q] > r ? m->mem_rc[q] : r;
+    return r;
 }
 
 /* Minimum image along one axis: d - L * rint(d / L). */
@@ -270,11 +287,24 @@ double or_wca_pair(const or_model* m, const double d[3], double r2, double Fi[3]
     return or_wca_pair_s(m, m->sigma_wca, d, r2, Fi);
 }
 
-/* Cutoff of a type pair. */
+/* Two bilayer particles (reading P1): the lipid potential with the well
+ * depth and cutoff of their species pair. */
+double or_membrane_pair(const or_model* m, int si, int sj, const double d[3], double r2, const double* ni,
+                        const double* nj, double Fi[3], double Ti[3], double Tj[3])
+{
+    or_model q = *m;
+    q.eps = m->mem_eps[3 * si + sj];
+    q.rc = m->mem_rc[3 * si + sj];
+    return or_lipid_pair(&q, d, r2, ni, nj, Fi, Ti, Tj);
+}
+
+/* Cutoff of a type pair: the species pair's for two bilayer particles, the
+ * WCA range for a bilayer particle and a cytoskeleton protein, the
+ * protein-protein WCA range for two cytoskeleton proteins. */
 static inline double or_pair_cut(const or_model* m, int ti, int tj)
 {
-    if (ti == OR_LIPID && tj == OR_LIPID) return m->rc;
-    if (ti == OR_LIPID || tj == OR_LIPID) return or_wca_cut(m);
+    if (or_membrane(ti) && or_membrane(tj)) return m->mem_rc[3 * or_species(ti) + or_species(tj)];
+    if (or_membrane(ti) || or_membrane(tj)) return or_wca_cut(m);
     return or_wca_pp_cut(m);
 }
 
@@ -282,9 +312,10 @@ static inline double or_pair_cut(const or_model* m, int ti, int tj)
 double or_pair_terms(const or_model* m, int ti, int tj, const double d[3], double r2,
                      const double* ni, const double* nj, double Fi[3], double Ti[3], double Tj[3])
 {
-    if (ti == OR_LIPID && tj == OR_LIPID) return or_lipid_pair(m, d, r2, ni, nj, Fi, Ti, Tj);
+    if (or_membrane(ti) && or_membrane(tj))
+        return or_membrane_pair(m, or_species(ti), or_species(tj), d, r2, ni, nj, Fi, Ti, Tj);
     for (int k = 0; k < 3; k++) { Ti[k] = 0.0; Tj[k] = 0.0; }
-    double sig = (ti == OR_LIPID || tj == OR_LIPID) ? m->sigma_wca : m->sigma_pp;
+    double sig = (or_membrane(ti) || or_membrane(tj)) ? m->sigma_wca : m->sigma_pp;
     return or_wca_pair_s(m, sig, d, r2, Fi);
 }
 
@@ -353,14 +384,15 @@ static inline int or_excluded(const or_bondmap* bm, int ida, int idb)
 }
 
 /* Does pair (i, j) interact?  Strict FP64 inclusion d^2 < rc^2 with the
- * type-pair cutoff; 1-2 and 1-3 bonded protein pairs are excluded from the
- * excluded-volume term. */
+ * type-pair cutoff; 1-2 and 1-3 bonded pairs are excluded from the
+ * excluded-volume term (the cytoskeleton's chains, and a membrane protein
+ * anchored to them: reading P3); two bilayer particles never are. */
 static inline int or_interacts(const or_model* m, const or_bondmap* bm, int ti, int tj, int idi, int idj,
                                double r2)
 {
     double rc = or_pair_cut(m, ti, tj);
     if (!(r2 < rc * rc)) return 0;
-    if (!(ti == OR_LIPID && tj == OR_LIPID) && or_excluded(bm, idi, idj)) return 0;
+    if (!(or_membrane(ti) && or_membrane(tj)) && or_excluded(bm, idi, idj)) return 0;
     return 1;
 }
 
@@ -617,11 +649,12 @@ static inline long long or_minimg_grid(long long d, long long L, int per)
 /* ---------------------------------------------------------------- EM centroid update */
 
 /* M-step of the continuous k-means update: each centroid moves to the mean
- * of its lipids (the lipid cells are reused for proteins, "Force
- * Evaluation").  Reading, exact integer arithmetic on the 2^-40 grid:
- *   S_k = sum_{lipids i in k} minimg(x_i - c_k),  n_k = their count,
+ * of its bilayer particles, the lipids and the membrane proteins (the lipid
+ * cells are reused for the cytoskeleton's proteins, "Force Evaluation").
+ * Reading, exact integer arithmetic on the 2^-40 grid:
+ *   S_k = sum_{bilayer i in k} minimg(x_i - c_k),  n_k = their count,
  *   c_k <- c_k + floor((2 S_k + n_k) / (2 n_k))   (mean, ties rounding up);
- * cells without lipids keep their centroid; periodic axes wrap into
+ * cells without bilayer particles keep their centroid; periodic axes wrap into
  * [0, L).  Positions off the grid are rounded to it first. */
 void or_lloyd(int n, const double* x, const unsigned char* type, const int* cell, int K, const double* c_in,
               double* c_out, const double* box, const int* per)
@@ -631,7 +664,7 @@ void or_lloyd(int n, const double* x, const unsigned char* type, const int* cell
     long long L[3];
     for (int a = 0; a < 3; a++) L[a] = per[a] ? or_to_grid(box[a]) : 0;
     for (int i = 0; i < n; i++) {
-        if (type[i] != OR_LIPID) continue;
+        if (!or_membrane(type[i])) continue;
         int k = cell[i];
         for (int a = 0; a < 3; a++) {
             long long d = or_to_grid(x[3 * i + a]) - or_to_grid(c_in[3 * k + a]);
@@ -888,7 +921,7 @@ int or_sys_set_particles(or_sys* s, int n, const double* pos, const double* vel,
     memcpy(s->type, type, (size_t)n);
     memcpy(s->id, id, sizeof(unsigned) * (size_t)n);
     for (int i = 0; i < n; i++) for (int k = 0; k < 3; k++) {
-        int lip = type[i] == OR_LIPID;
+        int lip = or_membrane(type[i]);
         s->n_[3 * i + k] = lip ? or_from_grid(or_to_grid(ori[3 * i + k])) : 0.0;
         s->w[3 * i + k] = lip ? or_from_grid(or_to_grid(angvel[3 * i + k])) : 0.0;
     }
@@ -948,7 +981,8 @@ static void or_permute(or_sys* s, const int* perm)
 /* Separate protein cells ("Force Evaluation": for a cell whose cytoskeleton
  * is partly or fully detached, the proteins get a Voronoi cell set of their
  * own).  Reading D1: with K_P = n_protein_centroids > 0, cells 0..K_L-1
- * cluster the lipids and K_L..K_L+K_P-1 the proteins; each particle belongs
+ * cluster the bilayer (lipids and membrane proteins) and K_L..K_L+K_P-1 the
+ * cytoskeleton's proteins; each particle belongs
  * to the nearest centroid of its own set, and each centroid moves to the
  * mean of its own members.  Reading D2: the neighbouring-cell rule is the
  * same over both sets together, so the quad loop over a cell and its
@@ -971,7 +1005,7 @@ static void or_assign_sets(or_sys* s)
     for (int set = 0; set < 2; set++) {
         int m = 0;
         for (int i = 0; i < n; i++) {
-            if ((s->type[i] != OR_LIPID) != set) continue;
+            if ((!or_membrane(s->type[i])) != set) continue;
             for (int a = 0; a < 3; a++) xs[3 * m + a] = s->x[3 * i + a];
             idx[m++] = i;
         }
@@ -982,7 +1016,7 @@ static void or_assign_sets(or_sys* s)
     free(xs); free(idx); free(cs);
 }
 
-/* M-step: lipids only for the shared cells; with separate sets every
+/* M-step: bilayer particles only for the shared cells; with separate sets every
  * particle is a member of its own set's cell. */
 static void or_mstep_sets(or_sys* s, double* c_out)
 {
@@ -1039,13 +1073,13 @@ static int or_finish_cells(or_sys* s)
 static int or_seed_set(or_sys* s, int proteins, int K, double* c)
 {
     int m = 0;
-    for (int i = 0; i < s->n; i++) if ((s->type[i] != OR_LIPID) == proteins) m++;
+    for (int i = 0; i < s->n; i++) if ((!or_membrane(s->type[i])) == proteins) m++;
     if (m < K) return -1;
     int* mem = (int*)malloc(sizeof(int) * (size_t)(m > 0 ? m : 1));
     int q = 0;
     for (int idv = 0; idv <= s->max_id; idv++) {
         int slot = s->slot_of_id[idv];
-        if (slot >= 0 && (s->type[slot] != OR_LIPID) == proteins) mem[q++] = slot;
+        if (slot >= 0 && (!or_membrane(s->type[slot])) == proteins) mem[q++] = slot;
     }
     for (int k = 0; k < K; k++) {
         long long pick = ((long long)k * m) / K;
@@ -1055,10 +1089,11 @@ static int or_seed_set(or_sys* s, int proteins, int K, double* c)
     return 0;
 }
 
-/* Initial k-means: centroids given, or seeded from the lipids in id order
- * (c_k = lipid floor(k N_L / K)), with separate protein cells the protein
- * centroids likewise from the proteins; then n_lloyd_init rounds of
- * [E-step, M-step] (shared cells: E over all particles, M over lipids);
+/* Initial k-means: centroids given, or seeded from the bilayer particles in
+ * id order (c_k = bilayer particle floor(k N_L / K)), with separate protein
+ * cells the protein centroids likewise from the cytoskeleton's proteins; then
+ * n_lloyd_init rounds of [E-step, M-step] (shared cells: E over all
+ * particles, M over the bilayer);
  * then the two-level reorder. */
 int or_sys_init_cells(or_sys* s, const double* centroids)
 {
@@ -1151,10 +1186,11 @@ static void or_compute(or_sys* s)
     /* harmonic volume constraint ("Validation and Benchmark": a harmonic
      * volume constraint keeps the cell's surface-to-volume ratio; the form
      * is not given).  Reading V1: the enclosed volume of a particle
-     * membrane by the divergence theorem over the lipids' area elements,
-     * V = (1/3) sum a (x_i - x_c).n_i, a the area per lipid, x_c a fixed
+     * membrane by the divergence theorem over the bilayer particles' area
+     * elements (lipids and membrane proteins), V = (1/3) sum a
+     * (x_i - x_c).n_i, a the area per particle, x_c a fixed
      * reference point inside.  Reading V2: U_V = k_V (V - V0)^2 / 2 acts as
-     * the uniform pressure P = -k_V (V - V0) on each lipid's area element,
+     * the uniform pressure P = -k_V (V - V0) on each area element,
      * F_i += P a n_i (moving one element by delta along its normal changes
      * the enclosed volume by a delta), and exerts no torque (a uniform
      * pressure has no moment about the element's own centre).  U_V is
@@ -1164,13 +1200,13 @@ static void or_compute(or_sys* s)
     if (s->vol_on) {
         double V = 0.0;
         for (int i = 0; i < n; i++) {
-            if (s->type[i] != OR_LIPID) continue;
+            if (!or_membrane(s->type[i])) continue;
             double d[3] = { s->x[3 * i] - s->xc[0], s->x[3 * i + 1] - s->xc[1], s->x[3 * i + 2] - s->xc[2] };
             V += s->a_vol * dot3(d, s->n_ + 3 * i) / 3.0;
         }
         const double Pa = -s->kv * (V - s->v0) * s->a_vol;
         for (int i = 0; i < n; i++) {
-            if (s->type[i] != OR_LIPID) continue;
+            if (!or_membrane(s->type[i])) continue;
             for (int c = 0; c < 3; c++) s->F[3 * i + c] += Pa * s->n_[3 * i + c];
         }
         s->vol = V;
@@ -1182,7 +1218,7 @@ static void or_compute(or_sys* s)
         U += up[i];
         W += wp[i];
         kt += 0.5 * s->r.mass * dot3(s->v + 3 * i, s->v + 3 * i);
-        if (s->type[i] == OR_LIPID) kr += 0.5 * s->r.inertia * dot3(s->w + 3 * i, s->w + 3 * i);
+        if (or_membrane(s->type[i])) kr += 0.5 * s->r.inertia * dot3(s->w + 3 * i, s->w + 3 * i);
     }
     s->energies[0] = U;
     s->energies[1] = ub;
@@ -1209,7 +1245,7 @@ double or_sys_volume(or_sys* s, double area, const double* xc)
 {
     double V = 0.0;
     for (int i = 0; i < s->n; i++) {
-        if (s->type[i] != OR_LIPID) continue;
+        if (!or_membrane(s->type[i])) continue;
         double d[3] = { s->x[3 * i] - xc[0], s->x[3 * i + 1] - xc[1], s->x[3 * i + 2] - xc[2] };
         V += area * dot3(d, s->n_ + 3 * i) / 3.0;
     }
@@ -1218,7 +1254,7 @@ double or_sys_volume(or_sys* s, double area, const double* xc)
 
 /* Height map for the membrane fluctuation measurement ("Validation and
  * Benchmark": the instantaneous vertical fluctuation dh(x, y) along the
- * upper rim of a fixed cell; reading H1): lipids above z_min whose distance
+ * upper rim of a fixed cell; reading H1): bilayer particles above z_min whose distance
  * rho from the axis through (ax, ay) lies in [rho_in, rho_out) are binned on
  * the grid [x0 + i dx, x0 + (i + 1) dx) x [y0 + j dy, ...), i < nx, j < ny;
  * h[j nx + i] = their mean z (0 where the bin is empty), count = their
@@ -1228,7 +1264,7 @@ void or_height_map(const or_sys* s, double x0, double y0, double dx, double dy, 
 {
     for (int q = 0; q < nx * ny; q++) { h[q] = 0.0; count[q] = 0; }
     for (int i = 0; i < s->n; i++) {
-        if (s->type[i] != OR_LIPID) continue;
+        if (!or_membrane(s->type[i])) continue;
         const double* x = s->x + 3 * i;
         if (!(x[2] > z_min)) continue;
         const double rx = x[0] - ax, ry = x[1] - ay;
@@ -1273,7 +1309,7 @@ static void or_kick(or_sys* s, double h)
     #pragma omp parallel for schedule(static)
     for (int i = 0; i < s->n; i++) {
         for (int c = 0; c < 3; c++) s->v[3 * i + c] += hm * s->F[3 * i + c];
-        if (s->type[i] == OR_LIPID) {
+        if (or_membrane(s->type[i])) {
             const double* nn = s->n_ + 3 * i;
             const double* t = s->T + 3 * i;
             double tn = dot3(t, nn);
@@ -1287,7 +1323,7 @@ static void or_drift(or_sys* s, double h)
     #pragma omp parallel for schedule(static)
     for (int i = 0; i < s->n; i++) {
         for (int c = 0; c < 3; c++) s->x[3 * i + c] += h * s->v[3 * i + c];
-        if (s->type[i] == OR_LIPID) {
+        if (or_membrane(s->type[i])) {
             double* nn = s->n_ + 3 * i;
             double* w = s->w + 3 * i;
             double th[3] = { h * w[0], h * w[1], h * w[2] };
@@ -1308,7 +1344,7 @@ static void or_thermostat(or_sys* s)
         double xi[3];
         or_noise3(s->r.seed, s->r.instance, s->id[i], (uint64_t)s->step, 0u, xi);
         for (int c = 0; c < 3; c++) s->v[3 * i + c] = ct * s->v[3 * i + c] + st * xi[c];
-        if (s->type[i] == OR_LIPID) {
+        if (or_membrane(s->type[i])) {
             const double* nn = s->n_ + 3 * i;
             or_noise3(s->r.seed, s->r.instance, s->id[i], (uint64_t)s->step, 1u, xi);
             double xn = dot3(xi, nn);
@@ -1329,7 +1365,7 @@ static double or_max_displacement(or_sys* s)
 }
 
 /* BAOAB Langevin steps (Leimkuhler & Matthews 2013), translational for all
- * particles and rotational for lipids:
+ * particles and rotational for the bilayer's (lipids and membrane proteins):
  *   B: v += dt/2 F/m, w += dt/2 (tau - (tau.n) n)/I
  *   A: x += dt/2 v, n rotated by dt/2 w (Cayley), w projected onto n-perp
  *   O: v = c v + sqrt((1-c^2) kT/m) xi, w = c w + sqrt((1-c^2) kT/I) P_perp xi
@@ -1362,7 +1398,7 @@ int or_sys_integrate(or_sys* s, int nsteps)
  * mesh oracle): per step, with the current forces,
  *   v += dt F/m, then v <- (v.F) F / |F|^2 when v.F > 0, else v <- 0,
  *   scaled down so that |dt v| <= max_move; x += dt v;
- *   for lipids w += dt tau_perp / I with tau_perp = tau - (tau.n) n, then
+ *   for bilayer particles w += dt tau_perp / I with tau_perp = tau - (tau.n) n, then
  *   w <- (w.tau_perp) tau_perp / |tau_perp|^2 when positive, else 0,
  *   scaled down so that |dt w| <= max_turn; n rotated by dt w (Cayley map,
  *   renormalised);
@@ -1384,7 +1420,7 @@ int or_sys_quench(or_sys* s, int nsteps, double dt, double max_move, double max_
             if (mv > max_move)
                 for (int c = 0; c < 3; c++) v[c] = v[c] * (max_move / mv);
             for (int c = 0; c < 3; c++) s->x[3 * i + c] = s->x[3 * i + c] + dt * v[c];
-            if (s->type[i] == OR_LIPID) {
+            if (or_membrane(s->type[i])) {
                 double* w = s->w + 3 * i;
                 double* nn = s->n_ + 3 * i;
                 const double* t = s->T + 3 * i;

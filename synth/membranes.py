@@ -7,7 +7,9 @@ FP64 oracle consume.  They contain none of the simulation method's arithmetic
 Particle types follow the two-component red-cell model the paper simulates
 (Introduction; "Initial structure generation"): lipids (type 0) carry an
 orientation, spectrin-network junctions (type 1) and spectrin beads (type 2)
-are point particles linked by harmonic bonds.
+are point particles linked by harmonic bonds; band-3 (type 3) and
+glycophorin (type 4) sit in the bilayer with an orientation like the lipids
+(``with_membrane_proteins``).
 
 Every system is returned as a ``Membrane`` with host numpy arrays in id order:
 
@@ -36,7 +38,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-LIPID, JUNCTION, SPECTRIN = 0, 1, 2
+LIPID, JUNCTION, SPECTRIN, BAND3, GLYCOPHORIN = 0, 1, 2, 3, 4
+BILAYER = (LIPID, BAND3, GLYCOPHORIN)
 
 LIPID_SPACING = 1.12                     # nearest-neighbour lipid distance (sigma)
 ROW_PITCH = LIPID_SPACING * math.sqrt(3.0) / 2.0
@@ -69,6 +72,11 @@ class Membrane:
     @property
     def n_lipids(self) -> int:
         return int(np.count_nonzero(self.type == LIPID))
+
+    @property
+    def n_bilayer(self) -> int:
+        """Particles with a director: lipids and membrane proteins."""
+        return int(np.count_nonzero(np.isin(self.type, BILAYER)))
 
     def copy(self) -> "Membrane":
         return Membrane(self.pos.copy(), self.vel.copy(), self.ori.copy(), self.angvel.copy(),
@@ -500,6 +508,69 @@ def request_stream(n_requests: int = 256, rate_per_s: float = 1.0, seed: int = 4
             n_est = int(nl * 1.55)
         out.append({"arrival_s": t, "steps": steps, "n_est": n_est, "build": build, "kT": kT})
     return out
+
+
+def with_membrane_proteins(mem: Membrane, seed: int = 0, glycophorin: bool = True, anchored_beads: float = 0.25,
+                           mobile_band3: float = 0.05, kb_anchor: float = 50.0) -> Membrane:
+    """The membrane with the two-component model's bilayer proteins
+    ("Initial structure generation": glycophorin bound to the actin
+    junctions, immobile band-3 bound to the spectrin, mobile band-3 free in
+    the bilayer), made by relabelling lipids, so that every id keeps its
+    place and the bilayer still holds ids 0..N_B-1:
+
+    * glycophorin: for each junction, the nearest lipid not yet taken, joined
+      to it by an anchor bond;
+    * immobile band-3: for a seeded share `anchored_beads` of the spectrin
+      beads, the nearest lipid not yet taken, joined to the bead;
+    * mobile band-3: a seeded share `mobile_band3` of the remaining lipids.
+
+    Anchor bonds start at rest (r0 = the distance at construction) with
+    constant kb_anchor.  Geometry and random draws only."""
+    from scipy.spatial import cKDTree
+    out = mem.copy()
+    rng = _rng(seed)
+    lip = np.flatnonzero(out.type == LIPID)
+    taken = np.zeros(out.n, bool)
+    tree = cKDTree(out.pos[lip])
+    anchors = []
+    targets = []
+    if glycophorin:
+        targets += [(int(i), GLYCOPHORIN) for i in np.flatnonzero(out.type == JUNCTION)]
+    beads = np.flatnonzero(out.type == SPECTRIN)
+    if anchored_beads > 0 and len(beads):
+        pick = np.sort(rng.choice(beads, int(round(anchored_beads * len(beads))), replace=False))
+        targets += [(int(i), BAND3) for i in pick]
+    for p, t in targets:
+        k = 8
+        while True:
+            _, q = tree.query(out.pos[p], k=min(k, len(lip)))
+            free = [lip[j] for j in np.atleast_1d(q) if not taken[lip[j]]]
+            if free or k >= len(lip):
+                break
+            k *= 4
+        if not free:
+            continue
+        m = int(free[0])
+        taken[m] = True
+        out.type[m] = t
+        anchors.append((int(out.id[m]), int(out.id[p]), float(np.linalg.norm(out.pos[m] - out.pos[p]))))
+    rest = np.flatnonzero((out.type == LIPID) & ~taken)
+    if mobile_band3 > 0 and len(rest):
+        out.type[rng.choice(rest, int(round(mobile_band3 * len(rest))), replace=False)] = BAND3
+    if anchors:
+        a = np.array([[x[0], x[1]] for x in anchors], np.int32)
+        out.bonds = np.vstack([out.bonds, a]).astype(np.int32)
+        out.r0 = np.concatenate([out.r0, [x[2] for x in anchors]])
+        out.kb = np.concatenate([out.kb, np.full(len(anchors), kb_anchor)])
+    out.name = (mem.name or "membrane") + "+proteins"
+    return out
+
+
+def rbc_4m_proteins(seed: int = 2) -> Membrane:
+    """The 4,000,000-particle cell with the full protein set: 33,000
+    glycophorin (one per junction), immobile band-3 on a quarter of the
+    spectrin beads and 5 % of the other lipids as mobile band-3."""
+    return with_membrane_proteins(biconcave(seed=seed), seed=seed + 100)
 
 
 def _with_cells(mem: Membrane) -> Membrane:
