@@ -109,8 +109,8 @@ def lib():
                                         C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, P, P]
             L.or_sys_quench.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_double, P]
             L.or_mesh_build.argtypes = [C.c_int, P, C.c_int, P, C.c_double, C.c_int, C.c_double, C.c_double,
-                                        C.c_double, C.c_double, C.c_double, C.c_ulonglong, C.c_longlong, P, P, P, P,
-                                        C.c_longlong, P, P, P, P]
+                                        C.c_double, C.c_double, C.c_double, C.c_ulonglong, C.c_double, C.c_int,
+                                        C.c_int, C.c_double, C.c_longlong, P, P, P, P, C.c_longlong, P, P, P, P]
             L.or_sys_get_state.argtypes = [P, P, P, P, P, P]
             L.or_sys_get_forces.argtypes = [P, P, P]
             L.or_sys_get_cells.argtypes = [P, P, P, P, P, P, P, P]
@@ -208,14 +208,16 @@ def bond_pair(d, kb, r0):
     return U, Fa
 
 
-def mesh_build(verts, faces, spacing=1.12, beads=4, slack=1.03, kb=100.0, offset=1.0, d_min=0.8, d_ll=0.2, seed=0):
-    """Particles and bonds of a triangular mesh (readings M1-M6 of
+def mesh_build(verts, faces, spacing=1.12, beads=4, slack=1.03, kb=100.0, offset=1.0, d_min=0.8, d_ll=0.2, seed=0,
+               band3_fraction=0.0, glycophorin=0, band3_edges=0, kb_anchor=50.0):
+    """Particles and bonds of a triangular mesh (readings M1-M11 of
     orbc_oracle_mesh.c): returns dict(pos, ori, type, bonds, r0, kb)."""
     v = _c(verts, np.float64)
     f = _c(faces, np.int32)
     n, nb = C.c_longlong(0), C.c_longlong(0)
     args = (len(v), _p(v), len(f), _p(f), float(spacing), int(beads), float(slack), float(kb), float(offset),
-            float(d_min), float(d_ll), int(seed))
+            float(d_min), float(d_ll), int(seed), float(band3_fraction), int(glycophorin), int(band3_edges),
+            float(kb_anchor))
     if lib().or_mesh_build(*args, 0, None, None, None, C.byref(n), 0, None, None, None, C.byref(nb)) != 0:
         raise ValueError("invalid mesh")
     pos, ori = np.zeros((n.value, 3)), np.zeros((n.value, 3))

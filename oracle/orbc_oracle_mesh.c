@@ -39,6 +39,22 @@
  *      against the squared distance): uniform random points at membrane
  *      density would otherwise put pairs so close that a single pair term
  *      leaves the range of the force sums;
+ *   M8 glycophorin (when asked for): one per vertex, at the vertex itself
+ *      with the vertex normal as director, bonded to its junction (rest
+ *      length |v - J_v|, constant kb_anchor);
+ *   M9 immobile band-3 (when asked for, beads >= 1): one per edge at the
+ *      midpoint (a + b) / 2 of its two vertices, director the normalised
+ *      FP64 sum of the two vertices' exact normal sums, bonded to the
+ *      chain's bead floor((beads - 1) / 2) (rest length the distance at
+ *      construction, constant kb_anchor);
+ *   M10 mobile band-3: face sample k of face f is a band-3 instead of a
+ *      lipid when word 2 at counter (f, k, 0, 3), as (w + 1/2) 2^-32, is
+ *      below band3_fraction; it is kept or dropped by the lipids' rules;
+ *   M11 glycophorin and immobile band-3 are protein particles for the
+ *      minimum distance d_min of the face samples; the bilayer comes first
+ *      in id order: kept face samples, glycophorin (vertex order), immobile
+ *      band-3 (edge order), then junctions and spectrin as in M5; the
+ *      anchor bonds follow the chains' bonds, glycophorin's first;
  *   M7 the velocity quench (the paper names no scheme): quick-min with
  *      rotations -- v += dt F/m, then v is replaced by its component along
  *      F, or zero when it points against F, and scaled down so that
@@ -90,11 +106,12 @@ static double or_norm(const double* a)
  * only); cap / bcap bound what is written.  Returns 0, or -1 for an invalid
  * mesh (a vertex index out of range, a degenerate face). */
 int or_mesh_build(int nv, const double* verts, int nf, const int* faces, double spacing, int beads, double slack,
-                  double kb, double offset, double d_min, double d_ll, uint64_t seed, long long cap, double* pos,
-                  double* ori,
+                  double kb, double offset, double d_min, double d_ll, uint64_t seed, double band3_fraction,
+                  int glycophorin, int band3_edges, double kb_anchor, long long cap, double* pos, double* ori,
                   unsigned char* type, long long* n_out, long long bcap, int* bonds, double* r0, double* kbo,
                   long long* nb_out)
 {
+    if (band3_edges && beads < 1) return -1;
     const double a_lip = 0.8660254037844386 * spacing * spacing;   /* sqrt(3)/2 s^2 */
     for (int q = 0; q < 3 * nf; q++)
         if (faces[q] < 0 || faces[q] >= nv) return -1;
@@ -151,8 +168,11 @@ int or_mesh_build(int nv, const double* verts, int nf, const int* faces, double 
         fcount[f] = (long long)fl + (or_u01(w[0]) < lam - fl ? 1 : 0);
         ncand += fcount[f];
     }
-    const long long nprot = nv + ne * beads;
+    const long long ncyt = nv + ne * beads;                       /* junctions and spectrin */
+    const long long ngly = glycophorin ? nv : 0, nb3e = band3_edges ? ne : 0;
+    const long long nprot = ncyt + ngly + nb3e;                    /* every protein particle */
     double* prot = malloc(sizeof(double) * 3 * (size_t)(nprot > 0 ? nprot : 1));
+    double* pdir = malloc(sizeof(double) * 3 * (size_t)(ngly + nb3e > 0 ? ngly + nb3e : 1));
     for (int v = 0; v < nv; v++)
         for (int k = 0; k < 3; k++) prot[3 * v + k] = junc[3 * v + k];
     for (long long e = 0; e < ne; e++) {
@@ -165,9 +185,31 @@ int or_mesh_build(int nv, const double* verts, int nf, const int* faces, double 
             for (int k = 0; k < 3; k++) prot[3 * (nv + e * beads + (j - 1)) + k] = junc[3 * a + k] + d[k] * t;
         }
     }
+    /* glycophorin on the vertices, band-3 on the edges' midpoints (M8, M9) */
+    for (long long v = 0; v < ngly; v++) {
+        double n[3] = { (double)nacc[3 * v], (double)nacc[3 * v + 1], (double)nacc[3 * v + 2] };
+        double l = or_norm(n);
+        for (int k = 0; k < 3; k++) {
+            prot[3 * (ncyt + v) + k] = verts[3 * v + k];
+            pdir[3 * v + k] = l > 0.0 ? n[k] / l : 0.0;
+        }
+    }
+    for (long long e = 0; e < nb3e; e++) {
+        const int h = owner[e], f = h / 3, i = h % 3;
+        const int a = faces[3 * f + i], b = faces[3 * f + (i + 1) % 3];
+        double n[3];
+        for (int k = 0; k < 3; k++) n[k] = (double)nacc[3 * a + k] + (double)nacc[3 * b + k];
+        double l = or_norm(n);
+        for (int k = 0; k < 3; k++) {
+            prot[3 * (ncyt + ngly + e) + k] = (verts[3 * a + k] + verts[3 * b + k]) * 0.5;
+            pdir[3 * (ngly + e) + k] = l > 0.0 ? n[k] / l : 0.0;
+        }
+    }
 
-    /* 2. lipid candidates: uniform samples of every face, in candidate order */
+    /* 2. lipid candidates: uniform samples of every face, in candidate order
+     *    (some of them mobile band-3, M10) */
     double* cand = malloc(sizeof(double) * 6 * (size_t)(ncand > 0 ? ncand : 1));
+    unsigned char* ctype = malloc((size_t)(ncand > 0 ? ncand : 1));
     long long ic = 0;
     for (int f = 0; f < nf; f++) {
         const double *a = verts + 3 * faces[3 * f], *b = verts + 3 * faces[3 * f + 1], *c = verts + 3 * faces[3 * f + 2];
@@ -180,6 +222,7 @@ int or_mesh_build(int nv, const double* verts, int nf, const int* faces, double 
             uint32_t w[4];
             or_words(seed, (uint32_t)f, (uint32_t)s, 3u, w);
             const double sr1 = sqrt(or_u01(w[0])), r2 = or_u01(w[1]);
+            ctype[ic] = or_u01(w[2]) < band3_fraction ? 3 : 0;
             const double ca = 1.0 - sr1, cb = sr1 * (1.0 - r2), cc = sr1 * r2;
             for (int k = 0; k < 3; k++) {
                 cand[6 * ic + k] = (ca * a[k] + cb * b[k]) + cc * c[k];
@@ -212,18 +255,29 @@ int or_mesh_build(int nv, const double* verts, int nf, const int* faces, double 
         if (!keep) continue;
         if (pos && nl < cap) {
             for (int k = 0; k < 3; k++) { pos[3 * nl + k] = p[k]; ori[3 * nl + k] = p[3 + k]; }
-            type[nl] = 0;
+            type[nl] = ctype[i];
         }
         nl++;
     }
     free(cand);
-    /* 5. proteins after the lipids */
-    const long long n = nl + nprot;
-    if (pos)
-        for (long long q = 0; q < nprot && nl + q < cap; q++) {
-            for (int k = 0; k < 3; k++) { pos[3 * (nl + q) + k] = prot[3 * q + k]; ori[3 * (nl + q) + k] = 0.0; }
-            type[nl + q] = q < nv ? 1 : 2;
+    free(ctype);
+    /* 5. the bilayer's proteins after the face samples, then the
+     *    cytoskeleton (M11) */
+    const long long nbil = nl + ngly + nb3e;
+    const long long n = nbil + ncyt;
+    if (pos) {
+        for (long long q = 0; q < ngly + nb3e && nl + q < cap; q++) {
+            for (int k = 0; k < 3; k++) {
+                pos[3 * (nl + q) + k] = prot[3 * (ncyt + q) + k];
+                ori[3 * (nl + q) + k] = pdir[3 * q + k];
+            }
+            type[nl + q] = q < ngly ? 4 : 3;
         }
+        for (long long q = 0; q < ncyt && nbil + q < cap; q++) {
+            for (int k = 0; k < 3; k++) { pos[3 * (nbil + q) + k] = prot[3 * q + k]; ori[3 * (nbil + q) + k] = 0.0; }
+            type[nbil + q] = q < nv ? 1 : 2;
+        }
+    }
     /* bonds of every chain */
     long long nb = 0;
     for (long long e = 0; e < ne; e++) {
@@ -233,8 +287,8 @@ int or_mesh_build(int nv, const double* verts, int nf, const int* faces, double 
         or_sub3(junc + 3 * b, junc + 3 * a, d);
         const double rest = slack * or_norm(d) / (double)(beads + 1);
         for (int j = 0; j <= beads; j++) {
-            const long long u = j == 0 ? nl + a : nl + nv + e * beads + (j - 1);
-            const long long w = j == beads ? nl + b : nl + nv + e * beads + j;
+            const long long u = j == 0 ? nbil + a : nbil + nv + e * beads + (j - 1);
+            const long long w = j == beads ? nbil + b : nbil + nv + e * beads + j;
             if (bonds && nb < bcap) {
                 bonds[2 * nb] = (int)u;
                 bonds[2 * nb + 1] = (int)w;
@@ -244,8 +298,23 @@ int or_mesh_build(int nv, const double* verts, int nf, const int* faces, double 
             nb++;
         }
     }
+    /* anchors: glycophorin to its junction, band-3 to its chain's middle bead */
+    for (long long q = 0; q < ngly + nb3e; q++) {
+        const long long u = nl + q;
+        const long long pw = q < ngly ? q : nv + (q - ngly) * beads + (beads - 1) / 2;
+        double d[3];
+        or_sub3(prot + 3 * (ncyt + q), prot + 3 * pw, d);
+        if (bonds && nb < bcap) {
+            bonds[2 * nb] = (int)u;
+            bonds[2 * nb + 1] = (int)(nbil + pw);
+            r0[nb] = or_norm(d);
+            kbo[nb] = kb_anchor;
+        }
+        nb++;
+    }
     *n_out = n;
     *nb_out = nb;
+    free(pdir);
     free(nacc);
     free(junc);
     free(owner);

@@ -163,3 +163,119 @@ def test_quench_separates_an_overlapping_pair():
     r = np.linalg.norm(np.diff(s.state()["pos"], axis=0))
     assert abs(r - 2.0 ** (1.0 / 6.0)) < 1e-9 and e_prev == pytest.approx(-1.0, abs=1e-12) and fmax < 1e-8
     assert np.abs(s.state()["vel"]).max() == 0.0
+
+
+# --------------------------------------------------------------------------- bilayer proteins on the mesh
+
+def test_membrane_proteins_on_vertices_edges_and_faces():
+    """Glycophorin on every vertex (at the vertex, along the vertex normal),
+    immobile band-3 on every edge (at its midpoint), mobile band-3 among the
+    face samples; the bilayer first in id order, then junctions and
+    spectrin ("Initial structure generation")."""
+    R = 12.0
+    v, f = M.icosphere_mesh(3, R)
+    beads = 3
+    out = build(v, f, beads=beads, glycophorin=1, band3_edges=1, band3_fraction=0.25, seed=4)
+    typ, p, n = out["type"], out["pos"], out["ori"]
+    nv = len(v)
+    ne = nv + len(f) - 2                                            # Euler
+    cnt = np.bincount(typ, minlength=5)
+    assert cnt[4] == nv and cnt[1] == nv and cnt[2] == ne * beads
+    nb3_face = cnt[3] - ne
+    nface = cnt[0] + nb3_face
+    assert abs(nb3_face - 0.25 * nface) < 5 * math.sqrt(nface * 0.25 * 0.75)
+    nbil = cnt[0] + cnt[3] + cnt[4]
+    assert np.isin(typ[:nbil], (0, 3, 4)).all() and np.isin(typ[nbil:], (1, 2)).all()
+    gly = np.flatnonzero(typ == 4)
+    assert np.array_equal(p[gly], v)                                # exactly the vertices, in order
+    assert np.allclose(np.linalg.norm(n[gly], axis=1), 1.0)
+    assert (np.einsum("ij,ij->i", n[gly], p[gly]) > 0).all()        # outward
+    # the edges' band-3: one per mesh edge, at its midpoint
+    e3 = gly[-1] + 1 + np.arange(ne)
+    assert (typ[e3] == 3).all()
+    mid = {tuple(np.round((v[a] + v[b]) * 0.5, 12)) for a, b in
+           {tuple(sorted((int(f[t, i]), int(f[t, (i + 1) % 3])))) for t in range(len(f)) for i in range(3)}}
+    assert {tuple(np.round(x, 12)) for x in p[e3]} == mid
+    assert np.allclose(np.linalg.norm(n[e3], axis=1), 1.0)
+    assert (np.einsum("ij,ij->i", n[e3], p[e3]) > 0).all()
+
+
+def test_anchor_bonds_start_at_rest_and_join_the_right_partners():
+    """Each glycophorin is bonded to the junction `offset` beneath it, each
+    edge band-3 to the middle bead of its own edge's chain; every anchor's
+    rest length is its length at construction, with constant kb_anchor."""
+    R, off, beads = 12.0, 1.0, 3
+    v, f = M.icosphere_mesh(2, R)
+    out = build(v, f, beads=beads, offset=off, glycophorin=1, band3_edges=1, kb_anchor=37.0, d_min=0.0, d_ll=0.0)
+    typ, p = out["type"], out["pos"]
+    bonds, r0, kb = out["bonds"], out["r0"], out["kb"]
+    bil = np.isin(typ, (0, 3, 4))
+    anchor = bil[bonds[:, 0]] != bil[bonds[:, 1]]
+    nv = len(v)
+    ne = nv + len(f) - 2
+    assert anchor.sum() == nv + ne and (kb[anchor] == 37.0).all() and (kb[~anchor] == 100.0).all()
+    # the anchors follow the chains' bonds
+    assert not anchor[: (~anchor).sum()].any()
+    for (a, b), r in zip(bonds[anchor].tolist(), r0[anchor]):
+        assert r == pytest.approx(np.linalg.norm(p[a] - p[b]), rel=1e-15)
+        if typ[a] == 4:
+            assert typ[b] == 1
+            assert r == pytest.approx(off, rel=1e-12)               # the junction beneath the vertex
+        else:
+            assert typ[a] == 3 and typ[b] == 2
+            # beads = 3: the middle bead is the chain's centre, below the edge's midpoint
+            assert r == pytest.approx(off, abs=0.2)
+    # each edge band-3's bead is the middle one of the chain joining that
+    # edge's two junctions
+    nbil = int(bil.sum())
+    chain_adj = {}
+    for x, y in bonds[~anchor].tolist():
+        chain_adj.setdefault(x, []).append(y)
+        chain_adj.setdefault(y, []).append(x)
+    for (a, b) in bonds[anchor].tolist():
+        if typ[a] != 3:
+            continue
+        ends, steps = [], []
+        for first in chain_adj[b]:
+            prev, cur, k = b, first, 1
+            while typ[cur] == 2:
+                nxt = [q for q in chain_adj[cur] if q != prev]
+                prev, cur, k = cur, nxt[0], k + 1
+            ends.append(cur - nbil)                                  # junction id -> vertex index
+            steps.append(k)
+        assert steps == [2, 2]                                       # the middle of three beads
+        assert np.array_equal(p[a], (v[ends[0]] + v[ends[1]]) * 0.5)
+
+
+def test_face_band3_do_not_move_the_samples():
+    """The band-3 share only relabels face samples: positions and
+    directors are those of the lipid-only build, and the shares 0 and 1
+    give all lipids and all band-3."""
+    v, f = M.icosphere_mesh(3, 10.0)
+    a = build(v, f, beads=2, seed=9)
+    b = build(v, f, beads=2, seed=9, band3_fraction=0.4)
+    assert np.array_equal(a["pos"], b["pos"]) and np.array_equal(a["ori"], b["ori"])
+    face = a["type"] == 0
+    assert set(np.unique(b["type"][face]).tolist()) == {0, 3}
+    c = build(v, f, beads=2, seed=9, band3_fraction=1.0)
+    assert (c["type"][face] == 3).all()
+
+
+def test_minimum_distance_holds_against_the_surface_proteins():
+    v, f = M.icosphere_mesh(4, 12.0)
+    d_min = 0.9
+    out = build(v, f, beads=3, d_min=d_min, d_ll=0.3, glycophorin=1, band3_edges=1, band3_fraction=0.1, seed=2)
+    typ, p = out["type"], out["pos"]
+    nv = len(v)
+    ne = nv + len(f) - 2
+    nbil = int(np.isin(typ, (0, 3, 4)).sum())
+    face = np.arange(nbil - nv - ne)                                 # the kept face samples
+    prot = np.arange(nbil - nv - ne, len(typ))                       # every protein particle
+    d = np.linalg.norm(p[face][:, None, :] - p[prot][None, :, :], axis=2)
+    assert d.min() >= d_min
+
+
+def test_band3_on_edges_needs_beads():
+    v, f = M.icosphere_mesh(1, 10.0)
+    with pytest.raises(ValueError):
+        build(v, f, beads=0, band3_edges=1)
