@@ -90,9 +90,9 @@ PRECISION = {"f32": ("F32_FORCE_F64_STATE", "FP32 pair/bond forces; FP64 integra
                                                "fixed-point state")}
 
 
-def params_for(mem, precision: str, G):
+def params_for(mem, precision: str, G, **kw):
     return G.make_params(kT=mem.kT, n_centroids=mem.n_centroids, box=mem.box, periodic=mem.periodic,
-                         seed=2, precision=getattr(G, PRECISION[precision][0]))
+                         seed=2, precision=getattr(G, PRECISION[precision][0]), **kw)
 
 
 def oracle_params(mem, oracle):
@@ -373,10 +373,11 @@ def run_ours(args, rank, world):
             "rebuild_every": CADENCE_EVERY, "skin_sigma": CADENCE_SKIN, "dtype": "f32",
             "speedup_over_every_step": None}
         cadence["speedup_over_every_step"] = round((ms / args.steps) / cadence["ms_per_step"], 3)
-    volume = detached = None
+    volume = detached = proteins = None
     if args.precision == "f32" and not args.no_variants and args.workload == "rbc-4m":
         volume = volume_variant(mem, G, torch, stream, variant, args.steps, ms / args.steps)
         detached = detached_variant(G, torch, stream, args.steps)
+        proteins = protein_variant(G, torch, stream, args.steps, ms / args.steps)
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -431,9 +432,49 @@ def run_ours(args, rank, world):
             "roofline": roof, "kernel_ms_per_launch": breakdown, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks.summary(), "step_roofline": step_roof, "pair_roofline": pair_roof, "fp64_variant": f64,
             "f32_increment_variant": f32step, "skin_cadence_variant": cadence, "volume_variant": volume,
-            "detached_variant": detached,
+            "detached_variant": detached, "protein_variant": proteins,
             "ensemble": ens, "serve": serve}
     return line
+
+
+# Bilayer species table of the protein-set variant (lipid, band-3,
+# glycophorin; 0 = the lipid-lipid value).  The paper prints none of the
+# cited model's constants: these only exercise the species-pair path with
+# cutoffs wider than the lipids' (a wider search) and unequal well depths.
+PROTEIN_EPS = [[0.0, 1.2, 0.9], [1.2, 1.4, 1.1], [0.9, 1.1, 0.0]]
+PROTEIN_RC = [[0.0, 2.8, 0.0], [2.8, 2.9, 2.7], [0.0, 2.7, 0.0]]
+
+
+def protein_variant(G, torch, stream, steps, plain_ms):
+    """The 4M cell with the two-component model's full protein set (33,000
+    glycophorin bonded to the junctions, band-3 bonded to a quarter of the
+    spectrin beads, 5 % of the other lipids as mobile band-3) and the species
+    table above, every step rebuilt."""
+    import numpy as np
+    from synth import membranes as M
+    mem = M.rbc_4m_proteins()
+    cnt = np.bincount(mem.type, minlength=5)
+    p = params_for(mem, "f32", G, eps_mem=PROTEIN_EPS, rc_mem=PROTEIN_RC)
+    g = G.System(p, stream=stream.cuda_stream)
+    g.load_membrane(mem)
+    g.init_cells()
+    g.integrate(3)
+    g.set_timing(True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.integrate(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1)
+    kt = {k: round(v["ms"] / max(v["launches"], 1), 4) for k, v in g.kernel_times().items()}
+    g.close()
+    return {"workload": "rbc-4m with glycophorin, anchored and mobile band-3", "particles": mem.n,
+            "lipids": int(cnt[0]), "band3": int(cnt[3]), "glycophorin": int(cnt[4]),
+            "anchor_bonds": int(len(mem.bonds) - len(M.rbc_4m().bonds)),
+            "eps_mem": PROTEIN_EPS, "rc_mem": PROTEIN_RC, "dtype": "f32",
+            "value": round(mem.n * steps / (t * 1e-3), 1), "unit": UNIT, "ms_per_step": round(t / steps, 4),
+            "cost_over_lipid_only_ms_per_step": round(t / steps - plain_ms, 4), "kernel_ms_per_launch": kt}
 
 
 def detached_variant(G, torch, stream, steps):

@@ -69,9 +69,13 @@ typedef enum {
 } orbc_precision;
 
 /* Particle types of the two-component red-cell model ("Initial structure
- * generation"): lipids carry an orientation; junctions and spectrin beads
- * are point particles joined by bonds. */
-enum { ORBC_LIPID = 0, ORBC_JUNCTION = 1, ORBC_SPECTRIN = 2 };
+ * generation"): lipids carry an orientation; junctions (actin) and spectrin
+ * beads are point particles joined by bonds; band-3 and glycophorin are
+ * proteins of the bilayer and carry an orientation like the lipids.  A
+ * band-3 joined by a bond to the spectrin is immobile, one without a bond
+ * mobile; glycophorin is joined to the junctions.  Lipids, band-3 and
+ * glycophorin are the "bilayer" particles. */
+enum { ORBC_LIPID = 0, ORBC_JUNCTION = 1, ORBC_SPECTRIN = 2, ORBC_BAND3 = 3, ORBC_GLYCOPHORIN = 4 };
 
 /*
  * Model, integrator and cell-list parameters.  orbc_default_params() fills
@@ -83,15 +87,22 @@ enum { ORBC_LIPID = 0, ORBC_JUNCTION = 1, ORBC_SPECTRIN = 2 };
  *   a = (n_i x rh).(n_j x rh) + s0 (n_j - n_i).rh - s0^2, phi = 1 + mu (a - 1)
  *   U = eps[(rmin/r)^4 - 2 (rmin/r)^2] + (1 - phi) eps      r < rmin
  *   U = -eps cos^(2 zeta)((pi/2)(r - rmin)/(rc - rmin)) phi  rmin <= r < rc
- * with rmin = 2^(1/6) sigma.  Every pair that is not lipid-lipid is purely
- * repulsive WCA, 4 eps_wca [(s/r)^12 - (s/r)^6] + eps_wca for r < 2^(1/6) s,
- * with s = sigma_wca for lipid-protein pairs and s = sigma_wca_pp for
- * protein-protein pairs; protein pairs that are bonded or share a bond
- * partner (1-2, 1-3) are excluded from it ("Force Evaluation": protein
- * interactions use the lipid cells with a wider search cutoff).
+ * with rmin = 2^(1/6) sigma.  Two bilayer particles (lipid, band-3,
+ * glycophorin) interact through this potential with the well depth
+ * eps_mem[s_i][s_j] and cutoff rc_mem[s_i][s_j] of their species pair
+ * (s = 0 lipid, 1 band-3, 2 glycophorin; an entry of 0 takes eps or
+ * rc_lipid; the paper names the proteins but prints none of the cited
+ * model's constants, so the table is the caller's).  Every other pair is
+ * purely repulsive WCA, 4 eps_wca [(s/r)^12 - (s/r)^6] + eps_wca for
+ * r < 2^(1/6) s, with s = sigma_wca for bilayer-cytoskeleton pairs and
+ * s = sigma_wca_pp for pairs of cytoskeleton proteins; pairs that are bonded
+ * or share a bond partner (1-2, 1-3) are excluded from the WCA term (a
+ * spectrin chain's beads, an anchored protein and its anchor), never from
+ * the bilayer potential ("Force Evaluation": protein interactions use the
+ * lipid cells with a wider search cutoff).
  *
  * Integrator: BAOAB Langevin (translational for all particles, rotational
- * for lipids with Cayley rotations of the director), noise from
+ * for the bilayer's with Cayley rotations of the director), noise from
  * Philox4x32-10 keyed by (seed, instance; particle id, step, substream).
  */
 typedef struct {
@@ -115,6 +126,9 @@ typedef struct {
                                                    /* proteins (detached cytoskeleton)     */
     int eval_ctas;                                 /* pair evaluation CTAs per SM: 5 or 7, */
                                                    /* 0 = 7 (launch shape; results equal)  */
+    double eps_mem[3][3];                          /* bilayer species pairs: well depth,   */
+    double rc_mem[3][3];                           /* cutoff; symmetric, >= 0, 0 = eps or  */
+                                                   /* rc_lipid; [0][0] must be 0           */
 } orbc_params;
 
 typedef struct orbc_system orbc_system;   /* opaque; owns its device memory */
@@ -125,18 +139,24 @@ typedef struct orbc_system orbc_system;   /* opaque; owns its device memory */
  * gamma_t = gamma_r = 1, mass = inertia = 1, no periodic axis,
  * n_centroids = 64, n_lloyd_init = 10, rebuild_every = 1, skin = 0,
  * grid_h = 0, seed = 0, instance = 0, ORBC_F32_FORCE_F64_STATE,
- * n_protein_centroids = 0, eval_ctas = 0.
+ * n_protein_centroids = 0, eval_ctas = 0, eps_mem = rc_mem = 0 (every bilayer
+ * species pair as the lipid pair).  Errors of the table (orbc_create):
+ * ORBC_E_ARG for a negative, non-finite or asymmetric entry, a nonzero [0][0]
+ * entry, or a cutoff outside (2^(1/6) sigma, 64 sigma).
  *
  * Separate protein cells ("Force Evaluation": a cell whose cytoskeleton is
  * partly or fully detached from the bilayer gets a separate set of Voronoi
  * cells for its proteins): with n_protein_centroids = K_P > 0, cells
- * 0..K_L-1 (K_L = n_centroids) cluster the lipids and K_L..K_L+K_P-1 the
- * proteins; each particle belongs to the nearest centroid of its own set,
- * each centroid is the mean of its own members, each set is numbered along
- * its own Morton curve, and the neighbouring-cell rule runs over both sets
- * together, so the pair search finds every type pair.  The ids must then be
- * type-major (the lipids hold ids 0..N_L-1) and every bond joins two
- * proteins; the arena does not take such systems. */
+ * 0..K_L-1 (K_L = n_centroids) cluster the bilayer (lipids, band-3,
+ * glycophorin) and K_L..K_L+K_P-1 the cytoskeleton's proteins; each
+ * particle belongs to the nearest centroid of its own set, each centroid is
+ * the mean of its own members, each set is numbered along its own Morton
+ * curve, and the neighbouring-cell rule runs over both sets together, so the
+ * pair search finds every type pair.  The ids must then be type-major (the
+ * bilayer holds ids 0..N_L-1) and every bond joins two cytoskeleton proteins
+ * (a detached network has no anchors); the arena does not take such
+ * systems.  With shared cells (K_P = 0) the centroids are the means of the
+ * bilayer particles. */
 ORBC_API void orbc_default_params(orbc_params* p);
 
 /* Creates a handle.  cuda_stream is a cudaStream_t (NULL = the library's own
@@ -148,8 +168,8 @@ ORBC_API int orbc_create(const orbc_params* params, void* cuda_stream, orbc_syst
 
 /* Copies n particles from host memory ("Initial structure generation": the
  * system's particles with their types).  pos, vel: [n][3]; ori, angvel:
- * [n][3], read for lipids only (ori must be unit, angvel is projected
- * perpendicular to it); type: [n] (ORBC_LIPID/JUNCTION/SPECTRIN); id: [n],
+ * [n][3], read for bilayer particles only (ori must be unit, angvel is
+ * projected perpendicular to it); type: [n] (ORBC_LIPID .. ORBC_GLYCOPHORIN); id: [n],
  * a permutation of 0..n-1.  The arrays are validated and copied on the host;
  * the device set-up (allocation, upload, bond lists) runs at the first call
  * that needs the device, which then reports its errors (ORBC_E_NOMEM,
@@ -170,11 +190,12 @@ ORBC_API int orbc_set_particles(orbc_system* s, int n, const double* pos, const 
 ORBC_API int orbc_set_bonds(orbc_system* s, int nb, const int* ij, const double* r0, const double* kb);
 
 /* Initial k-means clustering ("Spatial Searching Algorithm"): centroids
- * [n_centroids][3] from host memory, or NULL to seed them from the lipids in
- * id order (centroid k = lipid floor(k N_L / K)); then n_lloyd_init rounds of
+ * [n_centroids][3] from host memory, or NULL to seed them from the bilayer
+ * particles in id order (centroid k = bilayer particle floor(k N_L / K));
+ * then n_lloyd_init rounds of
  * nearest-centroid assignment and centroid update; then the two-level
  * reorder (centroids along a Morton curve, particles stably by cell) and the
- * neighbouring-cell lists.  Errors: ORBC_E_ARG (more centroids than lipids),
+ * neighbouring-cell lists.  Errors: ORBC_E_ARG (more centroids than bilayer particles),
  * ORBC_E_STATE (no particles, or a cell with more than 64 neighbouring cells:
  * each cell's row is held at a fixed stride of 64, which a membrane with
  * about 60 particles per cell fills to about 8; a particle cloud in 3-D or a
@@ -309,10 +330,15 @@ typedef struct {
     int beads;                  /* spectrin particles per mesh edge (0 .. 64)                         */
     int pad0;
     unsigned long long seed;    /* Philox key of the face counts and samples                          */
+    double band3_fraction;      /* share of the face samples that are mobile band-3 (0 .. 1)          */
+    double kb_anchor;           /* anchor bond constant (glycophorin-junction, band-3-spectrin)       */
+    int glycophorin;            /* 1: a glycophorin on every vertex, bonded to its junction          */
+    int band3_edges;            /* 1: an immobile band-3 on every edge, bonded to its chain (beads>0) */
 } orbc_mesh_params;
 
 /* Fills mp with spacing 1.12, slack 1.03, kb 100, offset 1, d_min 0.8,
- * d_ll 0.2, beads 4, seed 0. */
+ * d_ll 0.2, beads 4, seed 0, band3_fraction 0, kb_anchor 50, glycophorin 0,
+ * band3_edges 0. */
 ORBC_API void orbc_default_mesh_params(orbc_mesh_params* mp);
 
 /* Builds the particles and bonds of a membrane on a triangular mesh, on the
@@ -326,16 +352,29 @@ ORBC_API void orbc_default_mesh_params(orbc_mesh_params* mp);
  * cross products); each undirected edge carries `beads` spectrin particles
  * evenly spaced between its junctions, chained by harmonic bonds.  A
  * candidate closer than d_min to a protein particle or closer than d_ll to
- * an earlier candidate is dropped.  Output (host, id order): the kept
- * lipids, then the junctions (vertex order), then the spectrin (edge order):
- * pos, ori [n][3] (ori zero for proteins), type [n]; bonds [nb][2] ids, r0,
+ * an earlier candidate is dropped.  The bilayer's proteins: with
+ * glycophorin = 1 a glycophorin sits on every vertex (director n_v), bonded
+ * to its junction; with band3_edges = 1 an immobile band-3 sits at the
+ * midpoint (a + b) / 2 of every edge (director the normalised sum of the two
+ * vertices' normal sums), bonded to the chain's bead floor((beads - 1) / 2);
+ * each anchor's rest length is its length at construction, its constant
+ * kb_anchor; candidate k of face f is a mobile band-3 instead of a lipid when
+ * word 2 at counter (f, k, 0, 3), as (w + 1/2) 2^-32, is below
+ * band3_fraction.  Glycophorin and edge band-3 count as protein particles
+ * for d_min.  Output (host, id order): the kept face samples (lipids and
+ * mobile band-3), the glycophorin (vertex order), the edge band-3 (edge
+ * order), then the junctions (vertex order), then the spectrin (edge
+ * order): pos, ori [n][3] (ori zero for the cytoskeleton), type [n]; bonds
+ * [nb][2] ids (the chains', then the anchors, glycophorin's first), r0,
  * kb [nb].  *n_out and *nb_out always receive the totals; the arrays are
  * written when cap >= n and bond_cap >= nb (pass 0 to query the sizes).
  * The result does not depend on the launch shape.  cuda_stream: as in
  * orbc_cell_sort; the call synchronises it and frees its scratch.
  * Errors: ORBC_E_ARG (null pointer, vertex index out of range, a degenerate
- * face, non-finite or |x| >= 4096 coordinates, invalid parameters, or a
- * nonzero capacity smaller than the totals), ORBC_E_NOMEM, ORBC_E_CUDA. */
+ * face, non-finite or |x| >= 4096 coordinates, invalid parameters (also
+ * band3_fraction outside [0, 1], a negative kb_anchor, band3_edges with no
+ * beads), or a nonzero capacity smaller than the totals), ORBC_E_NOMEM,
+ * ORBC_E_CUDA. */
 ORBC_API int orbc_mesh_build(const orbc_mesh_params* mp, int nv, const double* verts, int nf, const int* faces,
                              long long cap, double* pos, double* ori, unsigned char* type, long long* n_out,
                              long long bond_cap, int* bonds, double* r0, double* kb, long long* nb_out,
@@ -343,7 +382,7 @@ ORBC_API int orbc_mesh_build(const orbc_mesh_params* mp, int nv, const double* v
 
 /* Velocity quench of the handle's system (after orbc_init_cells): nsteps
  * steps of v += dt F/m, v replaced by its component along F (zero when it
- * points against F) and limited to |dt v| <= max_move, x += dt v; for lipids
+ * points against F) and limited to |dt v| <= max_move, x += dt v; for bilayer particles
  * the same with w, the torque's part normal to the director and max_turn,
  * the director turned by the Cayley map of dt w; cells rebuilt and forces
  * evaluated every step.  Velocities and angular velocities are zero at the
@@ -364,12 +403,13 @@ ORBC_API int orbc_set_step_fusion(orbc_system* s, int on);
 /* Harmonic volume constraint on the handle's membrane ("Validation and
  * Benchmark": the whole-cell run holds its surface-to-volume ratio by a
  * harmonic volume constraint; the paper states no functional form, so the
- * enclosed volume is taken from the lipids by the divergence theorem with
- * each lipid's director as its surface normal):
- *   V = sum over lipids of (a / 3) (x_i - c) . n_i,   U_V = k_V (V - V0)^2 / 2,
- * a = area_per_lipid (sigma^2), c = center (sigma, a fixed point inside the
- * membrane).  U_V acts as the uniform pressure P = -k_V (V - V0) on each
- * lipid's area element: the force P a n_i and no torque (moving one element
+ * enclosed volume is taken from the bilayer particles (lipids and membrane
+ * proteins) by the divergence theorem with each one's director as its
+ * surface normal):
+ *   V = sum over the bilayer of (a / 3) (x_i - c) . n_i,   U_V = k_V (V - V0)^2 / 2,
+ * a = area_per_lipid (sigma^2, the area per bilayer particle), c = center
+ * (sigma, a fixed point inside the membrane).  U_V acts as the uniform
+ * pressure P = -k_V (V - V0) on each area element: the force P a n_i and no torque (moving one element
  * by delta along its normal changes the enclosed volume by a delta; a
  * uniform pressure has no moment about the element).  U_V is added to the
  * bond energy (energies[1]) and nothing to the virial.  Each (x_i - c).n_i
@@ -391,7 +431,7 @@ ORBC_API int orbc_get_volume(orbc_system* s, double area_per_lipid, const double
 
 /* Height map of the membrane's upper rim for the fluctuation measurement
  * ("Validation and Benchmark": the instantaneous vertical fluctuation
- * dh(x, y) along the upper rim of a cell held in place): the lipids with
+ * dh(x, y) along the upper rim of a cell held in place): the bilayer particles with
  * z > z_min whose distance rho from the vertical axis through (axis[0],
  * axis[1]) lies in [rho_in, rho_out) are binned on the grid
  * x in [x0 + i dx, x0 + (i + 1) dx), y in [y0 + j dy, ...), i < nx, j < ny;

@@ -1,6 +1,7 @@
 """GB300-native hot path of OpenRBC's Voronoi-cell-list coarse-grained MD
 (arXiv 1701.02059): adaptive Voronoi cell list, orientation-dependent lipid
-pair forces, spectrin bonds and a BAOAB Langevin integrator, all in CUDA
+pair forces for the bilayer's lipids and proteins (band-3, glycophorin),
+spectrin and anchor bonds and a BAOAB Langevin integrator, all in CUDA
 kernels for sm_103a behind the C ABI of include/orbc.h.
 
 ``System`` is a thin wrapper over that ABI (host numpy arrays in, host numpy
@@ -14,10 +15,11 @@ import ctypes as C
 import numpy as np
 
 from . import _native
-from ._native import F32_FORCE_F32_STEP, F32_FORCE_F64_STATE, F64_ALL, OrbcError, Params, default_params, load
+from ._native import (BAND3, F32_FORCE_F32_STEP, F32_FORCE_F64_STATE, F64_ALL, GLYCOPHORIN, JUNCTION, LIPID, SPECTRIN,
+                      OrbcError, Params, default_params, load)
 
 __all__ = ["System", "Arena", "autotune", "Params", "default_params", "load", "OrbcError", "F32_FORCE_F64_STATE", "F64_ALL",
-           "F32_FORCE_F32_STEP"]
+           "F32_FORCE_F32_STEP", "LIPID", "JUNCTION", "SPECTRIN", "BAND3", "GLYCOPHORIN"]
 
 
 def _p(a):
@@ -25,12 +27,19 @@ def _p(a):
 
 
 def make_params(**kw) -> Params:
-    """orbc_params with the library defaults, overridden by keyword."""
+    """orbc_params with the library defaults, overridden by keyword
+    (eps_mem, rc_mem: 3 x 3 tables over the bilayer species lipid, band-3,
+    glycophorin)."""
     p = default_params()
     for k, v in kw.items():
         if k in ("box", "periodic"):
             for a in range(3):
                 getattr(p, k)[a] = v[a]
+        elif k in ("eps_mem", "rc_mem"):
+            t = np.asarray(v, np.float64).reshape(3, 3)
+            for a in range(3):
+                for b in range(3):
+                    getattr(p, k)[a][b] = float(t[a, b])
         else:
             setattr(p, k, v)
     return p

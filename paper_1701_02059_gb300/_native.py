@@ -12,6 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liborbc.so")
 
 ORBC_OK, ORBC_E_ARG, ORBC_E_NOMEM, ORBC_E_CUDA, ORBC_E_STATE, ORBC_E_NAN, ORBC_E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
+# particle types (orbc.h): lipid, junction (actin), spectrin bead, band-3, glycophorin
+LIPID, JUNCTION, SPECTRIN, BAND3, GLYCOPHORIN = 0, 1, 2, 3, 4
 F32_FORCE_F64_STATE, F64_ALL, F32_FORCE_F32_STEP = 0, 1, 2
 STATUS_NAMES = {0: "ORBC_OK", -1: "ORBC_E_ARG", -2: "ORBC_E_NOMEM", -3: "ORBC_E_CUDA", -4: "ORBC_E_STATE",
                 -5: "ORBC_E_NAN", -6: "ORBC_E_TIMEOUT"}
@@ -41,14 +43,16 @@ class Params(C.Structure):
                 ("box", C.c_double * 3), ("periodic", C.c_int * 3),
                 ("n_centroids", C.c_int), ("n_lloyd_init", C.c_int), ("rebuild_every", C.c_int),
                 ("skin", C.c_double), ("grid_h", C.c_double), ("seed", C.c_ulonglong), ("instance", C.c_uint),
-                ("precision", C.c_int), ("n_protein_centroids", C.c_int), ("eval_ctas", C.c_int)]
+                ("precision", C.c_int), ("n_protein_centroids", C.c_int), ("eval_ctas", C.c_int),
+                ("eps_mem", (C.c_double * 3) * 3), ("rc_mem", (C.c_double * 3) * 3)]
 
 
 class MeshParams(C.Structure):
     """Mirror of orbc_mesh_params."""
     _fields_ = [("spacing", C.c_double), ("slack", C.c_double), ("kb", C.c_double), ("offset", C.c_double),
                 ("d_min", C.c_double), ("d_ll", C.c_double), ("beads", C.c_int), ("pad0", C.c_int),
-                ("seed", C.c_ulonglong)]
+                ("seed", C.c_ulonglong), ("band3_fraction", C.c_double), ("kb_anchor", C.c_double),
+                ("glycophorin", C.c_int), ("band3_edges", C.c_int)]
 
 
 class OrbcError(RuntimeError):

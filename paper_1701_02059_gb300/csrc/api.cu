@@ -210,6 +210,26 @@ static Inst make_inst(const Params& P) {
     I.seed = P.seed; I.instance = P.instance;
     I.rebuild_every = P.rebuild_every;
     I.n_lloyd = P.n_lloyd_init;
+    // bilayer species pairs: the lipid-lipid entry and every entry left at 0
+    // take eps and rc_lipid, so their constants equal the lipid pair's
+    for (int q = 0; q < 9; q++) {
+        const double e = (q > 0 && P.eps_mem[q] > 0) ? P.eps_mem[q] : P.eps;
+        const double rc = (q > 0 && P.rc_mem[q] > 0) ? P.rc_mem[q] : P.rc_lipid;
+        const double w = 1.5707963267948966 / (rc - two_sixth * P.sigma);
+        I.mm_eps_d[q] = e;
+        I.mm_rc_d[q] = rc;
+        I.mm_rc2[q] = rc * rc;
+        I.mm_eps[q] = (float)e;
+        I.mm_aw[q] = (float)w;
+        I.mm_e2za[q] = (float)(e * 2.0 * P.zeta * w);
+        const float rcf = std::sqrt((float)I.mm_rc2[q]);
+        I.mm_lo[q] = (rcf - kCutBand) * (rcf - kCutBand);
+        I.mm_hi[q] = (rcf + kCutBand) * (rcf + kCutBand);
+        I.rs = std::max(I.rs, rc);
+    }
+    I.rsf = (float)I.rs;
+    for (int a = 0; a < 3; a++)
+        I.mm_rcf[a] = std::sqrt(std::max((float)I.mm_rc2[3 * a], std::max((float)I.mm_rc2[3 * a + 1], (float)I.mm_rc2[3 * a + 2])));
     return I;
 }
 
@@ -397,8 +417,16 @@ void Ensemble::setup(const std::vector<const HostInstance*>& list) {
         inst_h[b].partner = h.partner;
         inst_h[b].id_base = h.id_base;
         inst_h[b].all_members = h.all_members;
-        // centroid members: the lipids, or every particle of a protein cell set
-        inst_h[b].nlip = h.all_members ? h.n : (int)std::count(h.type.begin(), h.type.end(), (unsigned char)kLipid);
+        // centroid members: the bilayer particles, or every particle of a
+        // protein cell set
+        inst_h[b].nlip = h.all_members ? h.n : (int)std::count_if(h.type.begin(), h.type.end(), bilayer);
+        inst_h[b].has_mp = std::any_of(h.type.begin(), h.type.end(), [](unsigned char t) { return t >= kBand3; });
+        if (!h.r0.empty()) {
+            std::vector<unsigned char> bil((size_t)h.n);
+            for (int i = 0; i < h.n; i++) bil[h.id[i]] = bilayer(h.type[i]);
+            for (size_t q = 0; q < h.r0.size() && !inst_h[b].bonded_bilayer; q++)
+                inst_h[b].bonded_bilayer = bil[(size_t)h.bonds[2 * q]] || bil[(size_t)h.bonds[2 * q + 1]];
+        }
         inst_h[b].vol_on = h.vol_kv > 0.0;
         inst_h[b].kv = h.vol_kv;
         inst_h[b].v0 = h.vol_v0;
@@ -483,7 +511,7 @@ void Ensemble::setup(const std::vector<const HostInstance*>& list) {
             parallel_for(nch, [&](long long c0, long long c1) {
                 for (long long ch = c0; ch < c1; ch++)
                     for (long long idv = ch * per; idv < std::min<long long>(h.n, (ch + 1) * per); idv++)
-                        cnt[ch + 1] += h.all_members || h.type[by_id[idv]] == kLipid;
+                        cnt[ch + 1] += h.all_members || bilayer(h.type[by_id[idv]]);
             }, 1);
             for (int ch = 0; ch < nch; ch++) cnt[ch + 1] += cnt[ch];
             std::vector<int> lip((size_t)cnt[nch]);
@@ -491,7 +519,7 @@ void Ensemble::setup(const std::vector<const HostInstance*>& list) {
                 for (long long ch = c0; ch < c1; ch++) {
                     long long o = cnt[ch];
                     for (long long idv = ch * per; idv < std::min<long long>(h.n, (ch + 1) * per); idv++)
-                        if (h.all_members || h.type[by_id[idv]] == kLipid) lip[(size_t)o++] = by_id[idv];
+                        if (h.all_members || bilayer(h.type[by_id[idv]])) lip[(size_t)o++] = by_id[idv];
                 }
             }, 1);
             if ((int)lip.size() < K)
@@ -605,7 +633,9 @@ void Ensemble::integrate(int nsteps) {
     if (!forces_valid) launch_pairs(false, false);
     // with FP32 forces, each step's force launch also runs the next step's
     // B-A-O-A (the last step's forces are evaluated alone, before the final B)
-    const bool fuse = fuse_steps && !force_f64();
+    // (the fused evaluation has no instantiation for bilayer species pairs
+    // or bonded bilayer particles)
+    const bool fuse = fuse_steps && !force_f64() && !any_mp();
     for (int s = 0; s < nsteps; s++) {
         step_body(s > 0, fuse && s > 0, fuse && s + 1 < nsteps);
         for (auto& x : step_h) x++;
@@ -873,11 +903,11 @@ static void pull_state(orbc_system* s);
 // N_L.  Type-major ids keep every particle's id.
 static void split_sets(const HostInstance& h, HostInstance& L, HostInstance& P) {
     const int n = h.n;
-    const int nl = (int)std::count(h.type.begin(), h.type.end(), (unsigned char)kLipid);
+    const int nl = (int)std::count_if(h.type.begin(), h.type.end(), bilayer);
     for (int i = 0; i < n; i++)
-        if ((h.type[i] == kLipid) != ((int)h.id[i] < nl))
-            throw ArgError("separate protein cells need type-major ids (the lipids hold ids 0..N_L-1)");
-    if (nl < 1 || nl == n) throw ArgError("separate protein cells need lipids and proteins");
+        if (bilayer(h.type[i]) != ((int)h.id[i] < nl))
+            throw ArgError("separate protein cells need type-major ids (the bilayer holds ids 0..N_L-1)");
+    if (nl < 1 || nl == n) throw ArgError("separate protein cells need a bilayer and cytoskeleton proteins");
     L = HostInstance();
     P = HostInstance();
     L.prm = h.prm;
@@ -895,7 +925,7 @@ static void split_sets(const HostInstance& h, HostInstance& L, HostInstance& P) 
     }
     int o[2] = {0, 0};
     for (int i = 0; i < n; i++) {
-        const int w = h.type[i] == kLipid ? 0 : 1;
+        const int w = bilayer(h.type[i]) ? 0 : 1;
         HostInstance& t = *to[w];
         for (int a = 0; a < 3; a++) {
             t.xq[(size_t)3 * o[w] + a] = h.xq[(size_t)3 * i + a];
@@ -909,7 +939,8 @@ static void split_sets(const HostInstance& h, HostInstance& L, HostInstance& P) 
     }
     for (size_t q = 0; q < h.r0.size(); q++) {
         const int a = h.bonds[2 * q], b = h.bonds[2 * q + 1];
-        if (a < nl || b < nl) throw ArgError("with separate protein cells every bond joins two proteins");
+        if (a < nl || b < nl)
+            throw ArgError("with separate protein cells every bond joins two cytoskeleton proteins (no anchors)");
         P.bonds.push_back(a - nl);
         P.bonds.push_back(b - nl);
         P.r0.push_back(h.r0[q]);
@@ -1000,6 +1031,8 @@ Params orbc::to_params(const orbc_params* p) {
     P.precision = (int)p->precision;
     P.n_protein_centroids = p->n_protein_centroids;
     P.eval_ctas = p->eval_ctas == 0 ? 7 : p->eval_ctas;
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) { P.eps_mem[3 * a + b] = p->eps_mem[a][b]; P.rc_mem[3 * a + b] = p->rc_mem[a][b]; }
     return P;
 }
 
@@ -1022,6 +1055,18 @@ void orbc::check_params(const Params& P) {
     if (P.precision < 0 || P.precision > 2) throw ArgError("unknown precision");
     if (P.n_protein_centroids < 0) throw ArgError("n_protein_centroids must be >= 0");
     if (P.eval_ctas != 5 && P.eval_ctas != 7) throw ArgError("eval_ctas must be 0, 5 or 7");
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            const double e = P.eps_mem[3 * a + b], rc = P.rc_mem[3 * a + b];
+            if (!(fin(e) && e >= 0 && fin(rc) && rc >= 0))
+                throw ArgError("bilayer species table: entries must be finite and >= 0");
+            if (e != P.eps_mem[3 * b + a] || rc != P.rc_mem[3 * b + a])
+                throw ArgError("bilayer species table must be symmetric");
+            if (rc > 0 && !(rc > 1.122462048309373 * P.sigma && rc < 64.0))
+                throw ArgError("bilayer species cutoff must lie in (2^(1/6) sigma, 64 sigma)");
+        }
+    if (P.eps_mem[0] != 0 || P.rc_mem[0] != 0)
+        throw ArgError("the lipid-lipid entry of the species table is eps and rc_lipid (leave it 0)");
 }
 
 
@@ -1066,7 +1111,7 @@ HostInstance orbc::host_instance(const Params& prm, int n, const double* pos, co
         for (long long i = i0; i < i1; i++) {
             if (id[i] >= (unsigned)n || seen[id[i]].exchange(1, std::memory_order_relaxed))
                 throw ArgError("ids must be a permutation of 0..n-1");
-            if (type[i] > 2) throw ArgError("unknown particle type");
+            if (type[i] > kMaxType) throw ArgError("unknown particle type");
         }
     });
     parallel_for(n, [&](long long i0, long long i1) {
@@ -1079,7 +1124,7 @@ HostInstance orbc::host_instance(const Params& prm, int n, const double* pos, co
                 h.xq[(size_t)3 * i + a] = llrint(x * kGrid);
                 h.vq[(size_t)3 * i + a] = llrint(v * kGrid);
             }
-            if (type[i] == kLipid) {
+            if (bilayer(type[i])) {
                 double o[3], w[3];
                 for (int a = 0; a < 3; a++) { o[a] = ori[3 * i + a]; w[a] = angvel[3 * i + a]; }
                 for (int a = 0; a < 3; a++)
@@ -1347,6 +1392,7 @@ void orbc_default_mesh_params(orbc_mesh_params* mp) {
     std::memset(mp, 0, sizeof(*mp));
     mp->spacing = 1.12; mp->slack = 1.03; mp->kb = 100.0; mp->offset = 1.0; mp->d_min = 0.8; mp->d_ll = 0.2;
     mp->beads = 4; mp->seed = 0;
+    mp->band3_fraction = 0.0; mp->kb_anchor = 50.0; mp->glycophorin = 0; mp->band3_edges = 0;
 }
 
 int orbc_quench(orbc_system* s, int nsteps, double dt, double max_move, double max_turn, double* fmax_out) {

@@ -1100,7 +1100,7 @@ __global__ void __launch_bounds__(256) k_gather_particles(View v, View o, const 
     m.x = mirror_coord(x[0], v.cq[k], I, 0, v);
     m.y = mirror_coord(x[1], v.cq[(size_t)v.Ktot + k], I, 1, v);
     m.z = mirror_coord(x[2], v.cq[(size_t)2 * v.Ktot + k], I, 2, v);
-    m.w = t;
+    m.w = t | (v.bptr[I.p0 + id] < v.bptr[I.p0 + id + 1] ? kMirrorBonded : 0);
     v.mq[p] = m;
     float4 no;
     no.x = ll_to_float(nq[0]) * (float)kGridInv;
@@ -1164,7 +1164,7 @@ __global__ void __launch_bounds__(256, 6) k_cell_props(View v, unsigned long lon
         const float4 no = v.mo[p];
         const float dx = m.x * kMirrorUnit, dy = m.y * kMirrorUnit, dz = m.z * kMirrorUnit;
         mx = fmaxf(mx, sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))));
-        if ((m.w & 0xff) == kLipid) { nx += no.x; ny += no.y; nz += no.z; }
+        if (bilayer(m.w & 0xff)) { nx += no.x; ny += no.y; nz += no.z; }
     }
     for (int off = 16; off; off >>= 1) {
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
@@ -1263,7 +1263,8 @@ __global__ void k_mirrors(View v) {
     m.x = mirror_coord(v.xq[p], v.cq[c], I, 0, v);
     m.y = mirror_coord(v.xq[N + p], v.cq[(size_t)v.Ktot + c], I, 1, v);
     m.z = mirror_coord(v.xq[2 * N + p], v.cq[(size_t)2 * v.Ktot + c], I, 2, v);
-    m.w = v.type[p];
+    const unsigned id = v.id[p];
+    m.w = v.type[p] | (v.bptr[I.p0 + id] < v.bptr[I.p0 + id + 1] ? kMirrorBonded : 0);
     float4 no;
     no.x = ll_to_float(v.nq[p]) * (float)kGridInv;
     no.y = ll_to_float(v.nq[N + p]) * (float)kGridInv;

@@ -46,6 +46,9 @@ struct Params {
     int precision = 0;   // 0 = FP32 forces, FP64 increments; 1 = FP64 everywhere; 2 = FP32 forces and increments
     int n_protein_centroids = 0;   // > 0: the proteins get a cell set of their own
     int eval_ctas = 7;             // pair evaluation launched for 5 or 7 CTAs per SM
+    // bilayer species pairs [3 s_i + s_j] (lipid, band-3, glycophorin): the
+    // lipid potential's well depth and cutoff, 0 = the lipid-lipid value
+    double eps_mem[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, rc_mem[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 // One instance as given by the caller (host memory, id order not required).
@@ -195,6 +198,14 @@ public:
     // FP32 (ORBC_F32_FORCE_F32_STEP)
     bool force_f64() const { return precision == 1; }
     bool step_f32() const { return precision == 2; }
+    // the pair evaluation with bilayer species pairs and exclusions of
+    // bilayer-cytoskeleton pairs: some instance holds band-3 or glycophorin,
+    // or a bilayer particle with a bond
+    bool any_mp() const {
+        for (const Inst& I : inst_h)
+            if (I.has_mp || I.bonded_bilayer) return true;
+        return false;
+    }
 
     View view();
     View view_alt();

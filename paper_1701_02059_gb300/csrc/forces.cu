@@ -35,13 +35,12 @@ constexpr int kStageCap = 624;     // staged particles per pass
 constexpr int kQCap = 32;          // queued hits per lane before a flush
 constexpr int kMaxNbr = 32;        // neighbouring cells per pass (one per lane of the set-up warp)
 constexpr float kFilterBand = 1e-4f;
-constexpr float kCutBand = 1e-6f;
 
 // ---------------------------------------------------------------- pair terms
 // Lipid pair (see the header of orbc.h for the potential).  d = x_j - x_i.
 // Returns U; adds force on i and torque on i.
-template <typename T>
-__device__ inline T lipid_terms(const Inst& I, T dx, T dy, T dz, T r2, T nix, T niy, T niz, T njx, T njy, T njz,
+template <typename T, typename IC>
+__device__ inline T lipid_terms(const IC& I, T dx, T dy, T dz, T r2, T nix, T niy, T niz, T njx, T njy, T njz,
                                 T& fx, T& fy, T& fz, T& tx, T& ty, T& tz, T* tj);
 
 __device__ inline float taylor_cos(float x) {
@@ -149,10 +148,10 @@ __device__ inline float lipid_terms_f(const IC& I, float dx, float dy, float dz,
     return U;
 }
 
-template <>
-__device__ inline double lipid_terms<double>(const Inst& I, double dx, double dy, double dz, double r2, double nix,
-                                             double niy, double niz, double njx, double njy, double njz, double& fx,
-                                             double& fy, double& fz, double& tx, double& ty, double& tz, double* tj) {
+template <typename T, typename IC>
+__device__ inline T lipid_terms(const IC& I, T dx, T dy, T dz, T r2, T nix, T niy, T niz, T njx, T njy, T njz,
+                                T& fx, T& fy, T& fz, T& tx, T& ty, T& tz, T* tj) {
+    static_assert(sizeof(T) == 8, "the FP32 terms are lipid_terms_f");
     double r = sqrt(r2);
     double hx = -dx / r, hy = -dy / r, hz = -dz / r;
     double s0 = I.s0_d;
@@ -265,16 +264,40 @@ template <> struct Acc<double> {
     __device__ long long Tq(int a) const { return t[a]; }
 };
 
-// exact FP64 inclusion decision for a pair inside the cutoff band
-__device__ inline bool exact_inside(const View& v, const Inst& I, int pi, int pj, int cls) {
+// exact FP64 inclusion decision for a pair inside the cutoff band; m: the
+// bilayer species pair (cls 0)
+__device__ inline bool exact_inside(const View& v, const Inst& I, int pi, int pj, int cls, int m = 0) {
     size_t N = v.N;
     double d2 = dist2_grid_d(v.xq[pj], v.xq[N + pj], v.xq[2 * N + pj], v.xq[pi], v.xq[N + pi], v.xq[2 * N + pi], I);
-    return d2 < (cls == 0 ? I.rc2_ll : (cls == 1 ? I.rc2_wca : I.rc2_pp));
+    return d2 < (cls == 0 ? I.mm_rc2[m] : (cls == 1 ? I.rc2_wca : I.rc2_pp));
 }
 
+// Pair class of two types: 0 two bilayer particles (the lipid potential), 1
+// a bilayer particle and a cytoskeleton protein, 2 two cytoskeleton proteins
+// (both WCA); m: the bilayer species pair 3 s_i + s_j of class 0.
+__device__ inline int pair_class(int ti, int tj, int& m) {
+    const bool bi = bilayer(ti), bj = bilayer(tj);
+    m = (bi && bj) ? 3 * species(ti) + species(tj) : 0;
+    return (bi && bj) ? 0 : ((bi || bj) ? 1 : 2);
+}
+
+// The lipid potential's constants of one bilayer species pair, in the field
+// names of Inst (FP32 and FP64), for the pair-term functions.
+struct LipK {
+    float eps, rmin, mu, s0, aw, eps2z_aw;
+    int zeta;
+    double eps_d, rmin_d, rc_d, mu_d, s0_d;
+    __device__ LipK(const Inst& I, int m)
+        : eps(I.mm_eps[m]), rmin(I.rmin), mu(I.mu), s0(I.s0), aw(I.mm_aw[m]), eps2z_aw(I.mm_e2za[m]), zeta(I.zeta),
+          eps_d(I.mm_eps_d[m]), rmin_d(I.rmin_d), rc_d(I.mm_rc_d[m]), mu_d(I.mu_d), s0_d(I.s0_d) {}
+};
+
 // 1-2 and 1-3 bonded pairs carry no excluded-volume term (bonded directly,
-// or sharing a bond partner).
-__device__ inline bool is_excluded(const View& v, const Inst& I, unsigned idi, unsigned idj) {
+// or sharing a bond partner).  Ids are local to i's instance I; slot pj
+// outside I (the partner cell set of a membrane, which no bond reaches) is
+// never excluded.
+__device__ inline bool is_excluded(const View& v, const Inst& I, unsigned idi, unsigned idj, int pj) {
+    if ((unsigned)(pj - I.p0) >= (unsigned)I.n) return false;
     const int s = v.bptr[I.p0 + idi], e = v.bptr[I.p0 + idi + 1];
     const int s2 = v.bptr[I.p0 + idj], e2 = v.bptr[I.p0 + idj + 1];
     for (int q = s; q < e; q++) {
@@ -332,15 +355,15 @@ struct NbrInfo {
     int ox, oy, oz; // exact offset c_l - c_k at 2^-26 sigma (wrap-around int32)
 };
 
-template <typename T, bool S0>
-__device__ inline T lipid_dispatch(const Inst& I, T dx, T dy, T dz, T r2, T nix, T niy, T niz, T njx, T njy, T njz,
+template <typename T, bool S0, typename IC = Inst>
+__device__ inline T lipid_dispatch(const IC& I, T dx, T dy, T dz, T r2, T nix, T niy, T niz, T njx, T njy, T njz,
                                    T& fx, T& fy, T& fz, T& tx, T& ty, T& tz, int zc, T* tj) {
     if constexpr (sizeof(T) == 4) {
         if (zc == 4)
-            return lipid_terms_f<4, S0>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz, tj);
-        return lipid_terms_f<0>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz, tj);
+            return lipid_terms_f<4, S0, IC>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz, tj);
+        return lipid_terms_f<0, true, IC>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz, tj);
     } else {
-        return lipid_terms<double>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz, tj);
+        return lipid_terms<double, IC>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz, tj);
     }
 }
 
@@ -586,20 +609,21 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                         const float4 oj = so[j];
                         const int pj = __float_as_int(oj.w);
                         const int tj = mj.w & 0xff;
-                        const bool ll = (ti == kLipid) && (tj == kLipid);
-                        const int cls = ll ? 0 : ((ti == kLipid || tj == kLipid) ? 1 : 2);
+                        int m;
+                        const int cls = pair_class(ti, tj, m);
+                        const bool ll = cls == 0;
                         const int dxq = (int)((unsigned)mj.x - (unsigned)qi.x);
                         const int dyq = (int)((unsigned)mj.y - (unsigned)qi.y);
                         const int dzq = (int)((unsigned)mj.z - (unsigned)qi.z);
                         const float dxf = (float)dxq * kMirrorUnit, dyf = (float)dyq * kMirrorUnit,
                                     dzf = (float)dzq * kMirrorUnit;
                         const float r2f = fmaf(dxf, dxf, fmaf(dyf, dyf, dzf * dzf));
-                        const float lo = cls == 0 ? ll_lo : (cls == 1 ? w_lo : p_lo);
-                        const float hi = cls == 0 ? ll_hi : (cls == 1 ? w_hi : p_hi);
+                        const float lo = cls == 0 ? (I.has_mp ? I.mm_lo[m] : ll_lo) : (cls == 1 ? w_lo : p_lo);
+                        const float hi = cls == 0 ? (I.has_mp ? I.mm_hi[m] : ll_hi) : (cls == 1 ? w_hi : p_hi);
                         if (r2f >= hi) continue;
                         bool in = r2f < lo;
-                        if (!in) in = exact_inside(v, I, pi, pj, cls);
-                        if (in && cls == 2 && is_excluded(v, I, v.id[pi], v.id[pj])) in = false;
+                        if (!in) in = exact_inside(v, I, pi, pj, cls, m);
+                        if (in && cls != 0 && is_excluded(v, I, v.id[pi], v.id[pj], pj)) in = false;
                         if (!in) continue;
                         T fx = 0, fy = 0, fz = 0, tx = 0, ty = 0, tz = 0, U;
                         T dx, dy, dz, r2;
@@ -621,8 +645,12 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_pairs(View v, long long* __
                                 njx = grid_to_double(v.nq[pj]); njy = grid_to_double(v.nq[N + pj]);
                                 njz = grid_to_double(v.nq[2 * N + pj]);
                             }
-                            U = lipid_dispatch<T, S0>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx, ty, tz, zc,
-                                                  (T*)nullptr);
+                            if (I.has_mp)
+                                U = lipid_dispatch<T, S0, LipK>(LipK(I, m), dx, dy, dz, r2, nix, niy, niz, njx, njy, njz,
+                                                                fx, fy, fz, tx, ty, tz, zc, (T*)nullptr);
+                            else
+                                U = lipid_dispatch<T, S0>(I, dx, dy, dz, r2, nix, niy, niz, njx, njy, njz, fx, fy, fz, tx,
+                                                          ty, tz, zc, (T*)nullptr);
                         } else {
                             U = wca_terms<T>(I, cls == 2, dx, dy, dz, r2, fx, fy, fz);
                         }
@@ -772,7 +800,7 @@ __global__ void __launch_bounds__(kPairThreads, 8)
     k_pair_search(View v, int* __restrict__ nlist, int* __restrict__ ncnt, int cap, int2* __restrict__ ovf,
                   int* __restrict__ novf, int ovf_cap, int4* __restrict__ rowoff) {
     // sY: staged mirrors (int4 by the bulk copy), then in the tangent frame
-    //     (FP32), w = 0 for a lipid and 1 for a protein
+    //     (FP32), w = 0 for a bilayer particle and 1 for a cytoskeleton protein
     // sQ: the list entry of each staged particle
     __shared__ alignas(16) float4 sY[kSearchStage];
     __shared__ int sQ[kSearchStage];
@@ -792,7 +820,7 @@ __global__ void __launch_bounds__(kPairThreads, 8)
     const size_t N = v.N;
     const float sk = 2.0f * (float)I.skin + kFilterBand;
     const float rsb = I.rsf + sk, rs2f = rsb * rsb;
-    const float cl = sqrtf(I.rc2f_ll) + sk, cw = sqrtf(I.rc2f_wca) + sk, cp = sqrtf(I.rc2f_pp) + sk;
+    const float cw = sqrtf(I.rc2f_wca) + sk, cp = sqrtf(I.rc2f_pp) + sk;
     unsigned phase = 0;
     if (tid == 0) mbar_init(&bar, 1);
     __syncthreads();
@@ -891,13 +919,17 @@ __global__ void __launch_bounds__(kPairThreads, 8)
             ti = qi.w & 0xff;
             F.apply(qi.x * kMirrorUnit, qi.y * kMirrorUnit, qi.z * kMirrorUnit, yix, yiy, yiz);
         }
-        // squared search radius for a lipid and for a protein partner
-        const float cutL = ti == kLipid ? cl * cl : cw * cw;
-        const float cutP = ti == kLipid ? cw * cw : cp * cp;
+        // squared search radius for a bilayer and for a cytoskeleton partner
+        // (for a bilayer particle the widest cutoff of its species)
+        const bool bi = bilayer(ti);
+        const float cl = I.mm_rcf[species(ti)] + sk;
+        const float cutL = bi ? cl * cl : cw * cw;
+        const float cutP = bi ? cw * cw : cp * cp;
         const float cutD = cutP - cutL;
         // the group box's cull radius: the search cutoff, or for a group
-        // without lipids (a protein cell) the larger of its two cutoffs
-        const bool glip = __any_sync(0xffffffffu, ivalid && ti == kLipid);
+        // without bilayer particles (a protein cell) the larger of its two
+        // cutoffs
+        const bool glip = __any_sync(0xffffffffu, ivalid && bi);
         const float rcull2 = glip ? rs2f : fmaxf(cw, cp) * fmaxf(cw, cp);
         float blo[3] = {ivalid ? yix : 3.0e38f, ivalid ? yiy : 3.0e38f, ivalid ? yiz : 3.0e38f};
         float bhi[3] = {ivalid ? yix : -3.0e38f, ivalid ? yiy : -3.0e38f, ivalid ? yiz : -3.0e38f};
@@ -940,7 +972,7 @@ __global__ void __launch_bounds__(kPairThreads, 8)
                     const int z = (int)((unsigned)rj.z + (unsigned)inf.oz);
                     float4 w;
                     F.apply(x * kMirrorUnit, y * kMirrorUnit, z * kMirrorUnit, w.x, w.y, w.z);
-                    w.w = ((rj.w & 0xff) == kLipid) ? 0.0f : 1.0f;
+                    w.w = bilayer(rj.w & 0xff) ? 0.0f : 1.0f;
                     sY[j] = w;
                     sQ[j] = (inf.row << kRowShift) | (inf.start + (j - inf.base));
                 }
@@ -1020,21 +1052,25 @@ __device__ inline bool listed_pair(const View& v, const Inst& I, int zc, int pi,
                                    float p_hi, float& fx, float& fy, float& fz, float& tx, float& ty, float& tz) {
     const int pj = __float_as_int(oj.w);
     const int tj = mj.w & 0xff;
-    const bool ll = (ti == kLipid) && (tj == kLipid);
-    const int cls = ll ? 0 : ((ti == kLipid || tj == kLipid) ? 1 : 2);
+    int m;
+    const int cls = pair_class(ti, tj, m);
+    const bool ll = cls == 0;
     const int dxq = (int)((unsigned)mj.x + (unsigned)o.x - (unsigned)qi.x);
     const int dyq = (int)((unsigned)mj.y + (unsigned)o.y - (unsigned)qi.y);
     const int dzq = (int)((unsigned)mj.z + (unsigned)o.z - (unsigned)qi.z);
     const float dx = (float)dxq * kMirrorUnit, dy = (float)dyq * kMirrorUnit, dz = (float)dzq * kMirrorUnit;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float lo = cls == 0 ? ll_lo : (cls == 1 ? w_lo : p_lo);
-    const float hi = cls == 0 ? ll_hi : (cls == 1 ? w_hi : p_hi);
+    const float lo = cls == 0 ? (I.has_mp ? I.mm_lo[m] : ll_lo) : (cls == 1 ? w_lo : p_lo);
+    const float hi = cls == 0 ? (I.has_mp ? I.mm_hi[m] : ll_hi) : (cls == 1 ? w_hi : p_hi);
     if (r2 >= hi) return false;
     bool in = r2 < lo;
-    if (!in) in = exact_inside(v, I, pi, pj, cls);
-    if (in && cls == 2 && is_excluded(v, I, v.id[pi], v.id[pj])) in = false;
+    if (!in) in = exact_inside(v, I, pi, pj, cls, m);
+    if (in && cls != 0 && is_excluded(v, I, v.id[pi], v.id[pj], pj)) in = false;
     if (!in) return false;
-    if (ll)
+    if (ll && I.has_mp)
+        lipid_dispatch<float, S0, LipK>(LipK(I, m), dx, dy, dz, r2, oi.x, oi.y, oi.z, oj.x, oj.y, oj.z, fx, fy, fz, tx,
+                                        ty, tz, zc, (float*)nullptr);
+    else if (ll)
         lipid_dispatch<float, S0>(I, dx, dy, dz, r2, oi.x, oi.y, oi.z, oj.x, oj.y, oj.z, fx, fy, fz, tx, ty, tz, zc,
                                   (float*)nullptr);
     else
@@ -1061,7 +1097,10 @@ struct PairC {
 // read from global memory (L1/L2), the constants of the pair terms in
 // registers, the force and torque summed as exact split integers; terms of
 // 1000 or more go to the int64 side array (big = true).
-template <int Z, bool S0>
+// MP: the batch holds band-3 or glycophorin, whose pairs take the constants
+// of their bilayer species pair (the lipid-only instantiation tests the
+// lipid type alone).
+template <int Z, bool S0, bool MP = false>
 __device__ __forceinline__ void eval_list(const View& v, int q, const int* __restrict__ nlist,
                                           const int* __restrict__ ncnt, int cap, const int4* __restrict__ rowoff,
                                           SplitAcc af[3], SplitAcc at[3], int& nterm, bool& big, int& pi_out) {
@@ -1078,6 +1117,10 @@ __device__ __forceinline__ void eval_list(const View& v, int q, const int* __res
     const int zc = (Z > 0) ? Z : C.zeta;
     const int4* __restrict__ ro = rowoff + (size_t)k * kAdjRow;
     const int n = min(ncnt[q], cap);
+    // a particle without bonds has no excluded pair: its list skips the test
+    // (the lipid-only instantiation runs only when no bilayer particle has a
+    // bond, so that only pairs of cytoskeleton proteins can be excluded)
+    const bool ibond = (qi.w & kMirrorBonded) != 0;
     for (int a = 0; a < 3; a++) { af[a].zero(); at[a].zero(); }
     nterm = 0;
     big = false;
@@ -1092,20 +1135,36 @@ __device__ __forceinline__ void eval_list(const View& v, int q, const int* __res
         const int4 mj = __ldg(v.mqr + qj);
         const float4 oj = __ldg(v.mor + qj);
         const int tj = mj.w & 0xff;
-        const bool ll = (ti == kLipid) && (tj == kLipid);
-        const int cls = ll ? 0 : ((ti == kLipid || tj == kLipid) ? 1 : 2);
+        int m = 0;
+        int cls;
+        if constexpr (MP) {
+            cls = pair_class(ti, tj, m);
+        } else {
+            const bool l2 = (ti == kLipid) && (tj == kLipid);
+            cls = l2 ? 0 : ((ti == kLipid || tj == kLipid) ? 1 : 2);
+        }
+        const bool ll = cls == 0;
         const int dxq = (int)((unsigned)mj.x + (unsigned)o.x - (unsigned)qi.x);
         const int dyq = (int)((unsigned)mj.y + (unsigned)o.y - (unsigned)qi.y);
         const int dzq = (int)((unsigned)mj.z + (unsigned)o.z - (unsigned)qi.z);
         const float dx = (float)dxq * kMirrorUnit, dy = (float)dyq * kMirrorUnit, dz = (float)dzq * kMirrorUnit;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float lo = cls == 0 ? C.ll_lo : (cls == 1 ? C.w_lo : C.p_lo);
-        const float hi = cls == 0 ? C.ll_hi : (cls == 1 ? C.w_hi : C.p_hi);
+        const float lo = cls == 0 ? (MP ? I.mm_lo[m] : C.ll_lo) : (cls == 1 ? C.w_lo : C.p_lo);
+        const float hi = cls == 0 ? (MP ? I.mm_hi[m] : C.ll_hi) : (cls == 1 ? C.w_hi : C.p_hi);
         if (r2 >= hi) continue;
-        if (!(r2 < lo) && !exact_inside(v, I, pi, __float_as_int(oj.w), cls)) continue;
-        if (cls == 2 && is_excluded(v, I, v.id[pi], v.id[__float_as_int(oj.w)])) continue;
+        if (!(r2 < lo) && !exact_inside(v, I, pi, __float_as_int(oj.w), cls, m)) continue;
+        if ((MP ? (cls != 0 && ibond) : cls == 2) &&
+            is_excluded(v, I, v.id[pi], v.id[__float_as_int(oj.w)], __float_as_int(oj.w)))
+            continue;
         float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (ll) {
+        if (ll && MP) {
+            PairC Cm = C;
+            Cm.eps = I.mm_eps[m];
+            Cm.aw = I.mm_aw[m];
+            Cm.eps2z_aw = I.mm_e2za[m];
+            lipid_terms_f<0, true>(Cm, dx, dy, dz, r2, oi.x, oi.y, oi.z, oj.x, oj.y, oj.z, f[0], f[1], f[2], f[3],
+                                   f[4], f[5]);
+        } else if (ll) {
             if (zc == 4)
                 lipid_terms_f<4, S0>(C, dx, dy, dz, r2, oi.x, oi.y, oi.z, oj.x, oj.y, oj.z, f[0], f[1], f[2], f[3],
                                      f[4], f[5]);
@@ -1142,7 +1201,8 @@ __device__ __forceinline__ void eval_list(const View& v, int q, const int* __res
 // Compiled for 5 and 7 CTAs per SM (the autotuner's second dimension):
 // seven (72 registers, a few spilled) hide more of the gathers' latency than
 // five without spills, 0.785 against 0.857 ms on the 4M cell.
-template <int Z, bool S0, int MINB>
+// MP: the batch holds band-3 or glycophorin (eval_list).
+template <int Z, bool S0, int MINB, bool MP = false>
 __global__ void __launch_bounds__(128, MINB)
     k_pair_eval(View v, const int* __restrict__ nlist, const int* __restrict__ ncnt, int cap,
                 const int4* __restrict__ rowoff) {
@@ -1152,7 +1212,7 @@ __global__ void __launch_bounds__(128, MINB)
     SplitAcc af[3], at[3];
     int nterm, pi;
     bool big;
-    eval_list<Z, S0>(v, q, nlist, ncnt, cap, rowoff, af, at, nterm, big, pi);
+    eval_list<Z, S0, MP>(v, q, nlist, ncnt, cap, rowoff, af, at, nterm, big, pi);
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         long long fb = 0, tb = 0;
@@ -1205,7 +1265,7 @@ __global__ void __launch_bounds__(128, 4)
     }
     if (side) sflag[pi] = 0;
     const Inst& I = v.inst[find_inst(v.inst_p0, v.B, pi)];
-    if (I.vol_on && v.type[pi] == kLipid) {
+    if (I.vol_on && bilayer(v.type[pi])) {
         // the volume constraint's pressure on the lipid's area element, as
         // the constraint's own launch computes it
         const double V = I.a3 * volume_of(__ldg(&v.vol[2 * (&I - v.inst)]), __ldg(&v.vol[2 * (&I - v.inst) + 1]));
@@ -1402,7 +1462,13 @@ void Ensemble::launch_pairs(bool energies, bool dump) {
         if (ctas == 5) k_pair_eval<Z, S, 5><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff); \
         else k_pair_eval<Z, S, 7><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);          \
     } while (0)
-        if (z4 && s0z) {
+        if (any_mp()) {
+            // band-3 or glycophorin present: the general evaluation with the
+            // bilayer species pairs' constants
+            if (ctas == 5) k_pair_eval<0, true, 5, true><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);
+            else k_pair_eval<0, true, 7, true><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);
+            k_pair_overflow<0, true><<<152, 128, 0, stream>>>(v, d_novf, d_novf_n, ovf_cap, d_rowoff, nullptr);
+        } else if (z4 && s0z) {
             ORBC_EVAL(4, false);
             k_pair_overflow<4, false><<<152, 128, 0, stream>>>(v, d_novf, d_novf_n, ovf_cap, d_rowoff, nullptr);
         } else if (z4) {

@@ -46,7 +46,7 @@ __global__ void k_kick_d(View v, long long* __restrict__ steps) {
     const int b = find_inst(v.inst_p0, v.B, p);
     const Inst& I = v.inst[b];
     const size_t N = v.N;
-    const bool lipid = v.type[p] == kLipid;
+    const bool lipid = bilayer(v.type[p]);
     long long vq[3], wq[3] = {0, 0, 0};
     double Nd[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < 3; a++) vq[a] = v.vq[a * N + p];
@@ -73,7 +73,7 @@ __global__ void k_kick(View v, long long* __restrict__ steps) {
     const Inst& I = v.inst[b];
     const Consts<T> C(I);
     const size_t N = v.N;
-    const bool lipid = v.type[p] == kLipid;
+    const bool lipid = bilayer(v.type[p]);
     long long vq[3], nq[3] = {0, 0, 0}, wq[3] = {0, 0, 0};
     for (int a = 0; a < 3; a++) vq[a] = v.vq[a * N + p];
     if (lipid) for (int a = 0; a < 3; a++) { nq[a] = v.nq[a * N + p]; wq[a] = v.wq[a * N + p]; }
@@ -98,7 +98,7 @@ __global__ void k_kinetic(View v, long long* __restrict__ energy) {
         double s = 0.0, r = 0.0;
         for (int a = 0; a < 3; a++) { double x = grid_to_double(v.vq[a * N + p]); s += x * x; }
         kt = __double2ll_rn(0.5 * I.mass * s * 4294967296.0);
-        if (v.type[p] == kLipid) {
+        if (bilayer(v.type[p])) {
             for (int a = 0; a < 3; a++) { double x = grid_to_double(v.wq[a * N + p]); r += x * x; }
             kr = __double2ll_rn(0.5 * I.inertia * r * 4294967296.0);
         }
@@ -148,7 +148,7 @@ __global__ void k_quench(View v, double dt, double max_move, double max_turn) {
         v.xq[a * N + p] += V::grid(dt * u[a]);
         v.vq[a * N + p] = V::grid(u[a]);
     }
-    if (v.type[p] != kLipid) return;
+    if (!bilayer(v.type[p])) return;
     long long nq[3], wq[3];
     double n[3], t[3], w[3];
     for (int a = 0; a < 3; a++) {

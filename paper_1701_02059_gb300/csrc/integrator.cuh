@@ -148,7 +148,7 @@ __device__ inline void baoa_body(const View& v, const View& o, int p, const long
     const Consts<T> C(I);
     const size_t N = v.N;
     const unsigned char type = v.type[p];
-    const bool lipid = type == kLipid;
+    const bool lipid = bilayer(type);
     long long xq[3], vq[3], nq[3] = {0, 0, 0}, wq[3] = {0, 0, 0};
     for (int a = 0; a < 3; a++) { xq[a] = v.xq[a * N + p]; vq[a] = v.vq[a * N + p]; }
     if (lipid) for (int a = 0; a < 3; a++) { nq[a] = v.nq[a * N + p]; wq[a] = v.wq[a * N + p]; }
@@ -246,7 +246,7 @@ __device__ inline void baoa_d_body(const View& v, const View& o, int p, const lo
     const Inst& I = v.inst[b];
     const size_t N = v.N;
     const unsigned char type = v.type[p];
-    const bool lipid = type == kLipid;
+    const bool lipid = bilayer(type);
     long long xq[3], vq[3], nq[3] = {0, 0, 0}, wq[3] = {0, 0, 0};
     for (int a = 0; a < 3; a++) { xq[a] = v.xq[a * N + p]; vq[a] = v.vq[a * N + p]; }
     if (lipid) for (int a = 0; a < 3; a++) { nq[a] = v.nq[a * N + p]; wq[a] = v.wq[a * N + p]; }

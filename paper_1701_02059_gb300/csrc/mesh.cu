@@ -26,7 +26,18 @@
 //     rest length slack |J_b - J_a| / (beads + 1);
 //   - a candidate is dropped when a protein particle lies closer than d_min,
 //     or an earlier candidate (kept or not) closer than d_ll;
-//   - ids: kept lipids in candidate order, then junctions, then spectrin.
+//   - the bilayer's proteins, when asked for: glycophorin on every vertex
+//     (at the vertex, director n_v) bonded to its junction; immobile band-3
+//     on every edge (at the midpoint (a + b) / 2, director the normalised
+//     FP64 sum of the two vertices' exact normal sums) bonded to the chain's
+//     bead floor((beads - 1) / 2); each anchor's rest length its length at
+//     construction, constant kb_anchor; a face sample is a mobile band-3
+//     instead of a lipid when word 2 at counter (f, k, 0, 3) is below
+//     band3_fraction; glycophorin and edge band-3 count as proteins for
+//     d_min;
+//   - ids: the bilayer first (kept face samples in candidate order,
+//     glycophorin, edge band-3), then junctions, then spectrin; bonds: the
+//     chains', then the anchors (glycophorin's first).
 #include "abi_common.cuh"
 
 #include <algorithm>
@@ -177,9 +188,55 @@ __global__ void k_mesh_beads(MeshDev m, const int* __restrict__ own, const int* 
     }
 }
 
-// Lipid candidates: sample k of face f, director = unit face normal.
+// The bilayer's proteins: glycophorin on the vertices, band-3 on the edges'
+// midpoints, after the ncyt cytoskeleton particles in prot, with their
+// directors in dir.
+__global__ void k_mesh_surface(MeshDev m, const long long* __restrict__ nacc, const int* __restrict__ own,
+                               const int* __restrict__ eidx, long long ncyt, int ngly, int band3_edges,
+                               double* __restrict__ prot, double* __restrict__ dir) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ngly) {
+        const double n[3] = {__ll2double_rn(nacc[3 * t]), __ll2double_rn(nacc[3 * t + 1]), __ll2double_rn(nacc[3 * t + 2])};
+        const double l = norm_d(n);
+        for (int k = 0; k < 3; k++) {
+            prot[3 * (ncyt + t) + k] = m.v[3 * t + k];
+            dir[3 * t + k] = l > 0.0 ? __ddiv_rn(n[k], l) : 0.0;
+        }
+    }
+    if (band3_edges && t < 3 * m.F && own[t]) {
+        const int f = t / 3, i = t % 3;
+        const int a = m.f[t], b = m.f[3 * f + (i + 1) % 3];
+        const long long q = ngly + (long long)eidx[t];
+        double n[3];
+        for (int k = 0; k < 3; k++) n[k] = __dadd_rn(__ll2double_rn(nacc[3 * a + k]), __ll2double_rn(nacc[3 * b + k]));
+        const double l = norm_d(n);
+        for (int k = 0; k < 3; k++) {
+            prot[3 * (ncyt + q) + k] = __dmul_rn(__dadd_rn(m.v[3 * a + k], m.v[3 * b + k]), 0.5);
+            dir[3 * q + k] = l > 0.0 ? __ddiv_rn(n[k], l) : 0.0;
+        }
+    }
+}
+
+// Anchor bonds: surface protein q (output id nl + q) to its junction or to
+// its edge chain's middle bead (output id nbil + that particle).
+__global__ void k_mesh_anchors(const double* __restrict__ prot, long long ncyt, int ngly, long long nsurf, int V,
+                               int beads, long long nl, long long nbil, int* __restrict__ ends,
+                               double* __restrict__ rest) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nsurf) return;
+    const long long pw = q < ngly ? q : (long long)V + (q - ngly) * beads + (beads - 1) / 2;
+    const double* x = prot + 3 * (ncyt + q);
+    const double* y = prot + 3 * pw;
+    const double d[3] = {__dsub_rn(x[0], y[0]), __dsub_rn(x[1], y[1]), __dsub_rn(x[2], y[2])};
+    ends[2 * q] = (int)(nl + q);
+    ends[2 * q + 1] = (int)(nbil + pw);
+    rest[q] = norm_d(d);
+}
+
+// Lipid candidates: sample k of face f, director = unit face normal; type 3
+// (mobile band-3) when word 2 is below b3, else 0.
 __global__ void k_mesh_samples(MeshDev m, const int* __restrict__ foff, long long nc, unsigned long long seed,
-                               double* __restrict__ cand) {
+                               double b3, double* __restrict__ cand, unsigned char* __restrict__ ctype) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nc) return;
     int lo = 0, hi = m.F - 1;                 // the face: foff[f] <= i < foff[f + 1]
@@ -197,6 +254,7 @@ __global__ void k_mesh_samples(MeshDev m, const int* __restrict__ foff, long lon
     const double l = norm_d(cr);
     const uint4 w = words(seed, (unsigned)f, (unsigned)s, 3u);
     const double sr1 = __dsqrt_rn(u01(w.x)), r2 = u01(w.y);
+    ctype[i] = u01(w.z) < b3 ? 3 : 0;
     const double ca = __dsub_rn(1.0, sr1), cb = __dmul_rn(sr1, __dsub_rn(1.0, r2)), cc = __dmul_rn(sr1, r2);
     for (int k = 0; k < 3; k++) {
         cand[6 * i + k] = __dadd_rn(__dadd_rn(__dmul_rn(ca, a[k]), __dmul_rn(cb, b[k])), __dmul_rn(cc, c[k]));
@@ -259,19 +317,29 @@ __global__ void k_mesh_reject(Hash H, const double* __restrict__ cand, long long
     keep[i] = ok ? 1 : 0;
 }
 
-__global__ void k_mesh_out(const double* __restrict__ cand, long long nc, const int* __restrict__ keep,
-                           const int* __restrict__ kidx, long long nl, const double* __restrict__ prot, long long np,
-                           int V, double* __restrict__ pos, double* __restrict__ ori, unsigned char* __restrict__ type) {
+// Output in id order: kept face samples, the bilayer's proteins (after
+// the ncyt cytoskeleton particles in prot), then the cytoskeleton.
+__global__ void k_mesh_out(const double* __restrict__ cand, const unsigned char* __restrict__ ctype, long long nc,
+                           const int* __restrict__ keep, const int* __restrict__ kidx, long long nl,
+                           const double* __restrict__ prot, const double* __restrict__ dir, long long ncyt, int ngly,
+                           long long nsurf, int V, double* __restrict__ pos, double* __restrict__ ori,
+                           unsigned char* __restrict__ type) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nbil = nl + nsurf;
     if (i < nc && keep[i]) {
         const long long o = kidx[i];
         for (int k = 0; k < 3; k++) { pos[3 * o + k] = cand[6 * i + k]; ori[3 * o + k] = cand[6 * i + 3 + k]; }
-        type[o] = 0;
+        type[o] = ctype[i];
     }
-    if (i < np) {
-        const long long o = nl + i;
+    if (i < ncyt) {
+        const long long o = nbil + i;
         for (int k = 0; k < 3; k++) { pos[3 * o + k] = prot[3 * i + k]; ori[3 * o + k] = 0.0; }
         type[o] = i < V ? 1 : 2;
+    }
+    if (i < nsurf) {
+        const long long o = nl + i;
+        for (int k = 0; k < 3; k++) { pos[3 * o + k] = prot[3 * (ncyt + i) + k]; ori[3 * o + k] = dir[3 * i + k]; }
+        type[o] = i < ngly ? 4 : 3;
     }
 }
 
@@ -313,6 +381,9 @@ extern "C" int orbc_mesh_build(const orbc_mesh_params* mp, int nv, const double*
     if (!mp || !verts || !faces || !n_out || !nb_out || nv < 3 || nf < 1) return ORBC_E_ARG;
     if (!(mp->spacing > 0) || mp->beads < 0 || mp->beads > 64 || !(mp->slack > 0) || !(mp->kb >= 0) ||
         !(mp->d_min >= 0) || !(mp->d_ll >= 0) || !std::isfinite(mp->offset))
+        return ORBC_E_ARG;
+    if (!(mp->band3_fraction >= 0 && mp->band3_fraction <= 1) || !(mp->kb_anchor >= 0) ||
+        !std::isfinite(mp->kb_anchor) || (mp->band3_edges && mp->beads < 1))
         return ORBC_E_ARG;
     if ((cap > 0 && (!pos || !ori || !type)) || (bond_cap > 0 && (!bonds || !r0 || !kb))) return ORBC_E_ARG;
     for (long long q = 0; q < 3ll * nv; q++)
@@ -358,18 +429,26 @@ extern "C" int orbc_mesh_build(const orbc_mesh_params* mp, int nv, const double*
         CK(cudaMemcpyAsync(&hne, eidx + nh, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         const long long nc = hnc, ne = hne, beads = mp->beads;
-        const long long np = nv + ne * beads, nbond = ne * (beads + 1);
+        // cytoskeleton (junctions, beads), then the bilayer's proteins
+        const int ngly = mp->glycophorin ? nv : 0;
+        const long long ncyt = nv + ne * beads, nsurf = ngly + (mp->band3_edges ? ne : 0);
+        const long long np = ncyt + nsurf, nchain = ne * (beads + 1), nbond = nchain + nsurf;
         if (nc + np > (1ll << 30)) return ORBC_E_ARG;
         // proteins
         double* prot = S.get<double>(3 * (size_t)np);
+        double* pdir = S.get<double>(3 * (size_t)nsurf);
         double* rest = S.get<double>((size_t)nbond);
         int* ends = S.get<int>(2 * (size_t)nbond);
         k_mesh_junctions<<<nb(nv, 256), 256, 0, st>>>(m, nacc, mp->offset, prot);
         k_mesh_beads<<<nb(nh, 256), 256, 0, st>>>(m, own, eidx, mp->beads, mp->slack, prot, rest, ends);
+        if (nsurf > 0)
+            k_mesh_surface<<<nb(std::max<long long>(nh, nv), 256), 256, 0, st>>>(m, nacc, own, eidx, ncyt, ngly,
+                                                                                 mp->band3_edges, prot, pdir);
         CK(cudaGetLastError());
         // lipid candidates and the minimum distances
         double* cand = S.get<double>(6 * (size_t)nc);
-        if (nc > 0) k_mesh_samples<<<nb(nc, 256), 256, 0, st>>>(m, foff, nc, mp->seed, cand);
+        unsigned char* ctype = S.get<unsigned char>((size_t)nc);
+        if (nc > 0) k_mesh_samples<<<nb(nc, 256), 256, 0, st>>>(m, foff, nc, mp->seed, mp->band3_fraction, cand, ctype);
         int* keep = S.get<int>((size_t)nc + 1);
         int* kidx = S.get<int>((size_t)nc + 1);
         const double dmin2 = mp->d_min * mp->d_min, dll2 = mp->d_ll * mp->d_ll;
@@ -407,7 +486,7 @@ extern "C" int orbc_mesh_build(const orbc_mesh_params* mp, int nv, const double*
         int hnl = 0;
         CK(cudaMemcpyAsync(&hnl, kidx + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        const long long nl = hnl, n = nl + np;
+        const long long nl = hnl, nbil = nl + nsurf, n = nl + np;
         *n_out = n;
         *nb_out = nbond;
         if (cap >= n && pos) {
@@ -416,17 +495,21 @@ extern "C" int orbc_mesh_build(const orbc_mesh_params* mp, int nv, const double*
             unsigned char* dty = S.get<unsigned char>((size_t)n);
             const long long span = std::max(nc, np);
             if (span > 0)
-                k_mesh_out<<<nb(span, 256), 256, 0, st>>>(cand, nc, keep, kidx, nl, prot, np, nv, dpos, dori, dty);
+                k_mesh_out<<<nb(span, 256), 256, 0, st>>>(cand, ctype, nc, keep, kidx, nl, prot, pdir, ncyt, ngly,
+                                                          nsurf, nv, dpos, dori, dty);
             CK(cudaMemcpyAsync(pos, dpos, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
             CK(cudaMemcpyAsync(ori, dori, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
             CK(cudaMemcpyAsync(type, dty, (size_t)n, cudaMemcpyDeviceToHost, st));
         }
         if (bond_cap >= nbond && bonds && nbond > 0) {
-            k_shift_ends<<<nb(2 * nbond, 256), 256, 0, st>>>(ends, 2 * nbond, (int)nl);
+            if (nchain > 0) k_shift_ends<<<nb(2 * nchain, 256), 256, 0, st>>>(ends, 2 * nchain, (int)nbil);
+            if (nsurf > 0)
+                k_mesh_anchors<<<nb(nsurf, 256), 256, 0, st>>>(prot, ncyt, ngly, nsurf, nv, mp->beads, nl, nbil,
+                                                               ends + 2 * nchain, rest + nchain);
             CK(cudaMemcpyAsync(bonds, ends, sizeof(int) * 2 * nbond, cudaMemcpyDeviceToHost, st));
             CK(cudaMemcpyAsync(r0, rest, sizeof(double) * nbond, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
-            for (long long q = 0; q < nbond; q++) kb[q] = mp->kb;
+            for (long long q = 0; q < nbond; q++) kb[q] = q < nchain ? mp->kb : mp->kb_anchor;
         }
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(st));

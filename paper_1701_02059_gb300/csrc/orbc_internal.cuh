@@ -28,6 +28,22 @@ constexpr float kMagic = 12582912.0f;                // 1.5 * 2^23
 constexpr int kMagicBits = 0x4B400000;
 constexpr int kMaxBondsPerParticle = 8;
 constexpr int kLipid = 0;
+constexpr int kBand3 = 3;
+constexpr int kGlycophorin = 4;
+constexpr int kMaxType = 4;
+// flag in a mirror's type word (above the type byte): the particle has bonds
+constexpr int kMirrorBonded = 0x100;
+// Half-width (sigma) of the band around a cutoff inside which the FP32
+// distance test defers to the exact FP64 decision.
+constexpr float kCutBand = 1e-6f;
+
+// Bilayer particles (lipids and the membrane proteins band-3 and
+// glycophorin) carry a director and meet each other through the lipid
+// potential with the constants of their species pair; junctions and
+// spectrin beads are the cytoskeleton.
+__host__ __device__ inline bool bilayer(int t) { return t == kLipid || t >= kBand3; }
+// species index of a bilayer type: lipid 0, band-3 1, glycophorin 2
+__host__ __device__ inline int species(int t) { return t < kBand3 ? 0 : t - 2; }
 // Largest magnitude of one pair, bond or constraint term (force or torque
 // component, eps/sigma or eps; a volume term in sigma^3): 2^24, so that a
 // particle's 2^-32 fixed-point sum of a few hundred terms stays inside int64.
@@ -84,6 +100,17 @@ struct Inst {
     // this set's ids in the membrane (Philox counters, pair dumps), and
     // whether every particle is a centroid member (else only the lipids)
     int partner, id_base, all_members;
+    // bilayer species pairs, index 3 s_i + s_j (lipid, band-3, glycophorin):
+    // the lipid potential's well depth and cutoff of each pair (the
+    // lipid-lipid entry is eps and rc), the FP32 constants (eps, aw,
+    // eps 2 zeta aw), the squared FP64 cutoff and the FP32 band of the
+    // inclusion decision; mm_rcf[s] is the largest FP32 cutoff of species s.
+    // has_mp: the instance holds band-3 or glycophorin particles;
+    // bonded_bilayer: some bilayer particle has a bond (an anchor), so a
+    // bilayer-cytoskeleton pair may be excluded from the WCA term.
+    int has_mp, bonded_bilayer;
+    float mm_eps[9], mm_aw[9], mm_e2za[9], mm_lo[9], mm_hi[9], mm_rcf[3];
+    double mm_eps_d[9], mm_rc_d[9], mm_rc2[9];
 };
 
 // ---------------------------------------------------------------- packed device arrays
@@ -116,7 +143,7 @@ struct View {
     long long *F, *T;               // [3][N]
     long long* Fbig;                // [6][N] wide per-pair contributions (normally zero)
     // mirrors for the pair kernel
-    int4* mq;                       // x - c at 2^-26 sigma, w = type
+    int4* mq;                       // x - c at 2^-26 sigma, w = type | kMirrorBonded (has bonds)
     float4* mo;                     // director, w = slot (int bits)
     int4* mqr;                      // the same two, each tile of 128 particles of a cell
     float4* mor;                    // in the order of the pair kernel's group ranks
@@ -350,7 +377,7 @@ __device__ inline Frame tangent_frame(float nx, float ny, float nz) {
     return f;
 }
 
-// Volume constraint: the sum D of (x - c).n over the lipids is kept as two
+// Volume constraint: the sum D of (x - c).n over the bilayer is kept as two
 // integer sums, of the terms' floors at 2^-24 sigma and of their remainders
 // at 2^-48; the enclosed volume is (a/3) D.
 constexpr double kVolUnit = 16777216.0;                 // 2^24: fixed point of (x - c).n, 2^-24 sigma
@@ -360,10 +387,10 @@ __host__ __device__ inline double volume_of(long long hi, long long lo) {
     return (double)hi * kVolUnitInv + (double)lo * kVolFineInv;
 }
 
-// A particle that moves its cell's centroid (the M-step): the lipids, or
-// every particle of a protein cell set.
+// A particle that moves its cell's centroid (the M-step): the bilayer's
+// (lipids and membrane proteins), or every particle of a protein cell set.
 __host__ __device__ inline bool centroid_member(const Inst& I, unsigned char type) {
-    return I.all_members || type == kLipid;
+    return I.all_members || bilayer(type);
 }
 
 // Raises status bits for the launch and for the instance I (a reference

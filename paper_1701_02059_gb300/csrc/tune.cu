@@ -26,10 +26,12 @@ namespace orbc {
 static const int kTileCandidates[] = {32, 45, 61, 80, 100};
 static const int kEvalCtas[] = {5, 7};
 
-// Shape of a system for the cache: particle, lipid and bond counts, periodic
-// axes and box, precision, and the extent of the particles (rounded).
+// Shape of a system for the cache: particle, lipid, membrane-protein and bond
+// counts, periodic axes and box, precision, and the extent of the particles
+// (rounded).
 static std::string tune_key(const HostInstance& h) {
     const int nl = (int)std::count(h.type.begin(), h.type.end(), (unsigned char)kLipid);
+    const int nmp = (int)std::count_if(h.type.begin(), h.type.end(), [](unsigned char t) { return t >= kBand3; });
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     for (int i = 0; i < h.n; i++)
         for (int a = 0; a < 3; a++) {
@@ -39,6 +41,7 @@ static std::string tune_key(const HostInstance& h) {
         }
     std::ostringstream k;
     k << "n=" << h.n << ",lipids=" << nl << ",bonds=" << h.r0.size() << ",prec=" << h.prm.precision;
+    if (nmp) k << ",mp=" << nmp;
     for (int a = 0; a < 3; a++)
         k << ",p" << a << "=" << h.prm.periodic[a] << ":" << std::lround(h.prm.box[a]) << ":"
           << std::lround(hi[a] - lo[a]);
@@ -125,7 +128,7 @@ extern "C" int orbc_autotune(const orbc_params* params, int n, const double* pos
                 return;
             }
         }
-        const int nl = (int)std::count(h.type.begin(), h.type.end(), (unsigned char)kLipid);
+        const int nl = (int)std::count_if(h.type.begin(), h.type.end(), bilayer);
         cudaStream_t st;
         CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
         int bestK = -1, bestC = 7, lastK = -1;

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kVolThreads) k_volume_sum(View v, int b_only, 
         const int p = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
         int b = -1;
         long long th = 0, tl = 0;
-        if (p < (int)N && v.type[p] == kLipid) {
+        if (p < (int)N && bilayer(v.type[p])) {
             const int bi = find_inst(v.inst_p0, v.B, p);
             const Inst& I = v.inst[bi];
             if (b_only >= 0 ? bi == b_only : I.vol_on != 0) {
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kVolThreads) k_volume_apply(View v, const long
     T pa = 0;                                      // P a of instance bc
     bool on = false;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < (int)N; p += stride) {
-        if (v.type[p] != kLipid) continue;
+        if (!bilayer(v.type[p])) continue;
         const int b = find_inst(v.inst_p0, v.B, p);
         const Inst& I = v.inst[b];
         if (b != bc) {
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kVolThreads) k_height_map(View v, HeightArgs A
     const size_t N = v.N;
     const int p_lo = v.inst_p0[A.b], p_hi = v.inst_p0[A.b + 1];
     for (int p = p_lo + blockIdx.x * blockDim.x + threadIdx.x; p < p_hi; p += gridDim.x * blockDim.x) {
-        if (v.type[p] != kLipid) continue;
+        if (!bilayer(v.type[p])) continue;
         const long long zq = v.xq[2 * N + p];
         const double x = grid_to_double(v.xq[p]), y = grid_to_double(v.xq[N + p]), z = grid_to_double(zq);
         if (!(z > A.z_min)) continue;

@@ -29,6 +29,14 @@ MESHES = {
     "biconcave-600": (lambda: M.biconcave_mesh(600, 20_000), dict(beads=4, seed=2)),
     "triangle-open": (lambda: (np.array([[0.0, 0.0, 0.0], [30.0, 0.0, 0.0], [0.0, 20.0, 0.0]]),
                                np.array([[0, 1, 2]], np.int32)), dict(beads=2, d_min=0.0, d_ll=0.0, offset=0.0)),
+    # the bilayer's proteins: glycophorin on the vertices, band-3 on the
+    # edges and among the face samples, anchored to the network
+    "icosphere-f6-proteins": (lambda: M.icosphere_mesh(6, 14.0),
+                              dict(beads=3, seed=6, glycophorin=1, band3_edges=1, band3_fraction=0.1, kb_anchor=40.0)),
+    "biconcave-600-proteins": (lambda: M.biconcave_mesh(600, 20_000),
+                               dict(beads=4, seed=3, glycophorin=1, band3_edges=1, band3_fraction=0.05)),
+    "triangle-open-band3": (lambda: (np.array([[0.0, 0.0, 0.0], [30.0, 0.0, 0.0], [0.0, 20.0, 0.0]]),
+                                     np.array([[0, 1, 2]], np.int32)), dict(beads=1, band3_edges=1, band3_fraction=0.5)),
 }
 
 
@@ -55,13 +63,17 @@ def test_mesh_build_rejects_bad_meshes():
     with pytest.raises(G.OrbcError) as e:
         G.mesh_build(v, deg)
     assert e.value.code == _native.ORBC_E_ARG
+    for kw in (dict(beads=0, band3_edges=1), dict(band3_fraction=1.5), dict(kb_anchor=-1.0)):
+        with pytest.raises(G.OrbcError) as e:
+            G.mesh_build(v, f, **kw)
+        assert e.value.code == _native.ORBC_E_ARG, kw
 
 
 def _membrane(out, kT=0.0, K=None):
     n = len(out["type"])
-    return M.Membrane(out["pos"], np.zeros((n, 3)), np.where(out["type"][:, None] == 0, out["ori"], 0.0),
+    return M.Membrane(out["pos"], np.zeros((n, 3)), np.where(np.isin(out["type"], M.BILAYER)[:, None], out["ori"], 0.0),
                       np.zeros((n, 3)), out["type"], np.arange(n, dtype=np.uint32), out["bonds"], out["r0"],
-                      out["kb"], (0.0, 0.0, 0.0), (0, 0, 0), K or max(1, n // 61), kT)
+                      out["kb"], np.zeros(3), np.zeros(3, np.int32), K or max(1, n // 61), kT)
 
 
 def test_quench_matches_oracle_and_removes_collisions():
@@ -118,3 +130,39 @@ def test_red_cell_from_a_mesh():
     fm = g.quench(20, 0.01)
     assert np.isfinite(fm) and fm < f0
     g.close()
+
+
+def test_protein_set_from_a_mesh_quenches_and_runs_like_the_oracle():
+    """The full protein set built the paper's way (glycophorin on the
+    vertices, immobile band-3 on the edges, mobile band-3 on the faces, all
+    anchored): quenched on the GPU and in the oracle, then 20 Langevin steps
+    from the oracle's quenched state agree within the FP32-force tolerance."""
+    v, f = M.icosphere_mesh(6, 14.0)
+    out = G.mesh_build(v, f, beads=3, seed=8, glycophorin=1, band3_edges=1, band3_fraction=0.1)
+    mem = _membrane(out)
+    g = G.System(G.make_params(kT=0.0, n_centroids=mem.n_centroids, seed=0))
+    g.load_membrane(mem)
+    g.init_cells()
+    g.compute_forces()
+    f0 = np.linalg.norm(g.forces()[0], axis=1).max()
+    fm = g.quench(30, 0.01)
+    o = oracle.OracleSystem(oracle.model(), oracle.run(kT=0.0, n_centroids=mem.n_centroids, seed=0))
+    o.load(mem)
+    o.init_cells()
+    fo = o.quench(30, 0.01)
+    assert fm < 0.2 * f0 and fo < 0.2 * f0
+    so = o.state()
+    q = mem.copy()
+    q.pos, q.ori, q.kT = so["pos"], so["ori"], 0.2
+    a = G.System(G.make_params(kT=0.2, n_centroids=mem.n_centroids, seed=4))
+    a.load_membrane(q)
+    b = oracle.OracleSystem(oracle.model(), oracle.run(kT=0.2, n_centroids=mem.n_centroids, seed=4))
+    b.load(q)
+    a.init_cells()
+    b.init_cells()
+    a.integrate(20)
+    b.integrate(20)
+    rms = np.sqrt(((a.state()["pos"] - b.state()["pos"]) ** 2).sum(1).mean())
+    assert rms <= 1e-5, rms
+    g.close()
+    a.close()
