@@ -7,7 +7,7 @@ B-A-O-A update, Voronoi rebuild (M-step, Morton relabel, E-step, stable sort,
 radii, neighbouring cells), pair + bond forces, final B.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload rbc-4m|rbc-1m|vesicle-62k|patch-2304] [--precision f32|f64]
+                    [--workload rbc-4m|rbc-1m|rbc-1m-proteins|vesicle-62k|patch-2304] [--precision f32|f64]
 
 --impl reference times the FP64 CPU oracle on this machine's host cores on a
 bounded sample of the same workload.  Under torchrun (N > 1) every rank runs
@@ -76,6 +76,9 @@ def workload(name: str):
     if name == "rbc-1m":
         # the same biconcave cell at a quarter of the particles (profiling captures)
         return M.biconcave(n_lipids=892_756, n_junctions=8_250, n_centroids=16_384, seed=2, name="rbc-1m")
+    if name == "rbc-1m-proteins":
+        # the 1M cell with the protein set of the 4M protein variant (profiling captures)
+        return M.with_membrane_proteins(workload("rbc-1m"), seed=102)
     if name == "vesicle-62k":
         return M.vesicle_62k()
     if name == "patch-2304":
@@ -91,12 +94,19 @@ PRECISION = {"f32": ("F32_FORCE_F64_STATE", "FP32 pair/bond forces; FP64 integra
 
 
 def params_for(mem, precision: str, G, **kw):
+    import numpy as np
+    if np.isin(mem.type, (3, 4)).any():
+        # band-3 or glycophorin: the species table of the protein variant
+        kw.setdefault("eps_mem", PROTEIN_EPS)
+        kw.setdefault("rc_mem", PROTEIN_RC)
     return G.make_params(kT=mem.kT, n_centroids=mem.n_centroids, box=mem.box, periodic=mem.periodic,
                          seed=2, precision=getattr(G, PRECISION[precision][0]), **kw)
 
 
 def oracle_params(mem, oracle):
-    return (oracle.model(box=mem.box, periodic=mem.periodic),
+    import numpy as np
+    tab = dict(mem_eps=PROTEIN_EPS, mem_rc=PROTEIN_RC) if np.isin(mem.type, (3, 4)).any() else {}
+    return (oracle.model(box=mem.box, periodic=mem.periodic, **tab),
             oracle.run(kT=mem.kT, n_centroids=mem.n_centroids, seed=2))
 
 

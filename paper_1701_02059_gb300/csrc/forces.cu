@@ -1149,21 +1149,27 @@ __device__ __forceinline__ void eval_list(const View& v, int q, const int* __res
         const int dzq = (int)((unsigned)mj.z + (unsigned)o.z - (unsigned)qi.z);
         const float dx = (float)dxq * kMirrorUnit, dy = (float)dyq * kMirrorUnit, dz = (float)dzq * kMirrorUnit;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float lo = cls == 0 ? (MP ? I.mm_lo[m] : C.ll_lo) : (cls == 1 ? C.w_lo : C.p_lo);
-        const float hi = cls == 0 ? (MP ? I.mm_hi[m] : C.ll_hi) : (cls == 1 ? C.w_hi : C.p_hi);
+        // (a lipid pair, m = 0, keeps the constants held in registers)
+        const bool tab = MP && m != 0;
+        const float lo = cls == 0 ? (tab ? I.mm_lo[m] : C.ll_lo) : (cls == 1 ? C.w_lo : C.p_lo);
+        const float hi = cls == 0 ? (tab ? I.mm_hi[m] : C.ll_hi) : (cls == 1 ? C.w_hi : C.p_hi);
         if (r2 >= hi) continue;
         if (!(r2 < lo) && !exact_inside(v, I, pi, __float_as_int(oj.w), cls, m)) continue;
         if ((MP ? (cls != 0 && ibond) : cls == 2) &&
             is_excluded(v, I, v.id[pi], v.id[__float_as_int(oj.w)], __float_as_int(oj.w)))
             continue;
         float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (ll && MP) {
+        if (ll && tab) {
             PairC Cm = C;
             Cm.eps = I.mm_eps[m];
             Cm.aw = I.mm_aw[m];
             Cm.eps2z_aw = I.mm_e2za[m];
-            lipid_terms_f<0, true>(Cm, dx, dy, dz, r2, oi.x, oi.y, oi.z, oj.x, oj.y, oj.z, f[0], f[1], f[2], f[3],
-                                   f[4], f[5]);
+            if (zc == 4)
+                lipid_terms_f<4, S0>(Cm, dx, dy, dz, r2, oi.x, oi.y, oi.z, oj.x, oj.y, oj.z, f[0], f[1], f[2], f[3],
+                                     f[4], f[5]);
+            else
+                lipid_terms_f<0, true>(Cm, dx, dy, dz, r2, oi.x, oi.y, oi.z, oj.x, oj.y, oj.z, f[0], f[1], f[2],
+                                       f[3], f[4], f[5]);
         } else if (ll) {
             if (zc == 4)
                 lipid_terms_f<4, S0>(C, dx, dy, dz, r2, oi.x, oi.y, oi.z, oj.x, oj.y, oj.z, f[0], f[1], f[2], f[3],
@@ -1463,10 +1469,15 @@ void Ensemble::launch_pairs(bool energies, bool dump) {
         else k_pair_eval<Z, S, 7><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);          \
     } while (0)
         if (any_mp()) {
-            // band-3 or glycophorin present: the general evaluation with the
-            // bilayer species pairs' constants
-            if (ctas == 5) k_pair_eval<0, true, 5, true><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);
-            else k_pair_eval<0, true, 7, true><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);
+            // band-3 or glycophorin present (or a bonded bilayer particle):
+            // the evaluation with the bilayer species pairs' constants
+            if (z4 && s0z) {
+                if (ctas == 5) k_pair_eval<4, false, 5, true><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);
+                else k_pair_eval<4, false, 7, true><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);
+            } else {
+                if (ctas == 5) k_pair_eval<0, true, 5, true><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);
+                else k_pair_eval<0, true, 7, true><<<ng, 128, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_rowoff);
+            }
             k_pair_overflow<0, true><<<152, 128, 0, stream>>>(v, d_novf, d_novf_n, ovf_cap, d_rowoff, nullptr);
         } else if (z4 && s0z) {
             ORBC_EVAL(4, false);

@@ -358,3 +358,28 @@ def test_anchored_lipids_take_the_exclusions():
     o.integrate(30)
     assert np.sqrt(((g.state()["pos"] - o.state()["pos"]) ** 2).sum(1).mean()) <= 1e-5
     g.close()
+
+
+@pytest.mark.parametrize("zeta,s0", [(3, 0.0), (4, 0.05)])
+def test_species_pairs_with_other_potential_parameters(zeta, s0):
+    """The species-pair evaluation's general instantiation (another tail
+    exponent, a spontaneous-curvature term) against the oracle: pair set
+    bit-exact, forces within the FP32 tolerance, 50-step trajectory."""
+    mem = vesicle_proteins()
+    tab = dict(eps_mem=TE, rc_mem=TR)
+    g = G.System(G.make_params(kT=mem.kT, n_centroids=mem.n_centroids, seed=0, zeta=zeta, sin_theta0=s0, **tab))
+    g.load_membrane(mem)
+    m = oracle.model(zeta=zeta, sin_theta0=s0, mem_eps=TE, mem_rc=TR)
+    o = oracle.OracleSystem(m, oracle.run(kT=mem.kT, n_centroids=mem.n_centroids, seed=0))
+    o.load(mem)
+    g.init_cells()
+    o.init_cells()
+    assert np.array_equal(g.pairs(), sorted_pairs(o.pairs()))
+    g.compute_forces()
+    o.compute_forces()
+    ef, et = errors(g, o)
+    assert ef <= 1e-5 and et <= 1e-5, (ef, et)
+    g.integrate(50)
+    o.integrate(50)
+    assert np.sqrt(((g.state()["pos"] - o.state()["pos"]) ** 2).sum(1).mean()) <= 1e-5
+    g.close()
