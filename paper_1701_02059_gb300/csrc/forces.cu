@@ -796,6 +796,11 @@ struct SNbr {
 };
 
 // Eight CTAs per SM (the shared-memory limit): 0.833 against 0.863 ms at seven.
+// MP (band-3 or glycophorin in the batch): the staged particles carry three
+// partner classes (lipid 0, cytoskeleton 1, bilayer protein 2) and each
+// particle culls them at its own cutoff for that class, so that a lipid's
+// list is not widened to the cutoff of its widest protein pair.
+template <bool MP>
 __global__ void __launch_bounds__(kPairThreads, 8)
     k_pair_search(View v, int* __restrict__ nlist, int* __restrict__ ncnt, int cap, int2* __restrict__ ovf,
                   int* __restrict__ novf, int ovf_cap, int4* __restrict__ rowoff) {
@@ -920,12 +925,23 @@ __global__ void __launch_bounds__(kPairThreads, 8)
             F.apply(qi.x * kMirrorUnit, qi.y * kMirrorUnit, qi.z * kMirrorUnit, yix, yiy, yiz);
         }
         // squared search radius for a bilayer and for a cytoskeleton partner
-        // (for a bilayer particle the widest cutoff of its species)
+        // (for a bilayer particle the widest cutoff of its species; with MP
+        // the lipid partners' and the bilayer proteins' apart)
         const bool bi = bilayer(ti);
-        const float cl = I.mm_rcf[species(ti)] + sk;
+        const int si = species(ti);
+        const float cl = (MP ? sqrtf((float)I.mm_rc2[3 * si]) : I.mm_rcf[si]) + sk;
         const float cutL = bi ? cl * cl : cw * cw;
         const float cutP = bi ? cw * cw : cp * cp;
         const float cutD = cutP - cutL;
+        // MP: the cutoff of a partner of class c in {0, 1, 2} as
+        // cutL + c (qa + c qb), through cutP at c = 1 and cutM at c = 2
+        float qa = cutD, qb = 0.f;
+        if (MP) {
+            const float cm = fmaxf(sqrtf((float)I.mm_rc2[3 * si + 1]), sqrtf((float)I.mm_rc2[3 * si + 2])) + sk;
+            const float cutM = bi ? cm * cm : cw * cw;
+            qb = 0.5f * (cutM - cutL) - cutD;
+            qa = cutD - qb;
+        }
         // the group box's cull radius: the search cutoff, or for a group
         // without bilayer particles (a protein cell) the larger of its two
         // cutoffs
@@ -972,7 +988,8 @@ __global__ void __launch_bounds__(kPairThreads, 8)
                     const int z = (int)((unsigned)rj.z + (unsigned)inf.oz);
                     float4 w;
                     F.apply(x * kMirrorUnit, y * kMirrorUnit, z * kMirrorUnit, w.x, w.y, w.z);
-                    w.w = bilayer(rj.w & 0xff) ? 0.0f : 1.0f;
+                    const int tj = rj.w & 0xff;
+                    w.w = MP ? (tj == kLipid ? 0.0f : (bilayer(tj) ? 2.0f : 1.0f)) : (bilayer(tj) ? 0.0f : 1.0f);
                     sY[j] = w;
                     sQ[j] = (inf.row << kRowShift) | (inf.start + (j - inf.base));
                 }
@@ -1014,7 +1031,8 @@ __global__ void __launch_bounds__(kPairThreads, 8)
                             const float4 y = sY[j];
                             const float ex = y.x - yix, ey = y.y - yiy, ez = y.z - yiz;
                             const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                            if (d2 < fmaf(y.w, cutD, cutL) && j != selfj) hits |= 1u << (8 * h + u);
+                            const float cut = MP ? fmaf(y.w, fmaf(y.w, qb, qa), cutL) : fmaf(y.w, cutD, cutL);
+                            if (d2 < cut && j != selfj) hits |= 1u << (8 * h + u);
                         }
                     }
                     if (cnt - c0 < 32) hits &= (1u << (cnt - c0)) - 1u;
@@ -1159,11 +1177,15 @@ __device__ __forceinline__ void eval_list(const View& v, int q, const int* __res
             is_excluded(v, I, v.id[pi], v.id[__float_as_int(oj.w)], __float_as_int(oj.w)))
             continue;
         float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (ll && tab) {
+        if (ll && MP) {
+            // one code path for every species pair (lanes with different
+            // pairs stay converged): the pair's constants picked first
             PairC Cm = C;
-            Cm.eps = I.mm_eps[m];
-            Cm.aw = I.mm_aw[m];
-            Cm.eps2z_aw = I.mm_e2za[m];
+            if (tab) {
+                Cm.eps = I.mm_eps[m];
+                Cm.aw = I.mm_aw[m];
+                Cm.eps2z_aw = I.mm_e2za[m];
+            }
             if (zc == 4)
                 lipid_terms_f<4, S0>(Cm, dx, dy, dz, r2, oi.x, oi.y, oi.z, oj.x, oj.y, oj.z, f[0], f[1], f[2], f[3],
                                      f[4], f[5]);
@@ -1451,7 +1473,10 @@ void Ensemble::launch_pairs(bool energies, bool dump) {
         if (!list_valid) {
             tic("pair_search");
             CK(cudaMemsetAsync(d_novf_n, 0, sizeof(int), stream));
-            k_pair_search<<<g, t, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_novf, d_novf_n, ovf_cap, d_rowoff);
+            if (any_mp())
+                k_pair_search<true><<<g, t, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_novf, d_novf_n, ovf_cap, d_rowoff);
+            else
+                k_pair_search<false><<<g, t, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_novf, d_novf_n, ovf_cap, d_rowoff);
             launches++;
             CK(cudaGetLastError());
             toc();
@@ -1534,7 +1559,8 @@ void Ensemble::launch_pairs_step(bool msums) {
     if (!list_valid) {
         tic("pair_search");
         CK(cudaMemsetAsync(d_novf_n, 0, sizeof(int), stream));
-        k_pair_search<<<Ktot, kPairThreads, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_novf, d_novf_n, ovf_cap, d_rowoff);
+        k_pair_search<false><<<Ktot, kPairThreads, 0, stream>>>(v, d_nlist, d_ncnt, list_cap, d_novf, d_novf_n, ovf_cap,
+                                                                d_rowoff);
         launches++;
         CK(cudaGetLastError());
         toc();
