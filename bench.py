@@ -43,10 +43,11 @@ FLOP_PER_CANDIDATE = 9.0
 # drifts with their Cayley maps and the renormalisation, the
 # Ornstein-Uhlenbeck update with its noise scaling), counted from the
 # kernel's expressions with FMA = 2 and a division as 1: per lipid (kick 18,
-# first drift 31, O 30, second drift 42) and per point particle (3 + 3 + 9
-# + 3).  The int64 <-> FP64 conversions (about 60 per lipid) use the same
-# pipe but are not counted.
-FLOP64_PER_LIPID_STEP = 121.0
+# first drift 35 and second drift 39 with the Cayley factor's three-term
+# series and the renormalisation's exact integer norm, O 30) and per point
+# particle (3 + 3 + 9 + 3).  The int64 <-> FP64 conversions (about 60 per
+# lipid) use the same pipe but are not counted.
+FLOP64_PER_LIPID_STEP = 122.0
 FLOP64_PER_BEAD_STEP = 18.0
 # FP64 peak: the recipe's nominal GB300 figure (no measured FP64 peak exists)
 FP64_TFLOPS = 1.25
@@ -607,7 +608,7 @@ def run_reference(args, rank, world):
 
 
 # revisions of the kernels whose ncu summaries are committed under profiles/
-KERNEL_REV = {"k_pair_search": "search-v3", "k_pair_eval": "eval-v3", "k_baoa_d": "baoa-d-v3"}
+KERNEL_REV = {"k_pair_search": "search-v4", "k_pair_eval": "eval-v4", "k_baoa_d": "baoa-d-v4"}
 
 
 def ensemble_jobs(n_instances: int, steps: int):

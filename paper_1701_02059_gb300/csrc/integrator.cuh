@@ -59,10 +59,11 @@ __device__ inline void cayley(long long nq[3], const long long wq[3], T h) {
     nq[2] += V::grid(k * (b2 + c2));
 }
 
-// Unit-norm correction n <- n (1 - delta/2), delta = |n|^2 - 1, first order
-// (|delta| stays at the rounding level, ~1e-9).
-__device__ inline void renormalise(long long nq[3], float) {
-    // exact |n_q|^2 - 2^80 in 128-bit integer arithmetic
+// |n_q|^2 - 2^80 for a director on the 2^-40 grid, exact in 128-bit integer
+// arithmetic (the excess of its squared length over unit length in units of
+// 2^-80); 0 when it is far from unit length (|excess| >= 2^63, not reached
+// in practice: the correction is then skipped).
+__device__ inline long long norm2_excess(const long long nq[3]) {
     unsigned long long H = 0, L = 0;
     for (int a = 0; a < 3; a++) {
         unsigned long long u = (unsigned long long)(nq[a] < 0 ? -nq[a] : nq[a]);
@@ -71,9 +72,19 @@ __device__ inline void renormalise(long long nq[3], float) {
         H += hi + (L2 < L ? 1ull : 0ull);
         L = L2;
     }
-    long long hd = (long long)H - (1ll << 16);     // multiples of 2^64
-    if (hd != 0 && hd != -1) return;               // far from unit length: leave (not reached in practice)
-    long long D = (long long)L;                    // exact when |D| < 2^63
+    const long long hd = (long long)H - (1ll << 16);     // multiples of 2^64
+    const long long D = (long long)L;
+    // exact when the 128-bit excess fits in int64
+    if (hd == 0 && D >= 0) return D;
+    if (hd == -1 && D < 0) return D;
+    return 0;
+}
+
+// Unit-norm correction n <- n (1 - delta/2), delta = |n|^2 - 1, first order
+// (|delta| stays at the rounding level, ~1e-9).
+__device__ inline void renormalise(long long nq[3], float) {
+    const long long D = norm2_excess(nq);
+    if (D == 0) return;
     float delta = ll_to_float(D) * 8.271806125530277e-25f;   // 2^-80
     for (int a = 0; a < 3; a++) nq[a] -= float_to_grid(Num<float>::st(nq[a]) * 0.5f * delta);
 }
@@ -221,10 +232,19 @@ __device__ inline void kick_grid(long long vq[3], long long wq[3], const double 
 // velocity stays perpendicular to the director (the kicks and the noise are
 // projected onto the plane normal to it, and each rotation turns the
 // director about it), so a x B = a (a.N) - |a|^2 N = -|a|^2 N up to rounding.
+// The factor 2/(1 + |a|^2): for |a|^2 <= 2^-14 (every rotation of a few
+// degrees or less per half step) the alternating series
+// 2 (1 - aa + aa^2 - aa^3), whose truncation error 2 aa^4 / (1 + aa) is
+// below 2^-55 relative, i.e. within the FP64 rounding of the quotient, in
+// three fused multiply-adds instead of a division; larger |a|^2 divide.
+__device__ inline double cayley_factor(double aa) {
+    if (aa <= 6.103515625e-05) return fma(aa, fma(aa, fma(-2.0, aa, 2.0), -2.0), 2.0);
+    return 2.0 / (1.0 + aa);
+}
 __device__ inline void cayley_grid(const double N[3], const double W[3], const Inst& I, long long d[3]) {
     const double a0 = I.ca_d * W[0], a1 = I.ca_d * W[1], a2 = I.ca_d * W[2];
     const double aa = a0 * a0 + a1 * a1 + a2 * a2;
-    const double k = 2.0 / (1.0 + aa);
+    const double k = cayley_factor(aa);
     const double b0 = a1 * N[2] - a2 * N[1], b1 = a2 * N[0] - a0 * N[2], b2 = a0 * N[1] - a1 * N[0];
     d[0] = rg(k * fma(-aa, N[0], b0));
     d[1] = rg(k * fma(-aa, N[1], b1));
@@ -295,8 +315,10 @@ __device__ inline void baoa_d_body(const View& v, const View& o, int p, const lo
         long long d[3];
         cayley_grid(Nd, Wd, I, d);
         for (int a = 0; a < 3; a++) { nq[a] += d[a]; Nd[a] = gd(nq[a]); }
-        // unit-norm correction n <- n (1 - delta/2), delta = |n|^2 - 1
-        const double hdelta = 0.5 * ((Nd[0] * Nd[0] + Nd[1] * Nd[1] + Nd[2] * Nd[2]) * 8.271806125530277e-25 - 1.0);
+        // unit-norm correction n <- n (1 - delta/2), delta = |n|^2 - 1, with
+        // |N|^2 - 2^80 exact in 128-bit integer arithmetic (integer pipes)
+        // and delta/2 = that 2^-81, one conversion and one product
+        const double hdelta = gd(norm2_excess(nq)) * 4.1359030627651384e-25;   // 2^-81
         for (int a = 0; a < 3; a++) nq[a] -= rg(Nd[a] * hdelta);
     }
     for (int a = 0; a < 3; a++) { o.xq[a * N + p] = xq[a]; o.vq[a * N + p] = vq[a]; }
