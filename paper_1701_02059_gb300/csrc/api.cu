@@ -186,6 +186,7 @@ static Inst make_inst(const Params& P) {
     I.aw = (float)(1.5707963267948966 / (P.rc_lipid - two_sixth * P.sigma));
     I.eps2z_aw = (float)(P.eps * 2.0 * P.zeta * (1.5707963267948966 / (P.rc_lipid - two_sixth * P.sigma)));
     I.skin = P.skin;
+    I.skinf = (float)P.skin;
     for (int a = 0; a < 3; a++) {
         I.periodic[a] = P.periodic[a];
         I.box[a] = P.periodic[a] ? P.box[a] : 0.0;

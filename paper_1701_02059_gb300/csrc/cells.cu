@@ -1144,10 +1144,11 @@ __device__ inline void warp_bitonic_u32(unsigned (&r)[4], int lane) {
 }
 
 // Per-cell quantities read back from the gathered mirrors: one warp per cell
-// computes the cell radius R_k = max |x - c_k| (FP32 with the FP64
-// definition inside a band), the pair kernel's cell normal (mean lipid
-// director, unit; +z without lipid direction) and, in each tile of 128
-// particles, every particle's rank along the tile's longer tangent extent.
+// computes the squared cell radius R_k^2 = max |x - c_k|^2 (FP32 with the
+// FP64 definition inside a band; left in R for k_cell_radius), the pair
+// kernel's cell normal (mean bilayer director, unit; +z without one) and, in
+// each tile of 128 particles, every particle's rank along the tile's longer
+// tangent extent.  rmax_bits: each instance's largest R_k^2 (bit pattern).
 // Launched with 256 threads (8 warps, one cell each).
 __global__ void __launch_bounds__(256, 6) k_cell_props(View v, unsigned long long* __restrict__ rmax_bits /* [B] */) {
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1188,11 +1189,11 @@ __global__ void __launch_bounds__(256, 6) k_cell_props(View v, unsigned long lon
     unsigned long long bb = (unsigned long long)__double_as_longlong(best);
     for (int off = 16; off; off >>= 1) bb = max(bb, (unsigned long long)__shfl_xor_sync(0xffffffffu, bb, off));
     best = __longlong_as_double((long long)bb);
+    // the squared radius for now (k_cell_radius takes the square roots, one
+    // cell per thread), and each instance's largest square
     if (lane == 0) {
-        const double R = __dsqrt_rn(best);
-        v.R[k] = R;
-        v.Rf[k] = (float)R;
-        atomicMax(&rmax_bits[b], (unsigned long long)__double_as_longlong(R));
+        v.R[k] = best;
+        atomicMax(&rmax_bits[b], bb);
     }
     // pair-kernel frame
     const float nn = sqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
@@ -1276,6 +1277,17 @@ __global__ void k_mirrors(View v) {
     v.mor[q] = no;
 }
 
+// Cell radii R_k = sqrt(R_k^2) from k_cell_props and their FP32 copies, one
+// thread per cell: an FP64 instruction occupies the FP64 pipe for a whole
+// warp, so 32 cells share each square root instead of one.
+__global__ void k_cell_radius(View v) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= v.Ktot) return;
+    const double R = __dsqrt_rn(v.R[k]);
+    v.R[k] = R;
+    v.Rf[k] = (float)R;
+}
+
 // ============================================================== neighbouring cells
 // nbr(k) = { j : |c_k - c_j| < ((R_k + R_j) + r_s + 2 skin)(1 + 1e-12) },
 // evaluated exactly as the FP64 definition for candidates within a band of
@@ -1285,7 +1297,7 @@ constexpr float kBandA = 2e-3f;
 // exact neighbouring-cell test of (k, j), FP32 with a margin outside the
 // band and the definition's FP64 operations inside it
 __device__ inline bool adj_test(const View& v, const Inst& I, int k, int j, double Rk, float Rkf, float df,
-                                long long cx, long long cy, long long cz, double tail, float tailf) {
+                                long long cx, long long cy, long long cz, float tailf) {
     // FP32 prefilter: radii rounded to FP32 differ from the definition's
     // FP64 sum by far less than the band
     const float tf = (Rkf + v.Rf[j]) + tailf;
@@ -1319,18 +1331,25 @@ __global__ void __launch_bounds__(256, 6) k_adj_warp(View v, const unsigned long
     const double Rk = v.R[k];
     const float Rkf = v.Rf[k];
     const long long cx = v.cq[k], cy = v.cq[(size_t)v.Ktot + k], cz = v.cq[(size_t)2 * v.Ktot + k];
-    const double tail = (I.rs) + (I.skin + I.skin);
-    const float tailf = (float)tail;
+    // the cell's scalars in FP32 (every lane of the warp computes them, and
+    // an FP64 operation costs a full warp's turn on the FP64 pipe): they only
+    // set the FP32 prefilter and the search reach, whose band kBandA is far
+    // wider than their rounding
+    const float tailf = I.rsf + 2.0f * I.skinf;
     if (lane == 0) rown[wb] = 0;
     __syncwarp();
-    const float reach_own = (float)(Rk + __longlong_as_double((long long)rmax_bits[b]) + I.rs + 2.0 * I.skin) + kBandA;
+    auto reach_of = [&](float Rmaxf) { return ((Rkf + Rmaxf) + tailf) + kBandA; };
+    // the largest radius of the set from its largest square (FP32: it only
+    // sets the reach)
+    auto rmax_of = [&](int s) { return sqrtf((float)__longlong_as_double((long long)rmax_bits[s])); };
+    const float reach_own = reach_of(rmax_of(b));
     float rho = reach_own - kBandA;
     // the centroids of one set through its own grid G: every centroid within
     // the reach R_k + R_max(G) + r_s + 2 skin is tested with the exact rule;
     // own: the set of cell k, whose nearest non-neighbour bounds the
     // E-step's certificate (the other set's cells join the row only)
-    auto scan = [&](const Inst& G, double Rmax, bool own) {
-        const float reach = (float)(Rk + Rmax + I.rs + 2.0 * I.skin) + kBandA;
+    auto scan = [&](const Inst& G, float Rmaxf, bool own) {
+        const float reach = reach_of(Rmaxf);
         float p[3];
         int g[3];
         g[0] = grid_coord(cx, G, 0, p[0]);
@@ -1392,7 +1411,7 @@ __global__ void __launch_bounds__(256, 6) k_adj_warp(View v, const unsigned long
                     const float dx = axis_dist(p[0], c.x, G, 0), dy = axis_dist(p[1], c.y, G, 1),
                                 dz = axis_dist(p[2], c.z, G, 2);
                     const float df = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                    if (adj_test(v, I, k, j, Rk, Rkf, df, cx, cy, cz, tail, tailf)) {
+                    if (adj_test(v, I, k, j, Rk, Rkf, df, cx, cy, cz, tailf)) {
                         const int at = atomicAdd(&rown[wb], 1);
                         if (at < kAdjRow) row[wb][at] = j;
                     } else if (own) {
@@ -1402,9 +1421,8 @@ __global__ void __launch_bounds__(256, 6) k_adj_warp(View v, const unsigned long
             }
         }
     };
-    scan(I, __longlong_as_double((long long)rmax_bits[b]), true);
-    if (I.partner >= 0)
-        scan(v.inst[I.partner], __longlong_as_double((long long)rmax_bits[I.partner]), false);
+    scan(I, rmax_of(b), true);
+    if (I.partner >= 0) scan(v.inst[I.partner], rmax_of(I.partner), false);
     for (int off = 16; off; off >>= 1) rho = fminf(rho, __shfl_xor_sync(0xffffffffu, rho, off));
     __syncwarp();
     int n = rown[wb];
@@ -1594,7 +1612,8 @@ void Ensemble::finish_cells() {
     CK(cudaMemsetAsync(d_rmax, 0, sizeof(unsigned long long) * B, stream));
     k_gather_particles<<<nblk(N, 256), 256, 0, stream>>>(nv, ov, d_perm, d_cell_new, d_xref);
     k_cell_props<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(nv, d_rmax);
-    launches += 2;
+    k_cell_radius<<<nblk(Ktot, 256), 256, 0, stream>>>(nv);
+    launches += 3;
     CK(cudaGetLastError());
     // neighbouring cells
     k_adj_warp<<<nblk((long long)Ktot * 32, 256), 256, 0, stream>>>(nv, d_rmax, d_adjcount, d_rho, d_adjpad);
