@@ -224,6 +224,7 @@ static Inst make_inst(const Params& P) {
         I.mm_aw[q] = (float)w;
         I.mm_e2za[q] = (float)(e * 2.0 * P.zeta * w);
         const float rcf = std::sqrt((float)I.mm_rc2[q]);
+        I.mm_rcp[q] = rcf;
         I.mm_lo[q] = (rcf - kCutBand) * (rcf - kCutBand);
         I.mm_hi[q] = (rcf + kCutBand) * (rcf + kCutBand);
         I.rs = std::max(I.rs, rc);

@@ -1518,7 +1518,7 @@ __global__ void k_displacement(View v, const long long* __restrict__ xref, unsig
         float d = ll_to_float(minimg_q(v.xq[a * N + p] - xref[a * N + p], I.boxq[a], I.periodic[a])) * (float)kGridInv;
         d2 = fmaf(d, d, d2);
     }
-    float s = (float)I.skin * (1.0f - 1e-5f);
+    float s = I.skinf * (1.0f - 1e-5f);
     if (d2 > s * s) atomicOr(flag, 1u);
 }
 

@@ -823,7 +823,7 @@ __global__ void __launch_bounds__(kPairThreads, 8)
     const AdjDesc* __restrict__ row = v.adjd + (size_t)k * kAdjRow;
     const int a1 = min(v.adjn[k], kAdjRow);
     const size_t N = v.N;
-    const float sk = 2.0f * (float)I.skin + kFilterBand;
+    const float sk = 2.0f * I.skinf + kFilterBand;
     const float rsb = I.rsf + sk, rs2f = rsb * rsb;
     const float cw = sqrtf(I.rc2f_wca) + sk, cp = sqrtf(I.rc2f_pp) + sk;
     unsigned phase = 0;
@@ -929,7 +929,7 @@ __global__ void __launch_bounds__(kPairThreads, 8)
         // the lipid partners' and the bilayer proteins' apart)
         const bool bi = bilayer(ti);
         const int si = species(ti);
-        const float cl = (MP ? sqrtf((float)I.mm_rc2[3 * si]) : I.mm_rcf[si]) + sk;
+        const float cl = (MP ? I.mm_rcp[3 * si] : I.mm_rcf[si]) + sk;
         const float cutL = bi ? cl * cl : cw * cw;
         const float cutP = bi ? cw * cw : cp * cp;
         const float cutD = cutP - cutL;
@@ -937,7 +937,7 @@ __global__ void __launch_bounds__(kPairThreads, 8)
         // cutL + c (qa + c qb), through cutP at c = 1 and cutM at c = 2
         float qa = cutD, qb = 0.f;
         if (MP) {
-            const float cm = fmaxf(sqrtf((float)I.mm_rc2[3 * si + 1]), sqrtf((float)I.mm_rc2[3 * si + 2])) + sk;
+            const float cm = fmaxf(I.mm_rcp[3 * si + 1], I.mm_rcp[3 * si + 2]) + sk;
             const float cutM = bi ? cm * cm : cw * cw;
             qb = 0.5f * (cutM - cutL) - cutD;
             qa = cutD - qb;

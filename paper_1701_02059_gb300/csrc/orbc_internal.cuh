@@ -104,12 +104,13 @@ struct Inst {
     // the lipid potential's well depth and cutoff of each pair (the
     // lipid-lipid entry is eps and rc), the FP32 constants (eps, aw,
     // eps 2 zeta aw), the squared FP64 cutoff and the FP32 band of the
-    // inclusion decision; mm_rcf[s] is the largest FP32 cutoff of species s.
+    // inclusion decision; mm_rcp the FP32 cutoff of each pair and mm_rcf[s]
+    // the largest one of species s.
     // has_mp: the instance holds band-3 or glycophorin particles;
     // bonded_bilayer: some bilayer particle has a bond (an anchor), so a
     // bilayer-cytoskeleton pair may be excluded from the WCA term.
     int has_mp, bonded_bilayer;
-    float mm_eps[9], mm_aw[9], mm_e2za[9], mm_lo[9], mm_hi[9], mm_rcf[3];
+    float mm_eps[9], mm_aw[9], mm_e2za[9], mm_lo[9], mm_hi[9], mm_rcf[3], mm_rcp[9];
     double mm_eps_d[9], mm_rc_d[9], mm_rc2[9];
 };
 
