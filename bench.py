@@ -657,7 +657,8 @@ def run_ensemble(n_instances=64, steps=500, budget_gb=120.0, max_steps=500):
             "particles_per_cell": round(ppc, 1),
             "tuned_per_size_class": {f"class {c}": {"particles_per_cell": round(v[0], 1), "eval_ctas": v[1]}
                                      for c, v in sorted(tuned.items())},
-            "batched": {k: round(sb[k], 4) for k in keep} | {"gpu_launches": sb["gpu_launches"]},
+            "batched": {k: round(sb[k], 4) for k in keep} | {"gpu_launches": sb["gpu_launches"]}
+            | {k: sb[k] for k in ("admit_s", "run_s", "retire_s", "repack_s", "batched_steps")},
             "plain": {k: round(sp[k], 4) for k in keep},
             "p99_speedup": round(sp["p99_s"] / sb["p99_s"], 3),
             "throughput_speedup": round(sb["particle_steps_per_s"] / sp["particle_steps_per_s"], 3),
