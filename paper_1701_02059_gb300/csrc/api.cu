@@ -53,7 +53,7 @@ void Ensemble::free_all() {
     for (void* p : allocs_) cudaFreeAsync(p, stream);
     allocs_.clear();
     bytes_ = 0;
-    for (int* p : scan_tmp_) if (p) cudaFree(p);
+    for (int* p : scan_tmp_) if (p) cudaFreeAsync(p, stream);
     scan_tmp_.clear();
     scan_tmp_n_.clear();
     if (ev0_) { cudaEventDestroy(ev0_); ev0_ = nullptr; }
@@ -506,8 +506,10 @@ void Ensemble::setup(const std::vector<const HostInstance*>& list) {
             parallel_for(h.n, [&](long long i0, long long i1) {
                 for (long long i = i0; i < i1; i++) by_id[h.id[i]] = (int)i;
             });
-            // the lipid slots in id order: counts per chunk of ids, then fill
-            const int nch = 64;
+            // the member slots in id order: counts per chunk of ids, then
+            // fill (one chunk per 64k ids, at most 64: a small instance runs
+            // inline instead of paying for host threads)
+            const int nch = (int)std::min<long long>(64, std::max<long long>(1, (long long)h.n >> 16));
             const long long per = ((long long)h.n + nch - 1) / nch;
             std::vector<long long> cnt(nch + 1, 0);
             parallel_for(nch, [&](long long c0, long long c1) {

@@ -59,8 +59,10 @@ void Ensemble::scan_exclusive(const int* in, int* out, long long n) {
     while (true) {
         if ((int)scan_tmp_.size() <= level) { scan_tmp_.push_back(nullptr); scan_tmp_n_.push_back(0); }
         if (scan_tmp_n_[level] < 2 * m + 2) {
-            if (scan_tmp_[level]) cudaFree(scan_tmp_[level]);
-            CK(cudaMalloc(&scan_tmp_[level], sizeof(int) * (2 * m + 2)));
+            // stream-ordered pool memory: no device-wide synchronisation, as
+            // a plain allocation and free would have
+            if (scan_tmp_[level]) CK(cudaFreeAsync(scan_tmp_[level], stream));
+            CK(cudaMallocAsync(&scan_tmp_[level], sizeof(int) * (2 * m + 2), stream));
             scan_tmp_n_[level] = 2 * m + 2;
         }
         lv.push_back({scan_tmp_[level], m});
