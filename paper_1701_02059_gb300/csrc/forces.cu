@@ -810,6 +810,9 @@ __global__ void __launch_bounds__(kPairThreads, 8)
     __shared__ alignas(16) float4 sY[kSearchStage];
     __shared__ int sQ[kSearchStage];
     __shared__ alignas(16) unsigned short cand[kPairThreads / 32][kSearchStage];
+    // each lane's own particle's position in its warp's candidate list (the
+    // self pair is removed once per 32 candidates instead of per test)
+    __shared__ unsigned short spos[kPairThreads / 32][32];
     __shared__ SNbr nb[kMaxNbr];
     __shared__ int s_cnt[kPairThreads];
     __shared__ unsigned long long bar;
@@ -998,6 +1001,10 @@ __global__ void __launch_bounds__(kPairThreads, 8)
 
             if (wactive) {
                 int cnt = 0;
+                spos[warp][lane] = 0xffffu;
+                __syncwarp();
+                // staged index of lane 0's own particle (own cell, this pass)
+                const int self0 = sself + (it0 + igrp * gs - cs);
                 for (int c0 = 0; c0 < total; c0 += nsplit * 32) {
                     const int j = c0 + lane * nsplit + jsplit;
                     bool in = false;
@@ -1009,12 +1016,19 @@ __global__ void __launch_bounds__(kPairThreads, 8)
                         in = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < rcull2;
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, in);
-                    if (in) cand[warp][cnt + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)j;
+                    if (in) {
+                        const int at = cnt + __popc(bal & ((1u << lane) - 1u));
+                        cand[warp][at] = (unsigned short)j;
+                        // the own particle of lane t of this group
+                        const int t = j - self0;
+                        if (sslo >= 0 && j >= sslo && j < sshi && t >= 0 && t < gs) spos[warp][t] = (unsigned short)at;
+                    }
                     cnt += __popc(bal);
                 }
                 // pad to a multiple of 32 with a valid staged index
                 if (cnt + lane < ((cnt + 31) & ~31)) cand[warp][cnt + lane] = 0;
                 __syncwarp();
+                const int sp = selfj >= 0 ? (int)spos[warp][lane] : -1;   // 0xffff: not in this warp's list
                 // every lane tests the same 32 candidates (broadcast reads)
                 // into a bit mask, then writes its hits; the padding of the
                 // candidate list past cnt is never read as a hit
@@ -1032,10 +1046,11 @@ __global__ void __launch_bounds__(kPairThreads, 8)
                             const float ex = y.x - yix, ey = y.y - yiy, ez = y.z - yiz;
                             const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
                             const float cut = MP ? fmaf(y.w, fmaf(y.w, qb, qa), cutL) : fmaf(y.w, cutD, cutL);
-                            if (d2 < cut && j != selfj) hits |= 1u << (8 * h + u);
+                            if (d2 < cut) hits |= 1u << (8 * h + u);
                         }
                     }
                     if (cnt - c0 < 32) hits &= (1u << (cnt - c0)) - 1u;
+                    if ((unsigned)(sp - c0) < 32u) hits &= ~(1u << (sp - c0));
                     while (hits) {
                         const int u = __ffs(hits) - 1;
                         hits &= hits - 1u;
