@@ -608,7 +608,7 @@ def run_reference(args, rank, world):
 
 
 # revisions of the kernels whose ncu summaries are committed under profiles/
-KERNEL_REV = {"k_pair_search": "search-v6", "k_pair_eval": "eval-v4", "k_baoa_d": "baoa-d-v4"}
+KERNEL_REV = {"k_pair_search": "search-v7", "k_pair_eval": "eval-v4", "k_baoa_d": "baoa-d-v4"}
 
 
 def ensemble_jobs(n_instances: int, steps: int):

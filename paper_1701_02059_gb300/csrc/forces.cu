@@ -807,6 +807,7 @@ __global__ void __launch_bounds__(kPairThreads, 8)
     // sY: staged mirrors (int4 by the bulk copy), then in the tangent frame
     //     (FP32), w = 0 for a bilayer particle and 1 for a cytoskeleton protein
     // sQ: the list entry of each staged particle
+    // cand: per warp, the byte offsets (16 j) in sY of the culled candidates
     __shared__ alignas(16) float4 sY[kSearchStage];
     __shared__ int sQ[kSearchStage];
     __shared__ alignas(16) unsigned short cand[kPairThreads / 32][kSearchStage];
@@ -1018,7 +1019,7 @@ __global__ void __launch_bounds__(kPairThreads, 8)
                     const unsigned bal = __ballot_sync(0xffffffffu, in);
                     if (in) {
                         const int at = cnt + __popc(bal & ((1u << lane) - 1u));
-                        cand[warp][at] = (unsigned short)j;
+                        cand[warp][at] = (unsigned short)(j << 4);   // byte offset of sY[j]
                         // the own particle of lane t of this group
                         const int t = j - self0;
                         if (sslo >= 0 && j >= sslo && j < sshi && t >= 0 && t < gs) spos[warp][t] = (unsigned short)at;
@@ -1033,6 +1034,7 @@ __global__ void __launch_bounds__(kPairThreads, 8)
                 // into a bit mask, then writes its hits; the padding of the
                 // candidate list past cnt is never read as a hit
                 static_assert(kSearchStage % 32 == 0, "candidate lists are read 32 at a time");
+                static_assert(kSearchStage * 16 <= 65536, "candidate byte offsets fit 16 bits");
                 for (int c0 = 0; c0 < cnt; c0 += 32) {
                     unsigned hits = 0u;
 #pragma unroll
@@ -1041,8 +1043,8 @@ __global__ void __launch_bounds__(kPairThreads, 8)
                         const unsigned cw8[4] = {c8.x, c8.y, c8.z, c8.w};
 #pragma unroll
                         for (int u = 0; u < 8; u++) {
-                            const int j = (int)((cw8[u >> 1] >> (16 * (u & 1))) & 0xffffu);
-                            const float4 y = sY[j];
+                            const unsigned off = (cw8[u >> 1] >> (16 * (u & 1))) & 0xffffu;
+                            const float4 y = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(sY) + off);
                             const float ex = y.x - yix, ey = y.y - yiy, ez = y.z - yiz;
                             const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
                             const float cut = MP ? fmaf(y.w, fmaf(y.w, qb, qa), cutL) : fmaf(y.w, cutD, cutL);
@@ -1054,7 +1056,7 @@ __global__ void __launch_bounds__(kPairThreads, 8)
                     while (hits) {
                         const int u = __ffs(hits) - 1;
                         hits &= hits - 1u;
-                        const int e = sQ[cand[warp][c0 + u]];
+                        const int e = sQ[cand[warp][c0 + u] >> 4];
                         const int pos = atomicAdd(&s_cnt[r], 1);
                         if (pos < cap) {
                             nlist[(size_t)pos * N + qi_idx] = e;
