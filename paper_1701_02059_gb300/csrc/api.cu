@@ -201,6 +201,17 @@ static Inst make_inst(const Params& P) {
     I.st_d = std::sqrt(std::max(0.0, (1.0 - ct * ct) * P.kT / P.mass));
     I.sr_d = std::sqrt(std::max(0.0, (1.0 - cr * cr) * P.kT / P.inertia));
     I.hm8_d = std::ldexp(I.h_m_d, 8); I.hi8_d = std::ldexp(I.h_i_d, 8);
+    // the double as an integer times a power of two (exact): x = f 2^e,
+    // f in [1/2, 1), m = f 2^53, s = 53 - e
+    auto fix = [](double x, unsigned long long& m, int& s) {
+        int e = 0;
+        const double f = std::frexp(x, &e);
+        m = (unsigned long long)std::ldexp(f, 53);
+        s = 53 - e;
+        if (!(x > 0) || s < 1 || s > 127) { m = 0; s = 1; }   // not reached for valid dt, mass
+    };
+    fix(I.hm8_d, I.hm8_m, I.hm8_s);
+    fix(I.hdt_d, I.hdt_m, I.hdt_s);
     I.st40_d = std::ldexp(I.st_d, 40); I.sr40_d = std::ldexp(I.sr_d, 40); I.ca_d = std::ldexp(0.5 * h, -40);
     const double noise_scale = 3.4641016151377544 * 1.16415321826934814453125e-10;   // sqrt(12) 2^-33
     I.stn_d = I.st40_d * noise_scale;

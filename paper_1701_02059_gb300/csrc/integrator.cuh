@@ -213,11 +213,38 @@ __device__ inline void baoa_body(const View& v, const View& o, int p, const long
 __device__ inline double gd(long long q) { return __ll2double_rn(q); }
 __device__ inline long long rg(double x) { return __double2ll_rn(x); }
 
+// round(q m 2^-s) to the nearest integer, ties to even, from the exact
+// 128-bit product (1 <= s <= 127, |q| m < 2^(64 + s)): the same rounding as
+// __double2ll_rn of the exact product, so a kick or drift computed this way
+// rounds once where the FP64 product would round to 53 bits first; integer
+// pipes only.
+__device__ inline long long mul_round(long long q, unsigned long long m, int s) {
+    const unsigned long long a = (unsigned long long)(q < 0 ? -q : q);
+    const unsigned long long lo = a * m, hi = __umul64hi(a, m);
+    unsigned long long r;
+    bool up;
+    if (s < 64) {
+        r = (hi << (64 - s)) | (lo >> s);
+        const unsigned long long rem = lo & ((1ull << s) - 1ull), half = 1ull << (s - 1);
+        up = rem > half || (rem == half && (r & 1ull));
+    } else if (s == 64) {
+        r = hi;
+        up = lo > (1ull << 63) || (lo == (1ull << 63) && (r & 1ull));
+    } else {
+        const int t = s - 64;
+        r = hi >> t;
+        const unsigned long long rem = hi & ((1ull << t) - 1ull), half = 1ull << (t - 1);
+        up = rem > half || (rem == half && (lo != 0 || (r & 1ull)));
+    }
+    r += up ? 1ull : 0ull;
+    return q < 0 ? -(long long)r : (long long)r;
+}
+
 // Half kick(s): v += round(h_m 2^8 F), w += round(h_i 2^8 (T - (T.n) n)) in
 // grid units, with N the director in grid units.
 __device__ inline void kick_grid(long long vq[3], long long wq[3], const double N[3], bool lipid, const Inst& I,
                                  int reps, const long long F[3], const long long Tq[3]) {
-    for (int a = 0; a < 3; a++) vq[a] += reps * rg(I.hm8_d * gd(F[a]));
+    for (int a = 0; a < 3; a++) vq[a] += reps * mul_round(F[a], I.hm8_m, I.hm8_s);
     if (lipid) {
         const double T0 = gd(Tq[0]), T1 = gd(Tq[1]), T2 = gd(Tq[2]);
         const double u = (T0 * N[0] + T1 * N[1] + T2 * N[2]) * 8.271806125530277e-25;   // (T.N) 2^-80
@@ -278,7 +305,7 @@ __device__ inline void baoa_d_body(const View& v, const View& o, int p, const lo
     double Vd[3], Wd[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < 3; a++) {
         Vd[a] = gd(vq[a]);
-        xq[a] += rg(I.hdt_d * Vd[a]);
+        xq[a] += mul_round(vq[a], I.hdt_m, I.hdt_s);
     }
     if (lipid) {
         for (int a = 0; a < 3; a++) Wd[a] = gd(wq[a]);
@@ -292,11 +319,7 @@ __device__ inline void baoa_d_body(const View& v, const View& o, int p, const lo
     const uint2 key = make_uint2((unsigned)I.seed, (unsigned)(I.seed >> 32) ^ I.instance);
     const uint4 w0 = philox4x32_10(make_uint4(id, (unsigned)step, (unsigned)(step >> 32), 0u), key);
     const double xi[3] = {noise_int(w0.x), noise_int(w0.y), noise_int(w0.z)};
-    for (int a = 0; a < 3; a++) {
-        const long long d = rg(fma(I.ct_m1_d, Vd[a], I.stn_d * xi[a]));
-        vq[a] += d;
-        Vd[a] = gd(vq[a]);
-    }
+    for (int a = 0; a < 3; a++) vq[a] += rg(fma(I.ct_m1_d, Vd[a], I.stn_d * xi[a]));
     if (lipid) {
         const uint4 w1 = philox4x32_10(make_uint4(id, (unsigned)step, (unsigned)(step >> 32), 1u), key);
         // the noise scaled by sr first: its projection is linear
@@ -310,7 +333,7 @@ __device__ inline void baoa_d_body(const View& v, const View& o, int p, const lo
         }
     }
     // A
-    for (int a = 0; a < 3; a++) xq[a] += rg(I.hdt_d * Vd[a]);
+    for (int a = 0; a < 3; a++) xq[a] += mul_round(vq[a], I.hdt_m, I.hdt_s);
     if (lipid) {
         long long d[3];
         cayley_grid(Nd, Wd, I, d);

@@ -82,6 +82,11 @@ struct Inst {
     // torque at 2^-32 to a grid increment at 2^-40), st 2^40 and sr 2^40,
     // and dt/4 2^-40 (half the Cayley rotation vector from w in grid units)
     double hm8_d, hi8_d, st40_d, sr40_d, ca_d;
+    // h_m 2^8 and dt/2 as exact integer fixed point, m 2^-s (m < 2^54): the
+    // translational kick and the drifts multiply the int64 state by them
+    // exactly and round once
+    unsigned long long hm8_m, hdt_m;
+    int hm8_s, hdt_s;
     // st and sr 2^40 times the noise's scale sqrt(12) 2^-33 (multiplying the
     // noise's exact integer part)
     double stn_d, srn_d;
