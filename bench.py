@@ -45,13 +45,14 @@ FLOP_PER_CANDIDATE = 9.0
 # kernel's expressions with FMA = 2 and a division as 1: per lipid (the
 # angular kick 15, first drift's Cayley map 32 and second drift's 36 with the
 # Cayley factor's three-term series and the renormalisation's exact integer
-# norm, O 30) and per point particle (the O step's 9).  The translational
-# kick and the drifts are exact 128-bit integer products of the int64 state
-# with the FP64 constants (integer pipes, one rounding) and are not FP64
-# flops; the int64 <-> FP64 conversions (about 50 per lipid) use the FP64
-# pipe but are not counted.
-FLOP64_PER_LIPID_STEP = 113.0
-FLOP64_PER_BEAD_STEP = 9.0
+# norm, the angular Ornstein-Uhlenbeck update 21); a point particle has none.
+# The translational kick, the drifts and the velocity's Ornstein-Uhlenbeck
+# update are exact 128-bit integer products (and a sum of two) of the int64
+# state with the FP64 constants (integer pipes, one rounding) and are not
+# FP64 flops; the int64 <-> FP64 conversions (about 40 per lipid) use the
+# FP64 pipe but are not counted.
+FLOP64_PER_LIPID_STEP = 104.0
+FLOP64_PER_BEAD_STEP = 0.0
 # FP64 peak: the recipe's nominal GB300 figure (no measured FP64 peak exists)
 FP64_TFLOPS = 1.25
 # algorithmic HBM bytes of one step per particle (cells rebuilt every step):
@@ -611,7 +612,7 @@ def run_reference(args, rank, world):
 
 
 # revisions of the kernels whose ncu summaries are committed under profiles/
-KERNEL_REV = {"k_pair_search": "search-v7", "k_pair_eval": "eval-v4", "k_baoa_d": "baoa-d-v5"}
+KERNEL_REV = {"k_pair_search": "search-v7", "k_pair_eval": "eval-v4", "k_baoa_d": "baoa-d-v6"}
 
 
 def ensemble_jobs(n_instances: int, steps: int):

@@ -62,8 +62,9 @@ typedef enum {
 typedef enum {
     ORBC_F32_FORCE_F64_STATE = 0,  /* FP32 pair/bond forces; FP64 integrator increments (angular kicks,
                                       Ornstein-Uhlenbeck update, Cayley map, renormalisation; the
-                                      translational kick and the drifts as exact integer products of the
-                                      int64 state with the FP64 constants, rounded once) and FP64
+                                      translational kick, the drifts and the velocity's Ornstein-Uhlenbeck
+                                      update as exact integer products of the int64 state with the FP64
+                                      constants, rounded once) and FP64
                                       per-particle energy/virial partials                               */
     ORBC_F64_ALL = 1,              /* FP64 pair/bond forces and FP64 integrator increments             */
     ORBC_F32_FORCE_F32_STEP = 2    /* FP32 pair/bond forces and FP32 integrator increments (rounded onto

@@ -216,6 +216,21 @@ static Inst make_inst(const Params& P) {
     const double noise_scale = 3.4641016151377544 * 1.16415321826934814453125e-10;   // sqrt(12) 2^-33
     I.stn_d = I.st40_d * noise_scale;
     I.srn_d = I.sr40_d * noise_scale;
+    // signed: ct_m1 = expm1(-gamma dt) <= 0; a zero constant takes the other's
+    // scale (its product vanishes)
+    auto fix_s = [&](double x, long long& m, int& s) {
+        unsigned long long u = 0;
+        fix(std::fabs(x), u, s);
+        m = x < 0 ? -(long long)u : (long long)u;
+    };
+    fix_s(I.ct_m1_d, I.ctm1_m, I.ctm1_s);
+    fix_s(I.stn_d, I.stn_m, I.stn_s);
+    if (I.ctm1_m == 0) I.ctm1_s = I.stn_s;
+    if (I.stn_m == 0) I.stn_s = I.ctm1_s;
+    // the 128-bit sum holds |v| < 2^52 grid units times a 53-bit mantissa
+    // shifted by up to 21 bits, or a 33-bit noise integer times one shifted
+    // by up to 40
+    I.ou_int = (I.stn_s <= I.ctm1_s) ? (I.ctm1_s - I.stn_s <= 40) : (I.stn_s - I.ctm1_s <= 21);
     I.h_m = (float)I.h_m_d; I.h_i = (float)I.h_i_d; I.hdt = (float)I.hdt_d;
     I.ct_m1 = (float)I.ct_m1_d; I.cr_m1 = (float)I.cr_m1_d; I.st = (float)I.st_d; I.sr = (float)I.sr_d;
     I.mass = P.mass; I.inertia = P.inertia;

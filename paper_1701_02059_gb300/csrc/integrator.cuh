@@ -278,6 +278,24 @@ __device__ inline void cayley_grid(const double N[3], const double W[3], const I
     d[2] = rg(k * fma(-aa, N[2], b2));
 }
 
+// round(a ma 2^-sa + b mb 2^-sb) to the nearest integer, ties to even, from
+// the exact 128-bit sum of the two products, aligned to the larger scale
+// (the host keeps the alignment inside 128 bits: ou_int); integer pipes.
+__device__ inline long long mul2_round(long long a, long long ma, int sa, long long b, long long mb, int sb) {
+    __int128 pa = (__int128)a * ma, pb = (__int128)b * mb;
+    int s = sa;
+    // (shifts on the two's-complement bits)
+    if (sb > sa) { pa = (__int128)((unsigned __int128)pa << (sb - sa)); s = sb; }
+    else if (sa > sb) pb = (__int128)((unsigned __int128)pb << (sa - sb));
+    const __int128 t = pa + pb;
+    const bool neg = t < 0;
+    const unsigned __int128 u = neg ? (unsigned __int128)(-t) : (unsigned __int128)t;
+    unsigned __int128 r = u >> s;
+    const unsigned __int128 rem = u - (r << s), half = (unsigned __int128)1 << (s - 1);
+    if (rem > half || (rem == half && (r & 1))) r++;
+    return neg ? -(long long)r : (long long)r;
+}
+
 // The noise's integer part 2 (w - 2^31) + 1 (exact); the factor
 // sqrt(12) 2^-33 is folded into the host constants stn_d and srn_d.
 __device__ inline double noise_int(unsigned w) {
@@ -302,11 +320,8 @@ __device__ inline void baoa_d_body(const View& v, const View& o, int p, const lo
     // (final B of the previous step), B
     kick_grid(vq, wq, Nd, lipid, I, FUSED ? 2 : 1, F, Tq);
     // A
-    double Vd[3], Wd[3] = {0.0, 0.0, 0.0};
-    for (int a = 0; a < 3; a++) {
-        Vd[a] = gd(vq[a]);
-        xq[a] += mul_round(vq[a], I.hdt_m, I.hdt_s);
-    }
+    double Wd[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < 3; a++) xq[a] += mul_round(vq[a], I.hdt_m, I.hdt_s);
     if (lipid) {
         for (int a = 0; a < 3; a++) Wd[a] = gd(wq[a]);
         long long d[3];
@@ -318,8 +333,12 @@ __device__ inline void baoa_d_body(const View& v, const View& o, int p, const lo
     const unsigned long long step = (unsigned long long)steps[b] + (FUSED ? 1ull : 0ull);
     const uint2 key = make_uint2((unsigned)I.seed, (unsigned)(I.seed >> 32) ^ I.instance);
     const uint4 w0 = philox4x32_10(make_uint4(id, (unsigned)step, (unsigned)(step >> 32), 0u), key);
-    const double xi[3] = {noise_int(w0.x), noise_int(w0.y), noise_int(w0.z)};
-    for (int a = 0; a < 3; a++) vq[a] += rg(fma(I.ct_m1_d, Vd[a], I.stn_d * xi[a]));
+    const unsigned wv[3] = {w0.x, w0.y, w0.z};
+    for (int a = 0; a < 3; a++) {
+        const long long sn = 2 * (long long)(int)(wv[a] ^ 0x80000000u) + 1;   // the noise's exact integer
+        vq[a] += I.ou_int ? mul2_round(vq[a], I.ctm1_m, I.ctm1_s, sn, I.stn_m, I.stn_s)
+                          : rg(fma(I.ct_m1_d, gd(vq[a]), I.stn_d * (double)sn));
+    }
     if (lipid) {
         const uint4 w1 = philox4x32_10(make_uint4(id, (unsigned)step, (unsigned)(step >> 32), 1u), key);
         // the noise scaled by sr first: its projection is linear

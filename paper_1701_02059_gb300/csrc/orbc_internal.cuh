@@ -87,6 +87,12 @@ struct Inst {
     // exactly and round once
     unsigned long long hm8_m, hdt_m;
     int hm8_s, hdt_s;
+    // the Ornstein-Uhlenbeck update of v, round(ct_m1 v + stn xi), as the
+    // exact sum of two integer products (ctm1_m 2^-ctm1_s, stn_m 2^-stn_s,
+    // signed) when the two scales are close enough for a 128-bit sum
+    // (ou_int), else in FP64
+    long long ctm1_m, stn_m;
+    int ctm1_s, stn_s, ou_int;
     // st and sr 2^40 times the noise's scale sqrt(12) 2^-33 (multiplying the
     // noise's exact integer part)
     double stn_d, srn_d;
