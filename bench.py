@@ -612,7 +612,7 @@ def run_reference(args, rank, world):
 
 
 # revisions of the kernels whose ncu summaries are committed under profiles/
-KERNEL_REV = {"k_pair_search": "search-v7", "k_pair_eval": "eval-v4", "k_baoa_d": "baoa-d-v6"}
+KERNEL_REV = {"k_pair_search": "search-v7", "k_pair_eval": "eval-v4", "k_baoa_d": "baoa-d-v7"}
 
 
 def ensemble_jobs(n_instances: int, steps: int):

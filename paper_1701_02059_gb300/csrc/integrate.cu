@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 4) k_baoa(View v, co
 }
 
 template <bool FUSED>
-__global__ void __launch_bounds__(256, 2) k_baoa_d(View v, const long long* __restrict__ steps,
+__global__ void __launch_bounds__(256, 3) k_baoa_d(View v, const long long* __restrict__ steps,
                                                    long long* __restrict__ msum, int* __restrict__ mcnt) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= v.N) return;
