@@ -508,6 +508,41 @@ ORBC_API int orbc_arena_admit(orbc_arena* a, const orbc_params* params, int n, c
                               const double* ori, const double* angvel, const unsigned char* type, const unsigned* id,
                               int nb, const int* ij, const double* r0, const double* kb, long long nsteps, int* slot);
 
+/* One request of orbc_arena_admit_many: orbc_arena_admit's arguments. */
+typedef struct orbc_arena_request {
+    const orbc_params* params;
+    int n;
+    const double* pos;
+    const double* vel;
+    const double* ori;
+    const double* angvel;
+    const unsigned char* type;
+    const unsigned* id;
+    int nb;
+    const int* ij;
+    const double* r0;
+    const double* kb;
+    long long nsteps;
+} orbc_arena_request;
+
+/* Admits req[0..count) in order, as orbc_arena_admit would one after the
+ * other, with up to `threads` of them (<= 0: 8; at most 16) validated,
+ * quantised and initialised at once on host threads of the library, each
+ * with a CUDA stream of its own.  The budget test is orbc_arena_admit's,
+ * taken in request order: a request's initialisation starts only when it
+ * fits beside the admitted instances and the initialisations under way
+ * ahead of it, and it is refused only when it does not fit once every
+ * request ahead of it is admitted.  Stops at the first request that fails:
+ * *admitted receives the number admitted (always a prefix of req), slots[k]
+ * the slot of request k (-1 from *admitted on), and the return value is the
+ * failing request's error (ORBC_OK when all were admitted); initialisations
+ * of later requests already under way are discarded.  The caller keeps its
+ * arrays; calls on one arena must not overlap.
+ * Errors: ORBC_E_NOMEM (budget), ORBC_E_ARG (null req, slots or admitted,
+ * count < 0, or a request's own argument errors), ORBC_E_STATE, ORBC_E_CUDA. */
+ORBC_API int orbc_arena_admit_many(orbc_arena* a, const orbc_arena_request* req, int count, int threads, int* slots,
+                                   int* admitted);
+
 /* Re-packs the batch if instances were admitted or finished, then advances
  * every resident instance by s = min(max_steps, fewest steps any of them has
  * left) steps (use_graphs != 0: replay of a captured step).  Instances that
@@ -536,6 +571,11 @@ ORBC_API int orbc_arena_poll(orbc_arena* a, int* done_slots, int cap, int* ndone
  * Errors: ORBC_E_ARG (slot not finished), ORBC_E_CUDA. */
 ORBC_API int orbc_arena_retire(orbc_arena* a, int slot, double* pos, double* vel, double* ori, double* angvel,
                                long long* step);
+
+/* HBM bytes slot `slot` holds against the budget (its share of the batch
+ * and, while it waits or has finished, its snapshot): 0 for a free slot.
+ * Errors: ORBC_E_ARG (null handle or bytes, slot out of range). */
+ORBC_API int orbc_arena_slot_bytes(const orbc_arena* a, int slot, unsigned long long* bytes);
 
 /* Counts of resident, pending (admitted, not yet packed) and finished
  * instances, resident particles and reserved bytes; each output nullable. */

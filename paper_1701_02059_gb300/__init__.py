@@ -361,6 +361,43 @@ class Arena:
         self.n_of_slot[slot.value] = len(arrs[4])
         return slot.value
 
+    def admit_many(self, items, threads: int = 8):
+        """Admit [(params, mem, nsteps), ...] in order, up to `threads`
+        initialised at once; returns the admitted prefix's slots.  When a
+        request fails, raises OrbcError for it with .slots = that prefix."""
+        from ._native import ArenaRequest
+        keep, reqs = [], (ArenaRequest * max(len(items), 1))()
+        for k, (params, mem, nsteps) in enumerate(items):
+            arrs = [np.ascontiguousarray(mem.pos, np.float64), np.ascontiguousarray(mem.vel, np.float64),
+                    np.ascontiguousarray(mem.ori, np.float64), np.ascontiguousarray(mem.angvel, np.float64),
+                    np.ascontiguousarray(mem.type, np.uint8), np.ascontiguousarray(mem.id, np.uint32),
+                    np.ascontiguousarray(mem.bonds, np.int32), np.ascontiguousarray(mem.r0, np.float64),
+                    np.ascontiguousarray(mem.kb, np.float64)]
+            keep.append((params, arrs))
+            r = reqs[k]
+            r.params = C.pointer(params)
+            r.n = len(arrs[4])
+            r.pos, r.vel, r.ori, r.angvel, r.type, r.id = (_p(a) for a in arrs[:6])
+            r.nb = len(arrs[7])
+            r.ij, r.r0, r.kb = _p(arrs[6]), _p(arrs[7]), _p(arrs[8])
+            r.nsteps = int(nsteps)
+        slots = np.full(max(len(items), 1), -1, np.int32)
+        done = C.c_int(0)
+        rc = self._L.orbc_arena_admit_many(self._h, reqs, len(items), int(threads), _p(slots), C.byref(done))
+        out = [int(x) for x in slots[:done.value]]
+        for k, s in enumerate(out):
+            self.n_of_slot[s] = reqs[k].n
+        if rc != 0:
+            e = OrbcError(rc, f"orbc_arena_admit_many: {self._L.orbc_arena_last_error(self._h).decode()}")
+            e.slots = out
+            raise e
+        return out
+
+    def slot_bytes(self, slot: int) -> int:
+        b = C.c_ulonglong(0)
+        self._check(self._L.orbc_arena_slot_bytes(self._h, int(slot), C.byref(b)), "orbc_arena_slot_bytes")
+        return b.value
+
     def run(self, max_steps: int, graphs: bool = True) -> int:
         s = C.c_int(0)
         self._check(self._L.orbc_arena_run(self._h, int(max_steps), 1 if graphs else 0, C.byref(s)), "orbc_arena_run")

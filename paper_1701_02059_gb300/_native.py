@@ -23,7 +23,7 @@ EXPORTS = [
     "orbc_rebuild_cells", "orbc_compute_forces", "orbc_integrate", "orbc_get_state", "orbc_get_forces",
     "orbc_get_cells", "orbc_get_adjacency_len", "orbc_dump_pairs", "orbc_set_timing", "orbc_set_wait_test", "orbc_get_kernel_times",
     "orbc_get_launch_count", "orbc_last_error", "orbc_destroy", "orbc_cell_sort", "orbc_cell_sort_noalloc",
-    "orbc_arena_create", "orbc_arena_admit", "orbc_arena_run", "orbc_arena_poll", "orbc_arena_retire",
+    "orbc_arena_create", "orbc_arena_admit", "orbc_arena_admit_many", "orbc_arena_slot_bytes", "orbc_arena_run", "orbc_arena_poll", "orbc_arena_retire",
     "orbc_arena_info", "orbc_arena_launch_count", "orbc_arena_last_error", "orbc_arena_destroy",
     "orbc_autotune", "orbc_arena_stats", "orbc_set_particles_device", "orbc_get_state_device",
     "orbc_get_forces_device", "orbc_default_mesh_params", "orbc_mesh_build", "orbc_quench",
@@ -45,6 +45,13 @@ class Params(C.Structure):
                 ("skin", C.c_double), ("grid_h", C.c_double), ("seed", C.c_ulonglong), ("instance", C.c_uint),
                 ("precision", C.c_int), ("n_protein_centroids", C.c_int), ("eval_ctas", C.c_int),
                 ("eps_mem", (C.c_double * 3) * 3), ("rc_mem", (C.c_double * 3) * 3)]
+
+
+class ArenaRequest(C.Structure):
+    """orbc_arena_request: one request of orbc_arena_admit_many."""
+    _fields_ = [("params", C.POINTER(Params)), ("n", C.c_int), ("pos", C.c_void_p), ("vel", C.c_void_p),
+                ("ori", C.c_void_p), ("angvel", C.c_void_p), ("type", C.c_void_p), ("id", C.c_void_p),
+                ("nb", C.c_int), ("ij", C.c_void_p), ("r0", C.c_void_p), ("kb", C.c_void_p), ("nsteps", C.c_longlong)]
 
 
 class MeshParams(C.Structure):
@@ -108,6 +115,8 @@ def load(path: str | None = None):
     L.orbc_arena_create.argtypes = [C.c_ulonglong, C.c_int, V, C.POINTER(V)]
     L.orbc_arena_admit.argtypes = [V, C.POINTER(Params), C.c_int, V, V, V, V, V, V, C.c_int, V, V, V,
                                    C.c_longlong, C.POINTER(C.c_int)]
+    L.orbc_arena_admit_many.argtypes = [V, C.POINTER(ArenaRequest), C.c_int, C.c_int, V, C.POINTER(C.c_int)]
+    L.orbc_arena_slot_bytes.argtypes = [V, C.c_int, C.POINTER(C.c_ulonglong)]
     L.orbc_arena_run.argtypes = [V, C.c_int, C.c_int, C.POINTER(C.c_int)]
     L.orbc_arena_poll.argtypes = [V, V, C.c_int, C.POINTER(C.c_int)]
     L.orbc_arena_retire.argtypes = [V, C.c_int, V, V, V, V, C.POINTER(C.c_longlong)]

@@ -11,7 +11,11 @@
 
 #include <algorithm>
 #include <chrono>
+#include <condition_variable>
 #include <memory>
+#include <mutex>
+#include <system_error>
+#include <thread>
 
 namespace orbc {
 
@@ -251,7 +255,9 @@ static size_t instance_bytes_lower_bound(const HostInstance& h) {
 class Arena {
 public:
     Arena(size_t budget, int precision, cudaStream_t st, bool own) :
-        budget_(budget), precision_(precision), stream_(st), own_stream_(own) {}
+        budget_(budget), precision_(precision), stream_(st), own_stream_(own) {
+        CK(cudaGetDevice(&device_));
+    }
     ~Arena() {
         batch_.reset();
         slots_.clear();
@@ -266,33 +272,30 @@ public:
         return s;
     }
 
-    int admit(HostInstance& h, long long nsteps) {
-        if (nsteps < 1) throw ArgError("nsteps must be >= 1");
-        if (h.prm.precision != precision_) throw ArgError("instance precision differs from the arena's");
-        if (h.prm.rebuild_every != 1) throw ArgError("arena instances rebuild their cells every step");
-        if (h.prm.n_centroids > (int)h.n) throw ArgError("more centroids than particles");
-        // refuse from the sizes alone, before any device allocation, when the
-        // arrays every set-up allocates already exceed the budget (the same
-        // test as after the set-up, on a lower bound of its bytes); the exact
-        // check follows the set-up
-        const size_t lb = instance_bytes_lower_bound(h);
-        if (reserved() + lb + lb / 2 > budget_) throw CudaError(cudaErrorMemoryAllocation, "over the HBM budget");
-        // a batch of one initialises the instance exactly as a plain system does
+    static CudaError over_budget() { return CudaError(cudaErrorMemoryAllocation, "over the HBM budget"); }
+
+    // Set-up, k-means initialisation and first forces of one instance on
+    // stream st, carried out to a snapshot (a batch of one initialises the
+    // instance exactly as a plain system does).  fits(b) is called with the
+    // set-up's allocation once it is known and throws when that is over the
+    // budget; *bytes receives the set-up's and the snapshot's bytes.
+    template <typename Fits>
+    std::unique_ptr<Snapshot> prepare(HostInstance& h, cudaStream_t st, size_t* bytes, Fits&& fits) {
         auto snap = std::make_unique<Snapshot>();
-        size_t bytes = 0;
-        {
-            Ensemble e(stream_);
-            e.setup(h);
-            bytes = e.bytes_allocated();
-            if (reserved() + bytes + bytes / 2 > budget_) throw CudaError(cudaErrorMemoryAllocation, "over the HBM budget");
-            e.init_cells();
-            e.compute_forces(false);
-            const unsigned st = e.read_status(true);
-            if (st) throw StateError("instance initialisation flagged status " + std::to_string(st));
-            e.export_instance(0, *snap);
-        }
-        bytes += snap->bytes;
-        if (reserved() + bytes > budget_) throw CudaError(cudaErrorMemoryAllocation, "over the HBM budget");
+        Ensemble e(st);
+        e.setup(h);
+        *bytes = e.bytes_allocated();
+        fits(*bytes);
+        e.init_cells();
+        e.compute_forces(false);
+        const unsigned status = e.read_status(true);
+        if (status) throw StateError("instance initialisation flagged status " + std::to_string(status));
+        e.export_instance(0, *snap);
+        *bytes += snap->bytes;
+        return snap;
+    }
+
+    int commit(HostInstance& h, long long nsteps, std::unique_ptr<Snapshot> snap, size_t bytes) {
         int slot = -1;
         for (int i = 0; i < (int)slots_.size(); i++)
             if (slots_[i].state == ArenaSlot::kFree) { slot = i; break; }
@@ -304,13 +307,158 @@ public:
         S.bytes = bytes;
         S.n = h.n;
         S.snap = std::move(snap);
-        S.bonds = h.bonds;
-        S.r0 = h.r0;
-        S.kb = h.kb;
+        S.bonds = std::move(h.bonds);
+        S.r0 = std::move(h.r0);
+        S.kb = std::move(h.kb);
         dirty_ = true;
         return slot;
     }
 
+    // Checks of an admission that need neither the device nor the budget.
+    void precheck(const HostInstance& h, long long nsteps) const {
+        if (nsteps < 1) throw ArgError("nsteps must be >= 1");
+        if (h.prm.precision != precision_) throw ArgError("instance precision differs from the arena's");
+        if (h.prm.rebuild_every != 1) throw ArgError("arena instances rebuild their cells every step");
+        if (h.prm.n_centroids > (int)h.n) throw ArgError("more centroids than particles");
+    }
+
+    int admit(HostInstance& h, long long nsteps) {
+        precheck(h, nsteps);
+        // refuse from the sizes alone, before any device allocation, when the
+        // arrays every set-up allocates already exceed the budget (the same
+        // test as after the set-up, on a lower bound of its bytes); the exact
+        // check follows the set-up
+        const size_t lb = instance_bytes_lower_bound(h);
+        if (reserved() + lb + lb / 2 > budget_) throw over_budget();
+        size_t bytes = 0;
+        auto snap = prepare(h, stream_, &bytes, [&](size_t b) {
+            if (reserved() + b + b / 2 > budget_) throw over_budget();
+        });
+        if (reserved() + bytes > budget_) throw over_budget();
+        return commit(h, nsteps, std::move(snap), bytes);
+    }
+
+    // Admits requests 0..count-1 in order with up to `threads` set-ups under
+    // way at once, each on a stream of its own.  make(k) builds request k's
+    // host instance (validation and quantisation, also in the workers).  The
+    // budget tests are admit()'s, taken in request order: a set-up starts
+    // when the committed instances, the set-ups under way and its own lower
+    // bound fit, waits while set-ups ahead of it may still free room, and is
+    // refused once none is ahead; a later request never takes room an
+    // earlier one needs.  Stops at the first request that fails: returns its
+    // index (count when all were admitted) with its code and message, and
+    // discards the set-ups of the requests after it.
+    template <typename Make>
+    int admit_many(int count, int threads, Make&& make, const long long* nsteps, int* slots, int* code,
+                   std::string* msg) {
+        struct Cancelled {};
+        std::mutex mu;
+        std::condition_variable cv;
+        std::vector<size_t> held(count, 0);   // reservation of each set-up under way
+        int next = 0, gate = 0, committed = 0, failed = count;
+        *code = ORBC_OK;
+        // bytes held by the set-ups under way ahead of request k
+        auto ahead = [&](int k) {
+            size_t s = 0;
+            for (int j = committed; j < k; j++) s += held[j];
+            return s;
+        };
+        // waits until the committed instances, the set-ups ahead of k and
+        // need fit; refuses once every request ahead of k is committed
+        auto wait_for_room = [&](std::unique_lock<std::mutex>& lk, int k, size_t need) {
+            for (;;) {
+                if (failed < k) throw Cancelled{};
+                if (reserved() + ahead(k) + need <= budget_) return;
+                if (committed == k) throw over_budget();
+                cv.wait(lk);
+            }
+        };
+        auto worker = [&] {
+            cudaStream_t st = nullptr;
+            if (cudaSetDevice(device_) != cudaSuccess || cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                std::lock_guard<std::mutex> lk(mu);
+                // a request this worker would have taken fails with the
+                // CUDA error; others already taken finish
+                if (next < count && next < failed) {
+                    failed = next;
+                    *code = ORBC_E_CUDA;
+                    *msg = "could not create an admission stream";
+                }
+                cv.notify_all();
+                return;
+            }
+            for (;;) {
+                int k;
+                {
+                    std::lock_guard<std::mutex> lk(mu);
+                    if (next >= count || next > failed) break;
+                    k = next++;
+                }
+                std::string err;
+                const int rc = guarded_call(&err, [&] {
+                    try {
+                        HostInstance h = make(k);
+                        precheck(h, nsteps[k]);
+                        const size_t lb = instance_bytes_lower_bound(h);
+                        {
+                            std::unique_lock<std::mutex> lk(mu);
+                            cv.wait(lk, [&] { return gate == k || failed < k; });
+                            try {
+                                wait_for_room(lk, k, lb + lb / 2);
+                            } catch (...) {
+                                gate = k + 1;
+                                cv.notify_all();
+                                throw;
+                            }
+                            held[k] = lb + lb / 2;
+                            gate = k + 1;
+                            cv.notify_all();
+                        }
+                        size_t bytes = 0;
+                        auto snap = prepare(h, st, &bytes, [&](size_t b) {
+                            std::unique_lock<std::mutex> lk(mu);
+                            wait_for_room(lk, k, b + b / 2);
+                            held[k] = b + b / 2;
+                        });
+                        std::unique_lock<std::mutex> lk(mu);
+                        cv.wait(lk, [&] { return committed == k || failed < k; });
+                        if (failed < k) throw Cancelled{};
+                        held[k] = 0;
+                        if (reserved() + bytes > budget_) throw over_budget();
+                        snap->stream = stream_;   // released later on the arena's stream
+                        slots[k] = commit(h, nsteps[k], std::move(snap), bytes);
+                        committed = k + 1;
+                        cv.notify_all();
+                    } catch (const Cancelled&) {
+                    }
+                });
+                std::lock_guard<std::mutex> lk(mu);
+                held[k] = 0;
+                if (rc != ORBC_OK && k < failed) {
+                    failed = k;
+                    *code = rc;
+                    *msg = err;
+                }
+                if (gate == k && rc != ORBC_OK) gate = k + 1;
+                cv.notify_all();
+            }
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        };
+        threads = std::max(1, std::min(threads, count));
+        std::vector<std::thread> pool;
+        try {
+            for (int t = 1; t < threads; t++) pool.emplace_back(worker);
+        } catch (const std::system_error&) {
+            // fewer workers: the ones started and this thread take every request
+        }
+        worker();
+        for (auto& t : pool) t.join();
+        return std::min(failed, committed);
+    }
+
+    // Steps every resident instance by min(max_steps, fewest steps left).
     // Steps every resident instance by min(max_steps, fewest steps left).
     int run(int max_steps, bool graphs) {
         if (max_steps < 1) throw ArgError("max_steps must be >= 1");
@@ -431,6 +579,12 @@ public:
         if (bytes) *bytes = (unsigned long long)reserved();
     }
 
+    // HBM bytes a slot holds against the budget (-1: no such slot).
+    long long slot_bytes(int slot) const {
+        if (slot < 0 || slot >= (int)slots_.size()) return -1;
+        return slots_[slot].state == ArenaSlot::kFree ? 0 : (long long)slots_[slot].bytes;
+    }
+
     long long launches() const { return launches_ + (batch_ ? batch_->launches : 0); }
     unsigned last_status_ = 0;
     std::string err;
@@ -477,6 +631,7 @@ private:
     int precision_;
     cudaStream_t stream_;
     bool own_stream_;
+    int device_ = 0;
     std::unique_ptr<Ensemble> batch_;
     std::vector<int> batch_slot_;
     std::vector<ArenaSlot> slots_;
@@ -539,6 +694,36 @@ int orbc_arena_admit(orbc_arena* h, const orbc_params* params, int n, const doub
     });
 }
 
+int orbc_arena_admit_many(orbc_arena* h, const orbc_arena_request* req, int count, int threads, int* slots,
+                          int* admitted) {
+    if (!h || count < 0 || (count > 0 && (!req || !slots)) || !admitted) return ORBC_E_ARG;
+    *admitted = 0;
+    for (int k = 0; k < count; k++) slots[k] = -1;
+    if (count == 0) return ORBC_OK;
+    std::vector<long long> nsteps(count);
+    for (int k = 0; k < count; k++) nsteps[k] = req[k].nsteps;
+    int code = ORBC_OK;
+    std::string msg;
+    const int rc = guarded_call(&h->err, [&] {
+        *admitted = h->a->admit_many(
+            count, threads <= 0 ? 8 : std::min(threads, 16),
+            [&](int k) {
+                const orbc_arena_request& r = req[k];
+                if (!r.params) throw ArgError("request without parameters");
+                Params P = to_params(r.params);
+                check_params(P);
+                if (P.n_protein_centroids > 0) throw ArgError("the arena takes no separate protein cells");
+                HostInstance inst = host_instance(P, r.n, r.pos, r.vel, r.ori, r.angvel, r.type, r.id);
+                host_bonds(inst, r.nb, r.ij, r.r0, r.kb);
+                return inst;
+            },
+            nsteps.data(), slots, &code, &msg);
+    });
+    if (rc != ORBC_OK) return rc;
+    if (code != ORBC_OK) h->err = "request " + std::to_string(*admitted) + ": " + msg;
+    return code;
+}
+
 int orbc_arena_run(orbc_arena* h, int max_steps, int use_graphs, int* steps_done) {
     if (!h) return ORBC_E_ARG;
     if (steps_done) *steps_done = 0;
@@ -570,6 +755,14 @@ int orbc_arena_info(const orbc_arena* h, int* resident, int* pending, int* done,
                     unsigned long long* bytes_reserved) {
     if (!h) return ORBC_E_ARG;
     h->a->info(resident, pending, done, particles, bytes_reserved);
+    return ORBC_OK;
+}
+
+int orbc_arena_slot_bytes(const orbc_arena* h, int slot, unsigned long long* bytes) {
+    if (!h || !bytes) return ORBC_E_ARG;
+    const long long b = h->a->slot_bytes(slot);
+    if (b < 0) return ORBC_E_ARG;
+    *bytes = (unsigned long long)b;
     return ORBC_OK;
 }
 

@@ -24,7 +24,7 @@ def _percentiles(lat):
 
 
 def serve_batched(jobs, hbm_budget_bytes: int, max_steps: int = 50, graphs: bool = True, keep_states: bool = False,
-                  precision: int = F32_FORCE_F64_STATE, stream: int | None = None):
+                  precision: int = F32_FORCE_F64_STATE, stream: int | None = None, admit_threads: int = 8):
     """Continuous batching: requests are admitted as they arrive and as the
     budget allows, every resident request advances in one batched launch per
     phase, finished ones are retired.  Returns per-job records (latency =
@@ -41,28 +41,32 @@ def serve_batched(jobs, hbm_budget_bytes: int, max_steps: int = 50, graphs: bool
     mem_stats = {"peak_reserved_bytes": 0, "largest_request_bytes": 0, "budget_refusals": 0}
     while waiting or slot_job:
         now = time.perf_counter() - t0
-        # admit everything that has arrived, in arrival order, while it fits
-        while waiting and jobs[waiting[0]]["arrival_s"] <= now:
-            i = waiting[0]
+        # admit everything that has arrived, in arrival order, while it fits;
+        # the library initialises up to admit_threads of them at once
+        arrived = []
+        while len(arrived) < len(waiting) and jobs[waiting[len(arrived)]]["arrival_s"] <= now:
+            arrived.append(waiting[len(arrived)])
+        if arrived:
             ta = time.perf_counter()
-            before = arena.info()["bytes"]
+            refused = None
             try:
-                s = arena.admit(jobs[i]["params"], jobs[i]["mem"], jobs[i]["steps"])
-                spent["admit_s"] += time.perf_counter() - ta
+                slots = arena.admit_many([(jobs[i]["params"], jobs[i]["mem"], jobs[i]["steps"]) for i in arrived],
+                                         admit_threads)
             except OrbcError as e:
-                spent["admit_s"] += time.perf_counter() - ta
                 if e.code != ORBC_E_NOMEM:
                     raise
+                slots, refused = e.slots, e
+            spent["admit_s"] += time.perf_counter() - ta
+            for i, s in zip(arrived, slots):
+                mem_stats["largest_request_bytes"] = max(mem_stats["largest_request_bytes"], arena.slot_bytes(s))
+                slot_job[s] = i
+                waiting.pop(0)
+                rec[i] = {"arrival_s": jobs[i]["arrival_s"], "admitted_s": time.perf_counter() - t0}
+            mem_stats["peak_reserved_bytes"] = max(mem_stats["peak_reserved_bytes"], arena.info()["bytes"])
+            if refused is not None:
                 mem_stats["budget_refusals"] += 1
                 if not slot_job:
-                    raise RuntimeError(f"request {i} does not fit the HBM budget on an empty GPU") from e
-                break
-            after = arena.info()["bytes"]
-            mem_stats["peak_reserved_bytes"] = max(mem_stats["peak_reserved_bytes"], after)
-            mem_stats["largest_request_bytes"] = max(mem_stats["largest_request_bytes"], after - before)
-            slot_job[s] = i
-            waiting.pop(0)
-            rec[i] = {"arrival_s": jobs[i]["arrival_s"], "admitted_s": time.perf_counter() - t0}
+                    raise RuntimeError(f"request {waiting[0]} does not fit the HBM budget on an empty GPU") from refused
         if slot_job:
             tr = time.perf_counter()
             arena.run(max_steps, graphs)

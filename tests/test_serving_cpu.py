@@ -52,6 +52,21 @@ class _FakeArena:
         _FakeArena.log.append(("admit", params, self.used))
         return s
 
+    def admit_many(self, items, threads=4):
+        # the library's contract: an admitted prefix, then the first
+        # failure raised with the prefix's slots
+        slots = []
+        for params, mem, nsteps in items:
+            try:
+                slots.append(self.admit(params, mem, nsteps))
+            except serving.OrbcError as e:
+                e.slots = slots
+                raise
+        return slots
+
+    def slot_bytes(self, s):
+        return self.size.get(s, 0)
+
     def run(self, max_steps, graphs=True):
         k = min(min(self.left.values()), max_steps)
         for s in self.left:
