@@ -69,6 +69,11 @@ __global__ void k_slot_of_id(View v) {
 
 static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
+// defined with the plain system's getters: int64 fixed point of a slot range
+// to FP64 [n][3] in id order
+__global__ void k_to_id_order(const unsigned* __restrict__ id, const long long* __restrict__ q, size_t N, int p0, int n,
+                              double unit, double* __restrict__ out);
+
 static void d2d(void* dst, const void* src, size_t bytes, cudaStream_t st) {
     if (bytes) CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st));
 }
@@ -546,18 +551,25 @@ public:
         ArenaSlot& S = slots_[slot];
         const Snapshot& s = *S.snap;
         const int n = s.n;
-        std::vector<unsigned> ids(n);
-        std::vector<long long> buf((size_t)3 * n);
-        CK(cudaMemcpyAsync(ids.data(), s.id, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, stream_));
+        // to FP64 in id order on the device, then one copy per array
         double* outs[4] = {pos, vel, ori, angvel};
-        for (int q = 0; q < 4; q++) {
-            if (!outs[q]) continue;
-            CK(cudaMemcpyAsync(buf.data(), s.state[q], sizeof(long long) * 3 * n, cudaMemcpyDeviceToHost, stream_));
+        double* tmp = nullptr;
+        CK(cudaMallocAsync(&tmp, sizeof(double) * 12 * (size_t)std::max(n, 1), stream_));
+        try {
+            for (int q = 0; q < 4; q++) {
+                if (!outs[q]) continue;
+                double* t = tmp + (size_t)3 * q * n;
+                k_to_id_order<<<nblk(n, 256), 256, 0, stream_>>>(s.id, s.state[q], (size_t)n, 0, n, kGridInv, t);
+                launches_++;
+                CK(cudaGetLastError());
+                CK(cudaMemcpyAsync(outs[q], t, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost, stream_));
+            }
             CK(cudaStreamSynchronize(stream_));
-            for (int a = 0; a < 3; a++)
-                for (int i = 0; i < n; i++) outs[q][(size_t)3 * ids[i] + a] = (double)buf[(size_t)a * n + i] * kGridInv;
+        } catch (...) {
+            cudaFreeAsync(tmp, stream_);
+            throw;
         }
-        CK(cudaStreamSynchronize(stream_));
+        CK(cudaFreeAsync(tmp, stream_));
         if (step) *step = s.step;
         S.snap.reset();
         S.state = ArenaSlot::kFree;
