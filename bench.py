@@ -409,20 +409,25 @@ def run_ours(args, rank, world):
         h2d = sum(a.nbytes for a in (pmem.pos, pmem.vel, pmem.ori, pmem.angvel, pmem.type, pmem.id, pmem.bonds,
                                      pmem.r0, pmem.kb))
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record(stream)
         g2 = G.System(params_for(mem, args.precision, G), stream=stream.cuda_stream)
         g2.load_membrane(pmem)
+        ev[1].record(stream)
         g2.init_cells()
+        ev[2].record(stream)
         g2.integrate(args.steps)
+        ev[3].record(stream)
         st = g2.state(out=pout)
-        e1.record(stream)
+        ev[4].record(stream)
         torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1)
+        ems = ev[0].elapsed_time(ev[4])
+        phases = {k: round(ev[i].elapsed_time(ev[i + 1]), 2)
+                  for i, k in enumerate(("upload_ms", "init_cells_ms", "steps_ms", "read_back_ms"))}
         d2h = sum(st[k].nbytes for k in ("pos", "vel", "ori", "angvel"))
         e2e = {"value": mem.n * args.steps * world / (ems * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-               "includes": "upload, k-means initialisation, steps, state read-back",
+               "includes": "upload, k-means initialisation, steps, state read-back", "phases": phases,
                "host_buffers": "page-locked (allocated before the timed region)"}
         g2.close()
 
