@@ -1069,7 +1069,9 @@ constexpr float kBandR = 1e-5f;
 // Gather of the cell-sorted state, one thread per new slot p: the particle
 // of old slot perm[p] moves with its state, type and id, learns its new cell
 // (the E-step's result for the old slot) and gets its exact mirror relative
-// to that cell's centroid.
+// to that cell's centroid.  Every load and the mirror come before the first
+// store: as far as the compiler knows the stores may alias the sources, and
+// interleaved they would serialise the loads' latencies.
 __global__ void __launch_bounds__(256) k_gather_particles(View v, View o, const int* __restrict__ perm,
                                                           const int* __restrict__ cell_new,
                                                           long long* __restrict__ xref) {
@@ -1078,35 +1080,40 @@ __global__ void __launch_bounds__(256) k_gather_particles(View v, View o, const 
     const size_t N = v.N;
     const int so = perm[p];
     const int k = cell_new[so];
-    const int b = find_inst(v.inst_p0, v.B, p);
-    const Inst& I = v.inst[b];
-    long long x[3], nq[3];
+    long long x[3], vq[3], nq[3], wq[3];
     for (int a = 0; a < 3; a++) {
         x[a] = o.xq[a * N + so];
+        vq[a] = o.vq[a * N + so];
         nq[a] = o.nq[a * N + so];
-        v.xq[a * N + p] = x[a];
-        v.vq[a * N + p] = o.vq[a * N + so];
-        v.nq[a * N + p] = nq[a];
-        v.wq[a * N + p] = o.wq[a * N + so];
-        if (xref) xref[a * N + p] = x[a];
+        wq[a] = o.wq[a * N + so];
     }
     const unsigned char t = o.type[so];
     const unsigned id = o.id[so];
-    v.type[p] = t;
-    v.id[p] = id;
-    v.cell[p] = k;
-    v.slot_of_id[I.p0 + id] = p;
+    const int b = find_inst(v.inst_p0, v.B, p);
+    const Inst& I = v.inst[b];
     int4 m;
     m.x = mirror_coord(x[0], v.cq[k], I, 0, v);
     m.y = mirror_coord(x[1], v.cq[(size_t)v.Ktot + k], I, 1, v);
     m.z = mirror_coord(x[2], v.cq[(size_t)2 * v.Ktot + k], I, 2, v);
-    m.w = t | (v.bptr[I.p0 + id] < v.bptr[I.p0 + id + 1] ? kMirrorBonded : 0);
-    v.mq[p] = m;
+    const int q0 = I.p0 + (int)id;
+    m.w = t | (v.bptr[q0] < v.bptr[q0 + 1] ? kMirrorBonded : 0);
     float4 no;
     no.x = ll_to_float(nq[0]) * (float)kGridInv;
     no.y = ll_to_float(nq[1]) * (float)kGridInv;
     no.z = ll_to_float(nq[2]) * (float)kGridInv;
     no.w = __int_as_float(p);
+    for (int a = 0; a < 3; a++) {
+        v.xq[a * N + p] = x[a];
+        v.vq[a * N + p] = vq[a];
+        v.nq[a * N + p] = nq[a];
+        v.wq[a * N + p] = wq[a];
+        if (xref) xref[a * N + p] = x[a];
+    }
+    v.type[p] = t;
+    v.id[p] = id;
+    v.cell[p] = k;
+    v.slot_of_id[q0] = p;
+    v.mq[p] = m;
     v.mo[p] = no;
 }
 
