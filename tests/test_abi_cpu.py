@@ -92,6 +92,12 @@ def test_arena_null_handles_and_arguments_are_rejected(lib):
     assert L.orbc_arena_admit(None, C.byref(p), 1, None, None, None, None, None, None, 0, None, None, None, 1,
                               C.byref(slot)) == _native.ORBC_E_ARG
     assert L.orbc_arena_info(None, None, None, None, None, None) == _native.ORBC_E_ARG
+    done = C.c_int(3)
+    reqs = (_native.ArenaRequest * 1)()
+    slots = (C.c_int * 1)()
+    assert L.orbc_arena_admit_many(None, reqs, 1, 4, slots, C.byref(done)) == _native.ORBC_E_ARG
+    b = C.c_ulonglong(7)
+    assert L.orbc_arena_slot_bytes(None, 0, C.byref(b)) == _native.ORBC_E_ARG and b.value == 7
     assert L.orbc_arena_launch_count(None) == -1
     assert L.orbc_arena_stats(None, None, None, None, None) == _native.ORBC_E_ARG
     assert L.orbc_arena_last_error(None) == b"null handle"
