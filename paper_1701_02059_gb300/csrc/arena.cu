@@ -378,9 +378,12 @@ public:
                 cv.wait(lk);
             }
         };
-        auto worker = [&] {
+        // spawned workers make the arena's device current; the calling
+        // thread keeps its own current device, as every other arena call does
+        auto worker = [&](bool spawned) {
             cudaStream_t st = nullptr;
-            if (cudaSetDevice(device_) != cudaSuccess || cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            if ((spawned && cudaSetDevice(device_) != cudaSuccess) ||
+                cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
                 cudaGetLastError();
                 std::lock_guard<std::mutex> lk(mu);
                 // a request this worker would have taken fails with the
@@ -397,7 +400,7 @@ public:
                 int k;
                 {
                     std::lock_guard<std::mutex> lk(mu);
-                    if (next >= count || next > failed) break;
+                    if (next >= failed) break;   // failed <= count
                     k = next++;
                 }
                 std::string err;
@@ -454,11 +457,11 @@ public:
         threads = std::max(1, std::min(threads, count));
         std::vector<std::thread> pool;
         try {
-            for (int t = 1; t < threads; t++) pool.emplace_back(worker);
+            for (int t = 1; t < threads; t++) pool.emplace_back(worker, true);
         } catch (const std::system_error&) {
             // fewer workers: the ones started and this thread take every request
         }
-        worker();
+        worker(false);
         for (auto& t : pool) t.join();
         return std::min(failed, committed);
     }
