@@ -467,7 +467,6 @@ public:
     }
 
     // Steps every resident instance by min(max_steps, fewest steps left).
-    // Steps every resident instance by min(max_steps, fewest steps left).
     int run(int max_steps, bool graphs) {
         if (max_steps < 1) throw ArgError("max_steps must be >= 1");
         const auto t0 = std::chrono::steady_clock::now();
