@@ -117,3 +117,28 @@ def test_autotune_rejects_bad_arguments(lib):
                            None, None) == _native.ORBC_E_ARG                # no output
     assert L.orbc_autotune(C.byref(p), 4, None, None, None, None, None, None, 0, None, None, None, 5, None, C.byref(K),
                            None, None) == _native.ORBC_E_ARG                # null particle arrays
+
+
+def test_ctypes_mirrors_have_the_c_layout():
+    """Every struct the binding passes across the boundary has the size and
+    field offsets the C compiler gives the header's declaration."""
+    from paper_1701_02059_gb300 import _native
+    import tempfile
+    mirrors = {"orbc_params": _native.Params, "orbc_mesh_params": _native.MeshParams,
+               "orbc_arena_request": _native.ArenaRequest}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "orbc.h"', 'int main(void) {']
+    expect = []
+    for cname, ct in mirrors.items():
+        lines.append(f'    printf("%zu\\n", sizeof({cname}));')
+        expect.append(C.sizeof(ct))
+        for f in ct._fields_:
+            lines.append(f'    printf("%zu\\n", offsetof({cname}, {f[0]}));')
+            expect.append(getattr(ct, f[0]).offset)
+    lines += ['    return 0;', '}']
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "layout.c")
+        open(c, "w").write("\n".join(lines) + "\n")
+        exe = os.path.join(d, "layout")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == expect
